@@ -1,0 +1,204 @@
+/*
+ * d3m.h -- C ABI of the GB300 (sm_103a) D3M dual-system solver.
+ *
+ * The library factors and solves the reduced block-sparse dual matrix K of the Direct
+ * Domain Decomposition Method (D3M; Moshfegh, Makris, Vouvakis, "Parallel Direct Domain
+ * Decomposition Methods (D3M) for Finite Elements", IEEE AP-S/URSI 2019):
+ *   - Sec. I: the sparse FEM system is reduced to a block-wise sparse matrix K that is
+ *     solved by a special block LDL^T suited to block-DAG task scheduling;
+ *   - Sec. II: in the "dual factorization and solution" step every nonzero block of K is a
+ *     task doing a dense update, a dense triangular solve and a dense factorization; the
+ *     task graph (B-DAG) comes from a symbolic simulation of the sequential algorithm;
+ *     dual task weights come from GEMM, sytrf and triSolve;
+ *   - Fig. 1(b)/(c): the sparsity of K and its task graph.
+ * K is complex symmetric (K^T = K, not Hermitian) and indefinite.  The library computes
+ * the unpivoted factorization P K P^T = L D L^T (L unit lower, D diagonal) and solves
+ * K X = B by forward, diagonal and backward sweeps.
+ *
+ * Conventions shared by all calls
+ *   - complex numbers are interleaved (re, im) pairs: "c128" = 2 x double, "c64" = 2 x float;
+ *   - K is given by its LOWER block triangle in block-CSC order over the caller's (original)
+ *     interface numbering: column g holds rows rowidx[colptr[g] .. colptr[g+1]-1], strictly
+ *     ascending, the first one being g itself (diagonal block present); block (f, g) is an
+ *     m_f x m_g dense block stored column-major with leading dimension m_f; blocks follow
+ *     one another in that CSC order with no gaps;
+ *   - right-hand sides and solutions are n x nrhs column-major with leading dimension n,
+ *     n = sum_f m_f, rows in the caller's numbering;
+ *   - every pointer may be host or device memory unless a call says otherwise; host buffers
+ *     are copied by the library on the given stream;
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  No call synchronizes the
+ *     stream except d3m_get_info / d3m_get_factor_block / d3m_get_pivots and the refinement
+ *     loop inside d3m_solve, which reads one convergence word per iteration.
+ *
+ * Ownership: the caller owns every buffer it passes and the stream.  The library owns the
+ * factors, a copy of K (kept for the FP64 residual), the task graph and its workspaces, from
+ * d3m_create until d3m_destroy.  A handle is not thread-safe; use one per host thread.
+ *
+ * Errors: every int-returning call returns D3M_OK (0) or one of the D3M_ERR_* codes below;
+ * d3m_last_error(h) gives a one-line text for the last failing call on h.
+ */
+#ifndef D3M_H
+#define D3M_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct d3m_ctx* d3m_handle;
+
+enum {
+  D3M_OK = 0,
+  D3M_ERR_INVALID = 1,        /* bad pattern, permutation, option or argument */
+  D3M_ERR_OOM = 2,            /* device or host allocation failed */
+  D3M_ERR_CUDA = 3,           /* a CUDA runtime call failed (text in d3m_last_error) */
+  D3M_ERR_PIVOT = 4,          /* |d| below 1e3 * u * max|S_kk| in some diagonal block */
+  D3M_ERR_NOT_CONVERGED = 5,  /* refinement hit its cap or stagnated; best x is written */
+  D3M_ERR_TIMEOUT = 6,        /* a bounded device wait expired; the kernel returned */
+  D3M_ERR_STATE = 7           /* call out of order (e.g. solve before factor) */
+};
+
+/* Arithmetic of the factorization (d3m_options.precision). */
+enum {
+  D3M_FP64 = 0,          /* complex128 factors, FP64 SIMT tile engine, no refinement */
+  D3M_MIXED_BF16X3 = 1,  /* complex64 factors; Schur/TRSM products on tcgen05 tensor cores as
+                            split-BF16x3 (a = a_hi + a_lo; hi*hi + hi*lo + lo*hi) with FP32
+                            accumulation in TMEM; FP64 residual + iterative refinement */
+  D3M_MIXED_SIMT32 = 2   /* complex64 factors on an FP32 SIMT tile engine (no tensor cores);
+                            FP64 residual + iterative refinement */
+};
+
+typedef struct {
+  int32_t nblk;             /* N, number of interface blocks */
+  int32_t m;                /* uniform block size, used when blk_size == NULL */
+  const int32_t* blk_size;  /* [N] per-block sizes m_f (host), or NULL */
+  const int64_t* colptr;    /* [N+1] host, lower block-CSC column pointers */
+  const int32_t* rowidx;    /* [colptr[N]] host, row block indices */
+} d3m_pattern;
+
+typedef struct {
+  int32_t precision;        /* D3M_FP64 | D3M_MIXED_BF16X3 | D3M_MIXED_SIMT32 */
+  int32_t refine_max_iter;  /* cap on refinement steps (default 20) */
+  double refine_tol;        /* target normwise backward error omega (default 1e-12) */
+  int64_t timeout_ns;       /* bound on any device-side wait (default 5 s) */
+  int32_t tile;             /* tile edge; 0 = default (128 tensor-core, 64 SIMT) */
+  int32_t max_nrhs;         /* largest nrhs a solve may use (default 32) */
+  int32_t fp64_omega;       /* D3M_FP64 only: 1 = also compute omega after the solve
+                               (one FP64 residual; default 0) */
+  int32_t debug_flags;      /* D3M_DEBUG_* test hooks, 0 in normal use */
+} d3m_options;
+
+/* Test hook: upload the task graph with one extra unmet dependency on the last task, so the
+ * device queue starves and every waiting block hits the bounded wait (-> D3M_ERR_TIMEOUT). */
+#define D3M_DEBUG_STALL_LAST_TASK 1
+
+typedef struct {
+  int64_t n;                /* sum of block sizes */
+  int32_t nblk;             /* N */
+  int32_t tile;             /* tile edge b */
+  int64_t nnzb_K;           /* stored lower blocks of K */
+  int64_t nblk_L_offdiag;   /* off-diagonal blocks of L after fill */
+  int32_t etree_depth;      /* depth of the block elimination tree */
+  int32_t max_col_height;   /* max off-diagonal blocks in one column of L */
+  int64_t ntiles;           /* lower tiles of L (tasks of the factorization DAG) */
+  int64_t ntile_updates;    /* tile GEMM updates (K-list entries) */
+  int64_t ndep_edges;       /* edges of the tile task graph */
+  double factor_flops;      /* algorithmic flops of the block factorization (complex MAC = 8):
+                               N (4/3) m^3 + n_L 4 m^3 (TRSM) + n_L 4 m^3 + n_off 8 m^3 (updates) */
+  double solve_flops_per_rhs; /* 8 (2 nnz_offdiag(L) + sum m_k^2) + 6 n (forward + diagonal +
+                                 backward sweeps, complex MAC = 8) */
+  double residual_flops_per_rhs; /* 8 * entries of K (both triangles) */
+  int64_t device_bytes;     /* device memory owned by the handle */
+  /* last factor / solve (valid after d3m_get_info synchronizes) */
+  int32_t status;           /* status of the last factor or solve */
+  int32_t refine_iters;     /* solves done by the last d3m_solve / d3m_adjoint */
+  double omega;             /* max over columns of the final backward error (NaN if not computed) */
+  double omega_first;       /* backward error after the first (unrefined) solve */
+  double min_abs_pivot;     /* min |d| over all pivots of the last factorization */
+  double max_abs_pivot;     /* max |d| */
+  double factor_kernel_ms;  /* device time of the last factorization kernel (CUDA events) */
+  double solve_ms;          /* device time of the last d3m_solve / d3m_adjoint (events) */
+  double residual_ms;       /* device time in FP64 residual kernels of that solve */
+} d3m_info;
+
+/* Default options (precision D3M_MIXED_BF16X3). */
+void d3m_default_options(d3m_options* opt);
+
+/* Nested-dissection order of the interfaces of an nx x ny x nz domain grid (host only, no GPU).
+ * Interfaces are numbered in domain order (domain id (ix*ny + iy)*nz + iz), then axis x, y, z,
+ * one per pair of face neighbours.  The box is split along its longest extent (ties to the
+ * lower axis) at lo + floor(extent/2); the interfaces across the cut are ordered last in
+ * natural order; the lower half-box comes first; a box of extent 1 in every axis or with at
+ * most one interface keeps natural order.  perm[new] = old, length = number of interfaces.
+ * Returns D3M_ERR_INVALID for non-positive extents. */
+int d3m_order_grid_nd(int32_t nx, int32_t ny, int32_t nz, int32_t* perm);
+
+/* Symbolic analysis only (host, no GPU): fills the structural fields of `info` (n, nblk, tile,
+ * nnzb_K, nblk_L_offdiag, etree_depth, max_col_height, ntiles, ntile_updates, ndep_edges,
+ * factor_flops, solve_flops_per_rhs, residual_flops_per_rhs).  perm may be NULL (identity).
+ * This is the paper's symbolic simulation that yields the task graph (Sec. II). */
+int d3m_analyze(const d3m_pattern* pat, const int32_t* perm, int32_t tile, d3m_info* info);
+
+/* Create a solver for one pattern: validates the pattern and perm (perm[new] = old, NULL =
+ * identity), runs the symbolic analysis, builds the tile task graph and allocates every
+ * device buffer on the current device.  `opt` NULL = defaults. */
+int d3m_create(d3m_handle* out, const d3m_pattern* pat, const int32_t* perm,
+               const d3m_options* opt, void* stream);
+
+/* Numeric factorization.  K: c128 lower blocks as described above (host or device).  The
+ * library copies K, then runs one persistent kernel whose blocks pull ready tile tasks from
+ * a device queue with atomic dependency counters (Sec. II task model, Fig. 1(c)).
+ * D3M_ERR_PIVOT if a pivot falls below the breakdown threshold, D3M_ERR_TIMEOUT if a device
+ * wait expired.  Errors found on the device are returned by the next call that synchronizes
+ * (d3m_get_info) and by d3m_solve. */
+int d3m_factor(d3m_handle h, const void* K, void* stream);
+
+/* Solve K X = B for nrhs columns (1 <= nrhs <= max_nrhs).  B, X: c128, n x nrhs column-major
+ * (host or device; may not alias).  FP64 mode: one forward/diagonal/backward sweep.  Mixed
+ * modes: x = 0, r = b; repeat { d = solve_c64(r); x += d (FP64); r = b - K x (FP64, block
+ * SpMV over the stored K) } until max_col omega <= refine_tol or the cap; D3M_ERR_NOT_CONVERGED
+ * if the cap is hit or omega fails to halve over two steps (X then holds the best iterate). */
+int d3m_solve(d3m_handle h, const void* B, void* X, int32_t nrhs, void* stream);
+
+/* Adjoint solve with the same factors: K^T Lambda = G, which is K Lambda = G since K^T = K.
+ * Same refinement and layout as d3m_solve.  For J = Re(sum_j g_j^T x_j), Lambda gives
+ * dJ/db = conj(Lambda) (PyTorch convention dJ/dRe + i dJ/dIm). */
+int d3m_adjoint(d3m_handle h, const void* G, void* Lambda, int32_t nrhs, void* stream);
+
+/* dJ/deps_i = Re(k2 * sum_j sum_{u in unknowns of I(i)} Lambda_uj X_uj) for every domain i,
+ * where dK/deps_i = -k2 on the unknowns of the interfaces of domain i.  dom_ptr [ndom+1] and
+ * dom_if (host int32) list each domain's interfaces (caller numbering).  Lambda, X: device
+ * c128 n x nrhs.  dJ_deps: host double [ndom]; synchronizes the stream. */
+int d3m_grad_eps(d3m_handle h, const void* Lambda, const void* X, int32_t nrhs,
+                 int32_t ndom, const int32_t* dom_ptr, const int32_t* dom_if, double k2,
+                 double* dJ_deps, void* stream);
+
+/* Gradient of J = Re(sum_j g_j^T x_j) with respect to the stored lower blocks of K:
+ * dJ/dK_fg = -(Lambda_f X_g^T + [f != g] X_f Lambda_g^T), summed over columns (the outer
+ * product -Lambda X^T restricted to K's pattern; an off-diagonal stored block also stands
+ * for its transpose).  Output dK: device c128 in K's block layout (unconjugated). */
+int d3m_grad_pattern(d3m_handle h, const void* Lambda, const void* X, int32_t nrhs,
+                     void* dK, void* stream);
+
+/* Copy factor block L_ij (i >= j, NEW numbering; i == j gives the unit lower diagonal block)
+ * to host memory as c128, m_i x m_j column-major.  Returns D3M_ERR_INVALID if (i, j) is not
+ * in the filled pattern.  Synchronizes the stream. */
+int d3m_get_factor_block(d3m_handle h, int32_t i, int32_t j, void* host_out, void* stream);
+
+/* Copy the pivots D_j of block column j (NEW numbering) to host memory as c128 [m_j]. */
+int d3m_get_pivots(d3m_handle h, int32_t j, void* host_out, void* stream);
+
+/* Synchronizes the stream, then fills `info` (structure + the last factor/solve results). */
+int d3m_get_info(d3m_handle h, d3m_info* info, void* stream);
+
+/* Text of the last error on h (static string if h is NULL).  Never NULL. */
+const char* d3m_last_error(d3m_handle h);
+
+/* Frees every library-owned buffer.  Safe on NULL. */
+void d3m_destroy(d3m_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* D3M_H */

@@ -1,0 +1,746 @@
+// C ABI of the D3M dual-system solver (declarations and contracts in include/d3m.h).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "d3m.h"
+#include "device.cuh"
+#include "kernels.h"
+#include "symbolic.h"
+
+using namespace d3m;
+
+struct d3m_ctx {
+  Symbolic S;
+  d3m_options opt{};
+  bool fp64 = true, tc = false;
+  int b = 64;
+  int device = 0, nsm = 0;
+  size_t csize = 16;                 // bytes of one factor element
+  std::string err;
+  std::vector<void*> allocs;
+  int64_t dev_bytes = 0;
+  bool factored = false;
+  int last_status = D3M_OK;
+  int refine_iters = 0;
+  double omega = NAN, omega_first = NAN;
+  int omega_valid = 0;
+  float fact_ms = 0.f, solve_ms = 0.f, resid_ms = 0.f;
+  bool have_fact_ev = false, have_solve_ev = false;
+  cudaEvent_t ev_f0 = nullptr, ev_f1 = nullptr, ev_s0 = nullptr, ev_s1 = nullptr;
+  std::vector<cudaEvent_t> ev_res;   // pairs around residual kernels of the last solve
+  int nres_ev = 0;
+  // factor data
+  double2* K = nullptr;
+  TileTask* tasks = nullptr;
+  KEntry* klist = nullptr;
+  int32_t* ndeps = nullptr;
+  int32_t* cnt = nullptr;
+  int64_t* succ_ptr = nullptr;
+  int32_t* succ = nullptr;
+  int32_t* ready = nullptr;
+  int32_t* init_ready = nullptr;
+  Ctl* ctl = nullptr;
+  Ctl* ctl0 = nullptr;               // initial queue state, copied into ctl by every factor call
+  Ctl* h_ctl = nullptr;              // pinned copy of ctl after the factorization
+  void* L = nullptr;
+  void* Linv = nullptr;
+  void* D = nullptr;
+  void* opA = nullptr;
+  void* opB = nullptr;
+  TcMaps maps;
+  // solve
+  SolveItem* fwd_items = nullptr;
+  SolveItem* bwd_items = nullptr;
+  int64_t* fwd_slot = nullptr;
+  int64_t* bwd_slot = nullptr;
+  int32_t* lev_blocks = nullptr;
+  std::vector<int64_t> lev_ptr;
+  int32_t* tstart = nullptr;
+  int64_t* tcolptr = nullptr;
+  int64_t* pad2orig = nullptr;
+  void* Y = nullptr;
+  void* P = nullptr;
+  int max_rows = 0;
+  // refinement / residual
+  double2* d_b = nullptr;
+  double2* d_x = nullptr;
+  double2* d_xbest = nullptr;
+  double2* d_r = nullptr;
+  int64_t* kblk_off = nullptr;
+  int64_t* res_ptr = nullptr;
+  int32_t* res_blk = nullptr;
+  int32_t* res_src = nullptr;
+  int32_t* res_tr = nullptr;
+  int32_t* m_orig = nullptr;
+  int64_t* xoff_orig = nullptr;
+  int2* chunks = nullptr;
+  int nchunks = 0;
+  unsigned* norms = nullptr;         // [3 * max_nrhs + 1]: rmax, xmax, bmax, kmax
+  double* omega_dev = nullptr;       // [max_nrhs]
+  double* stat_dev = nullptr;        // [1]
+  double* h_stat = nullptr;          // pinned [1]
+  // gradients
+  int32_t* rowidx = nullptr;
+  int32_t* blk_col = nullptr;
+  int64_t* colptr = nullptr;
+  double2* contract = nullptr;
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+int set_err(d3m_ctx* h, int code, const std::string& msg) {
+  if (h) h->err = msg;
+  g_err = msg;
+  return code;
+}
+
+#define CUDA_TRY(h, call)                                                                   \
+  do {                                                                                      \
+    cudaError_t e_ = (call);                                                                \
+    if (e_ != cudaSuccess)                                                                  \
+      return set_err(h, D3M_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+template <typename T>
+T* dalloc(d3m_ctx* h, size_t count) {
+  if (count == 0) count = 1;
+  void* p = nullptr;
+  if (cudaMalloc(&p, count * sizeof(T)) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  h->allocs.push_back(p);
+  h->dev_bytes += (int64_t)(count * sizeof(T));
+  return (T*)p;
+}
+
+template <typename T>
+int upload(d3m_ctx* h, T** dst, const std::vector<T>& v) {
+  *dst = dalloc<T>(h, v.size());
+  if (!*dst) return set_err(h, D3M_ERR_OOM, "cudaMalloc failed (" + std::to_string(v.size() * sizeof(T)) + " bytes)");
+  if (!v.empty()) CUDA_TRY(h, cudaMemcpy(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return D3M_OK;
+}
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+void fill_structure(const Symbolic& S, d3m_info* info) {
+  info->n = S.n;
+  info->nblk = S.N;
+  info->tile = S.b;
+  info->nnzb_K = S.nnzb_K;
+  info->nblk_L_offdiag = S.nL_off;
+  info->etree_depth = S.depth;
+  info->max_col_height = S.max_height;
+  info->ntiles = S.tcolptr.empty() ? 0 : S.tcolptr.back();
+  info->ntile_updates = S.n_tile_updates;
+  info->ndep_edges = S.n_edges;
+  info->factor_flops = S.factor_flops;
+  info->solve_flops_per_rhs = S.solve_flops_rhs;
+  info->residual_flops_per_rhs = S.residual_flops_rhs;
+}
+
+int factor_error(d3m_ctx* h) {
+  const Ctl& c = *h->h_ctl;
+  if (c.err == D3M_ERR_PIVOT)
+    return set_err(h, D3M_ERR_PIVOT, "pivot below the breakdown threshold (task " + std::to_string(c.err_task) + ")");
+  if (c.err == D3M_ERR_TIMEOUT)
+    return set_err(h, D3M_ERR_TIMEOUT, "bounded device wait expired in the factorization queue");
+  if (c.err != 0) return set_err(h, c.err, "factorization failed");
+  if (c.done != (int)h->S.tasks.size())
+    return set_err(h, D3M_ERR_TIMEOUT, "factorization finished " + std::to_string(c.done) + " of " +
+                                           std::to_string(h->S.tasks.size()) + " tasks");
+  return D3M_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void d3m_default_options(d3m_options* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->precision = D3M_MIXED_BF16X3;
+  o->refine_max_iter = 20;
+  o->refine_tol = 1e-12;
+  o->timeout_ns = 5000000000LL;
+  o->tile = 0;
+  o->max_nrhs = 32;
+  o->fp64_omega = 0;
+  o->debug_flags = 0;
+}
+
+int d3m_order_grid_nd(int32_t nx, int32_t ny, int32_t nz, int32_t* perm) {
+  if (!perm) return set_err(nullptr, D3M_ERR_INVALID, "perm is NULL");
+  std::vector<int32_t> p;
+  int rc = order_grid_nd(nx, ny, nz, p);
+  if (rc != D3M_OK) return set_err(nullptr, rc, "grid extents must be positive");
+  std::copy(p.begin(), p.end(), perm);
+  return D3M_OK;
+}
+
+int d3m_analyze(const d3m_pattern* pat, const int32_t* perm, int32_t tile, d3m_info* info) {
+  if (!info) return set_err(nullptr, D3M_ERR_INVALID, "info is NULL");
+  Symbolic S;
+  std::string err;
+  int rc = analyze(pat, perm, tile > 0 ? tile : 128, false, S, err);
+  if (rc != D3M_OK) return set_err(nullptr, rc, err);
+  std::memset(info, 0, sizeof(*info));
+  fill_structure(S, info);
+  info->omega = NAN;
+  info->omega_first = NAN;
+  return D3M_OK;
+}
+
+int d3m_create(d3m_handle* out, const d3m_pattern* pat, const int32_t* perm, const d3m_options* opt,
+               void* stream) {
+  (void)stream;
+  if (!out) return set_err(nullptr, D3M_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  d3m_ctx* h = new (std::nothrow) d3m_ctx();
+  if (!h) return set_err(nullptr, D3M_ERR_OOM, "host allocation failed");
+  if (opt) h->opt = *opt;
+  else d3m_default_options(&h->opt);
+  const int prec = h->opt.precision;
+  if (prec != D3M_FP64 && prec != D3M_MIXED_BF16X3 && prec != D3M_MIXED_SIMT32) {
+    delete h;
+    return set_err(nullptr, D3M_ERR_INVALID, "unknown precision");
+  }
+  if (h->opt.max_nrhs <= 0) h->opt.max_nrhs = 32;
+  if (h->opt.refine_max_iter <= 0) h->opt.refine_max_iter = 20;
+  if (!(h->opt.refine_tol > 0)) h->opt.refine_tol = 1e-12;
+  if (h->opt.timeout_ns <= 0) h->opt.timeout_ns = 5000000000LL;
+  h->fp64 = (prec == D3M_FP64);
+  h->tc = (prec == D3M_MIXED_BF16X3);
+  h->b = h->tc ? 128 : 64;
+  if (h->opt.tile != 0 && h->opt.tile != h->b) {
+    delete h;
+    return set_err(nullptr, D3M_ERR_INVALID, "tile must be 0 or " + std::to_string(h->tc ? 128 : 64) + " for this precision");
+  }
+  h->csize = h->fp64 ? sizeof(double2) : sizeof(float2);
+  std::string err;
+  int rc = analyze(pat, perm, h->b, true, h->S, err);
+  if (rc != D3M_OK) {
+    delete h;
+    return set_err(nullptr, rc, err);
+  }
+  *out = h;
+  const Symbolic& S = h->S;
+  const int64_t ntiles = (int64_t)S.tasks.size();
+  const int b = h->b;
+  const int mr = h->opt.max_nrhs;
+  if (cudaGetDevice(&h->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess) {
+    cudaGetLastError();
+    return set_err(h, D3M_ERR_CUDA, "no CUDA device");
+  }
+  int cc_major = 0, cc_minor = 0;
+  cudaDeviceGetAttribute(&cc_major, cudaDevAttrComputeCapabilityMajor, h->device);
+  cudaDeviceGetAttribute(&cc_minor, cudaDevAttrComputeCapabilityMinor, h->device);
+  if (cc_major != 10 || cc_minor != 3)
+    return set_err(h, D3M_ERR_CUDA, "this library is built for sm_103a (GB300) only; device is sm_" +
+                                        std::to_string(cc_major) + std::to_string(cc_minor));
+#define ALLOC(ptr, T, count)                                                                     \
+  do {                                                                                           \
+    ptr = dalloc<T>(h, (size_t)(count));                                                         \
+    if (!ptr) return set_err(h, D3M_ERR_OOM, "cudaMalloc failed for " #ptr);                    \
+  } while (0)
+#define UPLOAD(ptr, vec)                        \
+  do {                                          \
+    int rc_ = upload(h, &ptr, vec);             \
+    if (rc_ != D3M_OK) return rc_;              \
+  } while (0)
+  // factorization
+  ALLOC(h->K, double2, S.kblk_off.back());
+  UPLOAD(h->tasks, S.tasks);
+  UPLOAD(h->klist, S.klist);
+  {
+    std::vector<int32_t> nd = S.ndeps;
+    if ((h->opt.debug_flags & D3M_DEBUG_STALL_LAST_TASK) && !nd.empty()) nd.back() += 1;
+    UPLOAD(h->ndeps, nd);
+  }
+  ALLOC(h->cnt, int32_t, ntiles);
+  UPLOAD(h->succ_ptr, S.succ_ptr);
+  UPLOAD(h->succ, S.succ);
+  ALLOC(h->ready, int32_t, ntiles);
+  UPLOAD(h->init_ready, S.init_ready);
+  ALLOC(h->ctl, Ctl, 1);
+  ALLOC(h->ctl0, Ctl, 1);
+  {
+    Ctl c0;
+    std::memset(&c0, 0, sizeof c0);
+    c0.tail = (int32_t)S.init_ready.size();
+    c0.min_piv_bits = 0x7f7fffffu;   // FLT_MAX
+    c0.max_piv_bits = 0u;
+    CUDA_TRY(h, cudaMemcpy(h->ctl0, &c0, sizeof c0, cudaMemcpyHostToDevice));
+  }
+  CUDA_TRY(h, cudaMallocHost(&h->h_ctl, sizeof(Ctl)));
+  std::memset(h->h_ctl, 0, sizeof(Ctl));
+  h->L = dalloc<unsigned char>(h, (size_t)ntiles * b * b * h->csize);
+  h->Linv = dalloc<unsigned char>(h, (size_t)S.NT * b * b * h->csize);
+  h->D = dalloc<unsigned char>(h, (size_t)S.NT * b * h->csize);
+  if (!h->L || !h->Linv || !h->D) return set_err(h, D3M_ERR_OOM, "cudaMalloc failed for the factor tiles");
+  if (h->tc) {
+    // operand planes (bf16): A: [tile][2 splits][2 planes][b rows][b], B: [tile][2][3][b][b]
+    h->opA = dalloc<unsigned char>(h, (size_t)ntiles * 4 * b * b * 2);
+    h->opB = dalloc<unsigned char>(h, (size_t)ntiles * 6 * b * b * 2);
+    if (!h->opA || !h->opB) return set_err(h, D3M_ERR_OOM, "cudaMalloc failed for the tensor-core operands");
+    std::string e2;
+    if (tc_make_maps(h->opA, h->opB, ntiles, &h->maps, e2) != 0) return set_err(h, D3M_ERR_CUDA, e2);
+  }
+  // solve
+  UPLOAD(h->fwd_items, S.fwd_items);
+  UPLOAD(h->bwd_items, S.bwd_items);
+  UPLOAD(h->fwd_slot, S.fwd_slot_ptr);
+  UPLOAD(h->bwd_slot, S.bwd_slot_ptr);
+  {
+    std::vector<int32_t> lb;
+    h->lev_ptr.assign(1, 0);
+    for (const auto& l : S.lev_blocks) {
+      lb.insert(lb.end(), l.begin(), l.end());
+      h->lev_ptr.push_back((int64_t)lb.size());
+    }
+    UPLOAD(h->lev_blocks, lb);
+    std::vector<int64_t> p2o(S.npad, -1);
+    for (int k = 0; k < S.N; ++k)
+      for (int u = 0; u < S.m[k]; ++u) p2o[S.xoff[k] + u] = S.xoff_orig[S.perm[k]] + u;
+    UPLOAD(h->pad2orig, p2o);
+    int mrows = 0;
+    for (int k = 0; k < S.N; ++k) mrows = std::max(mrows, S.ntile[k] * b);
+    h->max_rows = mrows;
+  }
+  UPLOAD(h->tstart, S.tstart);
+  UPLOAD(h->tcolptr, S.tcolptr);
+  h->Y = dalloc<unsigned char>(h, (size_t)S.npad * mr * h->csize);
+  h->P = dalloc<unsigned char>(h, (size_t)std::max<int64_t>(1, S.max_level_items) * (b / 64) * b * mr * h->csize);
+  if (!h->Y || !h->P) return set_err(h, D3M_ERR_OOM, "cudaMalloc failed for the solve workspace");
+  // refinement + residual
+  ALLOC(h->d_b, double2, S.n * mr);
+  ALLOC(h->d_x, double2, S.n * mr);
+  ALLOC(h->d_xbest, double2, S.n * mr);
+  ALLOC(h->d_r, double2, S.n * mr);
+  UPLOAD(h->kblk_off, S.kblk_off);
+  UPLOAD(h->res_ptr, S.res_ptr);
+  UPLOAD(h->res_blk, S.res_blk);
+  UPLOAD(h->res_src, S.res_src);
+  UPLOAD(h->res_tr, S.res_tr);
+  UPLOAD(h->m_orig, S.m_orig);
+  UPLOAD(h->xoff_orig, S.xoff_orig);
+  {
+    std::vector<int2> ch;
+    for (int f = 0; f < S.N; ++f)
+      for (int r = 0; r < S.m_orig[f]; r += 32) ch.push_back(make_int2(f, r));
+    h->nchunks = (int)ch.size();
+    UPLOAD(h->chunks, ch);
+    std::vector<int32_t> bc(S.nnzb_K);
+    for (int g = 0; g < S.N; ++g)
+      for (int64_t p = S.colptr[g]; p < S.colptr[g + 1]; ++p) bc[p] = g;
+    UPLOAD(h->blk_col, bc);
+  }
+  UPLOAD(h->rowidx, S.rowidx);
+  UPLOAD(h->colptr, S.colptr);
+  ALLOC(h->norms, unsigned, 3 * mr + 1);
+  ALLOC(h->omega_dev, double, mr);
+  ALLOC(h->stat_dev, double, 1);
+  ALLOC(h->contract, double2, S.N);
+  CUDA_TRY(h, cudaMallocHost(&h->h_stat, sizeof(double)));
+  CUDA_TRY(h, cudaEventCreate(&h->ev_f0));
+  CUDA_TRY(h, cudaEventCreate(&h->ev_f1));
+  CUDA_TRY(h, cudaEventCreate(&h->ev_s0));
+  CUDA_TRY(h, cudaEventCreate(&h->ev_s1));
+  h->ev_res.resize(2 * (h->opt.refine_max_iter + 2));
+  for (auto& e : h->ev_res) CUDA_TRY(h, cudaEventCreate(&e));
+#undef ALLOC
+#undef UPLOAD
+  return D3M_OK;
+}
+
+static ResidualParams residual_params(d3m_ctx* h, const double2* X, const double2* B, int nrhs) {
+  ResidualParams p;
+  p.K = h->K;
+  p.kblk_off = h->kblk_off;
+  p.res_ptr = h->res_ptr;
+  p.res_blk = h->res_blk;
+  p.res_src = h->res_src;
+  p.res_tr = h->res_tr;
+  p.m_orig = h->m_orig;
+  p.xoff_orig = h->xoff_orig;
+  p.chunks = h->chunks;
+  p.nrhs = nrhs;
+  p.rc = std::min(nrhs, 8);
+  p.n = h->S.n;
+  p.X = X;
+  p.B = B;
+  p.R = h->d_r;
+  const int mr = h->opt.max_nrhs;
+  p.rmax = h->norms;
+  p.xmax = h->norms + mr;
+  p.kmax = h->norms + 3 * mr;
+  return p;
+}
+
+int d3m_factor(d3m_handle h, const void* Kin, void* stream) {
+  if (!h) return set_err(nullptr, D3M_ERR_INVALID, "handle is NULL");
+  if (!Kin) return set_err(h, D3M_ERR_INVALID, "K is NULL");
+  cudaStream_t st = (cudaStream_t)stream;
+  const Symbolic& S = h->S;
+  const int64_t ntiles = (int64_t)S.tasks.size();
+  const size_t kbytes = (size_t)S.kblk_off.back() * sizeof(double2);
+  CUDA_TRY(h, cudaMemcpyAsync(h->K, Kin, kbytes, is_device_ptr(Kin) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+  // reset the task graph state
+  CUDA_TRY(h, cudaMemcpyAsync(h->cnt, h->ndeps, ntiles * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+  CUDA_TRY(h, cudaMemsetAsync(h->ready, 0xff, ntiles * sizeof(int32_t), st));
+  const int n0 = (int)S.init_ready.size();
+  if (n0 > 0) CUDA_TRY(h, cudaMemcpyAsync(h->ready, h->init_ready, n0 * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+  CUDA_TRY(h, cudaMemcpyAsync(h->ctl, h->ctl0, sizeof(Ctl), cudaMemcpyDeviceToDevice, st));
+  // ||K||_inf for the backward error
+  const int mr = h->opt.max_nrhs;
+  CUDA_TRY(h, cudaMemsetAsync(h->norms + 3 * mr, 0, sizeof(unsigned), st));
+  ResidualParams rp = residual_params(h, nullptr, nullptr, 1);
+  int rc = launch_knorm(rp, h->nchunks, st);
+  if (rc) return set_err(h, D3M_ERR_CUDA, std::string("knorm launch: ") + cudaGetErrorString((cudaError_t)rc));
+  FactorParams p;
+  p.tasks = h->tasks;
+  p.klist = h->klist;
+  p.cnt = h->cnt;
+  p.succ_ptr = h->succ_ptr;
+  p.succ = h->succ;
+  p.ready = h->ready;
+  p.ctl = h->ctl;
+  p.ntasks = (int32_t)ntiles;
+  p.b = h->b;
+  p.K = h->K;
+  p.L = h->L;
+  p.Linv = h->Linv;
+  p.D = h->D;
+  p.opA = h->opA;
+  p.opB = h->opB;
+  p.timeout_ns = h->opt.timeout_ns;
+  p.piv_tol = 1e3 * (h->fp64 ? 1.1102230246251565e-16 : 5.9604644775390625e-08);
+  CUDA_TRY(h, cudaEventRecord(h->ev_f0, st));
+  if (h->tc) rc = launch_factor_tc(p, h->maps, h->nsm, st);
+  else rc = launch_factor_simt(p, h->fp64, h->nsm, st);
+  if (rc) return set_err(h, D3M_ERR_CUDA, std::string("factor launch: ") + cudaGetErrorString((cudaError_t)rc));
+  CUDA_TRY(h, cudaEventRecord(h->ev_f1, st));
+  CUDA_TRY(h, cudaMemcpyAsync(h->h_ctl, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+  h->have_fact_ev = true;
+  h->factored = true;
+  h->last_status = D3M_OK;
+  return D3M_OK;
+}
+
+static int sweep(d3m_ctx* h, const double2* src, double2* dst, int nrhs, int accumulate, cudaStream_t st) {
+  const Symbolic& S = h->S;
+  SweepLaunch a;
+  a.b = h->b;
+  a.nrhs = nrhs;
+  a.nlevels = S.nlevels;
+  a.max_rows = h->max_rows;
+  a.accumulate = accumulate;
+  a.n = S.n;
+  a.npad = S.npad;
+  a.src = src;
+  a.dst = dst;
+  a.pad2orig = h->pad2orig;
+  a.L = h->L;
+  a.Linv = h->Linv;
+  a.D = h->D;
+  a.Y = h->Y;
+  a.P = h->P;
+  a.fwd_item_ptr = S.fwd_item_ptr.data();
+  a.bwd_item_ptr = S.bwd_item_ptr.data();
+  a.fwd_items = h->fwd_items;
+  a.bwd_items = h->bwd_items;
+  a.fwd_slot_ptr = h->fwd_slot;
+  a.bwd_slot_ptr = h->bwd_slot;
+  a.lev_blocks = h->lev_blocks;
+  a.lev_ptr = h->lev_ptr.data();
+  a.tstart = h->tstart;
+  a.tcolptr = h->tcolptr;
+  int rc = launch_sweep(a, h->fp64, st);
+  if (rc) return set_err(h, D3M_ERR_CUDA, std::string("sweep launch: ") + cudaGetErrorString((cudaError_t)rc));
+  return D3M_OK;
+}
+
+// r = b - K x and omega (device); returns D3M_OK or a launch error
+static int residual_omega(d3m_ctx* h, const double2* X, const double2* B, int nrhs, cudaStream_t st) {
+  const int mr = h->opt.max_nrhs;
+  CUDA_TRY(h, cudaMemsetAsync(h->norms, 0, 2 * mr * sizeof(unsigned), st));
+  ResidualParams rp = residual_params(h, X, B, nrhs);
+  if (h->nres_ev + 2 <= (int)h->ev_res.size()) CUDA_TRY(h, cudaEventRecord(h->ev_res[h->nres_ev], st));
+  int rc = launch_residual(rp, h->nchunks, st);
+  if (rc) return set_err(h, D3M_ERR_CUDA, std::string("residual launch: ") + cudaGetErrorString((cudaError_t)rc));
+  if (h->nres_ev + 2 <= (int)h->ev_res.size()) {
+    CUDA_TRY(h, cudaEventRecord(h->ev_res[h->nres_ev + 1], st));
+    h->nres_ev += 2;
+  }
+  rc = launch_omega(h->norms, h->norms + mr, h->norms + 2 * mr, h->norms + 3 * mr, nrhs, h->omega_dev, h->stat_dev, st);
+  if (rc) return set_err(h, D3M_ERR_CUDA, std::string("omega launch: ") + cudaGetErrorString((cudaError_t)rc));
+  return D3M_OK;
+}
+
+static int solve_impl(d3m_ctx* h, const void* Bin, void* Xout, int nrhs, cudaStream_t st) {
+  if (!Bin || !Xout) return set_err(h, D3M_ERR_INVALID, "B or X is NULL");
+  if (nrhs < 1 || nrhs > h->opt.max_nrhs)
+    return set_err(h, D3M_ERR_INVALID, "nrhs out of range [1, max_nrhs]");
+  if (!h->factored) return set_err(h, D3M_ERR_STATE, "solve before factor");
+  const Symbolic& S = h->S;
+  const size_t vbytes = (size_t)S.n * nrhs * sizeof(double2);
+  const bool bdev = is_device_ptr(Bin), xdev = is_device_ptr(Xout);
+  const double2* B = (const double2*)Bin;
+  if (!bdev) {
+    CUDA_TRY(h, cudaMemcpyAsync(h->d_b, Bin, vbytes, cudaMemcpyHostToDevice, st));
+    B = h->d_b;
+  }
+  double2* X = xdev ? (double2*)Xout : h->d_x;
+  if ((const void*)X == (const void*)B) return set_err(h, D3M_ERR_INVALID, "B and X may not alias");
+  h->nres_ev = 0;
+  h->omega = NAN;
+  h->omega_first = NAN;
+  h->omega_valid = 0;
+  h->refine_iters = 0;
+  CUDA_TRY(h, cudaEventRecord(h->ev_s0, st));
+  int status = D3M_OK;
+  const int mr = h->opt.max_nrhs;
+  if (h->fp64) {
+    int rc = sweep(h, B, X, nrhs, 0, st);
+    if (rc) return rc;
+    h->refine_iters = 1;
+    if (h->opt.fp64_omega) {
+      CUDA_TRY(h, cudaMemsetAsync(h->norms + 2 * mr, 0, mr * sizeof(unsigned), st));
+      rc = launch_absmax(B, S.n, nrhs, h->norms + 2 * mr, st);
+      if (rc) return set_err(h, D3M_ERR_CUDA, "absmax launch failed");
+      rc = residual_omega(h, X, B, nrhs, st);
+      if (rc) return rc;
+      CUDA_TRY(h, cudaMemcpyAsync(h->h_stat, h->stat_dev, sizeof(double), cudaMemcpyDeviceToHost, st));
+      CUDA_TRY(h, cudaStreamSynchronize(st));
+      h->omega = h->omega_first = *h->h_stat;
+      h->omega_valid = 1;
+    }
+  } else {
+    CUDA_TRY(h, cudaMemsetAsync(h->norms + 2 * mr, 0, mr * sizeof(unsigned), st));
+    int rc = launch_absmax(B, S.n, nrhs, h->norms + 2 * mr, st);
+    if (rc) return set_err(h, D3M_ERR_CUDA, "absmax launch failed");
+    double best = INFINITY;
+    std::vector<double> hist;
+    const double2* src = B;
+    for (int it = 0; it < h->opt.refine_max_iter; ++it) {
+      rc = sweep(h, src, X, nrhs, it > 0 ? 1 : 0, st);     // x (+)= solve(r)
+      if (rc) return rc;
+      rc = residual_omega(h, X, B, nrhs, st);                // r = b - K x, omega
+      if (rc) return rc;
+      CUDA_TRY(h, cudaMemcpyAsync(h->h_stat, h->stat_dev, sizeof(double), cudaMemcpyDeviceToHost, st));
+      if (it == 0) CUDA_TRY(h, cudaMemcpyAsync(h->h_ctl, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+      CUDA_TRY(h, cudaStreamSynchronize(st));
+      if (it == 0) {
+        int fe = factor_error(h);
+        if (fe != D3M_OK) {
+          h->last_status = fe;
+          return fe;
+        }
+      }
+      const double w = *h->h_stat;
+      h->refine_iters = it + 1;
+      if (it == 0) h->omega_first = w;
+      hist.push_back(w);
+      if (w < best) {
+        best = w;
+        if (w > h->opt.refine_tol)
+          CUDA_TRY(h, cudaMemcpyAsync(h->d_xbest, X, vbytes, cudaMemcpyDeviceToDevice, st));
+      }
+      h->omega = w;
+      h->omega_valid = 1;
+      if (w <= h->opt.refine_tol) break;
+      const size_t k = hist.size();
+      const bool stagnated = (k >= 3 && !(hist[k - 1] <= 0.5 * hist[k - 3])) || !std::isfinite(w);
+      if (stagnated || it + 1 == h->opt.refine_max_iter) {
+        if (w > best) {
+          CUDA_TRY(h, cudaMemcpyAsync(X, h->d_xbest, vbytes, cudaMemcpyDeviceToDevice, st));
+          h->omega = best;
+        }
+        status = D3M_ERR_NOT_CONVERGED;
+        set_err(h, status, "refinement did not reach the tolerance (omega " + std::to_string(h->omega) + ")");
+        break;
+      }
+      src = h->d_r;
+    }
+  }
+  CUDA_TRY(h, cudaEventRecord(h->ev_s1, st));
+  h->have_solve_ev = true;
+  if (!xdev) CUDA_TRY(h, cudaMemcpyAsync(Xout, X, vbytes, cudaMemcpyDeviceToHost, st));
+  h->last_status = status;
+  return status;
+}
+
+int d3m_solve(d3m_handle h, const void* B, void* X, int32_t nrhs, void* stream) {
+  if (!h) return set_err(nullptr, D3M_ERR_INVALID, "handle is NULL");
+  return solve_impl(h, B, X, nrhs, (cudaStream_t)stream);
+}
+
+int d3m_adjoint(d3m_handle h, const void* G, void* Lambda, int32_t nrhs, void* stream) {
+  if (!h) return set_err(nullptr, D3M_ERR_INVALID, "handle is NULL");
+  // K^T = K: the adjoint system is solved with the same factors and refinement
+  return solve_impl(h, G, Lambda, nrhs, (cudaStream_t)stream);
+}
+
+int d3m_grad_eps(d3m_handle h, const void* Lambda, const void* X, int32_t nrhs, int32_t ndom,
+                 const int32_t* dom_ptr, const int32_t* dom_if, double k2, double* dJ, void* stream) {
+  if (!h) return set_err(nullptr, D3M_ERR_INVALID, "handle is NULL");
+  if (!Lambda || !X || !dom_ptr || !dom_if || !dJ || ndom < 0 || nrhs < 1)
+    return set_err(h, D3M_ERR_INVALID, "bad argument to d3m_grad_eps");
+  if (!is_device_ptr(Lambda) || !is_device_ptr(X)) return set_err(h, D3M_ERR_INVALID, "Lambda and X must be device memory");
+  cudaStream_t st = (cudaStream_t)stream;
+  const Symbolic& S = h->S;
+  int rc = launch_contract((const double2*)Lambda, (const double2*)X, S.n, nrhs, h->xoff_orig, h->m_orig, S.N,
+                           h->contract, st);
+  if (rc) return set_err(h, D3M_ERR_CUDA, "contract launch failed");
+  std::vector<double2> sf(S.N);
+  CUDA_TRY(h, cudaMemcpyAsync(sf.data(), h->contract, S.N * sizeof(double2), cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(h, cudaStreamSynchronize(st));
+  for (int i = 0; i < ndom; ++i) {
+    double re = 0.0;
+    for (int q = dom_ptr[i]; q < dom_ptr[i + 1]; ++q) {
+      const int f = dom_if[q];
+      if (f < 0 || f >= S.N) return set_err(h, D3M_ERR_INVALID, "dom_if entry out of range");
+      re += sf[f].x;
+    }
+    dJ[i] = k2 * re;   // Re(k2 * s) with real k2
+  }
+  return D3M_OK;
+}
+
+int d3m_grad_pattern(d3m_handle h, const void* Lambda, const void* X, int32_t nrhs, void* dK, void* stream) {
+  if (!h) return set_err(nullptr, D3M_ERR_INVALID, "handle is NULL");
+  if (!Lambda || !X || !dK || nrhs < 1) return set_err(h, D3M_ERR_INVALID, "bad argument to d3m_grad_pattern");
+  if (!is_device_ptr(Lambda) || !is_device_ptr(X) || !is_device_ptr(dK))
+    return set_err(h, D3M_ERR_INVALID, "Lambda, X and dK must be device memory");
+  const Symbolic& S = h->S;
+  int rc = launch_grad_pattern((const double2*)Lambda, (const double2*)X, S.n, nrhs, h->colptr, h->rowidx, h->blk_col,
+                               h->kblk_off, h->xoff_orig, h->m_orig, S.nnzb_K, (double2*)dK, (cudaStream_t)stream);
+  if (rc) return set_err(h, D3M_ERR_CUDA, "grad_pattern launch failed");
+  return D3M_OK;
+}
+
+int d3m_get_factor_block(d3m_handle h, int32_t i, int32_t j, void* host_out, void* stream) {
+  if (!h) return set_err(nullptr, D3M_ERR_INVALID, "handle is NULL");
+  const Symbolic& S = h->S;
+  if (!host_out || i < 0 || j < 0 || i >= S.N || j >= S.N || i < j) return set_err(h, D3M_ERR_INVALID, "bad block index");
+  if (i != j && !std::binary_search(S.str[j].begin(), S.str[j].end(), i))
+    return set_err(h, D3M_ERR_INVALID, "block not in the filled pattern");
+  CUDA_TRY(h, cudaStreamSynchronize((cudaStream_t)stream));
+  const int b = h->b, mi = S.m[i], mj = S.m[j];
+  double2* out = (double2*)host_out;
+  std::vector<unsigned char> tile((size_t)b * b * h->csize);
+  for (int J = S.tstart[j]; J < S.tstart[j + 1]; ++J)
+    for (int I = S.tstart[i]; I < S.tstart[i + 1]; ++I) {
+      const int r0 = (I - S.tstart[i]) * b, c0 = (J - S.tstart[j]) * b;
+      const int64_t t = (I >= J) ? S.tile_of(I, J) : -1;
+      if (t < 0) {
+        for (int c = c0; c < std::min(mj, c0 + b); ++c)
+          for (int r = r0; r < std::min(mi, r0 + b); ++r) out[(int64_t)c * mi + r] = make_double2(0, 0);
+        continue;
+      }
+      CUDA_TRY(h, cudaMemcpy(tile.data(), (unsigned char*)h->L + (size_t)t * b * b * h->csize, tile.size(),
+                             cudaMemcpyDeviceToHost));
+      for (int c = c0; c < std::min(mj, c0 + b); ++c)
+        for (int r = r0; r < std::min(mi, r0 + b); ++r) {
+          const size_t e = (size_t)(r - r0) * b + (c - c0);
+          double2 v;
+          if (h->fp64) v = ((double2*)tile.data())[e];
+          else {
+            const float2 f = ((float2*)tile.data())[e];
+            v = make_double2(f.x, f.y);
+          }
+          out[(int64_t)c * mi + r] = v;
+        }
+    }
+  return D3M_OK;
+}
+
+int d3m_get_pivots(d3m_handle h, int32_t j, void* host_out, void* stream) {
+  if (!h) return set_err(nullptr, D3M_ERR_INVALID, "handle is NULL");
+  const Symbolic& S = h->S;
+  if (!host_out || j < 0 || j >= S.N) return set_err(h, D3M_ERR_INVALID, "bad block index");
+  CUDA_TRY(h, cudaStreamSynchronize((cudaStream_t)stream));
+  const int mj = S.m[j];
+  std::vector<unsigned char> buf((size_t)mj * h->csize);
+  CUDA_TRY(h, cudaMemcpy(buf.data(), (unsigned char*)h->D + (size_t)S.tstart[j] * h->b * h->csize, buf.size(),
+                         cudaMemcpyDeviceToHost));
+  double2* out = (double2*)host_out;
+  for (int u = 0; u < mj; ++u) {
+    if (h->fp64) out[u] = ((double2*)buf.data())[u];
+    else {
+      const float2 f = ((float2*)buf.data())[u];
+      out[u] = make_double2(f.x, f.y);
+    }
+  }
+  return D3M_OK;
+}
+
+int d3m_get_info(d3m_handle h, d3m_info* info, void* stream) {
+  if (!h || !info) return set_err(h, D3M_ERR_INVALID, "handle or info is NULL");
+  CUDA_TRY(h, cudaStreamSynchronize((cudaStream_t)stream));
+  CUDA_TRY(h, cudaGetLastError());
+  std::memset(info, 0, sizeof(*info));
+  fill_structure(h->S, info);
+  info->device_bytes = h->dev_bytes;
+  int st = h->last_status;
+  if (h->factored) {
+    int fe = factor_error(h);
+    if (fe != D3M_OK) st = fe;
+    info->min_abs_pivot = (double)([](unsigned u) { float f; std::memcpy(&f, &u, 4); return f; })(h->h_ctl->min_piv_bits);
+    info->max_abs_pivot = (double)([](unsigned u) { float f; std::memcpy(&f, &u, 4); return f; })(h->h_ctl->max_piv_bits);
+  }
+  info->status = st;
+  info->refine_iters = h->refine_iters;
+  info->omega = h->omega_valid ? h->omega : NAN;
+  info->omega_first = h->omega_valid ? h->omega_first : NAN;
+  if (h->have_fact_ev) CUDA_TRY(h, cudaEventElapsedTime(&h->fact_ms, h->ev_f0, h->ev_f1));
+  if (h->have_solve_ev) CUDA_TRY(h, cudaEventElapsedTime(&h->solve_ms, h->ev_s0, h->ev_s1));
+  float rsum = 0.f;
+  for (int e = 0; e + 1 < h->nres_ev; e += 2) {
+    float t = 0.f;
+    CUDA_TRY(h, cudaEventElapsedTime(&t, h->ev_res[e], h->ev_res[e + 1]));
+    rsum += t;
+  }
+  info->factor_kernel_ms = h->fact_ms;
+  info->solve_ms = h->solve_ms;
+  info->residual_ms = rsum;
+  return D3M_OK;
+}
+
+const char* d3m_last_error(d3m_handle h) {
+  if (h) return h->err.c_str();
+  return g_err.c_str();
+}
+
+void d3m_destroy(d3m_handle h) {
+  if (!h) return;
+  for (void* p : h->allocs) cudaFree(p);
+  if (h->h_ctl) cudaFreeHost(h->h_ctl);
+  if (h->h_stat) cudaFreeHost(h->h_stat);
+  cudaEvent_t evs[4] = {h->ev_f0, h->ev_f1, h->ev_s0, h->ev_s1};
+  for (cudaEvent_t e : evs)
+    if (e) cudaEventDestroy(e);
+  for (cudaEvent_t e : h->ev_res)
+    if (e) cudaEventDestroy(e);
+  delete h;
+}
+
+}  // extern "C"

@@ -1,0 +1,198 @@
+// Device-side helpers shared by the factorization kernels: complex arithmetic and the task
+// queue of the persistent scheduler.
+//
+// Scheduler (replaces the paper's static list schedule, Sec. II, with a dynamic queue):
+//   ready[]  : task ids in the order they became ready (slot s holds the s-th push, -1 = empty)
+//   head     : next slot to claim (atomicAdd); tail: next slot to fill (atomicAdd)
+//   cnt[t]   : unmet dependencies of task t; the producer that drops it to 0 pushes t.
+// A block claims a slot, then waits (bounded by timeout_ns of %globaltimer, with backoff)
+// until the slot is filled.  Every slot < ntasks is eventually filled while some block
+// runs a task, so the only way a wait expires is a broken graph or an abort; then the block
+// records D3M_ERR_TIMEOUT, raises `abort`, and returns.
+// Memory order: data writes -> __syncthreads -> fence (release) -> atomicSub on successors;
+// the pusher fences again before publishing the id; the consumer fences after reading it
+// (acquire) and reads producer data with L1-bypassing loads or the TMA (async proxy).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "d3m.h"
+#include "symbolic.h"
+
+namespace d3m {
+
+struct Ctl {
+  int32_t head, tail, done, abort;
+  int32_t err, err_task, pad0, pad1;
+  uint32_t min_piv_bits, max_piv_bits;  // |d| as float bits (non-negative => ordered as uint)
+  int32_t pad2[6];
+};
+
+struct FactorParams {
+  const TileTask* tasks;
+  const KEntry* klist;
+  int32_t* cnt;
+  const int64_t* succ_ptr;
+  const int32_t* succ;
+  int32_t* ready;
+  Ctl* ctl;
+  int32_t ntasks;
+  int32_t b;
+  const double2* K;      // library copy of K (c128)
+  void* L;               // [ntiles][b][b] complex (row-major tiles)
+  void* Linv;            // [NT][b][b] inverse of the unit-lower diagonal tiles
+  void* D;               // [NT][b] pivots
+  void* opA;             // tensor-core operand planes (bf16) of L tiles
+  void* opB;             // tensor-core operand planes (bf16) of W tiles / T_J
+  int64_t timeout_ns;
+  double piv_tol;        // breakdown: |d| < piv_tol * max|S| of the diagonal tile
+};
+
+// ------------------------------------------------------------------ complex helpers
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// acc + a*b
+__device__ __forceinline__ double2 cfma(double2 a, double2 b, double2 c) {
+  c.x = fma(a.x, b.x, c.x); c.x = fma(-a.y, b.y, c.x);
+  c.y = fma(a.x, b.y, c.y); c.y = fma(a.y, b.x, c.y);
+  return c;
+}
+__device__ __forceinline__ float2 cfma(float2 a, float2 b, float2 c) {
+  c.x = fmaf(a.x, b.x, c.x); c.x = fmaf(-a.y, b.y, c.x);
+  c.y = fmaf(a.x, b.y, c.y); c.y = fmaf(a.y, b.x, c.y);
+  return c;
+}
+// acc - a*b
+__device__ __forceinline__ double2 cfms(double2 a, double2 b, double2 c) {
+  c.x = fma(-a.x, b.x, c.x); c.x = fma(a.y, b.y, c.x);
+  c.y = fma(-a.x, b.y, c.y); c.y = fma(-a.y, b.x, c.y);
+  return c;
+}
+__device__ __forceinline__ float2 cfms(float2 a, float2 b, float2 c) {
+  c.x = fmaf(-a.x, b.x, c.x); c.x = fmaf(a.y, b.y, c.x);
+  c.y = fmaf(-a.x, b.y, c.y); c.y = fmaf(-a.y, b.x, c.y);
+  return c;
+}
+__device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
+  double s = 1.0 / (b.x * b.x + b.y * b.y);
+  return make_double2((a.x * b.x + a.y * b.y) * s, (a.y * b.x - a.x * b.y) * s);
+}
+__device__ __forceinline__ float2 cdiv(float2 a, float2 b) {
+  float s = 1.0f / (b.x * b.x + b.y * b.y);
+  return make_float2((a.x * b.x + a.y * b.y) * s, (a.y * b.x - a.x * b.y) * s);
+}
+__device__ __forceinline__ double cabs2(double2 a) { return a.x * a.x + a.y * a.y; }
+__device__ __forceinline__ float cabs2(float2 a) { return a.x * a.x + a.y * a.y; }
+
+template <typename R> struct CT;
+template <> struct CT<double> {
+  using C = double2;
+  static __device__ __forceinline__ C make(double x, double y) { return make_double2(x, y); }
+  static __device__ __forceinline__ C from(double2 v) { return v; }
+  static constexpr double u = 1.1102230246251565e-16;  // 2^-53
+};
+template <> struct CT<float> {
+  using C = float2;
+  static __device__ __forceinline__ C make(float x, float y) { return make_float2(x, y); }
+  static __device__ __forceinline__ C from(double2 v) { return make_float2((float)v.x, (float)v.y); }
+  static constexpr double u = 5.9604644775390625e-08;  // 2^-24
+};
+
+// L1-bypassing loads of data written by other blocks during the same launch
+__device__ __forceinline__ double2 ld_cg(const double2* p) { return __ldcg(p); }
+__device__ __forceinline__ float2 ld_cg(const float2* p) { return __ldcg(p); }
+__device__ __forceinline__ float4 ld_cg4(const float4* p) { return __ldcg(p); }
+
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ int ld_volatile(const int32_t* p) { return *(const volatile int32_t*)p; }
+
+__device__ __forceinline__ void set_error(Ctl* ctl, int code, int task) {
+  if (atomicCAS(&ctl->err, 0, code) == 0) ctl->err_task = task;
+  atomicExch(&ctl->abort, 1);
+}
+
+// ------------------------------------------------------------------ scheduler
+// Claim the next ready task for this block (all threads call; returns -1 when done/aborted).
+__device__ __forceinline__ int sched_pop(const FactorParams& p, int* s_task) {
+  if (threadIdx.x == 0) {
+    int task = -1;
+    if (!ld_volatile(&p.ctl->abort)) {
+      int slot = atomicAdd(&p.ctl->head, 1);
+      if (slot < p.ntasks) {
+        const uint64_t t0 = globaltimer_ns();
+        unsigned ns = 32;
+        for (;;) {
+          task = ld_volatile(&p.ready[slot]);
+          if (task >= 0) break;
+          if (ld_volatile(&p.ctl->abort)) { task = -1; break; }
+          if (globaltimer_ns() - t0 > (uint64_t)p.timeout_ns) {
+            set_error(p.ctl, D3M_ERR_TIMEOUT, -1 - slot);
+            task = -1;
+            break;
+          }
+          __nanosleep(ns);
+          if (ns < 256) ns <<= 1;
+        }
+        __threadfence();  // acquire: producer data is visible after this point
+      }
+    }
+    *s_task = task;
+  }
+  __syncthreads();
+  const int t = *s_task;
+  __syncthreads();
+  return t;
+}
+
+// Release the successors of `task` (all threads call; warp 0 does the work).
+__device__ __forceinline__ void sched_complete(const FactorParams& p, int task) {
+  // writes of this thread become visible to later TMA (async-proxy) reads of other blocks
+  asm volatile("fence.proxy.async.global;" ::: "memory");
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    __threadfence();  // release: this block's tile writes before the counter updates
+    const int64_t e0 = p.succ_ptr[task], e1 = p.succ_ptr[task + 1];
+    for (int64_t e = e0 + threadIdx.x; e < e1; e += 32) {
+      const int s = p.succ[e];
+      if (atomicSub(&p.cnt[s], 1) == 1) {
+        __threadfence();
+        const int pos = atomicAdd(&p.ctl->tail, 1);
+        atomicExch(&p.ready[pos], s);
+      }
+    }
+    if (threadIdx.x == 0) atomicAdd(&p.ctl->done, 1);
+  }
+}
+
+__device__ __forceinline__ void record_pivot_stats(Ctl* ctl, float amin, float amax) {
+  atomicMin(&ctl->min_piv_bits, __float_as_uint(amin));
+  atomicMax(&ctl->max_piv_bits, __float_as_uint(amax));
+}
+
+// Entry (r, c) of the K tile of task T (padding: unit diagonal inside diagonal blocks).
+template <typename R>
+__device__ __forceinline__ typename CT<R>::C k_entry(const TileTask& T, const double2* K, int r, int c) {
+  using C = typename CT<R>::C;
+  if (r >= T.rv || c >= T.cv) {
+    const bool one = T.same_block && (T.r0 + r == T.c0 + c);
+    return CT<R>::make(one ? (R)1 : (R)0, (R)0);
+  }
+  if (T.k_off < 0) return CT<R>::make((R)0, (R)0);
+  const int rr = T.r0 + r, cc = T.c0 + c;
+  const int64_t idx = T.k_tr ? ((int64_t)rr * T.k_ld + cc) : ((int64_t)cc * T.k_ld + rr);
+  return CT<R>::from(__ldg(K + T.k_off + idx));
+}
+
+}  // namespace d3m

@@ -1,0 +1,210 @@
+// Persistent block-DAG factorization with a SIMT tile engine (tile edge 64).
+//
+// R = double: the plain FP64 (complex128) path; R = float: complex64 factors without tensor
+// cores (used as the SIMT reference of the mixed path).
+//
+// Each task owns one lower tile (I, J) of L (paper Sec. II: per nonzero block a task doing
+// the dense update, the dense triangular solve and the dense factorization):
+//   1. S = K_IJ - sum_K L_IK (D_K L_JK^T)         (K-list in increasing K, fixed order)
+//   2a. I == J: unpivoted LDL^T of S in shared memory (scalar pivots, no conjugation),
+//       breakdown check |d| >= piv_tol * max|S|; store L_JJ, D_J and L_JJ^{-1} (for the solve)
+//   2b. I != J: L_IJ = S L_JJ^{-T} D_J^{-1} by a column sweep (right-looking triangular solve).
+// GB300 FP64 runs at a small fraction of FP32 throughput, so the FP64 path is bound by the
+// DFMA rate: a simple register-blocked 64x64 complex tile product is enough to saturate it.
+#include <cuda_runtime.h>
+
+#include "device.cuh"
+
+namespace d3m {
+
+namespace {
+constexpr int TB = 64;     // tile edge
+constexpr int LDS = 65;    // padded shared-memory row stride (elements)
+constexpr int NTHR = 256;
+}  // namespace
+
+template <typename R>
+__global__ void __launch_bounds__(NTHR, 1) factor_simt_kernel(FactorParams p) {
+  using C = typename CT<R>::C;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* sA = reinterpret_cast<C*>(smem_raw);       // [64][65]
+  C* sB = sA + TB * LDS;                         // [64][65]
+  __shared__ C s_col[TB];
+  __shared__ C s_d[TB];
+  __shared__ C s_tmp[TB];
+  __shared__ R s_red[NTHR / 32];
+  __shared__ int s_task;
+
+  C* Lg = reinterpret_cast<C*>(p.L);
+  C* Linv = reinterpret_cast<C*>(p.Linv);
+  C* Dg = reinterpret_cast<C*>(p.D);
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+
+  for (;;) {
+    const int task = sched_pop(p, &s_task);
+    if (task < 0) break;
+    const TileTask T = p.tasks[task];
+
+    // ---------------------------------------------------------------- 1. Schur updates
+    C acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] = CT<R>::make(0, 0);
+    for (int e = 0; e < T.nk; ++e) {
+      const KEntry ke = p.klist[T.kl_off + e];
+      const C* La = Lg + (int64_t)ke.a_tile * TB * TB;
+      const C* Lb = Lg + (int64_t)ke.b_tile * TB * TB;
+      const C* dK = Dg + (int64_t)ke.kcol * TB;
+      __syncthreads();
+      for (int i = tid; i < TB * TB; i += NTHR) {
+        const int r = i >> 6, c = i & 63;
+        sA[r * LDS + c] = ld_cg(La + i);
+        sB[r * LDS + c] = cmul(ld_cg(Lb + i), ld_cg(dK + c));   // W_JK = L_JK D_K
+      }
+      __syncthreads();
+#pragma unroll 4
+      for (int k = 0; k < TB; ++k) {
+        C a[4], bb[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) a[i] = sA[(ty + 16 * i) * LDS + k];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) bb[j] = sB[(tx + 16 * j) * LDS + k];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[i][j] = cfma(a[i], bb[j], acc[i][j]);
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int r = ty + 16 * i, c = tx + 16 * j;
+        sA[r * LDS + c] = csub(k_entry<R>(T, p.K, r, c), acc[i][j]);
+      }
+    __syncthreads();
+
+    if (T.is_diag) {
+      // ------------------------------------------------------------ 2a. diagonal tile
+      R mx = 0;
+      for (int i = tid; i < TB * TB; i += NTHR) {
+        const int r = i >> 6, c = i & 63;
+        if (c <= r && r < T.rv) mx = fmax(mx, (R)sqrt(cabs2(sA[r * LDS + c])));
+      }
+      for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      if ((tid & 31) == 0) s_red[tid >> 5] = mx;
+      __syncthreads();
+      if (tid == 0) {
+        R v = 0;
+        for (int w = 0; w < NTHR / 32; ++w) v = fmax(v, s_red[w]);
+        s_red[0] = v;
+      }
+      __syncthreads();
+      const R smax = s_red[0];
+      for (int c = 0; c < TB; ++c) {
+        const C d = sA[c * LDS + c];
+        if (tid > c && tid < TB) {
+          const C v = sA[tid * LDS + c];
+          s_tmp[tid] = v;
+          s_col[tid] = cdiv(v, d);
+        }
+        if (tid == 0) s_d[c] = d;
+        __syncthreads();
+        const int w = TB - 1 - c;
+        for (int i = tid; i < w * w; i += NTHR) {
+          const int r = c + 1 + i / w, s = c + 1 + i % w;
+          if (s <= r) sA[r * LDS + s] = cfms(s_col[r], s_tmp[s], sA[r * LDS + s]);
+        }
+        if (tid > c && tid < TB) sA[tid * LDS + c] = s_col[tid];
+        __syncthreads();
+      }
+      // pivot checks on the real (non-padding) unknowns
+      if (tid < 32) {
+        R amin = (R)3.0e38, amax = 0;
+        for (int c = tid; c < T.cv; c += 32) {
+          const R a = (R)sqrt(cabs2(s_d[c]));
+          amin = fmin(amin, a);
+          amax = fmax(amax, a);
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+          amin = fmin(amin, __shfl_xor_sync(0xffffffffu, amin, o));
+          amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+        }
+        if (tid == 0) {
+          record_pivot_stats(p.ctl, (float)amin, (float)amax);
+          if (!(amin >= (R)p.piv_tol * smax)) set_error(p.ctl, D3M_ERR_PIVOT, task);
+        }
+      }
+      // store L_JJ (unit lower), D_J
+      C* Lt = Lg + (int64_t)T.tile * TB * TB;
+      for (int i = tid; i < TB * TB; i += NTHR) {
+        const int r = i >> 6, c = i & 63;
+        C v = (c < r) ? sA[r * LDS + c] : CT<R>::make(c == r ? (R)1 : (R)0, 0);
+        Lt[i] = v;
+      }
+      if (tid < TB) Dg[(int64_t)T.col * TB + tid] = s_d[tid];
+      __syncthreads();
+      // in-place inverse of the unit lower tile: for j = 62..0,
+      // X_ij = -(L_ij + sum_{j<k<i} X_ik L_kj)   (columns > j already hold X)
+      for (int j = TB - 2; j >= 0; --j) {
+        if (tid > j && tid < TB) {
+          C t = sA[tid * LDS + j];
+          for (int k = j + 1; k < tid; ++k) t = cfma(sA[tid * LDS + k], sA[k * LDS + j], t);
+          s_tmp[tid] = CT<R>::make(-t.x, -t.y);
+        }
+        __syncthreads();
+        if (tid > j && tid < TB) sA[tid * LDS + j] = s_tmp[tid];
+        __syncthreads();
+      }
+      C* Li = Linv + (int64_t)T.col * TB * TB;
+      for (int i = tid; i < TB * TB; i += NTHR) {
+        const int r = i >> 6, c = i & 63;
+        Li[i] = (c < r) ? sA[r * LDS + c] : CT<R>::make(c == r ? (R)1 : (R)0, 0);
+      }
+    } else {
+      // ------------------------------------------------------------ 2b. off-diagonal tile
+      const C* Ld = Lg + (int64_t)T.diag * TB * TB;
+      for (int i = tid; i < TB * TB; i += NTHR) {
+        const int r = i >> 6, c = i & 63;
+        sB[r * LDS + c] = ld_cg(Ld + i);
+      }
+      if (tid < TB) s_d[tid] = ld_cg(Dg + (int64_t)T.col * TB + tid);
+      __syncthreads();
+      // X L_JJ^T = S: column c of X is final once columns < c are eliminated
+      for (int c = 0; c < TB - 1; ++c) {
+        const int w = TB - 1 - c;
+        for (int i = tid; i < TB * w; i += NTHR) {
+          const int r = i / w, cc = c + 1 + i % w;
+          sA[r * LDS + cc] = cfms(sA[r * LDS + c], sB[cc * LDS + c], sA[r * LDS + cc]);
+        }
+        __syncthreads();
+      }
+      C* Lt = Lg + (int64_t)T.tile * TB * TB;
+      for (int i = tid; i < TB * TB; i += NTHR) {
+        const int r = i >> 6, c = i & 63;
+        Lt[i] = cdiv(sA[r * LDS + c], s_d[c]);
+      }
+    }
+    sched_complete(p, task);
+  }
+}
+
+int launch_factor_simt(const FactorParams& p, bool fp64, int nblocks, cudaStream_t st) {
+  const size_t smem = (fp64 ? sizeof(double2) : sizeof(float2)) * 2 * TB * LDS;
+  cudaError_t e;
+  if (fp64) {
+    e = cudaFuncSetAttribute(factor_simt_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return (int)e;
+    factor_simt_kernel<double><<<nblocks, NTHR, smem, st>>>(p);
+  } else {
+    e = cudaFuncSetAttribute(factor_simt_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return (int)e;
+    factor_simt_kernel<float><<<nblocks, NTHR, smem, st>>>(p);
+  }
+  return (int)cudaGetLastError();
+}
+
+}  // namespace d3m

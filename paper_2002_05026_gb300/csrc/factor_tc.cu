@@ -1,0 +1,597 @@
+// Persistent block-DAG factorization with a tcgen05 tensor-core tile engine (tile edge 128).
+//
+// Arithmetic: complex64 factors.  Every product of the factorization (the Schur updates
+// S_IJ -= L_IK D_K L_JK^T -- the paper's GEMM tasks, Sec. II -- and the triangular solve
+// L_IJ = S_IJ (D_J^{-1} L_JJ^{-1})^T) runs on the 5th-generation tensor cores as split-BF16x3:
+// a = a_hi + a_lo with a_hi = bf16(a), a_lo = bf16(a - a_hi); a*b ~ a_hi b_hi + a_hi b_lo +
+// a_lo b_hi, accumulated in FP32 in tensor memory (Henry, Tang, Heinecke, "Leveraging the
+// bfloat16 artificial intelligence datatype for higher-precision computations", ARITH 2019).
+// Complex products use the real embedding with stacked B planes: with B stored as three
+// 128-row planes [-B_i; B_r; B_i], one M=128 x N=256 MMA with A_r over rows [B_r; B_i] and one
+// with A_i over rows [-B_i; B_r] give [Re | Im] of A B^T in a 256-column accumulator.
+//
+// Data movement: every finished L tile is written once, by its owner, as bf16 operand planes
+// (opA: L_IJ [hi_r, hi_i, lo_r, lo_i]; opB: W_IJ = L_IJ D_J as [-W_i, W_r, W_i] x [hi, lo], or
+// T_J = D_J^{-1} L_JJ^{-1} for a diagonal tile), row-major with the K index contiguous.  TMA
+// tiled loads (64-byte swizzle) stage 32-wide K chunks into shared memory for the MMAs.
+//
+// Roles inside a 256-thread block: warp 0 lane 0 issues TMA loads, warp 1 lane 0 issues MMAs,
+// all 8 warps run the epilogues (warp w reads TMEM lanes 32*(w%4).., columns half w/4).
+// Diagonal tiles are factored (unpivoted LDL^T) and inverted with SIMT FP32 in shared memory.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstring>
+
+#include "device.cuh"
+#include "kernels.h"
+
+namespace d3m {
+
+namespace {
+constexpr int TB = 128;
+constexpr int NTHR = 256;
+constexpr int KC = 32;                          // K elements per chunk (64 bytes of bf16)
+constexpr uint32_t PLANE = TB * KC * 2;         // 8 KB: one 128-row plane of one chunk
+constexpr uint32_t STAGE_A = 4 * PLANE;         // 32 KB
+constexpr uint32_t STAGE_B = 6 * PLANE;         // 48 KB
+constexpr uint32_t STAGE = STAGE_A + STAGE_B;   // 80 KB
+constexpr uint32_t SMEM_S = 0;                  // TRSM A operand (4 chunks x 32 KB)
+constexpr uint32_t SMEM_T = 128 * 1024;         // TRSM B stages (2 x 48 KB)
+constexpr uint32_t SMEM_BYTES = SMEM_T + 2 * STAGE_B;   // 224 KB
+constexpr int LDS = 129;                        // c64 diagonal tile row stride (elements)
+constexpr uint32_t DIAG_AUX = 130 * 1024;       // d / column / scratch vectors of a diagonal task
+constexpr uint32_t TMEM_COLS = 512;
+constexpr uint32_t ACC1 = 0, ACC2 = 256;        // TMEM columns of the two accumulators
+
+// instruction descriptor: kind::f16, A/B bf16, D f32, both K-major, M = 128, N = 256
+constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((256u >> 3) << 17) | ((128u >> 4) << 24);
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// ------------------------------------------------------------------ mbarrier
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: false when the deadline passed (the caller records a timeout).
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint64_t deadline) {
+  while (!mbar_try_wait(bar, parity)) {
+    if (globaltimer_ns() > deadline) return false;
+  }
+  return true;
+}
+
+// ------------------------------------------------------------------ TMA
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const void* tmap, int x, int y, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(tmap)), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+__device__ __forceinline__ void tma_prefetch_desc(const void* tmap) {
+  asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(tmap)) : "memory");
+}
+
+// ------------------------------------------------------------------ tcgen05
+// Shared-memory matrix descriptor: K-major, 64-byte swizzle, 8-row groups 512 bytes apart.
+__device__ __forceinline__ uint64_t desc_sw64(uint32_t saddr) {
+  uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;                 // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(512u >> 4) << 32;       // stride byte offset
+  d |= (uint64_t)1 << 46;                 // descriptor version
+  d |= (uint64_t)4 << 61;                 // 64-byte swizzle
+  return d;
+}
+__device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t accum) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+      "l"(adesc), "l"(bdesc), "r"(IDESC), "r"(accum)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// ------------------------------------------------------------------ bf16 split helpers
+__device__ __forceinline__ void split2(float a, __nv_bfloat16& hi, __nv_bfloat16& lo) {
+  hi = __float2bfloat16_rn(a);
+  lo = __float2bfloat16_rn(a - __bfloat162float(hi));
+}
+// 8 values -> one 16-byte word of bf16 (hi or lo part)
+__device__ __forceinline__ uint4 pack8(const __nv_bfloat16* v) {
+  uint4 u;
+  u.x = (uint32_t)__bfloat16_as_ushort(v[0]) | ((uint32_t)__bfloat16_as_ushort(v[1]) << 16);
+  u.y = (uint32_t)__bfloat16_as_ushort(v[2]) | ((uint32_t)__bfloat16_as_ushort(v[3]) << 16);
+  u.z = (uint32_t)__bfloat16_as_ushort(v[4]) | ((uint32_t)__bfloat16_as_ushort(v[5]) << 16);
+  u.w = (uint32_t)__bfloat16_as_ushort(v[6]) | ((uint32_t)__bfloat16_as_ushort(v[7]) << 16);
+  return u;
+}
+
+// Write 32 consecutive K values (one chunk) of one row into a global operand plane row
+// (row-major, 128 bf16 per row) as hi and lo parts: dst_hi/dst_lo point at element c0.
+__device__ __forceinline__ void store_plane32(__nv_bfloat16* dst_hi, __nv_bfloat16* dst_lo, const float* v, float sign) {
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    __nv_bfloat16 h[8], l[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) split2(sign * v[q * 8 + e], h[e], l[e]);
+    reinterpret_cast<uint4*>(dst_hi)[q] = pack8(h);
+    reinterpret_cast<uint4*>(dst_lo)[q] = pack8(l);
+  }
+}
+
+// Write 32 K values of row r into a shared-memory K-major SW64 plane (one chunk) as hi/lo.
+__device__ __forceinline__ void store_smem_plane32(unsigned char* plane_hi, unsigned char* plane_lo, int r,
+                                                   const float* v) {
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    __nv_bfloat16 h[8], l[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) split2(v[q * 8 + e], h[e], l[e]);
+    const uint32_t off = (uint32_t)r * 64u + ((uint32_t)(q ^ ((r >> 1) & 3)) << 4);
+    *reinterpret_cast<uint4*>(plane_hi + off) = pack8(h);
+    *reinterpret_cast<uint4*>(plane_lo + off) = pack8(l);
+  }
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(NTHR, 1)
+    factor_tc_kernel(const FactorParams p, const __grid_constant__ CUtensorMap mapA,
+                     const __grid_constant__ CUtensorMap mapB) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  // 1024-byte alignment of the dynamic region (swizzle atoms)
+  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  __shared__ __align__(8) uint64_t bar_full[2], bar_empty[2], bar_tfull[2], bar_tempty[2], bar_acc, bar_acc2;
+  __shared__ uint32_t s_tmem;
+  __shared__ int s_task;
+  __shared__ float s_red[NTHR / 32];
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  float2* Lg = reinterpret_cast<float2*>(p.L);
+  float2* Linv = reinterpret_cast<float2*>(p.Linv);
+  float2* Dg = reinterpret_cast<float2*>(p.D);
+  __nv_bfloat16* opA = reinterpret_cast<__nv_bfloat16*>(p.opA);
+  __nv_bfloat16* opB = reinterpret_cast<__nv_bfloat16*>(p.opB);
+
+  if (tid == 0) {
+    for (int s = 0; s < 2; ++s) {
+      mbar_init(smem_u32(&bar_full[s]), 1);
+      mbar_init(smem_u32(&bar_empty[s]), 1);
+      mbar_init(smem_u32(&bar_tfull[s]), 1);
+      mbar_init(smem_u32(&bar_tempty[s]), 1);
+    }
+    mbar_init(smem_u32(&bar_acc), 1);
+    mbar_init(smem_u32(&bar_acc2), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    tma_prefetch_desc(&mapA);
+    tma_prefetch_desc(&mapB);
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = s_tmem;
+
+  // pipeline counters (each kept by the thread that uses it)
+  uint32_t g_load = 0, g_mma = 0, t_load = 0, t_mma = 0;
+  uint32_t n_acc = 0, n_acc2 = 0;
+  bool failed = false;
+
+  for (;;) {
+    const int task = sched_pop(p, &s_task);
+    if (task < 0) break;
+    const TileTask T = p.tasks[task];
+    const uint64_t deadline = globaltimer_ns() + (uint64_t)p.timeout_ns;
+    const int nchunk = T.nk * (TB / KC);
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+
+    // ---------------------------------------------------------------- phase 1: Schur GEMM
+    if (nchunk > 0) {
+      if (warp == 0) {
+        if (lane == 0) {
+          for (int c = 0; c < nchunk && !failed; ++c) {
+            const uint32_t s = g_load & 1, use = g_load >> 1;
+            if (!mbar_wait(smem_u32(&bar_empty[s]), (use & 1) ^ 1, deadline)) { failed = true; break; }
+            const KEntry ke = p.klist[T.kl_off + c / (TB / KC)];
+            const int x = (c % (TB / KC)) * KC;
+            const uint32_t sb = smem_u32(smem + s * STAGE);
+            const uint32_t fb = smem_u32(&bar_full[s]);
+            mbar_expect_tx(fb, STAGE);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) tma_load_2d(sb + q * PLANE, &mapA, x, ke.a_tile * 512 + q * 128, fb);
+#pragma unroll
+            for (int q = 0; q < 6; ++q) tma_load_2d(sb + STAGE_A + q * PLANE, &mapB, x, ke.b_tile * 768 + q * 128, fb);
+            ++g_load;
+          }
+        }
+        __syncwarp();
+      } else if (warp == 1) {
+        if (lane == 0) {
+          for (int c = 0; c < nchunk && !failed; ++c) {
+            const uint32_t s = g_mma & 1, use = g_mma >> 1;
+            if (!mbar_wait(smem_u32(&bar_full[s]), use & 1, deadline)) { failed = true; break; }
+            tc_fence_after();
+            const uint32_t sb = smem_u32(smem + s * STAGE);
+#pragma unroll
+            for (int kk = 0; kk < 2; ++kk) {
+              const uint32_t ko = kk * 32;
+              const uint32_t a_hr = sb + 0 * PLANE + ko, a_hi = sb + 1 * PLANE + ko;
+              const uint32_t a_lr = sb + 2 * PLANE + ko, a_li = sb + 3 * PLANE + ko;
+              const uint32_t bh = sb + STAGE_A + ko, bl = sb + STAGE_A + 3 * PLANE + ko;
+              const uint32_t first = (c == 0 && kk == 0) ? 0u : 1u;
+              // lo*hi and hi*lo first, then hi*hi
+              mma_bf16(tmem + ACC1, desc_sw64(a_lr), desc_sw64(bh + PLANE), first);
+              mma_bf16(tmem + ACC1, desc_sw64(a_li), desc_sw64(bh), 1u);
+              mma_bf16(tmem + ACC1, desc_sw64(a_hr), desc_sw64(bl + PLANE), 1u);
+              mma_bf16(tmem + ACC1, desc_sw64(a_hi), desc_sw64(bl), 1u);
+              mma_bf16(tmem + ACC1, desc_sw64(a_hr), desc_sw64(bh + PLANE), 1u);
+              mma_bf16(tmem + ACC1, desc_sw64(a_hi), desc_sw64(bh), 1u);
+            }
+            mma_commit(smem_u32(&bar_empty[s]));
+            ++g_mma;
+          }
+          mma_commit(smem_u32(&bar_acc));
+        }
+        __syncwarp();
+      }
+      if (!mbar_wait(smem_u32(&bar_acc), n_acc & 1, deadline)) failed = true;
+      ++n_acc;
+      tc_fence_after();
+    }
+    if (__syncthreads_or(failed)) {
+      if (tid == 0) set_error(p.ctl, D3M_ERR_TIMEOUT, task);
+      break;
+    }
+
+    // off-diagonal: prefetch the first two chunks of T_J (B operand of the TRSM product)
+    if (!T.is_diag && tid == 0) {
+      for (int c = 0; c < 2; ++c) {
+        const uint32_t s = t_load & 1, use = t_load >> 1;
+        if (!mbar_wait(smem_u32(&bar_tempty[s]), (use & 1) ^ 1, deadline)) { failed = true; break; }
+        const uint32_t sb = smem_u32(smem + SMEM_T + s * STAGE_B);
+        const uint32_t fb = smem_u32(&bar_tfull[s]);
+        mbar_expect_tx(fb, STAGE_B);
+#pragma unroll
+        for (int q = 0; q < 6; ++q) tma_load_2d(sb + q * PLANE, &mapB, c * KC, T.diag * 768 + q * 128, fb);
+        ++t_load;
+      }
+    }
+
+    // ---------------------------------------------------------------- phase 2: S = K - acc
+    const int quarter = warp & 3, half = warp >> 2;
+    const int r = quarter * 32 + lane;
+    if (T.is_diag) {
+      float2* sS = reinterpret_cast<float2*>(smem);   // [128][129]
+      float2* s_d = reinterpret_cast<float2*>(smem + DIAG_AUX);
+      float2* s_col = s_d + TB;
+      float2* s_tmp = s_col + TB;
+      for (int pass = 0; pass < 2; ++pass) {
+        const int c0 = half * 64 + pass * 32;
+        float vr[32], vi[32];
+        if (nchunk > 0) {
+          tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + ACC1 + c0, vr);
+          tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + ACC1 + 128 + c0, vi);
+        } else {
+#pragma unroll
+          for (int i = 0; i < 32; ++i) vr[i] = vi[i] = 0.f;
+        }
+#pragma unroll 4
+        for (int i = 0; i < 32; ++i) {
+          const float2 kv = k_entry<float>(T, p.K, r, c0 + i);
+          sS[r * LDS + c0 + i] = make_float2(kv.x - vr[i], kv.y - vi[i]);
+        }
+      }
+      tc_fence_before();
+      __syncthreads();
+      // max |S| over the real lower triangle (breakdown scale)
+      float mx = 0.f;
+      for (int i = tid; i < TB * TB; i += NTHR) {
+        const int rr = i >> 7, cc = i & 127;
+        if (cc <= rr && rr < T.rv) mx = fmaxf(mx, sqrtf(cabs2(sS[rr * LDS + cc])));
+      }
+      for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      if (lane == 0) s_red[warp] = mx;
+      // unpivoted LDL^T, right-looking on the lower triangle
+      for (int c = 0; c < TB; ++c) {
+        const float2 d = sS[c * LDS + c];
+        if (tid > c && tid < TB) {
+          const float2 v = sS[tid * LDS + c];
+          s_tmp[tid] = v;
+          s_col[tid] = cdiv(v, d);
+        }
+        if (tid == 0) s_d[c] = d;
+        __syncthreads();
+        for (int rr = c + 1 + (tid >> 1); rr < TB; rr += NTHR / 2) {
+          const float2 l = s_col[rr];
+          for (int ss = c + 1 + (tid & 1); ss <= rr; ss += 2)
+            sS[rr * LDS + ss] = cfms(l, s_tmp[ss], sS[rr * LDS + ss]);
+        }
+        if (tid > c && tid < TB) sS[tid * LDS + c] = s_col[tid];
+        __syncthreads();
+      }
+      if (tid < 32) {
+        float smax = 0.f;
+        for (int w = 0; w < NTHR / 32; ++w) smax = fmaxf(smax, s_red[w]);
+        float amin = 3.0e38f, amax = 0.f;
+        for (int c = tid; c < T.cv; c += 32) {
+          const float a = sqrtf(cabs2(s_d[c]));
+          amin = fminf(amin, a);
+          amax = fmaxf(amax, a);
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+          amin = fminf(amin, __shfl_xor_sync(0xffffffffu, amin, o));
+          amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+        }
+        if (tid == 0) {
+          record_pivot_stats(p.ctl, amin, amax);
+          if (!(amin >= (float)p.piv_tol * smax)) set_error(p.ctl, D3M_ERR_PIVOT, task);
+        }
+      }
+      // store L_JJ (unit lower) and D_J
+      float2* Lt = Lg + (int64_t)T.tile * TB * TB;
+      for (int i = tid; i < TB * TB; i += NTHR) {
+        const int rr = i >> 7, cc = i & 127;
+        Lt[i] = (cc < rr) ? sS[rr * LDS + cc] : make_float2(cc == rr ? 1.f : 0.f, 0.f);
+      }
+      if (tid < TB) Dg[(int64_t)T.col * TB + tid] = s_d[tid];
+      __syncthreads();
+      // in-place inverse of the unit lower tile (columns right to left)
+      for (int j = TB - 2; j >= 0; --j) {
+        // rows j+1..127; two threads per row split the dot product
+        const int rr = j + 1 + (tid >> 1);
+        float2 t = make_float2(0.f, 0.f);
+        if (rr < TB) {
+          for (int k = j + 1 + (tid & 1); k < rr; k += 2) t = cfma(sS[rr * LDS + k], sS[k * LDS + j], t);
+        }
+        t.x += __shfl_xor_sync(0xffffffffu, t.x, 1);
+        t.y += __shfl_xor_sync(0xffffffffu, t.y, 1);
+        if (rr < TB && (tid & 1) == 0) {
+          const float2 l = sS[rr * LDS + j];
+          s_tmp[rr] = make_float2(-(l.x + t.x), -(l.y + t.y));
+        }
+        __syncthreads();
+        if (tid > j && tid < TB) sS[tid * LDS + j] = s_tmp[tid];
+        __syncthreads();
+      }
+      // Linv (c64, for the solve) and T_J = D^{-1} Linv as B planes [-T_i, T_r, T_i] x [hi, lo]
+      float2* Li = Linv + (int64_t)T.col * TB * TB;
+      for (int i = tid; i < TB * TB; i += NTHR) {
+        const int rr = i >> 7, cc = i & 127;
+        Li[i] = (cc < rr) ? sS[rr * LDS + cc] : make_float2(cc == rr ? 1.f : 0.f, 0.f);
+      }
+      {
+        const int n = tid & 127, kh = tid >> 7;   // row n, K half kh (64 columns)
+        const float2 dinv = cdiv(make_float2(1.f, 0.f), s_d[n]);
+        __nv_bfloat16* base = opB + (int64_t)T.tile * 768 * TB;
+        for (int q = 0; q < 2; ++q) {
+          const int c0 = kh * 64 + q * 32;
+          float tr[32], ti[32];
+#pragma unroll
+          for (int i = 0; i < 32; ++i) {
+            const int k = c0 + i;
+            const float2 lv = (k < n) ? sS[n * LDS + k] : make_float2(k == n ? 1.f : 0.f, 0.f);
+            const float2 tv = cmul(dinv, lv);
+            tr[i] = tv.x;
+            ti[i] = tv.y;
+          }
+          // split s: rows 384*s + plane*128 + n
+          store_plane32(base + (0 * 128 + n) * TB + c0, base + (384 + 0 * 128 + n) * TB + c0, ti, -1.f);
+          store_plane32(base + (1 * 128 + n) * TB + c0, base + (384 + 1 * 128 + n) * TB + c0, tr, 1.f);
+          store_plane32(base + (2 * 128 + n) * TB + c0, base + (384 + 2 * 128 + n) * TB + c0, ti, 1.f);
+        }
+      }
+    } else {
+      // S planes for the TRSM product (A operand, SW64 K-major, 4 chunks)
+      for (int pass = 0; pass < 2; ++pass) {
+        const int c0 = half * 64 + pass * 32;
+        float vr[32], vi[32];
+        if (nchunk > 0) {
+          tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + ACC1 + c0, vr);
+          tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + ACC1 + 128 + c0, vi);
+        } else {
+#pragma unroll
+          for (int i = 0; i < 32; ++i) vr[i] = vi[i] = 0.f;
+        }
+#pragma unroll 4
+        for (int i = 0; i < 32; ++i) {
+          const float2 kv = k_entry<float>(T, p.K, r, c0 + i);
+          vr[i] = kv.x - vr[i];
+          vi[i] = kv.y - vi[i];
+        }
+        unsigned char* ch = smem + SMEM_S + (c0 / KC) * STAGE_A;
+        store_smem_plane32(ch + 0 * PLANE, ch + 2 * PLANE, r, vr);
+        store_smem_plane32(ch + 1 * PLANE, ch + 3 * PLANE, r, vi);
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      tc_fence_before();
+      __syncthreads();
+      // ---------------------------------------------------------------- phase 3: TRSM product
+      if (warp == 0) {
+        if (lane == 0) {
+          for (int c = 2; c < TB / KC && !failed; ++c) {
+            const uint32_t s = t_load & 1, use = t_load >> 1;
+            if (!mbar_wait(smem_u32(&bar_tempty[s]), (use & 1) ^ 1, deadline)) { failed = true; break; }
+            const uint32_t sb = smem_u32(smem + SMEM_T + s * STAGE_B);
+            const uint32_t fb = smem_u32(&bar_tfull[s]);
+            mbar_expect_tx(fb, STAGE_B);
+#pragma unroll
+            for (int q = 0; q < 6; ++q) tma_load_2d(sb + q * PLANE, &mapB, c * KC, T.diag * 768 + q * 128, fb);
+            ++t_load;
+          }
+        }
+        __syncwarp();
+      } else if (warp == 1) {
+        if (lane == 0) {
+          tc_fence_after();
+          for (int c = 0; c < TB / KC && !failed; ++c) {
+            const uint32_t s = t_mma & 1, use = t_mma >> 1;
+            if (!mbar_wait(smem_u32(&bar_tfull[s]), use & 1, deadline)) { failed = true; break; }
+            tc_fence_after();
+            const uint32_t ab = smem_u32(smem + SMEM_S + c * STAGE_A);
+            const uint32_t tb = smem_u32(smem + SMEM_T + s * STAGE_B);
+#pragma unroll
+            for (int kk = 0; kk < 2; ++kk) {
+              const uint32_t ko = kk * 32;
+              const uint32_t a_hr = ab + 0 * PLANE + ko, a_hi = ab + 1 * PLANE + ko;
+              const uint32_t a_lr = ab + 2 * PLANE + ko, a_li = ab + 3 * PLANE + ko;
+              const uint32_t bh = tb + ko, bl = tb + 3 * PLANE + ko;
+              const uint32_t first = (c == 0 && kk == 0) ? 0u : 1u;
+              mma_bf16(tmem + ACC2, desc_sw64(a_lr), desc_sw64(bh + PLANE), first);
+              mma_bf16(tmem + ACC2, desc_sw64(a_li), desc_sw64(bh), 1u);
+              mma_bf16(tmem + ACC2, desc_sw64(a_hr), desc_sw64(bl + PLANE), 1u);
+              mma_bf16(tmem + ACC2, desc_sw64(a_hi), desc_sw64(bl), 1u);
+              mma_bf16(tmem + ACC2, desc_sw64(a_hr), desc_sw64(bh + PLANE), 1u);
+              mma_bf16(tmem + ACC2, desc_sw64(a_hi), desc_sw64(bh), 1u);
+            }
+            mma_commit(smem_u32(&bar_tempty[s]));
+            ++t_mma;
+          }
+          mma_commit(smem_u32(&bar_acc2));
+        }
+        __syncwarp();
+      }
+      if (!mbar_wait(smem_u32(&bar_acc2), n_acc2 & 1, deadline)) failed = true;
+      ++n_acc2;
+      tc_fence_after();
+      if (__syncthreads_or(failed)) {
+        if (tid == 0) set_error(p.ctl, D3M_ERR_TIMEOUT, task);
+        break;
+      }
+      // D_J into the (now idle) TRSM stage area
+      float2* s_d = reinterpret_cast<float2*>(smem + SMEM_T);
+      if (tid < TB) s_d[tid] = ld_cg(Dg + (int64_t)T.col * TB + tid);
+      __syncthreads();
+      // ---------------------------------------------------------------- phase 4: store L_IJ
+      float2* Lt = Lg + (int64_t)T.tile * TB * TB;
+      __nv_bfloat16* A = opA + (int64_t)T.tile * 512 * TB;
+      __nv_bfloat16* B = opB + (int64_t)T.tile * 768 * TB;
+      for (int pass = 0; pass < 2; ++pass) {
+        const int c0 = half * 64 + pass * 32;
+        float lr[32], li[32], wr[32], wi[32];
+        tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + ACC2 + c0, lr);
+        tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + ACC2 + 128 + c0, li);
+        float4* Lrow = reinterpret_cast<float4*>(Lt + (int64_t)r * TB + c0);
+#pragma unroll
+        for (int i = 0; i < 32; i += 2) Lrow[i / 2] = make_float4(lr[i], li[i], lr[i + 1], li[i + 1]);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+          const float2 w = cmul(make_float2(lr[i], li[i]), s_d[c0 + i]);
+          wr[i] = w.x;
+          wi[i] = w.y;
+        }
+        // opA: rows 256*s + plane*128 + r  (planes r, i)
+        store_plane32(A + (0 * 128 + r) * TB + c0, A + (256 + 0 * 128 + r) * TB + c0, lr, 1.f);
+        store_plane32(A + (1 * 128 + r) * TB + c0, A + (256 + 1 * 128 + r) * TB + c0, li, 1.f);
+        // opB: rows 384*s + plane*128 + r  (planes -i, r, i)
+        store_plane32(B + (0 * 128 + r) * TB + c0, B + (384 + 0 * 128 + r) * TB + c0, wi, -1.f);
+        store_plane32(B + (1 * 128 + r) * TB + c0, B + (384 + 1 * 128 + r) * TB + c0, wr, 1.f);
+        store_plane32(B + (2 * 128 + r) * TB + c0, B + (384 + 2 * 128 + r) * TB + c0, wi, 1.f);
+      }
+    }
+    tc_fence_before();
+    sched_complete(p, task);
+  }
+
+  // teardown: after a failed wait, give in-flight copies and MMAs time to land (bounded)
+  if (failed || ld_volatile(&p.ctl->abort)) {
+    const uint64_t t0 = globaltimer_ns();
+    while (globaltimer_ns() - t0 < 2000000ull) __nanosleep(1000);
+  }
+  // TMEM is released by the allocating warp
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+}
+
+// ------------------------------------------------------------------ host side
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+int tc_make_maps(void* opA, void* opB, int64_t ntiles, TcMaps* out, std::string& err) {
+  static EncodeTiledFn encode = nullptr;
+  if (!encode) {
+    cudaDriverEntryPointQueryResult q;
+    void* fn = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn) {
+      cudaGetLastError();
+      err = "cuTensorMapEncodeTiled is not available from the driver";
+      return 1;
+    }
+    encode = (EncodeTiledFn)fn;
+  }
+  static_assert(sizeof(CUtensorMap) == 128, "CUtensorMap size");
+  const cuuint32_t box[2] = {(cuuint32_t)KC, (cuuint32_t)TB};
+  const cuuint32_t estr[2] = {1, 1};
+  const cuuint64_t stride[1] = {(cuuint64_t)TB * 2};
+  CUtensorMap ma, mb;
+  const cuuint64_t dimA[2] = {(cuuint64_t)TB, (cuuint64_t)ntiles * 512};
+  const cuuint64_t dimB[2] = {(cuuint64_t)TB, (cuuint64_t)ntiles * 768};
+  CUresult r1 = encode(&ma, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, opA, dimA, stride, box, estr,
+                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  CUresult r2 = encode(&mb, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, opB, dimB, stride, box, estr,
+                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r1 != CUDA_SUCCESS || r2 != CUDA_SUCCESS) {
+    err = "cuTensorMapEncodeTiled failed (" + std::to_string((int)r1) + ", " + std::to_string((int)r2) + ")";
+    return 1;
+  }
+  std::memcpy(out->a, &ma, 128);
+  std::memcpy(out->b, &mb, 128);
+  return 0;
+}
+
+int launch_factor_tc(const FactorParams& p, const TcMaps& maps, int nblocks, cudaStream_t st) {
+  const size_t smem = SMEM_BYTES + 1024;   // + alignment slack
+  cudaError_t e = cudaFuncSetAttribute(factor_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return (int)e;
+  CUtensorMap ma, mb;
+  std::memcpy(&ma, maps.a, 128);
+  std::memcpy(&mb, maps.b, 128);
+  factor_tc_kernel<<<nblocks, NTHR, smem, st>>>(p, ma, mb);
+  return (int)cudaGetLastError();
+}
+
+}  // namespace d3m

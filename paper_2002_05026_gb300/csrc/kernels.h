@@ -1,0 +1,80 @@
+// Launch interfaces of the device kernels (host side of the library).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "symbolic.h"
+
+namespace d3m {
+
+struct FactorParams;
+
+struct ResidualParams {
+  const double2* K;
+  const int64_t* kblk_off;
+  const int64_t* res_ptr;
+  const int32_t* res_blk;
+  const int32_t* res_src;
+  const int32_t* res_tr;
+  const int32_t* m_orig;
+  const int64_t* xoff_orig;
+  const int2* chunks;      // (block f, first row) of every 32-row chunk
+  int nrhs;
+  int rc;                  // rhs per thread block (<= 8)
+  int64_t n;
+  const double2* X;
+  const double2* B;
+  double2* R;
+  unsigned* rmax;          // [nrhs] max |r| as float bits
+  unsigned* xmax;          // [nrhs] max |x|
+  unsigned* kmax;          // ||K||_inf
+};
+
+struct SweepLaunch {
+  int b, nrhs, nlevels, max_rows, accumulate;
+  int64_t n, npad;
+  const double2* src;              // right-hand side (caller numbering, c128)
+  double2* dst;                    // solution (caller numbering, c128): = or += result
+  const int64_t* pad2orig;         // [npad] original row of a padded row, -1 for padding
+  const void* L;
+  const void* Linv;
+  const void* D;
+  void* Y;                         // [nrhs][npad] work vector
+  void* P;                         // partials
+  const int64_t* fwd_item_ptr;     // host [nlevels+1]
+  const int64_t* bwd_item_ptr;     // host [nlevels+1]
+  const SolveItem* fwd_items;      // device
+  const SolveItem* bwd_items;      // device
+  const int64_t* fwd_slot_ptr;     // device [NT]
+  const int64_t* bwd_slot_ptr;     // device [NT]
+  const int32_t* lev_blocks;       // device, blocks grouped by level
+  const int64_t* lev_ptr;          // host [nlevels+1]
+  const int32_t* tstart;           // device [N+1]
+  const int64_t* tcolptr;          // device [NT+1]
+};
+
+// Tensor maps (CUtensorMap, 128 bytes each) of the tensor-core operand planes.
+struct TcMaps {
+  alignas(64) unsigned char a[128];
+  alignas(64) unsigned char b[128];
+};
+
+int launch_factor_simt(const FactorParams& p, bool fp64, int nblocks, cudaStream_t st);
+int tc_make_maps(void* opA, void* opB, int64_t ntiles, TcMaps* out, std::string& err);
+int launch_factor_tc(const FactorParams& p, const TcMaps& maps, int nblocks, cudaStream_t st);
+int launch_sweep(const SweepLaunch& a, bool fp64, cudaStream_t st);
+int launch_residual(const ResidualParams& p, int nchunks, cudaStream_t st);
+int launch_knorm(const ResidualParams& p, int nchunks, cudaStream_t st);
+int launch_absmax(const double2* V, int64_t n, int nrhs, unsigned* out, cudaStream_t st);
+int launch_omega(const unsigned* rmax, const unsigned* xmax, const unsigned* bmax, const unsigned* kmax,
+                 int nrhs, double* omega, double* stat, cudaStream_t st);
+int launch_contract(const double2* Lam, const double2* X, int64_t n, int nrhs, const int64_t* xoff_orig,
+                    const int32_t* m_orig, int nblk, double2* out, cudaStream_t st);
+int launch_grad_pattern(const double2* Lam, const double2* X, int64_t n, int nrhs, const int64_t* colptr,
+                        const int32_t* rowidx, const int32_t* blk_col, const int64_t* kblk_off,
+                        const int64_t* xoff_orig, const int32_t* m_orig, int64_t nnzb, double2* dK,
+                        cudaStream_t st);
+
+}  // namespace d3m

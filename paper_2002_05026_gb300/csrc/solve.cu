@@ -1,0 +1,528 @@
+// Forward / diagonal / backward block sweeps (the "solution" half of the paper's "dual
+// factorization and solution", Sec. II), the FP64 residual r = b - K x over the stored K
+// (block SpMV, symmetric use of the lower blocks), the backward-error norms and the adjoint
+// contractions.
+//
+// Sweeps are level-scheduled over the block elimination tree (all blocks of one level are
+// independent): per level a gather kernel computes the off-block products of every tile
+// (forward: L_IJ y_J into tile row I; backward: L_IJ^T w_I into tile column J) as partials,
+// then a block kernel reduces them in a fixed order and runs the in-block tile chain with the
+// stored inverses of the diagonal tiles.  Vectors are permuted and padded to the tile grid:
+// Y[j * npad + row].
+#include <cuda_runtime.h>
+
+#include "device.cuh"
+#include "kernels.h"
+
+namespace d3m {
+
+namespace {
+constexpr int GT = 256;   // threads of gather / block kernels
+constexpr int HR = 64;    // rows of one staged half-tile
+
+template <typename R>
+__device__ __forceinline__ typename CT<R>::C czero() { return CT<R>::make(0, 0); }
+}  // namespace
+
+// ------------------------------------------------------------------ permutation + padding
+template <typename R>
+__global__ void permute_in_kernel(const double2* __restrict__ src, int64_t n,
+                                  typename CT<R>::C* __restrict__ Y, int64_t npad,
+                                  const int64_t* __restrict__ pad2orig, int nrhs) {
+  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (g >= npad) return;
+  const int64_t o = pad2orig[g];
+  for (int j = 0; j < nrhs; ++j)
+    Y[j * npad + g] = (o >= 0) ? CT<R>::from(src[j * n + o]) : CT<R>::make(0, 0);
+}
+
+template <typename R>
+__global__ void permute_out_kernel(const typename CT<R>::C* __restrict__ W, int64_t npad,
+                                   double2* __restrict__ X, int64_t n,
+                                   const int64_t* __restrict__ pad2orig, int nrhs, int accumulate) {
+  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (g >= npad) return;
+  const int64_t o = pad2orig[g];
+  if (o < 0) return;
+  for (int j = 0; j < nrhs; ++j) {
+    const typename CT<R>::C w = W[j * npad + g];
+    double2 v = make_double2((double)w.x, (double)w.y);
+    if (accumulate) {
+      const double2 x = X[j * n + o];
+      v.x += x.x;
+      v.y += x.y;
+    }
+    X[j * n + o] = v;
+  }
+}
+
+// ------------------------------------------------------------------ gather (off-block tiles)
+// grid.x = items of the level * (b / 64) halves.  FWD: P[slot][r][j] (rows of this half) =
+// sum_k L[r][k] Y[src*b + k][j].  BWD: P[slot*nh + h][c][j] = sum_{r in half h} L[r][c] W[src*b + r][j].
+template <typename R, bool FWD>
+__global__ void __launch_bounds__(GT) gather_kernel(const SolveItem* __restrict__ items,
+                                                    const typename CT<R>::C* __restrict__ L,
+                                                    const typename CT<R>::C* __restrict__ Y,
+                                                    typename CT<R>::C* __restrict__ P,
+                                                    int64_t npad, int b, int nrhs) {
+  using C = typename CT<R>::C;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int nh = b / HR;
+  const int ldl = b + 1;
+  C* sL = reinterpret_cast<C*>(smem_raw);      // [64][b+1]
+  C* sY = sL + HR * ldl;                       // [rows][nrhs]
+  const SolveItem it = items[blockIdx.x / nh];
+  const int h = blockIdx.x % nh;
+  const C* Lt = L + (int64_t)it.tile * b * b + (int64_t)h * HR * b;
+  for (int i = threadIdx.x; i < HR * b; i += GT) {
+    const int r = i / b, c = i - r * b;
+    sL[r * ldl + c] = Lt[i];
+  }
+  if (FWD) {
+    for (int i = threadIdx.x; i < b * nrhs; i += GT) {
+      const int k = i % b, j = i / b;
+      sY[k * nrhs + j] = Y[j * npad + (int64_t)it.src * b + k];
+    }
+  } else {
+    for (int i = threadIdx.x; i < HR * nrhs; i += GT) {
+      const int k = i % HR, j = i / HR;
+      sY[k * nrhs + j] = Y[j * npad + (int64_t)it.src * b + h * HR + k];
+    }
+  }
+  __syncthreads();
+  if (FWD) {
+    // thread: row r of this half, rhs j = g, g + G, ...
+    const int G = GT / HR;
+    const int r = threadIdx.x % HR, g = threadIdx.x / HR;
+    C* out = P + (int64_t)it.slot * nh * b * nrhs;   // sub-slot 0 of the item
+    for (int j = g; j < nrhs; j += G) {
+      C acc = czero<R>();
+      for (int k = 0; k < b; ++k) acc = cfma(sL[r * ldl + k], sY[k * nrhs + j], acc);
+      out[(int64_t)(h * HR + r) * nrhs + j] = acc;
+    }
+  } else {
+    const int G = GT / b;
+    const int c = threadIdx.x % b, g = threadIdx.x / b;
+    C* out = P + ((int64_t)it.slot * nh + h) * b * nrhs;
+    for (int j = g; j < nrhs; j += G) {
+      C acc = czero<R>();
+      for (int r = 0; r < HR; ++r) acc = cfma(sL[r * ldl + c], sY[r * nrhs + j], acc);
+      out[(int64_t)c * nrhs + j] = acc;
+    }
+  }
+}
+
+// ------------------------------------------------------------------ in-block chains
+struct BlockSweep {
+  const int32_t* blocks;     // blocks of this level
+  const int32_t* tstart;     // [N+1]
+  const int64_t* tcolptr;    // [NT+1]
+  const int64_t* slot_ptr;   // [NT] first | count << 32
+  int64_t npad;
+  int b, nrhs, rc;           // rhs handled per block (grid.y = ceil(nrhs / rc))
+};
+
+// Stage a 64-row chunk of a b x b tile into shared memory.
+template <typename C>
+__device__ __forceinline__ void stage_rows(C* sL, const C* src, int b, int r0) {
+  const int ldl = b + 1;
+  for (int i = threadIdx.x; i < HR * b; i += GT) {
+    const int r = i / b, c = i - r * b;
+    sL[r * ldl + c] = src[(int64_t)(r0 + r) * b + c];
+  }
+}
+
+// forward: r = y_k - sum partials;  y_t = Linv_tt r_t;  r_t' -= L_t't y_t;  z = D^{-1} y
+template <typename R>
+__global__ void __launch_bounds__(GT) block_fwd_kernel(BlockSweep s, const typename CT<R>::C* __restrict__ L,
+                                                       const typename CT<R>::C* __restrict__ Linv,
+                                                       const typename CT<R>::C* __restrict__ D,
+                                                       typename CT<R>::C* __restrict__ Y,
+                                                       const typename CT<R>::C* __restrict__ P) {
+  using C = typename CT<R>::C;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int b = s.b, ldl = b + 1, nh = b / HR;
+  const int k = s.blocks[blockIdx.x];
+  const int j0 = blockIdx.y * s.rc;
+  const int rc = min(s.rc, s.nrhs - j0);
+  const int t0 = s.tstart[k], nt = s.tstart[k + 1] - t0;
+  const int rows = nt * b;
+  C* sL = reinterpret_cast<C*>(smem_raw);      // [64][b+1]
+  C* sv = sL + HR * ldl;                       // [rows][rc]  running r / y
+  C* sy = sv + (int64_t)rows * s.rc;           // [b][rc]     y_t
+  (void)nh;
+  // 1. r = Y - sum of partials (fixed slot order)
+  for (int i = threadIdx.x; i < rows * rc; i += GT) {
+    const int row = i % rows, j = i / rows;
+    const int I = t0 + row / b;
+    C v = Y[(int64_t)(j0 + j) * s.npad + (int64_t)t0 * b + row];
+    const int64_t sp = s.slot_ptr[I];
+    const int64_t first = sp & 0xffffffffLL, cnt = sp >> 32;
+    for (int64_t q = 0; q < cnt; ++q) {
+      const C pv = P[((first + q) * (b / HR)) * (int64_t)b * s.nrhs + (int64_t)(row % b) * s.nrhs + j0 + j];
+      v = csub(v, pv);
+    }
+    sv[row * s.rc + j] = v;
+  }
+  __syncthreads();
+  for (int t = 0; t < nt; ++t) {
+    const int J = t0 + t;
+    // y_t = Linv_J r_t
+    for (int h = 0; h < b / HR; ++h) {
+      stage_rows(sL, Linv + (int64_t)J * b * b, b, h * HR);
+      __syncthreads();
+      for (int i = threadIdx.x; i < HR * rc; i += GT) {
+        const int r = i % HR, j = i / HR;
+        C acc = czero<R>();
+        for (int c = 0; c < b; ++c) acc = cfma(sL[r * ldl + c], sv[(t * b + c) * s.rc + j], acc);
+        sy[(h * HR + r) * s.rc + j] = acc;
+      }
+      __syncthreads();
+    }
+    for (int i = threadIdx.x; i < b * rc; i += GT) {
+      const int r = i % b, j = i / b;
+      sv[(t * b + r) * s.rc + j] = sy[r * s.rc + j];
+    }
+    __syncthreads();
+    // r_t' -= L_{t', t} y_t  for t' > t (tile ids follow the diagonal tile in column J)
+    for (int tp = t + 1; tp < nt; ++tp) {
+      const C* Lt = L + (s.tcolptr[J] + (tp - t)) * (int64_t)b * b;
+      for (int h = 0; h < b / HR; ++h) {
+        stage_rows(sL, Lt, b, h * HR);
+        __syncthreads();
+        for (int i = threadIdx.x; i < HR * rc; i += GT) {
+          const int r = i % HR, j = i / HR;
+          C acc = sv[(tp * b + h * HR + r) * s.rc + j];
+          for (int c = 0; c < b; ++c) acc = cfms(sL[r * ldl + c], sy[c * s.rc + j], acc);
+          sv[(tp * b + h * HR + r) * s.rc + j] = acc;
+        }
+        __syncthreads();
+      }
+    }
+  }
+  // z = D^{-1} y  (Y now holds z)
+  for (int i = threadIdx.x; i < rows * rc; i += GT) {
+    const int row = i % rows, j = i / rows;
+    const C d = D[(int64_t)t0 * b + row];
+    Y[(int64_t)(j0 + j) * s.npad + (int64_t)t0 * b + row] = cdiv(sv[row * s.rc + j], d);
+  }
+}
+
+// backward: r = z_k - sum partials;  for t = nt-1..0: w_t = Linv_tt^T r_t; r_t' -= L_{t,t'}^T w_t (t' < t)
+template <typename R>
+__global__ void __launch_bounds__(GT) block_bwd_kernel(BlockSweep s, const typename CT<R>::C* __restrict__ L,
+                                                       const typename CT<R>::C* __restrict__ Linv,
+                                                       typename CT<R>::C* __restrict__ Y,
+                                                       const typename CT<R>::C* __restrict__ P) {
+  using C = typename CT<R>::C;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int b = s.b, ldl = b + 1, nh = b / HR;
+  const int k = s.blocks[blockIdx.x];
+  const int j0 = blockIdx.y * s.rc;
+  const int rc = min(s.rc, s.nrhs - j0);
+  const int t0 = s.tstart[k], nt = s.tstart[k + 1] - t0;
+  const int rows = nt * b;
+  C* sL = reinterpret_cast<C*>(smem_raw);
+  C* sv = sL + HR * ldl;
+  C* sy = sv + (int64_t)rows * s.rc;
+  for (int i = threadIdx.x; i < rows * rc; i += GT) {
+    const int row = i % rows, j = i / rows;
+    const int J = t0 + row / b;
+    C v = Y[(int64_t)(j0 + j) * s.npad + (int64_t)t0 * b + row];
+    const int64_t sp = s.slot_ptr[J];
+    const int64_t first = sp & 0xffffffffLL, cnt = sp >> 32;
+    for (int64_t q = 0; q < cnt; ++q)
+      for (int h = 0; h < nh; ++h) {
+        const C pv = P[((first + q) * nh + h) * (int64_t)b * s.nrhs + (int64_t)(row % b) * s.nrhs + j0 + j];
+        v = csub(v, pv);
+      }
+    sv[row * s.rc + j] = v;
+  }
+  __syncthreads();
+  for (int t = nt - 1; t >= 0; --t) {
+    const int J = t0 + t;
+    // w_t = Linv_J^T r_t  : out[c] = sum_r Linv[r][c] r[r]
+    for (int i = threadIdx.x; i < b * rc; i += GT) sy[i] = czero<R>();
+    __syncthreads();
+    for (int h = 0; h < nh; ++h) {
+      stage_rows(sL, Linv + (int64_t)J * b * b, b, h * HR);
+      __syncthreads();
+      for (int i = threadIdx.x; i < b * rc; i += GT) {
+        const int c = i % b, j = i / b;
+        C acc = sy[c * s.rc + j];
+        for (int r = 0; r < HR; ++r) acc = cfma(sL[r * ldl + c], sv[(t * b + h * HR + r) * s.rc + j], acc);
+        sy[c * s.rc + j] = acc;
+      }
+      __syncthreads();
+    }
+    for (int i = threadIdx.x; i < b * rc; i += GT) {
+      const int r = i % b, j = i / b;
+      sv[(t * b + r) * s.rc + j] = sy[r * s.rc + j];
+    }
+    __syncthreads();
+    // r_t' -= L_{t, t'}^T w_t for t' < t; tile (t0+t, t0+t') is entry (t - t') of column t0+t'
+    for (int tp = 0; tp < t; ++tp) {
+      const C* Lt = L + (s.tcolptr[t0 + tp] + (t - tp)) * (int64_t)b * b;
+      for (int h = 0; h < nh; ++h) {
+        stage_rows(sL, Lt, b, h * HR);
+        __syncthreads();
+        for (int i = threadIdx.x; i < b * rc; i += GT) {
+          const int c = i % b, j = i / b;
+          C acc = sv[(tp * b + c) * s.rc + j];
+          for (int r = 0; r < HR; ++r) acc = cfms(sL[r * ldl + c], sy[(h * HR + r) * s.rc + j], acc);
+          sv[(tp * b + c) * s.rc + j] = acc;
+        }
+        __syncthreads();
+      }
+    }
+  }
+  for (int i = threadIdx.x; i < rows * rc; i += GT) {
+    const int row = i % rows, j = i / rows;
+    Y[(int64_t)(j0 + j) * s.npad + (int64_t)t0 * b + row] = sv[row * s.rc + j];
+  }
+}
+
+// ------------------------------------------------------------------ FP64 residual
+// r = b - K x (caller numbering), one thread per (row, rhs); |r| and |x| maxima per column.
+__global__ void __launch_bounds__(256) residual_kernel(ResidualParams p) {
+  const int rc = p.rc;
+  const int i = threadIdx.x % 32, jl = threadIdx.x / 32;
+  const int j = blockIdx.y * rc + jl;
+  const int2 ch = p.chunks[blockIdx.x];
+  const int f = ch.x, u = ch.y + i;
+  const int mf = p.m_orig[f];
+  const bool active = (u < mf) && (jl < rc) && (j < p.nrhs);
+  double2 acc = make_double2(0.0, 0.0);
+  if (active) {
+    for (int64_t e = p.res_ptr[f]; e < p.res_ptr[f + 1]; ++e) {
+      const int blk = p.res_blk[e], g = p.res_src[e];
+      const int mg = p.m_orig[g];
+      const double2* Kp = p.K + p.kblk_off[blk];
+      const double2* xg = p.X + (int64_t)j * p.n + p.xoff_orig[g];
+      if (p.res_tr[e]) {
+        const double2* row = Kp + (int64_t)u * mg;   // stored (g, f): entry (c, u)
+        for (int c = 0; c < mg; ++c) acc = cfma(__ldg(row + c), __ldg(xg + c), acc);
+      } else {
+        const double2* col = Kp + u;                 // stored (f, g): entry (u, c)
+        for (int c = 0; c < mg; ++c) acc = cfma(__ldg(col + (int64_t)c * mf), __ldg(xg + c), acc);
+      }
+    }
+  }
+  float ra = 0.f, xa = 0.f;
+  if (active) {
+    const int64_t o = (int64_t)j * p.n + p.xoff_orig[f] + u;
+    const double2 bv = p.B[o];
+    const double2 r = make_double2(bv.x - acc.x, bv.y - acc.y);
+    p.R[o] = r;
+    const float rx = (float)r.x, ry = (float)r.y;
+    ra = sqrtf(rx * rx + ry * ry);
+    const double2 xv = p.X[o];
+    const float xx = (float)xv.x, xy = (float)xv.y;
+    xa = sqrtf(xx * xx + xy * xy);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    ra = fmaxf(ra, __shfl_xor_sync(0xffffffffu, ra, o));
+    xa = fmaxf(xa, __shfl_xor_sync(0xffffffffu, xa, o));
+  }
+  if (i == 0 && jl < rc && j < p.nrhs) {
+    atomicMax(p.rmax + j, __float_as_uint(ra));
+    atomicMax(p.xmax + j, __float_as_uint(xa));
+  }
+}
+
+// ||K||_inf row sums (float magnitudes; a scale for omega) and ||b||_inf per column.
+__global__ void __launch_bounds__(256) knorm_kernel(ResidualParams p) {
+  const int i = threadIdx.x % 32, part = threadIdx.x / 32;   // 8 warps split the contributions
+  const int2 ch = p.chunks[blockIdx.x];
+  const int f = ch.x, u = ch.y + i;
+  const int mf = p.m_orig[f];
+  __shared__ float s_sum[8][32];
+  float sum = 0.f;
+  if (u < mf) {
+    for (int64_t e = p.res_ptr[f] + part; e < p.res_ptr[f + 1]; e += 8) {
+      const int blk = p.res_blk[e], g = p.res_src[e];
+      const int mg = p.m_orig[g];
+      const double2* Kp = p.K + p.kblk_off[blk];
+      for (int c = 0; c < mg; ++c) {
+        const double2 v = p.res_tr[e] ? __ldg(Kp + (int64_t)u * mg + c) : __ldg(Kp + (int64_t)c * mf + u);
+        const float a = (float)v.x, bb = (float)v.y;
+        sum += sqrtf(a * a + bb * bb);
+      }
+    }
+  }
+  s_sum[part][i] = sum;
+  __syncthreads();
+  if (part == 0) {
+    float t = 0.f;
+    for (int q = 0; q < 8; ++q) t += s_sum[q][i];
+    for (int o = 16; o > 0; o >>= 1) t = fmaxf(t, __shfl_xor_sync(0xffffffffu, t, o));
+    if (i == 0) atomicMax(p.kmax, __float_as_uint(t));
+  }
+}
+
+__global__ void vec_absmax_kernel(const double2* __restrict__ V, int64_t n, int nrhs, unsigned* out) {
+  const int j = blockIdx.y;
+  float a = 0.f;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double2 v = V[(int64_t)j * n + i];
+    const float x = (float)v.x, y = (float)v.y;
+    a = fmaxf(a, sqrtf(x * x + y * y));
+  }
+  for (int o = 16; o > 0; o >>= 1) a = fmaxf(a, __shfl_xor_sync(0xffffffffu, a, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out + j, __float_as_uint(a));
+}
+
+// omega_j = |r|_j / (||K|| |x|_j + |b|_j);  stat[0] = max_j omega_j
+__global__ void omega_kernel(const unsigned* rmax, const unsigned* xmax, const unsigned* bmax,
+                             const unsigned* kmax, int nrhs, double* omega, double* stat) {
+  double w = 0.0;
+  const double kn = (double)__uint_as_float(*kmax);
+  for (int j = 0; j < nrhs; ++j) {
+    const double r = __uint_as_float(rmax[j]), x = __uint_as_float(xmax[j]), bb = __uint_as_float(bmax[j]);
+    const double den = kn * x + bb;
+    const double o = den > 0 ? r / den : (r > 0 ? 1.0 : 0.0);
+    omega[j] = o;
+    w = fmax(w, o);
+  }
+  stat[0] = w;
+}
+
+// per-interface complex contraction s_f = sum_j sum_u Lambda_uj X_uj (FP64)
+__global__ void contract_kernel(const double2* __restrict__ Lam, const double2* __restrict__ X, int64_t n,
+                                int nrhs, const int64_t* __restrict__ xoff_orig, const int32_t* __restrict__ m_orig,
+                                double2* __restrict__ out) {
+  const int f = blockIdx.x;
+  const int mf = m_orig[f];
+  double2 acc = make_double2(0.0, 0.0);
+  for (int i = threadIdx.x; i < mf * nrhs; i += blockDim.x) {
+    const int u = i % mf, j = i / mf;
+    const int64_t o = (int64_t)j * n + xoff_orig[f] + u;
+    acc = cfma(Lam[o], X[o], acc);
+  }
+  __shared__ double2 s[256];
+  s[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) s[threadIdx.x] = cadd(s[threadIdx.x], s[threadIdx.x + w]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[f] = s[0];
+}
+
+// dK_fg(u, v) = -sum_j (Lam_f[u,j] X_g[v,j] + [f != g] X_f[u,j] Lam_g[v,j]), column-major block
+__global__ void grad_pattern_kernel(const double2* __restrict__ Lam, const double2* __restrict__ X, int64_t n,
+                                    int nrhs, const int64_t* __restrict__ colptr, const int32_t* __restrict__ rowidx,
+                                    const int32_t* __restrict__ blk_col, const int64_t* __restrict__ kblk_off,
+                                    const int64_t* __restrict__ xoff_orig, const int32_t* __restrict__ m_orig,
+                                    double2* __restrict__ dK) {
+  const int e = blockIdx.x;
+  const int g = blk_col[e], f = rowidx[e];
+  const int mf = m_orig[f], mg = m_orig[g];
+  double2* out = dK + kblk_off[e];
+  for (int64_t i = blockIdx.y * (int64_t)blockDim.x + threadIdx.x; i < (int64_t)mf * mg;
+       i += (int64_t)gridDim.y * blockDim.x) {
+    const int u = (int)(i % mf), v = (int)(i / mf);
+    double2 acc = make_double2(0.0, 0.0);
+    for (int j = 0; j < nrhs; ++j) {
+      const int64_t of = (int64_t)j * n + xoff_orig[f] + u, og = (int64_t)j * n + xoff_orig[g] + v;
+      acc = cfma(Lam[of], X[og], acc);
+      if (f != g) acc = cfma(X[of], Lam[og], acc);
+    }
+    out[i] = make_double2(-acc.x, -acc.y);
+  }
+  (void)colptr;
+}
+
+// ------------------------------------------------------------------ launchers
+template <typename R>
+static int sweep_impl(const SweepLaunch& a, cudaStream_t st) {
+  using C = typename CT<R>::C;
+  const int b = a.b;
+  const int nthreads = 256;
+  const int64_t gblocks = (a.npad + nthreads - 1) / nthreads;
+  const C* L = (const C*)a.L;
+  const C* Linv = (const C*)a.Linv;
+  const C* D = (const C*)a.D;
+  C* Y = (C*)a.Y;
+  C* P = (C*)a.P;
+  permute_in_kernel<R><<<(unsigned)gblocks, nthreads, 0, st>>>(a.src, a.n, Y, a.npad, a.pad2orig, a.nrhs);
+  const size_t gsm = sizeof(C) * ((size_t)HR * (b + 1) + (size_t)b * a.nrhs);
+  const int rc = a.nrhs < 8 ? a.nrhs : 8;
+  const size_t bsm = sizeof(C) * ((size_t)HR * (b + 1) + (size_t)a.max_rows * rc + (size_t)b * rc);
+  cudaFuncSetAttribute(gather_kernel<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm);
+  cudaFuncSetAttribute(gather_kernel<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm);
+  cudaFuncSetAttribute(block_fwd_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bsm);
+  cudaFuncSetAttribute(block_bwd_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bsm);
+  BlockSweep bs;
+  bs.tstart = a.tstart;
+  bs.tcolptr = a.tcolptr;
+  bs.npad = a.npad;
+  bs.b = b;
+  bs.nrhs = a.nrhs;
+  bs.rc = rc;
+  const int nh = b / HR;
+  const unsigned ny = (unsigned)((a.nrhs + rc - 1) / rc);
+  for (int lv = 0; lv < a.nlevels; ++lv) {
+    const int64_t i0 = a.fwd_item_ptr[lv], i1 = a.fwd_item_ptr[lv + 1];
+    if (i1 > i0)
+      gather_kernel<R, true><<<(unsigned)((i1 - i0) * nh), GT, gsm, st>>>(a.fwd_items + i0, L, Y, P, a.npad, b, a.nrhs);
+    bs.blocks = a.lev_blocks + a.lev_ptr[lv];
+    bs.slot_ptr = a.fwd_slot_ptr;
+    const unsigned nb = (unsigned)(a.lev_ptr[lv + 1] - a.lev_ptr[lv]);
+    block_fwd_kernel<R><<<dim3(nb, ny), GT, bsm, st>>>(bs, L, Linv, D, Y, P);
+  }
+  for (int lv = a.nlevels - 1; lv >= 0; --lv) {
+    const int64_t i0 = a.bwd_item_ptr[lv], i1 = a.bwd_item_ptr[lv + 1];
+    if (i1 > i0)
+      gather_kernel<R, false><<<(unsigned)((i1 - i0) * nh), GT, gsm, st>>>(a.bwd_items + i0, L, Y, P, a.npad, b, a.nrhs);
+    bs.blocks = a.lev_blocks + a.lev_ptr[lv];
+    bs.slot_ptr = a.bwd_slot_ptr;
+    const unsigned nb = (unsigned)(a.lev_ptr[lv + 1] - a.lev_ptr[lv]);
+    block_bwd_kernel<R><<<dim3(nb, ny), GT, bsm, st>>>(bs, L, Linv, Y, P);
+  }
+  permute_out_kernel<R><<<(unsigned)gblocks, nthreads, 0, st>>>(Y, a.npad, a.dst, a.n, a.pad2orig, a.nrhs, a.accumulate);
+  return (int)cudaGetLastError();
+}
+
+int launch_sweep(const SweepLaunch& a, bool fp64, cudaStream_t st) {
+  return fp64 ? sweep_impl<double>(a, st) : sweep_impl<float>(a, st);
+}
+
+int launch_residual(const ResidualParams& p, int nchunks, cudaStream_t st) {
+  const dim3 grid((unsigned)nchunks, (unsigned)((p.nrhs + p.rc - 1) / p.rc));
+  residual_kernel<<<grid, 32 * p.rc, 0, st>>>(p);
+  return (int)cudaGetLastError();
+}
+
+int launch_knorm(const ResidualParams& p, int nchunks, cudaStream_t st) {
+  knorm_kernel<<<nchunks, 256, 0, st>>>(p);
+  return (int)cudaGetLastError();
+}
+
+int launch_absmax(const double2* V, int64_t n, int nrhs, unsigned* out, cudaStream_t st) {
+  const int64_t nb = (n + 255) / 256;
+  vec_absmax_kernel<<<dim3((unsigned)(nb < 1024 ? nb : 1024), (unsigned)nrhs), 256, 0, st>>>(V, n, nrhs, out);
+  return (int)cudaGetLastError();
+}
+
+int launch_omega(const unsigned* rmax, const unsigned* xmax, const unsigned* bmax, const unsigned* kmax,
+                 int nrhs, double* omega, double* stat, cudaStream_t st) {
+  omega_kernel<<<1, 1, 0, st>>>(rmax, xmax, bmax, kmax, nrhs, omega, stat);
+  return (int)cudaGetLastError();
+}
+
+int launch_contract(const double2* Lam, const double2* X, int64_t n, int nrhs, const int64_t* xoff_orig,
+                    const int32_t* m_orig, int nblk, double2* out, cudaStream_t st) {
+  contract_kernel<<<nblk, 256, 0, st>>>(Lam, X, n, nrhs, xoff_orig, m_orig, out);
+  return (int)cudaGetLastError();
+}
+
+int launch_grad_pattern(const double2* Lam, const double2* X, int64_t n, int nrhs, const int64_t* colptr,
+                        const int32_t* rowidx, const int32_t* blk_col, const int64_t* kblk_off,
+                        const int64_t* xoff_orig, const int32_t* m_orig, int64_t nnzb, double2* dK, cudaStream_t st) {
+  grad_pattern_kernel<<<dim3((unsigned)nnzb, 16), 256, 0, st>>>(Lam, X, n, nrhs, colptr, rowidx, blk_col, kblk_off,
+                                                                 xoff_orig, m_orig, dK);
+  return (int)cudaGetLastError();
+}
+
+}  // namespace d3m

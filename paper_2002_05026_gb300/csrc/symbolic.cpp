@@ -1,0 +1,412 @@
+// Host symbolic analysis of the D3M dual matrix K (paper Sec. II: the task graph is produced
+// by a symbolic simulation of the sequential algorithm; Fig. 1(c)).
+//
+// Block level: struct(k) of the block factor (block elimination tree + fill).
+// Tile level: every block is cut into b x b tiles (padded to a multiple of b; the padding
+// unknowns carry a unit diagonal and no coupling, which leaves the factor of the real
+// unknowns unchanged).  One task per lower tile (I, J) of L accumulates its Schur updates
+// S_IJ = K_IJ - sum_K L_IK D_K L_JK^T in a fixed K order, then either factors the diagonal
+// tile (I == J) or applies the triangular solve L_IJ = S_IJ L_JJ^{-T} D_J^{-1}.
+#include "symbolic.h"
+
+#include <algorithm>
+#include <cstdio>
+#include <functional>
+#include <numeric>
+
+namespace d3m {
+
+int64_t Symbolic::tile_of(int I, int J) const {
+  if (J < 0 || J >= NT) return -1;
+  const int32_t* first = trow.data() + tcolptr[J];
+  const int32_t* last = trow.data() + tcolptr[J + 1];
+  const int32_t* it = std::lower_bound(first, last, I);
+  if (it == last || *it != I) return -1;
+  return tcolptr[J] + (it - first);
+}
+
+static int fail(std::string& err, const char* msg, long a = -1, long b = -1) {
+  char buf[256];
+  snprintf(buf, sizeof buf, msg, a, b);
+  err = buf;
+  return D3M_ERR_INVALID;
+}
+
+int analyze(const d3m_pattern* pat, const int32_t* perm_in, int b, bool build_tasks,
+            Symbolic& s, std::string& err) {
+  if (!pat || !pat->colptr || !pat->rowidx) return fail(err, "pattern or its arrays are NULL");
+  const int N = pat->nblk;
+  if (N <= 0) return fail(err, "nblk must be positive (got %ld)", N);
+  if (b <= 0 || b > 1024) return fail(err, "tile edge %ld out of range", b);
+  s = Symbolic();
+  s.N = N;
+  s.b = b;
+  // ---------------------------------------------------------------- validation
+  s.m_orig.resize(N);
+  for (int f = 0; f < N; ++f) {
+    int mf = pat->blk_size ? pat->blk_size[f] : pat->m;
+    if (mf <= 0) return fail(err, "block %ld has non-positive size %ld", f, mf);
+    s.m_orig[f] = mf;
+  }
+  if (pat->colptr[0] != 0) return fail(err, "colptr[0] must be 0");
+  s.colptr.assign(pat->colptr, pat->colptr + N + 1);
+  for (int g = 0; g < N; ++g) {
+    int64_t a = s.colptr[g], e = s.colptr[g + 1];
+    if (e <= a) return fail(err, "column %ld has no diagonal block", g);
+    if (pat->rowidx[a] != g) return fail(err, "column %ld does not start with its diagonal", g);
+    for (int64_t p = a + 1; p < e; ++p) {
+      int r = pat->rowidx[p];
+      if (r <= pat->rowidx[p - 1] || r >= N)
+        return fail(err, "column %ld: row indices must ascend within [col, N) (row %ld)", g, r);
+    }
+  }
+  s.nnzb_K = s.colptr[N];
+  s.rowidx.assign(pat->rowidx, pat->rowidx + s.nnzb_K);
+  s.kblk_off.assign(s.nnzb_K + 1, 0);
+  for (int g = 0; g < N; ++g)
+    for (int64_t p = s.colptr[g]; p < s.colptr[g + 1]; ++p)
+      s.kblk_off[p + 1] = s.kblk_off[p] + (int64_t)s.m_orig[s.rowidx[p]] * s.m_orig[g];
+  s.perm.resize(N);
+  s.inv.assign(N, -1);
+  for (int k = 0; k < N; ++k) {
+    int f = perm_in ? perm_in[k] : k;
+    if (f < 0 || f >= N || s.inv[f] >= 0) return fail(err, "perm is not a permutation (entry %ld)", k);
+    s.perm[k] = f;
+    s.inv[f] = k;
+  }
+  s.m.resize(N);
+  for (int k = 0; k < N; ++k) s.m[k] = s.m_orig[s.perm[k]];
+  s.xoff_orig.assign(N + 1, 0);
+  for (int f = 0; f < N; ++f) s.xoff_orig[f + 1] = s.xoff_orig[f] + s.m_orig[f];
+  s.n = s.xoff_orig[N];
+
+  // ---------------------------------------------------------------- block symbolic factor
+  std::vector<std::vector<int32_t>> rows(N);
+  for (int g = 0; g < N; ++g)
+    for (int64_t p = s.colptr[g] + 1; p < s.colptr[g + 1]; ++p) {
+      int i = s.inv[s.rowidx[p]], j = s.inv[g];
+      if (i < j) std::swap(i, j);
+      rows[j].push_back(i);
+    }
+  s.str.assign(N, {});
+  s.parent.assign(N, -1);
+  for (int k = 0; k < N; ++k) {
+    auto& r = rows[k];
+    std::sort(r.begin(), r.end());
+    r.erase(std::unique(r.begin(), r.end()), r.end());
+    s.str[k] = r;
+    if (!r.empty()) {
+      int p = r[0];
+      s.parent[k] = p;
+      rows[p].insert(rows[p].end(), r.begin() + 1, r.end());
+    }
+    std::vector<int32_t>().swap(r);
+  }
+  s.rowlist.assign(N, {});
+  for (int k = 0; k < N; ++k)
+    for (int i : s.str[k]) s.rowlist[i].push_back(k);
+  s.level.assign(N, 0);
+  for (int k = 0; k < N; ++k)
+    if (s.parent[k] >= 0) s.level[s.parent[k]] = std::max(s.level[s.parent[k]], s.level[k] + 1);
+  s.nlevels = 0;
+  for (int k = 0; k < N; ++k) s.nlevels = std::max(s.nlevels, s.level[k] + 1);
+  s.depth = s.nlevels;
+  s.lev_blocks.assign(s.nlevels, {});
+  for (int k = 0; k < N; ++k) s.lev_blocks[s.level[k]].push_back(k);
+  s.max_height = 0;
+  s.nL_off = 0;
+  s.n_upd_off = 0;
+  double F = 0, solve = 0;
+  for (int k = 0; k < N; ++k) {
+    const double mk = s.m[k];
+    const auto& st = s.str[k];
+    s.max_height = std::max<int>(s.max_height, (int)st.size());
+    s.nL_off += (int64_t)st.size();
+    s.n_upd_off += (int64_t)st.size() * (st.size() - 1) / 2;
+    F += (4.0 / 3.0) * mk * mk * mk;                    // FACTOR k
+    solve += 8.0 * mk * mk + 6.0 * mk;                 // two triangular sweeps + diagonal
+    for (size_t a = 0; a < st.size(); ++a) {
+      const double mj = s.m[st[a]];
+      F += 4.0 * mj * mk * mk;                          // TRSM (j, k)
+      F += 4.0 * mj * mj * mk;                          // UPDATE (j, j, k)
+      solve += 16.0 * mj * mk;                          // L_jk in both sweeps
+      for (size_t c = a + 1; c < st.size(); ++c) F += 8.0 * s.m[st[c]] * mj * mk;  // (i, j, k)
+    }
+  }
+  s.factor_flops = F;
+  s.solve_flops_rhs = solve;
+  double kent = 0;
+  for (int g = 0; g < N; ++g)
+    for (int64_t p = s.colptr[g]; p < s.colptr[g + 1]; ++p)
+      kent += (s.rowidx[p] == g ? 1.0 : 2.0) * s.m_orig[s.rowidx[p]] * s.m_orig[g];
+  s.residual_flops_rhs = 8.0 * kent;
+
+  // residual gather lists (caller numbering)
+  {
+    std::vector<std::vector<int32_t>> lb(N), ls(N), lt(N);
+    for (int g = 0; g < N; ++g)
+      for (int64_t p = s.colptr[g]; p < s.colptr[g + 1]; ++p) {
+        int f = s.rowidx[p];
+        lb[f].push_back((int32_t)p); ls[f].push_back(g); lt[f].push_back(0);
+        if (f != g) { lb[g].push_back((int32_t)p); ls[g].push_back(f); lt[g].push_back(1); }
+      }
+    s.res_ptr.assign(N + 1, 0);
+    for (int f = 0; f < N; ++f) {
+      s.res_ptr[f + 1] = s.res_ptr[f] + (int64_t)lb[f].size();
+      s.res_blk.insert(s.res_blk.end(), lb[f].begin(), lb[f].end());
+      s.res_src.insert(s.res_src.end(), ls[f].begin(), ls[f].end());
+      s.res_tr.insert(s.res_tr.end(), lt[f].begin(), lt[f].end());
+    }
+  }
+
+  // ---------------------------------------------------------------- tiles
+  s.ntile.resize(N);
+  s.tstart.assign(N + 1, 0);
+  for (int k = 0; k < N; ++k) {
+    s.ntile[k] = (s.m[k] + b - 1) / b;
+    s.tstart[k + 1] = s.tstart[k] + s.ntile[k];
+  }
+  s.NT = s.tstart[N];
+  s.npad = (int64_t)s.NT * b;
+  s.xoff.resize(N + 1);
+  for (int k = 0; k <= N; ++k) s.xoff[k] = (int64_t)s.tstart[k] * b;
+  s.tblk.resize(s.NT);
+  for (int k = 0; k < N; ++k)
+    for (int t = 0; t < s.ntile[k]; ++t) s.tblk[s.tstart[k] + t] = k;
+  s.tcolptr.assign(s.NT + 1, 0);
+  for (int J = 0; J < s.NT; ++J) {
+    int q = s.tblk[J];
+    int64_t cnt = s.tstart[q + 1] - J;
+    for (int p : s.str[q]) cnt += s.ntile[p];
+    s.tcolptr[J + 1] = s.tcolptr[J] + cnt;
+  }
+  s.trow.resize(s.tcolptr[s.NT]);
+  for (int J = 0; J < s.NT; ++J) {
+    int q = s.tblk[J];
+    int64_t w = s.tcolptr[J];
+    for (int I = J; I < s.tstart[q + 1]; ++I) s.trow[w++] = I;
+    for (int p : s.str[q])
+      for (int I = s.tstart[p]; I < s.tstart[p + 1]; ++I) s.trow[w++] = I;
+  }
+  s.diag_tile.resize(s.NT);
+  for (int J = 0; J < s.NT; ++J) s.diag_tile[J] = (int32_t)s.tcolptr[J];
+  const int64_t ntiles = s.tcolptr[s.NT];
+  if (ntiles >= (int64_t)1 << 31) return fail(err, "too many tiles for 32-bit task ids");
+
+  // counts of tile updates and task-graph edges (always computed)
+  s.n_tile_updates = 0;
+  s.n_edges = 0;
+  for (int J = 0; J < s.NT; ++J) {
+    int q = s.tblk[J];
+    for (int64_t t = s.tcolptr[J]; t < s.tcolptr[J + 1]; ++t) {
+      int I = s.trow[t], p = s.tblk[I];
+      int64_t nk = J - s.tstart[q];
+      const auto& rp = s.rowlist[p];
+      const auto& rq = s.rowlist[q];
+      size_t a = 0, c = 0;
+      while (a < rp.size() && c < rq.size()) {
+        if (rp[a] < rq[c]) ++a;
+        else if (rp[a] > rq[c]) ++c;
+        else { nk += s.ntile[rp[a]]; ++a; ++c; }
+      }
+      s.n_tile_updates += nk;
+      s.n_edges += (I == J) ? nk : 2 * nk + 1;
+    }
+  }
+  if (!build_tasks) return D3M_OK;
+
+  // ---------------------------------------------------------------- tasks + K-lists
+  s.tasks.resize(ntiles);
+  s.ndeps.assign(ntiles, 0);
+  std::vector<int64_t> kl_ptr(ntiles + 1, 0);
+  // pass 1: K-list lengths
+  auto common_blocks = [&](int p, int q, std::vector<int32_t>& out) {
+    out.clear();
+    const auto& rp = s.rowlist[p];
+    const auto& rq = s.rowlist[q];
+    if (p == q) { out = rq; return; }
+    std::set_intersection(rp.begin(), rp.end(), rq.begin(), rq.end(), std::back_inserter(out));
+  };
+  std::vector<int32_t> ks;
+  for (int J = 0; J < s.NT; ++J) {
+    int q = s.tblk[J];
+    for (int64_t t = s.tcolptr[J]; t < s.tcolptr[J + 1]; ++t) {
+      int I = s.trow[t], p = s.tblk[I];
+      common_blocks(p, q, ks);
+      int64_t nk = J - s.tstart[q];
+      for (int k : ks) nk += s.ntile[k];
+      kl_ptr[t + 1] = nk;
+    }
+  }
+  for (int64_t t = 0; t < ntiles; ++t) kl_ptr[t + 1] += kl_ptr[t];
+  s.klist.resize(kl_ptr[ntiles]);
+  // pass 2: fill tasks, K-lists, dependency counts and successor lists
+  std::vector<int64_t> scount(ntiles + 1, 0);
+  for (int J = 0; J < s.NT; ++J) {
+    int q = s.tblk[J];
+    for (int64_t t = s.tcolptr[J]; t < s.tcolptr[J + 1]; ++t) {
+      int I = s.trow[t], p = s.tblk[I];
+      common_blocks(p, q, ks);
+      int64_t w = kl_ptr[t];
+      auto push = [&](int K) {
+        int64_t a = s.tile_of(I, K), bb = s.tile_of(J, K);
+        s.klist[w++] = KEntry{(int32_t)a, (int32_t)bb, K, 0};
+      };
+      for (int k : ks)
+        for (int K = s.tstart[k]; K < s.tstart[k + 1]; ++K) push(K);
+      for (int K = s.tstart[q]; K < J; ++K) push(K);
+      TileTask& T = s.tasks[t];
+      T.tile = (int32_t)t;
+      T.diag = s.diag_tile[J];
+      T.col = J;
+      T.nk = (int32_t)(kl_ptr[t + 1] - kl_ptr[t]);
+      T.kl_off = kl_ptr[t];
+      T.is_diag = (I == J);
+      T.same_block = (p == q);
+      T.r0 = (I - s.tstart[p]) * b;
+      T.c0 = (J - s.tstart[q]) * b;
+      T.rv = std::min(b, s.m[p] - T.r0);
+      T.cv = std::min(b, s.m[q] - T.c0);
+      int fp = s.perm[p], fq = s.perm[q];
+      int scol = fq, srow = fp;
+      T.k_tr = 0;
+      if (fp < fq) { scol = fp; srow = fq; T.k_tr = 1; }
+      T.k_off = -1;
+      T.k_ld = s.m_orig[srow];
+      const int32_t* first = s.rowidx.data() + s.colptr[scol];
+      const int32_t* last = s.rowidx.data() + s.colptr[scol + 1];
+      const int32_t* it = std::lower_bound(first, last, srow);
+      if (it != last && *it == srow) T.k_off = s.kblk_off[s.colptr[scol] + (it - first)];
+      // dependencies
+      int nd = (I == J) ? T.nk : 2 * T.nk + 1;
+      s.ndeps[t] = nd;
+    }
+  }
+  // successor lists
+  for (int64_t t = 0; t < ntiles; ++t) {
+    const TileTask& T = s.tasks[t];
+    for (int64_t e = T.kl_off; e < T.kl_off + T.nk; ++e) {
+      scount[s.klist[e].a_tile + 1]++;
+      if (!T.is_diag) scount[s.klist[e].b_tile + 1]++;
+    }
+    if (!T.is_diag) scount[T.diag + 1]++;
+  }
+  for (int64_t t = 0; t < ntiles; ++t) scount[t + 1] += scount[t];
+  s.succ_ptr = scount;
+  s.succ.resize(scount[ntiles]);
+  std::vector<int64_t> wpos(scount.begin(), scount.end() - 1);
+  for (int64_t t = 0; t < ntiles; ++t) {
+    const TileTask& T = s.tasks[t];
+    for (int64_t e = T.kl_off; e < T.kl_off + T.nk; ++e) {
+      s.succ[wpos[s.klist[e].a_tile]++] = (int32_t)t;
+      if (!T.is_diag) s.succ[wpos[s.klist[e].b_tile]++] = (int32_t)t;
+    }
+    if (!T.is_diag) s.succ[wpos[T.diag]++] = (int32_t)t;
+  }
+  s.init_ready.clear();
+  for (int64_t t = 0; t < ntiles; ++t)
+    if (s.ndeps[t] == 0) s.init_ready.push_back((int32_t)t);
+
+  // ---------------------------------------------------------------- solve level sets
+  s.fwd_item_ptr.assign(s.nlevels + 1, 0);
+  s.bwd_item_ptr.assign(s.nlevels + 1, 0);
+  s.fwd_slot_ptr.assign(s.NT + 1, 0);
+  s.bwd_slot_ptr.assign(s.NT + 1, 0);
+  s.fwd_items.clear();
+  s.bwd_items.clear();
+  s.max_level_items = 0;
+  std::vector<int64_t> fcnt(s.NT, 0), bcnt(s.NT, 0);
+  for (int lv = 0; lv < s.nlevels; ++lv) {
+    int64_t f0 = (int64_t)s.fwd_items.size(), b0 = (int64_t)s.bwd_items.size();
+    for (int k : s.lev_blocks[lv]) {
+      for (int I = s.tstart[k]; I < s.tstart[k + 1]; ++I)       // forward: row I gathers
+        for (int j : s.rowlist[k])
+          for (int J = s.tstart[j]; J < s.tstart[j + 1]; ++J) {
+            int32_t slot = (int32_t)(s.fwd_items.size() - f0);
+            s.fwd_items.push_back(SolveItem{(int32_t)s.tile_of(I, J), J, I, slot});
+            fcnt[I]++;
+          }
+      for (int J = s.tstart[k]; J < s.tstart[k + 1]; ++J)       // backward: column J gathers
+        for (int i : s.str[k])
+          for (int I = s.tstart[i]; I < s.tstart[i + 1]; ++I) {
+            int32_t slot = (int32_t)(s.bwd_items.size() - b0);
+            s.bwd_items.push_back(SolveItem{(int32_t)s.tile_of(I, J), I, J, slot});
+            bcnt[J]++;
+          }
+    }
+    s.fwd_item_ptr[lv + 1] = (int64_t)s.fwd_items.size();
+    s.bwd_item_ptr[lv + 1] = (int64_t)s.bwd_items.size();
+    s.max_level_items = std::max(s.max_level_items, s.fwd_item_ptr[lv + 1] - f0);
+    s.max_level_items = std::max(s.max_level_items, s.bwd_item_ptr[lv + 1] - b0);
+  }
+  // items of one destination are contiguous (pushed in a row): record the first slot
+  // (relative to the level start) and the count, packed as first | count << 32
+  for (int I = 0; I < s.NT; ++I) { s.fwd_slot_ptr[I] = -1; s.bwd_slot_ptr[I] = -1; }
+  for (int lv = 0; lv < s.nlevels; ++lv) {
+    for (int64_t e = s.fwd_item_ptr[lv]; e < s.fwd_item_ptr[lv + 1]; ++e) {
+      int d = s.fwd_items[e].dst;
+      if (s.fwd_slot_ptr[d] < 0) s.fwd_slot_ptr[d] = s.fwd_items[e].slot;
+    }
+    for (int64_t e = s.bwd_item_ptr[lv]; e < s.bwd_item_ptr[lv + 1]; ++e) {
+      int d = s.bwd_items[e].dst;
+      if (s.bwd_slot_ptr[d] < 0) s.bwd_slot_ptr[d] = s.bwd_items[e].slot;
+    }
+  }
+  for (int I = 0; I < s.NT; ++I) {
+    int64_t f = s.fwd_slot_ptr[I] < 0 ? 0 : s.fwd_slot_ptr[I];
+    int64_t bb = s.bwd_slot_ptr[I] < 0 ? 0 : s.bwd_slot_ptr[I];
+    s.fwd_slot_ptr[I] = f | (fcnt[I] << 32);
+    s.bwd_slot_ptr[I] = bb | (bcnt[I] << 32);
+  }
+  return D3M_OK;
+}
+
+// ---------------------------------------------------------------- grid nested dissection
+int order_grid_nd(int nx, int ny, int nz, std::vector<int32_t>& perm) {
+  if (nx <= 0 || ny <= 0 || nz <= 0) return D3M_ERR_INVALID;
+  struct If { int c[3]; int ax; };
+  std::vector<If> ifs;
+  for (int ix = 0; ix < nx; ++ix)
+    for (int iy = 0; iy < ny; ++iy)
+      for (int iz = 0; iz < nz; ++iz) {
+        const int lim[3] = {nx, ny, nz};
+        const int c[3] = {ix, iy, iz};
+        for (int ax = 0; ax < 3; ++ax)
+          if (c[ax] + 1 < lim[ax]) ifs.push_back(If{{ix, iy, iz}, ax});
+      }
+  perm.clear();
+  std::function<void(const int*, const int*)> rec = [&](const int* lo, const int* hi) {
+    std::vector<int32_t> own;
+    for (size_t f = 0; f < ifs.size(); ++f) {
+      bool in = true;
+      for (int a = 0; a < 3; ++a) {
+        int c0 = ifs[f].c[a], c1 = c0 + (ifs[f].ax == a ? 1 : 0);
+        if (c0 < lo[a] || c1 >= hi[a]) { in = false; break; }
+      }
+      if (in) own.push_back((int32_t)f);
+    }
+    int ext[3] = {hi[0] - lo[0], hi[1] - lo[1], hi[2] - lo[2]};
+    int ax = 0;
+    for (int a = 1; a < 3; ++a)
+      if (ext[a] > ext[ax]) ax = a;
+    if (ext[ax] <= 1 || own.size() <= 1) {
+      perm.insert(perm.end(), own.begin(), own.end());
+      return;
+    }
+    int mid = lo[ax] + ext[ax] / 2;
+    int lhi[3] = {hi[0], hi[1], hi[2]};
+    int rlo[3] = {lo[0], lo[1], lo[2]};
+    lhi[ax] = mid;
+    rlo[ax] = mid;
+    rec(lo, lhi);
+    rec(rlo, hi);
+    for (int32_t f : own)
+      if (ifs[f].ax == ax && ifs[f].c[ax] == mid - 1) perm.push_back(f);
+  };
+  const int lo[3] = {0, 0, 0};
+  const int hi[3] = {nx, ny, nz};
+  rec(lo, hi);
+  return perm.size() == ifs.size() ? D3M_OK : D3M_ERR_INVALID;
+}
+
+}  // namespace d3m

@@ -1,0 +1,102 @@
+// Host-side symbolic analysis: block elimination tree, fill, tile task graph (B-DAG) and the
+// level sets of the solve sweeps.  Pure C++ (no CUDA), shared by d3m_analyze and d3m_create.
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "d3m.h"
+
+namespace d3m {
+
+// One task of the factorization DAG = one lower tile (I, J) of L (owner computes; paper
+// Sec. II: "each non-zero block of the dual matrix is represented by a task responsible for
+// possible dense update, dense triangular solver, and dense factorization").
+struct TileTask {
+  int32_t tile;        // own tile id (== task id)
+  int32_t diag;        // tile id of (J, J)
+  int32_t col;         // global tile column J
+  int32_t nk;          // length of the K-list (tile updates into this tile)
+  int64_t kl_off;      // offset of the K-list in the klist array
+  int64_t k_off;       // element (c128) offset of the stored K block, -1 for a fill block
+  int32_t k_ld;        // leading dimension of the stored K block
+  int32_t k_tr;        // 1: entry (r, c) of block (p, q) is stored(c, r) (use the transpose)
+  int32_t r0, c0;      // first row / column of the tile inside block (p, q)
+  int32_t rv, cv;      // valid rows / columns (the rest is padding up to the tile edge)
+  int32_t is_diag;     // I == J
+  int32_t same_block;  // p == q: padding unknowns get a unit diagonal
+};
+static_assert(sizeof(TileTask) == 64, "TileTask layout");
+
+// One K-list entry: S_IJ -= L_IK D_K L_JK^T uses tiles a = (I, K), b = (J, K), column K.
+struct KEntry {
+  int32_t a_tile, b_tile, kcol, pad;
+};
+
+// One solve gather item: partial = L(tile) * y(src tile) (forward) or L(tile)^T * w(src)
+// (backward), written to partial slot `slot` of destination tile row/column `dst`.
+struct SolveItem {
+  int32_t tile, src, dst, slot;
+};
+
+struct Symbolic {
+  // block level (NEW numbering)
+  int N = 0;
+  int b = 64;                                // tile edge
+  std::vector<int32_t> perm, inv;            // perm[new] = old
+  std::vector<int32_t> m, ntile, tstart;     // block size, tiles per block, first tile
+  std::vector<int64_t> xoff;                 // first unknown of block (padded, new order)
+  std::vector<int64_t> xoff_orig;            // first unknown of ORIGINAL block f
+  std::vector<std::vector<int32_t>> str;     // struct(k): rows i > k with L_ik != 0
+  std::vector<std::vector<int32_t>> rowlist; // blocks k < q with q in struct(k)
+  std::vector<int32_t> parent, level;
+  int depth = 0, max_height = 0, nlevels = 0;
+  int64_t n = 0, npad = 0;                   // unknowns (unpadded / padded)
+  int64_t nnzb_K = 0, nL_off = 0, n_upd_off = 0;
+  int64_t n_tile_updates = 0, n_edges = 0;
+  double factor_flops = 0, solve_flops_rhs = 0, residual_flops_rhs = 0;
+
+  // K layout (caller numbering, lower block-CSC)
+  std::vector<int64_t> colptr;
+  std::vector<int32_t> rowidx;
+  std::vector<int64_t> kblk_off;             // [nnzb+1] element offsets
+  std::vector<int32_t> m_orig;               // block sizes, caller numbering
+
+  // tile level
+  int NT = 0;                                // tile columns
+  std::vector<int64_t> tcolptr;              // [NT+1]
+  std::vector<int32_t> trow;                 // tile row of each tile
+  std::vector<int32_t> tblk;                 // block of each tile row/column index
+  std::vector<TileTask> tasks;
+  std::vector<KEntry> klist;
+  std::vector<int32_t> ndeps;
+  std::vector<int64_t> succ_ptr;
+  std::vector<int32_t> succ;
+  std::vector<int32_t> init_ready;
+  std::vector<int32_t> diag_tile;            // tile column J -> tile id of (J, J)
+
+  // solve level sets (forward uses levels ascending, backward descending)
+  std::vector<std::vector<int32_t>> lev_blocks;      // blocks of each level
+  std::vector<int64_t> fwd_item_ptr, bwd_item_ptr;   // per level, into fwd_items / bwd_items
+  std::vector<SolveItem> fwd_items, bwd_items;
+  std::vector<int64_t> fwd_slot_ptr, bwd_slot_ptr;   // [NT] first slot | count << 32
+  int64_t max_level_items = 0;
+
+  // residual (caller numbering): per output block f, the stored blocks contributing to r_f
+  std::vector<int64_t> res_ptr;              // [N+1]
+  std::vector<int32_t> res_blk;              // stored block index e
+  std::vector<int32_t> res_src;              // source block g (x_g)
+  std::vector<int32_t> res_tr;               // 1: use stored block transposed
+
+  int64_t tile_of(int I, int J) const;       // -1 if (I, J) not in the tile pattern
+};
+
+// Validate the pattern and permutation, then run the full analysis for tile edge b.
+// Returns D3M_OK or an error code with a message in `err`.
+int analyze(const d3m_pattern* pat, const int32_t* perm, int b, bool build_tasks,
+            Symbolic& s, std::string& err);
+
+// Grid nested dissection (see d3m_order_grid_nd).
+int order_grid_nd(int nx, int ny, int nz, std::vector<int32_t>& perm);
+
+}  // namespace d3m

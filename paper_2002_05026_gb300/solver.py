@@ -1,0 +1,144 @@
+"""Python front end of the C-ABI: a handle class over torch device tensors.
+
+Vectors are torch complex128 tensors of shape (n,) or (n, nrhs); the library wants them
+column-major, so an (n, nrhs) tensor is passed as the contiguous (nrhs, n) transpose.
+Every computation runs in libd3m.so; this file only moves pointers.
+"""
+from __future__ import annotations
+
+import ctypes
+from ctypes import POINTER, c_double, c_int32, c_void_p
+
+import numpy as np
+
+from . import _abi
+from ._abi import check, load
+
+PRECISIONS = {"fp64": _abi.D3M_FP64, "bf16x3": _abi.D3M_MIXED_BF16X3, "simt32": _abi.D3M_MIXED_SIMT32}
+
+
+def _stream_ptr(stream=None) -> int:
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def _as_colmajor(B):
+    """(n,) or (n, nrhs) -> contiguous (nrhs, n) complex128 tensor and nrhs."""
+    import torch
+    if B.dtype != torch.complex128:
+        raise TypeError("right-hand sides must be complex128")
+    if B.dim() == 1:
+        return B.contiguous().reshape(1, -1), 1, True
+    return B.T.contiguous(), B.shape[1], False
+
+
+class D3M:
+    """One factorization handle (d3m_create ... d3m_destroy)."""
+
+    def __init__(self, colptr, rowidx, m=None, blk_size=None, perm=None, precision="bf16x3",
+                 max_nrhs: int = 32, refine_tol: float = 1e-12, refine_max_iter: int = 20,
+                 timeout_ns: int = 0, fp64_omega: bool = False, debug_flags: int = 0, stream=None):
+        lib = load()
+        self._lib = lib
+        self.h = c_void_p()
+        pat, self._keep = _abi.make_pattern(colptr, rowidx, m, blk_size)
+        opt = _abi.d3m_default_options()
+        opt.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        opt.max_nrhs = max_nrhs
+        opt.refine_tol = refine_tol
+        opt.refine_max_iter = refine_max_iter
+        if timeout_ns:
+            opt.timeout_ns = timeout_ns
+        opt.fp64_omega = int(fp64_omega)
+        opt.debug_flags = debug_flags
+        pp = None
+        if perm is not None:
+            self._perm = np.ascontiguousarray(perm, dtype=np.int32)
+            pp = self._perm.ctypes.data_as(POINTER(c_int32))
+        self.precision = precision
+        self.stream = stream
+        rc = lib.d3m_create(ctypes.byref(self.h), ctypes.byref(pat), pp, ctypes.byref(opt),
+                            c_void_p(_stream_ptr(stream)))
+        check(rc, None if not self.h else self.h)
+        self.n = int(np.sum(blk_size)) if blk_size is not None else int(m) * (len(colptr) - 1)
+
+    # -------------------------------------------------------------- C-ABI calls
+    def factor(self, K):
+        """K: complex128 lower blocks (torch tensor on the device, or pinned/host)."""
+        ptr = K.data_ptr() if hasattr(K, "data_ptr") else K.ctypes.data
+        return check(self._lib.d3m_factor(self.h, c_void_p(ptr), c_void_p(_stream_ptr(self.stream))), self.h)
+
+    def solve(self, B, X=None, allow_not_converged: bool = False):
+        import torch
+        Bt, nrhs, vec = _as_colmajor(B)
+        Xt = torch.empty_like(Bt) if X is None else X
+        rc = self._lib.d3m_solve(self.h, c_void_p(Bt.data_ptr()), c_void_p(Xt.data_ptr()), nrhs,
+                                 c_void_p(_stream_ptr(self.stream)))
+        if not (allow_not_converged and rc == _abi.D3M_ERR_NOT_CONVERGED):
+            check(rc, self.h)
+        return Xt.reshape(-1) if vec else Xt.T
+
+    def adjoint(self, G):
+        import torch
+        Gt, nrhs, vec = _as_colmajor(G)
+        Lt = torch.empty_like(Gt)
+        check(self._lib.d3m_adjoint(self.h, c_void_p(Gt.data_ptr()), c_void_p(Lt.data_ptr()), nrhs,
+                                    c_void_p(_stream_ptr(self.stream))), self.h)
+        return Lt.reshape(-1) if vec else Lt.T
+
+    def grad_eps(self, Lam, X, dom_if, k2: float):
+        Lt, nrhs, _ = _as_colmajor(Lam)
+        Xt, _, _ = _as_colmajor(X)
+        ptr = np.zeros(len(dom_if) + 1, dtype=np.int32)
+        for i, I in enumerate(dom_if):
+            ptr[i + 1] = ptr[i] + len(I)
+        flat = np.ascontiguousarray(np.concatenate([np.asarray(I, dtype=np.int32) for I in dom_if])
+                                    if len(dom_if) else np.zeros(0), dtype=np.int32)
+        out = np.zeros(len(dom_if), dtype=np.float64)
+        check(self._lib.d3m_grad_eps(self.h, c_void_p(Lt.data_ptr()), c_void_p(Xt.data_ptr()), nrhs,
+                                     len(dom_if), ptr.ctypes.data_as(POINTER(c_int32)),
+                                     flat.ctypes.data_as(POINTER(c_int32)), c_double(k2),
+                                     out.ctypes.data_as(POINTER(c_double)),
+                                     c_void_p(_stream_ptr(self.stream))), self.h)
+        return out
+
+    def grad_pattern(self, Lam, X, nvals: int):
+        import torch
+        Lt, nrhs, _ = _as_colmajor(Lam)
+        Xt, _, _ = _as_colmajor(X)
+        dK = torch.empty(nvals, dtype=torch.complex128, device=Lt.device)
+        check(self._lib.d3m_grad_pattern(self.h, c_void_p(Lt.data_ptr()), c_void_p(Xt.data_ptr()), nrhs,
+                                         c_void_p(dK.data_ptr()), c_void_p(_stream_ptr(self.stream))), self.h)
+        return dK
+
+    def factor_block(self, i: int, j: int, mi: int, mj: int) -> np.ndarray:
+        out = np.zeros(mi * mj, dtype=np.complex128)
+        check(self._lib.d3m_get_factor_block(self.h, i, j, c_void_p(out.ctypes.data),
+                                             c_void_p(_stream_ptr(self.stream))), self.h)
+        return out.reshape(mj, mi).T
+
+    def pivots(self, j: int, mj: int) -> np.ndarray:
+        out = np.zeros(mj, dtype=np.complex128)
+        check(self._lib.d3m_get_pivots(self.h, j, c_void_p(out.ctypes.data), c_void_p(_stream_ptr(self.stream))),
+              self.h)
+        return out
+
+    def info(self) -> dict:
+        inf = _abi.d3m_info()
+        check(self._lib.d3m_get_info(self.h, ctypes.byref(inf), c_void_p(_stream_ptr(self.stream))), self.h)
+        return inf.as_dict()
+
+    def last_error(self) -> str:
+        return self._lib.d3m_last_error(self.h).decode()
+
+    def close(self):
+        if getattr(self, "h", None) and self.h:
+            self._lib.d3m_destroy(self.h)
+            self.h = c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,88 @@
+"""Host-side checks of the C ABI (no GPU): the library loads, exports every declared symbol,
+and its host-only entry points (ordering, symbolic analysis, validation) agree with the oracle."""
+import numpy as np
+import pytest
+
+import oracle as O
+import synth
+from paper_2002_05026_gb300 import _abi
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2002_05026_gb300 import build
+    build.build()
+    return _abi.load()
+
+
+def test_exports_every_declared_symbol(lib):
+    names = _abi.header_symbols()
+    assert len(names) >= 14
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_default_options(lib):
+    o = _abi.d3m_default_options()
+    assert o.precision == _abi.D3M_MIXED_BF16X3 and o.refine_tol == 1e-12 and o.max_nrhs == 32
+
+
+@pytest.mark.parametrize("g", [(2, 2, 1), (3, 1, 1), (1, 3, 1), (4, 1, 1), (8, 8, 1), (6, 6, 6), (5, 3, 2), (1, 1, 1)])
+def test_grid_nd_matches_oracle(lib, g):
+    assert _abi.d3m_order_grid_nd(*g).tolist() == O.nd_order(*g).tolist()
+
+
+def _oracle_counts(g, m, perm):
+    cp, ri = synth.lower_pattern(*g)
+    inv = np.empty(len(perm), dtype=int)
+    inv[perm] = np.arange(len(perm))
+    keys = []
+    for c in range(cp.size - 1):
+        for e in range(cp[c], cp[c + 1]):
+            i, j = inv[ri[e]], inv[c]
+            keys.append((max(i, j), min(i, j)))
+    st, par = O.block_symbolic(len(perm), keys)
+    return st, par
+
+
+@pytest.mark.parametrize("g,m", [((2, 2, 1), 64), ((8, 8, 1), 512), ((6, 6, 6), 512), ((4, 4, 1), 100), ((3, 2, 2), 7)])
+def test_analyze_matches_oracle_symbolic(lib, g, m):
+    perm = O.nd_order(*g)
+    cp, ri = synth.lower_pattern(*g)
+    info = _abi.d3m_analyze(cp, ri, m=m, perm=perm, tile=128)
+    st, par = _oracle_counts(g, m, perm)
+    assert info["nblk"] == len(perm)
+    assert info["nnzb_K"] == ri.size
+    assert info["nblk_L_offdiag"] == sum(len(s) for s in st)
+    assert info["etree_depth"] == O.etree_depth(par)
+    assert info["max_col_height"] == max(len(s) for s in st)
+    assert info["factor_flops"] == pytest.approx(O.factor_flops(st, m), rel=1e-12)
+    assert info["n"] == len(perm) * m
+
+
+def test_analyze_tile_counts_2x2(lib):
+    # 2x2 grid, m = 64, tile 64: one tile per block -> tiles = blocks of L (4 diagonal + 5);
+    # tile updates: col 2 gets 2 (from cols 0, 1) for (2,2), (3,2); col 3: (3,3) from 0, 1, 2
+    cp, ri = synth.lower_pattern(2, 2, 1)
+    info = _abi.d3m_analyze(cp, ri, m=64, perm=O.nd_order(2, 2, 1), tile=64)
+    assert info["ntiles"] == 9
+    # (2,0),(3,0),(2,1),(3,1): 0 updates; (2,2): 2; (3,2): 2; (3,3): 3 (k = 0, 1, 2)
+    assert info["ntile_updates"] == 7
+
+
+@pytest.mark.parametrize("bad", ["nodiag", "unsorted", "oob", "perm"])
+def test_invalid_patterns_rejected(lib, bad):
+    cp, ri = synth.lower_pattern(2, 2, 1)
+    cp, ri = cp.copy(), ri.copy()
+    perm = None
+    if bad == "nodiag":
+        ri[0] = 1
+    elif bad == "unsorted":
+        ri[1], ri[2] = ri[2], ri[1]
+    elif bad == "oob":
+        ri[-1] = 9
+    else:
+        perm = np.array([0, 0, 1, 2], dtype=np.int32)
+    with pytest.raises(_abi.D3MError) as e:
+        _abi.d3m_analyze(cp, ri, m=8, perm=perm)
+    assert e.value.code == _abi.D3M_ERR_INVALID
