@@ -1,0 +1,386 @@
+#!/usr/bin/env python
+"""Benchmark: D3M dual block LDL^T factor + solve on one GB300 (or N independent ones).
+
+Workload (default): 8 x 8 x 1 domain grid, 112 interfaces, m = 512 dual unknowns per
+interface (n = 57,344), nested-dissection order, M_i = G G^T - k^2 I + i tau I with k^2 = 2,
+tau = 0.05, 8 right-hand sides, seeded synthetic data.
+
+One step = d3m_factor (copy of K + persistent tile-task kernel) + d3m_solve (sweeps +
+FP64 residual refinement to omega <= 1e-12) through the C ABI, inputs resident in HBM.
+value = effective TFLOP/s = (algorithmic factor flops + solve flops x nrhs) / step time,
+summed over ranks (each rank solves its own instance: weak scaling, no data collective).
+
+Also reported: the plain FP64 GPU path on the same matrix (time-to-solution), the
+end-to-end number with host buffers (H2D of K and B, D2H of X inside the timed region),
+the roofline of the dominant kernel, clocks sampled during the timed region, and the CPU
+oracle on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "factor+solve time & TFLOP/s at 1e-9 rel err: mixed-prec vs FP64 block LDLᵀ"
+FP64_PEAK_GFLOPS = 1250.0     # GB300 FP64 nominal (152 SMs x 2.07 GHz x ~4 flop/clk/SM)
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="d3m", choices=["d3m", "reference"])
+    ap.add_argument("--workload", default="grid8x8_m512")
+    ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "simt32", "fp64"])
+    ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    return ap.parse_args()
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ CPU oracle sample
+def oracle_sample(p_blocks_np, p, perm, seconds: float):
+    """Time the oracle's right-looking block LDL^T on the first C block columns, with C chosen so
+    the run takes about `seconds`; returns (flops, time, C, share of the factor flops)."""
+    import numpy as np
+    import oracle as O
+    Kb = O.lower_blocks(p.colptr, p.rowidx, p_blocks_np, p.m)
+    Kp = O.permute_lower(Kb, perm)
+    st, _ = O.block_symbolic(p.nblk, Kp.keys())
+    m = p.m
+
+    def col_flops(k):
+        s = len(st[k])
+        return (4 / 3) * m ** 3 + s * 4 * m ** 3 + s * 4 * m ** 3 + s * (s - 1) / 2 * 8 * m ** 3
+
+    total = sum(col_flops(k) for k in range(p.nblk))
+    # calibrate the host rate on one block column's worth of work
+    t0 = time.perf_counter()
+    O.block_ldlt(Kp, p.nblk, m, ncols=1)
+    rate = col_flops(0) / max(time.perf_counter() - t0, 1e-6)
+    budget = rate * seconds
+    C, acc = 0, 0.0
+    while C < p.nblk and acc + col_flops(C) <= budget:
+        acc += col_flops(C)
+        C += 1
+    C = max(C, 1)
+    flops = sum(col_flops(k) for k in range(C))
+    t0 = time.perf_counter()
+    O.block_ldlt(Kp, p.nblk, m, ncols=C)
+    dt = time.perf_counter() - t0
+    return flops, dt, C, flops / total
+
+
+def make_workload(w, seed, device):
+    import numpy as np
+    import synth
+    p = synth.make_problem(w["nx"], w["ny"], w["nz"], w["m"], w["k2"], w["tau"], seed, device=device)
+    B = synth.rhs(seed + 1, p.n, w["nrhs"])
+    return p, np.ascontiguousarray(B.T)      # (nrhs, n) = column-major (n, nrhs)
+
+
+# ------------------------------------------------------------------ reference arm (the oracle)
+def reference_arm(args, rank, world):
+    if rank != 0:
+        return
+    import numpy as np
+    import synth
+    from paper_2002_05026_gb300 import d3m_order_grid_nd  # host-only ordering routine
+    w = synth.WORKLOADS[args.workload]
+    p, _ = make_workload(w, w["seed"], "cpu")
+    blocks = p.blocks.numpy()
+    perm = d3m_order_grid_nd(w["nx"], w["ny"], w["nz"])
+    per_step = min(args.cpu_seconds, 150.0 / max(1, args.steps + args.warmup))
+    for _ in range(args.warmup):
+        oracle_sample(blocks, p, perm, per_step)
+    vals, times = [], []
+    for _ in range(args.steps):
+        fl, dt, C, share = oracle_sample(blocks, p, perm, per_step)
+        vals.append(fl / dt / 1e12)
+        times.append(dt)
+    value = sum(vals) / len(vals)
+    cores = os.cpu_count()
+    sample = (f"oracle (numpy FP64) right-looking block LDL^T of the first {C} of {p.nblk} block "
+              f"columns ({100 * share:.1f}% of the factor flops) of the {args.workload} matrix")
+    line = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": args.workload, "grid": [w["nx"], w["ny"], w["nz"]], "m": w["m"],
+                       "nrhs": w["nrhs"], "k2": w["k2"], "tau": w["tau"]},
+            "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ main arm
+def main():
+    args = parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        reference_arm(args, rank, world)
+        return
+    import numpy as np
+    import torch
+    import synth
+    from paper_2002_05026_gb300 import D3M, build, d3m_order_grid_nd
+
+    build.build()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    def allmax(v: float) -> float:
+        if dist is None:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    w = synth.WORKLOADS[args.workload]
+    seed = w["seed"] + rank
+    p, Bnp = make_workload(w, seed, "cuda")
+    nrhs = w["nrhs"]
+    K = p.blocks                                            # device c128, lower blocks
+    Bt = torch.from_numpy(Bnp).cuda()                       # (nrhs, n)
+    Xt = torch.empty_like(Bt)
+    perm = d3m_order_grid_nd(w["nx"], w["ny"], w["nz"])
+    stream = torch.cuda.current_stream()
+    sp = ctypes.c_void_p(stream.cuda_stream)
+    s = D3M(p.colptr, p.rowidx, m=p.m, perm=perm, precision=args.precision, max_nrhs=nrhs)
+    lib = s._lib
+
+    def step(Kp, Bp, Xp):
+        rc = lib.d3m_factor(s.h, ctypes.c_void_p(Kp), sp)
+        if rc:
+            raise RuntimeError(s.last_error())
+        rc = lib.d3m_solve(s.h, ctypes.c_void_p(Bp), ctypes.c_void_p(Xp), nrhs, sp)
+        if rc:
+            raise RuntimeError(f"solve rc={rc}: {s.last_error()}")
+
+    for _ in range(args.warmup):
+        step(K.data_ptr(), Bt.data_ptr(), Xt.data_ptr())
+    info0 = s.info()
+    clk = ClockSampler(local)
+    clk.start()
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step(K.data_ptr(), Bt.data_ptr(), Xt.data_ptr())
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = clk.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    ms = allmax(ms)
+    info = s.info()
+    flops_step = info["factor_flops"] + info["solve_flops_per_rhs"] * nrhs
+    value = flops_step * world / (ms * 1e-3) / 1e12
+    launches = info["kernel_launches"] - info0["kernel_launches"]
+    X_mixed = Xt.clone()
+
+    # ---------------------------------------------------------------- roofline of the dominant kernel
+    peaks, peak_kind = measured_peaks()
+    b = info["tile"]
+    kern = []
+    if info["factor_kernel_calls"]:
+        fms = info["factor_kernel_ms_total"] / info["factor_kernel_calls"]
+        if args.precision == "bf16x3":
+            pk, unit, bound, pname = peaks["bf16_tflops_sustained"] / 3.0, "TFLOP/s", "tensor", \
+                "bf16_tflops_sustained/3 (split-BF16x3: 3 bf16 products per FP32-level product)"
+        elif args.precision == "fp64":
+            pk, unit, bound, pname = FP64_PEAK_GFLOPS / 1e3, "TFLOP/s", "alu", "FP64 nominal 1.25 TFLOP/s"
+        else:
+            pk, unit, bound, pname = 152 * 2.07e9 * 256 / 1e12, "TFLOP/s", "alu", "FP32 FMA 152 SMs x 128 x 2 x 2.07 GHz"
+        kern.append(("factor_kernel", info["factor_kernel_ms_total"],
+                     {"bound": bound, "achieved": info["factor_flops"] / (fms * 1e-3) / 1e12, "peak": pk,
+                      "unit": unit, "peak_source": pname, "kernel_ms": fms}))
+    if info["residual_calls"]:
+        rms = info["residual_ms_total"] / info["residual_calls"]
+        kern.append(("fp64_residual", info["residual_ms_total"],
+                     {"bound": "alu", "achieved": info["residual_flops_per_rhs"] * nrhs / (rms * 1e-3) / 1e12,
+                      "peak": FP64_PEAK_GFLOPS / 1e3, "unit": "TFLOP/s",
+                      "peak_source": "FP64 nominal 1.25 TFLOP/s", "kernel_ms": rms}))
+    if info["sweep_calls"]:
+        sms = info["sweep_ms_total"] / info["sweep_calls"]
+        esz = 16 if args.precision == "fp64" else 8
+        lbytes = 2.0 * info["ntiles"] * b * b * esz
+        kern.append(("solve_sweep", info["sweep_ms_total"],
+                     {"bound": "hbm", "achieved": lbytes / (sms * 1e-3) / 1e9, "peak": peaks["hbm_gbs"],
+                      "unit": "GB/s", "peak_source": "hbm_gbs", "kernel_ms": sms}))
+    kern.sort(key=lambda t: -t[1])
+    dom_name, _, roof = kern[0]
+    roof = dict(roof)
+    roof["kernel"] = dom_name
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = None
+    roof["peak_kind"] = peak_kind
+    breakdown = {k: {"ms_per_step": t / args.steps, **{kk: v for kk, v in r.items() if kk in ("achieved", "peak", "unit", "bound")}}
+                 for k, t, r in kern}
+
+    # ---------------------------------------------------------------- plain FP64 GPU path
+    fp64 = None
+    if not args.no_fp64 and args.precision != "fp64":
+        s64 = D3M(p.colptr, p.rowidx, m=p.m, perm=perm, precision="fp64", max_nrhs=nrhs)
+        X64 = torch.empty_like(Bt)
+
+        def step64():
+            lib.d3m_factor(s64.h, ctypes.c_void_p(K.data_ptr()), sp)
+            rc = lib.d3m_solve(s64.h, ctypes.c_void_p(Bt.data_ptr()), ctypes.c_void_p(X64.data_ptr()), nrhs, sp)
+            if rc:
+                raise RuntimeError(s64.last_error())
+
+        step64()
+        torch.cuda.synchronize()
+        s64.info()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(args.fp64_steps):
+            step64()
+        f1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = allmax(f0.elapsed_time(f1) / args.fp64_steps)
+        i64 = s64.info()
+        rel = (torch.linalg.norm(X_mixed - X64, dim=1) / torch.linalg.norm(X64, dim=1)).max().item()
+        fk = i64["factor_kernel_ms_total"] / max(1, i64["factor_kernel_calls"])
+        fp64 = {"ms_per_step": ms64, "tflops": flops_step / (ms64 * 1e-3) / 1e12,
+                "speedup_mixed_vs_fp64": ms64 / ms, "factor_kernel_ms": fk,
+                "factor_roofline": {"bound": "alu", "achieved": i64["factor_flops"] / (fk * 1e-3) / 1e12,
+                                    "peak": FP64_PEAK_GFLOPS / 1e3, "unit": "TFLOP/s",
+                                    "frac": i64["factor_flops"] / (fk * 1e-3) / 1e12 / (FP64_PEAK_GFLOPS / 1e3)},
+                "max_rel_diff_mixed_vs_fp64": rel}
+        s64.close()
+        del X64
+
+    # ---------------------------------------------------------------- end to end, host buffers
+    e2e = None
+    if not args.no_e2e:
+        Kh = K.cpu().pin_memory()
+        Bh = Bt.cpu().pin_memory()
+        Xh = torch.empty_like(Bh).pin_memory()
+        step(Kh.data_ptr(), Bh.data_ptr(), Xh.data_ptr())
+        torch.cuda.synchronize()
+        barrier()
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        for _ in range(args.steps):
+            step(Kh.data_ptr(), Bh.data_ptr(), Xh.data_ptr())
+        g1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        ems = allmax(g0.elapsed_time(g1) / args.steps)
+        e2e = {"value": flops_step * world / (ems * 1e-3) / 1e12, "unit": "TFLOP/s", "ms_per_step": ems,
+               "h2d_bytes_per_step": int(Kh.numel() * 16 + Bh.numel() * 16),
+               "d2h_bytes_per_step": int(Xh.numel() * 16)}
+        del Kh
+
+    # ---------------------------------------------------------------- CPU oracle sample
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        fl, dt, C, share = oracle_sample(K.cpu().numpy(), p, perm, args.cpu_seconds)
+        cpu = {"value": fl / dt / 1e12, "unit": "TFLOP/s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": (f"oracle (numpy FP64) right-looking block LDL^T of the first {C} of {p.nblk} block "
+                          f"columns ({100 * share:.1f}% of the factor flops), {dt:.1f} s")}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "c64+bf16x3/fp64-refine" if args.precision == "bf16x3" else
+                ("c128" if args.precision == "fp64" else "c64/fp64-refine"),
+                "data": "synthetic",
+                "config": {"workload": args.workload, "grid": [w["nx"], w["ny"], w["nz"]], "m": w["m"],
+                           "n": p.n, "nrhs": nrhs, "k2": w["k2"], "tau": w["tau"], "precision": args.precision,
+                           "order": "nested dissection", "l2": "inputs larger than L2 (K is "
+                           f"{K.numel() * 16 / 1e9:.2f} GB)"},
+                "roofline": roof, "kernels": breakdown,
+                "accuracy": {"omega": info["omega"], "omega_first_solve": info["omega_first"],
+                             "refine_solves": info["refine_iters"]},
+                "fp64_path": fp64, "e2e": e2e, "cpu_baseline": cpu, "clocks": clocks,
+                "gpu_launches": int(launches),
+                "flops_per_step": flops_step, "factor_flops": info["factor_flops"]}
+        print(json.dumps(line), flush=True)
+    s.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

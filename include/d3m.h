@@ -120,6 +120,13 @@ typedef struct {
   double factor_kernel_ms;  /* device time of the last factorization kernel (CUDA events) */
   double solve_ms;          /* device time of the last d3m_solve / d3m_adjoint (events) */
   double residual_ms;       /* device time in FP64 residual kernels of that solve */
+  int64_t kernel_launches;  /* kernels launched by this handle since d3m_create */
+  /* device time summed over every launch since the previous d3m_get_info (CUDA events):
+   * factorization kernels, FP64 residual kernels, and whole solve sweeps */
+  double factor_kernel_ms_total;
+  double residual_ms_total;
+  double sweep_ms_total;
+  int64_t factor_kernel_calls, residual_calls, sweep_calls;
 } d3m_info;
 
 /* Default options (precision D3M_MIXED_BF16X3). */

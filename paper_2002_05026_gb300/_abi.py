@@ -51,7 +51,10 @@ class d3m_info(ctypes.Structure):
                 ("residual_flops_per_rhs", c_double), ("device_bytes", c_int64),
                 ("status", c_int32), ("refine_iters", c_int32), ("omega", c_double),
                 ("omega_first", c_double), ("min_abs_pivot", c_double), ("max_abs_pivot", c_double),
-                ("factor_kernel_ms", c_double), ("solve_ms", c_double), ("residual_ms", c_double)]
+                ("factor_kernel_ms", c_double), ("solve_ms", c_double), ("residual_ms", c_double),
+                ("kernel_launches", c_int64), ("factor_kernel_ms_total", c_double),
+                ("residual_ms_total", c_double), ("sweep_ms_total", c_double),
+                ("factor_kernel_calls", c_int64), ("residual_calls", c_int64), ("sweep_calls", c_int64)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}

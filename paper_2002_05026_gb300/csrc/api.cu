@@ -27,15 +27,21 @@ struct d3m_ctx {
   std::vector<void*> allocs;
   int64_t dev_bytes = 0;
   bool factored = false;
+  bool factor_checked = false;       // status of the last factorization already read
   int last_status = D3M_OK;
   int refine_iters = 0;
   double omega = NAN, omega_first = NAN;
   int omega_valid = 0;
-  float fact_ms = 0.f, solve_ms = 0.f, resid_ms = 0.f;
-  bool have_fact_ev = false, have_solve_ev = false;
-  cudaEvent_t ev_f0 = nullptr, ev_f1 = nullptr, ev_s0 = nullptr, ev_s1 = nullptr;
-  std::vector<cudaEvent_t> ev_res;   // pairs around residual kernels of the last solve
-  int nres_ev = 0;
+  // device timing: event pairs recorded around launches, read by d3m_get_info
+  enum { EV_FACTOR = 0, EV_RESID = 1, EV_SWEEP = 2, EV_SOLVE = 3, EV_KINDS = 4 };
+  struct EvPair { cudaEvent_t a, b; int kind; };
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<EvPair> ev_pending;
+  EvPair ev_open[EV_KINDS];
+  double ev_total[EV_KINDS] = {0, 0, 0, 0};
+  int64_t ev_calls[EV_KINDS] = {0, 0, 0, 0};
+  double last_factor_ms = 0, last_solve_ms = 0, last_resid_ms = 0;
+  int64_t launches = 0;
   // factor data
   double2* K = nullptr;
   TileTask* tasks = nullptr;
@@ -109,6 +115,36 @@ int set_err(d3m_ctx* h, int code, const std::string& msg) {
     if (e_ != cudaSuccess)                                                                  \
       return set_err(h, D3M_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
   } while (0)
+
+cudaEvent_t ev_get(d3m_ctx* h) {
+  if (!h->ev_pool.empty()) {
+    cudaEvent_t e = h->ev_pool.back();
+    h->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return e;
+}
+
+void ev_begin(d3m_ctx* h, int kind, cudaStream_t st) {
+  d3m_ctx::EvPair& p = h->ev_open[kind];
+  p.a = ev_get(h);
+  p.b = ev_get(h);
+  p.kind = kind;
+  if (p.a) cudaEventRecord(p.a, st);
+}
+
+void ev_end(d3m_ctx* h, int kind, cudaStream_t st) {
+  d3m_ctx::EvPair& p = h->ev_open[kind];
+  if (!p.a || !p.b) return;
+  cudaEventRecord(p.b, st);
+  h->ev_pending.push_back(p);
+  p.a = p.b = nullptr;
+}
 
 template <typename T>
 T* dalloc(d3m_ctx* h, size_t count) {
@@ -360,12 +396,6 @@ int d3m_create(d3m_handle* out, const d3m_pattern* pat, const int32_t* perm, con
   ALLOC(h->stat_dev, double, 1);
   ALLOC(h->contract, double2, S.N);
   CUDA_TRY(h, cudaMallocHost(&h->h_stat, sizeof(double)));
-  CUDA_TRY(h, cudaEventCreate(&h->ev_f0));
-  CUDA_TRY(h, cudaEventCreate(&h->ev_f1));
-  CUDA_TRY(h, cudaEventCreate(&h->ev_s0));
-  CUDA_TRY(h, cudaEventCreate(&h->ev_s1));
-  h->ev_res.resize(2 * (h->opt.refine_max_iter + 2));
-  for (auto& e : h->ev_res) CUDA_TRY(h, cudaEventCreate(&e));
 #undef ALLOC
 #undef UPLOAD
   return D3M_OK;
@@ -415,6 +445,7 @@ int d3m_factor(d3m_handle h, const void* Kin, void* stream) {
   ResidualParams rp = residual_params(h, nullptr, nullptr, 1);
   int rc = launch_knorm(rp, h->nchunks, st);
   if (rc) return set_err(h, D3M_ERR_CUDA, std::string("knorm launch: ") + cudaGetErrorString((cudaError_t)rc));
+  h->launches += 1;
   FactorParams p;
   p.tasks = h->tasks;
   p.klist = h->klist;
@@ -433,14 +464,15 @@ int d3m_factor(d3m_handle h, const void* Kin, void* stream) {
   p.opB = h->opB;
   p.timeout_ns = h->opt.timeout_ns;
   p.piv_tol = 1e3 * (h->fp64 ? 1.1102230246251565e-16 : 5.9604644775390625e-08);
-  CUDA_TRY(h, cudaEventRecord(h->ev_f0, st));
+  ev_begin(h, d3m_ctx::EV_FACTOR, st);
   if (h->tc) rc = launch_factor_tc(p, h->maps, h->nsm, st);
   else rc = launch_factor_simt(p, h->fp64, h->nsm, st);
   if (rc) return set_err(h, D3M_ERR_CUDA, std::string("factor launch: ") + cudaGetErrorString((cudaError_t)rc));
-  CUDA_TRY(h, cudaEventRecord(h->ev_f1, st));
+  ev_end(h, d3m_ctx::EV_FACTOR, st);
+  h->launches += 1;
   CUDA_TRY(h, cudaMemcpyAsync(h->h_ctl, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
-  h->have_fact_ev = true;
   h->factored = true;
+  h->factor_checked = false;
   h->last_status = D3M_OK;
   return D3M_OK;
 }
@@ -473,8 +505,14 @@ static int sweep(d3m_ctx* h, const double2* src, double2* dst, int nrhs, int acc
   a.lev_ptr = h->lev_ptr.data();
   a.tstart = h->tstart;
   a.tcolptr = h->tcolptr;
+  ev_begin(h, d3m_ctx::EV_SWEEP, st);
   int rc = launch_sweep(a, h->fp64, st);
   if (rc) return set_err(h, D3M_ERR_CUDA, std::string("sweep launch: ") + cudaGetErrorString((cudaError_t)rc));
+  ev_end(h, d3m_ctx::EV_SWEEP, st);
+  int64_t nl = 2;
+  for (int lv = 0; lv < S.nlevels; ++lv)
+    nl += 2 + (S.fwd_item_ptr[lv + 1] > S.fwd_item_ptr[lv]) + (S.bwd_item_ptr[lv + 1] > S.bwd_item_ptr[lv]);
+  h->launches += nl;
   return D3M_OK;
 }
 
@@ -483,15 +521,13 @@ static int residual_omega(d3m_ctx* h, const double2* X, const double2* B, int nr
   const int mr = h->opt.max_nrhs;
   CUDA_TRY(h, cudaMemsetAsync(h->norms, 0, 2 * mr * sizeof(unsigned), st));
   ResidualParams rp = residual_params(h, X, B, nrhs);
-  if (h->nres_ev + 2 <= (int)h->ev_res.size()) CUDA_TRY(h, cudaEventRecord(h->ev_res[h->nres_ev], st));
+  ev_begin(h, d3m_ctx::EV_RESID, st);
   int rc = launch_residual(rp, h->nchunks, st);
   if (rc) return set_err(h, D3M_ERR_CUDA, std::string("residual launch: ") + cudaGetErrorString((cudaError_t)rc));
-  if (h->nres_ev + 2 <= (int)h->ev_res.size()) {
-    CUDA_TRY(h, cudaEventRecord(h->ev_res[h->nres_ev + 1], st));
-    h->nres_ev += 2;
-  }
+  ev_end(h, d3m_ctx::EV_RESID, st);
   rc = launch_omega(h->norms, h->norms + mr, h->norms + 2 * mr, h->norms + 3 * mr, nrhs, h->omega_dev, h->stat_dev, st);
   if (rc) return set_err(h, D3M_ERR_CUDA, std::string("omega launch: ") + cudaGetErrorString((cudaError_t)rc));
+  h->launches += 2;
   return D3M_OK;
 }
 
@@ -500,6 +536,17 @@ static int solve_impl(d3m_ctx* h, const void* Bin, void* Xout, int nrhs, cudaStr
   if (nrhs < 1 || nrhs > h->opt.max_nrhs)
     return set_err(h, D3M_ERR_INVALID, "nrhs out of range [1, max_nrhs]");
   if (!h->factored) return set_err(h, D3M_ERR_STATE, "solve before factor");
+  if (!h->factor_checked) {
+    // the first solve after a factorization reads its status (one synchronization)
+    CUDA_TRY(h, cudaStreamSynchronize(st));
+    h->factor_checked = true;
+    int fe = factor_error(h);
+    if (fe != D3M_OK) {
+      h->last_status = fe;
+      h->factored = false;
+      return fe;
+    }
+  }
   const Symbolic& S = h->S;
   const size_t vbytes = (size_t)S.n * nrhs * sizeof(double2);
   const bool bdev = is_device_ptr(Bin), xdev = is_device_ptr(Xout);
@@ -510,12 +557,11 @@ static int solve_impl(d3m_ctx* h, const void* Bin, void* Xout, int nrhs, cudaStr
   }
   double2* X = xdev ? (double2*)Xout : h->d_x;
   if ((const void*)X == (const void*)B) return set_err(h, D3M_ERR_INVALID, "B and X may not alias");
-  h->nres_ev = 0;
   h->omega = NAN;
   h->omega_first = NAN;
   h->omega_valid = 0;
   h->refine_iters = 0;
-  CUDA_TRY(h, cudaEventRecord(h->ev_s0, st));
+  ev_begin(h, d3m_ctx::EV_SOLVE, st);
   int status = D3M_OK;
   const int mr = h->opt.max_nrhs;
   if (h->fp64) {
@@ -526,6 +572,7 @@ static int solve_impl(d3m_ctx* h, const void* Bin, void* Xout, int nrhs, cudaStr
       CUDA_TRY(h, cudaMemsetAsync(h->norms + 2 * mr, 0, mr * sizeof(unsigned), st));
       rc = launch_absmax(B, S.n, nrhs, h->norms + 2 * mr, st);
       if (rc) return set_err(h, D3M_ERR_CUDA, "absmax launch failed");
+      h->launches += 1;
       rc = residual_omega(h, X, B, nrhs, st);
       if (rc) return rc;
       CUDA_TRY(h, cudaMemcpyAsync(h->h_stat, h->stat_dev, sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -537,6 +584,7 @@ static int solve_impl(d3m_ctx* h, const void* Bin, void* Xout, int nrhs, cudaStr
     CUDA_TRY(h, cudaMemsetAsync(h->norms + 2 * mr, 0, mr * sizeof(unsigned), st));
     int rc = launch_absmax(B, S.n, nrhs, h->norms + 2 * mr, st);
     if (rc) return set_err(h, D3M_ERR_CUDA, "absmax launch failed");
+    h->launches += 1;
     double best = INFINITY;
     std::vector<double> hist;
     const double2* src = B;
@@ -546,15 +594,7 @@ static int solve_impl(d3m_ctx* h, const void* Bin, void* Xout, int nrhs, cudaStr
       rc = residual_omega(h, X, B, nrhs, st);                // r = b - K x, omega
       if (rc) return rc;
       CUDA_TRY(h, cudaMemcpyAsync(h->h_stat, h->stat_dev, sizeof(double), cudaMemcpyDeviceToHost, st));
-      if (it == 0) CUDA_TRY(h, cudaMemcpyAsync(h->h_ctl, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
       CUDA_TRY(h, cudaStreamSynchronize(st));
-      if (it == 0) {
-        int fe = factor_error(h);
-        if (fe != D3M_OK) {
-          h->last_status = fe;
-          return fe;
-        }
-      }
       const double w = *h->h_stat;
       h->refine_iters = it + 1;
       if (it == 0) h->omega_first = w;
@@ -581,8 +621,7 @@ static int solve_impl(d3m_ctx* h, const void* Bin, void* Xout, int nrhs, cudaStr
       src = h->d_r;
     }
   }
-  CUDA_TRY(h, cudaEventRecord(h->ev_s1, st));
-  h->have_solve_ev = true;
+  ev_end(h, d3m_ctx::EV_SOLVE, st);
   if (!xdev) CUDA_TRY(h, cudaMemcpyAsync(Xout, X, vbytes, cudaMemcpyDeviceToHost, st));
   h->last_status = status;
   return status;
@@ -610,6 +649,7 @@ int d3m_grad_eps(d3m_handle h, const void* Lambda, const void* X, int32_t nrhs, 
   int rc = launch_contract((const double2*)Lambda, (const double2*)X, S.n, nrhs, h->xoff_orig, h->m_orig, S.N,
                            h->contract, st);
   if (rc) return set_err(h, D3M_ERR_CUDA, "contract launch failed");
+  h->launches += 1;
   std::vector<double2> sf(S.N);
   CUDA_TRY(h, cudaMemcpyAsync(sf.data(), h->contract, S.N * sizeof(double2), cudaMemcpyDeviceToHost, st));
   CUDA_TRY(h, cudaStreamSynchronize(st));
@@ -634,6 +674,7 @@ int d3m_grad_pattern(d3m_handle h, const void* Lambda, const void* X, int32_t nr
   int rc = launch_grad_pattern((const double2*)Lambda, (const double2*)X, S.n, nrhs, h->colptr, h->rowidx, h->blk_col,
                                h->kblk_off, h->xoff_orig, h->m_orig, S.nnzb_K, (double2*)dK, (cudaStream_t)stream);
   if (rc) return set_err(h, D3M_ERR_CUDA, "grad_pattern launch failed");
+  h->launches += 1;
   return D3M_OK;
 }
 
@@ -711,17 +752,41 @@ int d3m_get_info(d3m_handle h, d3m_info* info, void* stream) {
   info->refine_iters = h->refine_iters;
   info->omega = h->omega_valid ? h->omega : NAN;
   info->omega_first = h->omega_valid ? h->omega_first : NAN;
-  if (h->have_fact_ev) CUDA_TRY(h, cudaEventElapsedTime(&h->fact_ms, h->ev_f0, h->ev_f1));
-  if (h->have_solve_ev) CUDA_TRY(h, cudaEventElapsedTime(&h->solve_ms, h->ev_s0, h->ev_s1));
-  float rsum = 0.f;
-  for (int e = 0; e + 1 < h->nres_ev; e += 2) {
+  // fold the recorded event pairs into the totals; the last pair of a kind is the "last call"
+  double tot[d3m_ctx::EV_KINDS] = {0, 0, 0, 0};
+  int64_t cnt[d3m_ctx::EV_KINDS] = {0, 0, 0, 0};
+  bool resid_seen = false;
+  for (size_t e = 0; e < h->ev_pending.size(); ++e) {
+    const auto& pr = h->ev_pending[e];
     float t = 0.f;
-    CUDA_TRY(h, cudaEventElapsedTime(&t, h->ev_res[e], h->ev_res[e + 1]));
-    rsum += t;
+    CUDA_TRY(h, cudaEventElapsedTime(&t, pr.a, pr.b));
+    tot[pr.kind] += t;
+    cnt[pr.kind] += 1;
+    if (pr.kind == d3m_ctx::EV_FACTOR) h->last_factor_ms = t;
+    if (pr.kind == d3m_ctx::EV_SOLVE) {
+      h->last_solve_ms = t;
+      h->last_resid_ms = 0;
+      resid_seen = true;
+    }
+    if (pr.kind == d3m_ctx::EV_RESID) {
+      if (!resid_seen) h->last_resid_ms = 0;
+      resid_seen = true;
+      h->last_resid_ms += t;
+    }
+    h->ev_pool.push_back(pr.a);
+    h->ev_pool.push_back(pr.b);
   }
-  info->factor_kernel_ms = h->fact_ms;
-  info->solve_ms = h->solve_ms;
-  info->residual_ms = rsum;
+  h->ev_pending.clear();
+  info->factor_kernel_ms = h->last_factor_ms;
+  info->solve_ms = h->last_solve_ms;
+  info->residual_ms = h->last_resid_ms;
+  info->kernel_launches = h->launches;
+  info->factor_kernel_ms_total = tot[d3m_ctx::EV_FACTOR];
+  info->residual_ms_total = tot[d3m_ctx::EV_RESID];
+  info->sweep_ms_total = tot[d3m_ctx::EV_SWEEP];
+  info->factor_kernel_calls = cnt[d3m_ctx::EV_FACTOR];
+  info->residual_calls = cnt[d3m_ctx::EV_RESID];
+  info->sweep_calls = cnt[d3m_ctx::EV_SWEEP];
   return D3M_OK;
 }
 
@@ -735,11 +800,16 @@ void d3m_destroy(d3m_handle h) {
   for (void* p : h->allocs) cudaFree(p);
   if (h->h_ctl) cudaFreeHost(h->h_ctl);
   if (h->h_stat) cudaFreeHost(h->h_stat);
-  cudaEvent_t evs[4] = {h->ev_f0, h->ev_f1, h->ev_s0, h->ev_s1};
-  for (cudaEvent_t e : evs)
+  for (cudaEvent_t e : h->ev_pool)
     if (e) cudaEventDestroy(e);
-  for (cudaEvent_t e : h->ev_res)
-    if (e) cudaEventDestroy(e);
+  for (const auto& pr : h->ev_pending) {
+    if (pr.a) cudaEventDestroy(pr.a);
+    if (pr.b) cudaEventDestroy(pr.b);
+  }
+  for (const auto& pr : h->ev_open) {
+    if (pr.a) cudaEventDestroy(pr.a);
+    if (pr.b) cudaEventDestroy(pr.b);
+  }
   delete h;
 }
 

@@ -132,11 +132,11 @@ __device__ __forceinline__ void stage_rows(C* sL, const C* src, int b, int r0) {
   }
 }
 
-// forward: r = y_k - sum partials;  y_t = Linv_tt r_t;  r_t' -= L_t't y_t;  z = D^{-1} y
+// forward: r = b_k - sum partials;  y_t = Linv_tt r_t;  r_t' -= L_t't y_t  (Y keeps y: later
+// levels gather L_IJ y_J; the diagonal step z = D^{-1} y is applied by the backward kernel)
 template <typename R>
 __global__ void __launch_bounds__(GT) block_fwd_kernel(BlockSweep s, const typename CT<R>::C* __restrict__ L,
                                                        const typename CT<R>::C* __restrict__ Linv,
-                                                       const typename CT<R>::C* __restrict__ D,
                                                        typename CT<R>::C* __restrict__ Y,
                                                        const typename CT<R>::C* __restrict__ P) {
   using C = typename CT<R>::C;
@@ -200,18 +200,17 @@ __global__ void __launch_bounds__(GT) block_fwd_kernel(BlockSweep s, const typen
       }
     }
   }
-  // z = D^{-1} y  (Y now holds z)
   for (int i = threadIdx.x; i < rows * rc; i += GT) {
     const int row = i % rows, j = i / rows;
-    const C d = D[(int64_t)t0 * b + row];
-    Y[(int64_t)(j0 + j) * s.npad + (int64_t)t0 * b + row] = cdiv(sv[row * s.rc + j], d);
+    Y[(int64_t)(j0 + j) * s.npad + (int64_t)t0 * b + row] = sv[row * s.rc + j];
   }
 }
 
-// backward: r = z_k - sum partials;  for t = nt-1..0: w_t = Linv_tt^T r_t; r_t' -= L_{t,t'}^T w_t (t' < t)
+// backward: r = D^{-1} y_k - sum partials;  for t = nt-1..0: w_t = Linv_tt^T r_t; r_t' -= L_{t,t'}^T w_t (t' < t)
 template <typename R>
 __global__ void __launch_bounds__(GT) block_bwd_kernel(BlockSweep s, const typename CT<R>::C* __restrict__ L,
                                                        const typename CT<R>::C* __restrict__ Linv,
+                                                       const typename CT<R>::C* __restrict__ D,
                                                        typename CT<R>::C* __restrict__ Y,
                                                        const typename CT<R>::C* __restrict__ P) {
   using C = typename CT<R>::C;
@@ -228,7 +227,7 @@ __global__ void __launch_bounds__(GT) block_bwd_kernel(BlockSweep s, const typen
   for (int i = threadIdx.x; i < rows * rc; i += GT) {
     const int row = i % rows, j = i / rows;
     const int J = t0 + row / b;
-    C v = Y[(int64_t)(j0 + j) * s.npad + (int64_t)t0 * b + row];
+    C v = cdiv(Y[(int64_t)(j0 + j) * s.npad + (int64_t)t0 * b + row], D[(int64_t)t0 * b + row]);
     const int64_t sp = s.slot_ptr[J];
     const int64_t first = sp & 0xffffffffLL, cnt = sp >> 32;
     for (int64_t q = 0; q < cnt; ++q)
@@ -469,7 +468,7 @@ static int sweep_impl(const SweepLaunch& a, cudaStream_t st) {
     bs.blocks = a.lev_blocks + a.lev_ptr[lv];
     bs.slot_ptr = a.fwd_slot_ptr;
     const unsigned nb = (unsigned)(a.lev_ptr[lv + 1] - a.lev_ptr[lv]);
-    block_fwd_kernel<R><<<dim3(nb, ny), GT, bsm, st>>>(bs, L, Linv, D, Y, P);
+    block_fwd_kernel<R><<<dim3(nb, ny), GT, bsm, st>>>(bs, L, Linv, Y, P);
   }
   for (int lv = a.nlevels - 1; lv >= 0; --lv) {
     const int64_t i0 = a.bwd_item_ptr[lv], i1 = a.bwd_item_ptr[lv + 1];
@@ -478,7 +477,7 @@ static int sweep_impl(const SweepLaunch& a, cudaStream_t st) {
     bs.blocks = a.lev_blocks + a.lev_ptr[lv];
     bs.slot_ptr = a.bwd_slot_ptr;
     const unsigned nb = (unsigned)(a.lev_ptr[lv + 1] - a.lev_ptr[lv]);
-    block_bwd_kernel<R><<<dim3(nb, ny), GT, bsm, st>>>(bs, L, Linv, Y, P);
+    block_bwd_kernel<R><<<dim3(nb, ny), GT, bsm, st>>>(bs, L, Linv, D, Y, P);
   }
   permute_out_kernel<R><<<(unsigned)gblocks, nthreads, 0, st>>>(Y, a.npad, a.dst, a.n, a.pad2orig, a.nrhs, a.accumulate);
   return (int)cudaGetLastError();

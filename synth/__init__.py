@@ -91,6 +91,45 @@ def normal_rows(seed: int, tag: int, domain: int, rows, count: int) -> np.ndarra
     return out.reshape(rows.size, nblk * 4)[:, :count]
 
 
+def _philox_torch(c0, c1, c2, c3, k0: int, k1: int):
+    """Philox4x32-10 on torch int64 tensors holding 32-bit values.  The 32x32-bit products
+    are formed as wrapping 64-bit products, whose high and low 32-bit halves are exact."""
+    mask = 0xFFFFFFFF
+    k0 = int(k0) & mask
+    k1 = int(k1) & mask
+    for _ in range(10):
+        p0 = c0 * 0xD2511F53
+        p1 = c2 * 0xCD9E8D57
+        hi0, lo0 = (p0 >> 32) & mask, p0 & mask
+        hi1, lo1 = (p1 >> 32) & mask, p1 & mask
+        c0, c1, c2, c3 = hi1 ^ c1 ^ k0, lo1, hi0 ^ c3 ^ k1, lo0
+        k0 = (k0 + _PHILOX_W0) & mask
+        k1 = (k1 + _PHILOX_W1) & mask
+    return c0, c1, c2, c3
+
+
+def normal_rows_torch(seed: int, tag: int, domain: int, nrows: int, count: int, device):
+    """Same stream as normal_rows for rows 0..nrows-1, computed with torch on `device`
+    (equal to the numpy draw up to the rounding of log / sqrt / cos / sin)."""
+    import torch
+    nblk = (count + 3) // 4
+    j = torch.arange(nblk, dtype=torch.int64, device=device)
+    r = torch.arange(nrows, dtype=torch.int64, device=device)
+    c0 = j[None, :].expand(nrows, nblk)
+    c1 = r[:, None].expand(nrows, nblk)
+    c2 = torch.full((nrows, nblk), domain, dtype=torch.int64, device=device)
+    c3 = torch.zeros((nrows, nblk), dtype=torch.int64, device=device)
+    x0, x1, x2, x3 = _philox_torch(c0, c1, c2, c3, seed, tag)
+    out = torch.empty((nrows, nblk, 4), dtype=torch.float64, device=device)
+    scale = 1.0 / 4294967296.0
+    for (ua, ub, ia, ib) in ((x0, x1, 0, 1), (x2, x3, 2, 3)):
+        rad = torch.sqrt(-2.0 * torch.log((ua.to(torch.float64) + 0.5) * scale))
+        ang = (2.0 * math.pi) * ((ub.to(torch.float64) + 0.5) * scale)
+        out[:, :, ia] = rad * torch.cos(ang)
+        out[:, :, ib] = rad * torch.sin(ang)
+    return out.reshape(nrows, nblk * 4)[:, :count]
+
+
 def uniform01(seed: int, tag: int, ids) -> np.ndarray:
     """One uniform (0,1) double per id (counter (id, 0, 0, 0))."""
     ids = np.asarray(ids, dtype=np.uint64)
@@ -208,8 +247,9 @@ def domain_eps(seed: int, ndom: int, lo: float = 1.0, hi: float = 4.0) -> np.nda
 
 
 def make_problem(nx, ny, nz, m, k2, tau, seed, eps=None, real_g=False, device=None) -> Problem:
-    """Assemble K's lower blocks.  `device`: None/'cpu' for numpy, or a torch device for the
-    G G^T products (the result is then a torch complex128 tensor on that device)."""
+    """Assemble K's lower blocks.  `device`: None for numpy, or a torch device ("cpu", "cuda")
+    for the random draws and the G G^T products (the result is then a torch complex128
+    tensor on that device)."""
     dom_if = domain_interfaces(nx, ny, nz)
     ndom = nx * ny * nz
     colptr, rowidx = lower_pattern(nx, ny, nz)
@@ -224,7 +264,7 @@ def make_problem(nx, ny, nz, m, k2, tau, seed, eps=None, real_g=False, device=No
     for g in range(nf):
         for e in range(colptr[g], colptr[g + 1]):
             pos[(int(rowidx[e]), g)] = e
-    use_torch = device is not None and str(device) != "cpu"
+    use_torch = device is not None
     if use_torch:
         import torch
         blocks = torch.zeros(nnzb * m * m, dtype=torch.complex128, device=device)
@@ -235,14 +275,18 @@ def make_problem(nx, ny, nz, m, k2, tau, seed, eps=None, real_g=False, device=No
         r = len(I) * m
         if r == 0:
             continue
-        G = domain_G(seed, i, r, real_g).astype(np.complex128)
         sigma = -k2 * eps[i] + 1j * tau
         if use_torch:
             import torch
-            Gt = torch.from_numpy(np.ascontiguousarray(G)).to(device=device, dtype=torch.complex128)
+            z = normal_rows_torch(seed, TAG_G, i, r, r if real_g else 2 * r, device)
+            if real_g:
+                Gt = (z / math.sqrt(r)).to(torch.complex128)
+            else:
+                Gt = torch.complex(z[:, 0::2], z[:, 1::2]) / math.sqrt(2.0 * r)
             M = Gt @ Gt.T
             M.diagonal().add_(sigma)
         else:
+            G = domain_G(seed, i, r, real_g).astype(np.complex128)
             M = G @ G.T
             M[np.diag_indices(r)] += sigma
         for a, f in enumerate(I):

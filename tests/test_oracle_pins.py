@@ -336,3 +336,17 @@ def test_pattern_gradient_directional_derivative():
     # diagonal stored block appears once, so its symmetric gradient pairs with dK directly
     pred = np.real(sum(np.sum(G[k] * dK[k]) for k in Kb))
     assert abs(fd - pred) <= 1e-6 * abs(pred)
+
+
+def test_torch_philox_matches_definition():
+    torch = pytest.importorskip("torch")
+    for line in open(os.path.join(GOLDEN, "philox4x32_10_kat.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        v = [int(t, 16) for t in line.split()]
+        c = [torch.tensor([v[i]], dtype=torch.int64) for i in range(4)]
+        out = synth._philox_torch(*c, v[4], v[5])
+        assert [int(o[0]) for o in out] == v[6:10]
+    a = synth.normal_rows(5, 1, 3, np.arange(64), 130)
+    b = synth.normal_rows_torch(5, 1, 3, 64, 130, "cpu").numpy()
+    assert np.abs(a - b).max() < 1e-13
