@@ -73,7 +73,7 @@ class D3MSolveFn(torch.autograd.Function):
     def backward(ctx, gx):
         (x,) = ctx.saved_tensors
         op = ctx.op
-        lam = op.handle.adjoint(torch.conj(gx).contiguous())          # K^T = K: same factors
+        lam = op.handle.adjoint(torch.conj(gx).resolve_conj())        # K^T = K: same factors
         x2 = x if x.dim() == 2 else x.reshape(-1, 1)
         l2 = lam if lam.dim() == 2 else lam.reshape(-1, 1)
         geps = op.handle.grad_eps(l2, x2, op.dom_if, op.k2)

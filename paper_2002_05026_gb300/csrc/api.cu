@@ -60,6 +60,7 @@ struct d3m_ctx {
   void* D = nullptr;
   void* opA = nullptr;
   void* opB = nullptr;
+  void* Sacc = nullptr;
   TcMaps maps;
   // solve
   SolveItem* fwd_items = nullptr;
@@ -68,6 +69,8 @@ struct d3m_ctx {
   int64_t* bwd_slot = nullptr;
   int32_t* lev_blocks = nullptr;
   std::vector<int64_t> lev_ptr;
+  int32_t* lev_tiles = nullptr;
+  std::vector<int64_t> lev_tile_ptr;
   int32_t* tstart = nullptr;
   int64_t* tcolptr = nullptr;
   int64_t* pad2orig = nullptr;
@@ -199,7 +202,7 @@ int factor_error(d3m_ctx* h) {
   if (c.err == D3M_ERR_TIMEOUT)
     return set_err(h, D3M_ERR_TIMEOUT, "bounded device wait expired in the factorization queue");
   if (c.err != 0) return set_err(h, c.err, "factorization failed");
-  if (c.done != (int)h->S.tasks.size())
+  if (c.done != (int64_t)h->S.tasks.size())
     return set_err(h, D3M_ERR_TIMEOUT, "factorization finished " + std::to_string(c.done) + " of " +
                                            std::to_string(h->S.tasks.size()) + " tasks");
   return D3M_OK;
@@ -278,7 +281,8 @@ int d3m_create(d3m_handle* out, const d3m_pattern* pat, const int32_t* perm, con
   }
   *out = h;
   const Symbolic& S = h->S;
-  const int64_t ntiles = (int64_t)S.tasks.size();
+  const int64_t ntiles = S.ntiles;
+  const int64_t ntask = (int64_t)S.tasks.size();
   const int b = h->b;
   const int mr = h->opt.max_nrhs;
   if (cudaGetDevice(&h->device) != cudaSuccess ||
@@ -311,10 +315,10 @@ int d3m_create(d3m_handle* out, const d3m_pattern* pat, const int32_t* perm, con
     if ((h->opt.debug_flags & D3M_DEBUG_STALL_LAST_TASK) && !nd.empty()) nd.back() += 1;
     UPLOAD(h->ndeps, nd);
   }
-  ALLOC(h->cnt, int32_t, ntiles);
+  ALLOC(h->cnt, int32_t, ntask);
   UPLOAD(h->succ_ptr, S.succ_ptr);
   UPLOAD(h->succ, S.succ);
-  ALLOC(h->ready, int32_t, ntiles);
+  ALLOC(h->ready, int32_t, ntask);
   UPLOAD(h->init_ready, S.init_ready);
   ALLOC(h->ctl, Ctl, 1);
   ALLOC(h->ctl0, Ctl, 1);
@@ -331,7 +335,8 @@ int d3m_create(d3m_handle* out, const d3m_pattern* pat, const int32_t* perm, con
   h->L = dalloc<unsigned char>(h, (size_t)ntiles * b * b * h->csize);
   h->Linv = dalloc<unsigned char>(h, (size_t)S.NT * b * b * h->csize);
   h->D = dalloc<unsigned char>(h, (size_t)S.NT * b * h->csize);
-  if (!h->L || !h->Linv || !h->D) return set_err(h, D3M_ERR_OOM, "cudaMalloc failed for the factor tiles");
+  h->Sacc = dalloc<unsigned char>(h, (size_t)std::max<int64_t>(1, S.n_acc) * b * b * h->csize);
+  if (!h->L || !h->Linv || !h->D || !h->Sacc) return set_err(h, D3M_ERR_OOM, "cudaMalloc failed for the factor tiles");
   if (h->tc) {
     // operand planes (bf16): A: [tile][2 splits][2 planes][b rows][b], B: [tile][2][3][b][b]
     h->opA = dalloc<unsigned char>(h, (size_t)ntiles * 4 * b * b * 2);
@@ -353,13 +358,30 @@ int d3m_create(d3m_handle* out, const d3m_pattern* pat, const int32_t* perm, con
       h->lev_ptr.push_back((int64_t)lb.size());
     }
     UPLOAD(h->lev_blocks, lb);
+    std::vector<int32_t> lt;
+    h->lev_tile_ptr.assign(1, 0);
+    for (const auto& l : S.lev_blocks) {
+      for (int k : l)
+        for (int I = S.tstart[k]; I < S.tstart[k + 1]; ++I) lt.push_back(I);
+      h->lev_tile_ptr.push_back((int64_t)lt.size());
+    }
+    UPLOAD(h->lev_tiles, lt);
     std::vector<int64_t> p2o(S.npad, -1);
     for (int k = 0; k < S.N; ++k)
       for (int u = 0; u < S.m[k]; ++u) p2o[S.xoff[k] + u] = S.xoff_orig[S.perm[k]] + u;
     UPLOAD(h->pad2orig, p2o);
-    int mrows = 0;
-    for (int k = 0; k < S.N; ++k) mrows = std::max(mrows, S.ntile[k] * b);
+    int mrows = 0, mnt = 0;
+    for (int k = 0; k < S.N; ++k) {
+      mrows = std::max(mrows, S.ntile[k] * b);
+      mnt = std::max(mnt, S.ntile[k]);
+    }
     h->max_rows = mrows;
+    // the in-block sweep kernels keep one block's running vector (1 rhs at least) and two
+    // staged half tiles in shared memory, and list at most 512 tile jobs per block
+    const size_t need = h->csize * (2 * (size_t)64 * (b + 1) + (size_t)mrows + (size_t)b);
+    if (need > 220 * 1024 || (int64_t)mnt * (mnt + 1) / 2 * (b / 64) > 512)
+      return set_err(h, D3M_ERR_INVALID, "interface block too large for the solve kernels (m = " +
+                                             std::to_string(mrows) + ")");
   }
   UPLOAD(h->tstart, S.tstart);
   UPLOAD(h->tcolptr, S.tcolptr);
@@ -430,7 +452,7 @@ int d3m_factor(d3m_handle h, const void* Kin, void* stream) {
   if (!Kin) return set_err(h, D3M_ERR_INVALID, "K is NULL");
   cudaStream_t st = (cudaStream_t)stream;
   const Symbolic& S = h->S;
-  const int64_t ntiles = (int64_t)S.tasks.size();
+  const int64_t ntiles = (int64_t)S.tasks.size();   // all tasks (final + update)
   const size_t kbytes = (size_t)S.kblk_off.back() * sizeof(double2);
   CUDA_TRY(h, cudaMemcpyAsync(h->K, Kin, kbytes, is_device_ptr(Kin) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
   // reset the task graph state
@@ -462,6 +484,7 @@ int d3m_factor(d3m_handle h, const void* Kin, void* stream) {
   p.D = h->D;
   p.opA = h->opA;
   p.opB = h->opB;
+  p.Sacc = h->Sacc;
   p.timeout_ns = h->opt.timeout_ns;
   p.piv_tol = 1e3 * (h->fp64 ? 1.1102230246251565e-16 : 5.9604644775390625e-08);
   ev_begin(h, d3m_ctx::EV_FACTOR, st);
@@ -503,15 +526,17 @@ static int sweep(d3m_ctx* h, const double2* src, double2* dst, int nrhs, int acc
   a.bwd_slot_ptr = h->bwd_slot;
   a.lev_blocks = h->lev_blocks;
   a.lev_ptr = h->lev_ptr.data();
+  a.lev_tiles = h->lev_tiles;
+  a.lev_tile_ptr = h->lev_tile_ptr.data();
   a.tstart = h->tstart;
   a.tcolptr = h->tcolptr;
   ev_begin(h, d3m_ctx::EV_SWEEP, st);
   int rc = launch_sweep(a, h->fp64, st);
   if (rc) return set_err(h, D3M_ERR_CUDA, std::string("sweep launch: ") + cudaGetErrorString((cudaError_t)rc));
   ev_end(h, d3m_ctx::EV_SWEEP, st);
-  int64_t nl = 2;
+  int64_t nl = 3;   // permute in, diagonal scale, permute out
   for (int lv = 0; lv < S.nlevels; ++lv)
-    nl += 2 + (S.fwd_item_ptr[lv + 1] > S.fwd_item_ptr[lv]) + (S.bwd_item_ptr[lv + 1] > S.bwd_item_ptr[lv]);
+    nl += 2 + 2 * (S.fwd_item_ptr[lv + 1] > S.fwd_item_ptr[lv]) + 2 * (S.bwd_item_ptr[lv + 1] > S.bwd_item_ptr[lv]);
   h->launches += nl;
   return D3M_OK;
 }

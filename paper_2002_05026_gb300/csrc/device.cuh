@@ -44,6 +44,7 @@ struct FactorParams {
   void* D;               // [NT][b] pivots
   void* opA;             // tensor-core operand planes (bf16) of L tiles
   void* opB;             // tensor-core operand planes (bf16) of W tiles / T_J
+  void* Sacc;            // [n_acc][b][b] partial Schur accumulators (complex, working precision)
   int64_t timeout_ns;
   double piv_tol;        // breakdown: |d| < piv_tol * max|S| of the diagonal tile
 };
@@ -186,7 +187,7 @@ template <typename R>
 __device__ __forceinline__ typename CT<R>::C k_entry(const TileTask& T, const double2* K, int r, int c) {
   using C = typename CT<R>::C;
   if (r >= T.rv || c >= T.cv) {
-    const bool one = T.same_block && (T.r0 + r == T.c0 + c);
+    const bool one = (T.flags & TF_SAME_BLOCK) && (T.r0 + r == T.c0 + c);
     return CT<R>::make(one ? (R)1 : (R)0, (R)0);
   }
   if (T.k_off < 0) return CT<R>::make((R)0, (R)0);

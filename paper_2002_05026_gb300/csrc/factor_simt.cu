@@ -3,9 +3,10 @@
 // R = double: the plain FP64 (complex128) path; R = float: complex64 factors without tensor
 // cores (used as the SIMT reference of the mixed path).
 //
-// Each task owns one lower tile (I, J) of L (paper Sec. II: per nonzero block a task doing
+// Each task works on one lower tile (I, J) of L (paper Sec. II: per nonzero block a task doing
 // the dense update, the dense triangular solve and the dense factorization):
-//   1. S = K_IJ - sum_K L_IK (D_K L_JK^T)         (K-list in increasing K, fixed order)
+//   1. S = S_in - sum_{K in segment} L_IK (D_K L_JK^T)   (S_in = K_IJ or the tile's accumulator)
+//   UPDATE task: store S in the accumulator and stop.  FINAL task:
 //   2a. I == J: unpivoted LDL^T of S in shared memory (scalar pivots, no conjugation),
 //       breakdown check |d| >= piv_tol * max|S|; store L_JJ, D_J and L_JJ^{-1} (for the solve)
 //   2b. I != J: L_IJ = S L_JJ^{-T} D_J^{-1} by a column sweep (right-looking triangular solve).
@@ -38,6 +39,7 @@ __global__ void __launch_bounds__(NTHR, 1) factor_simt_kernel(FactorParams p) {
   C* Lg = reinterpret_cast<C*>(p.L);
   C* Linv = reinterpret_cast<C*>(p.Linv);
   C* Dg = reinterpret_cast<C*>(p.D);
+  C* Sacc = reinterpret_cast<C*>(p.Sacc);
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
 
@@ -78,16 +80,31 @@ __global__ void __launch_bounds__(NTHR, 1) factor_simt_kernel(FactorParams p) {
       }
     }
     __syncthreads();
+    C* Sa = (T.sidx >= 0) ? Sacc + (int64_t)T.sidx * TB * TB : nullptr;
+    if (T.flags & TF_UPDATE) {
+      // partial update: accumulator <- S_in - sum over this segment
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int r = ty + 16 * i, c = tx + 16 * j;
+          const C s_in = (T.flags & TF_S_IN) ? ld_cg(Sa + r * TB + c) : k_entry<R>(T, p.K, r, c);
+          Sa[r * TB + c] = csub(s_in, acc[i][j]);
+        }
+      sched_complete(p, task);
+      continue;
+    }
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         const int r = ty + 16 * i, c = tx + 16 * j;
-        sA[r * LDS + c] = csub(k_entry<R>(T, p.K, r, c), acc[i][j]);
+        const C s_in = (T.flags & TF_S_IN) ? ld_cg(Sa + r * TB + c) : k_entry<R>(T, p.K, r, c);
+        sA[r * LDS + c] = csub(s_in, acc[i][j]);
       }
     __syncthreads();
 
-    if (T.is_diag) {
+    if (T.flags & TF_DIAG) {
       // ------------------------------------------------------------ 2a. diagonal tile
       R mx = 0;
       for (int i = tid; i < TB * TB; i += NTHR) {

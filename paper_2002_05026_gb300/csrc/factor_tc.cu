@@ -184,6 +184,7 @@ __global__ void __launch_bounds__(NTHR, 1)
   float2* Lg = reinterpret_cast<float2*>(p.L);
   float2* Linv = reinterpret_cast<float2*>(p.Linv);
   float2* Dg = reinterpret_cast<float2*>(p.D);
+  float2* Sacc = reinterpret_cast<float2*>(p.Sacc);
   __nv_bfloat16* opA = reinterpret_cast<__nv_bfloat16*>(p.opA);
   __nv_bfloat16* opB = reinterpret_cast<__nv_bfloat16*>(p.opB);
 
@@ -282,8 +283,40 @@ __global__ void __launch_bounds__(NTHR, 1)
       break;
     }
 
+    const bool is_diag = (T.flags & TF_DIAG) != 0;
+    const bool s_in = (T.flags & TF_S_IN) != 0;
+    float2* Sa = (T.sidx >= 0) ? Sacc + (int64_t)T.sidx * TB * TB : nullptr;
+    const int quarter = warp & 3, half = warp >> 2;
+    const int r = quarter * 32 + lane;
+    if (T.flags & TF_UPDATE) {
+      // ------------------------------------------------------------ partial update task
+      for (int pass = 0; pass < 2; ++pass) {
+        const int c0 = half * 64 + pass * 32;
+        float vr[32], vi[32];
+        tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + ACC1 + c0, vr);
+        tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + ACC1 + 128 + c0, vi);
+        float4* row = reinterpret_cast<float4*>(Sa + (int64_t)r * TB + c0);
+#pragma unroll 4
+        for (int i = 0; i < 32; i += 2) {
+          float2 a0, a1;
+          if (s_in) {
+            const float4 v = ld_cg4(row + i / 2);
+            a0 = make_float2(v.x, v.y);
+            a1 = make_float2(v.z, v.w);
+          } else {
+            a0 = k_entry<float>(T, p.K, r, c0 + i);
+            a1 = k_entry<float>(T, p.K, r, c0 + i + 1);
+          }
+          row[i / 2] = make_float4(a0.x - vr[i], a0.y - vi[i], a1.x - vr[i + 1], a1.y - vi[i + 1]);
+        }
+      }
+      tc_fence_before();
+      sched_complete(p, task);
+      continue;
+    }
+
     // off-diagonal: prefetch the first two chunks of T_J (B operand of the TRSM product)
-    if (!T.is_diag && tid == 0) {
+    if (!is_diag && tid == 0) {
       for (int c = 0; c < 2; ++c) {
         const uint32_t s = t_load & 1, use = t_load >> 1;
         if (!mbar_wait(smem_u32(&bar_tempty[s]), (use & 1) ^ 1, deadline)) { failed = true; break; }
@@ -296,10 +329,8 @@ __global__ void __launch_bounds__(NTHR, 1)
       }
     }
 
-    // ---------------------------------------------------------------- phase 2: S = K - acc
-    const int quarter = warp & 3, half = warp >> 2;
-    const int r = quarter * 32 + lane;
-    if (T.is_diag) {
+    // ---------------------------------------------------------------- phase 2: S = S_in - acc
+    if (is_diag) {
       float2* sS = reinterpret_cast<float2*>(smem);   // [128][129]
       float2* s_d = reinterpret_cast<float2*>(smem + DIAG_AUX);
       float2* s_col = s_d + TB;
@@ -316,7 +347,7 @@ __global__ void __launch_bounds__(NTHR, 1)
         }
 #pragma unroll 4
         for (int i = 0; i < 32; ++i) {
-          const float2 kv = k_entry<float>(T, p.K, r, c0 + i);
+          const float2 kv = s_in ? ld_cg(Sa + (int64_t)r * TB + c0 + i) : k_entry<float>(T, p.K, r, c0 + i);
           sS[r * LDS + c0 + i] = make_float2(kv.x - vr[i], kv.y - vi[i]);
         }
       }
@@ -433,7 +464,7 @@ __global__ void __launch_bounds__(NTHR, 1)
         }
 #pragma unroll 4
         for (int i = 0; i < 32; ++i) {
-          const float2 kv = k_entry<float>(T, p.K, r, c0 + i);
+          const float2 kv = s_in ? ld_cg(Sa + (int64_t)r * TB + c0 + i) : k_entry<float>(T, p.K, r, c0 + i);
           vr[i] = kv.x - vr[i];
           vi[i] = kv.y - vi[i];
         }

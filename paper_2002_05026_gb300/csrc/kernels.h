@@ -51,6 +51,8 @@ struct SweepLaunch {
   const int64_t* bwd_slot_ptr;     // device [NT]
   const int32_t* lev_blocks;       // device, blocks grouped by level
   const int64_t* lev_ptr;          // host [nlevels+1]
+  const int32_t* lev_tiles;        // device, tile indices of the blocks of each level
+  const int64_t* lev_tile_ptr;     // host [nlevels+1]
   const int32_t* tstart;           // device [N+1]
   const int64_t* tcolptr;          // device [NT+1]
 };

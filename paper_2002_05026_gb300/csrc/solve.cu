@@ -18,6 +18,7 @@ namespace d3m {
 
 namespace {
 constexpr int GT = 256;   // threads of gather / block kernels
+constexpr size_t SWEEP_SMEM_LIMIT = 220 * 1024;
 constexpr int HR = 64;    // rows of one staged half-tile
 
 template <typename R>
@@ -56,9 +57,33 @@ __global__ void permute_out_kernel(const typename CT<R>::C* __restrict__ W, int6
   }
 }
 
+// ------------------------------------------------------------------ async staging
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void cp_async_elem(float2* dst, const float2* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_elem(double2* dst, const double2* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void cp_wait_one() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
+// Stage rows [r0, r0 + 64) of a b x b row-major tile into a padded [64][b+1] buffer (async).
+template <typename C>
+__device__ __forceinline__ void stage_async(C* sL, const C* tile, int b, int r0) {
+  const int ldl = b + 1;
+  const C* src = tile + (int64_t)r0 * b;
+  for (int i = threadIdx.x; i < HR * b; i += GT) {
+    const int r = i / b, c = i - r * b;
+    cp_async_elem(sL + r * ldl + c, src + i);
+  }
+}
+
 // ------------------------------------------------------------------ gather (off-block tiles)
 // grid.x = items of the level * (b / 64) halves.  FWD: P[slot][r][j] (rows of this half) =
 // sum_k L[r][k] Y[src*b + k][j].  BWD: P[slot*nh + h][c][j] = sum_{r in half h} L[r][c] W[src*b + r][j].
+// Partials are stored [row][nrhs].
 template <typename R, bool FWD>
 __global__ void __launch_bounds__(GT) gather_kernel(const SolveItem* __restrict__ items,
                                                     const typename CT<R>::C* __restrict__ L,
@@ -70,25 +95,18 @@ __global__ void __launch_bounds__(GT) gather_kernel(const SolveItem* __restrict_
   const int nh = b / HR;
   const int ldl = b + 1;
   C* sL = reinterpret_cast<C*>(smem_raw);      // [64][b+1]
-  C* sY = sL + HR * ldl;                       // [rows][nrhs]
+  C* sY = sL + HR * ldl;                       // [nrhs][rows]
   const SolveItem it = items[blockIdx.x / nh];
   const int h = blockIdx.x % nh;
-  const C* Lt = L + (int64_t)it.tile * b * b + (int64_t)h * HR * b;
-  for (int i = threadIdx.x; i < HR * b; i += GT) {
-    const int r = i / b, c = i - r * b;
-    sL[r * ldl + c] = Lt[i];
+  stage_async(sL, L + (int64_t)it.tile * b * b, b, h * HR);
+  cp_commit();
+  const int rows = FWD ? b : HR;
+  const int64_t y0 = (int64_t)it.src * b + (FWD ? 0 : h * HR);
+  for (int i = threadIdx.x; i < rows * nrhs; i += GT) {
+    const int k = i % rows, j = i / rows;
+    sY[j * rows + k] = Y[j * npad + y0 + k];
   }
-  if (FWD) {
-    for (int i = threadIdx.x; i < b * nrhs; i += GT) {
-      const int k = i % b, j = i / b;
-      sY[k * nrhs + j] = Y[j * npad + (int64_t)it.src * b + k];
-    }
-  } else {
-    for (int i = threadIdx.x; i < HR * nrhs; i += GT) {
-      const int k = i % HR, j = i / HR;
-      sY[k * nrhs + j] = Y[j * npad + (int64_t)it.src * b + h * HR + k];
-    }
-  }
+  cp_wait_all();
   __syncthreads();
   if (FWD) {
     // thread: row r of this half, rhs j = g, g + G, ...
@@ -97,7 +115,8 @@ __global__ void __launch_bounds__(GT) gather_kernel(const SolveItem* __restrict_
     C* out = P + (int64_t)it.slot * nh * b * nrhs;   // sub-slot 0 of the item
     for (int j = g; j < nrhs; j += G) {
       C acc = czero<R>();
-      for (int k = 0; k < b; ++k) acc = cfma(sL[r * ldl + k], sY[k * nrhs + j], acc);
+#pragma unroll 8
+      for (int k = 0; k < b; ++k) acc = cfma(sL[r * ldl + k], sY[j * b + k], acc);
       out[(int64_t)(h * HR + r) * nrhs + j] = acc;
     }
   } else {
@@ -106,7 +125,8 @@ __global__ void __launch_bounds__(GT) gather_kernel(const SolveItem* __restrict_
     C* out = P + ((int64_t)it.slot * nh + h) * b * nrhs;
     for (int j = g; j < nrhs; j += G) {
       C acc = czero<R>();
-      for (int r = 0; r < HR; ++r) acc = cfma(sL[r * ldl + c], sY[r * nrhs + j], acc);
+#pragma unroll 8
+      for (int r = 0; r < HR; ++r) acc = cfma(sL[r * ldl + c], sY[j * HR + r], acc);
       out[(int64_t)c * nrhs + j] = acc;
     }
   }
@@ -122,82 +142,141 @@ struct BlockSweep {
   int b, nrhs, rc;           // rhs handled per block (grid.y = ceil(nrhs / rc))
 };
 
-// Stage a 64-row chunk of a b x b tile into shared memory.
+constexpr int MAXJOBS = 512;      // tile jobs of one block chain (nt (nt+1)/2 * b/64)
+
+// Y(row) -= sum of the row's partials (fixed slot order) for every tile row of one level;
+// one thread per (tile, row, rhs), rhs fastest (coalesced partial reads).
+template <typename R>
+__global__ void __launch_bounds__(GT) reduce_kernel(const int32_t* __restrict__ tiles, int ntl,
+                                                    const int64_t* __restrict__ slot_ptr,
+                                                    const typename CT<R>::C* __restrict__ P,
+                                                    typename CT<R>::C* __restrict__ Y, int64_t npad, int b,
+                                                    int nrhs, int nsub) {
+  using C = typename CT<R>::C;
+  const int64_t idx = blockIdx.x * (int64_t)GT + threadIdx.x;
+  const int j = (int)(idx % nrhs);
+  const int64_t rest = idx / nrhs;
+  const int row = (int)(rest % b);
+  const int64_t tl = rest / b;
+  if (tl >= ntl) return;
+  const int I = tiles[tl];
+  const int64_t sp = slot_ptr[I];
+  const int64_t first = sp & 0xffffffffLL, cnt = (sp >> 32) * nsub;
+  if (cnt == 0) return;
+  const int nh = b / HR;
+  const C* pp = P + first * nh * (int64_t)b * nrhs + (int64_t)row * nrhs + j;
+  const int64_t stride = (int64_t)b * nrhs * (nsub == 1 ? nh : 1);
+  C a0 = czero<R>(), a1 = czero<R>(), a2 = czero<R>(), a3 = czero<R>();
+  int64_t q = 0;
+  for (; q + 4 <= cnt; q += 4) {
+    a0 = cadd(a0, pp[(q + 0) * stride]);
+    a1 = cadd(a1, pp[(q + 1) * stride]);
+    a2 = cadd(a2, pp[(q + 2) * stride]);
+    a3 = cadd(a3, pp[(q + 3) * stride]);
+  }
+  for (; q < cnt; ++q) a0 = cadd(a0, pp[q * stride]);
+  C* y = Y + (int64_t)j * npad + (int64_t)I * b + row;
+  *y = csub(*y, cadd(cadd(a0, a1), cadd(a2, a3)));
+}
+
+// z = D^{-1} y over the whole padded vector (between the forward and backward sweeps)
+template <typename R>
+__global__ void diag_scale_kernel(typename CT<R>::C* __restrict__ Y, const typename CT<R>::C* __restrict__ D,
+                                  int64_t npad, int nrhs) {
+  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (g >= npad) return;
+  const typename CT<R>::C d = D[g];
+  for (int j = 0; j < nrhs; ++j) Y[(int64_t)j * npad + g] = cdiv(Y[(int64_t)j * npad + g], d);
+}
+
+// load one block's rows of Y into sv[row][rc]
 template <typename C>
-__device__ __forceinline__ void stage_rows(C* sL, const C* src, int b, int r0) {
-  const int ldl = b + 1;
-  for (int i = threadIdx.x; i < HR * b; i += GT) {
-    const int r = i / b, c = i - r * b;
-    sL[r * ldl + c] = src[(int64_t)(r0 + r) * b + c];
+__device__ __forceinline__ void load_rows(const C* __restrict__ Y, int64_t npad, int64_t r0, int rows, int j0,
+                                          int rc, int ldv, C* sv) {
+  for (int i = threadIdx.x; i < rows * rc; i += GT) {
+    const int row = i % rows, j = i / rows;
+    sv[row * ldv + j] = Y[(int64_t)(j0 + j) * npad + r0 + row];
   }
 }
 
-// forward: r = b_k - sum partials;  y_t = Linv_tt r_t;  r_t' -= L_t't y_t  (Y keeps y: later
-// levels gather L_IJ y_J; the diagonal step z = D^{-1} y is applied by the backward kernel)
+// forward (partials already subtracted from Y):  y_t = Linv_tt r_t;  r_t' -= L_t't y_t  (Y keeps y: later
+// levels gather L_IJ y_J; the diagonal step z = D^{-1} y is applied by the backward kernel).
+// Tiles are staged with cp.async into two buffers: the next job's tile loads while the
+// current one is used.
 template <typename R>
 __global__ void __launch_bounds__(GT) block_fwd_kernel(BlockSweep s, const typename CT<R>::C* __restrict__ L,
                                                        const typename CT<R>::C* __restrict__ Linv,
-                                                       typename CT<R>::C* __restrict__ Y,
-                                                       const typename CT<R>::C* __restrict__ P) {
+                                                       typename CT<R>::C* __restrict__ Y) {
   using C = typename CT<R>::C;
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ const C* s_job[MAXJOBS];
   const int b = s.b, ldl = b + 1, nh = b / HR;
   const int k = s.blocks[blockIdx.x];
   const int j0 = blockIdx.y * s.rc;
   const int rc = min(s.rc, s.nrhs - j0);
   const int t0 = s.tstart[k], nt = s.tstart[k + 1] - t0;
   const int rows = nt * b;
-  C* sL = reinterpret_cast<C*>(smem_raw);      // [64][b+1]
-  C* sv = sL + HR * ldl;                       // [rows][rc]  running r / y
+  C* sL0 = reinterpret_cast<C*>(smem_raw);     // [64][b+1] x 2
+  C* sL1 = sL0 + HR * ldl;
+  C* sv = sL1 + HR * ldl;                      // [rows][rc]  running r / y
   C* sy = sv + (int64_t)rows * s.rc;           // [b][rc]     y_t
-  (void)nh;
-  // 1. r = Y - sum of partials (fixed slot order)
-  for (int i = threadIdx.x; i < rows * rc; i += GT) {
-    const int row = i % rows, j = i / rows;
-    const int I = t0 + row / b;
-    C v = Y[(int64_t)(j0 + j) * s.npad + (int64_t)t0 * b + row];
-    const int64_t sp = s.slot_ptr[I];
-    const int64_t first = sp & 0xffffffffLL, cnt = sp >> 32;
-    for (int64_t q = 0; q < cnt; ++q) {
-      const C pv = P[((first + q) * (b / HR)) * (int64_t)b * s.nrhs + (int64_t)(row % b) * s.nrhs + j0 + j];
-      v = csub(v, pv);
+  // job list: for t: Linv_t halves, then L_{t', t} halves for t' > t
+  int njobs = 0;
+  if (threadIdx.x == 0) {
+    for (int t = 0; t < nt; ++t) {
+      const int J = t0 + t;
+      for (int h = 0; h < nh; ++h) s_job[njobs++] = Linv + (int64_t)J * b * b + (int64_t)h * HR * b;
+      for (int tp = t + 1; tp < nt; ++tp)
+        for (int h = 0; h < nh; ++h)
+          s_job[njobs++] = L + (s.tcolptr[J] + (tp - t)) * (int64_t)b * b + (int64_t)h * HR * b;
     }
-    sv[row * s.rc + j] = v;
   }
+  njobs = 0;
+  for (int t = 0; t < nt; ++t) njobs += nh * (nt - t);
   __syncthreads();
+  stage_async(sL0, s_job[0], b, 0);
+  cp_commit();
+  load_rows(Y, s.npad, (int64_t)t0 * b, rows, j0, rc, s.rc, sv);
+  int job = 0;
   for (int t = 0; t < nt; ++t) {
-    const int J = t0 + t;
-    // y_t = Linv_J r_t
-    for (int h = 0; h < b / HR; ++h) {
-      stage_rows(sL, Linv + (int64_t)J * b * b, b, h * HR);
-      __syncthreads();
-      for (int i = threadIdx.x; i < HR * rc; i += GT) {
-        const int r = i % HR, j = i / HR;
-        C acc = czero<R>();
-        for (int c = 0; c < b; ++c) acc = cfma(sL[r * ldl + c], sv[(t * b + c) * s.rc + j], acc);
-        sy[(h * HR + r) * s.rc + j] = acc;
+    for (int q = 0; q < nh * (nt - t); ++q, ++job) {
+      C* cur = (job & 1) ? sL1 : sL0;
+      if (job + 1 < njobs) {
+        stage_async((job & 1) ? sL0 : sL1, s_job[job + 1], b, 0);
+        cp_commit();
+        cp_wait_one();
+      } else {
+        cp_wait_all();
       }
       __syncthreads();
-    }
-    for (int i = threadIdx.x; i < b * rc; i += GT) {
-      const int r = i % b, j = i / b;
-      sv[(t * b + r) * s.rc + j] = sy[r * s.rc + j];
-    }
-    __syncthreads();
-    // r_t' -= L_{t', t} y_t  for t' > t (tile ids follow the diagonal tile in column J)
-    for (int tp = t + 1; tp < nt; ++tp) {
-      const C* Lt = L + (s.tcolptr[J] + (tp - t)) * (int64_t)b * b;
-      for (int h = 0; h < b / HR; ++h) {
-        stage_rows(sL, Lt, b, h * HR);
-        __syncthreads();
+      const int h = q % nh;
+      if (q < nh) {
+        // y_t rows [h*64, h*64+64) = Linv_t[rows] r_t
+        for (int i = threadIdx.x; i < HR * rc; i += GT) {
+          const int r = i % HR, j = i / HR;
+          C acc = czero<R>();
+#pragma unroll 8
+          for (int c = 0; c < b; ++c) acc = cfma(cur[r * ldl + c], sv[(t * b + c) * s.rc + j], acc);
+          sy[(h * HR + r) * s.rc + j] = acc;
+        }
+        if (q == nh - 1) {
+          __syncthreads();
+          for (int i = threadIdx.x; i < b * rc; i += GT) {
+            const int r = i % b, j = i / b;
+            sv[(t * b + r) * s.rc + j] = sy[r * s.rc + j];
+          }
+        }
+      } else {
+        const int tp = t + 1 + (q - nh) / nh;
         for (int i = threadIdx.x; i < HR * rc; i += GT) {
           const int r = i % HR, j = i / HR;
           C acc = sv[(tp * b + h * HR + r) * s.rc + j];
-          for (int c = 0; c < b; ++c) acc = cfms(sL[r * ldl + c], sy[c * s.rc + j], acc);
+#pragma unroll 8
+          for (int c = 0; c < b; ++c) acc = cfms(cur[r * ldl + c], sy[c * s.rc + j], acc);
           sv[(tp * b + h * HR + r) * s.rc + j] = acc;
         }
-        __syncthreads();
       }
+      __syncthreads();
     }
   }
   for (int i = threadIdx.x; i < rows * rc; i += GT) {
@@ -206,73 +285,83 @@ __global__ void __launch_bounds__(GT) block_fwd_kernel(BlockSweep s, const typen
   }
 }
 
-// backward: r = D^{-1} y_k - sum partials;  for t = nt-1..0: w_t = Linv_tt^T r_t; r_t' -= L_{t,t'}^T w_t (t' < t)
+// backward (Y holds D^{-1} y minus partials):  for t = nt-1..0: w_t = Linv_tt^T r_t;
+// r_t' -= L_{t,t'}^T w_t (t' < t).  Same double-buffered staging as the forward kernel.
 template <typename R>
 __global__ void __launch_bounds__(GT) block_bwd_kernel(BlockSweep s, const typename CT<R>::C* __restrict__ L,
                                                        const typename CT<R>::C* __restrict__ Linv,
-                                                       const typename CT<R>::C* __restrict__ D,
-                                                       typename CT<R>::C* __restrict__ Y,
-                                                       const typename CT<R>::C* __restrict__ P) {
+                                                       typename CT<R>::C* __restrict__ Y) {
   using C = typename CT<R>::C;
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ const C* s_job[MAXJOBS];
   const int b = s.b, ldl = b + 1, nh = b / HR;
   const int k = s.blocks[blockIdx.x];
   const int j0 = blockIdx.y * s.rc;
   const int rc = min(s.rc, s.nrhs - j0);
   const int t0 = s.tstart[k], nt = s.tstart[k + 1] - t0;
   const int rows = nt * b;
-  C* sL = reinterpret_cast<C*>(smem_raw);
-  C* sv = sL + HR * ldl;
+  C* sL0 = reinterpret_cast<C*>(smem_raw);
+  C* sL1 = sL0 + HR * ldl;
+  C* sv = sL1 + HR * ldl;
   C* sy = sv + (int64_t)rows * s.rc;
-  for (int i = threadIdx.x; i < rows * rc; i += GT) {
-    const int row = i % rows, j = i / rows;
-    const int J = t0 + row / b;
-    C v = cdiv(Y[(int64_t)(j0 + j) * s.npad + (int64_t)t0 * b + row], D[(int64_t)t0 * b + row]);
-    const int64_t sp = s.slot_ptr[J];
-    const int64_t first = sp & 0xffffffffLL, cnt = sp >> 32;
-    for (int64_t q = 0; q < cnt; ++q)
-      for (int h = 0; h < nh; ++h) {
-        const C pv = P[((first + q) * nh + h) * (int64_t)b * s.nrhs + (int64_t)(row % b) * s.nrhs + j0 + j];
-        v = csub(v, pv);
-      }
-    sv[row * s.rc + j] = v;
+  int njobs = 0;
+  if (threadIdx.x == 0) {
+    for (int t = nt - 1; t >= 0; --t) {
+      const int J = t0 + t;
+      for (int h = 0; h < nh; ++h) s_job[njobs++] = Linv + (int64_t)J * b * b + (int64_t)h * HR * b;
+      for (int tp = 0; tp < t; ++tp)
+        for (int h = 0; h < nh; ++h)
+          s_job[njobs++] = L + (s.tcolptr[t0 + tp] + (t - tp)) * (int64_t)b * b + (int64_t)h * HR * b;
+    }
   }
+  njobs = 0;
+  for (int t = 0; t < nt; ++t) njobs += nh * (t + 1);
   __syncthreads();
+  stage_async(sL0, s_job[0], b, 0);
+  cp_commit();
+  load_rows(Y, s.npad, (int64_t)t0 * b, rows, j0, rc, s.rc, sv);
+  int job = 0;
   for (int t = nt - 1; t >= 0; --t) {
-    const int J = t0 + t;
-    // w_t = Linv_J^T r_t  : out[c] = sum_r Linv[r][c] r[r]
     for (int i = threadIdx.x; i < b * rc; i += GT) sy[i] = czero<R>();
-    __syncthreads();
-    for (int h = 0; h < nh; ++h) {
-      stage_rows(sL, Linv + (int64_t)J * b * b, b, h * HR);
-      __syncthreads();
-      for (int i = threadIdx.x; i < b * rc; i += GT) {
-        const int c = i % b, j = i / b;
-        C acc = sy[c * s.rc + j];
-        for (int r = 0; r < HR; ++r) acc = cfma(sL[r * ldl + c], sv[(t * b + h * HR + r) * s.rc + j], acc);
-        sy[c * s.rc + j] = acc;
+    for (int q = 0; q < nh * (t + 1); ++q, ++job) {
+      C* cur = (job & 1) ? sL1 : sL0;
+      if (job + 1 < njobs) {
+        stage_async((job & 1) ? sL0 : sL1, s_job[job + 1], b, 0);
+        cp_commit();
+        cp_wait_one();
+      } else {
+        cp_wait_all();
       }
       __syncthreads();
-    }
-    for (int i = threadIdx.x; i < b * rc; i += GT) {
-      const int r = i % b, j = i / b;
-      sv[(t * b + r) * s.rc + j] = sy[r * s.rc + j];
-    }
-    __syncthreads();
-    // r_t' -= L_{t, t'}^T w_t for t' < t; tile (t0+t, t0+t') is entry (t - t') of column t0+t'
-    for (int tp = 0; tp < t; ++tp) {
-      const C* Lt = L + (s.tcolptr[t0 + tp] + (t - tp)) * (int64_t)b * b;
-      for (int h = 0; h < nh; ++h) {
-        stage_rows(sL, Lt, b, h * HR);
-        __syncthreads();
+      const int h = q % nh;
+      if (q < nh) {
+        // w_t += Linv_t[rows of half h]^T r_t[rows of half h]
+        for (int i = threadIdx.x; i < b * rc; i += GT) {
+          const int c = i % b, j = i / b;
+          C acc = sy[c * s.rc + j];
+#pragma unroll 8
+          for (int r = 0; r < HR; ++r) acc = cfma(cur[r * ldl + c], sv[(t * b + h * HR + r) * s.rc + j], acc);
+          sy[c * s.rc + j] = acc;
+        }
+        if (q == nh - 1) {
+          __syncthreads();
+          for (int i = threadIdx.x; i < b * rc; i += GT) {
+            const int r = i % b, j = i / b;
+            sv[(t * b + r) * s.rc + j] = sy[r * s.rc + j];
+          }
+        }
+      } else {
+        // tile (t0+t, t0+tp): r_tp[c] -= sum_{r in half h} L[r][c] w_t[r]
+        const int tp = (q - nh) / nh;
         for (int i = threadIdx.x; i < b * rc; i += GT) {
           const int c = i % b, j = i / b;
           C acc = sv[(tp * b + c) * s.rc + j];
-          for (int r = 0; r < HR; ++r) acc = cfms(sL[r * ldl + c], sy[(h * HR + r) * s.rc + j], acc);
+#pragma unroll 8
+          for (int r = 0; r < HR; ++r) acc = cfms(cur[r * ldl + c], sy[(h * HR + r) * s.rc + j], acc);
           sv[(tp * b + c) * s.rc + j] = acc;
         }
-        __syncthreads();
       }
+      __syncthreads();
     }
   }
   for (int i = threadIdx.x; i < rows * rc; i += GT) {
@@ -446,8 +535,14 @@ static int sweep_impl(const SweepLaunch& a, cudaStream_t st) {
   C* P = (C*)a.P;
   permute_in_kernel<R><<<(unsigned)gblocks, nthreads, 0, st>>>(a.src, a.n, Y, a.npad, a.pad2orig, a.nrhs);
   const size_t gsm = sizeof(C) * ((size_t)HR * (b + 1) + (size_t)b * a.nrhs);
-  const int rc = a.nrhs < 8 ? a.nrhs : 8;
-  const size_t bsm = sizeof(C) * ((size_t)HR * (b + 1) + (size_t)a.max_rows * rc + (size_t)b * rc);
+  // rhs per block kernel: at most 8, fewer if the running vector would not fit in shared memory
+  int rc = a.nrhs < 8 ? a.nrhs : 8;
+  auto block_smem = [&](int r) {
+    return sizeof(C) * (2 * (size_t)HR * (b + 1) + (size_t)a.max_rows * r + (size_t)b * r);
+  };
+  while (rc > 1 && block_smem(rc) > SWEEP_SMEM_LIMIT) rc = (rc + 1) / 2;
+  const size_t bsm = block_smem(rc);
+  if (bsm > SWEEP_SMEM_LIMIT) return (int)cudaErrorInvalidConfiguration;
   cudaFuncSetAttribute(gather_kernel<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm);
   cudaFuncSetAttribute(gather_kernel<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm);
   cudaFuncSetAttribute(block_fwd_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bsm);
@@ -463,21 +558,32 @@ static int sweep_impl(const SweepLaunch& a, cudaStream_t st) {
   const unsigned ny = (unsigned)((a.nrhs + rc - 1) / rc);
   for (int lv = 0; lv < a.nlevels; ++lv) {
     const int64_t i0 = a.fwd_item_ptr[lv], i1 = a.fwd_item_ptr[lv + 1];
-    if (i1 > i0)
+    const int64_t ntl = a.lev_tile_ptr[lv + 1] - a.lev_tile_ptr[lv];
+    if (i1 > i0) {
       gather_kernel<R, true><<<(unsigned)((i1 - i0) * nh), GT, gsm, st>>>(a.fwd_items + i0, L, Y, P, a.npad, b, a.nrhs);
+      const int64_t nthr = ntl * b * a.nrhs;
+      reduce_kernel<R><<<(unsigned)((nthr + GT - 1) / GT), GT, 0, st>>>(a.lev_tiles + a.lev_tile_ptr[lv], (int)ntl,
+                                                                     a.fwd_slot_ptr, P, Y, a.npad, b, a.nrhs, 1);
+    }
     bs.blocks = a.lev_blocks + a.lev_ptr[lv];
     bs.slot_ptr = a.fwd_slot_ptr;
     const unsigned nb = (unsigned)(a.lev_ptr[lv + 1] - a.lev_ptr[lv]);
-    block_fwd_kernel<R><<<dim3(nb, ny), GT, bsm, st>>>(bs, L, Linv, Y, P);
+    block_fwd_kernel<R><<<dim3(nb, ny), GT, bsm, st>>>(bs, L, Linv, Y);
   }
+  diag_scale_kernel<R><<<(unsigned)gblocks, nthreads, 0, st>>>(Y, D, a.npad, a.nrhs);
   for (int lv = a.nlevels - 1; lv >= 0; --lv) {
     const int64_t i0 = a.bwd_item_ptr[lv], i1 = a.bwd_item_ptr[lv + 1];
-    if (i1 > i0)
+    const int64_t ntl = a.lev_tile_ptr[lv + 1] - a.lev_tile_ptr[lv];
+    if (i1 > i0) {
       gather_kernel<R, false><<<(unsigned)((i1 - i0) * nh), GT, gsm, st>>>(a.bwd_items + i0, L, Y, P, a.npad, b, a.nrhs);
+      const int64_t nthr = ntl * b * a.nrhs;
+      reduce_kernel<R><<<(unsigned)((nthr + GT - 1) / GT), GT, 0, st>>>(a.lev_tiles + a.lev_tile_ptr[lv], (int)ntl,
+                                                                     a.bwd_slot_ptr, P, Y, a.npad, b, a.nrhs, nh);
+    }
     bs.blocks = a.lev_blocks + a.lev_ptr[lv];
     bs.slot_ptr = a.bwd_slot_ptr;
     const unsigned nb = (unsigned)(a.lev_ptr[lv + 1] - a.lev_ptr[lv]);
-    block_bwd_kernel<R><<<dim3(nb, ny), GT, bsm, st>>>(bs, L, Linv, D, Y, P);
+    block_bwd_kernel<R><<<dim3(nb, ny), GT, bsm, st>>>(bs, L, Linv, Y);
   }
   permute_out_kernel<R><<<(unsigned)gblocks, nthreads, 0, st>>>(Y, a.npad, a.dst, a.n, a.pad2orig, a.nrhs, a.accumulate);
   return (int)cudaGetLastError();

@@ -11,6 +11,7 @@
 
 #include <algorithm>
 #include <cstdio>
+#include <cstring>
 #include <functional>
 #include <numeric>
 
@@ -201,25 +202,30 @@ int analyze(const d3m_pattern* pat, const int32_t* perm_in, int b, bool build_ta
     for (int64_t t = s.tcolptr[J]; t < s.tcolptr[J + 1]; ++t) {
       int I = s.trow[t], p = s.tblk[I];
       int64_t nk = J - s.tstart[q];
+      int64_t ns = (J > s.tstart[q]) ? 1 : 0;
       const auto& rp = s.rowlist[p];
       const auto& rq = s.rowlist[q];
-      size_t a = 0, c = 0;
-      while (a < rp.size() && c < rq.size()) {
-        if (rp[a] < rq[c]) ++a;
-        else if (rp[a] > rq[c]) ++c;
-        else { nk += s.ntile[rp[a]]; ++a; ++c; }
+      if (p == q) {
+        for (int k : rq) { nk += s.ntile[k]; ++ns; }
+      } else {
+        size_t a = 0, c = 0;
+        while (a < rp.size() && c < rq.size()) {
+          if (rp[a] < rq[c]) ++a;
+          else if (rp[a] > rq[c]) ++c;
+          else { nk += s.ntile[rp[a]]; ++ns; ++a; ++c; }
+        }
       }
       s.n_tile_updates += nk;
-      s.n_edges += (I == J) ? nk : 2 * nk + 1;
+      // segment sources, the chain between segments, and the diagonal tile for a TRSM
+      s.n_edges += ((I == J) ? nk : 2 * nk) + (ns > 1 ? ns - 1 : 0) + (I == J ? 0 : 1);
     }
   }
   if (!build_tasks) return D3M_OK;
 
   // ---------------------------------------------------------------- tasks + K-lists
-  s.tasks.resize(ntiles);
-  s.ndeps.assign(ntiles, 0);
+  // pass 1: K-lists (grouped by source block column) and segment counts per tile
+  s.ntiles = ntiles;
   std::vector<int64_t> kl_ptr(ntiles + 1, 0);
-  // pass 1: K-list lengths
   auto common_blocks = [&](int p, int q, std::vector<int32_t>& out) {
     out.clear();
     const auto& rp = s.rowlist[p];
@@ -228,6 +234,7 @@ int analyze(const d3m_pattern* pat, const int32_t* perm_in, int b, bool build_ta
     std::set_intersection(rp.begin(), rp.end(), rq.begin(), rq.end(), std::back_inserter(out));
   };
   std::vector<int32_t> ks;
+  std::vector<int32_t> nseg(ntiles, 0);
   for (int J = 0; J < s.NT; ++J) {
     int q = s.tblk[J];
     for (int64_t t = s.tcolptr[J]; t < s.tcolptr[J + 1]; ++t) {
@@ -236,76 +243,108 @@ int analyze(const d3m_pattern* pat, const int32_t* perm_in, int b, bool build_ta
       int64_t nk = J - s.tstart[q];
       for (int k : ks) nk += s.ntile[k];
       kl_ptr[t + 1] = nk;
+      nseg[t] = (int32_t)ks.size() + (J > s.tstart[q] ? 1 : 0);
     }
   }
   for (int64_t t = 0; t < ntiles; ++t) kl_ptr[t + 1] += kl_ptr[t];
   s.klist.resize(kl_ptr[ntiles]);
-  // pass 2: fill tasks, K-lists, dependency counts and successor lists
-  std::vector<int64_t> scount(ntiles + 1, 0);
+  int64_t nupd = 0;
+  for (int64_t t = 0; t < ntiles; ++t) nupd += std::max(0, nseg[t] - 1);
+  const int64_t ntask = ntiles + nupd;
+  if (ntask >= (int64_t)1 << 31) return fail(err, "too many tasks for 32-bit task ids");
+  s.tasks.resize(ntask);
+  s.ndeps.assign(ntask, 0);
+  s.n_acc = 0;
+  // task ids: final task of tile t = t; update tasks numbered after the tiles, by tile
+  std::vector<int64_t> upd_first(ntiles, -1);
+  {
+    int64_t nextu = ntiles;
+    for (int64_t t = 0; t < ntiles; ++t)
+      if (nseg[t] > 1) { upd_first[t] = nextu; nextu += nseg[t] - 1; }
+  }
+  // dependencies per task id, then successor lists (CSR)
+  std::vector<std::vector<int32_t>> tdeps(ntask);
   for (int J = 0; J < s.NT; ++J) {
     int q = s.tblk[J];
     for (int64_t t = s.tcolptr[J]; t < s.tcolptr[J + 1]; ++t) {
       int I = s.trow[t], p = s.tblk[I];
       common_blocks(p, q, ks);
       int64_t w = kl_ptr[t];
+      // segment boundaries (offsets into this tile's K-list)
+      std::vector<int64_t> sb;
+      sb.push_back(w);
       auto push = [&](int K) {
         int64_t a = s.tile_of(I, K), bb = s.tile_of(J, K);
         s.klist[w++] = KEntry{(int32_t)a, (int32_t)bb, K, 0};
       };
-      for (int k : ks)
+      for (int k : ks) {
         for (int K = s.tstart[k]; K < s.tstart[k + 1]; ++K) push(K);
-      for (int K = s.tstart[q]; K < J; ++K) push(K);
-      TileTask& T = s.tasks[t];
-      T.tile = (int32_t)t;
-      T.diag = s.diag_tile[J];
-      T.col = J;
-      T.nk = (int32_t)(kl_ptr[t + 1] - kl_ptr[t]);
-      T.kl_off = kl_ptr[t];
-      T.is_diag = (I == J);
-      T.same_block = (p == q);
-      T.r0 = (I - s.tstart[p]) * b;
-      T.c0 = (J - s.tstart[q]) * b;
-      T.rv = std::min(b, s.m[p] - T.r0);
-      T.cv = std::min(b, s.m[q] - T.c0);
+        sb.push_back(w);
+      }
+      if (J > s.tstart[q]) {
+        for (int K = s.tstart[q]; K < J; ++K) push(K);
+        sb.push_back(w);
+      }
+      const int ns = (int)sb.size() - 1;           // == nseg[t]
+      TileTask base;
+      std::memset(&base, 0, sizeof base);
+      base.tile = (int32_t)t;
+      base.diag = s.diag_tile[J];
+      base.col = J;
+      base.r0 = (I - s.tstart[p]) * b;
+      base.c0 = (J - s.tstart[q]) * b;
+      base.rv = std::min(b, s.m[p] - base.r0);
+      base.cv = std::min(b, s.m[q] - base.c0);
       int fp = s.perm[p], fq = s.perm[q];
       int scol = fq, srow = fp;
-      T.k_tr = 0;
-      if (fp < fq) { scol = fp; srow = fq; T.k_tr = 1; }
-      T.k_off = -1;
-      T.k_ld = s.m_orig[srow];
+      base.k_tr = 0;
+      if (fp < fq) { scol = fp; srow = fq; base.k_tr = 1; }
+      base.k_off = -1;
+      base.k_ld = s.m_orig[srow];
       const int32_t* first = s.rowidx.data() + s.colptr[scol];
       const int32_t* last = s.rowidx.data() + s.colptr[scol + 1];
       const int32_t* it = std::lower_bound(first, last, srow);
-      if (it != last && *it == srow) T.k_off = s.kblk_off[s.colptr[scol] + (it - first)];
-      // dependencies
-      int nd = (I == J) ? T.nk : 2 * T.nk + 1;
-      s.ndeps[t] = nd;
+      if (it != last && *it == srow) base.k_off = s.kblk_off[s.colptr[scol] + (it - first)];
+      base.flags = (I == J ? TF_DIAG : 0) | (p == q ? TF_SAME_BLOCK : 0);
+      base.sidx = ns > 1 ? (int32_t)(s.n_acc++) : -1;
+      auto seg_deps = [&](int sg, std::vector<int32_t>& d) {
+        for (int64_t e = sb[sg]; e < sb[sg + 1]; ++e) {
+          d.push_back(s.klist[e].a_tile);
+          if (I != J) d.push_back(s.klist[e].b_tile);
+        }
+      };
+      for (int sg = 0; sg < std::max(ns, 1); ++sg) {
+        const bool final_task = (sg == std::max(ns, 1) - 1);
+        const int64_t id = final_task ? t : upd_first[t] + sg;
+        TileTask T = base;
+        T.kl_off = ns > 0 ? sb[sg] : kl_ptr[t];
+        T.nk = ns > 0 ? (int32_t)(sb[sg + 1] - sb[sg]) : 0;
+        if (!final_task) T.flags |= TF_UPDATE;
+        if (sg > 0) T.flags |= TF_S_IN;
+        s.tasks[id] = T;
+        auto& d = tdeps[id];
+        if (ns > 0) seg_deps(sg, d);
+        if (sg > 0) d.push_back((int32_t)(upd_first[t] + sg - 1));
+        if (final_task && I != J) d.push_back(s.diag_tile[J]);
+        s.ndeps[id] = (int32_t)d.size();
+      }
     }
   }
   // successor lists
-  for (int64_t t = 0; t < ntiles; ++t) {
-    const TileTask& T = s.tasks[t];
-    for (int64_t e = T.kl_off; e < T.kl_off + T.nk; ++e) {
-      scount[s.klist[e].a_tile + 1]++;
-      if (!T.is_diag) scount[s.klist[e].b_tile + 1]++;
-    }
-    if (!T.is_diag) scount[T.diag + 1]++;
-  }
-  for (int64_t t = 0; t < ntiles; ++t) scount[t + 1] += scount[t];
+  std::vector<int64_t> scount(ntask + 1, 0);
+  for (int64_t id = 0; id < ntask; ++id)
+    for (int32_t d : tdeps[id]) scount[d + 1]++;
+  for (int64_t id = 0; id < ntask; ++id) scount[id + 1] += scount[id];
   s.succ_ptr = scount;
-  s.succ.resize(scount[ntiles]);
+  s.succ.resize(scount[ntask]);
   std::vector<int64_t> wpos(scount.begin(), scount.end() - 1);
-  for (int64_t t = 0; t < ntiles; ++t) {
-    const TileTask& T = s.tasks[t];
-    for (int64_t e = T.kl_off; e < T.kl_off + T.nk; ++e) {
-      s.succ[wpos[s.klist[e].a_tile]++] = (int32_t)t;
-      if (!T.is_diag) s.succ[wpos[s.klist[e].b_tile]++] = (int32_t)t;
-    }
-    if (!T.is_diag) s.succ[wpos[T.diag]++] = (int32_t)t;
-  }
+  for (int64_t id = 0; id < ntask; ++id)
+    for (int32_t d : tdeps[id]) s.succ[wpos[d]++] = (int32_t)id;
+  std::vector<std::vector<int32_t>>().swap(tdeps);
+  s.n_edges = (int64_t)s.succ.size();
   s.init_ready.clear();
-  for (int64_t t = 0; t < ntiles; ++t)
-    if (s.ndeps[t] == 0) s.init_ready.push_back((int32_t)t);
+  for (int64_t id = 0; id < ntask; ++id)
+    if (s.ndeps[id] == 0) s.init_ready.push_back((int32_t)id);
 
   // ---------------------------------------------------------------- solve level sets
   s.fwd_item_ptr.assign(s.nlevels + 1, 0);

@@ -9,22 +9,34 @@
 
 namespace d3m {
 
-// One task of the factorization DAG = one lower tile (I, J) of L (owner computes; paper
-// Sec. II: "each non-zero block of the dual matrix is represented by a task responsible for
-// possible dense update, dense triangular solver, and dense factorization").
+// Task flags.
+enum : int32_t {
+  TF_DIAG = 1,        // I == J
+  TF_SAME_BLOCK = 2,  // p == q: padding unknowns get a unit diagonal
+  TF_UPDATE = 4,      // partial-update task (else: the tile's final task)
+  TF_S_IN = 8,        // start from the tile's accumulator S (else from K_IJ)
+};
+
+// One task of the factorization DAG.  The paper's task model (Sec. II: every nonzero block is
+// a task doing a dense update, a dense triangular solve and a dense factorization) at tile
+// granularity: the updates of lower tile (I, J), S_IJ = K_IJ - sum_K L_IK D_K L_JK^T, are cut
+// into segments, one per source block column; every segment but the last is an UPDATE task
+// (S <- S_in - sum over the segment, kept in the tile's accumulator; segments chained in
+// increasing K), and the FINAL task (task id == tile id) applies the last segment and then
+// factors the diagonal tile (I == J) or applies the triangular solve (I != J).
 struct TileTask {
-  int32_t tile;        // own tile id (== task id)
+  int32_t tile;        // tile id (== id of the tile's final task)
   int32_t diag;        // tile id of (J, J)
   int32_t col;         // global tile column J
-  int32_t nk;          // length of the K-list (tile updates into this tile)
-  int64_t kl_off;      // offset of the K-list in the klist array
+  int32_t nk;          // tile updates of this task's segment
+  int64_t kl_off;      // offset of the segment in the klist array
   int64_t k_off;       // element (c128) offset of the stored K block, -1 for a fill block
   int32_t k_ld;        // leading dimension of the stored K block
   int32_t k_tr;        // 1: entry (r, c) of block (p, q) is stored(c, r) (use the transpose)
   int32_t r0, c0;      // first row / column of the tile inside block (p, q)
   int32_t rv, cv;      // valid rows / columns (the rest is padding up to the tile edge)
-  int32_t is_diag;     // I == J
-  int32_t same_block;  // p == q: padding unknowns get a unit diagonal
+  int32_t flags;       // TF_* bits
+  int32_t sidx;        // accumulator slot of the tile, -1 if it has a single segment
 };
 static_assert(sizeof(TileTask) == 64, "TileTask layout");
 
@@ -67,7 +79,9 @@ struct Symbolic {
   std::vector<int64_t> tcolptr;              // [NT+1]
   std::vector<int32_t> trow;                 // tile row of each tile
   std::vector<int32_t> tblk;                 // block of each tile row/column index
-  std::vector<TileTask> tasks;
+  std::vector<TileTask> tasks;             // [ntiles final tasks, then update tasks]
+  int64_t ntiles = 0;
+  int64_t n_acc = 0;                         // tiles with an accumulator slot
   std::vector<KEntry> klist;
   std::vector<int32_t> ndeps;
   std::vector<int64_t> succ_ptr;

@@ -28,6 +28,8 @@ def _as_colmajor(B):
     import torch
     if B.dtype != torch.complex128:
         raise TypeError("right-hand sides must be complex128")
+    # lazy conjugate / negative views would hand the raw (unconjugated) data to the library
+    B = B.resolve_conj().resolve_neg()
     if B.dim() == 1:
         return B.contiguous().reshape(1, -1), 1, True
     return B.T.contiguous(), B.shape[1], False
@@ -66,6 +68,8 @@ class D3M:
     # -------------------------------------------------------------- C-ABI calls
     def factor(self, K):
         """K: complex128 lower blocks (torch tensor on the device, or pinned/host)."""
+        if hasattr(K, "resolve_conj"):
+            K = K.resolve_conj().resolve_neg().contiguous()
         ptr = K.data_ptr() if hasattr(K, "data_ptr") else K.ctypes.data
         return check(self._lib.d3m_factor(self.h, c_void_p(ptr), c_void_p(_stream_ptr(self.stream))), self.h)
 

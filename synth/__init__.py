@@ -323,6 +323,7 @@ WORKLOADS = {
     "grid2x2_m64": dict(nx=2, ny=2, nz=1, m=64, k2=1.0, tau=0.1, nrhs=1, seed=20260101),
     "grid8x8_m512": dict(nx=8, ny=8, nz=1, m=512, k2=2.0, tau=0.05, nrhs=8, seed=20260102),
     "grid6x6x6_m512": dict(nx=6, ny=6, nz=6, m=512, k2=4.0, tau=0.02, nrhs=32, seed=20260103),
+    "grid4x4_m512": dict(nx=4, ny=4, nz=1, m=512, k2=2.0, tau=0.05, nrhs=8, seed=20260106),
     "adjoint8x8_m256": dict(nx=8, ny=8, nz=1, m=256, k2=2.0, tau=0.05, nrhs=1, seed=20260104),
 }
 
