@@ -92,6 +92,9 @@ typedef struct {
 /* Test hook: upload the task graph with one extra unmet dependency on the last task, so the
  * device queue starves and every waiting block hits the bounded wait (-> D3M_ERR_TIMEOUT). */
 #define D3M_DEBUG_STALL_LAST_TASK 1
+/* Tracing: every factorization task records {start ns, end ns, SM id, task flags} from
+ * %globaltimer into a device buffer (one record per task), read with d3m_get_trace. */
+#define D3M_DEBUG_TRACE 2
 
 typedef struct {
   int64_t n;                /* sum of block sizes */
@@ -195,6 +198,14 @@ int d3m_get_factor_block(d3m_handle h, int32_t i, int32_t j, void* host_out, voi
 
 /* Copy the pivots D_j of block column j (NEW numbering) to host memory as c128 [m_j]. */
 int d3m_get_pivots(d3m_handle h, int32_t j, void* host_out, void* stream);
+
+/* Task trace of the last factorization (handle created with D3M_DEBUG_TRACE): copies up to
+ * `cap` records of 8 int64 each {start_ns, end_ns, sm_id, flags | (tile << 8), t1, t2, t3, t4},
+ * indexed by task id, to host memory and stores the number of tasks in *count; t1..t4 are
+ * phase marks of the tensor-core engine (products done, S staged, factor / triangular solve
+ * done, tile stored; 0 where a phase does not occur).  Synchronizes the stream.
+ * D3M_ERR_STATE if tracing was not enabled. */
+int d3m_get_trace(d3m_handle h, int64_t* host_out, int64_t cap, int64_t* count, void* stream);
 
 /* Synchronizes the stream, then fills `info` (structure + the last factor/solve results). */
 int d3m_get_info(d3m_handle h, d3m_info* info, void* stream);

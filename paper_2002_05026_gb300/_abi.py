@@ -27,6 +27,7 @@ D3M_MIXED_BF16X3 = 1
 D3M_MIXED_SIMT32 = 2
 
 D3M_DEBUG_STALL_LAST_TASK = 1
+D3M_DEBUG_TRACE = 2
 
 ERROR_NAMES = {0: "OK", 1: "INVALID", 2: "OOM", 3: "CUDA", 4: "PIVOT", 5: "NOT_CONVERGED",
                6: "TIMEOUT", 7: "STATE"}
@@ -86,6 +87,7 @@ def load() -> ctypes.CDLL:
         "d3m_get_factor_block": (c_int32, [c_void_p, c_int32, c_int32, c_void_p, c_void_p]),
         "d3m_get_pivots": (c_int32, [c_void_p, c_int32, c_void_p, c_void_p]),
         "d3m_get_info": (c_int32, [c_void_p, P(d3m_info), c_void_p]),
+        "d3m_get_trace": (c_int32, [c_void_p, c_void_p, c_int64, P(c_int64), c_void_p]),
         "d3m_last_error": (c_char_p, [c_void_p]),
         "d3m_destroy": (None, [c_void_p]),
     }

@@ -61,6 +61,7 @@ struct d3m_ctx {
   void* opA = nullptr;
   void* opB = nullptr;
   void* Sacc = nullptr;
+  int64_t* trace = nullptr;
   TcMaps maps;
   // solve
   SolveItem* fwd_items = nullptr;
@@ -316,6 +317,10 @@ int d3m_create(d3m_handle* out, const d3m_pattern* pat, const int32_t* perm, con
     UPLOAD(h->ndeps, nd);
   }
   ALLOC(h->cnt, int32_t, ntask);
+  if (h->opt.debug_flags & D3M_DEBUG_TRACE) {
+    ALLOC(h->trace, int64_t, 8 * ntask);
+    CUDA_TRY(h, cudaMemset(h->trace, 0, 8 * ntask * sizeof(int64_t)));
+  }
   UPLOAD(h->succ_ptr, S.succ_ptr);
   UPLOAD(h->succ, S.succ);
   ALLOC(h->ready, int32_t, ntask);
@@ -485,6 +490,7 @@ int d3m_factor(d3m_handle h, const void* Kin, void* stream) {
   p.opA = h->opA;
   p.opB = h->opB;
   p.Sacc = h->Sacc;
+  p.trace = h->trace;
   p.timeout_ns = h->opt.timeout_ns;
   p.piv_tol = 1e3 * (h->fp64 ? 1.1102230246251565e-16 : 5.9604644775390625e-08);
   ev_begin(h, d3m_ctx::EV_FACTOR, st);
@@ -755,6 +761,19 @@ int d3m_get_pivots(d3m_handle h, int32_t j, void* host_out, void* stream) {
       const float2 f = ((float2*)buf.data())[u];
       out[u] = make_double2(f.x, f.y);
     }
+  }
+  return D3M_OK;
+}
+
+int d3m_get_trace(d3m_handle h, int64_t* host_out, int64_t cap, int64_t* count, void* stream) {
+  if (!h || !count) return set_err(h, D3M_ERR_INVALID, "handle or count is NULL");
+  if (!h->trace) return set_err(h, D3M_ERR_STATE, "tracing was not enabled at create (D3M_DEBUG_TRACE)");
+  const int64_t n = (int64_t)h->S.tasks.size();
+  *count = n;
+  CUDA_TRY(h, cudaStreamSynchronize((cudaStream_t)stream));
+  if (host_out && cap > 0) {
+    const int64_t m = std::min(cap, n);
+    CUDA_TRY(h, cudaMemcpy(host_out, h->trace, (size_t)m * 8 * sizeof(int64_t), cudaMemcpyDeviceToHost));
   }
   return D3M_OK;
 }

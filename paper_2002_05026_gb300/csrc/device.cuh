@@ -45,6 +45,7 @@ struct FactorParams {
   void* opA;             // tensor-core operand planes (bf16) of L tiles
   void* opB;             // tensor-core operand planes (bf16) of W tiles / T_J
   void* Sacc;            // [n_acc][b][b] partial Schur accumulators (complex, working precision)
+  int64_t* trace;        // [ntasks][8] task records, or nullptr
   int64_t timeout_ns;
   double piv_tol;        // breakdown: |d| < piv_tol * max|S| of the diagonal tile
 };
@@ -125,6 +126,29 @@ __device__ __forceinline__ void set_error(Ctl* ctl, int code, int task) {
 }
 
 // ------------------------------------------------------------------ scheduler
+__device__ __forceinline__ uint32_t sm_id() {
+  uint32_t s;
+  asm volatile("mov.u32 %0, %%smid;" : "=r"(s));
+  return s;
+}
+
+// Trace record of one task: start (at pop) and end (before its successors are released).
+constexpr int TRACE_W = 8;
+__device__ __forceinline__ void trace_begin(const FactorParams& p, int task) {
+  if (p.trace && threadIdx.x == 0) p.trace[TRACE_W * (int64_t)task] = (int64_t)globaltimer_ns();
+}
+__device__ __forceinline__ void trace_end(const FactorParams& p, int task, int flags, int tile) {
+  if (p.trace && threadIdx.x == 0) {
+    p.trace[TRACE_W * (int64_t)task + 1] = (int64_t)globaltimer_ns();
+    p.trace[TRACE_W * (int64_t)task + 2] = (int64_t)sm_id();
+    p.trace[TRACE_W * (int64_t)task + 3] = (int64_t)flags | ((int64_t)tile << 8);
+  }
+}
+// phase mark k (0..3) of a task
+__device__ __forceinline__ void trace_mark(const FactorParams& p, int task, int k) {
+  if (p.trace && threadIdx.x == 0) p.trace[TRACE_W * (int64_t)task + 4 + k] = (int64_t)globaltimer_ns();
+}
+
 // Claim the next ready task for this block (all threads call; returns -1 when done/aborted).
 __device__ __forceinline__ int sched_pop(const FactorParams& p, int* s_task) {
   if (threadIdx.x == 0) {
@@ -154,6 +178,7 @@ __device__ __forceinline__ int sched_pop(const FactorParams& p, int* s_task) {
   __syncthreads();
   const int t = *s_task;
   __syncthreads();
+  if (t >= 0) trace_begin(p, t);
   return t;
 }
 
@@ -162,6 +187,10 @@ __device__ __forceinline__ void sched_complete(const FactorParams& p, int task) 
   // writes of this thread become visible to later TMA (async-proxy) reads of other blocks
   asm volatile("fence.proxy.async.global;" ::: "memory");
   __syncthreads();
+  if (p.trace) {
+    const TileTask& T = p.tasks[task];
+    trace_end(p, task, T.flags, T.tile);
+  }
   if (threadIdx.x < 32) {
     __threadfence();  // release: this block's tile writes before the counter updates
     const int64_t e0 = p.succ_ptr[task], e1 = p.succ_ptr[task + 1];

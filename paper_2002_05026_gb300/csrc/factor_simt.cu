@@ -83,33 +83,48 @@ __global__ void __launch_bounds__(NTHR, 1) factor_simt_kernel(FactorParams p) {
     C* Sa = (T.sidx >= 0) ? Sacc + (int64_t)T.sidx * TB * TB : nullptr;
     if (T.flags & TF_UPDATE) {
       // partial update: accumulator <- S_in - sum over this segment
+      C kin[4][4];
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
           const int r = ty + 16 * i, c = tx + 16 * j;
-          const C s_in = (T.flags & TF_S_IN) ? ld_cg(Sa + r * TB + c) : k_entry<R>(T, p.K, r, c);
-          Sa[r * TB + c] = csub(s_in, acc[i][j]);
+          kin[i][j] = (T.flags & TF_S_IN) ? ld_cg(Sa + r * TB + c) : k_entry<R>(T, p.K, r, c);
         }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) Sa[(ty + 16 * i) * TB + tx + 16 * j] = csub(kin[i][j], acc[i][j]);
       sched_complete(p, task);
       continue;
     }
+    {
+      C kin[4][4];
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < 4; ++i)
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int r = ty + 16 * i, c = tx + 16 * j;
-        const C s_in = (T.flags & TF_S_IN) ? ld_cg(Sa + r * TB + c) : k_entry<R>(T, p.K, r, c);
-        sA[r * LDS + c] = csub(s_in, acc[i][j]);
-      }
+        for (int j = 0; j < 4; ++j) {
+          const int r = ty + 16 * i, c = tx + 16 * j;
+          kin[i][j] = (T.flags & TF_S_IN) ? ld_cg(Sa + r * TB + c) : k_entry<R>(T, p.K, r, c);
+        }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) sA[(ty + 16 * i) * LDS + tx + 16 * j] = csub(kin[i][j], acc[i][j]);
+    }
     __syncthreads();
 
     if (T.flags & TF_DIAG) {
       // ------------------------------------------------------------ 2a. diagonal tile
+      // max |S| over the real lower triangle; the upper triangle is zeroed to hold X^T, X = L^{-1}
       R mx = 0;
       for (int i = tid; i < TB * TB; i += NTHR) {
         const int r = i >> 6, c = i & 63;
-        if (c <= r && r < T.rv) mx = fmax(mx, (R)sqrt(cabs2(sA[r * LDS + c])));
+        if (c <= r) {
+          if (r < T.rv) mx = fmax(mx, (R)sqrt(cabs2(sA[r * LDS + c])));
+        } else {
+          sA[r * LDS + c] = CT<R>::make(0, 0);
+        }
       }
       for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
       if ((tid & 31) == 0) s_red[tid >> 5] = mx;
@@ -119,25 +134,48 @@ __global__ void __launch_bounds__(NTHR, 1) factor_simt_kernel(FactorParams p) {
         for (int w = 0; w < NTHR / 32; ++w) v = fmax(v, s_red[w]);
         s_red[0] = v;
       }
-      __syncthreads();
-      const R smax = s_red[0];
-      for (int c = 0; c < TB; ++c) {
-        const C d = sA[c * LDS + c];
-        if (tid > c && tid < TB) {
-          const C v = sA[tid * LDS + c];
-          s_tmp[tid] = v;
-          s_col[tid] = cdiv(v, d);
+      // unpivoted LDL^T fused with the inverse of L (see the tensor-core engine): at step c,
+      // l_r = S[r][c] / d_c and u_s = column c (X[c][s] above the diagonal, 1 on it, S[s][c]
+      // below); rank-1 update of every (r > c, s <= r), S below / X^T above the diagonal.
+      {
+        const int tr = tid >> 4, tcol = tid & 15;
+        for (int c = 0; c < TB; ++c) {
+          if (tid < TB) {
+            const C d = sA[c * LDS + c];
+            const C v = sA[tid * LDS + c];
+            if (tid > c) s_col[tid] = cdiv(v, d);
+            s_tmp[tid] = (tid == c) ? CT<R>::make(1, 0) : v;
+            if (tid == c) s_d[c] = d;
+          }
+          __syncthreads();
+          C lr[4], us[4];
+#pragma unroll
+          for (int a = 0; a < 4; ++a) {
+            lr[a] = s_col[tr + 16 * a];
+            us[a] = s_tmp[tcol + 16 * a];
+          }
+#pragma unroll
+          for (int a = 0; a < 4; ++a) {
+            const int r = tr + 16 * a;
+            if (r <= c) continue;
+            C v[4];
+            int off[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {          // all loads of the row first
+              const int s = tcol + 16 * q;
+              off[q] = (s > c) ? r * LDS + s : s * LDS + r;
+              if (s <= r) v[q] = sA[off[q]];
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+              if (tcol + 16 * q <= r) sA[off[q]] = cfms(lr[a], us[q], v[q]);
+          }
+          __syncthreads();
+          if (tid > c && tid < TB) sA[tid * LDS + c] = s_col[tid];
         }
-        if (tid == 0) s_d[c] = d;
-        __syncthreads();
-        const int w = TB - 1 - c;
-        for (int i = tid; i < w * w; i += NTHR) {
-          const int r = c + 1 + i / w, s = c + 1 + i % w;
-          if (s <= r) sA[r * LDS + s] = cfms(s_col[r], s_tmp[s], sA[r * LDS + s]);
-        }
-        if (tid > c && tid < TB) sA[tid * LDS + c] = s_col[tid];
         __syncthreads();
       }
+      const R smax = s_red[0];
       // pivot checks on the real (non-padding) unknowns
       if (tid < 32) {
         R amin = (R)3.0e38, amax = 0;
@@ -155,32 +193,16 @@ __global__ void __launch_bounds__(NTHR, 1) factor_simt_kernel(FactorParams p) {
           if (!(amin >= (R)p.piv_tol * smax)) set_error(p.ctl, D3M_ERR_PIVOT, task);
         }
       }
-      // store L_JJ (unit lower), D_J
+      // store L_JJ (unit lower), D_J, and L_JJ^{-1} (from the transposed upper storage)
       C* Lt = Lg + (int64_t)T.tile * TB * TB;
-      for (int i = tid; i < TB * TB; i += NTHR) {
-        const int r = i >> 6, c = i & 63;
-        C v = (c < r) ? sA[r * LDS + c] : CT<R>::make(c == r ? (R)1 : (R)0, 0);
-        Lt[i] = v;
-      }
-      if (tid < TB) Dg[(int64_t)T.col * TB + tid] = s_d[tid];
-      __syncthreads();
-      // in-place inverse of the unit lower tile: for j = 62..0,
-      // X_ij = -(L_ij + sum_{j<k<i} X_ik L_kj)   (columns > j already hold X)
-      for (int j = TB - 2; j >= 0; --j) {
-        if (tid > j && tid < TB) {
-          C t = sA[tid * LDS + j];
-          for (int k = j + 1; k < tid; ++k) t = cfma(sA[tid * LDS + k], sA[k * LDS + j], t);
-          s_tmp[tid] = CT<R>::make(-t.x, -t.y);
-        }
-        __syncthreads();
-        if (tid > j && tid < TB) sA[tid * LDS + j] = s_tmp[tid];
-        __syncthreads();
-      }
       C* Li = Linv + (int64_t)T.col * TB * TB;
       for (int i = tid; i < TB * TB; i += NTHR) {
         const int r = i >> 6, c = i & 63;
-        Li[i] = (c < r) ? sA[r * LDS + c] : CT<R>::make(c == r ? (R)1 : (R)0, 0);
+        const C one = CT<R>::make(c == r ? (R)1 : (R)0, 0);
+        Lt[i] = (c < r) ? sA[r * LDS + c] : one;
+        Li[i] = (c < r) ? sA[c * LDS + r] : one;
       }
+      if (tid < TB) Dg[(int64_t)T.col * TB + tid] = s_d[tid];
     } else {
       // ------------------------------------------------------------ 2b. off-diagonal tile
       const C* Ld = Lg + (int64_t)T.diag * TB * TB;

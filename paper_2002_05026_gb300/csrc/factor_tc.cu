@@ -167,14 +167,42 @@ __device__ __forceinline__ void store_smem_plane32(unsigned char* plane_hi, unsi
   }
 }
 
+// Accumulator tile layout (TMEM-native): element (r, c) of the 128 x 128 complex tile is float2
+// ((chunk * 16 + q) * 128 + r) * 2 + (c & 1) with chunk = c / 32, q = (c % 32) / 2, so the row-per-
+// thread epilogue reads and writes 16-byte words that are contiguous across the 128 rows.
+__device__ __forceinline__ float4* acc_slot(float2* Sa, int r, int c0) {
+  return reinterpret_cast<float4*>(Sa) + (int64_t)(c0 >> 5) * 16 * TB + r;   // + q * TB
+}
+
+// 32 consecutive entries (row r, columns c0..c0+31) of the update's starting value: the tile's
+// accumulator (Sa != nullptr) or K_IJ.  All loads are issued before any use.
+__device__ __forceinline__ void load_s_in(const TileTask& T, const double2* K, float2* Sa, int r, int c0,
+                                          float2* kin) {
+  if (Sa) {
+    const float4* s4 = acc_slot(Sa, r, c0);
+    float4 v[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = ld_cg4(s4 + i * TB);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      kin[2 * i] = make_float2(v[i].x, v[i].y);
+      kin[2 * i + 1] = make_float2(v[i].z, v[i].w);
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < 32; ++i) kin[i] = k_entry<float>(T, K, r, c0 + i);
+  }
+}
+
 }  // namespace
 
 __global__ void __launch_bounds__(NTHR, 1)
     factor_tc_kernel(const FactorParams p, const __grid_constant__ CUtensorMap mapA,
                      const __grid_constant__ CUtensorMap mapB) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  // 1024-byte alignment of the dynamic region (swizzle atoms)
-  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  // 1024-byte alignment of the dynamic region (swizzle atoms); pointer arithmetic on the shared
+  // array keeps the accesses in the shared address space
+  unsigned char* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   __shared__ __align__(8) uint64_t bar_full[2], bar_empty[2], bar_tfull[2], bar_tempty[2], bar_acc, bar_acc2;
   __shared__ uint32_t s_tmem;
   __shared__ int s_task;
@@ -282,6 +310,7 @@ __global__ void __launch_bounds__(NTHR, 1)
       if (tid == 0) set_error(p.ctl, D3M_ERR_TIMEOUT, task);
       break;
     }
+    trace_mark(p, task, 0);
 
     const bool is_diag = (T.flags & TF_DIAG) != 0;
     const bool s_in = (T.flags & TF_S_IN) != 0;
@@ -295,21 +324,15 @@ __global__ void __launch_bounds__(NTHR, 1)
         float vr[32], vi[32];
         tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + ACC1 + c0, vr);
         tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + ACC1 + 128 + c0, vi);
-        float4* row = reinterpret_cast<float4*>(Sa + (int64_t)r * TB + c0);
-#pragma unroll 4
-        for (int i = 0; i < 32; i += 2) {
-          float2 a0, a1;
-          if (s_in) {
-            const float4 v = ld_cg4(row + i / 2);
-            a0 = make_float2(v.x, v.y);
-            a1 = make_float2(v.z, v.w);
-          } else {
-            a0 = k_entry<float>(T, p.K, r, c0 + i);
-            a1 = k_entry<float>(T, p.K, r, c0 + i + 1);
-          }
-          row[i / 2] = make_float4(a0.x - vr[i], a0.y - vi[i], a1.x - vr[i + 1], a1.y - vi[i + 1]);
-        }
+        float4* slot = acc_slot(Sa, r, c0);
+        float2 kin[32];
+        load_s_in(T, p.K, s_in ? Sa : nullptr, r, c0, kin);   // all loads first
+#pragma unroll
+        for (int i = 0; i < 32; i += 2)
+          slot[(i / 2) * TB] = make_float4(kin[i].x - vr[i], kin[i].y - vi[i], kin[i + 1].x - vr[i + 1], kin[i + 1].y - vi[i + 1]);
       }
+      __syncthreads();
+      trace_mark(p, task, 3);
       tc_fence_before();
       sched_complete(p, task);
       continue;
@@ -345,40 +368,73 @@ __global__ void __launch_bounds__(NTHR, 1)
 #pragma unroll
           for (int i = 0; i < 32; ++i) vr[i] = vi[i] = 0.f;
         }
-#pragma unroll 4
-        for (int i = 0; i < 32; ++i) {
-          const float2 kv = s_in ? ld_cg(Sa + (int64_t)r * TB + c0 + i) : k_entry<float>(T, p.K, r, c0 + i);
-          sS[r * LDS + c0 + i] = make_float2(kv.x - vr[i], kv.y - vi[i]);
-        }
+        float2 kin[32];
+        load_s_in(T, p.K, s_in ? Sa : nullptr, r, c0, kin);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) sS[r * LDS + c0 + i] = make_float2(kin[i].x - vr[i], kin[i].y - vi[i]);
       }
       tc_fence_before();
       __syncthreads();
-      // max |S| over the real lower triangle (breakdown scale)
+      trace_mark(p, task, 1);
+      // max |S| over the real lower triangle (breakdown scale); zero the upper triangle, which
+      // will hold X = L^{-1} transposed
       float mx = 0.f;
       for (int i = tid; i < TB * TB; i += NTHR) {
         const int rr = i >> 7, cc = i & 127;
-        if (cc <= rr && rr < T.rv) mx = fmaxf(mx, sqrtf(cabs2(sS[rr * LDS + cc])));
+        if (cc <= rr) {
+          if (rr < T.rv) mx = fmaxf(mx, sqrtf(cabs2(sS[rr * LDS + cc])));
+        } else {
+          sS[rr * LDS + cc] = make_float2(0.f, 0.f);
+        }
       }
       for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
       if (lane == 0) s_red[warp] = mx;
-      // unpivoted LDL^T, right-looking on the lower triangle
-      for (int c = 0; c < TB; ++c) {
-        const float2 d = sS[c * LDS + c];
-        if (tid > c && tid < TB) {
-          const float2 v = sS[tid * LDS + c];
-          s_tmp[tid] = v;
-          s_col[tid] = cdiv(v, d);
+      __syncthreads();
+      // Unpivoted LDL^T fused with the inverse of L (right-looking on both):
+      // at step c, column c of sS holds X[c][s] above the diagonal (s < c), d_c on it and
+      // v_s = S[s][c] below it; with l_r = v_r / d_c, every (r > c, s <= r) is a rank-1 update
+      //   s > c:  S[r][s] -= l_r v_s                 (Schur complement, lower triangle)
+      //   s <= c: X[r][s] -= l_r X[c][s], X[c][c] = 1 (inverse, stored as Xt[s][r] above)
+      // Thread (tr, tc) of a 16 x 16 grid owns rows r = tr (mod 16) and columns s = tc (mod 16).
+      {
+        const int tr = tid >> 4, tcol = tid & 15;
+        for (int c = 0; c < TB; ++c) {
+          if (tid < TB) {
+            const float2 d = sS[c * LDS + c];
+            const float2 v = sS[tid * LDS + c];
+            if (tid > c) s_col[tid] = cdiv(v, d);
+            s_tmp[tid] = (tid == c) ? make_float2(1.f, 0.f) : v;   // u_s
+            if (tid == c) s_d[c] = d;
+          }
+          __syncthreads();
+          float2 lr[8], us[8];
+#pragma unroll
+          for (int a = 0; a < 8; ++a) {
+            lr[a] = s_col[tr + 16 * a];
+            us[a] = s_tmp[tcol + 16 * a];
+          }
+#pragma unroll
+          for (int a = 0; a < 8; ++a) {
+            const int rr = tr + 16 * a;
+            if (rr <= c) continue;
+            float2 v[8];
+            int off[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {          // all loads of the row first
+              const int ss = tcol + 16 * q;
+              off[q] = (ss > c) ? rr * LDS + ss : ss * LDS + rr;
+              if (ss <= rr) v[q] = sS[off[q]];
+            }
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+              if (tcol + 16 * q <= rr) sS[off[q]] = cfms(lr[a], us[q], v[q]);
+          }
+          __syncthreads();
+          if (tid > c && tid < TB) sS[tid * LDS + c] = s_col[tid];   // column c of L
         }
-        if (tid == 0) s_d[c] = d;
-        __syncthreads();
-        for (int rr = c + 1 + (tid >> 1); rr < TB; rr += NTHR / 2) {
-          const float2 l = s_col[rr];
-          for (int ss = c + 1 + (tid & 1); ss <= rr; ss += 2)
-            sS[rr * LDS + ss] = cfms(l, s_tmp[ss], sS[rr * LDS + ss]);
-        }
-        if (tid > c && tid < TB) sS[tid * LDS + c] = s_col[tid];
         __syncthreads();
       }
+      trace_mark(p, task, 2);
       if (tid < 32) {
         float smax = 0.f;
         for (int w = 0; w < NTHR / 32; ++w) smax = fmaxf(smax, s_red[w]);
@@ -397,37 +453,18 @@ __global__ void __launch_bounds__(NTHR, 1)
           if (!(amin >= (float)p.piv_tol * smax)) set_error(p.ctl, D3M_ERR_PIVOT, task);
         }
       }
-      // store L_JJ (unit lower) and D_J
+      // store L_JJ (unit lower), D_J
       float2* Lt = Lg + (int64_t)T.tile * TB * TB;
       for (int i = tid; i < TB * TB; i += NTHR) {
         const int rr = i >> 7, cc = i & 127;
         Lt[i] = (cc < rr) ? sS[rr * LDS + cc] : make_float2(cc == rr ? 1.f : 0.f, 0.f);
       }
       if (tid < TB) Dg[(int64_t)T.col * TB + tid] = s_d[tid];
-      __syncthreads();
-      // in-place inverse of the unit lower tile (columns right to left)
-      for (int j = TB - 2; j >= 0; --j) {
-        // rows j+1..127; two threads per row split the dot product
-        const int rr = j + 1 + (tid >> 1);
-        float2 t = make_float2(0.f, 0.f);
-        if (rr < TB) {
-          for (int k = j + 1 + (tid & 1); k < rr; k += 2) t = cfma(sS[rr * LDS + k], sS[k * LDS + j], t);
-        }
-        t.x += __shfl_xor_sync(0xffffffffu, t.x, 1);
-        t.y += __shfl_xor_sync(0xffffffffu, t.y, 1);
-        if (rr < TB && (tid & 1) == 0) {
-          const float2 l = sS[rr * LDS + j];
-          s_tmp[rr] = make_float2(-(l.x + t.x), -(l.y + t.y));
-        }
-        __syncthreads();
-        if (tid > j && tid < TB) sS[tid * LDS + j] = s_tmp[tid];
-        __syncthreads();
-      }
       // Linv (c64, for the solve) and T_J = D^{-1} Linv as B planes [-T_i, T_r, T_i] x [hi, lo]
       float2* Li = Linv + (int64_t)T.col * TB * TB;
       for (int i = tid; i < TB * TB; i += NTHR) {
         const int rr = i >> 7, cc = i & 127;
-        Li[i] = (cc < rr) ? sS[rr * LDS + cc] : make_float2(cc == rr ? 1.f : 0.f, 0.f);
+        Li[i] = (cc < rr) ? sS[cc * LDS + rr] : make_float2(cc == rr ? 1.f : 0.f, 0.f);
       }
       {
         const int n = tid & 127, kh = tid >> 7;   // row n, K half kh (64 columns)
@@ -439,7 +476,7 @@ __global__ void __launch_bounds__(NTHR, 1)
 #pragma unroll
           for (int i = 0; i < 32; ++i) {
             const int k = c0 + i;
-            const float2 lv = (k < n) ? sS[n * LDS + k] : make_float2(k == n ? 1.f : 0.f, 0.f);
+            const float2 lv = (k < n) ? sS[k * LDS + n] : make_float2(k == n ? 1.f : 0.f, 0.f);
             const float2 tv = cmul(dinv, lv);
             tr[i] = tv.x;
             ti[i] = tv.y;
@@ -450,6 +487,7 @@ __global__ void __launch_bounds__(NTHR, 1)
           store_plane32(base + (2 * 128 + n) * TB + c0, base + (384 + 2 * 128 + n) * TB + c0, ti, 1.f);
         }
       }
+      trace_mark(p, task, 3);
     } else {
       // S planes for the TRSM product (A operand, SW64 K-major, 4 chunks)
       for (int pass = 0; pass < 2; ++pass) {
@@ -462,11 +500,14 @@ __global__ void __launch_bounds__(NTHR, 1)
 #pragma unroll
           for (int i = 0; i < 32; ++i) vr[i] = vi[i] = 0.f;
         }
-#pragma unroll 4
-        for (int i = 0; i < 32; ++i) {
-          const float2 kv = s_in ? ld_cg(Sa + (int64_t)r * TB + c0 + i) : k_entry<float>(T, p.K, r, c0 + i);
-          vr[i] = kv.x - vr[i];
-          vi[i] = kv.y - vi[i];
+        {
+          float2 kin[32];
+          load_s_in(T, p.K, s_in ? Sa : nullptr, r, c0, kin);
+#pragma unroll
+          for (int i = 0; i < 32; ++i) {
+            vr[i] = kin[i].x - vr[i];
+            vi[i] = kin[i].y - vi[i];
+          }
         }
         unsigned char* ch = smem + SMEM_S + (c0 / KC) * STAGE_A;
         store_smem_plane32(ch + 0 * PLANE, ch + 2 * PLANE, r, vr);
@@ -475,6 +516,7 @@ __global__ void __launch_bounds__(NTHR, 1)
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       tc_fence_before();
       __syncthreads();
+      trace_mark(p, task, 1);
       // ---------------------------------------------------------------- phase 3: TRSM product
       if (warp == 0) {
         if (lane == 0) {
@@ -527,36 +569,67 @@ __global__ void __launch_bounds__(NTHR, 1)
         if (tid == 0) set_error(p.ctl, D3M_ERR_TIMEOUT, task);
         break;
       }
-      // D_J into the (now idle) TRSM stage area
+      trace_mark(p, task, 2);
+      // D_J into the (now idle) TRSM stage area; L_IJ (c64) staged row-major in [0, 128K) with the
+      // 16-byte units of each 128-byte span XOR-swizzled by the row (conflict-free row writes)
       float2* s_d = reinterpret_cast<float2*>(smem + SMEM_T);
       if (tid < TB) s_d[tid] = ld_cg(Dg + (int64_t)T.col * TB + tid);
-      __syncthreads();
-      // ---------------------------------------------------------------- phase 4: store L_IJ
-      float2* Lt = Lg + (int64_t)T.tile * TB * TB;
-      __nv_bfloat16* A = opA + (int64_t)T.tile * 512 * TB;
-      __nv_bfloat16* B = opB + (int64_t)T.tile * 768 * TB;
+      float4* stg = reinterpret_cast<float4*>(smem);
       for (int pass = 0; pass < 2; ++pass) {
         const int c0 = half * 64 + pass * 32;
-        float lr[32], li[32], wr[32], wi[32];
+        float lr[32], li[32];
         tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + ACC2 + c0, lr);
         tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + ACC2 + 128 + c0, li);
-        float4* Lrow = reinterpret_cast<float4*>(Lt + (int64_t)r * TB + c0);
 #pragma unroll
-        for (int i = 0; i < 32; i += 2) Lrow[i / 2] = make_float4(lr[i], li[i], lr[i + 1], li[i + 1]);
-#pragma unroll
-        for (int i = 0; i < 32; ++i) {
-          const float2 w = cmul(make_float2(lr[i], li[i]), s_d[c0 + i]);
-          wr[i] = w.x;
-          wi[i] = w.y;
+        for (int i = 0; i < 32; i += 2) {
+          const int u = (c0 + i) >> 1;
+          stg[r * 64 + (u ^ (r & 7))] = make_float4(lr[i], li[i], lr[i + 1], li[i + 1]);
         }
-        // opA: rows 256*s + plane*128 + r  (planes r, i)
-        store_plane32(A + (0 * 128 + r) * TB + c0, A + (256 + 0 * 128 + r) * TB + c0, lr, 1.f);
-        store_plane32(A + (1 * 128 + r) * TB + c0, A + (256 + 1 * 128 + r) * TB + c0, li, 1.f);
-        // opB: rows 384*s + plane*128 + r  (planes -i, r, i)
-        store_plane32(B + (0 * 128 + r) * TB + c0, B + (384 + 0 * 128 + r) * TB + c0, wi, -1.f);
-        store_plane32(B + (1 * 128 + r) * TB + c0, B + (384 + 1 * 128 + r) * TB + c0, wr, 1.f);
-        store_plane32(B + (2 * 128 + r) * TB + c0, B + (384 + 2 * 128 + r) * TB + c0, wi, 1.f);
       }
+      __syncthreads();
+      // ---------------------------------------------------------------- phase 4: store L_IJ
+      // coalesced: L c64 row-major; operand planes opA (L) and opB (W = L D_J), 16 bytes per thread
+      float4* Lt4 = reinterpret_cast<float4*>(Lg + (int64_t)T.tile * TB * TB);
+      for (int e = tid; e < TB * 64; e += NTHR) {
+        const int rr = e >> 6, u = e & 63;
+        Lt4[e] = stg[rr * 64 + (u ^ (rr & 7))];
+      }
+      uint4* A = reinterpret_cast<uint4*>(opA + (int64_t)T.tile * 512 * TB);
+      uint4* B = reinterpret_cast<uint4*>(opB + (int64_t)T.tile * 768 * TB);
+      for (int it = tid; it < TB * 16; it += NTHR) {
+        const int rr = it >> 4, c8 = it & 15;   // row, group of 8 columns
+        float2 l[8];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int u = c8 * 4 + k;
+          const float4 v = stg[rr * 64 + (u ^ (rr & 7))];
+          l[2 * k] = make_float2(v.x, v.y);
+          l[2 * k + 1] = make_float2(v.z, v.w);
+        }
+        __nv_bfloat16 h[6][8], lo[6][8];   // planes: L_r, L_i, -W_i, W_r, W_i (+ spare)
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const float2 w = cmul(l[k], s_d[c8 * 8 + k]);
+          split2(l[k].x, h[0][k], lo[0][k]);
+          split2(l[k].y, h[1][k], lo[1][k]);
+          split2(-w.y, h[2][k], lo[2][k]);
+          split2(w.x, h[3][k], lo[3][k]);
+          split2(w.y, h[4][k], lo[4][k]);
+        }
+        // opA rows: split * 256 + plane * 128 + row; 16 uint4 per 256-byte row
+        A[((0 * 256 + 0 * 128) + rr) * 16 + c8] = pack8(h[0]);
+        A[((0 * 256 + 1 * 128) + rr) * 16 + c8] = pack8(h[1]);
+        A[((1 * 256 + 0 * 128) + rr) * 16 + c8] = pack8(lo[0]);
+        A[((1 * 256 + 1 * 128) + rr) * 16 + c8] = pack8(lo[1]);
+        // opB rows: split * 384 + plane * 128 + row (planes -W_i, W_r, W_i)
+#pragma unroll
+        for (int pl = 0; pl < 3; ++pl) {
+          B[((0 * 384 + pl * 128) + rr) * 16 + c8] = pack8(h[2 + pl]);
+          B[((1 * 384 + pl * 128) + rr) * 16 + c8] = pack8(lo[2 + pl]);
+        }
+      }
+      __syncthreads();
+      trace_mark(p, task, 3);
     }
     tc_fence_before();
     sched_complete(p, task);

@@ -80,6 +80,80 @@ __device__ __forceinline__ void stage_async(C* sL, const C* tile, int b, int r0)
   }
 }
 
+// ------------------------------------------------------------------ register-blocked tile products
+// Each warp computes 8 outputs for all (<= 8) right-hand sides; the reduction index is split
+// over 4 lanes and summed with shuffles.  One tile element load feeds rc complex FMAs; the
+// vector loads are broadcasts (4 distinct addresses per warp instruction).
+constexpr int RCMAX = 8;
+
+template <typename C>
+__device__ __forceinline__ void quad_reduce(C* acc) {
+#pragma unroll
+  for (int j = 0; j < RCMAX; ++j) {
+    acc[j].x += __shfl_xor_sync(0xffffffffu, acc[j].x, 1);
+    acc[j].y += __shfl_xor_sync(0xffffffffu, acc[j].y, 1);
+    acc[j].x += __shfl_xor_sync(0xffffffffu, acc[j].x, 2);
+    acc[j].y += __shfl_xor_sync(0xffffffffu, acc[j].y, 2);
+  }
+}
+
+// dst[r][j] (=, or -=) sum_c M[r][c] V[c][j] for the 64 rows of a staged half tile M
+// ([64][ldl]); V element (c, j) at V[c * ldv + j]; dst element (r, j) at dst[r * ldd + j].
+template <typename R, bool SUB>
+__device__ __forceinline__ void rows_matvec(const typename CT<R>::C* M, int ldl, int b, const typename CT<R>::C* V,
+                                            int ldv, int rc, typename CT<R>::C* dst, int ldd) {
+  using C = typename CT<R>::C;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int r = warp * 8 + (lane >> 2), cq = lane & 3;
+  C acc[RCMAX];
+#pragma unroll
+  for (int j = 0; j < RCMAX; ++j) acc[j] = CT<R>::make(0, 0);
+  const C* mrow = M + r * ldl;
+  for (int c = cq; c < b; c += 4) {
+    const C m = mrow[c];
+    const C* v = V + c * ldv;
+#pragma unroll
+    for (int j = 0; j < RCMAX; ++j)
+      if (j < rc) acc[j] = cfma(m, v[j], acc[j]);
+  }
+  quad_reduce(acc);
+  if (cq == 0) {
+#pragma unroll
+    for (int j = 0; j < RCMAX; ++j)
+      if (j < rc) dst[r * ldd + j] = SUB ? csub(dst[r * ldd + j], acc[j]) : acc[j];
+  }
+}
+
+// dst[c][j] (=, +=, or -= by MODE 0 / 1 / 2) sum_{r < 64} M[r][c] V[r][j] for all b columns
+// of a staged half tile.
+template <typename R, int MODE>
+__device__ __forceinline__ void cols_matvec(const typename CT<R>::C* M, int ldl, int b, const typename CT<R>::C* V,
+                                            int ldv, int rc, typename CT<R>::C* dst, int ldd) {
+  using C = typename CT<R>::C;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int rq = lane & 3;
+  for (int c0 = 0; c0 < b; c0 += 64) {
+    const int c = c0 + warp * 8 + (lane >> 2);
+    C acc[RCMAX];
+#pragma unroll
+    for (int j = 0; j < RCMAX; ++j) acc[j] = CT<R>::make(0, 0);
+    for (int r = rq; r < HR; r += 4) {
+      const C m = M[r * ldl + c];
+      const C* v = V + r * ldv;
+#pragma unroll
+      for (int j = 0; j < RCMAX; ++j)
+        if (j < rc) acc[j] = cfma(m, v[j], acc[j]);
+    }
+    quad_reduce(acc);
+    if (rq == 0) {
+#pragma unroll
+      for (int j = 0; j < RCMAX; ++j)
+        if (j < rc)
+          dst[c * ldd + j] = MODE == 0 ? acc[j] : (MODE == 1 ? cadd(dst[c * ldd + j], acc[j]) : csub(dst[c * ldd + j], acc[j]));
+    }
+  }
+}
+
 // ------------------------------------------------------------------ gather (off-block tiles)
 // grid.x = items of the level * (b / 64) halves.  FWD: P[slot][r][j] (rows of this half) =
 // sum_k L[r][k] Y[src*b + k][j].  BWD: P[slot*nh + h][c][j] = sum_{r in half h} L[r][c] W[src*b + r][j].
@@ -95,7 +169,7 @@ __global__ void __launch_bounds__(GT) gather_kernel(const SolveItem* __restrict_
   const int nh = b / HR;
   const int ldl = b + 1;
   C* sL = reinterpret_cast<C*>(smem_raw);      // [64][b+1]
-  C* sY = sL + HR * ldl;                       // [nrhs][rows]
+  C* sY = sL + HR * ldl;                       // [rows][nrhs]
   const SolveItem it = items[blockIdx.x / nh];
   const int h = blockIdx.x % nh;
   stage_async(sL, L + (int64_t)it.tile * b * b, b, h * HR);
@@ -104,30 +178,18 @@ __global__ void __launch_bounds__(GT) gather_kernel(const SolveItem* __restrict_
   const int64_t y0 = (int64_t)it.src * b + (FWD ? 0 : h * HR);
   for (int i = threadIdx.x; i < rows * nrhs; i += GT) {
     const int k = i % rows, j = i / rows;
-    sY[j * rows + k] = Y[j * npad + y0 + k];
+    sY[k * nrhs + j] = Y[j * npad + y0 + k];
   }
   cp_wait_all();
   __syncthreads();
-  if (FWD) {
-    // thread: row r of this half, rhs j = g, g + G, ...
-    const int G = GT / HR;
-    const int r = threadIdx.x % HR, g = threadIdx.x / HR;
-    C* out = P + (int64_t)it.slot * nh * b * nrhs;   // sub-slot 0 of the item
-    for (int j = g; j < nrhs; j += G) {
-      C acc = czero<R>();
-#pragma unroll 8
-      for (int k = 0; k < b; ++k) acc = cfma(sL[r * ldl + k], sY[j * b + k], acc);
-      out[(int64_t)(h * HR + r) * nrhs + j] = acc;
-    }
-  } else {
-    const int G = GT / b;
-    const int c = threadIdx.x % b, g = threadIdx.x / b;
-    C* out = P + ((int64_t)it.slot * nh + h) * b * nrhs;
-    for (int j = g; j < nrhs; j += G) {
-      C acc = czero<R>();
-#pragma unroll 8
-      for (int r = 0; r < HR; ++r) acc = cfma(sL[r * ldl + c], sY[j * HR + r], acc);
-      out[(int64_t)c * nrhs + j] = acc;
+  for (int j0 = 0; j0 < nrhs; j0 += RCMAX) {
+    const int rc = min(RCMAX, nrhs - j0);
+    if (FWD) {
+      C* out = P + (int64_t)it.slot * nh * b * nrhs + (int64_t)h * HR * nrhs + j0;   // sub-slot 0
+      rows_matvec<R, false>(sL, ldl, b, sY + j0, nrhs, rc, out, nrhs);
+    } else {
+      C* out = P + ((int64_t)it.slot * nh + h) * b * nrhs + j0;
+      cols_matvec<R, 0>(sL, ldl, b, sY + j0, nrhs, rc, out, nrhs);
     }
   }
 }
@@ -252,13 +314,7 @@ __global__ void __launch_bounds__(GT) block_fwd_kernel(BlockSweep s, const typen
       const int h = q % nh;
       if (q < nh) {
         // y_t rows [h*64, h*64+64) = Linv_t[rows] r_t
-        for (int i = threadIdx.x; i < HR * rc; i += GT) {
-          const int r = i % HR, j = i / HR;
-          C acc = czero<R>();
-#pragma unroll 8
-          for (int c = 0; c < b; ++c) acc = cfma(cur[r * ldl + c], sv[(t * b + c) * s.rc + j], acc);
-          sy[(h * HR + r) * s.rc + j] = acc;
-        }
+        rows_matvec<R, false>(cur, ldl, b, sv + (int64_t)t * b * s.rc, s.rc, rc, sy + h * HR * s.rc, s.rc);
         if (q == nh - 1) {
           __syncthreads();
           for (int i = threadIdx.x; i < b * rc; i += GT) {
@@ -268,13 +324,7 @@ __global__ void __launch_bounds__(GT) block_fwd_kernel(BlockSweep s, const typen
         }
       } else {
         const int tp = t + 1 + (q - nh) / nh;
-        for (int i = threadIdx.x; i < HR * rc; i += GT) {
-          const int r = i % HR, j = i / HR;
-          C acc = sv[(tp * b + h * HR + r) * s.rc + j];
-#pragma unroll 8
-          for (int c = 0; c < b; ++c) acc = cfms(cur[r * ldl + c], sy[c * s.rc + j], acc);
-          sv[(tp * b + h * HR + r) * s.rc + j] = acc;
-        }
+        rows_matvec<R, true>(cur, ldl, b, sy, s.rc, rc, sv + (int64_t)(tp * b + h * HR) * s.rc, s.rc);
       }
       __syncthreads();
     }
@@ -336,13 +386,7 @@ __global__ void __launch_bounds__(GT) block_bwd_kernel(BlockSweep s, const typen
       const int h = q % nh;
       if (q < nh) {
         // w_t += Linv_t[rows of half h]^T r_t[rows of half h]
-        for (int i = threadIdx.x; i < b * rc; i += GT) {
-          const int c = i % b, j = i / b;
-          C acc = sy[c * s.rc + j];
-#pragma unroll 8
-          for (int r = 0; r < HR; ++r) acc = cfma(cur[r * ldl + c], sv[(t * b + h * HR + r) * s.rc + j], acc);
-          sy[c * s.rc + j] = acc;
-        }
+        cols_matvec<R, 1>(cur, ldl, b, sv + (int64_t)(t * b + h * HR) * s.rc, s.rc, rc, sy, s.rc);
         if (q == nh - 1) {
           __syncthreads();
           for (int i = threadIdx.x; i < b * rc; i += GT) {
@@ -353,13 +397,7 @@ __global__ void __launch_bounds__(GT) block_bwd_kernel(BlockSweep s, const typen
       } else {
         // tile (t0+t, t0+tp): r_tp[c] -= sum_{r in half h} L[r][c] w_t[r]
         const int tp = (q - nh) / nh;
-        for (int i = threadIdx.x; i < b * rc; i += GT) {
-          const int c = i % b, j = i / b;
-          C acc = sv[(tp * b + c) * s.rc + j];
-#pragma unroll 8
-          for (int r = 0; r < HR; ++r) acc = cfms(cur[r * ldl + c], sy[(h * HR + r) * s.rc + j], acc);
-          sv[(tp * b + c) * s.rc + j] = acc;
-        }
+        cols_matvec<R, 2>(cur, ldl, b, sy + h * HR * s.rc, s.rc, rc, sv + (int64_t)tp * b * s.rc, s.rc);
       }
       __syncthreads();
     }
