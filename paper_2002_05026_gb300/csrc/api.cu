@@ -95,6 +95,7 @@ struct d3m_ctx {
   unsigned* norms = nullptr;         // [3 * max_nrhs + 1]: rmax, xmax, bmax, kmax
   double* omega_dev = nullptr;       // [max_nrhs]
   double* stat_dev = nullptr;        // [1]
+  int* sweep_status = nullptr;       // device: set by a sweep kernel whose bounded wait expired
   double* h_stat = nullptr;          // pinned [1]
   // gradients
   int32_t* rowidx = nullptr;
@@ -384,7 +385,7 @@ int d3m_create(d3m_handle* out, const d3m_pattern* pat, const int32_t* perm, con
     // the in-block sweep kernels keep one block's running vector (1 rhs at least) and two
     // staged half tiles in shared memory, and list at most 512 tile jobs per block
     const size_t need = h->csize * (2 * (size_t)64 * (b + 1) + (size_t)mrows + (size_t)b);
-    if (need > 220 * 1024 || (int64_t)mnt * (mnt + 1) / 2 * (b / 64) > 512)
+    if (need > 220 * 1024 || (int64_t)mnt * (mnt + 1) / 2 * (b / 64) > 512 || mnt > 32)
       return set_err(h, D3M_ERR_INVALID, "interface block too large for the solve kernels (m = " +
                                              std::to_string(mrows) + ")");
   }
@@ -421,6 +422,8 @@ int d3m_create(d3m_handle* out, const d3m_pattern* pat, const int32_t* perm, con
   ALLOC(h->norms, unsigned, 3 * mr + 1);
   ALLOC(h->omega_dev, double, mr);
   ALLOC(h->stat_dev, double, 1);
+  ALLOC(h->sweep_status, int, 1);
+  CUDA_TRY(h, cudaMemset(h->sweep_status, 0, sizeof(int)));
   ALLOC(h->contract, double2, S.N);
   CUDA_TRY(h, cudaMallocHost(&h->h_stat, sizeof(double)));
 #undef ALLOC
@@ -509,6 +512,7 @@ int d3m_factor(d3m_handle h, const void* Kin, void* stream) {
 static int sweep(d3m_ctx* h, const double2* src, double2* dst, int nrhs, int accumulate, cudaStream_t st) {
   const Symbolic& S = h->S;
   SweepLaunch a;
+  a.status = h->sweep_status;
   a.b = h->b;
   a.nrhs = nrhs;
   a.nlevels = S.nlevels;
@@ -654,6 +658,15 @@ static int solve_impl(d3m_ctx* h, const void* Bin, void* Xout, int nrhs, cudaStr
   }
   ev_end(h, d3m_ctx::EV_SOLVE, st);
   if (!xdev) CUDA_TRY(h, cudaMemcpyAsync(Xout, X, vbytes, cudaMemcpyDeviceToHost, st));
+  if (!h->fp64 || h->opt.fp64_omega) {
+    // the refinement already synchronized: report an expired bounded wait of a sweep kernel
+    int sw = 0;
+    CUDA_TRY(h, cudaMemcpy(&sw, h->sweep_status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (sw != 0) {
+      h->last_status = sw;
+      return set_err(h, sw, "bounded device wait expired in a solve sweep");
+    }
+  }
   h->last_status = status;
   return status;
 }
@@ -786,6 +799,11 @@ int d3m_get_info(d3m_handle h, d3m_info* info, void* stream) {
   fill_structure(h->S, info);
   info->device_bytes = h->dev_bytes;
   int st = h->last_status;
+  {
+    int sw = 0;
+    CUDA_TRY(h, cudaMemcpy(&sw, h->sweep_status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (sw != 0) st = sw;
+  }
   if (h->factored) {
     int fe = factor_error(h);
     if (fe != D3M_OK) st = fe;

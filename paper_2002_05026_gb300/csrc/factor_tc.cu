@@ -140,19 +140,6 @@ __device__ __forceinline__ uint4 pack8(const __nv_bfloat16* v) {
   return u;
 }
 
-// Write 32 consecutive K values (one chunk) of one row into a global operand plane row
-// (row-major, 128 bf16 per row) as hi and lo parts: dst_hi/dst_lo point at element c0.
-__device__ __forceinline__ void store_plane32(__nv_bfloat16* dst_hi, __nv_bfloat16* dst_lo, const float* v, float sign) {
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    __nv_bfloat16 h[8], l[8];
-#pragma unroll
-    for (int e = 0; e < 8; ++e) split2(sign * v[q * 8 + e], h[e], l[e]);
-    reinterpret_cast<uint4*>(dst_hi)[q] = pack8(h);
-    reinterpret_cast<uint4*>(dst_lo)[q] = pack8(l);
-  }
-}
-
 // Write 32 K values of row r into a shared-memory K-major SW64 plane (one chunk) as hi/lo.
 __device__ __forceinline__ void store_smem_plane32(unsigned char* plane_hi, unsigned char* plane_lo, int r,
                                                    const float* v) {
@@ -356,8 +343,6 @@ __global__ void __launch_bounds__(NTHR, 1)
     if (is_diag) {
       float2* sS = reinterpret_cast<float2*>(smem);   // [128][129]
       float2* s_d = reinterpret_cast<float2*>(smem + DIAG_AUX);
-      float2* s_col = s_d + TB;
-      float2* s_tmp = s_col + TB;
       for (int pass = 0; pass < 2; ++pass) {
         const int c0 = half * 64 + pass * 32;
         float vr[32], vi[32];
@@ -376,63 +361,112 @@ __global__ void __launch_bounds__(NTHR, 1)
       tc_fence_before();
       __syncthreads();
       trace_mark(p, task, 1);
-      // max |S| over the real lower triangle (breakdown scale); zero the upper triangle, which
-      // will hold X = L^{-1} transposed
+      // max |S| over the real lower triangle (breakdown scale)
       float mx = 0.f;
       for (int i = tid; i < TB * TB; i += NTHR) {
         const int rr = i >> 7, cc = i & 127;
-        if (cc <= rr) {
-          if (rr < T.rv) mx = fmaxf(mx, sqrtf(cabs2(sS[rr * LDS + cc])));
-        } else {
-          sS[rr * LDS + cc] = make_float2(0.f, 0.f);
-        }
+        if (cc <= rr && rr < T.rv) mx = fmaxf(mx, sqrtf(cabs2(sS[rr * LDS + cc])));
       }
       for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
       if (lane == 0) s_red[warp] = mx;
       __syncthreads();
-      // Unpivoted LDL^T fused with the inverse of L (right-looking on both):
-      // at step c, column c of sS holds X[c][s] above the diagonal (s < c), d_c on it and
-      // v_s = S[s][c] below it; with l_r = v_r / d_c, every (r > c, s <= r) is a rank-1 update
-      //   s > c:  S[r][s] -= l_r v_s                 (Schur complement, lower triangle)
-      //   s <= c: X[r][s] -= l_r X[c][s], X[c][c] = 1 (inverse, stored as Xt[s][r] above)
+      // Unpivoted LDL^T fused with the inverse of L, right-looking on both, two columns per step.
+      // Storage: S (Schur complement, then L) below the diagonal; X = L^{-1} transposed above it
+      // (Xt[s][r] = X[r][s]).  Step (c, c+1), with a_s = column c and b_s = column c+1 of sS:
+      //   d_c, l_s(c) = a_s / d_c;  l' = l_{c+1}(c);  d_{c+1} = S[c+1][c+1] - l' S[c+1][c];
+      //   v'_s = b_s - l_s(c) S[c+1][c];  l_s(c+1) = v'_s / d_{c+1};
+      //   u0_s = X[c][s] (s < c), 1 (s = c), 0 (s = c+1), S[s][c] (s > c+1);
+      //   u1_s = X[c+1][s] - l' X[c][s] (s < c), -l' (s = c), 1 (s = c+1), v'_s (s > c+1);
+      //   every (r > c+1, s <= r): entry -= l_r(c) u0_s + l_r(c+1) u1_s  (S below, Xt above);
+      //   column c / c+1 of L and row c+1 of X are written back in the same phase.
       // Thread (tr, tc) of a 16 x 16 grid owns rows r = tr (mod 16) and columns s = tc (mod 16).
       {
+        // the upper triangle starts at zero (X = I below the diagonal)
+        for (int i = tid; i < TB * TB; i += NTHR) {
+          const int rr = i >> 7, cc = i & 127;
+          if (cc > rr) sS[rr * LDS + cc] = make_float2(0.f, 0.f);
+        }
+        __syncthreads();
         const int tr = tid >> 4, tcol = tid & 15;
-        for (int c = 0; c < TB; ++c) {
+        float2* s_l0 = s_d + TB;              // l_s(c)
+        float2* s_u0 = s_d + 2 * TB;          // u0_s
+        float2* s_l1 = s_d + 3 * TB;          // l_s(c+1)
+        float2* s_u1 = s_d + 4 * TB;          // u1_s
+        for (int c = 0; c < TB; c += 2) {
           if (tid < TB) {
-            const float2 d = sS[c * LDS + c];
-            const float2 v = sS[tid * LDS + c];
-            if (tid > c) s_col[tid] = cdiv(v, d);
-            s_tmp[tid] = (tid == c) ? make_float2(1.f, 0.f) : v;   // u_s
-            if (tid == c) s_d[c] = d;
+            const int sI = tid;
+            const float2 dc = sS[c * LDS + c];
+            const float2 v1 = sS[(c + 1) * LDS + c];
+            const float2 l1c = cdiv(v1, dc);
+            const float2 d1 = csub(sS[(c + 1) * LDS + c + 1], cmul(l1c, v1));
+            const float2 a = sS[sI * LDS + c];
+            const float2 bb = sS[sI * LDS + c + 1];
+            const float2 l0 = (sI > c) ? cdiv(a, dc) : make_float2(0.f, 0.f);
+            const float2 vp = csub(bb, cmul(l0, v1));
+            const float2 l1 = (sI > c + 1) ? cdiv(vp, d1) : make_float2(0.f, 0.f);
+            float2 u0, u1;
+            if (sI < c) {
+              u0 = a;
+              u1 = csub(bb, cmul(l1c, a));
+            } else if (sI == c) {
+              u0 = make_float2(1.f, 0.f);
+              u1 = make_float2(-l1c.x, -l1c.y);
+            } else if (sI == c + 1) {
+              u0 = make_float2(0.f, 0.f);
+              u1 = make_float2(1.f, 0.f);
+            } else {
+              u0 = a;
+              u1 = vp;
+            }
+            s_l0[sI] = l0;
+            s_u0[sI] = u0;
+            s_l1[sI] = l1;
+            s_u1[sI] = u1;
+            if (sI == 0) {
+              s_d[c] = dc;
+              s_d[c + 1] = d1;
+            }
           }
           __syncthreads();
-          float2 lr[8], us[8];
+          float2 la[8], lb[8], ua[8], ub[8];
 #pragma unroll
           for (int a = 0; a < 8; ++a) {
-            lr[a] = s_col[tr + 16 * a];
-            us[a] = s_tmp[tcol + 16 * a];
+            la[a] = s_l0[tr + 16 * a];
+            lb[a] = s_l1[tr + 16 * a];
+            ua[a] = s_u0[tcol + 16 * a];
+            ub[a] = s_u1[tcol + 16 * a];
           }
 #pragma unroll
           for (int a = 0; a < 8; ++a) {
             const int rr = tr + 16 * a;
-            if (rr <= c) continue;
+            if (rr <= c + 1) continue;
             float2 v[8];
             int off[8];
 #pragma unroll
             for (int q = 0; q < 8; ++q) {          // all loads of the row first
               const int ss = tcol + 16 * q;
-              off[q] = (ss > c) ? rr * LDS + ss : ss * LDS + rr;
+              off[q] = (ss > c + 1) ? rr * LDS + ss : ss * LDS + rr;
               if (ss <= rr) v[q] = sS[off[q]];
             }
 #pragma unroll
             for (int q = 0; q < 8; ++q)
-              if (tcol + 16 * q <= rr) sS[off[q]] = cfms(lr[a], us[q], v[q]);
+              if (tcol + 16 * q <= rr) sS[off[q]] = cfms(lb[a], ub[q], cfms(la[a], ua[q], v[q]));
+          }
+          if (tid < TB) {                          // write back L columns c, c+1 and X row c+1
+            const int sI = tid;
+            if (sI > c) sS[sI * LDS + c] = s_l0[sI];
+            if (sI > c + 1) sS[sI * LDS + c + 1] = s_l1[sI];
+            if (sI <= c) sS[sI * LDS + c + 1] = s_u1[sI];
           }
           __syncthreads();
-          if (tid > c && tid < TB) sS[tid * LDS + c] = s_col[tid];   // column c of L
         }
-        __syncthreads();
+        // L_JJ (unit lower) and D_J
+        float2* Lt = Lg + (int64_t)T.tile * TB * TB;
+        for (int i = tid; i < TB * TB; i += NTHR) {
+          const int rr = i >> 7, cc = i & 127;
+          Lt[i] = (cc < rr) ? sS[rr * LDS + cc] : make_float2(cc == rr ? 1.f : 0.f, 0.f);
+        }
+        if (tid < TB) Dg[(int64_t)T.col * TB + tid] = s_d[tid];
       }
       trace_mark(p, task, 2);
       if (tid < 32) {
@@ -453,13 +487,6 @@ __global__ void __launch_bounds__(NTHR, 1)
           if (!(amin >= (float)p.piv_tol * smax)) set_error(p.ctl, D3M_ERR_PIVOT, task);
         }
       }
-      // store L_JJ (unit lower), D_J
-      float2* Lt = Lg + (int64_t)T.tile * TB * TB;
-      for (int i = tid; i < TB * TB; i += NTHR) {
-        const int rr = i >> 7, cc = i & 127;
-        Lt[i] = (cc < rr) ? sS[rr * LDS + cc] : make_float2(cc == rr ? 1.f : 0.f, 0.f);
-      }
-      if (tid < TB) Dg[(int64_t)T.col * TB + tid] = s_d[tid];
       // Linv (c64, for the solve) and T_J = D^{-1} Linv as B planes [-T_i, T_r, T_i] x [hi, lo]
       float2* Li = Linv + (int64_t)T.col * TB * TB;
       for (int i = tid; i < TB * TB; i += NTHR) {
@@ -467,26 +494,30 @@ __global__ void __launch_bounds__(NTHR, 1)
         Li[i] = (cc < rr) ? sS[cc * LDS + rr] : make_float2(cc == rr ? 1.f : 0.f, 0.f);
       }
       {
-        const int n = tid & 127, kh = tid >> 7;   // row n, K half kh (64 columns)
-        const float2 dinv = cdiv(make_float2(1.f, 0.f), s_d[n]);
-        __nv_bfloat16* base = opB + (int64_t)T.tile * 768 * TB;
-        for (int q = 0; q < 2; ++q) {
-          const int c0 = kh * 64 + q * 32;
-          float tr[32], ti[32];
+        // T_J = D^{-1} L^{-1}: row n, columns k (X[n][k] = sS[k][n] for k < n); coalesced 16-byte
+        // stores of the planes [-T_i, T_r, T_i] x [hi, lo] (16 threads per 256-byte plane row)
+        uint4* Bt = reinterpret_cast<uint4*>(opB + (int64_t)T.tile * 768 * TB);
+        for (int it = tid; it < TB * 16; it += NTHR) {
+          const int n = it >> 4, c8 = it & 15;
+          const float2 dinv = cdiv(make_float2(1.f, 0.f), s_d[n]);
+          __nv_bfloat16 h[3][8], lo[3][8];
 #pragma unroll
-          for (int i = 0; i < 32; ++i) {
-            const int k = c0 + i;
+          for (int k8 = 0; k8 < 8; ++k8) {
+            const int k = c8 * 8 + k8;
             const float2 lv = (k < n) ? sS[k * LDS + n] : make_float2(k == n ? 1.f : 0.f, 0.f);
             const float2 tv = cmul(dinv, lv);
-            tr[i] = tv.x;
-            ti[i] = tv.y;
+            split2(-tv.y, h[0][k8], lo[0][k8]);
+            split2(tv.x, h[1][k8], lo[1][k8]);
+            split2(tv.y, h[2][k8], lo[2][k8]);
           }
-          // split s: rows 384*s + plane*128 + n
-          store_plane32(base + (0 * 128 + n) * TB + c0, base + (384 + 0 * 128 + n) * TB + c0, ti, -1.f);
-          store_plane32(base + (1 * 128 + n) * TB + c0, base + (384 + 1 * 128 + n) * TB + c0, tr, 1.f);
-          store_plane32(base + (2 * 128 + n) * TB + c0, base + (384 + 2 * 128 + n) * TB + c0, ti, 1.f);
+#pragma unroll
+          for (int pl = 0; pl < 3; ++pl) {
+            Bt[((0 * 384 + pl * 128) + n) * 16 + c8] = pack8(h[pl]);
+            Bt[((1 * 384 + pl * 128) + n) * 16 + c8] = pack8(lo[pl]);
+          }
         }
       }
+      __syncthreads();
       trace_mark(p, task, 3);
     } else {
       // S planes for the TRSM product (A operand, SW64 K-major, 4 chunks)

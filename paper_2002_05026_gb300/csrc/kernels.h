@@ -33,6 +33,7 @@ struct ResidualParams {
 };
 
 struct SweepLaunch {
+  int* status;                     // device word: D3M_ERR_TIMEOUT if a bounded wait expired
   int b, nrhs, nlevels, max_rows, accumulate;
   int64_t n, npad;
   const double2* src;              // right-hand side (caller numbering, c128)

@@ -18,7 +18,9 @@ namespace d3m {
 
 namespace {
 constexpr int GT = 256;   // threads of gather / block kernels
+constexpr int ET = 256;   // threads of elementwise kernels
 constexpr size_t SWEEP_SMEM_LIMIT = 220 * 1024;
+constexpr uint64_t SWEEP_TIMEOUT_NS = 2000000000ull;   // bound on one staging wait
 constexpr int HR = 64;    // rows of one staged half-tile
 
 template <typename R>
@@ -57,44 +59,66 @@ __global__ void permute_out_kernel(const typename CT<R>::C* __restrict__ W, int6
   }
 }
 
-// ------------------------------------------------------------------ async staging
+// ------------------------------------------------------------------ bulk-copy staging
+// A staged half tile is 64 rows of b elements in shared memory with a row stride of b elements
+// + 16 bytes (rows stay 16-byte aligned for the bulk copies; the pad spreads rows over banks).
+// Each row is one TMA bulk copy (cp.async.bulk, b * sizeof(C) = 1 KB) completing on an mbarrier.
 __device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-__device__ __forceinline__ void cp_async_elem(float2* dst, const float2* src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_elem(double2* dst, const double2* src) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
-__device__ __forceinline__ void cp_wait_one() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
-// Stage rows [r0, r0 + 64) of a b x b row-major tile into a padded [64][b+1] buffer (async).
 template <typename C>
-__device__ __forceinline__ void stage_async(C* sL, const C* tile, int b, int r0) {
-  const int ldl = b + 1;
-  const C* src = tile + (int64_t)r0 * b;
-  for (int i = threadIdx.x; i < HR * b; i += GT) {
-    const int r = i / b, c = i - r * b;
-    cp_async_elem(sL + r * ldl + c, src + i);
+__host__ __device__ constexpr int stage_ld(int b) { return b + (int)(16 / sizeof(C)); }
+
+__device__ __forceinline__ void mbar_init_s(uint64_t* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_wait_s(uint64_t* bar, uint32_t parity, uint64_t deadline) {
+  uint32_t ok = 0;
+  while (true) {
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if (globaltimer_ns() > deadline) return false;
   }
 }
 
+// Warp 0 issues the 64 row copies of rows [r0, r0 + 64) of a b x b row-major tile.
+template <typename C>
+__device__ __forceinline__ void stage_bulk(C* sL, const C* tile, int b, int r0, uint64_t* bar) {
+  if (threadIdx.x >= 32) return;
+  const uint32_t row_bytes = (uint32_t)(b * sizeof(C));
+  const int ldl = stage_ld<C>(b);
+  if (threadIdx.x == 0)
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(HR * row_bytes)
+                 : "memory");
+  __syncwarp();
+  for (int r = threadIdx.x; r < HR; r += 32)
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(sL + r * ldl)),
+        "l"(tile + (int64_t)(r0 + r) * b), "r"(row_bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
 // ------------------------------------------------------------------ register-blocked tile products
-// Each warp computes 8 outputs for all (<= 8) right-hand sides; the reduction index is split
-// over 4 lanes and summed with shuffles.  One tile element load feeds rc complex FMAs; the
-// vector loads are broadcasts (4 distinct addresses per warp instruction).
+// 8 warps; each warp computes 8 outputs for all (<= 8) right-hand sides with the reduction
+// index split over 4 lanes (summed with shuffles).  One tile element load feeds rc complex
+// FMAs; vector rows use an odd stride so the 4 rows read by a warp fall in distinct banks.
 constexpr int RCMAX = 8;
+
+__host__ __device__ constexpr int vec_ld(int rc) { return rc | 1; }
 
 template <typename C>
 __device__ __forceinline__ void quad_reduce(C* acc) {
 #pragma unroll
-  for (int j = 0; j < RCMAX; ++j) {
-    acc[j].x += __shfl_xor_sync(0xffffffffu, acc[j].x, 1);
-    acc[j].y += __shfl_xor_sync(0xffffffffu, acc[j].y, 1);
-    acc[j].x += __shfl_xor_sync(0xffffffffu, acc[j].x, 2);
-    acc[j].y += __shfl_xor_sync(0xffffffffu, acc[j].y, 2);
-  }
+  for (int j = 0; j < RCMAX; ++j)
+#pragma unroll
+    for (int o = 1; o < 4; o <<= 1) {
+      acc[j].x += __shfl_xor_sync(0xffffffffu, acc[j].x, o);
+      acc[j].y += __shfl_xor_sync(0xffffffffu, acc[j].y, o);
+    }
 }
 
 // dst[r][j] (=, or -=) sum_c M[r][c] V[c][j] for the 64 rows of a staged half tile M
@@ -109,12 +133,15 @@ __device__ __forceinline__ void rows_matvec(const typename CT<R>::C* M, int ldl,
 #pragma unroll
   for (int j = 0; j < RCMAX; ++j) acc[j] = CT<R>::make(0, 0);
   const C* mrow = M + r * ldl;
+#pragma unroll 4
   for (int c = cq; c < b; c += 4) {
     const C m = mrow[c];
     const C* v = V + c * ldv;
+    C vv[RCMAX];
 #pragma unroll
-    for (int j = 0; j < RCMAX; ++j)
-      if (j < rc) acc[j] = cfma(m, v[j], acc[j]);
+    for (int j = 0; j < RCMAX; ++j) vv[j] = (j < rc) ? v[j] : CT<R>::make(0, 0);
+#pragma unroll
+    for (int j = 0; j < RCMAX; ++j) acc[j] = cfma(m, vv[j], acc[j]);
   }
   quad_reduce(acc);
   if (cq == 0) {
@@ -137,12 +164,15 @@ __device__ __forceinline__ void cols_matvec(const typename CT<R>::C* M, int ldl,
     C acc[RCMAX];
 #pragma unroll
     for (int j = 0; j < RCMAX; ++j) acc[j] = CT<R>::make(0, 0);
+#pragma unroll 4
     for (int r = rq; r < HR; r += 4) {
       const C m = M[r * ldl + c];
       const C* v = V + r * ldv;
+      C vv[RCMAX];
 #pragma unroll
-      for (int j = 0; j < RCMAX; ++j)
-        if (j < rc) acc[j] = cfma(m, v[j], acc[j]);
+      for (int j = 0; j < RCMAX; ++j) vv[j] = (j < rc) ? v[j] : CT<R>::make(0, 0);
+#pragma unroll
+      for (int j = 0; j < RCMAX; ++j) acc[j] = cfma(m, vv[j], acc[j]);
     }
     quad_reduce(acc);
     if (rq == 0) {
@@ -163,39 +193,49 @@ __global__ void __launch_bounds__(GT) gather_kernel(const SolveItem* __restrict_
                                                     const typename CT<R>::C* __restrict__ L,
                                                     const typename CT<R>::C* __restrict__ Y,
                                                     typename CT<R>::C* __restrict__ P,
-                                                    int64_t npad, int b, int nrhs) {
+                                                    int64_t npad, int b, int nrhs, int* status) {
   using C = typename CT<R>::C;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int nh = b / HR;
-  const int ldl = b + 1;
-  C* sL = reinterpret_cast<C*>(smem_raw);      // [64][b+1]
-  C* sY = sL + HR * ldl;                       // [rows][nrhs]
+  const int ldl = stage_ld<C>(b);
+  C* sL = reinterpret_cast<C*>(smem_raw);      // [64][ldl]
+  C* sY = sL + HR * ldl;                       // [rows][ldy]
+  const int ldy = vec_ld(nrhs);
+  __shared__ __align__(8) uint64_t bar;
   const SolveItem it = items[blockIdx.x / nh];
   const int h = blockIdx.x % nh;
-  stage_async(sL, L + (int64_t)it.tile * b * b, b, h * HR);
-  cp_commit();
+  if (threadIdx.x == 0) {
+    mbar_init_s(&bar);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  stage_bulk(sL, L + (int64_t)it.tile * b * b, b, h * HR, &bar);
   const int rows = FWD ? b : HR;
   const int64_t y0 = (int64_t)it.src * b + (FWD ? 0 : h * HR);
   for (int i = threadIdx.x; i < rows * nrhs; i += GT) {
     const int k = i % rows, j = i / rows;
-    sY[k * nrhs + j] = Y[j * npad + y0 + k];
+    sY[k * ldy + j] = Y[j * npad + y0 + k];
   }
-  cp_wait_all();
-  __syncthreads();
+  const bool late = !mbar_wait_s(&bar, 0, globaltimer_ns() + SWEEP_TIMEOUT_NS);
+  if (__syncthreads_or(late)) {
+    if (threadIdx.x == 0) atomicExch(status, (int)D3M_ERR_TIMEOUT);
+    return;
+  }
   for (int j0 = 0; j0 < nrhs; j0 += RCMAX) {
     const int rc = min(RCMAX, nrhs - j0);
     if (FWD) {
       C* out = P + (int64_t)it.slot * nh * b * nrhs + (int64_t)h * HR * nrhs + j0;   // sub-slot 0
-      rows_matvec<R, false>(sL, ldl, b, sY + j0, nrhs, rc, out, nrhs);
+      rows_matvec<R, false>(sL, ldl, b, sY + j0, ldy, rc, out, nrhs);
     } else {
       C* out = P + ((int64_t)it.slot * nh + h) * b * nrhs + j0;
-      cols_matvec<R, 0>(sL, ldl, b, sY + j0, nrhs, rc, out, nrhs);
+      cols_matvec<R, 0>(sL, ldl, b, sY + j0, ldy, rc, out, nrhs);
     }
   }
 }
 
 // ------------------------------------------------------------------ in-block chains
 struct BlockSweep {
+  int* status;               // set to D3M_ERR_TIMEOUT if a bounded wait expires
   const int32_t* blocks;     // blocks of this level
   const int32_t* tstart;     // [N+1]
   const int64_t* tcolptr;    // [NT+1]
@@ -205,17 +245,18 @@ struct BlockSweep {
 };
 
 constexpr int MAXJOBS = 512;      // tile jobs of one block chain (nt (nt+1)/2 * b/64)
+constexpr int MAXNT = 32;         // tiles per interface block
 
 // Y(row) -= sum of the row's partials (fixed slot order) for every tile row of one level;
 // one thread per (tile, row, rhs), rhs fastest (coalesced partial reads).
 template <typename R>
-__global__ void __launch_bounds__(GT) reduce_kernel(const int32_t* __restrict__ tiles, int ntl,
+__global__ void __launch_bounds__(ET) reduce_kernel(const int32_t* __restrict__ tiles, int ntl,
                                                     const int64_t* __restrict__ slot_ptr,
                                                     const typename CT<R>::C* __restrict__ P,
                                                     typename CT<R>::C* __restrict__ Y, int64_t npad, int b,
                                                     int nrhs, int nsub) {
   using C = typename CT<R>::C;
-  const int64_t idx = blockIdx.x * (int64_t)GT + threadIdx.x;
+  const int64_t idx = blockIdx.x * (int64_t)ET + threadIdx.x;
   const int j = (int)(idx % nrhs);
   const int64_t rest = idx / nrhs;
   const int row = (int)(rest % b);
@@ -272,66 +313,80 @@ __global__ void __launch_bounds__(GT) block_fwd_kernel(BlockSweep s, const typen
   using C = typename CT<R>::C;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ const C* s_job[MAXJOBS];
-  const int b = s.b, ldl = b + 1, nh = b / HR;
+  const int b = s.b, ldl = stage_ld<C>(b), nh = b / HR;
+  __shared__ __align__(8) uint64_t bars[2];
   const int k = s.blocks[blockIdx.x];
   const int j0 = blockIdx.y * s.rc;
   const int rc = min(s.rc, s.nrhs - j0);
+  const int ldv = vec_ld(s.rc);                // row stride of the running vectors
   const int t0 = s.tstart[k], nt = s.tstart[k + 1] - t0;
   const int rows = nt * b;
   C* sL0 = reinterpret_cast<C*>(smem_raw);     // [64][b+1] x 2
   C* sL1 = sL0 + HR * ldl;
   C* sv = sL1 + HR * ldl;                      // [rows][rc]  running r / y
-  C* sy = sv + (int64_t)rows * s.rc;           // [b][rc]     y_t
+  C* sy = sv + (int64_t)rows * ldv;           // [b][rc]     y_t
   // job list: for t: Linv_t halves, then L_{t', t} halves for t' > t
-  int njobs = 0;
-  if (threadIdx.x == 0) {
-    for (int t = 0; t < nt; ++t) {
-      const int J = t0 + t;
-      for (int h = 0; h < nh; ++h) s_job[njobs++] = Linv + (int64_t)J * b * b + (int64_t)h * HR * b;
-      for (int tp = t + 1; tp < nt; ++tp)
-        for (int h = 0; h < nh; ++h)
-          s_job[njobs++] = L + (s.tcolptr[J] + (tp - t)) * (int64_t)b * b + (int64_t)h * HR * b;
-    }
-  }
-  njobs = 0;
-  for (int t = 0; t < nt; ++t) njobs += nh * (nt - t);
+  // job table: for t, the halves of Linv_t, then of L_{t', t} for t' > t (tile ids of column
+  // t0 + t inside the block are consecutive after its diagonal tile)
+  __shared__ int64_t s_cp[MAXNT];
+  if (threadIdx.x < nt) s_cp[threadIdx.x] = s.tcolptr[t0 + threadIdx.x];
   __syncthreads();
-  stage_async(sL0, s_job[0], b, 0);
-  cp_commit();
-  load_rows(Y, s.npad, (int64_t)t0 * b, rows, j0, rc, s.rc, sv);
+  int njobs = 0;
+  for (int t = 0; t < nt; ++t) njobs += nh * (nt - t);
+  for (int j = threadIdx.x; j < njobs; j += GT) {
+    int t = 0, base = 0;
+    while (base + nh * (nt - t) <= j) base += nh * (nt - t++);
+    const int q = j - base, h = q % nh, tp = t + q / nh;   // tp == t: Linv_t
+    s_job[j] = (tp == t) ? Linv + (int64_t)(t0 + t) * b * b + (int64_t)h * HR * b
+                         : L + (s_cp[t] + (tp - t)) * (int64_t)b * b + (int64_t)h * HR * b;
+  }
+  if (threadIdx.x == 0) {
+    mbar_init_s(&bars[0]);
+    mbar_init_s(&bars[1]);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  stage_bulk(sL0, s_job[0], b, 0, &bars[0]);
+  uint32_t phase[2] = {0u, 0u};
+  const uint64_t deadline = globaltimer_ns() + SWEEP_TIMEOUT_NS;
+  load_rows(Y, s.npad, (int64_t)t0 * b, rows, j0, rc, ldv, sv);
   int job = 0;
   for (int t = 0; t < nt; ++t) {
     for (int q = 0; q < nh * (nt - t); ++q, ++job) {
-      C* cur = (job & 1) ? sL1 : sL0;
+      const int buf = job & 1;
+      C* cur = buf ? sL1 : sL0;
       if (job + 1 < njobs) {
-        stage_async((job & 1) ? sL0 : sL1, s_job[job + 1], b, 0);
-        cp_commit();
-        cp_wait_one();
-      } else {
-        cp_wait_all();
+        // the other buffer was last read in the previous job (which ended with a barrier)
+        if (threadIdx.x < 32) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        stage_bulk(buf ? sL0 : sL1, s_job[job + 1], b, 0, &bars[buf ^ 1]);
       }
-      __syncthreads();
+      const bool late = !mbar_wait_s(&bars[buf], phase[buf], deadline);
+      phase[buf] ^= 1u;
+      if (__syncthreads_or(late)) {
+        if (threadIdx.x == 0) atomicExch(s.status, (int)D3M_ERR_TIMEOUT);
+        return;
+      }
       const int h = q % nh;
       if (q < nh) {
         // y_t rows [h*64, h*64+64) = Linv_t[rows] r_t
-        rows_matvec<R, false>(cur, ldl, b, sv + (int64_t)t * b * s.rc, s.rc, rc, sy + h * HR * s.rc, s.rc);
+        rows_matvec<R, false>(cur, ldl, b, sv + (int64_t)t * b * ldv, ldv, rc, sy + h * HR * ldv, ldv);
         if (q == nh - 1) {
           __syncthreads();
           for (int i = threadIdx.x; i < b * rc; i += GT) {
             const int r = i % b, j = i / b;
-            sv[(t * b + r) * s.rc + j] = sy[r * s.rc + j];
+            sv[(t * b + r) * ldv + j] = sy[r * ldv + j];
           }
         }
       } else {
         const int tp = t + 1 + (q - nh) / nh;
-        rows_matvec<R, true>(cur, ldl, b, sy, s.rc, rc, sv + (int64_t)(tp * b + h * HR) * s.rc, s.rc);
+        rows_matvec<R, true>(cur, ldl, b, sy, ldv, rc, sv + (int64_t)(tp * b + h * HR) * ldv, ldv);
       }
       __syncthreads();
     }
   }
   for (int i = threadIdx.x; i < rows * rc; i += GT) {
     const int row = i % rows, j = i / rows;
-    Y[(int64_t)(j0 + j) * s.npad + (int64_t)t0 * b + row] = sv[row * s.rc + j];
+    Y[(int64_t)(j0 + j) * s.npad + (int64_t)t0 * b + row] = sv[row * ldv + j];
   }
 }
 
@@ -344,67 +399,80 @@ __global__ void __launch_bounds__(GT) block_bwd_kernel(BlockSweep s, const typen
   using C = typename CT<R>::C;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ const C* s_job[MAXJOBS];
-  const int b = s.b, ldl = b + 1, nh = b / HR;
+  const int b = s.b, ldl = stage_ld<C>(b), nh = b / HR;
+  __shared__ __align__(8) uint64_t bars[2];
   const int k = s.blocks[blockIdx.x];
   const int j0 = blockIdx.y * s.rc;
   const int rc = min(s.rc, s.nrhs - j0);
+  const int ldv = vec_ld(s.rc);                // row stride of the running vectors
   const int t0 = s.tstart[k], nt = s.tstart[k + 1] - t0;
   const int rows = nt * b;
   C* sL0 = reinterpret_cast<C*>(smem_raw);
   C* sL1 = sL0 + HR * ldl;
   C* sv = sL1 + HR * ldl;
-  C* sy = sv + (int64_t)rows * s.rc;
-  int njobs = 0;
-  if (threadIdx.x == 0) {
-    for (int t = nt - 1; t >= 0; --t) {
-      const int J = t0 + t;
-      for (int h = 0; h < nh; ++h) s_job[njobs++] = Linv + (int64_t)J * b * b + (int64_t)h * HR * b;
-      for (int tp = 0; tp < t; ++tp)
-        for (int h = 0; h < nh; ++h)
-          s_job[njobs++] = L + (s.tcolptr[t0 + tp] + (t - tp)) * (int64_t)b * b + (int64_t)h * HR * b;
-    }
-  }
-  njobs = 0;
-  for (int t = 0; t < nt; ++t) njobs += nh * (t + 1);
+  C* sy = sv + (int64_t)rows * ldv;
+  // job table: for t = nt-1..0, the halves of Linv_t, then of L_{t, t'} for t' < t
+  __shared__ int64_t s_cp[MAXNT];
+  if (threadIdx.x < nt) s_cp[threadIdx.x] = s.tcolptr[t0 + threadIdx.x];
   __syncthreads();
-  stage_async(sL0, s_job[0], b, 0);
-  cp_commit();
-  load_rows(Y, s.npad, (int64_t)t0 * b, rows, j0, rc, s.rc, sv);
+  int njobs = 0;
+  for (int t = 0; t < nt; ++t) njobs += nh * (t + 1);
+  for (int j = threadIdx.x; j < njobs; j += GT) {
+    int t = nt - 1, base = 0;
+    while (base + nh * (t + 1) <= j) base += nh * (t-- + 1);
+    const int q = j - base, h = q % nh, k = q / nh;        // k == 0: Linv_t; else tile (t, k - 1)
+    s_job[j] = (k == 0) ? Linv + (int64_t)(t0 + t) * b * b + (int64_t)h * HR * b
+                        : L + (s_cp[k - 1] + (t - (k - 1))) * (int64_t)b * b + (int64_t)h * HR * b;
+  }
+  if (threadIdx.x == 0) {
+    mbar_init_s(&bars[0]);
+    mbar_init_s(&bars[1]);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  stage_bulk(sL0, s_job[0], b, 0, &bars[0]);
+  uint32_t phase[2] = {0u, 0u};
+  const uint64_t deadline = globaltimer_ns() + SWEEP_TIMEOUT_NS;
+  load_rows(Y, s.npad, (int64_t)t0 * b, rows, j0, rc, ldv, sv);
   int job = 0;
   for (int t = nt - 1; t >= 0; --t) {
-    for (int i = threadIdx.x; i < b * rc; i += GT) sy[i] = czero<R>();
+    for (int i = threadIdx.x; i < b * ldv; i += GT) sy[i] = czero<R>();
     for (int q = 0; q < nh * (t + 1); ++q, ++job) {
-      C* cur = (job & 1) ? sL1 : sL0;
+      const int buf = job & 1;
+      C* cur = buf ? sL1 : sL0;
       if (job + 1 < njobs) {
-        stage_async((job & 1) ? sL0 : sL1, s_job[job + 1], b, 0);
-        cp_commit();
-        cp_wait_one();
-      } else {
-        cp_wait_all();
+        // the other buffer was last read in the previous job (which ended with a barrier)
+        if (threadIdx.x < 32) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        stage_bulk(buf ? sL0 : sL1, s_job[job + 1], b, 0, &bars[buf ^ 1]);
       }
-      __syncthreads();
+      const bool late = !mbar_wait_s(&bars[buf], phase[buf], deadline);
+      phase[buf] ^= 1u;
+      if (__syncthreads_or(late)) {
+        if (threadIdx.x == 0) atomicExch(s.status, (int)D3M_ERR_TIMEOUT);
+        return;
+      }
       const int h = q % nh;
       if (q < nh) {
         // w_t += Linv_t[rows of half h]^T r_t[rows of half h]
-        cols_matvec<R, 1>(cur, ldl, b, sv + (int64_t)(t * b + h * HR) * s.rc, s.rc, rc, sy, s.rc);
+        cols_matvec<R, 1>(cur, ldl, b, sv + (int64_t)(t * b + h * HR) * ldv, ldv, rc, sy, ldv);
         if (q == nh - 1) {
           __syncthreads();
           for (int i = threadIdx.x; i < b * rc; i += GT) {
             const int r = i % b, j = i / b;
-            sv[(t * b + r) * s.rc + j] = sy[r * s.rc + j];
+            sv[(t * b + r) * ldv + j] = sy[r * ldv + j];
           }
         }
       } else {
         // tile (t0+t, t0+tp): r_tp[c] -= sum_{r in half h} L[r][c] w_t[r]
         const int tp = (q - nh) / nh;
-        cols_matvec<R, 2>(cur, ldl, b, sy + h * HR * s.rc, s.rc, rc, sv + (int64_t)tp * b * s.rc, s.rc);
+        cols_matvec<R, 2>(cur, ldl, b, sy + h * HR * ldv, ldv, rc, sv + (int64_t)tp * b * ldv, ldv);
       }
       __syncthreads();
     }
   }
   for (int i = threadIdx.x; i < rows * rc; i += GT) {
     const int row = i % rows, j = i / rows;
-    Y[(int64_t)(j0 + j) * s.npad + (int64_t)t0 * b + row] = sv[row * s.rc + j];
+    Y[(int64_t)(j0 + j) * s.npad + (int64_t)t0 * b + row] = sv[row * ldv + j];
   }
 }
 
@@ -572,11 +640,11 @@ static int sweep_impl(const SweepLaunch& a, cudaStream_t st) {
   C* Y = (C*)a.Y;
   C* P = (C*)a.P;
   permute_in_kernel<R><<<(unsigned)gblocks, nthreads, 0, st>>>(a.src, a.n, Y, a.npad, a.pad2orig, a.nrhs);
-  const size_t gsm = sizeof(C) * ((size_t)HR * (b + 1) + (size_t)b * a.nrhs);
+  const size_t gsm = sizeof(C) * ((size_t)HR * stage_ld<C>(b) + (size_t)b * vec_ld(a.nrhs));
   // rhs per block kernel: at most 8, fewer if the running vector would not fit in shared memory
   int rc = a.nrhs < 8 ? a.nrhs : 8;
   auto block_smem = [&](int r) {
-    return sizeof(C) * (2 * (size_t)HR * (b + 1) + (size_t)a.max_rows * r + (size_t)b * r);
+    return sizeof(C) * (2 * (size_t)HR * stage_ld<C>(b) + ((size_t)a.max_rows + (size_t)b) * vec_ld(r));
   };
   while (rc > 1 && block_smem(rc) > SWEEP_SMEM_LIMIT) rc = (rc + 1) / 2;
   const size_t bsm = block_smem(rc);
@@ -586,6 +654,7 @@ static int sweep_impl(const SweepLaunch& a, cudaStream_t st) {
   cudaFuncSetAttribute(block_fwd_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bsm);
   cudaFuncSetAttribute(block_bwd_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bsm);
   BlockSweep bs;
+  bs.status = a.status;
   bs.tstart = a.tstart;
   bs.tcolptr = a.tcolptr;
   bs.npad = a.npad;
@@ -598,9 +667,9 @@ static int sweep_impl(const SweepLaunch& a, cudaStream_t st) {
     const int64_t i0 = a.fwd_item_ptr[lv], i1 = a.fwd_item_ptr[lv + 1];
     const int64_t ntl = a.lev_tile_ptr[lv + 1] - a.lev_tile_ptr[lv];
     if (i1 > i0) {
-      gather_kernel<R, true><<<(unsigned)((i1 - i0) * nh), GT, gsm, st>>>(a.fwd_items + i0, L, Y, P, a.npad, b, a.nrhs);
+      gather_kernel<R, true><<<(unsigned)((i1 - i0) * nh), GT, gsm, st>>>(a.fwd_items + i0, L, Y, P, a.npad, b, a.nrhs, a.status);
       const int64_t nthr = ntl * b * a.nrhs;
-      reduce_kernel<R><<<(unsigned)((nthr + GT - 1) / GT), GT, 0, st>>>(a.lev_tiles + a.lev_tile_ptr[lv], (int)ntl,
+      reduce_kernel<R><<<(unsigned)((nthr + ET - 1) / ET), ET, 0, st>>>(a.lev_tiles + a.lev_tile_ptr[lv], (int)ntl,
                                                                      a.fwd_slot_ptr, P, Y, a.npad, b, a.nrhs, 1);
     }
     bs.blocks = a.lev_blocks + a.lev_ptr[lv];
@@ -613,9 +682,9 @@ static int sweep_impl(const SweepLaunch& a, cudaStream_t st) {
     const int64_t i0 = a.bwd_item_ptr[lv], i1 = a.bwd_item_ptr[lv + 1];
     const int64_t ntl = a.lev_tile_ptr[lv + 1] - a.lev_tile_ptr[lv];
     if (i1 > i0) {
-      gather_kernel<R, false><<<(unsigned)((i1 - i0) * nh), GT, gsm, st>>>(a.bwd_items + i0, L, Y, P, a.npad, b, a.nrhs);
+      gather_kernel<R, false><<<(unsigned)((i1 - i0) * nh), GT, gsm, st>>>(a.bwd_items + i0, L, Y, P, a.npad, b, a.nrhs, a.status);
       const int64_t nthr = ntl * b * a.nrhs;
-      reduce_kernel<R><<<(unsigned)((nthr + GT - 1) / GT), GT, 0, st>>>(a.lev_tiles + a.lev_tile_ptr[lv], (int)ntl,
+      reduce_kernel<R><<<(unsigned)((nthr + ET - 1) / ET), ET, 0, st>>>(a.lev_tiles + a.lev_tile_ptr[lv], (int)ntl,
                                                                      a.bwd_slot_ptr, P, Y, a.npad, b, a.nrhs, nh);
     }
     bs.blocks = a.lev_blocks + a.lev_ptr[lv];

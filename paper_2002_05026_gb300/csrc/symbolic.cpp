@@ -202,7 +202,7 @@ int analyze(const d3m_pattern* pat, const int32_t* perm_in, int b, bool build_ta
     for (int64_t t = s.tcolptr[J]; t < s.tcolptr[J + 1]; ++t) {
       int I = s.trow[t], p = s.tblk[I];
       int64_t nk = J - s.tstart[q];
-      int64_t ns = (J > s.tstart[q]) ? 1 : 0;
+      int64_t ns = (nk >= 2) ? 2 : nk;
       const auto& rp = s.rowlist[p];
       const auto& rq = s.rowlist[q];
       if (p == q) {
@@ -216,8 +216,10 @@ int analyze(const d3m_pattern* pat, const int32_t* perm_in, int b, bool build_ta
         }
       }
       s.n_tile_updates += nk;
-      // segment sources, the chain between segments, and the diagonal tile for a TRSM
-      s.n_edges += ((I == J) ? nk : 2 * nk) + (ns > 1 ? ns - 1 : 0) + (I == J ? 0 : 1);
+      // segment sources, the chain of update tasks into the final task, and the diagonal tile
+      // for a triangular solve (off-diagonal tiles give every segment to an update task)
+      if (I == J) s.n_edges += nk + (ns > 1 ? ns - 1 : 0);
+      else s.n_edges += 2 * nk + ns + 1;
     }
   }
   if (!build_tasks) return D3M_OK;
@@ -243,13 +245,23 @@ int analyze(const d3m_pattern* pat, const int32_t* perm_in, int b, bool build_ta
       int64_t nk = J - s.tstart[q];
       for (int k : ks) nk += s.ntile[k];
       kl_ptr[t + 1] = nk;
-      nseg[t] = (int32_t)ks.size() + (J > s.tstart[q] ? 1 : 0);
+      // the in-block part is cut into [tstart, J-1) and [J-1, J): the last tile column K = J-1
+      // becomes ready last (it is on the critical path), the others earlier
+      const int nib = J - s.tstart[q];
+      nseg[t] = (int32_t)ks.size() + (nib >= 2 ? 2 : nib);
     }
   }
   for (int64_t t = 0; t < ntiles; ++t) kl_ptr[t + 1] += kl_ptr[t];
   s.klist.resize(kl_ptr[ntiles]);
+  // update tasks per tile: off-diagonal tiles hand every segment to UPDATE tasks so that their
+  // final task (staging + triangular solve) is all that waits for the diagonal tile; a diagonal
+  // tile keeps its last segment in its final task
+  std::vector<uint8_t> offd(ntiles, 0);
+  for (int J = 0; J < s.NT; ++J)
+    for (int64_t t = s.tcolptr[J]; t < s.tcolptr[J + 1]; ++t) offd[t] = (s.trow[t] != J);
+  auto n_upd = [&](int64_t t) -> int64_t { return offd[t] ? nseg[t] : std::max(0, nseg[t] - 1); };
   int64_t nupd = 0;
-  for (int64_t t = 0; t < ntiles; ++t) nupd += std::max(0, nseg[t] - 1);
+  for (int64_t t = 0; t < ntiles; ++t) nupd += n_upd(t);
   const int64_t ntask = ntiles + nupd;
   if (ntask >= (int64_t)1 << 31) return fail(err, "too many tasks for 32-bit task ids");
   s.tasks.resize(ntask);
@@ -260,7 +272,7 @@ int analyze(const d3m_pattern* pat, const int32_t* perm_in, int b, bool build_ta
   {
     int64_t nextu = ntiles;
     for (int64_t t = 0; t < ntiles; ++t)
-      if (nseg[t] > 1) { upd_first[t] = nextu; nextu += nseg[t] - 1; }
+      if (n_upd(t) > 0) { upd_first[t] = nextu; nextu += n_upd(t); }
   }
   // dependencies per task id, then successor lists (CSR)
   std::vector<std::vector<int32_t>> tdeps(ntask);
@@ -281,8 +293,12 @@ int analyze(const d3m_pattern* pat, const int32_t* perm_in, int b, bool build_ta
         for (int K = s.tstart[k]; K < s.tstart[k + 1]; ++K) push(K);
         sb.push_back(w);
       }
+      if (J - s.tstart[q] >= 2) {
+        for (int K = s.tstart[q]; K < J - 1; ++K) push(K);
+        sb.push_back(w);
+      }
       if (J > s.tstart[q]) {
-        for (int K = s.tstart[q]; K < J; ++K) push(K);
+        push(J - 1);
         sb.push_back(w);
       }
       const int ns = (int)sb.size() - 1;           // == nseg[t]
@@ -306,27 +322,40 @@ int analyze(const d3m_pattern* pat, const int32_t* perm_in, int b, bool build_ta
       const int32_t* it = std::lower_bound(first, last, srow);
       if (it != last && *it == srow) base.k_off = s.kblk_off[s.colptr[scol] + (it - first)];
       base.flags = (I == J ? TF_DIAG : 0) | (p == q ? TF_SAME_BLOCK : 0);
-      base.sidx = ns > 1 ? (int32_t)(s.n_acc++) : -1;
+      const int nu = (int)n_upd(t);                 // update tasks of this tile
+      base.sidx = nu > 0 ? (int32_t)(s.n_acc++) : -1;
       auto seg_deps = [&](int sg, std::vector<int32_t>& d) {
         for (int64_t e = sb[sg]; e < sb[sg + 1]; ++e) {
           d.push_back(s.klist[e].a_tile);
           if (I != J) d.push_back(s.klist[e].b_tile);
         }
       };
-      for (int sg = 0; sg < std::max(ns, 1); ++sg) {
-        const bool final_task = (sg == std::max(ns, 1) - 1);
-        const int64_t id = final_task ? t : upd_first[t] + sg;
+      // update tasks: segments 0..nu-1, chained
+      for (int sg = 0; sg < nu; ++sg) {
+        const int64_t id = upd_first[t] + sg;
         TileTask T = base;
-        T.kl_off = ns > 0 ? sb[sg] : kl_ptr[t];
-        T.nk = ns > 0 ? (int32_t)(sb[sg + 1] - sb[sg]) : 0;
-        if (!final_task) T.flags |= TF_UPDATE;
-        if (sg > 0) T.flags |= TF_S_IN;
+        T.kl_off = sb[sg];
+        T.nk = (int32_t)(sb[sg + 1] - sb[sg]);
+        T.flags |= TF_UPDATE | (sg > 0 ? TF_S_IN : 0);
         s.tasks[id] = T;
         auto& d = tdeps[id];
-        if (ns > 0) seg_deps(sg, d);
-        if (sg > 0) d.push_back((int32_t)(upd_first[t] + sg - 1));
-        if (final_task && I != J) d.push_back(s.diag_tile[J]);
+        seg_deps(sg, d);
+        if (sg > 0) d.push_back((int32_t)(id - 1));
         s.ndeps[id] = (int32_t)d.size();
+      }
+      // final task: the remaining segment (diagonal tile only), then factor / triangular solve
+      {
+        TileTask T = base;
+        const bool has_seg = nu < ns;
+        T.kl_off = has_seg ? sb[nu] : kl_ptr[t];
+        T.nk = has_seg ? (int32_t)(sb[nu + 1] - sb[nu]) : 0;
+        if (nu > 0) T.flags |= TF_S_IN;
+        s.tasks[t] = T;
+        auto& d = tdeps[t];
+        if (has_seg) seg_deps(nu, d);
+        if (nu > 0) d.push_back((int32_t)(upd_first[t] + nu - 1));
+        if (I != J) d.push_back(s.diag_tile[J]);
+        s.ndeps[t] = (int32_t)d.size();
       }
     }
   }
