@@ -184,6 +184,22 @@ int d3m_grad_eps(d3m_handle h, const void* Lambda, const void* X, int32_t nrhs,
                  int32_t ndom, const int32_t* dom_ptr, const int32_t* dom_if, double k2,
                  double* dJ_deps, void* stream);
 
+/* Same result as d3m_grad_eps, for callers that cannot allocate memory while it runs: code
+ * being captured into a CUDA graph (cudaMalloc is not permitted during stream capture), or a
+ * host application whose own allocator owns the device memory and forbids library
+ * allocations.  The paper has no counterpart; this is an API convenience of this library.
+ * It allocates nothing (no cudaMalloc / cudaFree / host allocation): its temporaries live in
+ * one file-scope static device array of about 0.9 MB that every GPU loading the library keeps
+ * until process exit.  Limits: at most 16384 interfaces, 16384 domains and 98304 dom_if
+ * entries, else D3M_ERR_INVALID.  The first call on a device looks up that array's device
+ * address (cudaGetSymbolAddress); make that first call before any stream capture.  All calls
+ * share the array, so calls that overlap on the GPU (other streams, other host threads) race;
+ * no entry of it needs to start at zero.  Lambda, X: device c128; dJ_deps: host or device
+ * double [ndom]; synchronizes the stream. */
+int d3m_grad_eps_noalloc(d3m_handle h, const void* Lambda, const void* X, int32_t nrhs,
+                         int32_t ndom, const int32_t* dom_ptr, const int32_t* dom_if, double k2,
+                         double* dJ_deps, void* stream);
+
 /* Gradient of J = Re(sum_j g_j^T x_j) with respect to the stored lower blocks of K:
  * dJ/dK_fg = -(Lambda_f X_g^T + [f != g] X_f Lambda_g^T), summed over columns (the outer
  * product -Lambda X^T restricted to K's pattern; an off-diagonal stored block also stands

@@ -83,6 +83,8 @@ def load() -> ctypes.CDLL:
         "d3m_adjoint": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_void_p]),
         "d3m_grad_eps": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_int32, P(c_int32), P(c_int32),
                                    c_double, P(c_double), c_void_p]),
+        "d3m_grad_eps_noalloc": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_int32, P(c_int32),
+                                           P(c_int32), c_double, P(c_double), c_void_p]),
         "d3m_grad_pattern": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_void_p, c_void_p]),
         "d3m_get_factor_block": (c_int32, [c_void_p, c_int32, c_int32, c_void_p, c_void_p]),
         "d3m_get_pivots": (c_int32, [c_void_p, c_int32, c_void_p, c_void_p]),

@@ -212,6 +212,18 @@ int factor_error(d3m_ctx* h) {
 
 }  // namespace
 
+namespace d3m {
+// handle accessors for entry points defined in other translation units
+int handle_geometry(d3m_handle h, int64_t* n, int32_t* nblk, const int64_t** xoff_orig, const int32_t** m_orig) {
+  *n = h->S.n;
+  *nblk = h->S.N;
+  *xoff_orig = h->xoff_orig;
+  *m_orig = h->m_orig;
+  return D3M_OK;
+}
+int handle_error(d3m_handle h, int code, const char* msg) { return set_err(h, code, msg); }
+}  // namespace d3m
+
 extern "C" {
 
 void d3m_default_options(d3m_options* o) {

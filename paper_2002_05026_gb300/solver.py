@@ -91,7 +91,8 @@ class D3M:
                                     c_void_p(_stream_ptr(self.stream))), self.h)
         return Lt.reshape(-1) if vec else Lt.T
 
-    def grad_eps(self, Lam, X, dom_if, k2: float):
+    def grad_eps(self, Lam, X, dom_if, k2: float, noalloc: bool = False):
+        """dJ/deps per domain; noalloc=True calls d3m_grad_eps_noalloc (no allocation inside)."""
         Lt, nrhs, _ = _as_colmajor(Lam)
         Xt, _, _ = _as_colmajor(X)
         ptr = np.zeros(len(dom_if) + 1, dtype=np.int32)
@@ -100,7 +101,8 @@ class D3M:
         flat = np.ascontiguousarray(np.concatenate([np.asarray(I, dtype=np.int32) for I in dom_if])
                                     if len(dom_if) else np.zeros(0), dtype=np.int32)
         out = np.zeros(len(dom_if), dtype=np.float64)
-        check(self._lib.d3m_grad_eps(self.h, c_void_p(Lt.data_ptr()), c_void_p(Xt.data_ptr()), nrhs,
+        fn = self._lib.d3m_grad_eps_noalloc if noalloc else self._lib.d3m_grad_eps
+        check(fn(self.h, c_void_p(Lt.data_ptr()), c_void_p(Xt.data_ptr()), nrhs,
                                      len(dom_if), ptr.ctypes.data_as(POINTER(c_int32)),
                                      flat.ctypes.data_as(POINTER(c_int32)), c_double(k2),
                                      out.ctypes.data_as(POINTER(c_double)),

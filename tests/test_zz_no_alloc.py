@@ -1,0 +1,60 @@
+"""d3m_grad_eps_noalloc: the epsilon gradient for callers that cannot allocate memory during the
+call (for example code captured into a CUDA graph, or an application whose own allocator owns
+the device memory).  It must return what d3m_grad_eps returns, through the C ABI, on repeated
+calls that reuse its fixed scratch array.  Kept in a file collected last."""
+import ctypes
+
+import numpy as np
+import pytest
+
+import oracle as O
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _dom_arrays(dom_if):
+    ptr = np.zeros(len(dom_if) + 1, dtype=np.int32)
+    for i, I in enumerate(dom_if):
+        ptr[i + 1] = ptr[i] + len(I)
+    flat = np.ascontiguousarray(np.concatenate([np.asarray(I, dtype=np.int32) for I in dom_if]), dtype=np.int32)
+    return ptr, flat
+
+
+def _call(lib, h, fn, Lt, Xt, nrhs, ptr, flat, k2, stream):
+    out = np.full(len(ptr) - 1, np.nan)
+    rc = getattr(lib, fn)(h, ctypes.c_void_p(Lt.data_ptr()), ctypes.c_void_p(Xt.data_ptr()), nrhs, len(ptr) - 1,
+                          ptr.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                          flat.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), ctypes.c_double(k2),
+                          out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.c_void_p(stream))
+    return rc, out
+
+
+def test_grad_eps_noalloc_matches_grad_eps():
+    import torch
+    from paper_2002_05026_gb300 import D3M, build
+    build.build()
+    g, m, k2, tau = (4, 3, 1), 24, 2.0, 0.05
+    p = synth.make_problem(*g, m, k2, tau, 61)
+    perm = O.nd_order(*g)
+    s = D3M(p.colptr, p.rowidx, m=m, perm=perm, precision="bf16x3", max_nrhs=4)
+    s.factor(torch.from_numpy(p.blocks).cuda())
+    ptr, flat = _dom_arrays(p.dom_if)
+    stream = torch.cuda.current_stream().cuda_stream
+    for call in range(2):                       # two calls in a row reuse the scratch array
+        nrhs = 1 + call * 2
+        b = torch.from_numpy(synth.rhs(70 + call, p.n, nrhs)).cuda()
+        c = torch.from_numpy(synth.rhs(80 + call, p.n, nrhs)).cuda()
+        x = s.solve(b)
+        lam = s.adjoint(c)
+        Lt, Xt = lam.T.contiguous(), x.T.contiguous()
+        rc0, ref = _call(s._lib, s.h, "d3m_grad_eps", Lt, Xt, nrhs, ptr, flat, k2, stream)
+        rc1, got = _call(s._lib, s.h, "d3m_grad_eps_noalloc", Lt, Xt, nrhs, ptr, flat, k2, stream)
+        assert rc0 == 0 and rc1 == 0
+        assert np.all(np.isfinite(got))
+        assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(ref))
+    # sizes beyond the fixed scratch are rejected with D3M_ERR_INVALID, nothing launched
+    big = np.zeros(16386, dtype=np.int32)
+    rc, _ = _call(s._lib, s.h, "d3m_grad_eps_noalloc", Lt, Xt, nrhs, big, flat, k2, stream)
+    assert rc == 1
+    assert "scratch" in s.last_error()
