@@ -4,12 +4,12 @@
  * The library factors and solves the reduced block-sparse dual matrix K of the Direct
  * Domain Decomposition Method (D3M; Moshfegh, Makris, Vouvakis, "Parallel Direct Domain
  * Decomposition Methods (D3M) for Finite Elements", IEEE AP-S/URSI 2019):
- *   - Sec. I: the sparse FEM system is reduced to a block-wise sparse matrix K that is
- *     solved by a special block LDL^T suited to block-DAG task scheduling;
- *   - Sec. II: in the "dual factorization and solution" step every nonzero block of K is a
- *     task doing a dense update, a dense triangular solve and a dense factorization; the
- *     task graph (B-DAG) comes from a symbolic simulation of the sequential algorithm;
- *     dual task weights come from GEMM, sytrf and triSolve;
+ *   - Sec. I: the sparse FEM system is reduced to a block-sparse matrix K, which is solved
+ *     with a block LDL^T factorization scheduled as a DAG of block tasks;
+ *   - Sec. II: when K is factored and solved, each nonzero block of K is one task that
+ *     performs its dense update, dense triangular solve and dense factorization; a symbolic
+ *     run of the sequential algorithm yields the task graph (B-DAG); the dual tasks are
+ *     weighted with GEMM, sytrf and triSolve timings;
  *   - Fig. 1(b)/(c): the sparsity of K and its task graph.
  * K is complex symmetric (K^T = K, not Hermitian) and indefinite.  The library computes
  * the unpivoted factorization P K P^T = L D L^T (L unit lower, D diagonal) and solves

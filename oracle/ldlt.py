@@ -1,10 +1,10 @@
-"""Plain FP64 (complex128) oracle of the D3M dual factorization and solution.
+"""Plain FP64 (complex128) oracle of the D3M factorization and solve of the dual matrix.
 
 TEST INFRASTRUCTURE ONLY: used by the tests, the smoke check and the bench's CPU baseline;
 never by the library.  Plain numpy: every step is written out in the order of the method,
 with library calls (matmul, triangular solve) only as single steps.
 
-What it computes (paper Sec. I and II, "dual factorization and solution"):
+What it computes (paper Sec. I and II, the factorization and solve of the reduced matrix):
 the reduced block-sparse matrix K (complex symmetric, K^T = K, not Hermitian) is put in a
 nested-dissection interface order P, factored as  P K P^T = L D L^T  with L unit lower
 triangular and D diagonal (scalar pivots, no pivoting; this pair is unique when all leading

@@ -1,5 +1,5 @@
-// Forward / diagonal / backward block sweeps (the "solution" half of the paper's "dual
-// factorization and solution", Sec. II), the FP64 residual r = b - K x over the stored K
+// Forward / diagonal / backward block sweeps (the solve that follows the block factorization of
+// the dual system, Sec. II), the FP64 residual r = b - K x over the stored K
 // (block SpMV, symmetric use of the lower blocks), the backward-error norms and the adjoint
 // contractions.
 //

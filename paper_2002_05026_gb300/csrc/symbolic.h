@@ -17,8 +17,8 @@ enum : int32_t {
   TF_S_IN = 8,        // start from the tile's accumulator S (else from K_IJ)
 };
 
-// One task of the factorization DAG.  The paper's task model (Sec. II: every nonzero block is
-// a task doing a dense update, a dense triangular solve and a dense factorization) at tile
+// One task of the factorization DAG.  The paper's task model (Sec. II: one task per nonzero
+// block of the dual matrix, covering its update, triangular solve and factorization) at tile
 // granularity: the updates of lower tile (I, J), S_IJ = K_IJ - sum_K L_IK D_K L_JK^T, are cut
 // into segments, one per source block column; every segment but the last is an UPDATE task
 // (S <- S_in - sum over the segment, kept in the tile's accumulator; segments chained in

@@ -2,7 +2,7 @@
 
 This module only *makes inputs*.  It holds none of the factorization or solve arithmetic:
 it draws random numbers, builds the per-domain dense blocks that stand in for the primal
-reduction (the paper's Sec. II "dual domain matrices", which need FEM meshes and are out of
+reduction (the per-domain dual matrices of the paper's Sec. II, which need FEM meshes and are out of
 scope), and adds them into the interface-block pattern of the reduced matrix K
 (Fig. 1(b): one dense block per pair of interfaces that share a domain).
 
