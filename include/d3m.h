@@ -87,6 +87,10 @@ typedef struct {
   int32_t fp64_omega;       /* D3M_FP64 only: 1 = also compute omega after the solve
                                (one FP64 residual; default 0) */
   int32_t debug_flags;      /* D3M_DEBUG_* test hooks, 0 in normal use */
+  int32_t graphs;           /* 1 = capture each launch sequence (factorization with K in device
+                               memory; one refinement step of a solve) into a CUDA graph on
+                               first use and replay it afterwards; default 0 */
+  int32_t reserved0;
 } d3m_options;
 
 /* Test hook: upload the task graph with one extra unmet dependency on the last task, so the
@@ -130,6 +134,8 @@ typedef struct {
   double residual_ms_total;
   double sweep_ms_total;
   int64_t factor_kernel_calls, residual_calls, sweep_calls;
+  int32_t instances;        /* independent systems held by the handle (1 unless batched) */
+  int32_t reserved0;
 } d3m_info;
 
 /* Default options (precision D3M_MIXED_BF16X3). */
@@ -155,6 +161,27 @@ int d3m_analyze(const d3m_pattern* pat, const int32_t* perm, int32_t tile, d3m_i
  * device buffer on the current device.  `opt` NULL = defaults. */
 int d3m_create(d3m_handle* out, const d3m_pattern* pat, const int32_t* perm,
                const d3m_options* opt, void* stream);
+
+/* Batched solver: `count` independent systems (instances, e.g. frequency points or different
+ * domain grids, each with its own pattern, block sizes and perms[i]; perms NULL or perms[i]
+ * NULL = identity) held as ONE block-diagonal system.  Every later call works on all instances
+ * at once: d3m_factor runs a single persistent launch whose device queue holds the task graphs
+ * of all instances (they share no task, so they interleave freely and fill the GPU), and each
+ * level of a solve sweep covers that level of every instance.  Layouts are the instances'
+ * own, concatenated in instance order: K = the lower blocks of instance 0 in its pattern
+ * order, then those of instance 1, ...; B and X are n x nrhs column-major with
+ * n = sum n_i and instance i's unknowns at rows [sum_{j<i} n_j, ... + n_i) of every column
+ * (so every instance takes the same nrhs).  Refinement stops when the backward error of EVERY
+ * instance and column is <= refine_tol (omega is computed per instance, with ||K_i||, so a
+ * badly scaled instance cannot hide behind another); d3m_get_instance_omega returns them.
+ * Same errors as d3m_create, D3M_ERR_INVALID naming the first bad instance. */
+int d3m_create_batch(d3m_handle* out, int32_t count, const d3m_pattern* pats,
+                     const int32_t* const* perms, const d3m_options* opt, void* stream);
+
+/* Backward error of every instance after the last d3m_solve / d3m_adjoint (max over its
+ * columns; NaN if no omega was computed, e.g. D3M_FP64 without fp64_omega).  host_out has
+ * d3m_info.instances entries.  Synchronizes `stream`. */
+int d3m_get_instance_omega(d3m_handle h, double* host_out, void* stream);
 
 /* Numeric factorization.  K: c128 lower blocks as described above (host or device).  The
  * library copies K, then runs one persistent kernel whose blocks pull ready tile tasks from

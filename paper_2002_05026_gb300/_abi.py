@@ -41,7 +41,7 @@ class d3m_pattern(ctypes.Structure):
 class d3m_options(ctypes.Structure):
     _fields_ = [("precision", c_int32), ("refine_max_iter", c_int32), ("refine_tol", c_double),
                 ("timeout_ns", c_int64), ("tile", c_int32), ("max_nrhs", c_int32),
-                ("fp64_omega", c_int32), ("debug_flags", c_int32)]
+                ("fp64_omega", c_int32), ("debug_flags", c_int32), ("graphs", c_int32), ("reserved0", c_int32)]
 
 
 class d3m_info(ctypes.Structure):
@@ -55,7 +55,8 @@ class d3m_info(ctypes.Structure):
                 ("factor_kernel_ms", c_double), ("solve_ms", c_double), ("residual_ms", c_double),
                 ("kernel_launches", c_int64), ("factor_kernel_ms_total", c_double),
                 ("residual_ms_total", c_double), ("sweep_ms_total", c_double),
-                ("factor_kernel_calls", c_int64), ("residual_calls", c_int64), ("sweep_calls", c_int64)]
+                ("factor_kernel_calls", c_int64), ("residual_calls", c_int64), ("sweep_calls", c_int64),
+                ("instances", c_int32), ("reserved0", c_int32)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -78,6 +79,9 @@ def load() -> ctypes.CDLL:
         "d3m_order_grid_nd": (c_int32, [c_int32, c_int32, c_int32, P(c_int32)]),
         "d3m_analyze": (c_int32, [P(d3m_pattern), P(c_int32), c_int32, P(d3m_info)]),
         "d3m_create": (c_int32, [P(c_void_p), P(d3m_pattern), P(c_int32), P(d3m_options), c_void_p]),
+        "d3m_create_batch": (c_int32, [P(c_void_p), c_int32, P(d3m_pattern), P(P(c_int32)), P(d3m_options),
+                                       c_void_p]),
+        "d3m_get_instance_omega": (c_int32, [c_void_p, P(c_double), c_void_p]),
         "d3m_factor": (c_int32, [c_void_p, c_void_p, c_void_p]),
         "d3m_solve": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_void_p]),
         "d3m_adjoint": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_void_p]),

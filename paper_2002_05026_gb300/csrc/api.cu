@@ -72,6 +72,7 @@ struct d3m_ctx {
   std::vector<int64_t> lev_ptr;
   int32_t* lev_tiles = nullptr;
   std::vector<int64_t> lev_tile_ptr;
+  std::vector<int32_t> lev_maxnt;    // most tiles of one block, per level
   int32_t* tstart = nullptr;
   int64_t* tcolptr = nullptr;
   int64_t* pad2orig = nullptr;
@@ -92,8 +93,8 @@ struct d3m_ctx {
   int64_t* xoff_orig = nullptr;
   int2* chunks = nullptr;
   int nchunks = 0;
-  unsigned* norms = nullptr;         // [3 * max_nrhs + 1]: rmax, xmax, bmax, kmax
-  double* omega_dev = nullptr;       // [max_nrhs]
+  unsigned* norms = nullptr;         // [3 * ninst * max_nrhs + ninst]: rmax, xmax, bmax, kmax
+  double* omega_dev = nullptr;       // [ninst][max_nrhs]
   double* stat_dev = nullptr;        // [1]
   int* sweep_status = nullptr;       // device: set by a sweep kernel whose bounded wait expired
   double* h_stat = nullptr;          // pinned [1]
@@ -102,6 +103,17 @@ struct d3m_ctx {
   int32_t* blk_col = nullptr;
   int64_t* colptr = nullptr;
   double2* contract = nullptr;
+  // batched handles: independent systems stored as one block-diagonal system
+  int ninst = 1;
+  std::vector<int32_t> inst_blk;     // [ninst+1] first block (caller numbering) of each instance
+  int32_t* inst = nullptr;           // device [N]: instance of every block
+  int last_nrhs = 0;                 // nrhs of the last solve (for the per-instance omega)
+  // CUDA graphs (opt.graphs): launch sequences captured once on a private stream, replayed on
+  // the caller's stream; keyed by what the captured pointers and sizes depend on
+  cudaStream_t cap = nullptr;
+  bool capturing = false;
+  struct Graph { const void* src; int nrhs, accumulate; cudaGraphExec_t exec; int64_t launches; };
+  std::vector<Graph> g_factor, g_solve;
 };
 
 namespace {
@@ -136,6 +148,7 @@ cudaEvent_t ev_get(d3m_ctx* h) {
 }
 
 void ev_begin(d3m_ctx* h, int kind, cudaStream_t st) {
+  if (h->capturing) return;          // captured work is timed around its graph launch
   d3m_ctx::EvPair& p = h->ev_open[kind];
   p.a = ev_get(h);
   p.b = ev_get(h);
@@ -144,6 +157,7 @@ void ev_begin(d3m_ctx* h, int kind, cudaStream_t st) {
 }
 
 void ev_end(d3m_ctx* h, int kind, cudaStream_t st) {
+  if (h->capturing) return;
   d3m_ctx::EvPair& p = h->ev_open[kind];
   if (!p.a || !p.b) return;
   cudaEventRecord(p.b, st);
@@ -179,6 +193,49 @@ bool is_device_ptr(const void* p) {
     return false;
   }
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Replay (capturing on first use) the launch sequence `body` for key (src, nrhs, accumulate).
+// The body enqueues on the stream it is given; h->launches counts its kernels once per replay.
+template <typename F>
+int graph_run(d3m_ctx* h, std::vector<d3m_ctx::Graph>& cache, const void* src, int nrhs, int accumulate,
+              cudaStream_t st, F body) {
+  d3m_ctx::Graph* g = nullptr;
+  for (auto& c : cache)
+    if (c.src == src && c.nrhs == nrhs && c.accumulate == accumulate) g = &c;
+  if (!g) {
+    if (!h->cap && cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) != cudaSuccess)
+      return set_err(h, D3M_ERR_CUDA, "cannot create the capture stream");
+    const int64_t l0 = h->launches;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    if (cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeRelaxed) != cudaSuccess)
+      return set_err(h, D3M_ERR_CUDA, "cudaStreamBeginCapture failed");
+    h->capturing = true;
+    const int rc = body(h->cap);
+    h->capturing = false;
+    const cudaError_t e = cudaStreamEndCapture(h->cap, &graph);
+    if (rc != D3M_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return rc;
+    }
+    if (e != cudaSuccess || cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      cudaGetLastError();
+      return set_err(h, D3M_ERR_CUDA, "graph capture failed");
+    }
+    cudaGraphDestroy(graph);
+    if (cache.size() >= 8) {           // bounded cache: drop the oldest
+      cudaGraphExecDestroy(cache.front().exec);
+      cache.erase(cache.begin());
+    }
+    cache.push_back({src, nrhs, accumulate, exec, h->launches - l0});
+    h->launches = l0;
+    g = &cache.back();
+  }
+  CUDA_TRY(h, cudaGraphLaunch(g->exec, st));
+  h->launches += g->launches;
+  return D3M_OK;
 }
 
 void fill_structure(const Symbolic& S, d3m_info* info) {
@@ -237,6 +294,7 @@ void d3m_default_options(d3m_options* o) {
   o->max_nrhs = 32;
   o->fp64_omega = 0;
   o->debug_flags = 0;
+  o->graphs = 0;
 }
 
 int d3m_order_grid_nd(int32_t nx, int32_t ny, int32_t nz, int32_t* perm) {
@@ -261,13 +319,17 @@ int d3m_analyze(const d3m_pattern* pat, const int32_t* perm, int32_t tile, d3m_i
   return D3M_OK;
 }
 
-int d3m_create(d3m_handle* out, const d3m_pattern* pat, const int32_t* perm, const d3m_options* opt,
-               void* stream) {
-  (void)stream;
+}  // extern "C"
+
+// Shared by d3m_create and d3m_create_batch; inst_blk (batched handles) holds the first block
+// of every instance in the caller's numbering.
+static int create_impl(d3m_handle* out, const d3m_pattern* pat, const int32_t* perm, const d3m_options* opt,
+                       const std::vector<int32_t>* inst_blk) {
   if (!out) return set_err(nullptr, D3M_ERR_INVALID, "out is NULL");
   *out = nullptr;
   d3m_ctx* h = new (std::nothrow) d3m_ctx();
   if (!h) return set_err(nullptr, D3M_ERR_OOM, "host allocation failed");
+  if (inst_blk) h->inst_blk = *inst_blk;
   if (opt) h->opt = *opt;
   else d3m_default_options(&h->opt);
   const int prec = h->opt.precision;
@@ -384,6 +446,12 @@ int d3m_create(d3m_handle* out, const d3m_pattern* pat, const int32_t* perm, con
       h->lev_tile_ptr.push_back((int64_t)lt.size());
     }
     UPLOAD(h->lev_tiles, lt);
+    h->lev_maxnt.clear();
+    for (const auto& l : S.lev_blocks) {
+      int mx = 1;
+      for (int k : l) mx = std::max(mx, S.ntile[k]);
+      h->lev_maxnt.push_back(mx);
+    }
     std::vector<int64_t> p2o(S.npad, -1);
     for (int k = 0; k < S.N; ++k)
       for (int u = 0; u < S.m[k]; ++u) p2o[S.xoff[k] + u] = S.xoff_orig[S.perm[k]] + u;
@@ -431,8 +499,17 @@ int d3m_create(d3m_handle* out, const d3m_pattern* pat, const int32_t* perm, con
   }
   UPLOAD(h->rowidx, S.rowidx);
   UPLOAD(h->colptr, S.colptr);
-  ALLOC(h->norms, unsigned, 3 * mr + 1);
-  ALLOC(h->omega_dev, double, mr);
+  {
+    // instance of every block (caller numbering); one instance unless batched
+    std::vector<int32_t> ib(S.N, 0);
+    if (h->inst_blk.empty()) h->inst_blk = {0, S.N};
+    h->ninst = (int)h->inst_blk.size() - 1;
+    for (int i = 0; i < h->ninst; ++i)
+      for (int f = h->inst_blk[i]; f < h->inst_blk[i + 1]; ++f) ib[f] = i;
+    UPLOAD(h->inst, ib);
+  }
+  ALLOC(h->norms, unsigned, 3 * (size_t)h->ninst * mr + h->ninst);
+  ALLOC(h->omega_dev, double, (size_t)h->ninst * mr);
   ALLOC(h->stat_dev, double, 1);
   ALLOC(h->sweep_status, int, 1);
   CUDA_TRY(h, cudaMemset(h->sweep_status, 0, sizeof(int)));
@@ -440,6 +517,74 @@ int d3m_create(d3m_handle* out, const d3m_pattern* pat, const int32_t* perm, con
   CUDA_TRY(h, cudaMallocHost(&h->h_stat, sizeof(double)));
 #undef ALLOC
 #undef UPLOAD
+  return D3M_OK;
+}
+
+extern "C" {
+
+int d3m_create(d3m_handle* out, const d3m_pattern* pat, const int32_t* perm, const d3m_options* opt,
+               void* stream) {
+  (void)stream;
+  return create_impl(out, pat, perm, opt, nullptr);
+}
+
+int d3m_create_batch(d3m_handle* out, int32_t count, const d3m_pattern* pats, const int32_t* const* perms,
+                     const d3m_options* opt, void* stream) {
+  (void)stream;
+  if (!out) return set_err(nullptr, D3M_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  if (count < 1 || !pats) return set_err(nullptr, D3M_ERR_INVALID, "count must be >= 1 and pats non-NULL");
+  // block-diagonal union: instance i's blocks follow those of instances < i
+  std::vector<int32_t> bsz, rowidx, perm, inst_blk(1, 0);
+  std::vector<int64_t> colptr(1, 0);
+  for (int i = 0; i < count; ++i) {
+    const d3m_pattern& q = pats[i];
+    if (q.nblk < 1 || !q.colptr || !q.rowidx || (!q.blk_size && q.m < 1))
+      return set_err(nullptr, D3M_ERR_INVALID, "instance " + std::to_string(i) + ": bad pattern");
+    const int32_t off = inst_blk.back();
+    const int64_t eoff = colptr.back();
+    if (q.colptr[0] != 0 || q.colptr[q.nblk] < q.colptr[0])
+      return set_err(nullptr, D3M_ERR_INVALID, "instance " + std::to_string(i) + ": bad colptr");
+    for (int k = 0; k < q.nblk; ++k) {
+      bsz.push_back(q.blk_size ? q.blk_size[k] : q.m);
+      if (q.colptr[k + 1] < q.colptr[k])
+        return set_err(nullptr, D3M_ERR_INVALID, "instance " + std::to_string(i) + ": bad colptr");
+      colptr.push_back(eoff + q.colptr[k + 1]);
+    }
+    for (int64_t e = 0; e < q.colptr[q.nblk]; ++e) {
+      const int32_t r = q.rowidx[e];
+      // out-of-range rows are left for the symbolic analysis to reject, but must not alias
+      // another instance's blocks
+      rowidx.push_back(r >= 0 && r < q.nblk ? off + r : -1);
+    }
+    const int32_t* pi = perms ? perms[i] : nullptr;
+    for (int k = 0; k < q.nblk; ++k) {
+      const int32_t v = pi ? pi[k] : k;
+      perm.push_back(v >= 0 && v < q.nblk ? off + v : -1);
+    }
+    inst_blk.push_back(off + q.nblk);
+  }
+  d3m_pattern u;
+  u.nblk = inst_blk.back();
+  u.m = 0;
+  u.blk_size = bsz.data();
+  u.colptr = colptr.data();
+  u.rowidx = rowidx.data();
+  return create_impl(out, &u, perm.data(), opt, &inst_blk);
+}
+
+int d3m_get_instance_omega(d3m_handle h, double* host_out, void* stream) {
+  if (!h || !host_out) return set_err(h, D3M_ERR_INVALID, "handle or output is NULL");
+  const int mr = h->opt.max_nrhs;
+  std::vector<double> w((size_t)h->ninst * mr, NAN);
+  CUDA_TRY(h, cudaStreamSynchronize((cudaStream_t)stream));
+  if (h->omega_valid && h->last_nrhs > 0)
+    CUDA_TRY(h, cudaMemcpy(w.data(), h->omega_dev, w.size() * sizeof(double), cudaMemcpyDeviceToHost));
+  for (int i = 0; i < h->ninst; ++i) {
+    double o = h->omega_valid && h->last_nrhs > 0 ? 0.0 : NAN;
+    for (int j = 0; j < h->last_nrhs && h->omega_valid; ++j) o = std::max(o, w[(size_t)i * mr + j]);
+    host_out[i] = o;
+  }
   return D3M_OK;
 }
 
@@ -460,31 +605,32 @@ static ResidualParams residual_params(d3m_ctx* h, const double2* X, const double
   p.X = X;
   p.B = B;
   p.R = h->d_r;
-  const int mr = h->opt.max_nrhs;
+  const int mr = h->opt.max_nrhs, ni = h->ninst;
+  p.inst = h->inst;
+  p.ld_norm = mr;
   p.rmax = h->norms;
-  p.xmax = h->norms + mr;
-  p.kmax = h->norms + 3 * mr;
+  p.xmax = h->norms + (size_t)ni * mr;
+  p.bmax = h->norms + 2 * (size_t)ni * mr;
+  p.kmax = h->norms + 3 * (size_t)ni * mr;
   return p;
 }
 
-int d3m_factor(d3m_handle h, const void* Kin, void* stream) {
-  if (!h) return set_err(nullptr, D3M_ERR_INVALID, "handle is NULL");
-  if (!Kin) return set_err(h, D3M_ERR_INVALID, "K is NULL");
-  cudaStream_t st = (cudaStream_t)stream;
+// the launch sequence of one factorization (copy of K, queue reset, ||K_i||, persistent kernel,
+// status read-back into pinned memory)
+static int enqueue_factor(d3m_ctx* h, const void* Kin, bool kdev, cudaStream_t st) {
   const Symbolic& S = h->S;
   const int64_t ntiles = (int64_t)S.tasks.size();   // all tasks (final + update)
   const size_t kbytes = (size_t)S.kblk_off.back() * sizeof(double2);
-  CUDA_TRY(h, cudaMemcpyAsync(h->K, Kin, kbytes, is_device_ptr(Kin) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+  CUDA_TRY(h, cudaMemcpyAsync(h->K, Kin, kbytes, kdev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
   // reset the task graph state
   CUDA_TRY(h, cudaMemcpyAsync(h->cnt, h->ndeps, ntiles * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
   CUDA_TRY(h, cudaMemsetAsync(h->ready, 0xff, ntiles * sizeof(int32_t), st));
   const int n0 = (int)S.init_ready.size();
   if (n0 > 0) CUDA_TRY(h, cudaMemcpyAsync(h->ready, h->init_ready, n0 * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
   CUDA_TRY(h, cudaMemcpyAsync(h->ctl, h->ctl0, sizeof(Ctl), cudaMemcpyDeviceToDevice, st));
-  // ||K||_inf for the backward error
-  const int mr = h->opt.max_nrhs;
-  CUDA_TRY(h, cudaMemsetAsync(h->norms + 3 * mr, 0, sizeof(unsigned), st));
+  // ||K_i||_inf for the backward error
   ResidualParams rp = residual_params(h, nullptr, nullptr, 1);
+  CUDA_TRY(h, cudaMemsetAsync(rp.kmax, 0, h->ninst * sizeof(unsigned), st));
   int rc = launch_knorm(rp, h->nchunks, st);
   if (rc) return set_err(h, D3M_ERR_CUDA, std::string("knorm launch: ") + cudaGetErrorString((cudaError_t)rc));
   h->launches += 1;
@@ -515,6 +661,24 @@ int d3m_factor(d3m_handle h, const void* Kin, void* stream) {
   ev_end(h, d3m_ctx::EV_FACTOR, st);
   h->launches += 1;
   CUDA_TRY(h, cudaMemcpyAsync(h->h_ctl, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+  return D3M_OK;
+}
+
+int d3m_factor(d3m_handle h, const void* Kin, void* stream) {
+  if (!h) return set_err(nullptr, D3M_ERR_INVALID, "handle is NULL");
+  if (!Kin) return set_err(h, D3M_ERR_INVALID, "K is NULL");
+  cudaStream_t st = (cudaStream_t)stream;
+  const bool kdev = is_device_ptr(Kin);
+  int rc;
+  if (h->opt.graphs && kdev) {
+    // whole sequence as one graph; the event pair then spans the copy of K and ||K|| as well
+    ev_begin(h, d3m_ctx::EV_FACTOR, st);
+    rc = graph_run(h, h->g_factor, Kin, 0, 0, st, [&](cudaStream_t cs) { return enqueue_factor(h, Kin, true, cs); });
+    ev_end(h, d3m_ctx::EV_FACTOR, st);
+  } else {
+    rc = enqueue_factor(h, Kin, kdev, st);
+  }
+  if (rc != D3M_OK) return rc;
   h->factored = true;
   h->factor_checked = false;
   h->last_status = D3M_OK;
@@ -552,27 +716,26 @@ static int sweep(d3m_ctx* h, const double2* src, double2* dst, int nrhs, int acc
   a.lev_tile_ptr = h->lev_tile_ptr.data();
   a.tstart = h->tstart;
   a.tcolptr = h->tcolptr;
+  a.lev_maxnt = h->lev_maxnt.data();
   ev_begin(h, d3m_ctx::EV_SWEEP, st);
   int rc = launch_sweep(a, h->fp64, st);
   if (rc) return set_err(h, D3M_ERR_CUDA, std::string("sweep launch: ") + cudaGetErrorString((cudaError_t)rc));
   ev_end(h, d3m_ctx::EV_SWEEP, st);
-  int64_t nl = 3;   // permute in, diagonal scale, permute out
-  for (int lv = 0; lv < S.nlevels; ++lv)
-    nl += 2 + 2 * (S.fwd_item_ptr[lv + 1] > S.fwd_item_ptr[lv]) + 2 * (S.bwd_item_ptr[lv + 1] > S.bwd_item_ptr[lv]);
-  h->launches += nl;
+  h->launches += a.launches;
   return D3M_OK;
 }
 
 // r = b - K x and omega (device); returns D3M_OK or a launch error
 static int residual_omega(d3m_ctx* h, const double2* X, const double2* B, int nrhs, cudaStream_t st) {
-  const int mr = h->opt.max_nrhs;
-  CUDA_TRY(h, cudaMemsetAsync(h->norms, 0, 2 * mr * sizeof(unsigned), st));
+  const int mr = h->opt.max_nrhs, ni = h->ninst;
+  CUDA_TRY(h, cudaMemsetAsync(h->norms, 0, 3 * (size_t)ni * mr * sizeof(unsigned), st));
   ResidualParams rp = residual_params(h, X, B, nrhs);
   ev_begin(h, d3m_ctx::EV_RESID, st);
   int rc = launch_residual(rp, h->nchunks, st);
   if (rc) return set_err(h, D3M_ERR_CUDA, std::string("residual launch: ") + cudaGetErrorString((cudaError_t)rc));
   ev_end(h, d3m_ctx::EV_RESID, st);
-  rc = launch_omega(h->norms, h->norms + mr, h->norms + 2 * mr, h->norms + 3 * mr, nrhs, h->omega_dev, h->stat_dev, st);
+  rc = launch_omega(rp.rmax, rp.xmax, rp.bmax, rp.kmax, ni, mr, nrhs, h->omega_dev, h->stat_dev, st);
+  h->last_nrhs = nrhs;
   if (rc) return set_err(h, D3M_ERR_CUDA, std::string("omega launch: ") + cudaGetErrorString((cudaError_t)rc));
   h->launches += 2;
   return D3M_OK;
@@ -597,50 +760,53 @@ static int solve_impl(d3m_ctx* h, const void* Bin, void* Xout, int nrhs, cudaStr
   const Symbolic& S = h->S;
   const size_t vbytes = (size_t)S.n * nrhs * sizeof(double2);
   const bool bdev = is_device_ptr(Bin), xdev = is_device_ptr(Xout);
+  if (Bin == (const void*)Xout) return set_err(h, D3M_ERR_INVALID, "B and X may not alias");
+  const bool graphs = h->opt.graphs != 0;
   const double2* B = (const double2*)Bin;
-  if (!bdev) {
-    CUDA_TRY(h, cudaMemcpyAsync(h->d_b, Bin, vbytes, cudaMemcpyHostToDevice, st));
+  if (!bdev || graphs) {
+    // host B, or graph replay (captured launches read the library's own buffers)
+    CUDA_TRY(h, cudaMemcpyAsync(h->d_b, Bin, vbytes, bdev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
     B = h->d_b;
   }
-  double2* X = xdev ? (double2*)Xout : h->d_x;
-  if ((const void*)X == (const void*)B) return set_err(h, D3M_ERR_INVALID, "B and X may not alias");
+  double2* X = (xdev && !graphs) ? (double2*)Xout : h->d_x;
   h->omega = NAN;
   h->omega_first = NAN;
   h->omega_valid = 0;
   h->refine_iters = 0;
   ev_begin(h, d3m_ctx::EV_SOLVE, st);
   int status = D3M_OK;
-  const int mr = h->opt.max_nrhs;
+  // one refinement step: x (+)= solve(src); r = b - K x and omega (FP64); omega -> pinned host
+  auto step = [&](const double2* src, int acc, bool resid, cudaStream_t cs) -> int {
+    int rc = sweep(h, src, X, nrhs, acc, cs);
+    if (rc) return rc;
+    if (!resid) return D3M_OK;
+    rc = residual_omega(h, X, B, nrhs, cs);
+    if (rc) return rc;
+    CUDA_TRY(h, cudaMemcpyAsync(h->h_stat, h->stat_dev, sizeof(double), cudaMemcpyDeviceToHost, cs));
+    return D3M_OK;
+  };
+  auto run_step = [&](const double2* src, int acc, bool resid) -> int {
+    if (!graphs) return step(src, acc, resid, st);
+    return graph_run(h, h->g_solve, src, nrhs, acc | (resid ? 2 : 0), st,
+                     [&](cudaStream_t cs) { return step(src, acc, resid, cs); });
+  };
   if (h->fp64) {
-    int rc = sweep(h, B, X, nrhs, 0, st);
+    int rc = run_step(B, 0, h->opt.fp64_omega != 0);
     if (rc) return rc;
     h->refine_iters = 1;
     if (h->opt.fp64_omega) {
-      CUDA_TRY(h, cudaMemsetAsync(h->norms + 2 * mr, 0, mr * sizeof(unsigned), st));
-      rc = launch_absmax(B, S.n, nrhs, h->norms + 2 * mr, st);
-      if (rc) return set_err(h, D3M_ERR_CUDA, "absmax launch failed");
-      h->launches += 1;
-      rc = residual_omega(h, X, B, nrhs, st);
-      if (rc) return rc;
-      CUDA_TRY(h, cudaMemcpyAsync(h->h_stat, h->stat_dev, sizeof(double), cudaMemcpyDeviceToHost, st));
       CUDA_TRY(h, cudaStreamSynchronize(st));
       h->omega = h->omega_first = *h->h_stat;
       h->omega_valid = 1;
     }
   } else {
-    CUDA_TRY(h, cudaMemsetAsync(h->norms + 2 * mr, 0, mr * sizeof(unsigned), st));
-    int rc = launch_absmax(B, S.n, nrhs, h->norms + 2 * mr, st);
-    if (rc) return set_err(h, D3M_ERR_CUDA, "absmax launch failed");
-    h->launches += 1;
+    int rc = 0;
     double best = INFINITY;
     std::vector<double> hist;
     const double2* src = B;
     for (int it = 0; it < h->opt.refine_max_iter; ++it) {
-      rc = sweep(h, src, X, nrhs, it > 0 ? 1 : 0, st);     // x (+)= solve(r)
+      rc = run_step(src, it > 0 ? 1 : 0, true);             // x (+)= solve(r); r = b - K x, omega
       if (rc) return rc;
-      rc = residual_omega(h, X, B, nrhs, st);                // r = b - K x, omega
-      if (rc) return rc;
-      CUDA_TRY(h, cudaMemcpyAsync(h->h_stat, h->stat_dev, sizeof(double), cudaMemcpyDeviceToHost, st));
       CUDA_TRY(h, cudaStreamSynchronize(st));
       const double w = *h->h_stat;
       h->refine_iters = it + 1;
@@ -669,7 +835,8 @@ static int solve_impl(d3m_ctx* h, const void* Bin, void* Xout, int nrhs, cudaStr
     }
   }
   ev_end(h, d3m_ctx::EV_SOLVE, st);
-  if (!xdev) CUDA_TRY(h, cudaMemcpyAsync(Xout, X, vbytes, cudaMemcpyDeviceToHost, st));
+  if ((void*)X != Xout)
+    CUDA_TRY(h, cudaMemcpyAsync(Xout, X, vbytes, xdev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
   if (!h->fp64 || h->opt.fp64_omega) {
     // the refinement already synchronized: report an expired bounded wait of a sweep kernel
     int sw = 0;
@@ -810,6 +977,7 @@ int d3m_get_info(d3m_handle h, d3m_info* info, void* stream) {
   std::memset(info, 0, sizeof(*info));
   fill_structure(h->S, info);
   info->device_bytes = h->dev_bytes;
+  info->instances = h->ninst;
   int st = h->last_status;
   {
     int sw = 0;
@@ -871,6 +1039,9 @@ const char* d3m_last_error(d3m_handle h) {
 
 void d3m_destroy(d3m_handle h) {
   if (!h) return;
+  for (auto& g : h->g_factor) cudaGraphExecDestroy(g.exec);
+  for (auto& g : h->g_solve) cudaGraphExecDestroy(g.exec);
+  if (h->cap) cudaStreamDestroy(h->cap);
   for (void* p : h->allocs) cudaFree(p);
   if (h->h_ctl) cudaFreeHost(h->h_ctl);
   if (h->h_stat) cudaFreeHost(h->h_stat);

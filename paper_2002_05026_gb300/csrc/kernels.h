@@ -27,9 +27,12 @@ struct ResidualParams {
   const double2* X;
   const double2* B;
   double2* R;
-  unsigned* rmax;          // [nrhs] max |r| as float bits
-  unsigned* xmax;          // [nrhs] max |x|
-  unsigned* kmax;          // ||K||_inf
+  const int32_t* inst;     // [N] instance of every block (caller numbering); all 0 unless batched
+  int ld_norm;             // row stride of the per-(instance, column) maxima
+  unsigned* rmax;          // [instances][ld_norm] max |r| as float bits
+  unsigned* xmax;          // [instances][ld_norm] max |x|
+  unsigned* bmax;          // [instances][ld_norm] max |b|
+  unsigned* kmax;          // [instances] ||K_i||_inf
 };
 
 struct SweepLaunch {
@@ -56,6 +59,8 @@ struct SweepLaunch {
   const int64_t* lev_tile_ptr;     // host [nlevels+1]
   const int32_t* tstart;           // device [N+1]
   const int64_t* tcolptr;          // device [NT+1]
+  const int32_t* lev_maxnt;        // host [nlevels]: most tiles of one block in the level
+  int64_t launches;                // out: kernels launched by launch_sweep
 };
 
 // Tensor maps (CUtensorMap, 128 bytes each) of the tensor-core operand planes.
@@ -67,12 +72,12 @@ struct TcMaps {
 int launch_factor_simt(const FactorParams& p, bool fp64, int nblocks, cudaStream_t st);
 int tc_make_maps(void* opA, void* opB, int64_t ntiles, TcMaps* out, std::string& err);
 int launch_factor_tc(const FactorParams& p, const TcMaps& maps, int nblocks, cudaStream_t st);
-int launch_sweep(const SweepLaunch& a, bool fp64, cudaStream_t st);
+int launch_sweep(SweepLaunch& a, bool fp64, cudaStream_t st);
 int launch_residual(const ResidualParams& p, int nchunks, cudaStream_t st);
 int launch_knorm(const ResidualParams& p, int nchunks, cudaStream_t st);
 int launch_absmax(const double2* V, int64_t n, int nrhs, unsigned* out, cudaStream_t st);
 int launch_omega(const unsigned* rmax, const unsigned* xmax, const unsigned* bmax, const unsigned* kmax,
-                 int nrhs, double* omega, double* stat, cudaStream_t st);
+                 int ninst, int ld, int nrhs, double* omega, double* stat, cudaStream_t st);
 int launch_contract(const double2* Lam, const double2* X, int64_t n, int nrhs, const int64_t* xoff_orig,
                     const int32_t* m_orig, int nblk, double2* out, cudaStream_t st);
 int launch_grad_pattern(const double2* Lam, const double2* X, int64_t n, int nrhs, const int64_t* colptr,

@@ -11,6 +11,8 @@
 // Y[j * npad + row].
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "device.cuh"
 #include "kernels.h"
 
@@ -476,8 +478,276 @@ __global__ void __launch_bounds__(GT) block_bwd_kernel(BlockSweep s, const typen
   }
 }
 
+// ------------------------------------------------------------------ cluster-cooperative block chains
+// One thread-block cluster per (block, rhs group).  The block's rows are split into strips of 64
+// rows (tile t, half h); strip s = t * nh + h is owned by CTA rank s % cl (local slot s / cl),
+// which keeps its running vector in shared memory and streams only its own 64-row strips of L
+// (forward: rows of the tiles (t', t); backward: 64-column strips of the tiles (t, t')).
+// Step t of the chain: the owners of tile t read the full r_t from their partners' shared memory
+// (DSMEM) and form their half of y_t = Linv_tt r_t (backward: w_t = Linv_tt^T r_t); after a
+// cluster barrier every owner of a later tile reads the full y_t and updates its strip; a second
+// barrier closes the step.  The gathered partials of the level are subtracted when the strips
+// are loaded (and, backward, z = D^{-1} y is applied there), so a level needs no separate
+// reduce or diagonal-scaling launch.
+__device__ __forceinline__ uint32_t cluster_ctarank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+// all threads of all CTAs of the cluster; release / acquire orders shared-memory writes
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// generic address of the same shared-memory location in CTA `rank` of the cluster
+template <typename T>
+__device__ __forceinline__ const T* cluster_map(const T* p, uint32_t rank) {
+  uint64_t out;
+  asm volatile("mapa.u64 %0, %1, %2;" : "=l"(out) : "l"(p), "r"(rank));
+  return reinterpret_cast<const T*>(out);
+}
+
+// nrows row copies of rowlen elements (source row stride lds, shared row stride ldd) on one
+// mbarrier; issued by warp 0.
+template <typename C>
+__device__ __forceinline__ void stage_rows(C* dst, int ldd, const C* src, int lds, int nrows, int rowlen,
+                                           uint64_t* bar) {
+  if (threadIdx.x >= 32) return;
+  const uint32_t row_bytes = (uint32_t)(rowlen * sizeof(C));
+  if (threadIdx.x == 0)
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(nrows * row_bytes)
+                 : "memory");
+  __syncwarp();
+  for (int r = threadIdx.x; r < nrows; r += 32)
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst + r * ldd)),
+        "l"(src + (int64_t)r * lds), "r"(row_bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+// dst[c][j] (= or -=) sum_{r < nrows} M[r][c] V[r][j] for the 64 columns of a staged column strip
+template <typename R, bool SUB>
+__device__ __forceinline__ void colstrip_matvec(const typename CT<R>::C* M, int ldm, int nrows,
+                                                const typename CT<R>::C* V, int ldv, int rc,
+                                                typename CT<R>::C* dst, int ldd) {
+  using C = typename CT<R>::C;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int c = warp * 8 + (lane >> 2), rq = lane & 3;
+  C acc[RCMAX];
+#pragma unroll
+  for (int j = 0; j < RCMAX; ++j) acc[j] = CT<R>::make(0, 0);
+#pragma unroll 4
+  for (int r = rq; r < nrows; r += 4) {
+    const C m = M[r * ldm + c];
+    const C* v = V + r * ldv;
+    C vv[RCMAX];
+#pragma unroll
+    for (int j = 0; j < RCMAX; ++j) vv[j] = (j < rc) ? v[j] : CT<R>::make(0, 0);
+#pragma unroll
+    for (int j = 0; j < RCMAX; ++j) acc[j] = cfma(m, vv[j], acc[j]);
+  }
+  quad_reduce(acc);
+  if (rq == 0) {
+#pragma unroll
+    for (int j = 0; j < RCMAX; ++j)
+      if (j < rc) dst[c * ldd + j] = SUB ? csub(dst[c * ldd + j], acc[j]) : acc[j];
+  }
+}
+
+struct ChainSweep {
+  int* status;               // set to D3M_ERR_TIMEOUT if a bounded wait expires
+  const int32_t* blocks;     // blocks of this level
+  const int32_t* tstart;     // [N+1]
+  const int64_t* tcolptr;    // [NT+1]
+  const int64_t* slot_ptr;   // [NT] first | count << 32 (partials of this direction)
+  const void* P;             // partials of the level
+  const void* D;             // pivots (backward)
+  int64_t npad;
+  int b, nrhs, rc;           // rhs per cluster (grid.y = ceil(nrhs / rc))
+  int cl, nloc, stg;         // CTAs per cluster, strip slots per CTA, elements of one stage buffer
+  int has_partials;
+};
+
+constexpr int CHAIN_MAXJ = 128;   // staged strips of one CTA
+constexpr int CHAIN_MAXCL = 8;    // portable cluster size
+constexpr int CHAIN_MAXLOC = 4;   // strips per CTA
+
+template <typename R, bool FWD>
+__global__ void __launch_bounds__(GT) chain_kernel(ChainSweep s, const typename CT<R>::C* __restrict__ L,
+                                                   const typename CT<R>::C* __restrict__ Linv,
+                                                   typename CT<R>::C* __restrict__ Y) {
+  using C = typename CT<R>::C;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ const C* s_job[CHAIN_MAXJ];
+  __shared__ int64_t s_cp[MAXNT];
+  __shared__ int s_nj;
+  __shared__ __align__(8) uint64_t bars[2];
+  const int b = s.b, nh = b / HR, CL = s.cl;
+  const int rank = (int)cluster_ctarank();
+  const int k = s.blocks[blockIdx.x / CL];
+  const int j0 = blockIdx.y * s.rc;
+  const int rc = min(s.rc, s.nrhs - j0);
+  const int ldv = vec_ld(s.rc);
+  const int t0 = s.tstart[k], nt = s.tstart[k + 1] - t0;
+  const int S = nt * nh;
+  const int nloc = S > rank ? (S - rank + CL - 1) / CL : 0;
+  const int ldst = FWD ? stage_ld<C>(b) : stage_ld<C>(HR);
+  C* stg0 = reinterpret_cast<C*>(smem_raw);
+  C* stg1 = stg0 + s.stg;
+  C* sy = stg1 + s.stg;                              // [b][ldv]   gathered r_t or y_t
+  C* rbuf = sy + (int64_t)b * ldv;                   // [nloc][64][ldv]  running strips
+  C* obuf = rbuf + (int64_t)s.nloc * HR * ldv;       // [nloc][64][ldv]  solved strips
+  if (threadIdx.x < nt) s_cp[threadIdx.x] = s.tcolptr[t0 + threadIdx.x];
+  __syncthreads();
+  // staged strips in consumption order: per step, the strip of tile t first, then the updates
+  if (threadIdx.x == 0) {
+    int nj = 0;
+    for (int q = 0; q < nt; ++q) {
+      const int t = FWD ? q : nt - 1 - q;
+      for (int pass = 0; pass < 2; ++pass)
+        for (int l = 0; l < nloc; ++l) {
+          const int sid = rank + l * CL, tp = sid / nh, h = sid % nh;
+          const bool mine = pass == 0 ? tp == t : (FWD ? tp > t : tp < t);
+          if (!mine) continue;
+          const C* src;
+          if (pass == 0) src = Linv + (int64_t)(t0 + t) * b * b + (FWD ? (int64_t)h * HR * b : (int64_t)h * HR);
+          else if (FWD) src = L + (s_cp[t] + (tp - t)) * (int64_t)b * b + (int64_t)h * HR * b;
+          else src = L + (s_cp[tp] + (t - tp)) * (int64_t)b * b + (int64_t)h * HR;
+          s_job[nj++] = src;
+        }
+    }
+    s_nj = nj;
+    mbar_init_s(&bars[0]);
+    mbar_init_s(&bars[1]);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  const int nj = s_nj;
+  auto stage = [&](int jb) {
+    C* dst = (jb & 1) ? stg1 : stg0;
+    if (FWD) stage_rows(dst, ldst, s_job[jb], b, HR, b, &bars[jb & 1]);
+    else stage_rows(dst, ldst, s_job[jb], b, b, HR, &bars[jb & 1]);
+  };
+  if (nj > 0) stage(0);
+  // strips of r: Y rows (backward: D^{-1} y) minus the level's partials in fixed slot order
+  {
+    const C* P = reinterpret_cast<const C*>(s.P);
+    const C* D = reinterpret_cast<const C*>(s.D);
+    for (int l = 0; l < nloc; ++l) {
+      const int sid = rank + l * CL, tp = sid / nh, h = sid % nh;
+      const int I = t0 + tp;
+      int64_t first = 0, cnt = 0;
+      if (s.has_partials) {
+        const int64_t sp = s.slot_ptr[I];
+        first = sp & 0xffffffffLL;
+        cnt = (sp >> 32) * (FWD ? 1 : nh);
+      }
+      const int64_t stride = (int64_t)b * s.nrhs * (FWD ? nh : 1);
+      for (int i = threadIdx.x; i < HR * rc; i += GT) {
+        const int j = i % rc, row = i / rc;
+        const int64_t g = (int64_t)I * b + h * HR + row;
+        C v = Y[(int64_t)(j0 + j) * s.npad + g];
+        if (!FWD) v = cdiv(v, D[g]);
+        if (cnt) {
+          const C* pp = P + first * nh * (int64_t)b * s.nrhs + (int64_t)(h * HR + row) * s.nrhs + (j0 + j);
+          C a0 = czero<R>(), a1 = czero<R>(), a2 = czero<R>(), a3 = czero<R>();
+          int64_t q = 0;
+          for (; q + 4 <= cnt; q += 4) {
+            a0 = cadd(a0, pp[(q + 0) * stride]);
+            a1 = cadd(a1, pp[(q + 1) * stride]);
+            a2 = cadd(a2, pp[(q + 2) * stride]);
+            a3 = cadd(a3, pp[(q + 3) * stride]);
+          }
+          for (; q < cnt; ++q) a0 = cadd(a0, pp[q * stride]);
+          v = csub(v, cadd(cadd(a0, a1), cadd(a2, a3)));
+        }
+        rbuf[(l * HR + row) * ldv + j] = v;
+      }
+    }
+  }
+  uint32_t phase[2] = {0u, 0u};
+  const uint64_t deadline = globaltimer_ns() + SWEEP_TIMEOUT_NS;
+  bool bad = false;
+  int job = 0;
+  // wait for staged strip `job`, start the copy of the next one into the other buffer (its
+  // previous reader finished before the barrier that ended that job)
+  auto next_stage = [&]() -> const C* {
+    const int buf = job & 1;
+    if (!bad && job + 1 < nj) {
+      if (threadIdx.x < 32) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      stage(job + 1);
+    }
+    const bool late = !bad && !mbar_wait_s(&bars[buf], phase[buf], deadline);
+    phase[buf] ^= 1u;
+    bad = __syncthreads_or(late || bad);
+    ++job;
+    return buf ? stg1 : stg0;
+  };
+  // full vector of tile t (b rows) from the owners' strip buffers
+  auto gather_tile = [&](int t, const C* base) {
+    for (int i = threadIdx.x; i < b * rc; i += GT) {
+      const int j = i % rc, row = i / rc;
+      const int sid = t * nh + row / HR;
+      const C* src = cluster_map(base + (int64_t)(sid / CL) * HR * ldv, (uint32_t)(sid % CL));
+      sy[row * ldv + j] = src[(row % HR) * ldv + j];
+    }
+  };
+  __syncthreads();
+  cluster_sync_all();                                 // every strip of r is loaded
+  for (int q = 0; q < nt; ++q) {
+    const int t = FWD ? q : nt - 1 - q;
+    // ---- the owners of tile t solve their halves
+    bool own = false;
+    for (int l = 0; l < nloc; ++l) own |= (rank + l * CL) / nh == t;
+    if (own) {
+      gather_tile(t, rbuf);
+      __syncthreads();
+      for (int l = 0; l < nloc; ++l) {
+        const int sid = rank + l * CL, h = sid % nh;
+        if (sid / nh != t) continue;
+        const C* M = next_stage();
+        C* o = obuf + (int64_t)l * HR * ldv;
+        if (!bad) {
+          if (FWD) rows_matvec<R, false>(M, ldst, b, sy, ldv, rc, o, ldv);
+          else colstrip_matvec<R, false>(M, ldst, b, sy, ldv, rc, o, ldv);
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < HR * rc; i += GT) {
+          const int row = i % HR, j = i / HR;
+          Y[(int64_t)(j0 + j) * s.npad + (int64_t)(t0 + t) * b + h * HR + row] = o[row * ldv + j];
+        }
+      }
+    }
+    cluster_sync_all();                               // y_t (w_t) is complete
+    // ---- the owners of the remaining tiles apply it
+    bool upd = false;
+    for (int l = 0; l < nloc; ++l) {
+      const int tp = (rank + l * CL) / nh;
+      upd |= FWD ? tp > t : tp < t;
+    }
+    if (upd) {
+      gather_tile(t, obuf);
+      __syncthreads();
+      for (int l = 0; l < nloc; ++l) {
+        const int tp = (rank + l * CL) / nh;
+        if (!(FWD ? tp > t : tp < t)) continue;
+        const C* M = next_stage();
+        C* r = rbuf + (int64_t)l * HR * ldv;
+        if (!bad) {
+          if (FWD) rows_matvec<R, true>(M, ldst, b, sy, ldv, rc, r, ldv);
+          else colstrip_matvec<R, true>(M, ldst, b, sy, ldv, rc, r, ldv);
+        }
+        __syncthreads();
+      }
+    }
+    cluster_sync_all();                               // the strips of tile t+1 (t-1) are final
+  }
+  if (bad && threadIdx.x == 0) atomicExch(s.status, (int)D3M_ERR_TIMEOUT);
+}
+
 // ------------------------------------------------------------------ FP64 residual
-// r = b - K x (caller numbering), one thread per (row, rhs); |r| and |x| maxima per column.
+// r = b - K x (caller numbering), one thread per (row, rhs); |r|, |x| and |b| maxima per
+// (instance, column) (a batched handle holds several independent systems; one otherwise).
 __global__ void __launch_bounds__(256) residual_kernel(ResidualParams p) {
   const int rc = p.rc;
   const int i = threadIdx.x % 32, jl = threadIdx.x / 32;
@@ -502,7 +772,7 @@ __global__ void __launch_bounds__(256) residual_kernel(ResidualParams p) {
       }
     }
   }
-  float ra = 0.f, xa = 0.f;
+  float ra = 0.f, xa = 0.f, ba = 0.f;
   if (active) {
     const int64_t o = (int64_t)j * p.n + p.xoff_orig[f] + u;
     const double2 bv = p.B[o];
@@ -513,14 +783,19 @@ __global__ void __launch_bounds__(256) residual_kernel(ResidualParams p) {
     const double2 xv = p.X[o];
     const float xx = (float)xv.x, xy = (float)xv.y;
     xa = sqrtf(xx * xx + xy * xy);
+    const float bx = (float)bv.x, by = (float)bv.y;
+    ba = sqrtf(bx * bx + by * by);
   }
   for (int o = 16; o > 0; o >>= 1) {
     ra = fmaxf(ra, __shfl_xor_sync(0xffffffffu, ra, o));
     xa = fmaxf(xa, __shfl_xor_sync(0xffffffffu, xa, o));
+    ba = fmaxf(ba, __shfl_xor_sync(0xffffffffu, ba, o));
   }
   if (i == 0 && jl < rc && j < p.nrhs) {
-    atomicMax(p.rmax + j, __float_as_uint(ra));
-    atomicMax(p.xmax + j, __float_as_uint(xa));
+    const int q = p.inst[f] * p.ld_norm + j;
+    atomicMax(p.rmax + q, __float_as_uint(ra));
+    atomicMax(p.xmax + q, __float_as_uint(xa));
+    atomicMax(p.bmax + q, __float_as_uint(ba));
   }
 }
 
@@ -550,7 +825,7 @@ __global__ void __launch_bounds__(256) knorm_kernel(ResidualParams p) {
     float t = 0.f;
     for (int q = 0; q < 8; ++q) t += s_sum[q][i];
     for (int o = 16; o > 0; o >>= 1) t = fmaxf(t, __shfl_xor_sync(0xffffffffu, t, o));
-    if (i == 0) atomicMax(p.kmax, __float_as_uint(t));
+    if (i == 0) atomicMax(p.kmax + p.inst[f], __float_as_uint(t));
   }
 }
 
@@ -566,19 +841,28 @@ __global__ void vec_absmax_kernel(const double2* __restrict__ V, int64_t n, int 
   if ((threadIdx.x & 31) == 0) atomicMax(out + j, __float_as_uint(a));
 }
 
-// omega_j = |r|_j / (||K|| |x|_j + |b|_j);  stat[0] = max_j omega_j
+// omega_(i,j) = |r|_(i,j) / (||K_i|| |x|_(i,j) + |b|_(i,j)) for instance i, column j (entry
+// i * ld + j);  stat[0] = the largest.  One block of 256 threads.
 __global__ void omega_kernel(const unsigned* rmax, const unsigned* xmax, const unsigned* bmax,
-                             const unsigned* kmax, int nrhs, double* omega, double* stat) {
+                             const unsigned* kmax, int ninst, int ld, int nrhs, double* omega, double* stat) {
   double w = 0.0;
-  const double kn = (double)__uint_as_float(*kmax);
-  for (int j = 0; j < nrhs; ++j) {
-    const double r = __uint_as_float(rmax[j]), x = __uint_as_float(xmax[j]), bb = __uint_as_float(bmax[j]);
+  for (int e = threadIdx.x; e < ninst * nrhs; e += blockDim.x) {
+    const int i = e / nrhs, j = e % nrhs, q = i * ld + j;
+    const double kn = (double)__uint_as_float(kmax[i]);
+    const double r = __uint_as_float(rmax[q]), x = __uint_as_float(xmax[q]), bb = __uint_as_float(bmax[q]);
     const double den = kn * x + bb;
     const double o = den > 0 ? r / den : (r > 0 ? 1.0 : 0.0);
-    omega[j] = o;
+    omega[q] = o;
     w = fmax(w, o);
   }
-  stat[0] = w;
+  __shared__ double s_w[256];
+  s_w[threadIdx.x] = w;
+  __syncthreads();
+  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < h) s_w[threadIdx.x] = fmax(s_w[threadIdx.x], s_w[threadIdx.x + h]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) stat[0] = s_w[0];
 }
 
 // per-interface complex contraction s_f = sum_j sum_u Lambda_uj X_uj (FP64)
@@ -629,7 +913,7 @@ __global__ void grad_pattern_kernel(const double2* __restrict__ Lam, const doubl
 
 // ------------------------------------------------------------------ launchers
 template <typename R>
-static int sweep_impl(const SweepLaunch& a, cudaStream_t st) {
+static int sweep_impl(SweepLaunch& a, cudaStream_t st) {
   using C = typename CT<R>::C;
   const int b = a.b;
   const int nthreads = 256;
@@ -639,8 +923,94 @@ static int sweep_impl(const SweepLaunch& a, cudaStream_t st) {
   const C* D = (const C*)a.D;
   C* Y = (C*)a.Y;
   C* P = (C*)a.P;
+  const int nh = b / HR;
+  a.launches = 0;
   permute_in_kernel<R><<<(unsigned)gblocks, nthreads, 0, st>>>(a.src, a.n, Y, a.npad, a.pad2orig, a.nrhs);
+  ++a.launches;
   const size_t gsm = sizeof(C) * ((size_t)HR * stage_ld<C>(b) + (size_t)b * vec_ld(a.nrhs));
+  cudaFuncSetAttribute(gather_kernel<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm);
+  cudaFuncSetAttribute(gather_kernel<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm);
+  // cluster chains: usable when every level's largest block fits CHAIN_MAXCL x CHAIN_MAXLOC strips
+  const int crc = a.nrhs < RCMAX ? a.nrhs : RCMAX;
+  const int cldv = vec_ld(crc);
+  const int cstg = std::max(HR * stage_ld<C>(b), b * stage_ld<C>(HR));
+  bool chain = a.lev_maxnt != nullptr;
+  int max_loc = 1;
+  for (int lv = 0; chain && lv < a.nlevels; ++lv) {
+    const int S = a.lev_maxnt[lv] * nh;
+    const int cl = std::min(CHAIN_MAXCL, S);
+    const int nloc = (S + cl - 1) / cl;
+    if (nloc > CHAIN_MAXLOC || a.lev_maxnt[lv] > MAXNT) chain = false;
+    max_loc = std::max(max_loc, nloc);
+  }
+  auto chain_smem = [&](int nloc) {
+    return sizeof(C) * (2 * (size_t)cstg + (size_t)b * cldv + 2 * (size_t)nloc * HR * cldv);
+  };
+  if (chain && chain_smem(max_loc) > SWEEP_SMEM_LIMIT) chain = false;
+  if (chain) {
+    cudaFuncSetAttribute(chain_kernel<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)chain_smem(max_loc));
+    cudaFuncSetAttribute(chain_kernel<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)chain_smem(max_loc));
+    ChainSweep cs;
+    cs.status = a.status;
+    cs.tstart = a.tstart;
+    cs.tcolptr = a.tcolptr;
+    cs.P = P;
+    cs.D = D;
+    cs.npad = a.npad;
+    cs.b = b;
+    cs.nrhs = a.nrhs;
+    cs.rc = crc;
+    cs.stg = cstg;
+    const unsigned ny = (unsigned)((a.nrhs + crc - 1) / crc);
+    auto launch_chain = [&](int lv, bool fwd) -> cudaError_t {
+      const int S = a.lev_maxnt[lv] * nh;
+      cs.cl = std::min(CHAIN_MAXCL, S);
+      cs.nloc = (S + cs.cl - 1) / cs.cl;
+      cs.blocks = a.lev_blocks + a.lev_ptr[lv];
+      const unsigned nb = (unsigned)(a.lev_ptr[lv + 1] - a.lev_ptr[lv]);
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(nb * (unsigned)cs.cl, ny, 1);
+      cfg.blockDim = dim3(GT, 1, 1);
+      cfg.dynamicSmemBytes = chain_smem(cs.nloc);
+      cfg.stream = st;
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = (unsigned)cs.cl;
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      ++a.launches;
+      return fwd ? cudaLaunchKernelEx(&cfg, chain_kernel<R, true>, cs, L, Linv, Y)
+                 : cudaLaunchKernelEx(&cfg, chain_kernel<R, false>, cs, L, Linv, Y);
+    };
+    for (int lv = 0; lv < a.nlevels; ++lv) {
+      const int64_t i0 = a.fwd_item_ptr[lv], i1 = a.fwd_item_ptr[lv + 1];
+      if (i1 > i0) {
+        gather_kernel<R, true><<<(unsigned)((i1 - i0) * nh), GT, gsm, st>>>(a.fwd_items + i0, L, Y, P, a.npad, b, a.nrhs, a.status);
+        ++a.launches;
+      }
+      cs.slot_ptr = a.fwd_slot_ptr;
+      cs.has_partials = i1 > i0;
+      cudaError_t e = launch_chain(lv, true);
+      if (e != cudaSuccess) return (int)e;
+    }
+    for (int lv = a.nlevels - 1; lv >= 0; --lv) {
+      const int64_t i0 = a.bwd_item_ptr[lv], i1 = a.bwd_item_ptr[lv + 1];
+      if (i1 > i0) {
+        gather_kernel<R, false><<<(unsigned)((i1 - i0) * nh), GT, gsm, st>>>(a.bwd_items + i0, L, Y, P, a.npad, b, a.nrhs, a.status);
+        ++a.launches;
+      }
+      cs.slot_ptr = a.bwd_slot_ptr;
+      cs.has_partials = i1 > i0;
+      cudaError_t e = launch_chain(lv, false);
+      if (e != cudaSuccess) return (int)e;
+    }
+    permute_out_kernel<R><<<(unsigned)gblocks, nthreads, 0, st>>>(Y, a.npad, a.dst, a.n, a.pad2orig, a.nrhs, a.accumulate);
+    ++a.launches;
+    return (int)cudaGetLastError();
+  }
+  // single-CTA chains (blocks too large for one cluster)
   // rhs per block kernel: at most 8, fewer if the running vector would not fit in shared memory
   int rc = a.nrhs < 8 ? a.nrhs : 8;
   auto block_smem = [&](int r) {
@@ -649,8 +1019,6 @@ static int sweep_impl(const SweepLaunch& a, cudaStream_t st) {
   while (rc > 1 && block_smem(rc) > SWEEP_SMEM_LIMIT) rc = (rc + 1) / 2;
   const size_t bsm = block_smem(rc);
   if (bsm > SWEEP_SMEM_LIMIT) return (int)cudaErrorInvalidConfiguration;
-  cudaFuncSetAttribute(gather_kernel<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm);
-  cudaFuncSetAttribute(gather_kernel<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm);
   cudaFuncSetAttribute(block_fwd_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bsm);
   cudaFuncSetAttribute(block_bwd_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bsm);
   BlockSweep bs;
@@ -661,7 +1029,6 @@ static int sweep_impl(const SweepLaunch& a, cudaStream_t st) {
   bs.b = b;
   bs.nrhs = a.nrhs;
   bs.rc = rc;
-  const int nh = b / HR;
   const unsigned ny = (unsigned)((a.nrhs + rc - 1) / rc);
   for (int lv = 0; lv < a.nlevels; ++lv) {
     const int64_t i0 = a.fwd_item_ptr[lv], i1 = a.fwd_item_ptr[lv + 1];
@@ -671,13 +1038,16 @@ static int sweep_impl(const SweepLaunch& a, cudaStream_t st) {
       const int64_t nthr = ntl * b * a.nrhs;
       reduce_kernel<R><<<(unsigned)((nthr + ET - 1) / ET), ET, 0, st>>>(a.lev_tiles + a.lev_tile_ptr[lv], (int)ntl,
                                                                      a.fwd_slot_ptr, P, Y, a.npad, b, a.nrhs, 1);
+      a.launches += 2;
     }
     bs.blocks = a.lev_blocks + a.lev_ptr[lv];
     bs.slot_ptr = a.fwd_slot_ptr;
     const unsigned nb = (unsigned)(a.lev_ptr[lv + 1] - a.lev_ptr[lv]);
     block_fwd_kernel<R><<<dim3(nb, ny), GT, bsm, st>>>(bs, L, Linv, Y);
+    ++a.launches;
   }
   diag_scale_kernel<R><<<(unsigned)gblocks, nthreads, 0, st>>>(Y, D, a.npad, a.nrhs);
+  ++a.launches;
   for (int lv = a.nlevels - 1; lv >= 0; --lv) {
     const int64_t i0 = a.bwd_item_ptr[lv], i1 = a.bwd_item_ptr[lv + 1];
     const int64_t ntl = a.lev_tile_ptr[lv + 1] - a.lev_tile_ptr[lv];
@@ -686,17 +1056,20 @@ static int sweep_impl(const SweepLaunch& a, cudaStream_t st) {
       const int64_t nthr = ntl * b * a.nrhs;
       reduce_kernel<R><<<(unsigned)((nthr + ET - 1) / ET), ET, 0, st>>>(a.lev_tiles + a.lev_tile_ptr[lv], (int)ntl,
                                                                      a.bwd_slot_ptr, P, Y, a.npad, b, a.nrhs, nh);
+      a.launches += 2;
     }
     bs.blocks = a.lev_blocks + a.lev_ptr[lv];
     bs.slot_ptr = a.bwd_slot_ptr;
     const unsigned nb = (unsigned)(a.lev_ptr[lv + 1] - a.lev_ptr[lv]);
     block_bwd_kernel<R><<<dim3(nb, ny), GT, bsm, st>>>(bs, L, Linv, Y);
+    ++a.launches;
   }
   permute_out_kernel<R><<<(unsigned)gblocks, nthreads, 0, st>>>(Y, a.npad, a.dst, a.n, a.pad2orig, a.nrhs, a.accumulate);
+  ++a.launches;
   return (int)cudaGetLastError();
 }
 
-int launch_sweep(const SweepLaunch& a, bool fp64, cudaStream_t st) {
+int launch_sweep(SweepLaunch& a, bool fp64, cudaStream_t st) {
   return fp64 ? sweep_impl<double>(a, st) : sweep_impl<float>(a, st);
 }
 
@@ -718,8 +1091,8 @@ int launch_absmax(const double2* V, int64_t n, int nrhs, unsigned* out, cudaStre
 }
 
 int launch_omega(const unsigned* rmax, const unsigned* xmax, const unsigned* bmax, const unsigned* kmax,
-                 int nrhs, double* omega, double* stat, cudaStream_t st) {
-  omega_kernel<<<1, 1, 0, st>>>(rmax, xmax, bmax, kmax, nrhs, omega, stat);
+                 int ninst, int ld, int nrhs, double* omega, double* stat, cudaStream_t st) {
+  omega_kernel<<<1, 256, 0, st>>>(rmax, xmax, bmax, kmax, ninst, ld, nrhs, omega, stat);
   return (int)cudaGetLastError();
 }
 

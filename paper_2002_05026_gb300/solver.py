@@ -19,6 +19,8 @@ PRECISIONS = {"fp64": _abi.D3M_FP64, "bf16x3": _abi.D3M_MIXED_BF16X3, "simt32": 
 
 def _stream_ptr(stream=None) -> int:
     import torch
+    if stream is None and not torch.cuda.is_available():
+        return 0          # default stream; only host-side validation can run without a device
     s = stream if stream is not None else torch.cuda.current_stream()
     return int(s.cuda_stream)
 
@@ -35,25 +37,32 @@ def _as_colmajor(B):
     return B.T.contiguous(), B.shape[1], False
 
 
+def _options(precision, max_nrhs, refine_tol, refine_max_iter, timeout_ns, fp64_omega, debug_flags, graphs=False):
+    opt = _abi.d3m_default_options()
+    opt.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    opt.max_nrhs = max_nrhs
+    opt.refine_tol = refine_tol
+    opt.refine_max_iter = refine_max_iter
+    if timeout_ns:
+        opt.timeout_ns = timeout_ns
+    opt.fp64_omega = int(fp64_omega)
+    opt.debug_flags = debug_flags
+    opt.graphs = int(graphs)
+    return opt
+
+
 class D3M:
     """One factorization handle (d3m_create ... d3m_destroy)."""
 
     def __init__(self, colptr, rowidx, m=None, blk_size=None, perm=None, precision="bf16x3",
                  max_nrhs: int = 32, refine_tol: float = 1e-12, refine_max_iter: int = 20,
-                 timeout_ns: int = 0, fp64_omega: bool = False, debug_flags: int = 0, stream=None):
+                 timeout_ns: int = 0, fp64_omega: bool = False, debug_flags: int = 0, graphs: bool = False,
+                 stream=None):
         lib = load()
         self._lib = lib
         self.h = c_void_p()
         pat, self._keep = _abi.make_pattern(colptr, rowidx, m, blk_size)
-        opt = _abi.d3m_default_options()
-        opt.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
-        opt.max_nrhs = max_nrhs
-        opt.refine_tol = refine_tol
-        opt.refine_max_iter = refine_max_iter
-        if timeout_ns:
-            opt.timeout_ns = timeout_ns
-        opt.fp64_omega = int(fp64_omega)
-        opt.debug_flags = debug_flags
+        opt = _options(precision, max_nrhs, refine_tol, refine_max_iter, timeout_ns, fp64_omega, debug_flags, graphs)
         pp = None
         if perm is not None:
             self._perm = np.ascontiguousarray(perm, dtype=np.int32)
@@ -158,3 +167,51 @@ class D3M:
             self.close()
         except Exception:
             pass
+
+
+class D3MBatch(D3M):
+    """Many independent systems in one handle (d3m_create_batch): one persistent factorization
+    launch for all of them and level-merged solve sweeps.  `instances` is a list of
+    (colptr, rowidx, m_or_blk_size) tuples; `perms` a list of per-instance perms (or None).
+    K, B and X are the instances' own arrays concatenated in instance order."""
+
+    def __init__(self, instances, perms=None, precision="bf16x3", max_nrhs: int = 32, refine_tol: float = 1e-12,
+                 refine_max_iter: int = 20, timeout_ns: int = 0, fp64_omega: bool = False, debug_flags: int = 0,
+                 graphs: bool = False, stream=None):
+        lib = load()
+        self._lib = lib
+        self.h = c_void_p()
+        count = len(instances)
+        pats = (_abi.d3m_pattern * count)()
+        self._keep = []
+        self.sizes = []
+        for i, (colptr, rowidx, msz) in enumerate(instances):
+            if np.isscalar(msz):
+                pat, keep = _abi.make_pattern(colptr, rowidx, int(msz), None)
+                self.sizes.append(int(msz) * (len(colptr) - 1))
+            else:
+                pat, keep = _abi.make_pattern(colptr, rowidx, None, msz)
+                self.sizes.append(int(np.sum(msz)))
+            pats[i] = pat
+            self._keep.append(keep)
+        pp = None
+        if perms is not None:
+            self._perms = [None if q is None else np.ascontiguousarray(q, dtype=np.int32) for q in perms]
+            pp = (POINTER(c_int32) * count)(*[
+                ctypes.cast(None, POINTER(c_int32)) if q is None else q.ctypes.data_as(POINTER(c_int32))
+                for q in self._perms])
+        opt = _options(precision, max_nrhs, refine_tol, refine_max_iter, timeout_ns, fp64_omega, debug_flags, graphs)
+        self.precision = precision
+        self.stream = stream
+        rc = lib.d3m_create_batch(ctypes.byref(self.h), count, pats, pp, ctypes.byref(opt),
+                                  c_void_p(_stream_ptr(stream)))
+        check(rc, None if not self.h else self.h)
+        self.count = count
+        self.offsets = np.concatenate([[0], np.cumsum(self.sizes)]).astype(np.int64)
+        self.n = int(self.offsets[-1])
+
+    def instance_omega(self) -> np.ndarray:
+        out = np.zeros(self.count, dtype=np.float64)
+        check(self._lib.d3m_get_instance_omega(self.h, out.ctypes.data_as(POINTER(c_double)),
+                                               c_void_p(_stream_ptr(self.stream))), self.h)
+        return out

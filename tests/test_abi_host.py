@@ -86,3 +86,40 @@ def test_invalid_patterns_rejected(lib, bad):
     with pytest.raises(_abi.D3MError) as e:
         _abi.d3m_analyze(cp, ri, m=8, perm=perm)
     assert e.value.code == _abi.D3M_ERR_INVALID
+
+
+def test_batch_create_rejects_bad_instance(lib):
+    # validation happens before any device call: the error names the failing instance
+    from paper_2002_05026_gb300 import D3MBatch
+    cp, ri = synth.lower_pattern(2, 2, 1)
+    bad = ri.copy()
+    bad[-1] = 9
+    with pytest.raises(_abi.D3MError) as e:
+        D3MBatch([(cp, ri, 8), (cp, bad, 8)])
+    assert e.value.code == _abi.D3M_ERR_INVALID
+    with pytest.raises(_abi.D3MError) as e:
+        D3MBatch([(cp, ri, 8), (cp[:-1], ri, 8)])
+    assert e.value.code == _abi.D3M_ERR_INVALID
+
+
+def test_block_diagonal_union_analysis(lib):
+    # the batch is analysed as the block-diagonal union of its instances: counts add up and the
+    # elimination forest is as deep as its deepest tree
+    specs = [((2, 2, 1), 64), ((3, 3, 1), 32), ((4, 4, 1), 128)]
+    cps, ris, perms, sizes, infos = [], [], [], [], []
+    off = 0
+    for g, m in specs:
+        cp, ri = synth.lower_pattern(*g)
+        pm = O.nd_order(*g)
+        infos.append(_abi.d3m_analyze(cp, ri, m=m, perm=pm))
+        cps.append(cp[1:] + (cps[-1][-1] if cps else 0))
+        ris.append(ri + off)
+        perms.append(pm + off)
+        sizes += [m] * (cp.size - 1)
+        off += cp.size - 1
+    colptr = np.concatenate([[0]] + cps).astype(np.int64)
+    info = _abi.d3m_analyze(colptr, np.concatenate(ris), blk_size=np.array(sizes), perm=np.concatenate(perms))
+    for k in ("nblk", "nnzb_K", "nblk_L_offdiag", "ntiles", "ntile_updates", "ndep_edges"):
+        assert info[k] == sum(i[k] for i in infos), k
+    assert info["factor_flops"] == pytest.approx(sum(i["factor_flops"] for i in infos), rel=1e-12)
+    assert info["etree_depth"] == max(i["etree_depth"] for i in infos)

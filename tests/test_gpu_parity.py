@@ -207,3 +207,17 @@ def test_refactor_same_handle(torch_cuda):
         s.factor(torch_cuda.from_numpy(p.blocks_numpy()).cuda())
         X = s.solve(torch_cuda.from_numpy(np.ascontiguousarray(B)).cuda()).cpu().numpy()
         assert _fwd_err(X, O.block_solve(F, B)) <= 1e-9
+
+
+@pytest.mark.parametrize("precision", ["fp64", "bf16x3"])
+def test_full_interface_size_many_rhs(torch_cuda, precision):
+    # m = 512 as in the 8x8 and 6x6x6 workloads: the in-block chains span 4 (8) tiles of 128
+    # (64) rows, i.e. 8 row strips per interface block, one cluster of 8 CTAs per block;
+    # 11 right-hand sides = one group of 8 and a ragged group of 3
+    p, pm, Kb, F = _setup((2, 2, 2), 512, k2=2.0, tau=0.05, seed=77)
+    B = synth.rhs(5, p.n, 11)
+    s, X = _run(torch_cuda, p, pm, precision, B)
+    Xo = O.block_solve(F, B)
+    assert _fwd_err(X, Xo) <= (1e-10 if precision == "fp64" else 1e-9)
+    if precision != "fp64":
+        assert np.max(O.omega(Kb, p.nblk, p.m, X, B)) <= 1e-12
