@@ -243,10 +243,13 @@ int d3m_get_factor_block(d3m_handle h, int32_t i, int32_t j, void* host_out, voi
 int d3m_get_pivots(d3m_handle h, int32_t j, void* host_out, void* stream);
 
 /* Task trace of the last factorization (handle created with D3M_DEBUG_TRACE): copies up to
- * `cap` records of 8 int64 each {start_ns, end_ns, sm_id, flags | (tile << 8), t1, t2, t3, t4},
- * indexed by task id, to host memory and stores the number of tasks in *count; t1..t4 are
- * phase marks of the tensor-core engine (products done, S staged, factor / triangular solve
- * done, tile stored; 0 where a phase does not occur).  Synchronizes the stream.
+ * `cap` records of 10 int64 each {start_ns, end_ns, sm_id, flags | (tile << 8), t1, t2, t3,
+ * t4, ready_ns, releaser}, indexed by task id, to host memory and stores the number of tasks
+ * in *count; t1..t4 are phase marks of the tensor-core engine (products done, S staged,
+ * factor / triangular solve done, tile stored; -1 where a phase does not occur); ready_ns is
+ * when the task's last dependency was released and releaser the task that released it (both
+ * -1 for tasks ready at launch; every field is -1 before a task runs), so following releasers back from the last task to finish
+ * gives the critical path as it ran.  Synchronizes the stream.
  * D3M_ERR_STATE if tracing was not enabled. */
 int d3m_get_trace(d3m_handle h, int64_t* host_out, int64_t cap, int64_t* count, void* stream);
 

@@ -44,6 +44,8 @@ struct d3m_ctx {
   int64_t launches = 0;
   // factor data
   double2* K = nullptr;
+  float4* K2 = nullptr;              // double-float split of K for the residual
+  float4* X2 = nullptr;              // double-float split of x, n x max_nrhs
   TileTask* tasks = nullptr;
   KEntry* klist = nullptr;
   int32_t* ndeps = nullptr;
@@ -384,6 +386,7 @@ static int create_impl(d3m_handle* out, const d3m_pattern* pat, const int32_t* p
   } while (0)
   // factorization
   ALLOC(h->K, double2, S.kblk_off.back());
+  ALLOC(h->K2, float4, S.kblk_off.back());
   UPLOAD(h->tasks, S.tasks);
   UPLOAD(h->klist, S.klist);
   {
@@ -393,8 +396,8 @@ static int create_impl(d3m_handle* out, const d3m_pattern* pat, const int32_t* p
   }
   ALLOC(h->cnt, int32_t, ntask);
   if (h->opt.debug_flags & D3M_DEBUG_TRACE) {
-    ALLOC(h->trace, int64_t, 8 * ntask);
-    CUDA_TRY(h, cudaMemset(h->trace, 0, 8 * ntask * sizeof(int64_t)));
+    ALLOC(h->trace, int64_t, 10 * ntask);
+    CUDA_TRY(h, cudaMemset(h->trace, 0, 10 * ntask * sizeof(int64_t)));
   }
   UPLOAD(h->succ_ptr, S.succ_ptr);
   UPLOAD(h->succ, S.succ);
@@ -479,6 +482,7 @@ static int create_impl(d3m_handle* out, const d3m_pattern* pat, const int32_t* p
   ALLOC(h->d_x, double2, S.n * mr);
   ALLOC(h->d_xbest, double2, S.n * mr);
   ALLOC(h->d_r, double2, S.n * mr);
+  ALLOC(h->X2, float4, S.n * mr);
   UPLOAD(h->kblk_off, S.kblk_off);
   UPLOAD(h->res_ptr, S.res_ptr);
   UPLOAD(h->res_blk, S.res_blk);
@@ -591,6 +595,8 @@ int d3m_get_instance_omega(d3m_handle h, double* host_out, void* stream) {
 static ResidualParams residual_params(d3m_ctx* h, const double2* X, const double2* B, int nrhs) {
   ResidualParams p;
   p.K = h->K;
+  p.K2 = h->K2;
+  p.X2 = h->X2;
   p.kblk_off = h->kblk_off;
   p.res_ptr = h->res_ptr;
   p.res_blk = h->res_blk;
@@ -600,7 +606,6 @@ static ResidualParams residual_params(d3m_ctx* h, const double2* X, const double
   p.xoff_orig = h->xoff_orig;
   p.chunks = h->chunks;
   p.nrhs = nrhs;
-  p.rc = std::min(nrhs, 8);
   p.n = h->S.n;
   p.X = X;
   p.B = B;
@@ -654,6 +659,7 @@ static int enqueue_factor(d3m_ctx* h, const void* Kin, bool kdev, cudaStream_t s
   p.trace = h->trace;
   p.timeout_ns = h->opt.timeout_ns;
   p.piv_tol = 1e3 * (h->fp64 ? 1.1102230246251565e-16 : 5.9604644775390625e-08);
+  if (h->trace) CUDA_TRY(h, cudaMemsetAsync(h->trace, 0xff, (size_t)10 * ntiles * sizeof(int64_t), st));
   ev_begin(h, d3m_ctx::EV_FACTOR, st);
   if (h->tc) rc = launch_factor_tc(p, h->maps, h->nsm, st);
   else rc = launch_factor_simt(p, h->fp64, h->nsm, st);
@@ -965,7 +971,7 @@ int d3m_get_trace(d3m_handle h, int64_t* host_out, int64_t cap, int64_t* count, 
   CUDA_TRY(h, cudaStreamSynchronize((cudaStream_t)stream));
   if (host_out && cap > 0) {
     const int64_t m = std::min(cap, n);
-    CUDA_TRY(h, cudaMemcpy(host_out, h->trace, (size_t)m * 8 * sizeof(int64_t), cudaMemcpyDeviceToHost));
+    CUDA_TRY(h, cudaMemcpy(host_out, h->trace, (size_t)m * 10 * sizeof(int64_t), cudaMemcpyDeviceToHost));
   }
   return D3M_OK;
 }

@@ -133,7 +133,7 @@ __device__ __forceinline__ uint32_t sm_id() {
 }
 
 // Trace record of one task: start (at pop) and end (before its successors are released).
-constexpr int TRACE_W = 8;
+constexpr int TRACE_W = 10;
 __device__ __forceinline__ void trace_begin(const FactorParams& p, int task) {
   if (p.trace && threadIdx.x == 0) p.trace[TRACE_W * (int64_t)task] = (int64_t)globaltimer_ns();
 }
@@ -197,6 +197,10 @@ __device__ __forceinline__ void sched_complete(const FactorParams& p, int task) 
     for (int64_t e = e0 + threadIdx.x; e < e1; e += 32) {
       const int s = p.succ[e];
       if (atomicSub(&p.cnt[s], 1) == 1) {
+        if (p.trace) {
+          p.trace[TRACE_W * (int64_t)s + 8] = (int64_t)globaltimer_ns();
+          p.trace[TRACE_W * (int64_t)s + 9] = task;
+        }
         __threadfence();
         const int pos = atomicAdd(&p.ctl->tail, 1);
         atomicExch(&p.ready[pos], s);

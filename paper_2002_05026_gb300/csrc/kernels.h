@@ -13,6 +13,8 @@ struct FactorParams;
 
 struct ResidualParams {
   const double2* K;
+  const float4* K2;        // double-float split of K (hi_r, hi_i, lo_r, lo_i), K's layout
+  float4* X2;              // double-float split of X for the current residual (n x nrhs)
   const int64_t* kblk_off;
   const int64_t* res_ptr;
   const int32_t* res_blk;
@@ -22,7 +24,6 @@ struct ResidualParams {
   const int64_t* xoff_orig;
   const int2* chunks;      // (block f, first row) of every 32-row chunk
   int nrhs;
-  int rc;                  // rhs per thread block (<= 8)
   int64_t n;
   const double2* X;
   const double2* B;

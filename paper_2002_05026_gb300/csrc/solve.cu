@@ -746,60 +746,126 @@ __global__ void __launch_bounds__(GT) chain_kernel(ChainSweep s, const typename 
 }
 
 // ------------------------------------------------------------------ FP64 residual
-// r = b - K x (caller numbering), one thread per (row, rhs); |r|, |x| and |b| maxima per
-// (instance, column) (a batched handle holds several independent systems; one otherwise).
-__global__ void __launch_bounds__(256) residual_kernel(ResidualParams p) {
-  const int rc = p.rc;
-  const int i = threadIdx.x % 32, jl = threadIdx.x / 32;
-  const int j = blockIdx.y * rc + jl;
+// r = b - K x (caller numbering) to FP64 accuracy without the FP64 pipe doing the products.
+// GB300 issues FP32 instructions about 64x faster than FP64 ones, so every product runs on the
+// FP32 pipe in double-float form: K and x are held as unevaluated sums of two floats
+// (a = a_hi + a_lo, |a - a_hi - a_lo| <= 2^-48 |a|, split once per factorization / per call),
+// a_hi x_hi is formed exactly (product plus its FMA-recovered error), the two cross terms
+// a_hi x_lo + a_lo x_hi are added to that error, and the sum is kept as a renormalised pair
+// (s, c) (Knuth's two-sum of s and the product, then a fast two-sum), i.e. with about 2^-48
+// relative rounding per term.  Every 32 columns the pair is added into an FP64 accumulator,
+// and r = b - acc is formed in FP64.  Error: 2^-48 relative from the splits plus at most
+// 32 * 2^-48 of the chunk's absolute sum per chunk (typically a few 2^-48), then FP64 rounding
+// of the chunk sums: a few 1e-16 of |K||x| in practice, comparable to a plain FP64 dot product
+// and far below the 1e-12 backward-error target.
+// Thread (row u of block f, rhs group): RPT right-hand sides per thread share each K load.
+__device__ __forceinline__ void df_mac(float& s, float& c, float ah, float al, float xh, float xl) {
+  const float p = __fmul_rn(ah, xh);
+  float e = fmaf(ah, xh, -p);          // a_hi x_hi - p, exact
+  e = fmaf(ah, xl, e);
+  e = fmaf(al, xh, e);
+  const float t = __fadd_rn(s, p);     // two-sum s + p = t + err
+  const float bp = __fsub_rn(t, s);
+  const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(p, bp));
+  const float lo = __fadd_rn(c, __fadd_rn(err, e));
+  s = __fadd_rn(t, lo);                // renormalise: |c| stays within half an ulp of s
+  c = __fsub_rn(lo, __fsub_rn(s, t));
+}
+
+__device__ __forceinline__ float4 split_c(double2 v) {
+  const float hr = (float)v.x, hi = (float)v.y;
+  return make_float4(hr, hi, (float)(v.x - (double)hr), (float)(v.y - (double)hi));
+}
+
+// X2 = split(X) for the columns of one residual (n x nrhs, same layout)
+__global__ void split_x_kernel(const double2* __restrict__ X, float4* __restrict__ X2, int64_t total) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < total) X2[i] = split_c(X[i]);
+}
+
+constexpr int RES_CHUNK = 32;
+
+template <int RPT>
+__global__ void __launch_bounds__(128) residual_kernel(ResidualParams p) {
+  const int i = threadIdx.x % 32, w = threadIdx.x / 32;
+  const int j0 = (blockIdx.y * (blockDim.x / 32) + w) * RPT;
   const int2 ch = p.chunks[blockIdx.x];
   const int f = ch.x, u = ch.y + i;
   const int mf = p.m_orig[f];
-  const bool active = (u < mf) && (jl < rc) && (j < p.nrhs);
-  double2 acc = make_double2(0.0, 0.0);
+  const bool active = (u < mf) && (j0 < p.nrhs);
+  int nj = p.nrhs - j0;
+  nj = nj < RPT ? nj : RPT;
+  double accr[RPT], acci[RPT];
+#pragma unroll
+  for (int q = 0; q < RPT; ++q) accr[q] = acci[q] = 0.0;
   if (active) {
     for (int64_t e = p.res_ptr[f]; e < p.res_ptr[f + 1]; ++e) {
       const int blk = p.res_blk[e], g = p.res_src[e];
       const int mg = p.m_orig[g];
-      const double2* Kp = p.K + p.kblk_off[blk];
-      const double2* xg = p.X + (int64_t)j * p.n + p.xoff_orig[g];
-      if (p.res_tr[e]) {
-        const double2* row = Kp + (int64_t)u * mg;   // stored (g, f): entry (c, u)
-        for (int c = 0; c < mg; ++c) acc = cfma(__ldg(row + c), __ldg(xg + c), acc);
-      } else {
-        const double2* col = Kp + u;                 // stored (f, g): entry (u, c)
-        for (int c = 0; c < mg; ++c) acc = cfma(__ldg(col + (int64_t)c * mf), __ldg(xg + c), acc);
+      const float4* Kp = p.K2 + p.kblk_off[blk];
+      const bool tr = p.res_tr[e] != 0;
+      const float4* kb = tr ? Kp + (int64_t)u * mg : Kp + u;   // stored (g, f): (c, u) / (f, g): (u, c)
+      const int64_t ks = tr ? 1 : mf;
+      const float4* xg = p.X2 + (int64_t)j0 * p.n + p.xoff_orig[g];
+      for (int c0 = 0; c0 < mg; c0 += RES_CHUNK) {
+        const int c1 = min(mg, c0 + RES_CHUNK);
+        float sr[RPT], cr[RPT], si[RPT], ci[RPT];
+#pragma unroll
+        for (int q = 0; q < RPT; ++q) sr[q] = cr[q] = si[q] = ci[q] = 0.f;
+        for (int c = c0; c < c1; ++c) {
+          const float4 a = __ldg(kb + c * ks);          // (hi_r, hi_i, lo_r, lo_i)
+#pragma unroll
+          for (int q = 0; q < RPT; ++q) {
+            if (q < nj) {
+              const float4 x = __ldg(xg + (int64_t)q * p.n + c);
+              df_mac(sr[q], cr[q], a.x, a.z, x.x, x.z);       // + a_r x_r
+              df_mac(sr[q], cr[q], -a.y, -a.w, x.y, x.w);     // - a_i x_i
+              df_mac(si[q], ci[q], a.x, a.z, x.y, x.w);       // + a_r x_i
+              df_mac(si[q], ci[q], a.y, a.w, x.x, x.z);       // + a_i x_r
+            }
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < RPT; ++q) {
+          accr[q] += (double)sr[q] + (double)cr[q];
+          acci[q] += (double)si[q] + (double)ci[q];
+        }
       }
     }
   }
-  float ra = 0.f, xa = 0.f, ba = 0.f;
-  if (active) {
-    const int64_t o = (int64_t)j * p.n + p.xoff_orig[f] + u;
-    const double2 bv = p.B[o];
-    const double2 r = make_double2(bv.x - acc.x, bv.y - acc.y);
-    p.R[o] = r;
-    const float rx = (float)r.x, ry = (float)r.y;
-    ra = sqrtf(rx * rx + ry * ry);
-    const double2 xv = p.X[o];
-    const float xx = (float)xv.x, xy = (float)xv.y;
-    xa = sqrtf(xx * xx + xy * xy);
-    const float bx = (float)bv.x, by = (float)bv.y;
-    ba = sqrtf(bx * bx + by * by);
-  }
-  for (int o = 16; o > 0; o >>= 1) {
-    ra = fmaxf(ra, __shfl_xor_sync(0xffffffffu, ra, o));
-    xa = fmaxf(xa, __shfl_xor_sync(0xffffffffu, xa, o));
-    ba = fmaxf(ba, __shfl_xor_sync(0xffffffffu, ba, o));
-  }
-  if (i == 0 && jl < rc && j < p.nrhs) {
-    const int q = p.inst[f] * p.ld_norm + j;
-    atomicMax(p.rmax + q, __float_as_uint(ra));
-    atomicMax(p.xmax + q, __float_as_uint(xa));
-    atomicMax(p.bmax + q, __float_as_uint(ba));
+#pragma unroll
+  for (int q = 0; q < RPT; ++q) {
+    const int j = j0 + q;
+    float ra = 0.f, xa = 0.f, ba = 0.f;
+    if (active && q < nj) {
+      const int64_t o = (int64_t)j * p.n + p.xoff_orig[f] + u;
+      const double2 bv = p.B[o];
+      const double2 r = make_double2(bv.x - accr[q], bv.y - acci[q]);
+      p.R[o] = r;
+      const float rx = (float)r.x, ry = (float)r.y;
+      ra = sqrtf(rx * rx + ry * ry);
+      const double2 xv = p.X[o];
+      const float xx = (float)xv.x, xy = (float)xv.y;
+      xa = sqrtf(xx * xx + xy * xy);
+      const float bx = (float)bv.x, by = (float)bv.y;
+      ba = sqrtf(bx * bx + by * by);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      ra = fmaxf(ra, __shfl_xor_sync(0xffffffffu, ra, o));
+      xa = fmaxf(xa, __shfl_xor_sync(0xffffffffu, xa, o));
+      ba = fmaxf(ba, __shfl_xor_sync(0xffffffffu, ba, o));
+    }
+    if (i == 0 && j0 < p.nrhs && q < nj) {
+      const int qq = p.inst[f] * p.ld_norm + j;
+      atomicMax(p.rmax + qq, __float_as_uint(ra));
+      atomicMax(p.xmax + qq, __float_as_uint(xa));
+      atomicMax(p.bmax + qq, __float_as_uint(ba));
+    }
   }
 }
 
-// ||K||_inf row sums (float magnitudes; a scale for omega) and ||b||_inf per column.
+// ||K_i||_inf row sums (float magnitudes; a scale for omega), and the double-float split of K
+// used by the residual.
 __global__ void __launch_bounds__(256) knorm_kernel(ResidualParams p) {
   const int i = threadIdx.x % 32, part = threadIdx.x / 32;   // 8 warps split the contributions
   const int2 ch = p.chunks[blockIdx.x];
@@ -812,8 +878,12 @@ __global__ void __launch_bounds__(256) knorm_kernel(ResidualParams p) {
       const int blk = p.res_blk[e], g = p.res_src[e];
       const int mg = p.m_orig[g];
       const double2* Kp = p.K + p.kblk_off[blk];
+      const bool tr = p.res_tr[e] != 0;
+      float4* K2 = const_cast<float4*>(p.K2) + p.kblk_off[blk];
       for (int c = 0; c < mg; ++c) {
-        const double2 v = p.res_tr[e] ? __ldg(Kp + (int64_t)u * mg + c) : __ldg(Kp + (int64_t)c * mf + u);
+        const int64_t o = tr ? (int64_t)u * mg + c : (int64_t)c * mf + u;
+        const double2 v = __ldg(Kp + o);
+        if (!tr) K2[o] = split_c(v);            // every stored entry is visited once untransposed
         const float a = (float)v.x, bb = (float)v.y;
         sum += sqrtf(a * a + bb * bb);
       }
@@ -1074,8 +1144,16 @@ int launch_sweep(SweepLaunch& a, bool fp64, cudaStream_t st) {
 }
 
 int launch_residual(const ResidualParams& p, int nchunks, cudaStream_t st) {
-  const dim3 grid((unsigned)nchunks, (unsigned)((p.nrhs + p.rc - 1) / p.rc));
-  residual_kernel<<<grid, 32 * p.rc, 0, st>>>(p);
+  const int64_t total = p.n * (int64_t)p.nrhs;
+  split_x_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(p.X, p.X2, total);
+  // 4 warps per block, RPT right-hand sides per warp
+  if (p.nrhs == 1) {
+    residual_kernel<1><<<dim3((unsigned)nchunks, 1), 32, 0, st>>>(p);
+  } else {
+    const int groups = (p.nrhs + 1) / 2;                       // warps needed at RPT = 2
+    const int wpb = groups < 4 ? groups : 4;
+    residual_kernel<2><<<dim3((unsigned)nchunks, (unsigned)((groups + wpb - 1) / wpb)), 32 * wpb, 0, st>>>(p);
+  }
   return (int)cudaGetLastError();
 }
 

@@ -141,10 +141,11 @@ class D3M:
 
     def trace(self) -> np.ndarray:
         """Task records of the last factorization (handle created with debug_flags=2):
-        int64 [ntasks, 8] = start_ns, end_ns, sm_id, flags | tile << 8, t1..t4 (task id = row)."""
+        int64 [ntasks, 10] = start_ns, end_ns, sm_id, flags | tile << 8, t1..t4, ready_ns, releaser
+        (task id = row)."""
         cnt = ctypes.c_int64()
         check(self._lib.d3m_get_trace(self.h, None, 0, ctypes.byref(cnt), c_void_p(_stream_ptr(self.stream))), self.h)
-        out = np.zeros((cnt.value, 8), dtype=np.int64)
+        out = np.zeros((cnt.value, 10), dtype=np.int64)
         check(self._lib.d3m_get_trace(self.h, c_void_p(out.ctypes.data), cnt.value, ctypes.byref(cnt),
                                       c_void_p(_stream_ptr(self.stream))), self.h)
         return out
