@@ -91,6 +91,9 @@ typedef struct {
                                memory; one refinement step of a solve) into a CUDA graph on
                                first use and replay it afterwards; default 0 */
   int32_t reserved0;
+  double prio_slack;        /* tasks whose estimated slack is within prio_slack x the critical
+                               path are served first by the device scheduler (default 0.08;
+                               0 = only the critical path itself) */
 } d3m_options;
 
 /* Test hook: upload the task graph with one extra unmet dependency on the last task, so the
@@ -136,6 +139,8 @@ typedef struct {
   int64_t factor_kernel_calls, residual_calls, sweep_calls;
   int32_t instances;        /* independent systems held by the handle (1 unless batched) */
   int32_t reserved0;
+  int64_t prio_tasks;       /* tasks the device scheduler serves first: slack within 8% of the
+                               estimated critical path of the task graph */
 } d3m_info;
 
 /* Default options (precision D3M_MIXED_BF16X3). */

@@ -41,7 +41,8 @@ class d3m_pattern(ctypes.Structure):
 class d3m_options(ctypes.Structure):
     _fields_ = [("precision", c_int32), ("refine_max_iter", c_int32), ("refine_tol", c_double),
                 ("timeout_ns", c_int64), ("tile", c_int32), ("max_nrhs", c_int32),
-                ("fp64_omega", c_int32), ("debug_flags", c_int32), ("graphs", c_int32), ("reserved0", c_int32)]
+                ("fp64_omega", c_int32), ("debug_flags", c_int32), ("graphs", c_int32), ("reserved0", c_int32),
+                ("prio_slack", c_double)]
 
 
 class d3m_info(ctypes.Structure):
@@ -56,7 +57,7 @@ class d3m_info(ctypes.Structure):
                 ("kernel_launches", c_int64), ("factor_kernel_ms_total", c_double),
                 ("residual_ms_total", c_double), ("sweep_ms_total", c_double),
                 ("factor_kernel_calls", c_int64), ("residual_calls", c_int64), ("sweep_calls", c_int64),
-                ("instances", c_int32), ("reserved0", c_int32)]
+                ("instances", c_int32), ("reserved0", c_int32), ("prio_tasks", c_int64)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}

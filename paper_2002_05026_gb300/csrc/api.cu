@@ -54,6 +54,8 @@ struct d3m_ctx {
   int32_t* succ = nullptr;
   int32_t* ready = nullptr;
   int32_t* init_ready = nullptr;
+  int32_t* ready_hi = nullptr;       // priority lane
+  int32_t* init_ready_hi = nullptr;
   Ctl* ctl = nullptr;
   Ctl* ctl0 = nullptr;               // initial queue state, copied into ctl by every factor call
   Ctl* h_ctl = nullptr;              // pinned copy of ctl after the factorization
@@ -68,6 +70,8 @@ struct d3m_ctx {
   // solve
   SolveItem* fwd_items = nullptr;
   SolveItem* bwd_items = nullptr;
+  SolveGroup* fwd_groups = nullptr;
+  SolveGroup* bwd_groups = nullptr;
   int64_t* fwd_slot = nullptr;
   int64_t* bwd_slot = nullptr;
   int32_t* lev_blocks = nullptr;
@@ -81,6 +85,13 @@ struct d3m_ctx {
   void* Y = nullptr;
   void* P = nullptr;
   int max_rows = 0;
+  // inverses of the diagonal blocks (mixed precision): the solve applies each diagonal block as
+  // one product with its inverse
+  bool use_inv = false;
+  void* Inv = nullptr;
+  int64_t* inv_off = nullptr;
+  int2* inv_work = nullptr;
+  int n_inv_work = 0;
   // refinement / residual
   double2* d_b = nullptr;
   double2* d_x = nullptr;
@@ -254,6 +265,7 @@ void fill_structure(const Symbolic& S, d3m_info* info) {
   info->factor_flops = S.factor_flops;
   info->solve_flops_per_rhs = S.solve_flops_rhs;
   info->residual_flops_per_rhs = S.residual_flops_rhs;
+  info->prio_tasks = S.n_prio;
 }
 
 int factor_error(d3m_ctx* h) {
@@ -297,6 +309,7 @@ void d3m_default_options(d3m_options* o) {
   o->fp64_omega = 0;
   o->debug_flags = 0;
   o->graphs = 0;
+  o->prio_slack = 0.08;
 }
 
 int d3m_order_grid_nd(int32_t nx, int32_t ny, int32_t nz, int32_t* perm) {
@@ -343,6 +356,7 @@ static int create_impl(d3m_handle* out, const d3m_pattern* pat, const int32_t* p
   if (h->opt.refine_max_iter <= 0) h->opt.refine_max_iter = 20;
   if (!(h->opt.refine_tol > 0)) h->opt.refine_tol = 1e-12;
   if (h->opt.timeout_ns <= 0) h->opt.timeout_ns = 5000000000LL;
+  if (!(h->opt.prio_slack >= 0)) h->opt.prio_slack = 0.08;
   h->fp64 = (prec == D3M_FP64);
   h->tc = (prec == D3M_MIXED_BF16X3);
   h->b = h->tc ? 128 : 64;
@@ -352,7 +366,7 @@ static int create_impl(d3m_handle* out, const d3m_pattern* pat, const int32_t* p
   }
   h->csize = h->fp64 ? sizeof(double2) : sizeof(float2);
   std::string err;
-  int rc = analyze(pat, perm, h->b, true, h->S, err);
+  int rc = analyze(pat, perm, h->b, true, h->S, err, h->opt.prio_slack);
   if (rc != D3M_OK) {
     delete h;
     return set_err(nullptr, rc, err);
@@ -403,12 +417,15 @@ static int create_impl(d3m_handle* out, const d3m_pattern* pat, const int32_t* p
   UPLOAD(h->succ, S.succ);
   ALLOC(h->ready, int32_t, ntask);
   UPLOAD(h->init_ready, S.init_ready);
+  ALLOC(h->ready_hi, int32_t, std::max<int64_t>(1, S.n_prio));
+  UPLOAD(h->init_ready_hi, S.init_ready_hi);
   ALLOC(h->ctl, Ctl, 1);
   ALLOC(h->ctl0, Ctl, 1);
   {
     Ctl c0;
     std::memset(&c0, 0, sizeof c0);
     c0.tail = (int32_t)S.init_ready.size();
+    c0.tail_hi = (int32_t)S.init_ready_hi.size();
     c0.min_piv_bits = 0x7f7fffffu;   // FLT_MAX
     c0.max_piv_bits = 0u;
     CUDA_TRY(h, cudaMemcpy(h->ctl0, &c0, sizeof c0, cudaMemcpyHostToDevice));
@@ -431,6 +448,8 @@ static int create_impl(d3m_handle* out, const d3m_pattern* pat, const int32_t* p
   // solve
   UPLOAD(h->fwd_items, S.fwd_items);
   UPLOAD(h->bwd_items, S.bwd_items);
+  UPLOAD(h->fwd_groups, S.fwd_groups);
+  UPLOAD(h->bwd_groups, S.bwd_groups);
   UPLOAD(h->fwd_slot, S.fwd_slot_ptr);
   UPLOAD(h->bwd_slot, S.bwd_slot_ptr);
   {
@@ -474,8 +493,26 @@ static int create_impl(d3m_handle* out, const d3m_pattern* pat, const int32_t* p
   }
   UPLOAD(h->tstart, S.tstart);
   UPLOAD(h->tcolptr, S.tcolptr);
+  // mixed precision with blocks of at most 512 rows: build the diagonal blocks' inverses
+  h->use_inv = !h->fp64 && h->max_rows <= 512;
+  if (h->use_inv) {
+    std::vector<int64_t> off(S.N, 0);
+    std::vector<int2> work;
+    int64_t ninv = 0;
+    for (int k = 0; k < S.N; ++k) {
+      const int nt = S.ntile[k];
+      off[k] = ninv;
+      ninv += (int64_t)nt * (nt - 1) / 2;
+      for (int tq = 0; tq + 1 < nt; ++tq) work.push_back(make_int2(k, tq));
+    }
+    UPLOAD(h->inv_off, off);
+    UPLOAD(h->inv_work, work);
+    h->n_inv_work = (int)work.size();
+    h->Inv = dalloc<unsigned char>(h, (size_t)std::max<int64_t>(1, ninv) * b * b * h->csize);
+    if (!h->Inv) return set_err(h, D3M_ERR_OOM, "cudaMalloc failed for the block inverses");
+  }
   h->Y = dalloc<unsigned char>(h, (size_t)S.npad * mr * h->csize);
-  h->P = dalloc<unsigned char>(h, (size_t)std::max<int64_t>(1, S.max_level_items) * (b / 64) * b * mr * h->csize);
+  h->P = dalloc<unsigned char>(h, (size_t)std::max<int64_t>(1, S.max_level_groups) * (b / 64) * b * mr * h->csize);
   if (!h->Y || !h->P) return set_err(h, D3M_ERR_OOM, "cudaMalloc failed for the solve workspace");
   // refinement + residual
   ALLOC(h->d_b, double2, S.n * mr);
@@ -632,6 +669,10 @@ static int enqueue_factor(d3m_ctx* h, const void* Kin, bool kdev, cudaStream_t s
   CUDA_TRY(h, cudaMemsetAsync(h->ready, 0xff, ntiles * sizeof(int32_t), st));
   const int n0 = (int)S.init_ready.size();
   if (n0 > 0) CUDA_TRY(h, cudaMemcpyAsync(h->ready, h->init_ready, n0 * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+  CUDA_TRY(h, cudaMemsetAsync(h->ready_hi, 0xff, std::max<int64_t>(1, S.n_prio) * sizeof(int32_t), st));
+  const int n0h = (int)S.init_ready_hi.size();
+  if (n0h > 0)
+    CUDA_TRY(h, cudaMemcpyAsync(h->ready_hi, h->init_ready_hi, n0h * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
   CUDA_TRY(h, cudaMemcpyAsync(h->ctl, h->ctl0, sizeof(Ctl), cudaMemcpyDeviceToDevice, st));
   // ||K_i||_inf for the backward error
   ResidualParams rp = residual_params(h, nullptr, nullptr, 1);
@@ -646,6 +687,8 @@ static int enqueue_factor(d3m_ctx* h, const void* Kin, bool kdev, cudaStream_t s
   p.succ_ptr = h->succ_ptr;
   p.succ = h->succ;
   p.ready = h->ready;
+  p.ready_hi = h->ready_hi;
+  p.n_norm = (int32_t)(ntiles - S.n_prio);
   p.ctl = h->ctl;
   p.ntasks = (int32_t)ntiles;
   p.b = h->b;
@@ -666,6 +709,11 @@ static int enqueue_factor(d3m_ctx* h, const void* Kin, bool kdev, cudaStream_t s
   if (rc) return set_err(h, D3M_ERR_CUDA, std::string("factor launch: ") + cudaGetErrorString((cudaError_t)rc));
   ev_end(h, d3m_ctx::EV_FACTOR, st);
   h->launches += 1;
+  if (h->use_inv && h->n_inv_work > 0) {
+    rc = launch_inv_build(h->inv_work, h->n_inv_work, h->tstart, h->tcolptr, h->inv_off, h->L, h->Linv, h->Inv, h->b, st);
+    if (rc) return set_err(h, D3M_ERR_CUDA, std::string("block inverse launch: ") + cudaGetErrorString((cudaError_t)rc));
+    h->launches += 1;
+  }
   CUDA_TRY(h, cudaMemcpyAsync(h->h_ctl, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
   return D3M_OK;
 }
@@ -710,8 +758,10 @@ static int sweep(d3m_ctx* h, const double2* src, double2* dst, int nrhs, int acc
   a.D = h->D;
   a.Y = h->Y;
   a.P = h->P;
-  a.fwd_item_ptr = S.fwd_item_ptr.data();
-  a.bwd_item_ptr = S.bwd_item_ptr.data();
+  a.fwd_group_ptr = S.fwd_group_ptr.data();
+  a.bwd_group_ptr = S.bwd_group_ptr.data();
+  a.fwd_groups = h->fwd_groups;
+  a.bwd_groups = h->bwd_groups;
   a.fwd_items = h->fwd_items;
   a.bwd_items = h->bwd_items;
   a.fwd_slot_ptr = h->fwd_slot;
@@ -723,6 +773,9 @@ static int sweep(d3m_ctx* h, const double2* src, double2* dst, int nrhs, int acc
   a.tstart = h->tstart;
   a.tcolptr = h->tcolptr;
   a.lev_maxnt = h->lev_maxnt.data();
+  a.max_group = S.max_group;
+  a.Inv = h->use_inv ? h->Inv : nullptr;
+  a.inv_off = h->inv_off;
   ev_begin(h, d3m_ctx::EV_SWEEP, st);
   int rc = launch_sweep(a, h->fp64, st);
   if (rc) return set_err(h, D3M_ERR_CUDA, std::string("sweep launch: ") + cudaGetErrorString((cudaError_t)rc));

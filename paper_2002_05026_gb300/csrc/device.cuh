@@ -23,7 +23,7 @@ namespace d3m {
 
 struct Ctl {
   int32_t head, tail, done, abort;
-  int32_t err, err_task, pad0, pad1;
+  int32_t err, err_task, head_hi, tail_hi;
   uint32_t min_piv_bits, max_piv_bits;  // |d| as float bits (non-negative => ordered as uint)
   int32_t pad2[6];
 };
@@ -35,8 +35,10 @@ struct FactorParams {
   const int64_t* succ_ptr;
   const int32_t* succ;
   int32_t* ready;
+  int32_t* ready_hi;     // priority lane (tasks flagged TF_PRIO)
   Ctl* ctl;
   int32_t ntasks;
+  int32_t n_norm;        // tasks of the normal lane
   int32_t b;
   const double2* K;      // library copy of K (c128)
   void* L;               // [ntiles][b][b] complex (row-major tiles)
@@ -150,29 +152,56 @@ __device__ __forceinline__ void trace_mark(const FactorParams& p, int task, int 
 }
 
 // Claim the next ready task for this block (all threads call; returns -1 when done/aborted).
-__device__ __forceinline__ int sched_pop(const FactorParams& p, int* s_task) {
+// Two lanes: the priority lane is served first and claimed with a compare-and-swap only when a
+// pushed task is there; the normal lane keeps one claimed slot per block (*s_pending, -1 when
+// none), waited on between looks at the priority lane, so no block ever blocks on it alone.
+// A block leaves when its normal slot is past the lane's end and every task has completed.
+__device__ __forceinline__ int sched_pop(const FactorParams& p, int* s_task, int* s_pending) {
   if (threadIdx.x == 0) {
     int task = -1;
-    if (!ld_volatile(&p.ctl->abort)) {
-      int slot = atomicAdd(&p.ctl->head, 1);
-      if (slot < p.ntasks) {
-        const uint64_t t0 = globaltimer_ns();
-        unsigned ns = 32;
-        for (;;) {
-          task = ld_volatile(&p.ready[slot]);
-          if (task >= 0) break;
-          if (ld_volatile(&p.ctl->abort)) { task = -1; break; }
-          if (globaltimer_ns() - t0 > (uint64_t)p.timeout_ns) {
-            set_error(p.ctl, D3M_ERR_TIMEOUT, -1 - slot);
-            task = -1;
-            break;
+    int pend = *s_pending;
+    if (pend < 0 && !ld_volatile(&p.ctl->abort)) pend = atomicAdd(&p.ctl->head, 1);
+    const uint64_t t0 = globaltimer_ns();
+    unsigned ns = 32;
+    for (;;) {
+      if (ld_volatile(&p.ctl->abort)) { task = -1; break; }
+      const int hh = ld_volatile(&p.ctl->head_hi);
+      if (hh < ld_volatile(&p.ctl->tail_hi)) {
+        if (atomicCAS(&p.ctl->head_hi, hh, hh + 1) == hh) {
+          // the pusher reserved slot hh before writing it
+          for (;;) {
+            task = ld_volatile(&p.ready_hi[hh]);
+            if (task >= 0) break;
+            if (ld_volatile(&p.ctl->abort) || globaltimer_ns() - t0 > (uint64_t)p.timeout_ns) {
+              set_error(p.ctl, D3M_ERR_TIMEOUT, -1 - hh);
+              task = -1;
+              break;
+            }
           }
-          __nanosleep(ns);
-          if (ns < 256) ns <<= 1;
+          break;
         }
-        __threadfence();  // acquire: producer data is visible after this point
+        continue;
       }
+      if (pend < p.n_norm) {
+        task = ld_volatile(&p.ready[pend]);
+        if (task >= 0) {
+          pend = -1;
+          break;
+        }
+      } else if (ld_volatile(&p.ctl->done) >= p.ntasks) {
+        task = -1;
+        break;
+      }
+      if (globaltimer_ns() - t0 > (uint64_t)p.timeout_ns) {
+        set_error(p.ctl, D3M_ERR_TIMEOUT, -1 - pend);
+        task = -1;
+        break;
+      }
+      __nanosleep(ns);
+      if (ns < 256) ns <<= 1;
     }
+    if (task >= 0) __threadfence();  // acquire: producer data is visible after this point
+    *s_pending = pend;
     *s_task = task;
   }
   __syncthreads();
@@ -202,8 +231,13 @@ __device__ __forceinline__ void sched_complete(const FactorParams& p, int task) 
           p.trace[TRACE_W * (int64_t)s + 9] = task;
         }
         __threadfence();
-        const int pos = atomicAdd(&p.ctl->tail, 1);
-        atomicExch(&p.ready[pos], s);
+        if (p.tasks[s].flags & TF_PRIO) {
+          const int pos = atomicAdd(&p.ctl->tail_hi, 1);
+          atomicExch(&p.ready_hi[pos], s);
+        } else {
+          const int pos = atomicAdd(&p.ctl->tail, 1);
+          atomicExch(&p.ready[pos], s);
+        }
       }
     }
     if (threadIdx.x == 0) atomicAdd(&p.ctl->done, 1);

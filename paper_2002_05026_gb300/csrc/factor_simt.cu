@@ -34,7 +34,8 @@ __global__ void __launch_bounds__(NTHR, 1) factor_simt_kernel(FactorParams p) {
   __shared__ C s_d[TB];
   __shared__ C s_tmp[TB];
   __shared__ R s_red[NTHR / 32];
-  __shared__ int s_task;
+  __shared__ int s_task, s_pending;
+  if (threadIdx.x == 0) s_pending = -1;          // read and written by thread 0 only
 
   C* Lg = reinterpret_cast<C*>(p.L);
   C* Linv = reinterpret_cast<C*>(p.Linv);
@@ -44,7 +45,7 @@ __global__ void __launch_bounds__(NTHR, 1) factor_simt_kernel(FactorParams p) {
   const int tx = tid & 15, ty = tid >> 4;
 
   for (;;) {
-    const int task = sched_pop(p, &s_task);
+    const int task = sched_pop(p, &s_task, &s_pending);
     if (task < 0) break;
     const TileTask T = p.tasks[task];
 

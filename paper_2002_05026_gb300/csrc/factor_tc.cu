@@ -192,7 +192,8 @@ __global__ void __launch_bounds__(NTHR, 1)
   unsigned char* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   __shared__ __align__(8) uint64_t bar_full[2], bar_empty[2], bar_tfull[2], bar_tempty[2], bar_acc, bar_acc2;
   __shared__ uint32_t s_tmem;
-  __shared__ int s_task;
+  __shared__ int s_task, s_pending;
+  if (threadIdx.x == 0) s_pending = -1;          // read and written by thread 0 only
   __shared__ float s_red[NTHR / 32];
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -233,7 +234,7 @@ __global__ void __launch_bounds__(NTHR, 1)
   bool failed = false;
 
   for (;;) {
-    const int task = sched_pop(p, &s_task);
+    const int task = sched_pop(p, &s_task, &s_pending);
     if (task < 0) break;
     const TileTask T = p.tasks[task];
     const uint64_t deadline = globaltimer_ns() + (uint64_t)p.timeout_ns;

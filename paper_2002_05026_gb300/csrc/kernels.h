@@ -48,8 +48,10 @@ struct SweepLaunch {
   const void* D;
   void* Y;                         // [nrhs][npad] work vector
   void* P;                         // partials
-  const int64_t* fwd_item_ptr;     // host [nlevels+1]
-  const int64_t* bwd_item_ptr;     // host [nlevels+1]
+  const int64_t* fwd_group_ptr;    // host [nlevels+1]
+  const int64_t* bwd_group_ptr;    // host [nlevels+1]
+  const SolveGroup* fwd_groups;    // device
+  const SolveGroup* bwd_groups;    // device
   const SolveItem* fwd_items;      // device
   const SolveItem* bwd_items;      // device
   const int64_t* fwd_slot_ptr;     // device [NT]
@@ -61,6 +63,9 @@ struct SweepLaunch {
   const int32_t* tstart;           // device [N+1]
   const int64_t* tcolptr;          // device [NT+1]
   const int32_t* lev_maxnt;        // host [nlevels]: most tiles of one block in the level
+  int max_group;                   // most items summed by one gather block
+  const void* Inv;                 // off-diagonal tiles of the diagonal blocks' inverses, or nullptr
+  const int64_t* inv_off;          // device [N]: first tile of block k in Inv
   int64_t launches;                // out: kernels launched by launch_sweep
 };
 
@@ -74,6 +79,10 @@ int launch_factor_simt(const FactorParams& p, bool fp64, int nblocks, cudaStream
 int tc_make_maps(void* opA, void* opB, int64_t ntiles, TcMaps* out, std::string& err);
 int launch_factor_tc(const FactorParams& p, const TcMaps& maps, int nblocks, cudaStream_t st);
 int launch_sweep(SweepLaunch& a, bool fp64, cudaStream_t st);
+// Inverses of the unit-lower diagonal blocks (c64 tiles of edge b in {64, 128}), built from L and
+// the inverses of the diagonal tiles: work = (block, tile column) pairs.
+int launch_inv_build(const int2* work, int nwork, const int32_t* tstart, const int64_t* tcolptr,
+                     const int64_t* inv_off, const void* L, const void* Linv, void* Inv, int b, cudaStream_t st);
 int launch_residual(const ResidualParams& p, int nchunks, cudaStream_t st);
 int launch_knorm(const ResidualParams& p, int nchunks, cudaStream_t st);
 int launch_absmax(const double2* V, int64_t n, int nrhs, unsigned* out, cudaStream_t st);

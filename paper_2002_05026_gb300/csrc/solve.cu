@@ -123,9 +123,9 @@ __device__ __forceinline__ void quad_reduce(C* acc) {
     }
 }
 
-// dst[r][j] (=, or -=) sum_c M[r][c] V[c][j] for the 64 rows of a staged half tile M
-// ([64][ldl]); V element (c, j) at V[c * ldv + j]; dst element (r, j) at dst[r * ldd + j].
-template <typename R, bool SUB>
+// dst[r][j] (=, +=, or -= by MODE 0 / 1 / 2) sum_c M[r][c] V[c][j] for the 64 rows of a staged
+// half tile M ([64][ldl]); V element (c, j) at V[c * ldv + j]; dst element (r, j) at dst[r * ldd + j].
+template <typename R, int MODE>
 __device__ __forceinline__ void rows_matvec(const typename CT<R>::C* M, int ldl, int b, const typename CT<R>::C* V,
                                             int ldv, int rc, typename CT<R>::C* dst, int ldd) {
   using C = typename CT<R>::C;
@@ -149,7 +149,8 @@ __device__ __forceinline__ void rows_matvec(const typename CT<R>::C* M, int ldl,
   if (cq == 0) {
 #pragma unroll
     for (int j = 0; j < RCMAX; ++j)
-      if (j < rc) dst[r * ldd + j] = SUB ? csub(dst[r * ldd + j], acc[j]) : acc[j];
+      if (j < rc)
+        dst[r * ldd + j] = MODE == 0 ? acc[j] : (MODE == 1 ? cadd(dst[r * ldd + j], acc[j]) : csub(dst[r * ldd + j], acc[j]));
   }
 }
 
@@ -187,11 +188,37 @@ __device__ __forceinline__ void cols_matvec(const typename CT<R>::C* M, int ldl,
 }
 
 // ------------------------------------------------------------------ gather (off-block tiles)
-// grid.x = items of the level * (b / 64) halves.  FWD: P[slot][r][j] (rows of this half) =
-// sum_k L[r][k] Y[src*b + k][j].  BWD: P[slot*nh + h][c][j] = sum_{r in half h} L[r][c] W[src*b + r][j].
-// Partials are stored [row][nrhs].
+// grid = (groups of the level * (b / 64) halves, ceil(nrhs / 8) rhs groups).  A block sums the
+// products of its group's items (consecutive off-block tiles of one destination) for one
+// 64-row half h of the tiles and up to 8 right-hand sides:
+//   FWD: P[slot][h*64 + r][j] = sum_items sum_k L[h*64 + r][k] Y[src*b + k][j];
+//   BWD: P[slot*nh + h][c][j] = sum_items sum_{r < 64} L[h*64 + r][c] W[src*b + h*64 + r][j].
+// Each item's tile half and source rows are brought in by bulk copies on one mbarrier, double
+// buffered, so the next item loads while the current one is multiplied.
+template <typename C>
+__device__ __forceinline__ void stage_item(C* sT, C* sV, int ldl, int ldv, const C* tile, const C* Y, int64_t npad,
+                                           int64_t y0, int vlen, int j0, int rc, int b, int h, uint64_t* bar) {
+  if (threadIdx.x >= 32) return;
+  const uint32_t row_bytes = (uint32_t)(b * sizeof(C)), v_bytes = (uint32_t)(vlen * sizeof(C));
+  if (threadIdx.x == 0)
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+                 "r"(HR * row_bytes + rc * v_bytes)
+                 : "memory");
+  __syncwarp();
+  for (int r = threadIdx.x; r < HR + rc; r += 32) {
+    const C* src = r < HR ? tile + (int64_t)(h * HR + r) * b : Y + (int64_t)(j0 + r - HR) * npad + y0;
+    C* dst = r < HR ? sT + r * ldl : sV + (r - HR) * ldv;
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(r < HR ? row_bytes : v_bytes), "r"(smem_addr(bar))
+        : "memory");
+  }
+}
+
 template <typename R, bool FWD>
-__global__ void __launch_bounds__(GT) gather_kernel(const SolveItem* __restrict__ items,
+__global__ void __launch_bounds__(GT) gather_kernel(const SolveGroup* __restrict__ groups,
+                                                    const SolveItem* __restrict__ items,
                                                     const typename CT<R>::C* __restrict__ L,
                                                     const typename CT<R>::C* __restrict__ Y,
                                                     typename CT<R>::C* __restrict__ P,
@@ -200,37 +227,97 @@ __global__ void __launch_bounds__(GT) gather_kernel(const SolveItem* __restrict_
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int nh = b / HR;
   const int ldl = stage_ld<C>(b);
-  C* sL = reinterpret_cast<C*>(smem_raw);      // [64][ldl]
-  C* sY = sL + HR * ldl;                       // [rows][ldy]
-  const int ldy = vec_ld(nrhs);
-  __shared__ __align__(8) uint64_t bar;
-  const SolveItem it = items[blockIdx.x / nh];
+  const int vlen = FWD ? b : HR;                         // source rows per right-hand side
+  const int ldv = vlen + (int)(16 / sizeof(C));
+  const int stg = HR * ldl + RCMAX * ldv;                // elements of one stage buffer
+  C* buf[2] = {reinterpret_cast<C*>(smem_raw), reinterpret_cast<C*>(smem_raw) + stg};
+  __shared__ __align__(8) uint64_t bars[2];
+  const SolveGroup gr = groups[blockIdx.x / nh];
   const int h = blockIdx.x % nh;
+  const int j0 = blockIdx.y * RCMAX;
+  const int rc = min(RCMAX, nrhs - j0);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
-    mbar_init_s(&bar);
+    mbar_init_s(&bars[0]);
+    mbar_init_s(&bars[1]);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
-  stage_bulk(sL, L + (int64_t)it.tile * b * b, b, h * HR, &bar);
-  const int rows = FWD ? b : HR;
-  const int64_t y0 = (int64_t)it.src * b + (FWD ? 0 : h * HR);
-  for (int i = threadIdx.x; i < rows * nrhs; i += GT) {
-    const int k = i % rows, j = i / rows;
-    sY[k * ldy + j] = Y[j * npad + y0 + k];
-  }
-  const bool late = !mbar_wait_s(&bar, 0, globaltimer_ns() + SWEEP_TIMEOUT_NS);
-  if (__syncthreads_or(late)) {
-    if (threadIdx.x == 0) atomicExch(status, (int)D3M_ERR_TIMEOUT);
-    return;
-  }
-  for (int j0 = 0; j0 < nrhs; j0 += RCMAX) {
-    const int rc = min(RCMAX, nrhs - j0);
+  auto stage = [&](int k) {
+    const SolveItem it = items[gr.first + k];
+    const int64_t y0 = (int64_t)it.src * b + (FWD ? 0 : h * HR);
+    C* T = buf[k & 1];
+    stage_item(T, T + HR * ldl, ldl, ldv, L + (int64_t)it.tile * b * b, Y, npad, y0, vlen, j0, rc, b, h, &bars[k & 1]);
+  };
+  stage(0);
+  constexpr int NCH = FWD ? 1 : 2;                       // column chunks of 64 (backward, b = 128)
+  C acc[NCH][RCMAX];
+#pragma unroll
+  for (int q = 0; q < NCH; ++q)
+#pragma unroll
+    for (int j = 0; j < RCMAX; ++j) acc[q][j] = CT<R>::make(0, 0);
+  uint32_t phase[2] = {0u, 0u};
+  const uint64_t deadline = globaltimer_ns() + SWEEP_TIMEOUT_NS;
+  for (int k = 0; k < gr.count; ++k) {
+    if (k + 1 < gr.count) {
+      // the other buffer was last read in item k-1, which ended with a barrier
+      if (threadIdx.x < 32) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      stage(k + 1);
+    }
+    const bool late = !mbar_wait_s(&bars[k & 1], phase[k & 1], deadline);
+    phase[k & 1] ^= 1u;
+    if (__syncthreads_or(late)) {
+      if (threadIdx.x == 0) atomicExch(status, (int)D3M_ERR_TIMEOUT);
+      return;
+    }
+    const C* M = buf[k & 1];
+    const C* V = M + HR * ldl;
     if (FWD) {
-      C* out = P + (int64_t)it.slot * nh * b * nrhs + (int64_t)h * HR * nrhs + j0;   // sub-slot 0
-      rows_matvec<R, false>(sL, ldl, b, sY + j0, ldy, rc, out, nrhs);
+      // row r of the half, reduction index split over 4 lanes
+      const int r = warp * 8 + (lane >> 2), cq = lane & 3;
+#pragma unroll 4
+      for (int c = cq; c < b; c += 4) {
+        const C m = M[r * ldl + c];
+#pragma unroll
+        for (int j = 0; j < RCMAX; ++j)
+          if (j < rc) acc[0][j] = cfma(m, V[j * ldv + c], acc[0][j]);
+      }
     } else {
-      C* out = P + ((int64_t)it.slot * nh + h) * b * nrhs + j0;
-      cols_matvec<R, 0>(sL, ldl, b, sY + j0, ldy, rc, out, nrhs);
+      const int rq = lane & 3;
+#pragma unroll
+      for (int q = 0; q < NCH; ++q) {
+        const int c = q * 64 + warp * 8 + (lane >> 2);
+        if (c >= b) break;
+#pragma unroll 4
+        for (int r = rq; r < HR; r += 4) {
+          const C m = M[r * ldl + c];
+#pragma unroll
+          for (int j = 0; j < RCMAX; ++j)
+            if (j < rc) acc[q][j] = cfma(m, V[j * ldv + r], acc[q][j]);
+        }
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int q = 0; q < NCH; ++q) quad_reduce(acc[q]);
+  if ((lane & 3) == 0) {
+    if (FWD) {
+      const int r = warp * 8 + (lane >> 2);
+      C* out = P + (int64_t)gr.slot * nh * b * nrhs + (int64_t)(h * HR + r) * nrhs + j0;
+#pragma unroll
+      for (int j = 0; j < RCMAX; ++j)
+        if (j < rc) out[j] = acc[0][j];
+    } else {
+#pragma unroll
+      for (int q = 0; q < NCH; ++q) {
+        const int c = q * 64 + warp * 8 + (lane >> 2);
+        if (c >= b) break;
+        C* out = P + ((int64_t)gr.slot * nh + h) * b * nrhs + (int64_t)c * nrhs + j0;
+#pragma unroll
+        for (int j = 0; j < RCMAX; ++j)
+          if (j < rc) out[j] = acc[q][j];
+      }
     }
   }
 }
@@ -371,7 +458,7 @@ __global__ void __launch_bounds__(GT) block_fwd_kernel(BlockSweep s, const typen
       const int h = q % nh;
       if (q < nh) {
         // y_t rows [h*64, h*64+64) = Linv_t[rows] r_t
-        rows_matvec<R, false>(cur, ldl, b, sv + (int64_t)t * b * ldv, ldv, rc, sy + h * HR * ldv, ldv);
+        rows_matvec<R, 0>(cur, ldl, b, sv + (int64_t)t * b * ldv, ldv, rc, sy + h * HR * ldv, ldv);
         if (q == nh - 1) {
           __syncthreads();
           for (int i = threadIdx.x; i < b * rc; i += GT) {
@@ -381,7 +468,7 @@ __global__ void __launch_bounds__(GT) block_fwd_kernel(BlockSweep s, const typen
         }
       } else {
         const int tp = t + 1 + (q - nh) / nh;
-        rows_matvec<R, true>(cur, ldl, b, sy, ldv, rc, sv + (int64_t)(tp * b + h * HR) * ldv, ldv);
+        rows_matvec<R, 2>(cur, ldl, b, sy, ldv, rc, sv + (int64_t)(tp * b + h * HR) * ldv, ldv);
       }
       __syncthreads();
     }
@@ -525,8 +612,9 @@ __device__ __forceinline__ void stage_rows(C* dst, int ldd, const C* src, int ld
         : "memory");
 }
 
-// dst[c][j] (= or -=) sum_{r < nrows} M[r][c] V[r][j] for the 64 columns of a staged column strip
-template <typename R, bool SUB>
+// dst[c][j] (=, +=, or -= by MODE 0 / 1 / 2) sum_{r < nrows} M[r][c] V[r][j] for the 64 columns of
+// a staged column strip
+template <typename R, int MODE>
 __device__ __forceinline__ void colstrip_matvec(const typename CT<R>::C* M, int ldm, int nrows,
                                                 const typename CT<R>::C* V, int ldv, int rc,
                                                 typename CT<R>::C* dst, int ldd) {
@@ -550,7 +638,8 @@ __device__ __forceinline__ void colstrip_matvec(const typename CT<R>::C* M, int 
   if (rq == 0) {
 #pragma unroll
     for (int j = 0; j < RCMAX; ++j)
-      if (j < rc) dst[c * ldd + j] = SUB ? csub(dst[c * ldd + j], acc[j]) : acc[j];
+      if (j < rc)
+        dst[c * ldd + j] = MODE == 0 ? acc[j] : (MODE == 1 ? cadd(dst[c * ldd + j], acc[j]) : csub(dst[c * ldd + j], acc[j]));
   }
 }
 
@@ -566,13 +655,20 @@ struct ChainSweep {
   int b, nrhs, rc;           // rhs per cluster (grid.y = ceil(nrhs / rc))
   int cl, nloc, stg;         // CTAs per cluster, strip slots per CTA, elements of one stage buffer
   int has_partials;
+  const void* Inv;           // off-diagonal tiles of the inverses of the diagonal blocks (INV mode)
+  const int64_t* inv_off;    // [N] first tile of block k in Inv
+  int rrows;                 // rows of the largest block (INV mode: the whole r is gathered)
 };
 
 constexpr int CHAIN_MAXJ = 128;   // staged strips of one CTA
 constexpr int CHAIN_MAXCL = 8;    // portable cluster size
 constexpr int CHAIN_MAXLOC = 4;   // strips per CTA
 
-template <typename R, bool FWD>
+// INV mode: the diagonal block is applied as one product with its stored inverse,
+//   y_J = L_JJ^{-1} r_J (forward),  w_J = L_JJ^{-T} r_J (backward),
+// so every CTA only needs the whole r_J (one exchange through distributed shared memory) and
+// its own strips of the inverse: no sequential steps and no barriers between them.
+template <typename R, bool FWD, bool INV>
 __global__ void __launch_bounds__(GT) chain_kernel(ChainSweep s, const typename CT<R>::C* __restrict__ L,
                                                    const typename CT<R>::C* __restrict__ Linv,
                                                    typename CT<R>::C* __restrict__ Y) {
@@ -597,10 +693,30 @@ __global__ void __launch_bounds__(GT) chain_kernel(ChainSweep s, const typename 
   C* sy = stg1 + s.stg;                              // [b][ldv]   gathered r_t or y_t
   C* rbuf = sy + (int64_t)b * ldv;                   // [nloc][64][ldv]  running strips
   C* obuf = rbuf + (int64_t)s.nloc * HR * ldv;       // [nloc][64][ldv]  solved strips
+  C* sR = obuf + (int64_t)s.nloc * HR * ldv;         // INV: [rrows][ldv] the whole r_J
+  const C* Inv = reinterpret_cast<const C*>(s.Inv);
   if (threadIdx.x < nt) s_cp[threadIdx.x] = s.tcolptr[t0 + threadIdx.x];
   __syncthreads();
   // staged strips in consumption order: per step, the strip of tile t first, then the updates
-  if (threadIdx.x == 0) {
+  // (INV: per local strip, its tiles of the inverse)
+  if (threadIdx.x == 0 && INV) {
+    int nj = 0;
+    const int64_t ib = s.inv_off[k];
+    for (int l = 0; l < nloc; ++l) {
+      const int sid = rank + l * CL, tq = sid / nh, h = sid % nh;
+      const int64_t hoff = FWD ? (int64_t)h * HR * b : (int64_t)h * HR;
+      for (int t = FWD ? 0 : tq; t < (FWD ? tq + 1 : nt); ++t) {
+        // forward: tile (tq, t) of the inverse; backward: tile (t, tq)
+        const int tr = FWD ? tq : t, tc = FWD ? t : tq;
+        s_job[nj++] = (tr == tc ? Linv + (int64_t)(t0 + tr) * b * b : Inv + (ib + tr * (tr - 1) / 2 + tc) * (int64_t)b * b) + hoff;
+      }
+    }
+    s_nj = nj;
+    mbar_init_s(&bars[0]);
+    mbar_init_s(&bars[1]);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (threadIdx.x == 0 && !INV) {
     int nj = 0;
     for (int q = 0; q < nt; ++q) {
       const int t = FWD ? q : nt - 1 - q;
@@ -649,17 +765,17 @@ __global__ void __launch_bounds__(GT) chain_kernel(ChainSweep s, const typename 
         C v = Y[(int64_t)(j0 + j) * s.npad + g];
         if (!FWD) v = cdiv(v, D[g]);
         if (cnt) {
+          // 16 independent loads in flight per thread, summed in slot order within each batch
           const C* pp = P + first * nh * (int64_t)b * s.nrhs + (int64_t)(h * HR + row) * s.nrhs + (j0 + j);
-          C a0 = czero<R>(), a1 = czero<R>(), a2 = czero<R>(), a3 = czero<R>();
-          int64_t q = 0;
-          for (; q + 4 <= cnt; q += 4) {
-            a0 = cadd(a0, pp[(q + 0) * stride]);
-            a1 = cadd(a1, pp[(q + 1) * stride]);
-            a2 = cadd(a2, pp[(q + 2) * stride]);
-            a3 = cadd(a3, pp[(q + 3) * stride]);
+          C acc = czero<R>();
+          for (int64_t q0 = 0; q0 < cnt; q0 += 16) {
+            C t[16];
+#pragma unroll
+            for (int u = 0; u < 16; ++u) t[u] = (q0 + u < cnt) ? pp[(q0 + u) * stride] : czero<R>();
+#pragma unroll
+            for (int u = 0; u < 16; ++u) acc = cadd(acc, t[u]);
           }
-          for (; q < cnt; ++q) a0 = cadd(a0, pp[q * stride]);
-          v = csub(v, cadd(cadd(a0, a1), cadd(a2, a3)));
+          v = csub(v, acc);
         }
         rbuf[(l * HR + row) * ldv + j] = v;
       }
@@ -694,6 +810,40 @@ __global__ void __launch_bounds__(GT) chain_kernel(ChainSweep s, const typename 
   };
   __syncthreads();
   cluster_sync_all();                                 // every strip of r is loaded
+  if constexpr (INV) {
+    // the whole r_J from the owners' strips
+    for (int i = threadIdx.x; i < nt * b * rc; i += GT) {
+      const int j = i % rc, row = i / rc;
+      const int sid = row / HR;
+      const C* src = cluster_map(rbuf + (int64_t)(sid / CL) * HR * ldv, (uint32_t)(sid % CL));
+      sR[row * ldv + j] = src[(row % HR) * ldv + j];
+    }
+    __syncthreads();
+    for (int l = 0; l < nloc; ++l) {
+      const int sid = rank + l * CL, tq = sid / nh, h = sid % nh;
+      C* o = obuf + (int64_t)l * HR * ldv;
+      const int n = FWD ? tq + 1 : nt - tq;
+      for (int q = 0; q < n; ++q) {
+        const C* M = next_stage();
+        const C* V = sR + (int64_t)(FWD ? q : tq + q) * b * ldv;
+        if (!bad) {
+          if (FWD) {
+            if (q == 0) rows_matvec<R, 0>(M, ldst, b, V, ldv, rc, o, ldv);
+            else rows_matvec<R, 1>(M, ldst, b, V, ldv, rc, o, ldv);
+          } else {
+            if (q == 0) colstrip_matvec<R, 0>(M, ldst, b, V, ldv, rc, o, ldv);
+            else colstrip_matvec<R, 1>(M, ldst, b, V, ldv, rc, o, ldv);
+          }
+        }
+        __syncthreads();
+      }
+      for (int i = threadIdx.x; i < HR * rc; i += GT) {
+        const int row = i % HR, j = i / HR;
+        Y[(int64_t)(j0 + j) * s.npad + (int64_t)(t0 + tq) * b + h * HR + row] = o[row * ldv + j];
+      }
+    }
+    cluster_sync_all();                               // nobody reads this CTA's strips any more
+  } else {
   for (int q = 0; q < nt; ++q) {
     const int t = FWD ? q : nt - 1 - q;
     // ---- the owners of tile t solve their halves
@@ -708,8 +858,8 @@ __global__ void __launch_bounds__(GT) chain_kernel(ChainSweep s, const typename 
         const C* M = next_stage();
         C* o = obuf + (int64_t)l * HR * ldv;
         if (!bad) {
-          if (FWD) rows_matvec<R, false>(M, ldst, b, sy, ldv, rc, o, ldv);
-          else colstrip_matvec<R, false>(M, ldst, b, sy, ldv, rc, o, ldv);
+          if (FWD) rows_matvec<R, 0>(M, ldst, b, sy, ldv, rc, o, ldv);
+          else colstrip_matvec<R, 0>(M, ldst, b, sy, ldv, rc, o, ldv);
         }
         __syncthreads();
         for (int i = threadIdx.x; i < HR * rc; i += GT) {
@@ -734,13 +884,14 @@ __global__ void __launch_bounds__(GT) chain_kernel(ChainSweep s, const typename 
         const C* M = next_stage();
         C* r = rbuf + (int64_t)l * HR * ldv;
         if (!bad) {
-          if (FWD) rows_matvec<R, true>(M, ldst, b, sy, ldv, rc, r, ldv);
-          else colstrip_matvec<R, true>(M, ldst, b, sy, ldv, rc, r, ldv);
+          if (FWD) rows_matvec<R, 2>(M, ldst, b, sy, ldv, rc, r, ldv);
+          else colstrip_matvec<R, 2>(M, ldst, b, sy, ldv, rc, r, ldv);
         }
         __syncthreads();
       }
     }
     cluster_sync_all();                               // the strips of tile t+1 (t-1) are final
+  }
   }
   if (bad && threadIdx.x == 0) atomicExch(s.status, (int)D3M_ERR_TIMEOUT);
 }
@@ -775,6 +926,31 @@ __device__ __forceinline__ void df_mac(float& s, float& c, float ah, float al, f
 __device__ __forceinline__ float4 split_c(double2 v) {
   const float hr = (float)v.x, hi = (float)v.y;
   return make_float4(hr, hi, (float)(v.x - (double)hr), (float)(v.y - (double)hi));
+}
+
+// The same split with integer operations only (the split of K runs once per factorization
+// over every stored entry; FP64 conversions would make it FP64-pipe bound): hi = x truncated
+// to 24 significant bits, lo = the remaining 29 bits rounded to a float, |x - hi - lo| <=
+// 2^-47 |x|.  Zeros and magnitudes outside [2^-74, 2^127] take the FP64 conversion path.
+__device__ __forceinline__ void split_bits(double x, float& hi, float& lo) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const int e = (int)((u >> 52) & 0x7ff);
+  if (e < 949 || e > 1150) {
+    hi = (float)x;
+    lo = (float)(x - (double)hi);
+    return;
+  }
+  const unsigned sign = (unsigned)(u >> 63) << 31;
+  const unsigned long long mant = u & 0xFFFFFFFFFFFFFull;
+  hi = __uint_as_float(sign | ((unsigned)(e - 896) << 23) | (unsigned)(mant >> 29));
+  const float r = __uint2float_rn((unsigned)(mant & 0x1FFFFFFFull)) * __uint_as_float((unsigned)(e - 948) << 23);
+  lo = __uint_as_float(__float_as_uint(r) | sign);
+}
+__device__ __forceinline__ float4 split_c_bits(double2 v) {
+  float4 o;
+  split_bits(v.x, o.x, o.z);
+  split_bits(v.y, o.y, o.w);
+  return o;
 }
 
 // X2 = split(X) for the columns of one residual (n x nrhs, same layout)
@@ -882,10 +1058,9 @@ __global__ void __launch_bounds__(256) knorm_kernel(ResidualParams p) {
       float4* K2 = const_cast<float4*>(p.K2) + p.kblk_off[blk];
       for (int c = 0; c < mg; ++c) {
         const int64_t o = tr ? (int64_t)u * mg + c : (int64_t)c * mf + u;
-        const double2 v = __ldg(Kp + o);
-        if (!tr) K2[o] = split_c(v);            // every stored entry is visited once untransposed
-        const float a = (float)v.x, bb = (float)v.y;
-        sum += sqrtf(a * a + bb * bb);
+        const float4 v = split_c_bits(__ldg(Kp + o));
+        if (!tr) K2[o] = v;                     // every stored entry is visited once untransposed
+        sum += sqrtf(v.x * v.x + v.y * v.y);
       }
     }
   }
@@ -997,7 +1172,11 @@ static int sweep_impl(SweepLaunch& a, cudaStream_t st) {
   a.launches = 0;
   permute_in_kernel<R><<<(unsigned)gblocks, nthreads, 0, st>>>(a.src, a.n, Y, a.npad, a.pad2orig, a.nrhs);
   ++a.launches;
-  const size_t gsm = sizeof(C) * ((size_t)HR * stage_ld<C>(b) + (size_t)b * vec_ld(a.nrhs));
+  // gather: one stage buffer of a 64-row tile half and <= 8 source rows (padded by 16 bytes),
+  // two when a block sums several items (the next item loads while the current one is used)
+  const size_t gsm = (a.max_group > 1 ? 2 : 1) * sizeof(C) *
+                     ((size_t)HR * stage_ld<C>(b) + (size_t)RCMAX * (b + 16 / sizeof(C)));
+  const unsigned gy = (unsigned)((a.nrhs + RCMAX - 1) / RCMAX);
   cudaFuncSetAttribute(gather_kernel<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm);
   cudaFuncSetAttribute(gather_kernel<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm);
   // cluster chains: usable when every level's largest block fits CHAIN_MAXCL x CHAIN_MAXLOC strips
@@ -1013,13 +1192,23 @@ static int sweep_impl(SweepLaunch& a, cudaStream_t st) {
     if (nloc > CHAIN_MAXLOC || a.lev_maxnt[lv] > MAXNT) chain = false;
     max_loc = std::max(max_loc, nloc);
   }
+  // INV mode (inverses of the diagonal blocks were built with the factorization): the whole r_J
+  // of the largest block is gathered into shared memory as well
+  const bool inv = a.Inv != nullptr;
+  const size_t rrows = inv ? (size_t)a.max_rows : 0;
   auto chain_smem = [&](int nloc) {
-    return sizeof(C) * (2 * (size_t)cstg + (size_t)b * cldv + 2 * (size_t)nloc * HR * cldv);
+    return sizeof(C) * (2 * (size_t)cstg + (size_t)b * cldv + 2 * (size_t)nloc * HR * cldv + rrows * cldv);
   };
   if (chain && chain_smem(max_loc) > SWEEP_SMEM_LIMIT) chain = false;
+  if (inv && !chain) return (int)cudaErrorInvalidConfiguration;   // the host enables INV only where it fits
   if (chain) {
-    cudaFuncSetAttribute(chain_kernel<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)chain_smem(max_loc));
-    cudaFuncSetAttribute(chain_kernel<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)chain_smem(max_loc));
+    if (inv) {
+      cudaFuncSetAttribute(chain_kernel<R, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)chain_smem(max_loc));
+      cudaFuncSetAttribute(chain_kernel<R, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)chain_smem(max_loc));
+    } else {
+      cudaFuncSetAttribute(chain_kernel<R, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)chain_smem(max_loc));
+      cudaFuncSetAttribute(chain_kernel<R, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)chain_smem(max_loc));
+    }
     ChainSweep cs;
     cs.status = a.status;
     cs.tstart = a.tstart;
@@ -1029,15 +1218,18 @@ static int sweep_impl(SweepLaunch& a, cudaStream_t st) {
     cs.npad = a.npad;
     cs.b = b;
     cs.nrhs = a.nrhs;
-    cs.rc = crc;
     cs.stg = cstg;
-    const unsigned ny = (unsigned)((a.nrhs + crc - 1) / crc);
+    cs.Inv = a.Inv;
+    cs.inv_off = a.inv_off;
+    cs.rrows = (int)rrows;
     auto launch_chain = [&](int lv, bool fwd) -> cudaError_t {
       const int S = a.lev_maxnt[lv] * nh;
       cs.cl = std::min(CHAIN_MAXCL, S);
       cs.nloc = (S + cs.cl - 1) / cs.cl;
       cs.blocks = a.lev_blocks + a.lev_ptr[lv];
       const unsigned nb = (unsigned)(a.lev_ptr[lv + 1] - a.lev_ptr[lv]);
+      cs.rc = crc;
+      const unsigned ny = (unsigned)((a.nrhs + crc - 1) / crc);
       cudaLaunchConfig_t cfg = {};
       cfg.gridDim = dim3(nb * (unsigned)cs.cl, ny, 1);
       cfg.blockDim = dim3(GT, 1, 1);
@@ -1051,13 +1243,16 @@ static int sweep_impl(SweepLaunch& a, cudaStream_t st) {
       cfg.attrs = attr;
       cfg.numAttrs = 1;
       ++a.launches;
-      return fwd ? cudaLaunchKernelEx(&cfg, chain_kernel<R, true>, cs, L, Linv, Y)
-                 : cudaLaunchKernelEx(&cfg, chain_kernel<R, false>, cs, L, Linv, Y);
+      if (inv)
+        return fwd ? cudaLaunchKernelEx(&cfg, chain_kernel<R, true, true>, cs, L, Linv, Y)
+                   : cudaLaunchKernelEx(&cfg, chain_kernel<R, false, true>, cs, L, Linv, Y);
+      return fwd ? cudaLaunchKernelEx(&cfg, chain_kernel<R, true, false>, cs, L, Linv, Y)
+                 : cudaLaunchKernelEx(&cfg, chain_kernel<R, false, false>, cs, L, Linv, Y);
     };
     for (int lv = 0; lv < a.nlevels; ++lv) {
-      const int64_t i0 = a.fwd_item_ptr[lv], i1 = a.fwd_item_ptr[lv + 1];
+      const int64_t i0 = a.fwd_group_ptr[lv], i1 = a.fwd_group_ptr[lv + 1];
       if (i1 > i0) {
-        gather_kernel<R, true><<<(unsigned)((i1 - i0) * nh), GT, gsm, st>>>(a.fwd_items + i0, L, Y, P, a.npad, b, a.nrhs, a.status);
+        gather_kernel<R, true><<<dim3((unsigned)((i1 - i0) * nh), gy), GT, gsm, st>>>(a.fwd_groups + i0, a.fwd_items, L, Y, P, a.npad, b, a.nrhs, a.status);
         ++a.launches;
       }
       cs.slot_ptr = a.fwd_slot_ptr;
@@ -1066,9 +1261,9 @@ static int sweep_impl(SweepLaunch& a, cudaStream_t st) {
       if (e != cudaSuccess) return (int)e;
     }
     for (int lv = a.nlevels - 1; lv >= 0; --lv) {
-      const int64_t i0 = a.bwd_item_ptr[lv], i1 = a.bwd_item_ptr[lv + 1];
+      const int64_t i0 = a.bwd_group_ptr[lv], i1 = a.bwd_group_ptr[lv + 1];
       if (i1 > i0) {
-        gather_kernel<R, false><<<(unsigned)((i1 - i0) * nh), GT, gsm, st>>>(a.bwd_items + i0, L, Y, P, a.npad, b, a.nrhs, a.status);
+        gather_kernel<R, false><<<dim3((unsigned)((i1 - i0) * nh), gy), GT, gsm, st>>>(a.bwd_groups + i0, a.bwd_items, L, Y, P, a.npad, b, a.nrhs, a.status);
         ++a.launches;
       }
       cs.slot_ptr = a.bwd_slot_ptr;
@@ -1101,10 +1296,10 @@ static int sweep_impl(SweepLaunch& a, cudaStream_t st) {
   bs.rc = rc;
   const unsigned ny = (unsigned)((a.nrhs + rc - 1) / rc);
   for (int lv = 0; lv < a.nlevels; ++lv) {
-    const int64_t i0 = a.fwd_item_ptr[lv], i1 = a.fwd_item_ptr[lv + 1];
+    const int64_t i0 = a.fwd_group_ptr[lv], i1 = a.fwd_group_ptr[lv + 1];
     const int64_t ntl = a.lev_tile_ptr[lv + 1] - a.lev_tile_ptr[lv];
     if (i1 > i0) {
-      gather_kernel<R, true><<<(unsigned)((i1 - i0) * nh), GT, gsm, st>>>(a.fwd_items + i0, L, Y, P, a.npad, b, a.nrhs, a.status);
+      gather_kernel<R, true><<<dim3((unsigned)((i1 - i0) * nh), gy), GT, gsm, st>>>(a.fwd_groups + i0, a.fwd_items, L, Y, P, a.npad, b, a.nrhs, a.status);
       const int64_t nthr = ntl * b * a.nrhs;
       reduce_kernel<R><<<(unsigned)((nthr + ET - 1) / ET), ET, 0, st>>>(a.lev_tiles + a.lev_tile_ptr[lv], (int)ntl,
                                                                      a.fwd_slot_ptr, P, Y, a.npad, b, a.nrhs, 1);
@@ -1119,10 +1314,10 @@ static int sweep_impl(SweepLaunch& a, cudaStream_t st) {
   diag_scale_kernel<R><<<(unsigned)gblocks, nthreads, 0, st>>>(Y, D, a.npad, a.nrhs);
   ++a.launches;
   for (int lv = a.nlevels - 1; lv >= 0; --lv) {
-    const int64_t i0 = a.bwd_item_ptr[lv], i1 = a.bwd_item_ptr[lv + 1];
+    const int64_t i0 = a.bwd_group_ptr[lv], i1 = a.bwd_group_ptr[lv + 1];
     const int64_t ntl = a.lev_tile_ptr[lv + 1] - a.lev_tile_ptr[lv];
     if (i1 > i0) {
-      gather_kernel<R, false><<<(unsigned)((i1 - i0) * nh), GT, gsm, st>>>(a.bwd_items + i0, L, Y, P, a.npad, b, a.nrhs, a.status);
+      gather_kernel<R, false><<<dim3((unsigned)((i1 - i0) * nh), gy), GT, gsm, st>>>(a.bwd_groups + i0, a.bwd_items, L, Y, P, a.npad, b, a.nrhs, a.status);
       const int64_t nthr = ntl * b * a.nrhs;
       reduce_kernel<R><<<(unsigned)((nthr + ET - 1) / ET), ET, 0, st>>>(a.lev_tiles + a.lev_tile_ptr[lv], (int)ntl,
                                                                      a.bwd_slot_ptr, P, Y, a.npad, b, a.nrhs, nh);

@@ -34,7 +34,7 @@ static int fail(std::string& err, const char* msg, long a = -1, long b = -1) {
 }
 
 int analyze(const d3m_pattern* pat, const int32_t* perm_in, int b, bool build_tasks,
-            Symbolic& s, std::string& err) {
+            Symbolic& s, std::string& err, double prio_slack) {
   if (!pat || !pat->colptr || !pat->rowidx) return fail(err, "pattern or its arrays are NULL");
   const int N = pat->nblk;
   if (N <= 0) return fail(err, "nblk must be positive (got %ld)", N);
@@ -371,9 +371,49 @@ int analyze(const d3m_pattern* pat, const int32_t* perm_in, int b, bool build_ta
     for (int32_t d : tdeps[id]) s.succ[wpos[d]++] = (int32_t)id;
   std::vector<std::vector<int32_t>>().swap(tdeps);
   s.n_edges = (int64_t)s.succ.size();
+  // Priority: a static estimate of each task's duration (diagonal factorization + inverse,
+  // triangular-solve final, update segment of nk tile products) gives the longest path from
+  // the sources to a task's start (tl) and from its start to the end (bl); tasks whose slack
+  // CP - tl - bl is within prio_slack * CP go to the priority lane, which the device
+  // scheduler serves first, so the chain of diagonal factorizations does not queue behind
+  // hundreds of ready updates.
+  {
+    std::vector<double> cost(ntask), tl(ntask, 0.0), bl(ntask, 0.0);
+    for (int64_t id = 0; id < ntask; ++id) {
+      const TileTask& T = s.tasks[id];
+      cost[id] = (T.flags & TF_UPDATE) ? 4.0 + 3.0 * T.nk : ((T.flags & TF_DIAG) ? 110.0 + 3.0 * T.nk : 20.0 + 3.0 * T.nk);
+    }
+    std::vector<int32_t> indeg(s.ndeps.begin(), s.ndeps.end()), order;
+    order.reserve(ntask);
+    for (int64_t id = 0; id < ntask; ++id)
+      if (indeg[id] == 0) order.push_back((int32_t)id);
+    for (size_t q = 0; q < order.size(); ++q) {
+      const int32_t t = order[q];
+      for (int64_t e = s.succ_ptr[t]; e < s.succ_ptr[t + 1]; ++e) {
+        const int32_t v = s.succ[e];
+        tl[v] = std::max(tl[v], tl[t] + cost[t]);
+        if (--indeg[v] == 0) order.push_back(v);
+      }
+    }
+    double cp = 0.0;
+    for (int64_t q = (int64_t)order.size() - 1; q >= 0; --q) {
+      const int32_t t = order[q];
+      double m = 0.0;
+      for (int64_t e = s.succ_ptr[t]; e < s.succ_ptr[t + 1]; ++e) m = std::max(m, bl[s.succ[e]]);
+      bl[t] = cost[t] + m;
+      cp = std::max(cp, tl[t] + bl[t]);
+    }
+    s.n_prio = 0;
+    for (int64_t id = 0; id < ntask; ++id)
+      if (cp - tl[id] - bl[id] <= prio_slack * cp) {
+        s.tasks[id].flags |= TF_PRIO;
+        ++s.n_prio;
+      }
+  }
   s.init_ready.clear();
+  s.init_ready_hi.clear();
   for (int64_t id = 0; id < ntask; ++id)
-    if (s.ndeps[id] == 0) s.init_ready.push_back((int32_t)id);
+    if (s.ndeps[id] == 0) (s.tasks[id].flags & TF_PRIO ? s.init_ready_hi : s.init_ready).push_back((int32_t)id);
 
   // ---------------------------------------------------------------- solve level sets
   s.fwd_item_ptr.assign(s.nlevels + 1, 0);
@@ -383,7 +423,6 @@ int analyze(const d3m_pattern* pat, const int32_t* perm_in, int b, bool build_ta
   s.fwd_items.clear();
   s.bwd_items.clear();
   s.max_level_items = 0;
-  std::vector<int64_t> fcnt(s.NT, 0), bcnt(s.NT, 0);
   for (int lv = 0; lv < s.nlevels; ++lv) {
     int64_t f0 = (int64_t)s.fwd_items.size(), b0 = (int64_t)s.bwd_items.size();
     for (int k : s.lev_blocks[lv]) {
@@ -392,14 +431,12 @@ int analyze(const d3m_pattern* pat, const int32_t* perm_in, int b, bool build_ta
           for (int J = s.tstart[j]; J < s.tstart[j + 1]; ++J) {
             int32_t slot = (int32_t)(s.fwd_items.size() - f0);
             s.fwd_items.push_back(SolveItem{(int32_t)s.tile_of(I, J), J, I, slot});
-            fcnt[I]++;
           }
       for (int J = s.tstart[k]; J < s.tstart[k + 1]; ++J)       // backward: column J gathers
         for (int i : s.str[k])
           for (int I = s.tstart[i]; I < s.tstart[i + 1]; ++I) {
             int32_t slot = (int32_t)(s.bwd_items.size() - b0);
             s.bwd_items.push_back(SolveItem{(int32_t)s.tile_of(I, J), I, J, slot});
-            bcnt[J]++;
           }
     }
     s.fwd_item_ptr[lv + 1] = (int64_t)s.fwd_items.size();
@@ -407,24 +444,50 @@ int analyze(const d3m_pattern* pat, const int32_t* perm_in, int b, bool build_ta
     s.max_level_items = std::max(s.max_level_items, s.fwd_item_ptr[lv + 1] - f0);
     s.max_level_items = std::max(s.max_level_items, s.bwd_item_ptr[lv + 1] - b0);
   }
-  // items of one destination are contiguous (pushed in a row): record the first slot
-  // (relative to the level start) and the count, packed as first | count << 32
-  for (int I = 0; I < s.NT; ++I) { s.fwd_slot_ptr[I] = -1; s.bwd_slot_ptr[I] = -1; }
+  // Items of one destination are contiguous (pushed in a row).  A gather block sums the
+  // products of up to G consecutive items of one destination into one partial slot; G grows
+  // with the level's width so that wide levels write (and the chains read) fewer partials
+  // while narrow levels keep one item per block.  slot_ptr[dst] = first slot of the level
+  // (relative to its start) | number of slots << 32.
+  const int nh = s.b / 64;
+  constexpr int64_t kGatherBlocks = 304;     // about two gather blocks per SM
+  constexpr int64_t kGroupMax = 1;     // one item per gather block: per-item latency dominates
+  s.fwd_group_ptr.assign(s.nlevels + 1, 0);
+  s.bwd_group_ptr.assign(s.nlevels + 1, 0);
+  s.fwd_groups.clear();
+  s.bwd_groups.clear();
+  s.max_level_groups = 0;
+  s.max_group = 1;
+  for (int I = 0; I < s.NT; ++I) { s.fwd_slot_ptr[I] = 0; s.bwd_slot_ptr[I] = 0; }
+  auto make_groups = [&](const std::vector<SolveItem>& items, int64_t i0, int64_t i1,
+                         std::vector<SolveGroup>& groups, std::vector<int64_t>& slot_ptr) {
+    const int64_t g0 = (int64_t)groups.size();
+    const int64_t G = std::max<int64_t>(1, std::min<int64_t>(kGroupMax, (i1 - i0) * nh / kGatherBlocks));
+    int64_t e = i0;
+    while (e < i1) {
+      const int d = items[e].dst;
+      int64_t e1 = e;
+      while (e1 < i1 && items[e1].dst == d) ++e1;
+      const int64_t first_slot = (int64_t)groups.size() - g0;
+      for (int64_t q = e; q < e1; q += G) {
+        const int32_t cnt = (int32_t)std::min<int64_t>(G, e1 - q);
+        groups.push_back(SolveGroup{(int32_t)q, cnt, (int32_t)((int64_t)groups.size() - g0), d});
+        s.max_group = std::max(s.max_group, cnt);
+      }
+      const int64_t nslot = (int64_t)groups.size() - g0 - first_slot;
+      slot_ptr[d] = first_slot | (nslot << 32);
+      e = e1;
+    }
+    return (int64_t)groups.size() - g0;
+  };
   for (int lv = 0; lv < s.nlevels; ++lv) {
-    for (int64_t e = s.fwd_item_ptr[lv]; e < s.fwd_item_ptr[lv + 1]; ++e) {
-      int d = s.fwd_items[e].dst;
-      if (s.fwd_slot_ptr[d] < 0) s.fwd_slot_ptr[d] = s.fwd_items[e].slot;
-    }
-    for (int64_t e = s.bwd_item_ptr[lv]; e < s.bwd_item_ptr[lv + 1]; ++e) {
-      int d = s.bwd_items[e].dst;
-      if (s.bwd_slot_ptr[d] < 0) s.bwd_slot_ptr[d] = s.bwd_items[e].slot;
-    }
-  }
-  for (int I = 0; I < s.NT; ++I) {
-    int64_t f = s.fwd_slot_ptr[I] < 0 ? 0 : s.fwd_slot_ptr[I];
-    int64_t bb = s.bwd_slot_ptr[I] < 0 ? 0 : s.bwd_slot_ptr[I];
-    s.fwd_slot_ptr[I] = f | (fcnt[I] << 32);
-    s.bwd_slot_ptr[I] = bb | (bcnt[I] << 32);
+    const int64_t nf = make_groups(s.fwd_items, s.fwd_item_ptr[lv], s.fwd_item_ptr[lv + 1], s.fwd_groups,
+                                   s.fwd_slot_ptr);
+    const int64_t nb = make_groups(s.bwd_items, s.bwd_item_ptr[lv], s.bwd_item_ptr[lv + 1], s.bwd_groups,
+                                   s.bwd_slot_ptr);
+    s.fwd_group_ptr[lv + 1] = (int64_t)s.fwd_groups.size();
+    s.bwd_group_ptr[lv + 1] = (int64_t)s.bwd_groups.size();
+    s.max_level_groups = std::max(s.max_level_groups, std::max(nf, nb));
   }
   return D3M_OK;
 }

@@ -15,6 +15,7 @@ enum : int32_t {
   TF_SAME_BLOCK = 2,  // p == q: padding unknowns get a unit diagonal
   TF_UPDATE = 4,      // partial-update task (else: the tile's final task)
   TF_S_IN = 8,        // start from the tile's accumulator S (else from K_IJ)
+  TF_PRIO = 16,       // on or near the critical path: served from the priority lane
 };
 
 // One task of the factorization DAG.  The paper's task model (Sec. II: one task per nonzero
@@ -49,6 +50,11 @@ struct KEntry {
 // (backward), written to partial slot `slot` of destination tile row/column `dst`.
 struct SolveItem {
   int32_t tile, src, dst, slot;
+};
+
+// Consecutive items of one destination whose products one gather block sums into one partial.
+struct SolveGroup {
+  int32_t first, count, slot, dst;   // items [first, first + count) (global index), partial slot
 };
 
 struct Symbolic {
@@ -86,7 +92,9 @@ struct Symbolic {
   std::vector<int32_t> ndeps;
   std::vector<int64_t> succ_ptr;
   std::vector<int32_t> succ;
-  std::vector<int32_t> init_ready;
+  std::vector<int32_t> init_ready;           // tasks ready at launch, normal lane
+  std::vector<int32_t> init_ready_hi;        // tasks ready at launch, priority lane
+  int64_t n_prio = 0;                        // tasks flagged TF_PRIO
   std::vector<int32_t> diag_tile;            // tile column J -> tile id of (J, J)
 
   // solve level sets (forward uses levels ascending, backward descending)
@@ -95,6 +103,10 @@ struct Symbolic {
   std::vector<SolveItem> fwd_items, bwd_items;
   std::vector<int64_t> fwd_slot_ptr, bwd_slot_ptr;   // [NT] first slot | count << 32
   int64_t max_level_items = 0;
+  std::vector<int64_t> fwd_group_ptr, bwd_group_ptr;  // per level, into fwd_groups / bwd_groups
+  std::vector<SolveGroup> fwd_groups, bwd_groups;
+  int64_t max_level_groups = 0;
+  int32_t max_group = 1;                     // most items in one group
 
   // residual (caller numbering): per output block f, the stored blocks contributing to r_f
   std::vector<int64_t> res_ptr;              // [N+1]
@@ -105,10 +117,11 @@ struct Symbolic {
   int64_t tile_of(int I, int J) const;       // -1 if (I, J) not in the tile pattern
 };
 
-// Validate the pattern and permutation, then run the full analysis for tile edge b.
+// Validate the pattern and permutation, then run the full analysis for tile edge b.  Tasks whose
+// estimated slack is within prio_slack of the critical path are flagged TF_PRIO.
 // Returns D3M_OK or an error code with a message in `err`.
 int analyze(const d3m_pattern* pat, const int32_t* perm, int b, bool build_tasks,
-            Symbolic& s, std::string& err);
+            Symbolic& s, std::string& err, double prio_slack = 0.08);
 
 // Grid nested dissection (see d3m_order_grid_nd).
 int order_grid_nd(int nx, int ny, int nz, std::vector<int32_t>& perm);

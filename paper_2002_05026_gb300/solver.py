@@ -37,7 +37,8 @@ def _as_colmajor(B):
     return B.T.contiguous(), B.shape[1], False
 
 
-def _options(precision, max_nrhs, refine_tol, refine_max_iter, timeout_ns, fp64_omega, debug_flags, graphs=False):
+def _options(precision, max_nrhs, refine_tol, refine_max_iter, timeout_ns, fp64_omega, debug_flags, graphs=False,
+             prio_slack=None):
     opt = _abi.d3m_default_options()
     opt.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     opt.max_nrhs = max_nrhs
@@ -48,6 +49,8 @@ def _options(precision, max_nrhs, refine_tol, refine_max_iter, timeout_ns, fp64_
     opt.fp64_omega = int(fp64_omega)
     opt.debug_flags = debug_flags
     opt.graphs = int(graphs)
+    if prio_slack is not None:
+        opt.prio_slack = float(prio_slack)
     return opt
 
 
@@ -57,12 +60,13 @@ class D3M:
     def __init__(self, colptr, rowidx, m=None, blk_size=None, perm=None, precision="bf16x3",
                  max_nrhs: int = 32, refine_tol: float = 1e-12, refine_max_iter: int = 20,
                  timeout_ns: int = 0, fp64_omega: bool = False, debug_flags: int = 0, graphs: bool = False,
-                 stream=None):
+                 prio_slack=None, stream=None):
         lib = load()
         self._lib = lib
         self.h = c_void_p()
         pat, self._keep = _abi.make_pattern(colptr, rowidx, m, blk_size)
-        opt = _options(precision, max_nrhs, refine_tol, refine_max_iter, timeout_ns, fp64_omega, debug_flags, graphs)
+        opt = _options(precision, max_nrhs, refine_tol, refine_max_iter, timeout_ns, fp64_omega, debug_flags, graphs,
+                       prio_slack)
         pp = None
         if perm is not None:
             self._perm = np.ascontiguousarray(perm, dtype=np.int32)
