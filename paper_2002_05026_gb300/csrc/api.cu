@@ -79,6 +79,7 @@ struct d3m_ctx {
   int32_t* lev_tiles = nullptr;
   std::vector<int64_t> lev_tile_ptr;
   std::vector<int32_t> lev_maxnt;    // most tiles of one block, per level
+  std::vector<int32_t> lev_maxcnt_fwd, lev_maxcnt_bwd;   // most partials of one tile row / column
   int32_t* tstart = nullptr;
   int64_t* tcolptr = nullptr;
   int64_t* pad2orig = nullptr;
@@ -120,6 +121,8 @@ struct d3m_ctx {
   int ninst = 1;
   std::vector<int32_t> inst_blk;     // [ninst+1] first block (caller numbering) of each instance
   int32_t* inst = nullptr;           // device [N]: instance of every block
+  int32_t* tinst = nullptr;          // device [NT]: instance of every tile row (permuted numbering)
+  int* done = nullptr;               // device [ninst]: 1 once an instance converged in this solve
   int last_nrhs = 0;                 // nrhs of the last solve (for the per-instance omega)
   // CUDA graphs (opt.graphs): launch sequences captured once on a private stream, replayed on
   // the caller's stream; keyed by what the captured pointers and sizes depend on
@@ -474,6 +477,18 @@ static int create_impl(d3m_handle* out, const d3m_pattern* pat, const int32_t* p
       for (int k : l) mx = std::max(mx, S.ntile[k]);
       h->lev_maxnt.push_back(mx);
     }
+    h->lev_maxcnt_fwd.clear();
+    h->lev_maxcnt_bwd.clear();
+    for (const auto& l : S.lev_blocks) {
+      int64_t mf = 0, mb = 0;
+      for (int k : l)
+        for (int I = S.tstart[k]; I < S.tstart[k + 1]; ++I) {
+          mf = std::max<int64_t>(mf, S.fwd_slot_ptr[I] >> 32);
+          mb = std::max<int64_t>(mb, (S.bwd_slot_ptr[I] >> 32) * (b / 64));
+        }
+      h->lev_maxcnt_fwd.push_back((int32_t)mf);
+      h->lev_maxcnt_bwd.push_back((int32_t)mb);
+    }
     std::vector<int64_t> p2o(S.npad, -1);
     for (int k = 0; k < S.N; ++k)
       for (int u = 0; u < S.m[k]; ++u) p2o[S.xoff[k] + u] = S.xoff_orig[S.perm[k]] + u;
@@ -548,6 +563,11 @@ static int create_impl(d3m_handle* out, const d3m_pattern* pat, const int32_t* p
     for (int i = 0; i < h->ninst; ++i)
       for (int f = h->inst_blk[i]; f < h->inst_blk[i + 1]; ++f) ib[f] = i;
     UPLOAD(h->inst, ib);
+    std::vector<int32_t> ti(S.NT, 0);
+    for (int I = 0; I < S.NT; ++I) ti[I] = ib[S.perm[S.tblk[I]]];
+    UPLOAD(h->tinst, ti);
+    ALLOC(h->done, int, h->ninst);
+    CUDA_TRY(h, cudaMemset(h->done, 0, h->ninst * sizeof(int)));
   }
   ALLOC(h->norms, unsigned, 3 * (size_t)h->ninst * mr + h->ninst);
   ALLOC(h->omega_dev, double, (size_t)h->ninst * mr);
@@ -649,6 +669,8 @@ static ResidualParams residual_params(d3m_ctx* h, const double2* X, const double
   p.R = h->d_r;
   const int mr = h->opt.max_nrhs, ni = h->ninst;
   p.inst = h->inst;
+  p.done = h->done;
+  p.tol = h->opt.refine_tol;
   p.ld_norm = mr;
   p.rmax = h->norms;
   p.xmax = h->norms + (size_t)ni * mr;
@@ -773,9 +795,13 @@ static int sweep(d3m_ctx* h, const double2* src, double2* dst, int nrhs, int acc
   a.tstart = h->tstart;
   a.tcolptr = h->tcolptr;
   a.lev_maxnt = h->lev_maxnt.data();
+  a.lev_maxcnt_fwd = h->lev_maxcnt_fwd.data();
+  a.lev_maxcnt_bwd = h->lev_maxcnt_bwd.data();
   a.max_group = S.max_group;
   a.Inv = h->use_inv ? h->Inv : nullptr;
   a.inv_off = h->inv_off;
+  a.done = h->done;
+  a.tinst = h->tinst;
   ev_begin(h, d3m_ctx::EV_SWEEP, st);
   int rc = launch_sweep(a, h->fp64, st);
   if (rc) return set_err(h, D3M_ERR_CUDA, std::string("sweep launch: ") + cudaGetErrorString((cudaError_t)rc));
@@ -793,7 +819,8 @@ static int residual_omega(d3m_ctx* h, const double2* X, const double2* B, int nr
   int rc = launch_residual(rp, h->nchunks, st);
   if (rc) return set_err(h, D3M_ERR_CUDA, std::string("residual launch: ") + cudaGetErrorString((cudaError_t)rc));
   ev_end(h, d3m_ctx::EV_RESID, st);
-  rc = launch_omega(rp.rmax, rp.xmax, rp.bmax, rp.kmax, ni, mr, nrhs, h->omega_dev, h->stat_dev, st);
+  rc = launch_omega(rp.rmax, rp.xmax, rp.bmax, rp.kmax, ni, mr, nrhs, h->done, h->opt.refine_tol, h->omega_dev,
+                    h->stat_dev, st);
   h->last_nrhs = nrhs;
   if (rc) return set_err(h, D3M_ERR_CUDA, std::string("omega launch: ") + cudaGetErrorString((cudaError_t)rc));
   h->launches += 2;
@@ -832,6 +859,7 @@ static int solve_impl(d3m_ctx* h, const void* Bin, void* Xout, int nrhs, cudaStr
   h->omega_first = NAN;
   h->omega_valid = 0;
   h->refine_iters = 0;
+  CUDA_TRY(h, cudaMemsetAsync(h->done, 0, h->ninst * sizeof(int), st));   // every instance refines
   ev_begin(h, d3m_ctx::EV_SOLVE, st);
   int status = D3M_OK;
   // one refinement step: x (+)= solve(src); r = b - K x and omega (FP64); omega -> pinned host

@@ -29,6 +29,8 @@ struct ResidualParams {
   const double2* B;
   double2* R;
   const int32_t* inst;     // [N] instance of every block (caller numbering); all 0 unless batched
+  int* done;               // [instances] 1 once an instance's omega met the tolerance (skipped after)
+  double tol;              // refinement tolerance on omega
   int ld_norm;             // row stride of the per-(instance, column) maxima
   unsigned* rmax;          // [instances][ld_norm] max |r| as float bits
   unsigned* xmax;          // [instances][ld_norm] max |x|
@@ -63,8 +65,12 @@ struct SweepLaunch {
   const int32_t* tstart;           // device [N+1]
   const int64_t* tcolptr;          // device [NT+1]
   const int32_t* lev_maxnt;        // host [nlevels]: most tiles of one block in the level
+  const int32_t* lev_maxcnt_fwd;   // host [nlevels]: most forward partials of one tile row
+  const int32_t* lev_maxcnt_bwd;   // host [nlevels]: most backward partials of one tile column
   int max_group;                   // most items summed by one gather block
   const void* Inv;                 // off-diagonal tiles of the diagonal blocks' inverses, or nullptr
+  const int* done;                 // device [instances]: converged instances are skipped, or nullptr
+  const int32_t* tinst;            // device [NT]: instance of every tile row (permuted numbering)
   const int64_t* inv_off;          // device [N]: first tile of block k in Inv
   int64_t launches;                // out: kernels launched by launch_sweep
 };
@@ -87,7 +93,7 @@ int launch_residual(const ResidualParams& p, int nchunks, cudaStream_t st);
 int launch_knorm(const ResidualParams& p, int nchunks, cudaStream_t st);
 int launch_absmax(const double2* V, int64_t n, int nrhs, unsigned* out, cudaStream_t st);
 int launch_omega(const unsigned* rmax, const unsigned* xmax, const unsigned* bmax, const unsigned* kmax,
-                 int ninst, int ld, int nrhs, double* omega, double* stat, cudaStream_t st);
+                 int ninst, int ld, int nrhs, int* done, double tol, double* omega, double* stat, cudaStream_t st);
 int launch_contract(const double2* Lam, const double2* X, int64_t n, int nrhs, const int64_t* xoff_orig,
                     const int32_t* m_orig, int nblk, double2* out, cudaStream_t st);
 int launch_grad_pattern(const double2* Lam, const double2* X, int64_t n, int nrhs, const int64_t* colptr,

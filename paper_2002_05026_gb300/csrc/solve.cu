@@ -29,13 +29,21 @@ template <typename R>
 __device__ __forceinline__ typename CT<R>::C czero() { return CT<R>::make(0, 0); }
 }  // namespace
 
+// Converged instances of a batched handle (done[instance] = 1) are skipped by every kernel of a
+// refinement step: their x stays as it is and their rows are not swept again.
+struct Mask {
+  const int* done;           // [instances], nullptr = nothing masked
+  const int32_t* tinst;      // [NT] instance of every tile row (permuted numbering)
+  __device__ __forceinline__ bool off(int64_t tile) const { return done && done[tinst[tile]] != 0; }
+};
+
 // ------------------------------------------------------------------ permutation + padding
 template <typename R>
 __global__ void permute_in_kernel(const double2* __restrict__ src, int64_t n,
                                   typename CT<R>::C* __restrict__ Y, int64_t npad,
-                                  const int64_t* __restrict__ pad2orig, int nrhs) {
+                                  const int64_t* __restrict__ pad2orig, int nrhs, Mask mk, int b) {
   const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (g >= npad) return;
+  if (g >= npad || mk.off(g / b)) return;
   const int64_t o = pad2orig[g];
   for (int j = 0; j < nrhs; ++j)
     Y[j * npad + g] = (o >= 0) ? CT<R>::from(src[j * n + o]) : CT<R>::make(0, 0);
@@ -44,9 +52,9 @@ __global__ void permute_in_kernel(const double2* __restrict__ src, int64_t n,
 template <typename R>
 __global__ void permute_out_kernel(const typename CT<R>::C* __restrict__ W, int64_t npad,
                                    double2* __restrict__ X, int64_t n,
-                                   const int64_t* __restrict__ pad2orig, int nrhs, int accumulate) {
+                                   const int64_t* __restrict__ pad2orig, int nrhs, int accumulate, Mask mk, int b) {
   const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (g >= npad) return;
+  if (g >= npad || mk.off(g / b)) return;   // a converged instance keeps its x
   const int64_t o = pad2orig[g];
   if (o < 0) return;
   for (int j = 0; j < nrhs; ++j) {
@@ -222,10 +230,11 @@ __global__ void __launch_bounds__(GT) gather_kernel(const SolveGroup* __restrict
                                                     const typename CT<R>::C* __restrict__ L,
                                                     const typename CT<R>::C* __restrict__ Y,
                                                     typename CT<R>::C* __restrict__ P,
-                                                    int64_t npad, int b, int nrhs, int* status) {
+                                                    int64_t npad, int b, int nrhs, int* status, Mask mk) {
   using C = typename CT<R>::C;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int nh = b / HR;
+  if (mk.off(groups[blockIdx.x / nh].dst)) return;
   const int ldl = stage_ld<C>(b);
   const int vlen = FWD ? b : HR;                         // source rows per right-hand side
   const int ldv = vlen + (int)(16 / sizeof(C));
@@ -336,14 +345,16 @@ struct BlockSweep {
 constexpr int MAXJOBS = 512;      // tile jobs of one block chain (nt (nt+1)/2 * b/64)
 constexpr int MAXNT = 32;         // tiles per interface block
 
-// Y(row) -= sum of the row's partials (fixed slot order) for every tile row of one level;
-// one thread per (tile, row, rhs), rhs fastest (coalesced partial reads).
+// Y(row) -= sum of the row's partials (fixed slot order) for every tile row of one level, after
+// Y(row) /= D(row) when D is given (backward sweep: z = D^{-1} y first); one thread per (tile, row,
+// rhs), rhs fastest (coalesced partial reads), 16 partial loads in flight per thread.
 template <typename R>
 __global__ void __launch_bounds__(ET) reduce_kernel(const int32_t* __restrict__ tiles, int ntl,
                                                     const int64_t* __restrict__ slot_ptr,
                                                     const typename CT<R>::C* __restrict__ P,
                                                     typename CT<R>::C* __restrict__ Y, int64_t npad, int b,
-                                                    int nrhs, int nsub) {
+                                                    int nrhs, int nsub, const typename CT<R>::C* __restrict__ D,
+                                                    Mask mk) {
   using C = typename CT<R>::C;
   const int64_t idx = blockIdx.x * (int64_t)ET + threadIdx.x;
   const int j = (int)(idx % nrhs);
@@ -352,23 +363,28 @@ __global__ void __launch_bounds__(ET) reduce_kernel(const int32_t* __restrict__ 
   const int64_t tl = rest / b;
   if (tl >= ntl) return;
   const int I = tiles[tl];
+  if (mk.off(I)) return;
   const int64_t sp = slot_ptr[I];
   const int64_t first = sp & 0xffffffffLL, cnt = (sp >> 32) * nsub;
-  if (cnt == 0) return;
+  if (cnt == 0 && !D) return;
   const int nh = b / HR;
-  const C* pp = P + first * nh * (int64_t)b * nrhs + (int64_t)row * nrhs + j;
-  const int64_t stride = (int64_t)b * nrhs * (nsub == 1 ? nh : 1);
-  C a0 = czero<R>(), a1 = czero<R>(), a2 = czero<R>(), a3 = czero<R>();
-  int64_t q = 0;
-  for (; q + 4 <= cnt; q += 4) {
-    a0 = cadd(a0, pp[(q + 0) * stride]);
-    a1 = cadd(a1, pp[(q + 1) * stride]);
-    a2 = cadd(a2, pp[(q + 2) * stride]);
-    a3 = cadd(a3, pp[(q + 3) * stride]);
-  }
-  for (; q < cnt; ++q) a0 = cadd(a0, pp[q * stride]);
   C* y = Y + (int64_t)j * npad + (int64_t)I * b + row;
-  *y = csub(*y, cadd(cadd(a0, a1), cadd(a2, a3)));
+  C v = *y;
+  if (D) v = cdiv(v, D[(int64_t)I * b + row]);
+  if (cnt) {
+    const C* pp = P + first * nh * (int64_t)b * nrhs + (int64_t)row * nrhs + j;
+    const int64_t stride = (int64_t)b * nrhs * (nsub == 1 ? nh : 1);
+    C acc = czero<R>();
+    for (int64_t q0 = 0; q0 < cnt; q0 += 16) {
+      C t[16];
+#pragma unroll
+      for (int u = 0; u < 16; ++u) t[u] = (q0 + u < cnt) ? pp[(q0 + u) * stride] : czero<R>();
+#pragma unroll
+      for (int u = 0; u < 16; ++u) acc = cadd(acc, t[u]);
+    }
+    v = csub(v, acc);
+  }
+  *y = v;
 }
 
 // z = D^{-1} y over the whole padded vector (between the forward and backward sweeps)
@@ -655,6 +671,8 @@ struct ChainSweep {
   int b, nrhs, rc;           // rhs per cluster (grid.y = ceil(nrhs / rc))
   int cl, nloc, stg;         // CTAs per cluster, strip slots per CTA, elements of one stage buffer
   int has_partials;
+  int apply_d;               // backward: divide the loaded strips by D (else a reduce launch did)
+  Mask mk;
   const void* Inv;           // off-diagonal tiles of the inverses of the diagonal blocks (INV mode)
   const int64_t* inv_off;    // [N] first tile of block k in Inv
   int rrows;                 // rows of the largest block (INV mode: the whole r is gathered)
@@ -663,6 +681,7 @@ struct ChainSweep {
 constexpr int CHAIN_MAXJ = 128;   // staged strips of one CTA
 constexpr int CHAIN_MAXCL = 8;    // portable cluster size
 constexpr int CHAIN_MAXLOC = 4;   // strips per CTA
+constexpr int EXT_REDUCE = 12;    // partials per row above which a level gets a separate reduce launch
 
 // INV mode: the diagonal block is applied as one product with its stored inverse,
 //   y_J = L_JJ^{-1} r_J (forward),  w_J = L_JJ^{-T} r_J (backward),
@@ -685,6 +704,7 @@ __global__ void __launch_bounds__(GT) chain_kernel(ChainSweep s, const typename 
   const int rc = min(s.rc, s.nrhs - j0);
   const int ldv = vec_ld(s.rc);
   const int t0 = s.tstart[k], nt = s.tstart[k + 1] - t0;
+  if (s.mk.off(t0)) return;                           // every CTA of the cluster, before any barrier
   const int S = nt * nh;
   const int nloc = S > rank ? (S - rank + CL - 1) / CL : 0;
   const int ldst = FWD ? stage_ld<C>(b) : stage_ld<C>(HR);
@@ -763,7 +783,7 @@ __global__ void __launch_bounds__(GT) chain_kernel(ChainSweep s, const typename 
         const int j = i % rc, row = i / rc;
         const int64_t g = (int64_t)I * b + h * HR + row;
         C v = Y[(int64_t)(j0 + j) * s.npad + g];
-        if (!FWD) v = cdiv(v, D[g]);
+        if (!FWD && s.apply_d) v = cdiv(v, D[g]);
         if (cnt) {
           // 16 independent loads in flight per thread, summed in slot order within each batch
           const C* pp = P + first * nh * (int64_t)b * s.nrhs + (int64_t)(h * HR + row) * s.nrhs + (j0 + j);
@@ -967,6 +987,7 @@ __global__ void __launch_bounds__(128) residual_kernel(ResidualParams p) {
   const int j0 = (blockIdx.y * (blockDim.x / 32) + w) * RPT;
   const int2 ch = p.chunks[blockIdx.x];
   const int f = ch.x, u = ch.y + i;
+  if (p.done && p.done[p.inst[f]]) return;             // converged instance: r and its norms are kept
   const int mf = p.m_orig[f];
   const bool active = (u < mf) && (j0 < p.nrhs);
   int nj = p.nrhs - j0;
@@ -1087,18 +1108,30 @@ __global__ void vec_absmax_kernel(const double2* __restrict__ V, int64_t n, int 
 }
 
 // omega_(i,j) = |r|_(i,j) / (||K_i|| |x|_(i,j) + |b|_(i,j)) for instance i, column j (entry
-// i * ld + j);  stat[0] = the largest.  One block of 256 threads.
+// i * ld + j), recomputed for the instances still refining (a converged instance keeps the values
+// of the step that converged it, and done[i] is set once all its columns meet tol);
+// stat[0] = the largest over all instances.  One block of 256 threads.
 __global__ void omega_kernel(const unsigned* rmax, const unsigned* xmax, const unsigned* bmax,
-                             const unsigned* kmax, int ninst, int ld, int nrhs, double* omega, double* stat) {
+                             const unsigned* kmax, int ninst, int ld, int nrhs, int* done, double tol,
+                             double* omega, double* stat) {
   double w = 0.0;
-  for (int e = threadIdx.x; e < ninst * nrhs; e += blockDim.x) {
-    const int i = e / nrhs, j = e % nrhs, q = i * ld + j;
-    const double kn = (double)__uint_as_float(kmax[i]);
-    const double r = __uint_as_float(rmax[q]), x = __uint_as_float(xmax[q]), bb = __uint_as_float(bmax[q]);
-    const double den = kn * x + bb;
-    const double o = den > 0 ? r / den : (r > 0 ? 1.0 : 0.0);
-    omega[q] = o;
-    w = fmax(w, o);
+  for (int i = threadIdx.x; i < ninst; i += blockDim.x) {
+    double wi = 0.0;
+    if (!done[i]) {
+      const double kn = (double)__uint_as_float(kmax[i]);
+      for (int j = 0; j < nrhs; ++j) {
+        const int q = i * ld + j;
+        const double r = __uint_as_float(rmax[q]), x = __uint_as_float(xmax[q]), bb = __uint_as_float(bmax[q]);
+        const double den = kn * x + bb;
+        const double o = den > 0 ? r / den : (r > 0 ? 1.0 : 0.0);
+        omega[q] = o;
+        wi = fmax(wi, o);
+      }
+      if (wi <= tol) done[i] = 1;
+    } else {
+      for (int j = 0; j < nrhs; ++j) wi = fmax(wi, omega[i * ld + j]);
+    }
+    w = fmax(w, wi);
   }
   __shared__ double s_w[256];
   s_w[threadIdx.x] = w;
@@ -1170,7 +1203,8 @@ static int sweep_impl(SweepLaunch& a, cudaStream_t st) {
   C* P = (C*)a.P;
   const int nh = b / HR;
   a.launches = 0;
-  permute_in_kernel<R><<<(unsigned)gblocks, nthreads, 0, st>>>(a.src, a.n, Y, a.npad, a.pad2orig, a.nrhs);
+  const Mask mk{a.done, a.tinst};
+  permute_in_kernel<R><<<(unsigned)gblocks, nthreads, 0, st>>>(a.src, a.n, Y, a.npad, a.pad2orig, a.nrhs, mk, b);
   ++a.launches;
   // gather: one stage buffer of a 64-row tile half and <= 8 source rows (padded by 16 bytes),
   // two when a block sums several items (the next item loads while the current one is used)
@@ -1221,6 +1255,7 @@ static int sweep_impl(SweepLaunch& a, cudaStream_t st) {
     cs.stg = cstg;
     cs.Inv = a.Inv;
     cs.inv_off = a.inv_off;
+    cs.mk = mk;
     cs.rrows = (int)rrows;
     auto launch_chain = [&](int lv, bool fwd) -> cudaError_t {
       const int S = a.lev_maxnt[lv] * nh;
@@ -1252,26 +1287,46 @@ static int sweep_impl(SweepLaunch& a, cudaStream_t st) {
     for (int lv = 0; lv < a.nlevels; ++lv) {
       const int64_t i0 = a.fwd_group_ptr[lv], i1 = a.fwd_group_ptr[lv + 1];
       if (i1 > i0) {
-        gather_kernel<R, true><<<dim3((unsigned)((i1 - i0) * nh), gy), GT, gsm, st>>>(a.fwd_groups + i0, a.fwd_items, L, Y, P, a.npad, b, a.nrhs, a.status);
+        gather_kernel<R, true><<<dim3((unsigned)((i1 - i0) * nh), gy), GT, gsm, st>>>(a.fwd_groups + i0, a.fwd_items, L, Y, P, a.npad, b, a.nrhs, a.status, mk);
         ++a.launches;
       }
       cs.slot_ptr = a.fwd_slot_ptr;
       cs.has_partials = i1 > i0;
+      cs.apply_d = 0;
+      if (i1 > i0 && a.lev_maxcnt_fwd[lv] > EXT_REDUCE) {
+        // many partials per row: a wide reduce launch is cheaper than the cluster's strip loads
+        const int64_t ntl = a.lev_tile_ptr[lv + 1] - a.lev_tile_ptr[lv];
+        const int64_t nthr = ntl * b * a.nrhs;
+        reduce_kernel<R><<<(unsigned)((nthr + ET - 1) / ET), ET, 0, st>>>(a.lev_tiles + a.lev_tile_ptr[lv], (int)ntl,
+                                                                       a.fwd_slot_ptr, P, Y, a.npad, b, a.nrhs, 1, nullptr, mk);
+        ++a.launches;
+        cs.has_partials = 0;
+      }
       cudaError_t e = launch_chain(lv, true);
       if (e != cudaSuccess) return (int)e;
     }
     for (int lv = a.nlevels - 1; lv >= 0; --lv) {
       const int64_t i0 = a.bwd_group_ptr[lv], i1 = a.bwd_group_ptr[lv + 1];
       if (i1 > i0) {
-        gather_kernel<R, false><<<dim3((unsigned)((i1 - i0) * nh), gy), GT, gsm, st>>>(a.bwd_groups + i0, a.bwd_items, L, Y, P, a.npad, b, a.nrhs, a.status);
+        gather_kernel<R, false><<<dim3((unsigned)((i1 - i0) * nh), gy), GT, gsm, st>>>(a.bwd_groups + i0, a.bwd_items, L, Y, P, a.npad, b, a.nrhs, a.status, mk);
         ++a.launches;
       }
       cs.slot_ptr = a.bwd_slot_ptr;
       cs.has_partials = i1 > i0;
+      cs.apply_d = 1;
+      if (i1 > i0 && a.lev_maxcnt_bwd[lv] > EXT_REDUCE) {
+        const int64_t ntl = a.lev_tile_ptr[lv + 1] - a.lev_tile_ptr[lv];
+        const int64_t nthr = ntl * b * a.nrhs;
+        reduce_kernel<R><<<(unsigned)((nthr + ET - 1) / ET), ET, 0, st>>>(a.lev_tiles + a.lev_tile_ptr[lv], (int)ntl,
+                                                                       a.bwd_slot_ptr, P, Y, a.npad, b, a.nrhs, nh, D, mk);
+        ++a.launches;
+        cs.has_partials = 0;
+        cs.apply_d = 0;
+      }
       cudaError_t e = launch_chain(lv, false);
       if (e != cudaSuccess) return (int)e;
     }
-    permute_out_kernel<R><<<(unsigned)gblocks, nthreads, 0, st>>>(Y, a.npad, a.dst, a.n, a.pad2orig, a.nrhs, a.accumulate);
+    permute_out_kernel<R><<<(unsigned)gblocks, nthreads, 0, st>>>(Y, a.npad, a.dst, a.n, a.pad2orig, a.nrhs, a.accumulate, mk, b);
     ++a.launches;
     return (int)cudaGetLastError();
   }
@@ -1299,10 +1354,10 @@ static int sweep_impl(SweepLaunch& a, cudaStream_t st) {
     const int64_t i0 = a.fwd_group_ptr[lv], i1 = a.fwd_group_ptr[lv + 1];
     const int64_t ntl = a.lev_tile_ptr[lv + 1] - a.lev_tile_ptr[lv];
     if (i1 > i0) {
-      gather_kernel<R, true><<<dim3((unsigned)((i1 - i0) * nh), gy), GT, gsm, st>>>(a.fwd_groups + i0, a.fwd_items, L, Y, P, a.npad, b, a.nrhs, a.status);
+      gather_kernel<R, true><<<dim3((unsigned)((i1 - i0) * nh), gy), GT, gsm, st>>>(a.fwd_groups + i0, a.fwd_items, L, Y, P, a.npad, b, a.nrhs, a.status, mk);
       const int64_t nthr = ntl * b * a.nrhs;
       reduce_kernel<R><<<(unsigned)((nthr + ET - 1) / ET), ET, 0, st>>>(a.lev_tiles + a.lev_tile_ptr[lv], (int)ntl,
-                                                                     a.fwd_slot_ptr, P, Y, a.npad, b, a.nrhs, 1);
+                                                                     a.fwd_slot_ptr, P, Y, a.npad, b, a.nrhs, 1, nullptr, mk);
       a.launches += 2;
     }
     bs.blocks = a.lev_blocks + a.lev_ptr[lv];
@@ -1317,10 +1372,10 @@ static int sweep_impl(SweepLaunch& a, cudaStream_t st) {
     const int64_t i0 = a.bwd_group_ptr[lv], i1 = a.bwd_group_ptr[lv + 1];
     const int64_t ntl = a.lev_tile_ptr[lv + 1] - a.lev_tile_ptr[lv];
     if (i1 > i0) {
-      gather_kernel<R, false><<<dim3((unsigned)((i1 - i0) * nh), gy), GT, gsm, st>>>(a.bwd_groups + i0, a.bwd_items, L, Y, P, a.npad, b, a.nrhs, a.status);
+      gather_kernel<R, false><<<dim3((unsigned)((i1 - i0) * nh), gy), GT, gsm, st>>>(a.bwd_groups + i0, a.bwd_items, L, Y, P, a.npad, b, a.nrhs, a.status, mk);
       const int64_t nthr = ntl * b * a.nrhs;
       reduce_kernel<R><<<(unsigned)((nthr + ET - 1) / ET), ET, 0, st>>>(a.lev_tiles + a.lev_tile_ptr[lv], (int)ntl,
-                                                                     a.bwd_slot_ptr, P, Y, a.npad, b, a.nrhs, nh);
+                                                                     a.bwd_slot_ptr, P, Y, a.npad, b, a.nrhs, nh, nullptr, mk);
       a.launches += 2;
     }
     bs.blocks = a.lev_blocks + a.lev_ptr[lv];
@@ -1329,7 +1384,7 @@ static int sweep_impl(SweepLaunch& a, cudaStream_t st) {
     block_bwd_kernel<R><<<dim3(nb, ny), GT, bsm, st>>>(bs, L, Linv, Y);
     ++a.launches;
   }
-  permute_out_kernel<R><<<(unsigned)gblocks, nthreads, 0, st>>>(Y, a.npad, a.dst, a.n, a.pad2orig, a.nrhs, a.accumulate);
+  permute_out_kernel<R><<<(unsigned)gblocks, nthreads, 0, st>>>(Y, a.npad, a.dst, a.n, a.pad2orig, a.nrhs, a.accumulate, mk, b);
   ++a.launches;
   return (int)cudaGetLastError();
 }
@@ -1345,7 +1400,8 @@ int launch_residual(const ResidualParams& p, int nchunks, cudaStream_t st) {
   if (p.nrhs == 1) {
     residual_kernel<1><<<dim3((unsigned)nchunks, 1), 32, 0, st>>>(p);
   } else {
-    const int groups = (p.nrhs + 1) / 2;                       // warps needed at RPT = 2
+    // RPT = 2 measured faster than 4 (more warps in flight; the pair chains already give ILP)
+    const int groups = (p.nrhs + 1) / 2;
     const int wpb = groups < 4 ? groups : 4;
     residual_kernel<2><<<dim3((unsigned)nchunks, (unsigned)((groups + wpb - 1) / wpb)), 32 * wpb, 0, st>>>(p);
   }
@@ -1364,8 +1420,8 @@ int launch_absmax(const double2* V, int64_t n, int nrhs, unsigned* out, cudaStre
 }
 
 int launch_omega(const unsigned* rmax, const unsigned* xmax, const unsigned* bmax, const unsigned* kmax,
-                 int ninst, int ld, int nrhs, double* omega, double* stat, cudaStream_t st) {
-  omega_kernel<<<1, 256, 0, st>>>(rmax, xmax, bmax, kmax, ninst, ld, nrhs, omega, stat);
+                 int ninst, int ld, int nrhs, int* done, double tol, double* omega, double* stat, cudaStream_t st) {
+  omega_kernel<<<1, 256, 0, st>>>(rmax, xmax, bmax, kmax, ninst, ld, nrhs, done, tol, omega, stat);
   return (int)cudaGetLastError();
 }
 
