@@ -94,6 +94,10 @@ typedef struct {
   double prio_slack;        /* tasks whose estimated slack is within prio_slack x the critical
                                path are served first by the device scheduler (default 0.08;
                                0 = only the critical path itself) */
+  double refine_fwd_tol;    /* mixed modes: refinement also requires, per column, that the last
+                               correction d_k be <= refine_fwd_tol |x|, or that the error it
+                               leaves, rho/(1-rho) |d_k| with rho = |d_k|/|d_(k-1)| < 1, be
+                               (default 1e-10; 0 = backward error only) */
 } d3m_options;
 
 /* Test hook: upload the task graph with one extra unmet dependency on the last task, so the

@@ -109,9 +109,11 @@ struct d3m_ctx {
   int nchunks = 0;
   unsigned* norms = nullptr;         // [3 * ninst * max_nrhs + ninst]: rmax, xmax, bmax, kmax
   double* omega_dev = nullptr;       // [ninst][max_nrhs]
-  double* stat_dev = nullptr;        // [1]
+  double* stat_dev = nullptr;        // [2]: max omega, instances still refining
+  unsigned* dmax = nullptr;          // [ninst][max_nrhs] max |correction| of the step (float bits)
+  float* dprev = nullptr;            // [ninst][max_nrhs] the same for the previous step
   int* sweep_status = nullptr;       // device: set by a sweep kernel whose bounded wait expired
-  double* h_stat = nullptr;          // pinned [1]
+  double* h_stat = nullptr;          // pinned [2]
   // gradients
   int32_t* rowidx = nullptr;
   int32_t* blk_col = nullptr;
@@ -313,6 +315,7 @@ void d3m_default_options(d3m_options* o) {
   o->debug_flags = 0;
   o->graphs = 0;
   o->prio_slack = 0.08;
+  o->refine_fwd_tol = 1e-10;
 }
 
 int d3m_order_grid_nd(int32_t nx, int32_t ny, int32_t nz, int32_t* perm) {
@@ -360,6 +363,7 @@ static int create_impl(d3m_handle* out, const d3m_pattern* pat, const int32_t* p
   if (!(h->opt.refine_tol > 0)) h->opt.refine_tol = 1e-12;
   if (h->opt.timeout_ns <= 0) h->opt.timeout_ns = 5000000000LL;
   if (!(h->opt.prio_slack >= 0)) h->opt.prio_slack = 0.08;
+  if (!(h->opt.refine_fwd_tol >= 0)) h->opt.refine_fwd_tol = 1e-10;
   h->fp64 = (prec == D3M_FP64);
   h->tc = (prec == D3M_MIXED_BF16X3);
   h->b = h->tc ? 128 : 64;
@@ -571,11 +575,13 @@ static int create_impl(d3m_handle* out, const d3m_pattern* pat, const int32_t* p
   }
   ALLOC(h->norms, unsigned, 3 * (size_t)h->ninst * mr + h->ninst);
   ALLOC(h->omega_dev, double, (size_t)h->ninst * mr);
-  ALLOC(h->stat_dev, double, 1);
+  ALLOC(h->stat_dev, double, 2);
+  ALLOC(h->dmax, unsigned, (size_t)h->ninst * mr);
+  ALLOC(h->dprev, float, (size_t)h->ninst * mr);
   ALLOC(h->sweep_status, int, 1);
   CUDA_TRY(h, cudaMemset(h->sweep_status, 0, sizeof(int)));
   ALLOC(h->contract, double2, S.N);
-  CUDA_TRY(h, cudaMallocHost(&h->h_stat, sizeof(double)));
+  CUDA_TRY(h, cudaMallocHost(&h->h_stat, 2 * sizeof(double)));
 #undef ALLOC
 #undef UPLOAD
   return D3M_OK;
@@ -802,6 +808,8 @@ static int sweep(d3m_ctx* h, const double2* src, double2* dst, int nrhs, int acc
   a.inv_off = h->inv_off;
   a.done = h->done;
   a.tinst = h->tinst;
+  a.dmax = h->dmax;
+  a.ld_norm = h->opt.max_nrhs;
   ev_begin(h, d3m_ctx::EV_SWEEP, st);
   int rc = launch_sweep(a, h->fp64, st);
   if (rc) return set_err(h, D3M_ERR_CUDA, std::string("sweep launch: ") + cudaGetErrorString((cudaError_t)rc));
@@ -819,8 +827,8 @@ static int residual_omega(d3m_ctx* h, const double2* X, const double2* B, int nr
   int rc = launch_residual(rp, h->nchunks, st);
   if (rc) return set_err(h, D3M_ERR_CUDA, std::string("residual launch: ") + cudaGetErrorString((cudaError_t)rc));
   ev_end(h, d3m_ctx::EV_RESID, st);
-  rc = launch_omega(rp.rmax, rp.xmax, rp.bmax, rp.kmax, ni, mr, nrhs, h->done, h->opt.refine_tol, h->omega_dev,
-                    h->stat_dev, st);
+  rc = launch_omega(rp.rmax, rp.xmax, rp.bmax, rp.kmax, h->dmax, h->dprev, ni, mr, nrhs, h->done, h->opt.refine_tol,
+                    h->opt.refine_fwd_tol, h->omega_dev, h->stat_dev, st);
   h->last_nrhs = nrhs;
   if (rc) return set_err(h, D3M_ERR_CUDA, std::string("omega launch: ") + cudaGetErrorString((cudaError_t)rc));
   h->launches += 2;
@@ -860,16 +868,18 @@ static int solve_impl(d3m_ctx* h, const void* Bin, void* Xout, int nrhs, cudaStr
   h->omega_valid = 0;
   h->refine_iters = 0;
   CUDA_TRY(h, cudaMemsetAsync(h->done, 0, h->ninst * sizeof(int), st));   // every instance refines
+  CUDA_TRY(h, cudaMemsetAsync(h->dprev, 0, (size_t)h->ninst * h->opt.max_nrhs * sizeof(float), st));
   ev_begin(h, d3m_ctx::EV_SOLVE, st);
   int status = D3M_OK;
   // one refinement step: x (+)= solve(src); r = b - K x and omega (FP64); omega -> pinned host
   auto step = [&](const double2* src, int acc, bool resid, cudaStream_t cs) -> int {
+    CUDA_TRY(h, cudaMemsetAsync(h->dmax, 0, (size_t)h->ninst * h->opt.max_nrhs * sizeof(unsigned), cs));
     int rc = sweep(h, src, X, nrhs, acc, cs);
     if (rc) return rc;
     if (!resid) return D3M_OK;
     rc = residual_omega(h, X, B, nrhs, cs);
     if (rc) return rc;
-    CUDA_TRY(h, cudaMemcpyAsync(h->h_stat, h->stat_dev, sizeof(double), cudaMemcpyDeviceToHost, cs));
+    CUDA_TRY(h, cudaMemcpyAsync(h->h_stat, h->stat_dev, 2 * sizeof(double), cudaMemcpyDeviceToHost, cs));
     return D3M_OK;
   };
   auto run_step = [&](const double2* src, int acc, bool resid) -> int {
@@ -895,7 +905,8 @@ static int solve_impl(d3m_ctx* h, const void* Bin, void* Xout, int nrhs, cudaStr
       rc = run_step(src, it > 0 ? 1 : 0, true);             // x (+)= solve(r); r = b - K x, omega
       if (rc) return rc;
       CUDA_TRY(h, cudaStreamSynchronize(st));
-      const double w = *h->h_stat;
+      const double w = h->h_stat[0];
+      const bool all_done = h->h_stat[1] == 0.0;
       h->refine_iters = it + 1;
       if (it == 0) h->omega_first = w;
       hist.push_back(w);
@@ -906,7 +917,7 @@ static int solve_impl(d3m_ctx* h, const void* Bin, void* Xout, int nrhs, cudaStr
       }
       h->omega = w;
       h->omega_valid = 1;
-      if (w <= h->opt.refine_tol) break;
+      if (all_done) break;
       const size_t k = hist.size();
       const bool stagnated = (k >= 3 && !(hist[k - 1] <= 0.5 * hist[k - 3])) || !std::isfinite(w);
       if (stagnated || it + 1 == h->opt.refine_max_iter) {

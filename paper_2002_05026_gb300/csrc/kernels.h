@@ -71,6 +71,8 @@ struct SweepLaunch {
   const void* Inv;                 // off-diagonal tiles of the diagonal blocks' inverses, or nullptr
   const int* done;                 // device [instances]: converged instances are skipped, or nullptr
   const int32_t* tinst;            // device [NT]: instance of every tile row (permuted numbering)
+  unsigned* dmax;                  // device [instances][ld_norm]: max |correction| of the step
+  int ld_norm;
   const int64_t* inv_off;          // device [N]: first tile of block k in Inv
   int64_t launches;                // out: kernels launched by launch_sweep
 };
@@ -93,7 +95,8 @@ int launch_residual(const ResidualParams& p, int nchunks, cudaStream_t st);
 int launch_knorm(const ResidualParams& p, int nchunks, cudaStream_t st);
 int launch_absmax(const double2* V, int64_t n, int nrhs, unsigned* out, cudaStream_t st);
 int launch_omega(const unsigned* rmax, const unsigned* xmax, const unsigned* bmax, const unsigned* kmax,
-                 int ninst, int ld, int nrhs, int* done, double tol, double* omega, double* stat, cudaStream_t st);
+                 const unsigned* dmax, float* dprev, int ninst, int ld, int nrhs, int* done, double tol, double ftol,
+                 double* omega, double* stat, cudaStream_t st);
 int launch_contract(const double2* Lam, const double2* X, int64_t n, int nrhs, const int64_t* xoff_orig,
                     const int32_t* m_orig, int nblk, double2* out, cudaStream_t st);
 int launch_grad_pattern(const double2* Lam, const double2* X, int64_t n, int nrhs, const int64_t* colptr,

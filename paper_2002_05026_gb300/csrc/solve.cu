@@ -49,23 +49,34 @@ __global__ void permute_in_kernel(const double2* __restrict__ src, int64_t n,
     Y[j * npad + g] = (o >= 0) ? CT<R>::from(src[j * n + o]) : CT<R>::make(0, 0);
 }
 
+// X (=, or += when accumulate) W in caller numbering; dmax[instance * ld + j] = max |W| of the
+// step (float bits; the size of the correction drives the forward-error stopping test).
 template <typename R>
 __global__ void permute_out_kernel(const typename CT<R>::C* __restrict__ W, int64_t npad,
                                    double2* __restrict__ X, int64_t n,
-                                   const int64_t* __restrict__ pad2orig, int nrhs, int accumulate, Mask mk, int b) {
+                                   const int64_t* __restrict__ pad2orig, int nrhs, int accumulate, Mask mk, int b,
+                                   unsigned* dmax, int ld) {
   const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (g >= npad || mk.off(g / b)) return;   // a converged instance keeps its x
-  const int64_t o = pad2orig[g];
-  if (o < 0) return;
+  if (g - (threadIdx.x & 31) >= npad) return;              // whole warps past the end
+  // a warp's 32 rows lie in one tile (tiles are >= 64 rows and warps 32-aligned)
+  const bool act = g < npad && !mk.off(g / b) && pad2orig[g] >= 0;   // a converged instance keeps its x
+  const int64_t o = act ? pad2orig[g] : 0;
+  const int inst = (g < npad && mk.tinst) ? mk.tinst[g / b] : 0;
   for (int j = 0; j < nrhs; ++j) {
-    const typename CT<R>::C w = W[j * npad + g];
-    double2 v = make_double2((double)w.x, (double)w.y);
-    if (accumulate) {
-      const double2 x = X[j * n + o];
-      v.x += x.x;
-      v.y += x.y;
+    float a = 0.f;
+    if (act) {
+      const typename CT<R>::C w = W[j * npad + g];
+      double2 v = make_double2((double)w.x, (double)w.y);
+      a = sqrtf((float)(v.x * v.x + v.y * v.y));
+      if (accumulate) {
+        const double2 x = X[j * n + o];
+        v.x += x.x;
+        v.y += x.y;
+      }
+      X[j * n + o] = v;
     }
-    X[j * n + o] = v;
+    for (int s = 16; s > 0; s >>= 1) a = fmaxf(a, __shfl_xor_sync(0xffffffffu, a, s));
+    if (dmax && (threadIdx.x & 31) == 0 && a > 0.f) atomicMax(dmax + inst * ld + j, __float_as_uint(a));
   }
 }
 
@@ -1111,14 +1122,20 @@ __global__ void vec_absmax_kernel(const double2* __restrict__ V, int64_t n, int 
 // i * ld + j), recomputed for the instances still refining (a converged instance keeps the values
 // of the step that converged it, and done[i] is set once all its columns meet tol);
 // stat[0] = the largest over all instances.  One block of 256 threads.
+// An instance is done when every column has omega <= tol and a small forward error: the last
+// correction d_k is at most ftol of |x|, or, with the contraction rho = |d_k| / |d_(k-1)| < 1,
+// the error left in x (about rho / (1 - rho) |d_k|) is (ftol <= 0 skips the forward test).
+// stat[0] = the largest omega, stat[1] = instances not done.
 __global__ void omega_kernel(const unsigned* rmax, const unsigned* xmax, const unsigned* bmax,
-                             const unsigned* kmax, int ninst, int ld, int nrhs, int* done, double tol,
-                             double* omega, double* stat) {
+                             const unsigned* kmax, const unsigned* dmax, float* dprev, int ninst, int ld,
+                             int nrhs, int* done, double tol, double ftol, double* omega, double* stat) {
   double w = 0.0;
+  int open = 0;
   for (int i = threadIdx.x; i < ninst; i += blockDim.x) {
     double wi = 0.0;
     if (!done[i]) {
       const double kn = (double)__uint_as_float(kmax[i]);
+      bool ok = true;
       for (int j = 0; j < nrhs; ++j) {
         const int q = i * ld + j;
         const double r = __uint_as_float(rmax[q]), x = __uint_as_float(xmax[q]), bb = __uint_as_float(bmax[q]);
@@ -1126,21 +1143,36 @@ __global__ void omega_kernel(const unsigned* rmax, const unsigned* xmax, const u
         const double o = den > 0 ? r / den : (r > 0 ? 1.0 : 0.0);
         omega[q] = o;
         wi = fmax(wi, o);
+        const double d = __uint_as_float(dmax[q]), dp = dprev[q];
+        const double ratio = x > 0 ? d / x : (d > 0 ? 1.0 : 0.0);
+        const double rho = dp > 0 ? d / dp : 1.0;
+        const bool fwd = ftol <= 0 || ratio <= ftol || (rho < 1.0 && rho / (1.0 - rho) * ratio <= ftol);
+        ok = ok && o <= tol && fwd;
+        dprev[q] = (float)d;
       }
-      if (wi <= tol) done[i] = 1;
+      if (ok) done[i] = 1;
+      else ++open;
     } else {
       for (int j = 0; j < nrhs; ++j) wi = fmax(wi, omega[i * ld + j]);
     }
     w = fmax(w, wi);
   }
   __shared__ double s_w[256];
+  __shared__ int s_o[256];
   s_w[threadIdx.x] = w;
+  s_o[threadIdx.x] = open;
   __syncthreads();
   for (int h = blockDim.x / 2; h > 0; h >>= 1) {
-    if (threadIdx.x < h) s_w[threadIdx.x] = fmax(s_w[threadIdx.x], s_w[threadIdx.x + h]);
+    if (threadIdx.x < h) {
+      s_w[threadIdx.x] = fmax(s_w[threadIdx.x], s_w[threadIdx.x + h]);
+      s_o[threadIdx.x] += s_o[threadIdx.x + h];
+    }
     __syncthreads();
   }
-  if (threadIdx.x == 0) stat[0] = s_w[0];
+  if (threadIdx.x == 0) {
+    stat[0] = s_w[0];
+    stat[1] = (double)s_o[0];
+  }
 }
 
 // per-interface complex contraction s_f = sum_j sum_u Lambda_uj X_uj (FP64)
@@ -1326,7 +1358,7 @@ static int sweep_impl(SweepLaunch& a, cudaStream_t st) {
       cudaError_t e = launch_chain(lv, false);
       if (e != cudaSuccess) return (int)e;
     }
-    permute_out_kernel<R><<<(unsigned)gblocks, nthreads, 0, st>>>(Y, a.npad, a.dst, a.n, a.pad2orig, a.nrhs, a.accumulate, mk, b);
+    permute_out_kernel<R><<<(unsigned)gblocks, nthreads, 0, st>>>(Y, a.npad, a.dst, a.n, a.pad2orig, a.nrhs, a.accumulate, mk, b, a.dmax, a.ld_norm);
     ++a.launches;
     return (int)cudaGetLastError();
   }
@@ -1384,7 +1416,7 @@ static int sweep_impl(SweepLaunch& a, cudaStream_t st) {
     block_bwd_kernel<R><<<dim3(nb, ny), GT, bsm, st>>>(bs, L, Linv, Y);
     ++a.launches;
   }
-  permute_out_kernel<R><<<(unsigned)gblocks, nthreads, 0, st>>>(Y, a.npad, a.dst, a.n, a.pad2orig, a.nrhs, a.accumulate, mk, b);
+  permute_out_kernel<R><<<(unsigned)gblocks, nthreads, 0, st>>>(Y, a.npad, a.dst, a.n, a.pad2orig, a.nrhs, a.accumulate, mk, b, a.dmax, a.ld_norm);
   ++a.launches;
   return (int)cudaGetLastError();
 }
@@ -1420,8 +1452,9 @@ int launch_absmax(const double2* V, int64_t n, int nrhs, unsigned* out, cudaStre
 }
 
 int launch_omega(const unsigned* rmax, const unsigned* xmax, const unsigned* bmax, const unsigned* kmax,
-                 int ninst, int ld, int nrhs, int* done, double tol, double* omega, double* stat, cudaStream_t st) {
-  omega_kernel<<<1, 256, 0, st>>>(rmax, xmax, bmax, kmax, ninst, ld, nrhs, done, tol, omega, stat);
+                 const unsigned* dmax, float* dprev, int ninst, int ld, int nrhs, int* done, double tol, double ftol,
+                 double* omega, double* stat, cudaStream_t st) {
+  omega_kernel<<<1, 256, 0, st>>>(rmax, xmax, bmax, kmax, dmax, dprev, ninst, ld, nrhs, done, tol, ftol, omega, stat);
   return (int)cudaGetLastError();
 }
 
