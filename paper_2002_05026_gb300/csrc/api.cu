@@ -91,6 +91,8 @@ struct d3m_ctx {
   bool use_inv = false;
   void* Inv = nullptr;
   int64_t* inv_off = nullptr;
+  void* InvT = nullptr;
+  int64_t* invT_off = nullptr;
   int2* inv_work = nullptr;
   int n_inv_work = 0;
   // refinement / residual
@@ -515,20 +517,24 @@ static int create_impl(d3m_handle* out, const d3m_pattern* pat, const int32_t* p
   // mixed precision with blocks of at most 512 rows: build the diagonal blocks' inverses
   h->use_inv = !h->fp64 && h->max_rows <= 512;
   if (h->use_inv) {
-    std::vector<int64_t> off(S.N, 0);
+    std::vector<int64_t> off(S.N, 0), offT(S.N, 0);
     std::vector<int2> work;
-    int64_t ninv = 0;
+    int64_t ninv = 0, ninvT = 0;
     for (int k = 0; k < S.N; ++k) {
       const int nt = S.ntile[k];
       off[k] = ninv;
+      offT[k] = ninvT;
       ninv += (int64_t)nt * (nt - 1) / 2;
-      for (int tq = 0; tq + 1 < nt; ++tq) work.push_back(make_int2(k, tq));
+      ninvT += (int64_t)nt * (nt + 1) / 2;
+      for (int tq = 0; tq < nt; ++tq) work.push_back(make_int2(k, tq));
     }
     UPLOAD(h->inv_off, off);
+    UPLOAD(h->invT_off, offT);
     UPLOAD(h->inv_work, work);
     h->n_inv_work = (int)work.size();
     h->Inv = dalloc<unsigned char>(h, (size_t)std::max<int64_t>(1, ninv) * b * b * h->csize);
-    if (!h->Inv) return set_err(h, D3M_ERR_OOM, "cudaMalloc failed for the block inverses");
+    h->InvT = dalloc<unsigned char>(h, (size_t)std::max<int64_t>(1, ninvT) * b * b * h->csize);
+    if (!h->Inv || !h->InvT) return set_err(h, D3M_ERR_OOM, "cudaMalloc failed for the block inverses");
   }
   h->Y = dalloc<unsigned char>(h, (size_t)S.npad * mr * h->csize);
   h->P = dalloc<unsigned char>(h, (size_t)std::max<int64_t>(1, S.max_level_groups) * (b / 64) * b * mr * h->csize);
@@ -738,7 +744,8 @@ static int enqueue_factor(d3m_ctx* h, const void* Kin, bool kdev, cudaStream_t s
   ev_end(h, d3m_ctx::EV_FACTOR, st);
   h->launches += 1;
   if (h->use_inv && h->n_inv_work > 0) {
-    rc = launch_inv_build(h->inv_work, h->n_inv_work, h->tstart, h->tcolptr, h->inv_off, h->L, h->Linv, h->Inv, h->b, st);
+    rc = launch_inv_build(h->inv_work, h->n_inv_work, h->tstart, h->tcolptr, h->inv_off, h->invT_off, h->L, h->Linv,
+                          h->Inv, h->InvT, h->b, st);
     if (rc) return set_err(h, D3M_ERR_CUDA, std::string("block inverse launch: ") + cudaGetErrorString((cudaError_t)rc));
     h->launches += 1;
   }
@@ -806,6 +813,8 @@ static int sweep(d3m_ctx* h, const double2* src, double2* dst, int nrhs, int acc
   a.max_group = S.max_group;
   a.Inv = h->use_inv ? h->Inv : nullptr;
   a.inv_off = h->inv_off;
+  a.InvT = h->InvT;
+  a.invT_off = h->invT_off;
   a.done = h->done;
   a.tinst = h->tinst;
   a.dmax = h->dmax;

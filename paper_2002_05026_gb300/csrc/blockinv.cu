@@ -4,6 +4,8 @@
 //   Inv(t', t') = Linv_t't',   Inv(t, t') = -Linv_tt * sum_{s=t'}^{t-1} L(t, s) Inv(s, t')   (t > t').
 // One thread block per (block J, tile column t') forms Inv(t, t') for t = t'+1, ..., nt-1 in order
 // (each needs the ones above it in the same column).  Tiles are b x b, row-major, b in {64, 128}.
+// Every tile is also stored transposed, InvT(t', t) = Inv(t, t')^T (t >= t', diagonal included),
+// so that the backward solve streams contiguous row strips as well.
 // Products: shared-memory staged FP32 SIMT GEMM, each of the 256 threads owning a TM x TM
 // sub-tile (TM = b / 16).
 #include <cuda_runtime.h>
@@ -82,8 +84,9 @@ template <int B>
 __global__ void __launch_bounds__(IT) inv_build_kernel(const int2* __restrict__ work, const int32_t* __restrict__ tstart,
                                                        const int64_t* __restrict__ tcolptr,
                                                        const int64_t* __restrict__ inv_off,
+                                                       const int64_t* __restrict__ invT_off,
                                                        const float2* __restrict__ L, const float2* __restrict__ Linv,
-                                                       float2* __restrict__ Inv) {
+                                                       float2* __restrict__ Inv, float2* __restrict__ InvT) {
   constexpr int TM = B / 16, LDA = B + 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2* sA = reinterpret_cast<float2*>(smem_raw);   // [KC][B + 1]
@@ -92,9 +95,18 @@ __global__ void __launch_bounds__(IT) inv_build_kernel(const int2* __restrict__ 
   const int2 wk = work[blockIdx.x];
   const int k = wk.x, tq = wk.y;
   const int t0 = tstart[k], nt = tstart[k + 1] - t0;
-  const int64_t ib = inv_off[k];
+  const int64_t ib = inv_off[k], ibt = invT_off[k];
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   const int64_t tsz = (int64_t)B * B;
+  {
+    // InvT(tq, tq) = Linv_tq^T
+    const float2* src = Linv + (int64_t)(t0 + tq) * tsz;
+    float2* dst = InvT + (ibt + tq * (tq + 1) / 2 + tq) * tsz;
+    for (int i = threadIdx.x; i < B * B; i += IT) {
+      const int r = i / B, c = i % B;
+      dst[(int64_t)c * B + r] = src[i];
+    }
+  }
   for (int t = tq + 1; t < nt; ++t) {
     float2 acc[TM][TM];
 #pragma unroll
@@ -119,10 +131,15 @@ __global__ void __launch_bounds__(IT) inv_build_kernel(const int2* __restrict__ 
       for (int j = 0; j < TM; ++j) acc[i][j] = make_float2(0.f, 0.f);
     gemm_gs<B>(Linv + (int64_t)(t0 + t) * tsz, sC, sA, acc);
     float2* out = Inv + (ib + t * (t - 1) / 2 + tq) * tsz;
+    float2* outT = InvT + (ibt + t * (t + 1) / 2 + tq) * tsz;
 #pragma unroll
     for (int i = 0; i < TM; ++i)
 #pragma unroll
-      for (int j = 0; j < TM; ++j) out[(int64_t)(ty * TM + i) * B + tx * TM + j] = make_float2(-acc[i][j].x, -acc[i][j].y);
+      for (int j = 0; j < TM; ++j) {
+        const float2 v = make_float2(-acc[i][j].x, -acc[i][j].y);
+        out[(int64_t)(ty * TM + i) * B + tx * TM + j] = v;
+        outT[(int64_t)(tx * TM + j) * B + ty * TM + i] = v;
+      }
     __syncthreads();   // Inv(t, tq) is read back by this block for the next t
   }
 }
@@ -130,17 +147,18 @@ __global__ void __launch_bounds__(IT) inv_build_kernel(const int2* __restrict__ 
 }  // namespace
 
 int launch_inv_build(const int2* work, int nwork, const int32_t* tstart, const int64_t* tcolptr,
-                     const int64_t* inv_off, const void* L, const void* Linv, void* Inv, int b, cudaStream_t st) {
+                     const int64_t* inv_off, const int64_t* invT_off, const void* L, const void* Linv, void* Inv,
+                     void* InvT, int b, cudaStream_t st) {
   if (nwork <= 0) return 0;
   const size_t smem = sizeof(float2) * ((size_t)KC * (b + 1) + (size_t)KC * b + (size_t)b * (b + 1));
   if (b == 128) {
     cudaFuncSetAttribute(inv_build_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    inv_build_kernel<128><<<nwork, IT, smem, st>>>(work, tstart, tcolptr, inv_off, (const float2*)L,
-                                                   (const float2*)Linv, (float2*)Inv);
+    inv_build_kernel<128><<<nwork, IT, smem, st>>>(work, tstart, tcolptr, inv_off, invT_off, (const float2*)L,
+                                                   (const float2*)Linv, (float2*)Inv, (float2*)InvT);
   } else if (b == 64) {
     cudaFuncSetAttribute(inv_build_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    inv_build_kernel<64><<<nwork, IT, smem, st>>>(work, tstart, tcolptr, inv_off, (const float2*)L,
-                                                  (const float2*)Linv, (float2*)Inv);
+    inv_build_kernel<64><<<nwork, IT, smem, st>>>(work, tstart, tcolptr, inv_off, invT_off, (const float2*)L,
+                                                  (const float2*)Linv, (float2*)Inv, (float2*)InvT);
   } else {
     return (int)cudaErrorInvalidValue;
   }

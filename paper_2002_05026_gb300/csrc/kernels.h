@@ -74,6 +74,8 @@ struct SweepLaunch {
   unsigned* dmax;                  // device [instances][ld_norm]: max |correction| of the step
   int ld_norm;
   const int64_t* inv_off;          // device [N]: first tile of block k in Inv
+  const void* InvT;                // transposed inverse tiles (diagonal included)
+  const int64_t* invT_off;         // device [N]: first tile of block k in InvT
   int64_t launches;                // out: kernels launched by launch_sweep
 };
 
@@ -90,7 +92,8 @@ int launch_sweep(SweepLaunch& a, bool fp64, cudaStream_t st);
 // Inverses of the unit-lower diagonal blocks (c64 tiles of edge b in {64, 128}), built from L and
 // the inverses of the diagonal tiles: work = (block, tile column) pairs.
 int launch_inv_build(const int2* work, int nwork, const int32_t* tstart, const int64_t* tcolptr,
-                     const int64_t* inv_off, const void* L, const void* Linv, void* Inv, int b, cudaStream_t st);
+                     const int64_t* inv_off, const int64_t* invT_off, const void* L, const void* Linv, void* Inv,
+                     void* InvT, int b, cudaStream_t st);
 int launch_residual(const ResidualParams& p, int nchunks, cudaStream_t st);
 int launch_knorm(const ResidualParams& p, int nchunks, cudaStream_t st);
 int launch_absmax(const double2* V, int64_t n, int nrhs, unsigned* out, cudaStream_t st);

@@ -173,6 +173,39 @@ __device__ __forceinline__ void rows_matvec(const typename CT<R>::C* M, int ldl,
   }
 }
 
+// rows_matvec on a dense [64][b] strip (one bulk copy): the 4 column classes of each of a warp's 8
+// rows start at columns rotated by 4 per row, so every warp-wide load touches 32 consecutive
+// columns (no bank conflicts); b is a power of two.
+template <typename R, int MODE>
+__device__ __forceinline__ void rows_matvec_dense(const typename CT<R>::C* M, int b, const typename CT<R>::C* V,
+                                                  int ldv, int rc, typename CT<R>::C* dst, int ldd) {
+  using C = typename CT<R>::C;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int r = warp * 8 + (lane >> 2), cq = lane & 3, rot = 4 * (lane >> 2);
+  C acc[RCMAX];
+#pragma unroll
+  for (int j = 0; j < RCMAX; ++j) acc[j] = CT<R>::make(0, 0);
+  const C* mrow = M + r * b;
+#pragma unroll 4
+  for (int i = 0; i < b / 4; ++i) {
+    const int c = (4 * i + cq + rot) & (b - 1);
+    const C m = mrow[c];
+    const C* v = V + c * ldv;
+    C vv[RCMAX];
+#pragma unroll
+    for (int j = 0; j < RCMAX; ++j) vv[j] = (j < rc) ? v[j] : CT<R>::make(0, 0);
+#pragma unroll
+    for (int j = 0; j < RCMAX; ++j) acc[j] = cfma(m, vv[j], acc[j]);
+  }
+  quad_reduce(acc);
+  if (cq == 0) {
+#pragma unroll
+    for (int j = 0; j < RCMAX; ++j)
+      if (j < rc)
+        dst[r * ldd + j] = MODE == 0 ? acc[j] : (MODE == 1 ? cadd(dst[r * ldd + j], acc[j]) : csub(dst[r * ldd + j], acc[j]));
+  }
+}
+
 // dst[c][j] (=, +=, or -= by MODE 0 / 1 / 2) sum_{r < 64} M[r][c] V[r][j] for all b columns
 // of a staged half tile.
 template <typename R, int MODE>
@@ -212,27 +245,33 @@ __device__ __forceinline__ void cols_matvec(const typename CT<R>::C* M, int ldl,
 // 64-row half h of the tiles and up to 8 right-hand sides:
 //   FWD: P[slot][h*64 + r][j] = sum_items sum_k L[h*64 + r][k] Y[src*b + k][j];
 //   BWD: P[slot*nh + h][c][j] = sum_items sum_{r < 64} L[h*64 + r][c] W[src*b + h*64 + r][j].
-// Each item's tile half and source rows are brought in by bulk copies on one mbarrier, double
-// buffered, so the next item loads while the current one is multiplied.
+// An item's tile half is contiguous (64 rows of a row-major tile) and comes in as ONE bulk copy
+// into a dense [64][b] buffer; its source rows as one bulk copy per right-hand side.  Reads of the
+// dense half stay conflict-free: forward, the 8 rows x 4 column classes of a warp start at
+// columns rotated by 4 per row, so a warp touches 32 consecutive columns; backward, a thread owns
+// one output column and the warp reads 32 consecutive columns of one row.  Items of a group are
+// double buffered (the next loads while the current one is multiplied).
 template <typename C>
-__device__ __forceinline__ void stage_item(C* sT, C* sV, int ldl, int ldv, const C* tile, const C* Y, int64_t npad,
-                                           int64_t y0, int vlen, int j0, int rc, int b, int h, uint64_t* bar) {
+__device__ __forceinline__ void stage_item(C* sT, C* sV, int ldv, const C* half, const C* Y, int64_t npad,
+                                           int64_t y0, int vlen, int j0, int rc, int b, uint64_t* bar) {
   if (threadIdx.x >= 32) return;
-  const uint32_t row_bytes = (uint32_t)(b * sizeof(C)), v_bytes = (uint32_t)(vlen * sizeof(C));
-  if (threadIdx.x == 0)
+  const uint32_t t_bytes = (uint32_t)(HR * b * sizeof(C)), v_bytes = (uint32_t)(vlen * sizeof(C));
+  if (threadIdx.x == 0) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
-                 "r"(HR * row_bytes + rc * v_bytes)
+                 "r"(t_bytes + rc * v_bytes)
                  : "memory");
-  __syncwarp();
-  for (int r = threadIdx.x; r < HR + rc; r += 32) {
-    const C* src = r < HR ? tile + (int64_t)(h * HR + r) * b : Y + (int64_t)(j0 + r - HR) * npad + y0;
-    C* dst = r < HR ? sT + r * ldl : sV + (r - HR) * ldv;
     asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            smem_addr(dst)),
-        "l"(src), "r"(r < HR ? row_bytes : v_bytes), "r"(smem_addr(bar))
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_addr(sT)),
+        "l"(half), "r"(t_bytes), "r"(smem_addr(bar))
         : "memory");
   }
+  __syncwarp();
+  for (int j = threadIdx.x; j < rc; j += 32)
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(sV + j * ldv)),
+        "l"(Y + (int64_t)(j0 + j) * npad + y0), "r"(v_bytes), "r"(smem_addr(bar))
+        : "memory");
 }
 
 template <typename R, bool FWD>
@@ -246,10 +285,9 @@ __global__ void __launch_bounds__(GT) gather_kernel(const SolveGroup* __restrict
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int nh = b / HR;
   if (mk.off(groups[blockIdx.x / nh].dst)) return;
-  const int ldl = stage_ld<C>(b);
   const int vlen = FWD ? b : HR;                         // source rows per right-hand side
   const int ldv = vlen + (int)(16 / sizeof(C));
-  const int stg = HR * ldl + RCMAX * ldv;                // elements of one stage buffer
+  const int stg = HR * b + RCMAX * ldv;                  // elements of one stage buffer
   C* buf[2] = {reinterpret_cast<C*>(smem_raw), reinterpret_cast<C*>(smem_raw) + stg};
   __shared__ __align__(8) uint64_t bars[2];
   const SolveGroup gr = groups[blockIdx.x / nh];
@@ -267,15 +305,16 @@ __global__ void __launch_bounds__(GT) gather_kernel(const SolveGroup* __restrict
     const SolveItem it = items[gr.first + k];
     const int64_t y0 = (int64_t)it.src * b + (FWD ? 0 : h * HR);
     C* T = buf[k & 1];
-    stage_item(T, T + HR * ldl, ldl, ldv, L + (int64_t)it.tile * b * b, Y, npad, y0, vlen, j0, rc, b, h, &bars[k & 1]);
+    stage_item(T, T + HR * b, ldv, L + (int64_t)it.tile * b * b + (int64_t)h * HR * b, Y, npad, y0, vlen, j0, rc, b,
+               &bars[k & 1]);
   };
   stage(0);
-  constexpr int NCH = FWD ? 1 : 2;                       // column chunks of 64 (backward, b = 128)
-  C acc[NCH][RCMAX];
+  // backward: thread = (output column c, row group); b / 64 ... 256 / b row groups of 64 * b / 256 rows
+  const int ngrp = GT / b, rows_g = HR / ngrp;
+  const int bc = threadIdx.x % b, bg = threadIdx.x / b;
+  C acc[RCMAX];
 #pragma unroll
-  for (int q = 0; q < NCH; ++q)
-#pragma unroll
-    for (int j = 0; j < RCMAX; ++j) acc[q][j] = CT<R>::make(0, 0);
+  for (int j = 0; j < RCMAX; ++j) acc[j] = CT<R>::make(0, 0);
   uint32_t phase[2] = {0u, 0u};
   const uint64_t deadline = globaltimer_ns() + SWEEP_TIMEOUT_NS;
   for (int k = 0; k < gr.count; ++k) {
@@ -291,52 +330,51 @@ __global__ void __launch_bounds__(GT) gather_kernel(const SolveGroup* __restrict
       return;
     }
     const C* M = buf[k & 1];
-    const C* V = M + HR * ldl;
+    const C* V = M + HR * b;
     if (FWD) {
-      // row r of the half, reduction index split over 4 lanes
-      const int r = warp * 8 + (lane >> 2), cq = lane & 3;
+      const int r = warp * 8 + (lane >> 2), cq = lane & 3, rot = 4 * (lane >> 2);
 #pragma unroll 4
-      for (int c = cq; c < b; c += 4) {
-        const C m = M[r * ldl + c];
+      for (int i = 0; i < b / 4; ++i) {
+        const int c = (4 * i + cq + rot) & (b - 1);
+        const C m = M[r * b + c];
 #pragma unroll
         for (int j = 0; j < RCMAX; ++j)
-          if (j < rc) acc[0][j] = cfma(m, V[j * ldv + c], acc[0][j]);
+          if (j < rc) acc[j] = cfma(m, V[j * ldv + c], acc[j]);
       }
     } else {
-      const int rq = lane & 3;
-#pragma unroll
-      for (int q = 0; q < NCH; ++q) {
-        const int c = q * 64 + warp * 8 + (lane >> 2);
-        if (c >= b) break;
 #pragma unroll 4
-        for (int r = rq; r < HR; r += 4) {
-          const C m = M[r * ldl + c];
+      for (int rr = 0; rr < rows_g; ++rr) {
+        const int r = bg * rows_g + rr;
+        const C m = M[r * b + bc];
 #pragma unroll
-          for (int j = 0; j < RCMAX; ++j)
-            if (j < rc) acc[q][j] = cfma(m, V[j * ldv + r], acc[q][j]);
-        }
+        for (int j = 0; j < RCMAX; ++j)
+          if (j < rc) acc[j] = cfma(m, V[j * ldv + r], acc[j]);
       }
     }
     __syncthreads();
   }
-#pragma unroll
-  for (int q = 0; q < NCH; ++q) quad_reduce(acc[q]);
-  if ((lane & 3) == 0) {
-    if (FWD) {
+  if (FWD) {
+    quad_reduce(acc);
+    if ((lane & 3) == 0) {
       const int r = warp * 8 + (lane >> 2);
       C* out = P + (int64_t)gr.slot * nh * b * nrhs + (int64_t)(h * HR + r) * nrhs + j0;
 #pragma unroll
       for (int j = 0; j < RCMAX; ++j)
-        if (j < rc) out[j] = acc[0][j];
-    } else {
+        if (j < rc) out[j] = acc[j];
+    }
+  } else {
+    // sum the row groups of every column in a fixed order (reusing stage buffer 0)
+    C* red = buf[0];                                    // [ngrp][b][RCMAX]
 #pragma unroll
-      for (int q = 0; q < NCH; ++q) {
-        const int c = q * 64 + warp * 8 + (lane >> 2);
-        if (c >= b) break;
-        C* out = P + ((int64_t)gr.slot * nh + h) * b * nrhs + (int64_t)c * nrhs + j0;
+    for (int j = 0; j < RCMAX; ++j) red[(bg * b + bc) * RCMAX + j] = acc[j];
+    __syncthreads();
+    if (bg == 0) {
+      C* out = P + ((int64_t)gr.slot * nh + h) * b * nrhs + (int64_t)bc * nrhs + j0;
 #pragma unroll
-        for (int j = 0; j < RCMAX; ++j)
-          if (j < rc) out[j] = acc[q][j];
+      for (int j = 0; j < RCMAX; ++j) {
+        C v = red[bc * RCMAX + j];
+        for (int g = 1; g < ngrp; ++g) v = cadd(v, red[(g * b + bc) * RCMAX + j]);
+        if (j < rc) out[j] = v;
       }
     }
   }
@@ -686,6 +724,8 @@ struct ChainSweep {
   Mask mk;
   const void* Inv;           // off-diagonal tiles of the inverses of the diagonal blocks (INV mode)
   const int64_t* inv_off;    // [N] first tile of block k in Inv
+  const void* InvT;          // transposed tiles Inv(c, a)^T, c >= a (diagonal included), INV mode
+  const int64_t* invT_off;   // [N] first tile of block k in InvT
   int rrows;                 // rows of the largest block (INV mode: the whole r is gathered)
 };
 
@@ -733,13 +773,15 @@ __global__ void __launch_bounds__(GT) chain_kernel(ChainSweep s, const typename 
   if (threadIdx.x == 0 && INV) {
     int nj = 0;
     const int64_t ib = s.inv_off[k];
+    const C* InvT = reinterpret_cast<const C*>(s.InvT);
+    const int64_t ibt = s.invT_off[k];
     for (int l = 0; l < nloc; ++l) {
       const int sid = rank + l * CL, tq = sid / nh, h = sid % nh;
-      const int64_t hoff = FWD ? (int64_t)h * HR * b : (int64_t)h * HR;
+      const int64_t hoff = (int64_t)h * HR * b;       // row strip h (contiguous)
       for (int t = FWD ? 0 : tq; t < (FWD ? tq + 1 : nt); ++t) {
-        // forward: tile (tq, t) of the inverse; backward: tile (t, tq)
-        const int tr = FWD ? tq : t, tc = FWD ? t : tq;
-        s_job[nj++] = (tr == tc ? Linv + (int64_t)(t0 + tr) * b * b : Inv + (ib + tr * (tr - 1) / 2 + tc) * (int64_t)b * b) + hoff;
+        // forward: tile (tq, t) of the inverse; backward: tile (tq, t) of the transposed inverse
+        if (FWD) s_job[nj++] = (tq == t ? Linv + (int64_t)(t0 + tq) * b * b : Inv + (ib + tq * (tq - 1) / 2 + t) * (int64_t)b * b) + hoff;
+        else s_job[nj++] = InvT + (ibt + t * (t + 1) / 2 + tq) * (int64_t)b * b + hoff;
       }
     }
     s_nj = nj;
@@ -772,7 +814,8 @@ __global__ void __launch_bounds__(GT) chain_kernel(ChainSweep s, const typename 
   const int nj = s_nj;
   auto stage = [&](int jb) {
     C* dst = (jb & 1) ? stg1 : stg0;
-    if (FWD) stage_rows(dst, ldst, s_job[jb], b, HR, b, &bars[jb & 1]);
+    if (INV) stage_rows(dst, HR * b, s_job[jb], HR * b, 1, HR * b, &bars[jb & 1]);   // one dense strip
+    else if (FWD) stage_rows(dst, ldst, s_job[jb], b, HR, b, &bars[jb & 1]);
     else stage_rows(dst, ldst, s_job[jb], b, b, HR, &bars[jb & 1]);
   };
   if (nj > 0) stage(0);
@@ -858,13 +901,8 @@ __global__ void __launch_bounds__(GT) chain_kernel(ChainSweep s, const typename 
         const C* M = next_stage();
         const C* V = sR + (int64_t)(FWD ? q : tq + q) * b * ldv;
         if (!bad) {
-          if (FWD) {
-            if (q == 0) rows_matvec<R, 0>(M, ldst, b, V, ldv, rc, o, ldv);
-            else rows_matvec<R, 1>(M, ldst, b, V, ldv, rc, o, ldv);
-          } else {
-            if (q == 0) colstrip_matvec<R, 0>(M, ldst, b, V, ldv, rc, o, ldv);
-            else colstrip_matvec<R, 1>(M, ldst, b, V, ldv, rc, o, ldv);
-          }
+          if (q == 0) rows_matvec_dense<R, 0>(M, b, V, ldv, rc, o, ldv);
+          else rows_matvec_dense<R, 1>(M, b, V, ldv, rc, o, ldv);
         }
         __syncthreads();
       }
@@ -1238,10 +1276,10 @@ static int sweep_impl(SweepLaunch& a, cudaStream_t st) {
   const Mask mk{a.done, a.tinst};
   permute_in_kernel<R><<<(unsigned)gblocks, nthreads, 0, st>>>(a.src, a.n, Y, a.npad, a.pad2orig, a.nrhs, mk, b);
   ++a.launches;
-  // gather: one stage buffer of a 64-row tile half and <= 8 source rows (padded by 16 bytes),
-  // two when a block sums several items (the next item loads while the current one is used)
+  // gather: one stage buffer of a dense 64-row tile half and <= 8 source rows (padded by 16
+  // bytes), two when a block sums several items (the next item loads while the current one is used)
   const size_t gsm = (a.max_group > 1 ? 2 : 1) * sizeof(C) *
-                     ((size_t)HR * stage_ld<C>(b) + (size_t)RCMAX * (b + 16 / sizeof(C)));
+                     ((size_t)HR * b + (size_t)RCMAX * (b + 16 / sizeof(C)));
   const unsigned gy = (unsigned)((a.nrhs + RCMAX - 1) / RCMAX);
   cudaFuncSetAttribute(gather_kernel<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm);
   cudaFuncSetAttribute(gather_kernel<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm);
@@ -1287,6 +1325,8 @@ static int sweep_impl(SweepLaunch& a, cudaStream_t st) {
     cs.stg = cstg;
     cs.Inv = a.Inv;
     cs.inv_off = a.inv_off;
+    cs.InvT = a.InvT;
+    cs.invT_off = a.invT_off;
     cs.mk = mk;
     cs.rrows = (int)rrows;
     auto launch_chain = [&](int lv, bool fwd) -> cudaError_t {
