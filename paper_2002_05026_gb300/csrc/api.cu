@@ -45,6 +45,8 @@ struct d3m_ctx {
   // factor data
   double2* K = nullptr;
   float4* K2 = nullptr;              // double-float split of K for the residual
+  float4* K2T = nullptr;             // the split of the transposed off-diagonal blocks
+  int64_t* res_ktoff = nullptr;      // per residual entry: its transposed block in K2T
   float4* X2 = nullptr;              // double-float split of x, n x max_nrhs
   TileTask* tasks = nullptr;
   KEntry* klist = nullptr;
@@ -132,6 +134,8 @@ struct d3m_ctx {
   // the caller's stream; keyed by what the captured pointers and sizes depend on
   cudaStream_t cap = nullptr;
   bool capturing = false;
+  cudaStream_t side = nullptr;       // second stream of a factorization (norm and split of K)
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   struct Graph { const void* src; int nrhs, accumulate; cudaGraphExec_t exec; int64_t launches; };
   std::vector<Graph> g_factor, g_solve;
 };
@@ -397,6 +401,12 @@ static int create_impl(d3m_handle* out, const d3m_pattern* pat, const int32_t* p
   if (cc_major != 10 || cc_minor != 3)
     return set_err(h, D3M_ERR_CUDA, "this library is built for sm_103a (GB300) only; device is sm_" +
                                         std::to_string(cc_major) + std::to_string(cc_minor));
+  if (cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    return set_err(h, D3M_ERR_CUDA, "cannot create the factorization's second stream");
+  }
 #define ALLOC(ptr, T, count)                                                                     \
   do {                                                                                           \
     ptr = dalloc<T>(h, (size_t)(count));                                                         \
@@ -550,6 +560,19 @@ static int create_impl(d3m_handle* out, const d3m_pattern* pat, const int32_t* p
   UPLOAD(h->res_blk, S.res_blk);
   UPLOAD(h->res_src, S.res_src);
   UPLOAD(h->res_tr, S.res_tr);
+  {
+    // transposed copies of the off-diagonal stored blocks, one per transposed residual entry
+    std::vector<int64_t> kt(S.res_tr.size(), -1);
+    int64_t tot = 0;
+    for (int f = 0; f < S.N; ++f)
+      for (int64_t e = S.res_ptr[f]; e < S.res_ptr[f + 1]; ++e)
+        if (S.res_tr[e]) {
+          kt[e] = tot;
+          tot += (int64_t)S.m_orig[f] * S.m_orig[S.res_src[e]];
+        }
+    UPLOAD(h->res_ktoff, kt);
+    ALLOC(h->K2T, float4, std::max<int64_t>(1, tot));
+  }
   UPLOAD(h->m_orig, S.m_orig);
   UPLOAD(h->xoff_orig, S.xoff_orig);
   {
@@ -665,6 +688,8 @@ static ResidualParams residual_params(d3m_ctx* h, const double2* X, const double
   ResidualParams p;
   p.K = h->K;
   p.K2 = h->K2;
+  p.K2T = h->K2T;
+  p.res_ktoff = h->res_ktoff;
   p.X2 = h->X2;
   p.kblk_off = h->kblk_off;
   p.res_ptr = h->res_ptr;
@@ -708,12 +733,7 @@ static int enqueue_factor(d3m_ctx* h, const void* Kin, bool kdev, cudaStream_t s
   if (n0h > 0)
     CUDA_TRY(h, cudaMemcpyAsync(h->ready_hi, h->init_ready_hi, n0h * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
   CUDA_TRY(h, cudaMemcpyAsync(h->ctl, h->ctl0, sizeof(Ctl), cudaMemcpyDeviceToDevice, st));
-  // ||K_i||_inf for the backward error
-  ResidualParams rp = residual_params(h, nullptr, nullptr, 1);
-  CUDA_TRY(h, cudaMemsetAsync(rp.kmax, 0, h->ninst * sizeof(unsigned), st));
-  int rc = launch_knorm(rp, h->nchunks, st);
-  if (rc) return set_err(h, D3M_ERR_CUDA, std::string("knorm launch: ") + cudaGetErrorString((cudaError_t)rc));
-  h->launches += 1;
+  int rc = 0;
   FactorParams p;
   p.tasks = h->tasks;
   p.klist = h->klist;
@@ -743,12 +763,23 @@ static int enqueue_factor(d3m_ctx* h, const void* Kin, bool kdev, cudaStream_t s
   if (rc) return set_err(h, D3M_ERR_CUDA, std::string("factor launch: ") + cudaGetErrorString((cudaError_t)rc));
   ev_end(h, d3m_ctx::EV_FACTOR, st);
   h->launches += 1;
+  // ||K_i||_inf and the split of K (for the residual) on a second stream, concurrently with the
+  // block inverses: the persistent factorization holds every SM, the two smaller kernels share them
+  CUDA_TRY(h, cudaEventRecord(h->ev_fork, st));
+  CUDA_TRY(h, cudaStreamWaitEvent(h->side, h->ev_fork, 0));
+  ResidualParams rp = residual_params(h, nullptr, nullptr, 1);
+  CUDA_TRY(h, cudaMemsetAsync(rp.kmax, 0, h->ninst * sizeof(unsigned), h->side));
+  rc = launch_knorm(rp, h->nchunks, h->side);
+  if (rc) return set_err(h, D3M_ERR_CUDA, std::string("knorm launch: ") + cudaGetErrorString((cudaError_t)rc));
+  h->launches += 1;
+  CUDA_TRY(h, cudaEventRecord(h->ev_join, h->side));
   if (h->use_inv && h->n_inv_work > 0) {
     rc = launch_inv_build(h->inv_work, h->n_inv_work, h->tstart, h->tcolptr, h->inv_off, h->invT_off, h->L, h->Linv,
                           h->Inv, h->InvT, h->b, st);
     if (rc) return set_err(h, D3M_ERR_CUDA, std::string("block inverse launch: ") + cudaGetErrorString((cudaError_t)rc));
     h->launches += 1;
   }
+  CUDA_TRY(h, cudaStreamWaitEvent(st, h->ev_join, 0));
   CUDA_TRY(h, cudaMemcpyAsync(h->h_ctl, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
   return D3M_OK;
 }
@@ -1147,6 +1178,9 @@ const char* d3m_last_error(d3m_handle h) {
 void d3m_destroy(d3m_handle h) {
   if (!h) return;
   for (auto& g : h->g_factor) cudaGraphExecDestroy(g.exec);
+  if (h->side) cudaStreamDestroy(h->side);
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->ev_join) cudaEventDestroy(h->ev_join);
   for (auto& g : h->g_solve) cudaGraphExecDestroy(g.exec);
   if (h->cap) cudaStreamDestroy(h->cap);
   for (void* p : h->allocs) cudaFree(p);

@@ -14,6 +14,8 @@ struct FactorParams;
 struct ResidualParams {
   const double2* K;
   const float4* K2;        // double-float split of K (hi_r, hi_i, lo_r, lo_i), K's layout
+  const float4* K2T;       // the same split of the transposed off-diagonal blocks
+  const int64_t* res_ktoff;  // [residual entries] offset of a transposed entry's block in K2T
   float4* X2;              // double-float split of X for the current residual (n x nrhs)
   const int64_t* kblk_off;
   const int64_t* res_ptr;

@@ -1048,33 +1048,36 @@ __global__ void __launch_bounds__(128) residual_kernel(ResidualParams p) {
     for (int64_t e = p.res_ptr[f]; e < p.res_ptr[f + 1]; ++e) {
       const int blk = p.res_blk[e], g = p.res_src[e];
       const int mg = p.m_orig[g];
-      const float4* Kp = p.K2 + p.kblk_off[blk];
+      // stored (f, g): entry (u, c) at K2[c * mf + u]; a block stored as (g, f) is read from its
+      // transposed copy in the same layout, so a warp's 32 rows always read 32 consecutive entries
       const bool tr = p.res_tr[e] != 0;
-      const float4* kb = tr ? Kp + (int64_t)u * mg : Kp + u;   // stored (g, f): (c, u) / (f, g): (u, c)
-      const int64_t ks = tr ? 1 : mf;
+      const float4* kb = (tr ? p.K2T + p.res_ktoff[e] : p.K2 + p.kblk_off[blk]) + u;
+      const int64_t ks = mf;
       const float4* xg = p.X2 + (int64_t)j0 * p.n + p.xoff_orig[g];
       for (int c0 = 0; c0 < mg; c0 += RES_CHUNK) {
         const int c1 = min(mg, c0 + RES_CHUNK);
-        float sr[RPT], cr[RPT], si[RPT], ci[RPT];
+        // four independent pairs per right-hand side (one per real product) keep four
+        // dependent two-sum chains in flight per column instead of two
+        float s0[RPT], c0v[RPT], s1[RPT], c1v[RPT], s2[RPT], c2v[RPT], s3[RPT], c3v[RPT];
 #pragma unroll
-        for (int q = 0; q < RPT; ++q) sr[q] = cr[q] = si[q] = ci[q] = 0.f;
+        for (int q = 0; q < RPT; ++q) s0[q] = c0v[q] = s1[q] = c1v[q] = s2[q] = c2v[q] = s3[q] = c3v[q] = 0.f;
         for (int c = c0; c < c1; ++c) {
           const float4 a = __ldg(kb + c * ks);          // (hi_r, hi_i, lo_r, lo_i)
 #pragma unroll
           for (int q = 0; q < RPT; ++q) {
             if (q < nj) {
               const float4 x = __ldg(xg + (int64_t)q * p.n + c);
-              df_mac(sr[q], cr[q], a.x, a.z, x.x, x.z);       // + a_r x_r
-              df_mac(sr[q], cr[q], -a.y, -a.w, x.y, x.w);     // - a_i x_i
-              df_mac(si[q], ci[q], a.x, a.z, x.y, x.w);       // + a_r x_i
-              df_mac(si[q], ci[q], a.y, a.w, x.x, x.z);       // + a_i x_r
+              df_mac(s0[q], c0v[q], a.x, a.z, x.x, x.z);       // + a_r x_r
+              df_mac(s1[q], c1v[q], -a.y, -a.w, x.y, x.w);     // - a_i x_i
+              df_mac(s2[q], c2v[q], a.x, a.z, x.y, x.w);       // + a_r x_i
+              df_mac(s3[q], c3v[q], a.y, a.w, x.x, x.z);       // + a_i x_r
             }
           }
         }
 #pragma unroll
         for (int q = 0; q < RPT; ++q) {
-          accr[q] += (double)sr[q] + (double)cr[q];
-          acci[q] += (double)si[q] + (double)ci[q];
+          accr[q] += ((double)s0[q] + (double)c0v[q]) + ((double)s1[q] + (double)c1v[q]);
+          acci[q] += ((double)s2[q] + (double)c2v[q]) + ((double)s3[q] + (double)c3v[q]);
         }
       }
     }
@@ -1125,11 +1128,13 @@ __global__ void __launch_bounds__(256) knorm_kernel(ResidualParams p) {
       const int mg = p.m_orig[g];
       const double2* Kp = p.K + p.kblk_off[blk];
       const bool tr = p.res_tr[e] != 0;
-      float4* K2 = const_cast<float4*>(p.K2) + p.kblk_off[blk];
+      // untransposed visit: the split in K's layout; transposed visit: the split of the
+      // transposed block (entry (u, c) at c * mf + u), written with coalesced stores
+      float4* K2 = tr ? const_cast<float4*>(p.K2T) + p.res_ktoff[e] : const_cast<float4*>(p.K2) + p.kblk_off[blk];
       for (int c = 0; c < mg; ++c) {
         const int64_t o = tr ? (int64_t)u * mg + c : (int64_t)c * mf + u;
         const float4 v = split_c_bits(__ldg(Kp + o));
-        if (!tr) K2[o] = v;                     // every stored entry is visited once untransposed
+        K2[(int64_t)c * mf + u] = v;
         sum += sqrtf(v.x * v.x + v.y * v.y);
       }
     }
