@@ -90,7 +90,9 @@ typedef struct {
   int32_t graphs;           /* 1 = capture each launch sequence (factorization with K in device
                                memory; one refinement step of a solve) into a CUDA graph on
                                first use and replay it afterwards; default 0 */
-  int32_t reserved0;
+  int32_t seg_group;        /* source blocks whose Schur updates of a tile form one update task
+                               (0 = default: 8 in the mixed modes, 1 in FP64; 1 = a task per
+                               source block, the earliest start) */
   double prio_slack;        /* tasks whose estimated slack is within prio_slack x the critical
                                path are served first by the device scheduler (default 0.08;
                                0 = only the critical path itself) */

@@ -41,7 +41,7 @@ class d3m_pattern(ctypes.Structure):
 class d3m_options(ctypes.Structure):
     _fields_ = [("precision", c_int32), ("refine_max_iter", c_int32), ("refine_tol", c_double),
                 ("timeout_ns", c_int64), ("tile", c_int32), ("max_nrhs", c_int32),
-                ("fp64_omega", c_int32), ("debug_flags", c_int32), ("graphs", c_int32), ("reserved0", c_int32),
+                ("fp64_omega", c_int32), ("debug_flags", c_int32), ("graphs", c_int32), ("seg_group", c_int32),
                 ("prio_slack", c_double), ("refine_fwd_tol", c_double)]
 
 

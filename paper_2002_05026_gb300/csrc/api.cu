@@ -379,7 +379,11 @@ static int create_impl(d3m_handle* out, const d3m_pattern* pat, const int32_t* p
   }
   h->csize = h->fp64 ? sizeof(double2) : sizeof(float2);
   std::string err;
-  int rc = analyze(pat, perm, h->b, true, h->S, err, h->opt.prio_slack);
+  // mixed precision: a tile's Schur updates from up to 8 source blocks form one update task (the
+  // per-task epilogue through the accumulator dominates short segments); FP64 is DFMA bound and
+  // keeps one task per source block
+  if (h->opt.seg_group <= 0) h->opt.seg_group = h->fp64 ? 1 : 8;
+  int rc = analyze(pat, perm, h->b, true, h->S, err, h->opt.prio_slack, h->opt.seg_group);
   if (rc != D3M_OK) {
     delete h;
     return set_err(nullptr, rc, err);

@@ -973,9 +973,10 @@ __global__ void __launch_bounds__(GT) chain_kernel(ChainSweep s, const typename 
 // a_hi x_hi is formed exactly (product plus its FMA-recovered error), the two cross terms
 // a_hi x_lo + a_lo x_hi are added to that error, and the sum is kept as a renormalised pair
 // (s, c) (Knuth's two-sum of s and the product, then a fast two-sum), i.e. with about 2^-48
-// relative rounding per term.  Every 32 columns the pair is added into an FP64 accumulator,
-// and r = b - acc is formed in FP64.  Error: 2^-48 relative from the splits plus at most
-// 32 * 2^-48 of the chunk's absolute sum per chunk (typically a few 2^-48), then FP64 rounding
+// relative rounding per term.  Every 128 columns the pair is added into an FP64 accumulator
+// (more often costs FP64-pipe conversions), and r = b - acc is formed in FP64.  Error: 2^-48
+// relative from the splits plus at most 128 * 2^-48 of the chunk's absolute sum per chunk
+// (typically about 10 * 2^-48), then FP64 rounding
 // of the chunk sums: a few 1e-16 of |K||x| in practice, comparable to a plain FP64 dot product
 // and far below the 1e-12 backward-error target.
 // Thread (row u of block f, rhs group): RPT right-hand sides per thread share each K load.
@@ -1028,10 +1029,10 @@ __global__ void split_x_kernel(const double2* __restrict__ X, float4* __restrict
   if (i < total) X2[i] = split_c(X[i]);
 }
 
-constexpr int RES_CHUNK = 32;
+constexpr int RES_CHUNK = 128;
 
 template <int RPT>
-__global__ void __launch_bounds__(128) residual_kernel(ResidualParams p) {
+__global__ void __launch_bounds__(128, 8) residual_kernel(ResidualParams p) {
   const int i = threadIdx.x % 32, w = threadIdx.x / 32;
   const int j0 = (blockIdx.y * (blockDim.x / 32) + w) * RPT;
   const int2 ch = p.chunks[blockIdx.x];
@@ -1056,28 +1057,27 @@ __global__ void __launch_bounds__(128) residual_kernel(ResidualParams p) {
       const float4* xg = p.X2 + (int64_t)j0 * p.n + p.xoff_orig[g];
       for (int c0 = 0; c0 < mg; c0 += RES_CHUNK) {
         const int c1 = min(mg, c0 + RES_CHUNK);
-        // four independent pairs per right-hand side (one per real product) keep four
-        // dependent two-sum chains in flight per column instead of two
-        float s0[RPT], c0v[RPT], s1[RPT], c1v[RPT], s2[RPT], c2v[RPT], s3[RPT], c3v[RPT];
+        float sr[RPT], cr[RPT], si[RPT], ci[RPT];
 #pragma unroll
-        for (int q = 0; q < RPT; ++q) s0[q] = c0v[q] = s1[q] = c1v[q] = s2[q] = c2v[q] = s3[q] = c3v[q] = 0.f;
+        for (int q = 0; q < RPT; ++q) sr[q] = cr[q] = si[q] = ci[q] = 0.f;
+#pragma unroll 4
         for (int c = c0; c < c1; ++c) {
           const float4 a = __ldg(kb + c * ks);          // (hi_r, hi_i, lo_r, lo_i)
 #pragma unroll
           for (int q = 0; q < RPT; ++q) {
             if (q < nj) {
               const float4 x = __ldg(xg + (int64_t)q * p.n + c);
-              df_mac(s0[q], c0v[q], a.x, a.z, x.x, x.z);       // + a_r x_r
-              df_mac(s1[q], c1v[q], -a.y, -a.w, x.y, x.w);     // - a_i x_i
-              df_mac(s2[q], c2v[q], a.x, a.z, x.y, x.w);       // + a_r x_i
-              df_mac(s3[q], c3v[q], a.y, a.w, x.x, x.z);       // + a_i x_r
+              df_mac(sr[q], cr[q], a.x, a.z, x.x, x.z);       // + a_r x_r
+              df_mac(sr[q], cr[q], -a.y, -a.w, x.y, x.w);     // - a_i x_i
+              df_mac(si[q], ci[q], a.x, a.z, x.y, x.w);       // + a_r x_i
+              df_mac(si[q], ci[q], a.y, a.w, x.x, x.z);       // + a_i x_r
             }
           }
         }
 #pragma unroll
         for (int q = 0; q < RPT; ++q) {
-          accr[q] += ((double)s0[q] + (double)c0v[q]) + ((double)s1[q] + (double)c1v[q]);
-          acci[q] += ((double)s2[q] + (double)c2v[q]) + ((double)s3[q] + (double)c3v[q]);
+          accr[q] += (double)sr[q] + (double)cr[q];
+          acci[q] += (double)si[q] + (double)ci[q];
         }
       }
     }

@@ -34,7 +34,8 @@ static int fail(std::string& err, const char* msg, long a = -1, long b = -1) {
 }
 
 int analyze(const d3m_pattern* pat, const int32_t* perm_in, int b, bool build_tasks,
-            Symbolic& s, std::string& err, double prio_slack) {
+            Symbolic& s, std::string& err, double prio_slack, int seg_group) {
+  if (seg_group < 1) seg_group = 1;
   if (!pat || !pat->colptr || !pat->rowidx) return fail(err, "pattern or its arrays are NULL");
   const int N = pat->nblk;
   if (N <= 0) return fail(err, "nblk must be positive (got %ld)", N);
@@ -246,9 +247,10 @@ int analyze(const d3m_pattern* pat, const int32_t* perm_in, int b, bool build_ta
       for (int k : ks) nk += s.ntile[k];
       kl_ptr[t + 1] = nk;
       // the in-block part is cut into [tstart, J-1) and [J-1, J): the last tile column K = J-1
-      // becomes ready last (it is on the critical path), the others earlier
+      // becomes ready last (it is on the critical path), the others earlier; the source blocks
+      // before it go seg_group to a segment
       const int nib = J - s.tstart[q];
-      nseg[t] = (int32_t)ks.size() + (nib >= 2 ? 2 : nib);
+      nseg[t] = (int32_t)((ks.size() + seg_group - 1) / seg_group) + (nib >= 2 ? 2 : nib);
     }
   }
   for (int64_t t = 0; t < ntiles; ++t) kl_ptr[t + 1] += kl_ptr[t];
@@ -289,9 +291,9 @@ int analyze(const d3m_pattern* pat, const int32_t* perm_in, int b, bool build_ta
         int64_t a = s.tile_of(I, K), bb = s.tile_of(J, K);
         s.klist[w++] = KEntry{(int32_t)a, (int32_t)bb, K, 0};
       };
-      for (int k : ks) {
-        for (int K = s.tstart[k]; K < s.tstart[k + 1]; ++K) push(K);
-        sb.push_back(w);
+      for (size_t a = 0; a < ks.size(); ++a) {
+        for (int K = s.tstart[ks[a]]; K < s.tstart[ks[a] + 1]; ++K) push(K);
+        if ((a + 1) % seg_group == 0 || a + 1 == ks.size()) sb.push_back(w);
       }
       if (J - s.tstart[q] >= 2) {
         for (int K = s.tstart[q]; K < J - 1; ++K) push(K);

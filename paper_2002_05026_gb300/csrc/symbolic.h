@@ -121,7 +121,7 @@ struct Symbolic {
 // estimated slack is within prio_slack of the critical path are flagged TF_PRIO.
 // Returns D3M_OK or an error code with a message in `err`.
 int analyze(const d3m_pattern* pat, const int32_t* perm, int b, bool build_tasks,
-            Symbolic& s, std::string& err, double prio_slack = 0.08);
+            Symbolic& s, std::string& err, double prio_slack = 0.08, int seg_group = 1);
 
 // Grid nested dissection (see d3m_order_grid_nd).
 int order_grid_nd(int nx, int ny, int nz, std::vector<int32_t>& perm);

@@ -38,7 +38,7 @@ def _as_colmajor(B):
 
 
 def _options(precision, max_nrhs, refine_tol, refine_max_iter, timeout_ns, fp64_omega, debug_flags, graphs=False,
-             prio_slack=None):
+             prio_slack=None, seg_group=0):
     opt = _abi.d3m_default_options()
     opt.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     opt.max_nrhs = max_nrhs
@@ -51,6 +51,7 @@ def _options(precision, max_nrhs, refine_tol, refine_max_iter, timeout_ns, fp64_
     opt.graphs = int(graphs)
     if prio_slack is not None:
         opt.prio_slack = float(prio_slack)
+    opt.seg_group = int(seg_group)
     return opt
 
 
@@ -60,13 +61,13 @@ class D3M:
     def __init__(self, colptr, rowidx, m=None, blk_size=None, perm=None, precision="bf16x3",
                  max_nrhs: int = 32, refine_tol: float = 1e-12, refine_max_iter: int = 20,
                  timeout_ns: int = 0, fp64_omega: bool = False, debug_flags: int = 0, graphs: bool = False,
-                 prio_slack=None, stream=None):
+                 prio_slack=None, seg_group: int = 0, stream=None):
         lib = load()
         self._lib = lib
         self.h = c_void_p()
         pat, self._keep = _abi.make_pattern(colptr, rowidx, m, blk_size)
         opt = _options(precision, max_nrhs, refine_tol, refine_max_iter, timeout_ns, fp64_omega, debug_flags, graphs,
-                       prio_slack)
+                       prio_slack, seg_group)
         pp = None
         if perm is not None:
             self._perm = np.ascontiguousarray(perm, dtype=np.int32)
