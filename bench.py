@@ -32,6 +32,9 @@ if ROOT not in sys.path:
 
 METRIC = "factor+solve time & TFLOP/s at 1e-9 rel err: mixed-prec vs FP64 block LDLᵀ"
 FP64_PEAK_GFLOPS = 1250.0     # GB300 FP64 nominal (152 SMs x 2.07 GHz x ~4 flop/clk/SM)
+# the residual's products issue on the FP32 pipe in double-float form: 60 FP32 instructions per
+# complex multiply-add (8 flops) and right-hand side
+RESID_PEAK_TFLOPS = 152 * 128 * 2.07e9 * 8 / 60 / 1e12
 
 
 def parse_args():
@@ -56,6 +59,29 @@ def measured_peaks():
         with open(p) as f:
             return json.load(f), "measured"
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+# ------------------------------------------------------------------ recorded DRAM traffic
+# Per-launch DRAM bytes of a kernel come from an ncu capture (profiles/traffic_<workload>.txt,
+# lines "<kernel> <bytes per launch> <sha1 of its source file>"); a number whose kernel source
+# has changed since the capture is not reported.
+TRAFFIC_SOURCES = {"factor_kernel": "factor_tc.cu", "residual": "solve.cu", "solve_sweep": "solve.cu"}
+
+
+def recorded_traffic(workload: str, kernel: str):
+    import hashlib
+    path = os.path.join(ROOT, "profiles", f"traffic_{workload}.txt")
+    src = TRAFFIC_SOURCES.get(kernel)
+    if not src or not os.path.exists(path):
+        return None
+    with open(os.path.join(ROOT, "paper_2002_05026_gb300", "csrc", src), "rb") as f:
+        sha = hashlib.sha1(f.read()).hexdigest()
+    with open(path) as f:
+        for line in f:
+            parts = line.split()
+            if len(parts) == 3 and parts[0] == kernel and parts[2] == sha:
+                return float(parts[1])
+    return None
 
 
 # ------------------------------------------------------------------ clocks
@@ -460,10 +486,11 @@ def main():
                       "unit": unit, "peak_source": pname, "kernel_ms": fms}))
     if info["residual_calls"]:
         rms = info["residual_ms_total"] / info["residual_calls"]
-        kern.append(("fp64_residual", info["residual_ms_total"],
+        kern.append(("residual", info["residual_ms_total"],
                      {"bound": "alu", "achieved": info["residual_flops_per_rhs"] * nrhs / (rms * 1e-3) / 1e12,
-                      "peak": FP64_PEAK_GFLOPS / 1e3, "unit": "TFLOP/s",
-                      "peak_source": "FP64 nominal 1.25 TFLOP/s", "kernel_ms": rms}))
+                      "peak": RESID_PEAK_TFLOPS, "unit": "TFLOP/s",
+                      "peak_source": "FP32 issue rate (152 SMs x 128 lanes x 2.07 GHz) x 8 flops / 60 FP32 "
+                                     "instructions per double-float complex multiply-add", "kernel_ms": rms}))
     if info["sweep_calls"]:
         sms = info["sweep_ms_total"] / info["sweep_calls"]
         esz = 16 if args.precision == "fp64" else 8
@@ -476,7 +503,7 @@ def main():
     roof = dict(roof)
     roof["kernel"] = dom_name
     roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = None
+    roof["traffic"] = recorded_traffic(args.workload, dom_name)
     roof["peak_kind"] = peak_kind
     breakdown = {k: {"ms_per_step": t / args.steps, **{kk: v for kk, v in r.items() if kk in ("achieved", "peak", "unit", "bound")}}
                  for k, t, r in kern}

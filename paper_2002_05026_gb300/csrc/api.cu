@@ -47,6 +47,8 @@ struct d3m_ctx {
   float4* K2 = nullptr;              // double-float split of K for the residual
   float4* K2T = nullptr;             // the split of the transposed off-diagonal blocks
   int64_t* res_ktoff = nullptr;      // per residual entry: its transposed block in K2T
+  double2* part_acc = nullptr;       // residual partial sums [2][n * max_nrhs]
+  int* part_cnt = nullptr;           // residual arrival counters [chunks * rhs groups]
   float4* X2 = nullptr;              // double-float split of x, n x max_nrhs
   TileTask* tasks = nullptr;
   KEntry* klist = nullptr;
@@ -559,6 +561,7 @@ static int create_impl(d3m_handle* out, const d3m_pattern* pat, const int32_t* p
   ALLOC(h->d_xbest, double2, S.n * mr);
   ALLOC(h->d_r, double2, S.n * mr);
   ALLOC(h->X2, float4, S.n * mr);
+  ALLOC(h->part_acc, double2, 2 * S.n * mr);
   UPLOAD(h->kblk_off, S.kblk_off);
   UPLOAD(h->res_ptr, S.res_ptr);
   UPLOAD(h->res_blk, S.res_blk);
@@ -585,6 +588,8 @@ static int create_impl(d3m_handle* out, const d3m_pattern* pat, const int32_t* p
       for (int r = 0; r < S.m_orig[f]; r += 32) ch.push_back(make_int2(f, r));
     h->nchunks = (int)ch.size();
     UPLOAD(h->chunks, ch);
+    ALLOC(h->part_cnt, int, (size_t)h->nchunks * mr);
+    CUDA_TRY(h, cudaMemset(h->part_cnt, 0, (size_t)h->nchunks * mr * sizeof(int)));
     std::vector<int32_t> bc(S.nnzb_K);
     for (int g = 0; g < S.N; ++g)
       for (int64_t p = S.colptr[g]; p < S.colptr[g + 1]; ++p) bc[p] = g;
@@ -694,6 +699,9 @@ static ResidualParams residual_params(d3m_ctx* h, const double2* X, const double
   p.K2 = h->K2;
   p.K2T = h->K2T;
   p.res_ktoff = h->res_ktoff;
+  p.part_acc = h->part_acc;
+  p.part_ld = h->S.n * (int64_t)h->opt.max_nrhs;
+  p.part_cnt = h->part_cnt;
   p.X2 = h->X2;
   p.kblk_off = h->kblk_off;
   p.res_ptr = h->res_ptr;

@@ -16,6 +16,9 @@ struct ResidualParams {
   const float4* K2;        // double-float split of K (hi_r, hi_i, lo_r, lo_i), K's layout
   const float4* K2T;       // the same split of the transposed off-diagonal blocks
   const int64_t* res_ktoff;  // [residual entries] offset of a transposed entry's block in K2T
+  double2* part_acc;       // [2][part_ld] partial sums of the blocks sharing a row chunk
+  int64_t part_ld;         // n * max_nrhs
+  int* part_cnt;           // [row chunks * rhs groups] arrivals (returned to 0 by the last)
   float4* X2;              // double-float split of X for the current residual (n x nrhs)
   const int64_t* kblk_off;
   const int64_t* res_ptr;

@@ -1030,6 +1030,7 @@ __global__ void split_x_kernel(const double2* __restrict__ X, float4* __restrict
 }
 
 constexpr int RES_CHUNK = 128;
+constexpr int RES_PARTS = 2;      // blocks sharing one row chunk's contributions
 
 template <int RPT>
 __global__ void __launch_bounds__(128, 8) residual_kernel(ResidualParams p) {
@@ -1045,8 +1046,13 @@ __global__ void __launch_bounds__(128, 8) residual_kernel(ResidualParams p) {
   double accr[RPT], acci[RPT];
 #pragma unroll
   for (int q = 0; q < RPT; ++q) accr[q] = acci[q] = 0.0;
+  // the row's contributions are split over gridDim.z blocks (more, shorter warps: no half-empty
+  // last wave); the last block to finish adds the parts in part order and forms r
+  const int part = blockIdx.z, nparts = gridDim.z;
+  const int64_t eb = p.res_ptr[f], ee = p.res_ptr[f + 1], eh = (ee - eb + nparts - 1) / nparts;
+  const int64_t e_lo = min(ee, eb + part * eh), e_hi = min(ee, e_lo + eh);
   if (active) {
-    for (int64_t e = p.res_ptr[f]; e < p.res_ptr[f + 1]; ++e) {
+    for (int64_t e = e_lo; e < e_hi; ++e) {
       const int blk = p.res_blk[e], g = p.res_src[e];
       const int mg = p.m_orig[g];
       // stored (f, g): entry (u, c) at K2[c * mf + u]; a block stored as (g, f) is read from its
@@ -1080,6 +1086,32 @@ __global__ void __launch_bounds__(128, 8) residual_kernel(ResidualParams p) {
           acci[q] += (double)si[q] + (double)ci[q];
         }
       }
+    }
+  }
+  if (nparts > 1) {
+    __shared__ int s_last;
+#pragma unroll
+    for (int q = 0; q < RPT; ++q)
+      if (active && q < nj)
+        p.part_acc[(int64_t)part * p.part_ld + (int64_t)(j0 + q) * p.n + p.xoff_orig[f] + u] =
+            make_double2(accr[q], acci[q]);
+    __threadfence();
+    __syncthreads();
+    int* ctr = p.part_cnt + ((int64_t)blockIdx.y * gridDim.x + blockIdx.x);
+    if (threadIdx.x == 0) s_last = atomicAdd(ctr, 1) == nparts - 1;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    if (threadIdx.x == 0) *ctr = 0;                     // ready for the next residual
+#pragma unroll
+    for (int q = 0; q < RPT; ++q) {
+      accr[q] = acci[q] = 0.0;
+      if (active && q < nj)
+        for (int pp = 0; pp < nparts; ++pp) {
+          const double2 v = __ldcg(p.part_acc + (int64_t)pp * p.part_ld + (int64_t)(j0 + q) * p.n + p.xoff_orig[f] + u);
+          accr[q] += v.x;
+          acci[q] += v.y;
+        }
     }
   }
 #pragma unroll
@@ -1475,12 +1507,12 @@ int launch_residual(const ResidualParams& p, int nchunks, cudaStream_t st) {
   split_x_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(p.X, p.X2, total);
   // 4 warps per block, RPT right-hand sides per warp
   if (p.nrhs == 1) {
-    residual_kernel<1><<<dim3((unsigned)nchunks, 1), 32, 0, st>>>(p);
+    residual_kernel<1><<<dim3((unsigned)nchunks, 1, RES_PARTS), 32, 0, st>>>(p);
   } else {
     // RPT = 2 measured faster than 4 (more warps in flight; the pair chains already give ILP)
     const int groups = (p.nrhs + 1) / 2;
     const int wpb = groups < 4 ? groups : 4;
-    residual_kernel<2><<<dim3((unsigned)nchunks, (unsigned)((groups + wpb - 1) / wpb)), 32 * wpb, 0, st>>>(p);
+    residual_kernel<2><<<dim3((unsigned)nchunks, (unsigned)((groups + wpb - 1) / wpb), RES_PARTS), 32 * wpb, 0, st>>>(p);
   }
   return (int)cudaGetLastError();
 }
