@@ -463,9 +463,9 @@ static int create_impl(d3m_handle* out, const d3m_pattern* pat, const int32_t* p
   h->Sacc = dalloc<unsigned char>(h, (size_t)std::max<int64_t>(1, S.n_acc) * b * b * h->csize);
   if (!h->L || !h->Linv || !h->D || !h->Sacc) return set_err(h, D3M_ERR_OOM, "cudaMalloc failed for the factor tiles");
   if (h->tc) {
-    // operand planes (bf16): A: [tile][2 splits][2 planes][b rows][b], B: [tile][2][3][b][b]
+    // operand planes (bf16): A: [tile][2 splits][2 planes][b rows][b], B: [tile][2][2][b][b]
     h->opA = dalloc<unsigned char>(h, (size_t)ntiles * 4 * b * b * 2);
-    h->opB = dalloc<unsigned char>(h, (size_t)ntiles * 6 * b * b * 2);
+    h->opB = dalloc<unsigned char>(h, (size_t)ntiles * 4 * b * b * 2);
     if (!h->opA || !h->opB) return set_err(h, D3M_ERR_OOM, "cudaMalloc failed for the tensor-core operands");
     std::string e2;
     if (tc_make_maps(h->opA, h->opB, ntiles, &h->maps, e2) != 0) return set_err(h, D3M_ERR_CUDA, e2);

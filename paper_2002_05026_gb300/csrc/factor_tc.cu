@@ -6,12 +6,13 @@
 // a = a_hi + a_lo with a_hi = bf16(a), a_lo = bf16(a - a_hi); a*b ~ a_hi b_hi + a_hi b_lo +
 // a_lo b_hi, accumulated in FP32 in tensor memory (Henry, Tang, Heinecke, "Leveraging the
 // bfloat16 artificial intelligence datatype for higher-precision computations", ARITH 2019).
-// Complex products use the real embedding with stacked B planes: with B stored as three
-// 128-row planes [-B_i; B_r; B_i], one M=128 x N=256 MMA with A_r over rows [B_r; B_i] and one
-// with A_i over rows [-B_i; B_r] give [Re | Im] of A B^T in a 256-column accumulator.
+// Complex products use the real embedding with B stored as two 128-row planes [B_r; B_i]: one
+// M=128 x N=256 MMA of A_r over both planes adds [A_r B_r^T | A_r B_i^T] to a 256-column
+// accumulator, and two M=128 x N=128 MMAs of A_i add -A_i B_i^T (the instruction's negate-B
+// bit) to the real half and A_i B_r^T to the imaginary half: [Re | Im] of A B^T.
 //
 // Data movement: every finished L tile is written once, by its owner, as bf16 operand planes
-// (opA: L_IJ [hi_r, hi_i, lo_r, lo_i]; opB: W_IJ = L_IJ D_J as [-W_i, W_r, W_i] x [hi, lo], or
+// (opA: L_IJ [hi_r, hi_i, lo_r, lo_i]; opB: W_IJ = L_IJ D_J as [W_r, W_i] x [hi, lo], or
 // T_J = D_J^{-1} L_JJ^{-1} for a diagonal tile), row-major with the K index contiguous.  TMA
 // tiled loads (64-byte swizzle) stage 32-wide K chunks into shared memory for the MMAs.
 //
@@ -35,18 +36,23 @@ constexpr int NTHR = 256;
 constexpr int KC = 32;                          // K elements per chunk (64 bytes of bf16)
 constexpr uint32_t PLANE = TB * KC * 2;         // 8 KB: one 128-row plane of one chunk
 constexpr uint32_t STAGE_A = 4 * PLANE;         // 32 KB
-constexpr uint32_t STAGE_B = 6 * PLANE;         // 48 KB
-constexpr uint32_t STAGE = STAGE_A + STAGE_B;   // 80 KB
+constexpr uint32_t STAGE_B = 4 * PLANE;         // 32 KB
+constexpr uint32_t STAGE = STAGE_A + STAGE_B;   // 64 KB
+constexpr int NSTAGE = 3;                       // GEMM pipeline depth (192 KB)
 constexpr uint32_t SMEM_S = 0;                  // TRSM A operand (4 chunks x 32 KB)
-constexpr uint32_t SMEM_T = 128 * 1024;         // TRSM B stages (2 x 48 KB)
-constexpr uint32_t SMEM_BYTES = SMEM_T + 2 * STAGE_B;   // 224 KB
+constexpr uint32_t SMEM_T = 128 * 1024;         // TRSM B stages (2 x 32 KB)
+constexpr uint32_t SMEM_BYTES = NSTAGE * STAGE > SMEM_T + 2 * STAGE_B ? NSTAGE * STAGE : SMEM_T + 2 * STAGE_B;
+constexpr uint32_t BROWS = 512;                 // opB rows per tile: [hi, lo] x [B_r, B_i] x 128
 constexpr int LDS = 129;                        // c64 diagonal tile row stride (elements)
 constexpr uint32_t DIAG_AUX = 130 * 1024;       // d / column / scratch vectors of a diagonal task
 constexpr uint32_t TMEM_COLS = 512;
 constexpr uint32_t ACC1 = 0, ACC2 = 256;        // TMEM columns of the two accumulators
 
-// instruction descriptor: kind::f16, A/B bf16, D f32, both K-major, M = 128, N = 256
+// instruction descriptors: kind::f16, A/B bf16, D f32, both K-major, M = 128, N = 256 or 128
+// (bit 14: negate B)
 constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((256u >> 3) << 17) | ((128u >> 4) << 24);
+constexpr uint32_t IDESC_N128 = (1u << 4) | (1u << 7) | (1u << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
+constexpr uint32_t IDESC_N128_NEGB = IDESC_N128 | (1u << 14);
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -97,12 +103,20 @@ __device__ __forceinline__ uint64_t desc_sw64(uint32_t saddr) {
   d |= (uint64_t)4 << 61;                 // 64-byte swizzle
   return d;
 }
-__device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t accum) {
+__device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t accum,
+                                         uint32_t idesc = IDESC) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
       " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
-      "l"(adesc), "l"(bdesc), "r"(IDESC), "r"(accum)
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
       : "memory");
+}
+// [Re | Im] += A B^T for one split pair: A planes a_r, a_i; B planes b (B_r) and b + PLANE (B_i)
+// (accum = 0 on the very first product: the N = 256 MMA initialises every column)
+__device__ __forceinline__ void cmma(uint32_t d, uint32_t a_r, uint32_t a_i, uint32_t b, uint32_t accum) {
+  mma_bf16(d, desc_sw64(a_r), desc_sw64(b), accum);                              // [A_r B_r | A_r B_i]
+  mma_bf16(d, desc_sw64(a_i), desc_sw64(b + PLANE), 1u, IDESC_N128_NEGB);        // Re -= A_i B_i
+  mma_bf16(d + 128, desc_sw64(a_i), desc_sw64(b), 1u, IDESC_N128);               // Im += A_i B_r
 }
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
@@ -190,7 +204,7 @@ __global__ void __launch_bounds__(NTHR, 1)
   // 1024-byte alignment of the dynamic region (swizzle atoms); pointer arithmetic on the shared
   // array keeps the accesses in the shared address space
   unsigned char* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
-  __shared__ __align__(8) uint64_t bar_full[2], bar_empty[2], bar_tfull[2], bar_tempty[2], bar_acc, bar_acc2;
+  __shared__ __align__(8) uint64_t bar_full[NSTAGE], bar_empty[NSTAGE], bar_tfull[2], bar_tempty[2], bar_acc, bar_acc2;
   __shared__ uint32_t s_tmem;
   __shared__ int s_task, s_pending;
   if (threadIdx.x == 0) s_pending = -1;          // read and written by thread 0 only
@@ -205,9 +219,11 @@ __global__ void __launch_bounds__(NTHR, 1)
   __nv_bfloat16* opB = reinterpret_cast<__nv_bfloat16*>(p.opB);
 
   if (tid == 0) {
-    for (int s = 0; s < 2; ++s) {
+    for (int s = 0; s < NSTAGE; ++s) {
       mbar_init(smem_u32(&bar_full[s]), 1);
       mbar_init(smem_u32(&bar_empty[s]), 1);
+    }
+    for (int s = 0; s < 2; ++s) {
       mbar_init(smem_u32(&bar_tfull[s]), 1);
       mbar_init(smem_u32(&bar_tempty[s]), 1);
     }
@@ -246,7 +262,7 @@ __global__ void __launch_bounds__(NTHR, 1)
       if (warp == 0) {
         if (lane == 0) {
           for (int c = 0; c < nchunk && !failed; ++c) {
-            const uint32_t s = g_load & 1, use = g_load >> 1;
+            const uint32_t s = g_load % NSTAGE, use = g_load / NSTAGE;
             if (!mbar_wait(smem_u32(&bar_empty[s]), (use & 1) ^ 1, deadline)) { failed = true; break; }
             const KEntry ke = p.klist[T.kl_off + c / (TB / KC)];
             const int x = (c % (TB / KC)) * KC;
@@ -256,7 +272,7 @@ __global__ void __launch_bounds__(NTHR, 1)
 #pragma unroll
             for (int q = 0; q < 4; ++q) tma_load_2d(sb + q * PLANE, &mapA, x, ke.a_tile * 512 + q * 128, fb);
 #pragma unroll
-            for (int q = 0; q < 6; ++q) tma_load_2d(sb + STAGE_A + q * PLANE, &mapB, x, ke.b_tile * 768 + q * 128, fb);
+            for (int q = 0; q < 4; ++q) tma_load_2d(sb + STAGE_A + q * PLANE, &mapB, x, ke.b_tile * BROWS + q * 128, fb);
             ++g_load;
           }
         }
@@ -264,7 +280,7 @@ __global__ void __launch_bounds__(NTHR, 1)
       } else if (warp == 1) {
         if (lane == 0) {
           for (int c = 0; c < nchunk && !failed; ++c) {
-            const uint32_t s = g_mma & 1, use = g_mma >> 1;
+            const uint32_t s = g_mma % NSTAGE, use = g_mma / NSTAGE;
             if (!mbar_wait(smem_u32(&bar_full[s]), use & 1, deadline)) { failed = true; break; }
             tc_fence_after();
             const uint32_t sb = smem_u32(smem + s * STAGE);
@@ -273,15 +289,12 @@ __global__ void __launch_bounds__(NTHR, 1)
               const uint32_t ko = kk * 32;
               const uint32_t a_hr = sb + 0 * PLANE + ko, a_hi = sb + 1 * PLANE + ko;
               const uint32_t a_lr = sb + 2 * PLANE + ko, a_li = sb + 3 * PLANE + ko;
-              const uint32_t bh = sb + STAGE_A + ko, bl = sb + STAGE_A + 3 * PLANE + ko;
+              const uint32_t bh = sb + STAGE_A + ko, bl = sb + STAGE_A + 2 * PLANE + ko;
               const uint32_t first = (c == 0 && kk == 0) ? 0u : 1u;
               // lo*hi and hi*lo first, then hi*hi
-              mma_bf16(tmem + ACC1, desc_sw64(a_lr), desc_sw64(bh + PLANE), first);
-              mma_bf16(tmem + ACC1, desc_sw64(a_li), desc_sw64(bh), 1u);
-              mma_bf16(tmem + ACC1, desc_sw64(a_hr), desc_sw64(bl + PLANE), 1u);
-              mma_bf16(tmem + ACC1, desc_sw64(a_hi), desc_sw64(bl), 1u);
-              mma_bf16(tmem + ACC1, desc_sw64(a_hr), desc_sw64(bh + PLANE), 1u);
-              mma_bf16(tmem + ACC1, desc_sw64(a_hi), desc_sw64(bh), 1u);
+              cmma(tmem + ACC1, a_lr, a_li, bh, first);
+              cmma(tmem + ACC1, a_hr, a_hi, bl, 1u);
+              cmma(tmem + ACC1, a_hr, a_hi, bh, 1u);
             }
             mma_commit(smem_u32(&bar_empty[s]));
             ++g_mma;
@@ -335,7 +348,7 @@ __global__ void __launch_bounds__(NTHR, 1)
         const uint32_t fb = smem_u32(&bar_tfull[s]);
         mbar_expect_tx(fb, STAGE_B);
 #pragma unroll
-        for (int q = 0; q < 6; ++q) tma_load_2d(sb + q * PLANE, &mapB, c * KC, T.diag * 768 + q * 128, fb);
+        for (int q = 0; q < 4; ++q) tma_load_2d(sb + q * PLANE, &mapB, c * KC, T.diag * BROWS + q * 128, fb);
         ++t_load;
       }
     }
@@ -496,25 +509,24 @@ __global__ void __launch_bounds__(NTHR, 1)
       }
       {
         // T_J = D^{-1} L^{-1}: row n, columns k (X[n][k] = sS[k][n] for k < n); coalesced 16-byte
-        // stores of the planes [-T_i, T_r, T_i] x [hi, lo] (16 threads per 256-byte plane row)
-        uint4* Bt = reinterpret_cast<uint4*>(opB + (int64_t)T.tile * 768 * TB);
+        // stores of the planes [T_r, T_i] x [hi, lo] (16 threads per 256-byte plane row)
+        uint4* Bt = reinterpret_cast<uint4*>(opB + (int64_t)T.tile * BROWS * TB);
         for (int it = tid; it < TB * 16; it += NTHR) {
           const int n = it >> 4, c8 = it & 15;
           const float2 dinv = cdiv(make_float2(1.f, 0.f), s_d[n]);
-          __nv_bfloat16 h[3][8], lo[3][8];
+          __nv_bfloat16 h[2][8], lo[2][8];
 #pragma unroll
           for (int k8 = 0; k8 < 8; ++k8) {
             const int k = c8 * 8 + k8;
             const float2 lv = (k < n) ? sS[k * LDS + n] : make_float2(k == n ? 1.f : 0.f, 0.f);
             const float2 tv = cmul(dinv, lv);
-            split2(-tv.y, h[0][k8], lo[0][k8]);
-            split2(tv.x, h[1][k8], lo[1][k8]);
-            split2(tv.y, h[2][k8], lo[2][k8]);
+            split2(tv.x, h[0][k8], lo[0][k8]);
+            split2(tv.y, h[1][k8], lo[1][k8]);
           }
 #pragma unroll
-          for (int pl = 0; pl < 3; ++pl) {
-            Bt[((0 * 384 + pl * 128) + n) * 16 + c8] = pack8(h[pl]);
-            Bt[((1 * 384 + pl * 128) + n) * 16 + c8] = pack8(lo[pl]);
+          for (int pl = 0; pl < 2; ++pl) {
+            Bt[((0 * 256 + pl * 128) + n) * 16 + c8] = pack8(h[pl]);
+            Bt[((1 * 256 + pl * 128) + n) * 16 + c8] = pack8(lo[pl]);
           }
         }
       }
@@ -559,7 +571,7 @@ __global__ void __launch_bounds__(NTHR, 1)
             const uint32_t fb = smem_u32(&bar_tfull[s]);
             mbar_expect_tx(fb, STAGE_B);
 #pragma unroll
-            for (int q = 0; q < 6; ++q) tma_load_2d(sb + q * PLANE, &mapB, c * KC, T.diag * 768 + q * 128, fb);
+            for (int q = 0; q < 4; ++q) tma_load_2d(sb + q * PLANE, &mapB, c * KC, T.diag * BROWS + q * 128, fb);
             ++t_load;
           }
         }
@@ -578,14 +590,11 @@ __global__ void __launch_bounds__(NTHR, 1)
               const uint32_t ko = kk * 32;
               const uint32_t a_hr = ab + 0 * PLANE + ko, a_hi = ab + 1 * PLANE + ko;
               const uint32_t a_lr = ab + 2 * PLANE + ko, a_li = ab + 3 * PLANE + ko;
-              const uint32_t bh = tb + ko, bl = tb + 3 * PLANE + ko;
+              const uint32_t bh = tb + ko, bl = tb + 2 * PLANE + ko;
               const uint32_t first = (c == 0 && kk == 0) ? 0u : 1u;
-              mma_bf16(tmem + ACC2, desc_sw64(a_lr), desc_sw64(bh + PLANE), first);
-              mma_bf16(tmem + ACC2, desc_sw64(a_li), desc_sw64(bh), 1u);
-              mma_bf16(tmem + ACC2, desc_sw64(a_hr), desc_sw64(bl + PLANE), 1u);
-              mma_bf16(tmem + ACC2, desc_sw64(a_hi), desc_sw64(bl), 1u);
-              mma_bf16(tmem + ACC2, desc_sw64(a_hr), desc_sw64(bh + PLANE), 1u);
-              mma_bf16(tmem + ACC2, desc_sw64(a_hi), desc_sw64(bh), 1u);
+              cmma(tmem + ACC2, a_lr, a_li, bh, first);
+              cmma(tmem + ACC2, a_hr, a_hi, bl, 1u);
+              cmma(tmem + ACC2, a_hr, a_hi, bh, 1u);
             }
             mma_commit(smem_u32(&bar_tempty[s]));
             ++t_mma;
@@ -627,7 +636,7 @@ __global__ void __launch_bounds__(NTHR, 1)
         Lt4[e] = stg[rr * 64 + (u ^ (rr & 7))];
       }
       uint4* A = reinterpret_cast<uint4*>(opA + (int64_t)T.tile * 512 * TB);
-      uint4* B = reinterpret_cast<uint4*>(opB + (int64_t)T.tile * 768 * TB);
+      uint4* B = reinterpret_cast<uint4*>(opB + (int64_t)T.tile * BROWS * TB);
       for (int it = tid; it < TB * 16; it += NTHR) {
         const int rr = it >> 4, c8 = it & 15;   // row, group of 8 columns
         float2 l[8];
@@ -638,26 +647,25 @@ __global__ void __launch_bounds__(NTHR, 1)
           l[2 * k] = make_float2(v.x, v.y);
           l[2 * k + 1] = make_float2(v.z, v.w);
         }
-        __nv_bfloat16 h[6][8], lo[6][8];   // planes: L_r, L_i, -W_i, W_r, W_i (+ spare)
+        __nv_bfloat16 h[4][8], lo[4][8];   // planes: L_r, L_i, W_r, W_i
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
           const float2 w = cmul(l[k], s_d[c8 * 8 + k]);
           split2(l[k].x, h[0][k], lo[0][k]);
           split2(l[k].y, h[1][k], lo[1][k]);
-          split2(-w.y, h[2][k], lo[2][k]);
-          split2(w.x, h[3][k], lo[3][k]);
-          split2(w.y, h[4][k], lo[4][k]);
+          split2(w.x, h[2][k], lo[2][k]);
+          split2(w.y, h[3][k], lo[3][k]);
         }
         // opA rows: split * 256 + plane * 128 + row; 16 uint4 per 256-byte row
         A[((0 * 256 + 0 * 128) + rr) * 16 + c8] = pack8(h[0]);
         A[((0 * 256 + 1 * 128) + rr) * 16 + c8] = pack8(h[1]);
         A[((1 * 256 + 0 * 128) + rr) * 16 + c8] = pack8(lo[0]);
         A[((1 * 256 + 1 * 128) + rr) * 16 + c8] = pack8(lo[1]);
-        // opB rows: split * 384 + plane * 128 + row (planes -W_i, W_r, W_i)
+        // opB rows: split * 256 + plane * 128 + row (planes W_r, W_i)
 #pragma unroll
-        for (int pl = 0; pl < 3; ++pl) {
-          B[((0 * 384 + pl * 128) + rr) * 16 + c8] = pack8(h[2 + pl]);
-          B[((1 * 384 + pl * 128) + rr) * 16 + c8] = pack8(lo[2 + pl]);
+        for (int pl = 0; pl < 2; ++pl) {
+          B[((0 * 256 + pl * 128) + rr) * 16 + c8] = pack8(h[2 + pl]);
+          B[((1 * 256 + pl * 128) + rr) * 16 + c8] = pack8(lo[2 + pl]);
         }
       }
       __syncthreads();
@@ -703,7 +711,7 @@ int tc_make_maps(void* opA, void* opB, int64_t ntiles, TcMaps* out, std::string&
   const cuuint64_t stride[1] = {(cuuint64_t)TB * 2};
   CUtensorMap ma, mb;
   const cuuint64_t dimA[2] = {(cuuint64_t)TB, (cuuint64_t)ntiles * 512};
-  const cuuint64_t dimB[2] = {(cuuint64_t)TB, (cuuint64_t)ntiles * 768};
+  const cuuint64_t dimB[2] = {(cuuint64_t)TB, (cuuint64_t)ntiles * BROWS};
   CUresult r1 = encode(&ma, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, opA, dimA, stride, box, estr,
                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
