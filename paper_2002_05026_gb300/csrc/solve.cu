@@ -1033,7 +1033,7 @@ constexpr int RES_CHUNK = 128;
 constexpr int RES_PARTS = 2;      // blocks sharing one row chunk's contributions
 
 template <int RPT>
-__global__ void __launch_bounds__(128, 8) residual_kernel(ResidualParams p) {
+__global__ void __launch_bounds__(128, 6) residual_kernel(ResidualParams p) {
   const int i = threadIdx.x % 32, w = threadIdx.x / 32;
   const int j0 = (blockIdx.y * (blockDim.x / 32) + w) * RPT;
   const int2 ch = p.chunks[blockIdx.x];
@@ -1066,13 +1066,25 @@ __global__ void __launch_bounds__(128, 8) residual_kernel(ResidualParams p) {
         float sr[RPT], cr[RPT], si[RPT], ci[RPT];
 #pragma unroll
         for (int q = 0; q < RPT; ++q) sr[q] = cr[q] = si[q] = ci[q] = 0.f;
-#pragma unroll 4
+        // the next column's K entry and x values are loaded while this column is multiplied
+        float4 an = __ldg(kb + c0 * ks), xn[RPT];
+#pragma unroll
+        for (int q = 0; q < RPT; ++q) xn[q] = (q < nj) ? __ldg(xg + (int64_t)q * p.n + c0) : make_float4(0.f, 0.f, 0.f, 0.f);
         for (int c = c0; c < c1; ++c) {
-          const float4 a = __ldg(kb + c * ks);          // (hi_r, hi_i, lo_r, lo_i)
+          const float4 a = an;                           // (hi_r, hi_i, lo_r, lo_i)
+          float4 xv[RPT];
+#pragma unroll
+          for (int q = 0; q < RPT; ++q) xv[q] = xn[q];
+          if (c + 1 < c1) {
+            an = __ldg(kb + (c + 1) * ks);
+#pragma unroll
+            for (int q = 0; q < RPT; ++q)
+              if (q < nj) xn[q] = __ldg(xg + (int64_t)q * p.n + c + 1);
+          }
 #pragma unroll
           for (int q = 0; q < RPT; ++q) {
             if (q < nj) {
-              const float4 x = __ldg(xg + (int64_t)q * p.n + c);
+              const float4 x = xv[q];
               df_mac(sr[q], cr[q], a.x, a.z, x.x, x.z);       // + a_r x_r
               df_mac(sr[q], cr[q], -a.y, -a.w, x.y, x.w);     // - a_i x_i
               df_mac(si[q], ci[q], a.x, a.z, x.y, x.w);       // + a_r x_i
