@@ -115,11 +115,11 @@ struct d3m_ctx {
   int nchunks = 0;
   unsigned* norms = nullptr;         // [3 * ninst * max_nrhs + ninst]: rmax, xmax, bmax, kmax
   double* omega_dev = nullptr;       // [ninst][max_nrhs]
-  double* stat_dev = nullptr;        // [2]: max omega, instances still refining
+  double* stat_dev = nullptr;        // [3]: max omega, instances still refining, their progress measure
   unsigned* dmax = nullptr;          // [ninst][max_nrhs] max |correction| of the step (float bits)
   float* dprev = nullptr;            // [ninst][max_nrhs] the same for the previous step
   int* sweep_status = nullptr;       // device: set by a sweep kernel whose bounded wait expired
-  double* h_stat = nullptr;          // pinned [2]
+  double* h_stat = nullptr;          // pinned [3]
   // gradients
   int32_t* rowidx = nullptr;
   int32_t* blk_col = nullptr;
@@ -613,13 +613,13 @@ static int create_impl(d3m_handle* out, const d3m_pattern* pat, const int32_t* p
   }
   ALLOC(h->norms, unsigned, 3 * (size_t)h->ninst * mr + h->ninst);
   ALLOC(h->omega_dev, double, (size_t)h->ninst * mr);
-  ALLOC(h->stat_dev, double, 2);
+  ALLOC(h->stat_dev, double, 3);
   ALLOC(h->dmax, unsigned, (size_t)h->ninst * mr);
   ALLOC(h->dprev, float, (size_t)h->ninst * mr);
   ALLOC(h->sweep_status, int, 1);
   CUDA_TRY(h, cudaMemset(h->sweep_status, 0, sizeof(int)));
   ALLOC(h->contract, double2, S.N);
-  CUDA_TRY(h, cudaMallocHost(&h->h_stat, 2 * sizeof(double)));
+  CUDA_TRY(h, cudaMallocHost(&h->h_stat, 3 * sizeof(double)));
 #undef ALLOC
 #undef UPLOAD
   return D3M_OK;
@@ -931,7 +931,7 @@ static int solve_impl(d3m_ctx* h, const void* Bin, void* Xout, int nrhs, cudaStr
     if (!resid) return D3M_OK;
     rc = residual_omega(h, X, B, nrhs, cs);
     if (rc) return rc;
-    CUDA_TRY(h, cudaMemcpyAsync(h->h_stat, h->stat_dev, 2 * sizeof(double), cudaMemcpyDeviceToHost, cs));
+    CUDA_TRY(h, cudaMemcpyAsync(h->h_stat, h->stat_dev, 3 * sizeof(double), cudaMemcpyDeviceToHost, cs));
     return D3M_OK;
   };
   auto run_step = [&](const double2* src, int acc, bool resid) -> int {
@@ -961,7 +961,7 @@ static int solve_impl(d3m_ctx* h, const void* Bin, void* Xout, int nrhs, cudaStr
       const bool all_done = h->h_stat[1] == 0.0;
       h->refine_iters = it + 1;
       if (it == 0) h->omega_first = w;
-      hist.push_back(w);
+      hist.push_back(h->h_stat[2]);   // progress of the instances still open
       if (w < best) {
         best = w;
         if (w > h->opt.refine_tol)

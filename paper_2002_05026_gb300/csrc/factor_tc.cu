@@ -195,6 +195,273 @@ __device__ __forceinline__ void load_s_in(const TileTask& T, const double2* K, f
   }
 }
 
+
+// ---------------------------------------------------------------- diagonal tile: blocked LDL^T
+// The diagonal tile S (128 x 128, complex symmetric, lower triangle in sS) is factored as
+// S = L D L^T (unpivoted) and L is inverted, X = L^{-1}, in four panels of DW = 32 columns
+// (right-looking on both).  Storage: sS holds L strictly below the diagonal and X transposed
+// strictly above it (sS[c][r] = X[r][c]); d goes to s_d.  With block indices r, s, j and the
+// current panel k:
+//   diagonal block:  A_kk = L_kk D_k L_kk^T, X_kk = L_kk^{-1}           (two warps, registers)
+//   panel below:     W_rk = A_rk X_kk^T (= L_rk D_k), L_rk = W_rk D_k^{-1}
+//   trailing:        A_rs -= L_rk W_sk^T                                (r >= s > k)
+//   inverse:         Z_rj += L_rk X_kj (r > k, j <= k);  X_rj = -X_rr Z_rj once X_rr exists
+// (X_rj = -X_rr sum_{k=j}^{r-1} L_rk X_kj is the block form of L X = I).  Z_rj lives where X_rj
+// ends up, in the upper triangle, which starts at zero.  The diagonal block of panel k + 1 is
+// updated first, so that two warps factor it while the other six finish panel k's updates.
+constexpr int DW = 32;          // panel width
+constexpr int WT_LD = 96;       // row length of the W panel scratch (c-major: Wt[c][row - c1])
+
+// The DW x DW diagonal block at (c0, c0), two warps: warp 0 factors it (lane i = row i), warp 1
+// inverts L (lane j = column j of X) one phase of 8 columns behind, the two meeting at named
+// barrier 1 after every phase.  Registers are shifted as the elimination advances (slot m holds
+// column / row j + m at step j) so that all register indices are static and the loops stay
+// rolled (straight-line code of this size would run out of the instruction cache).
+template <int NM>
+__device__ __forceinline__ void ldlt_phase(float2 (&a)[DW], int j0, float2* sS, float2* s_d, int c0, int lane) {
+#pragma unroll 1
+  for (int j = j0; j < j0 + 8; ++j) {
+    // d_j = a_j[j]; l_i = a_i[j] / d_j; a_i[m] -= l_i a_m[j] for m > j.  Lanes m > j are the only
+    // sources of a_m[j], so the unused entries above a lane's diagonal never reach a result.
+    const float2 cj = a[0];
+    float2 dj;
+    dj.x = __shfl_sync(0xffffffffu, cj.x, j);
+    dj.y = __shfl_sync(0xffffffffu, cj.y, j);
+    const float2 l = cdiv(cj, dj);
+#pragma unroll
+    for (int m = 1; m < NM; ++m) {
+      float2 cm;
+      cm.x = __shfl_sync(0xffffffffu, cj.x, (j + m) & 31);
+      cm.y = __shfl_sync(0xffffffffu, cj.y, (j + m) & 31);
+      a[m - 1] = cfms(l, cm, a[m]);
+    }
+    a[NM - 1] = make_float2(0.f, 0.f);
+    if (lane > j) sS[(c0 + lane) * LDS + c0 + j] = l;
+    if (lane == j) s_d[c0 + j] = dj;
+  }
+}
+
+template <int NM>
+__device__ __forceinline__ void linv_phase(float2 (&x)[DW], int q0, float2* sS, int c0, int lane) {
+#pragma unroll 1
+  for (int q = q0; q < q0 + 8; ++q) {
+    // x holds rows q.. of column `lane` of X: X[q][lane] is final; X[m][lane] -= L[m][q] X[q][lane]
+    const float2 xq = x[0];
+    if (q > lane) sS[(c0 + lane) * LDS + c0 + q] = xq;      // X[q][lane] at sS[c0 + lane][c0 + q]
+#pragma unroll
+    for (int m = 1; m < NM; ++m) {
+      const int row = min(q + m, DW - 1);                    // rows past the block feed unused slots
+      x[m - 1] = cfms(sS[(c0 + row) * LDS + c0 + q], xq, x[m]);
+    }
+    x[NM - 1] = make_float2(0.f, 0.f);
+  }
+}
+
+__device__ __forceinline__ void diag_block_2warps(float2* sS, float2* s_d, int c0, int warp, int lane) {
+  float2 v[DW];
+  if (warp == 0) {
+#pragma unroll
+    for (int m = 0; m < DW; ++m) v[m] = (m <= lane) ? sS[(c0 + lane) * LDS + c0 + m] : make_float2(0.f, 0.f);
+    ldlt_phase<32>(v, 0, sS, s_d, c0, lane);
+    asm volatile("bar.sync 1, 64;" ::: "memory");
+    ldlt_phase<24>(v, 8, sS, s_d, c0, lane);
+    asm volatile("bar.sync 1, 64;" ::: "memory");
+    ldlt_phase<16>(v, 16, sS, s_d, c0, lane);
+    asm volatile("bar.sync 1, 64;" ::: "memory");
+    ldlt_phase<8>(v, 24, sS, s_d, c0, lane);
+    asm volatile("bar.sync 1, 64;" ::: "memory");
+  } else {
+#pragma unroll
+    for (int m = 0; m < DW; ++m) v[m] = make_float2(m == lane ? 1.f : 0.f, 0.f);
+    asm volatile("bar.sync 1, 64;" ::: "memory");
+    linv_phase<32>(v, 0, sS, c0, lane);
+    asm volatile("bar.sync 1, 64;" ::: "memory");
+    linv_phase<24>(v, 8, sS, c0, lane);
+    asm volatile("bar.sync 1, 64;" ::: "memory");
+    linv_phase<16>(v, 16, sS, c0, lane);
+    asm volatile("bar.sync 1, 64;" ::: "memory");
+    linv_phase<8>(v, 24, sS, c0, lane);
+  }
+}
+
+// X_kk[c][q] of the current diagonal block (unit lower triangular)
+__device__ __forceinline__ float2 xkk(const float2* sS, int c0, int c, int q) {
+  return q < c ? sS[(c0 + q) * LDS + c0 + c] : make_float2(q == c ? 1.f : 0.f, 0.f);
+}
+
+// All threads: W_rk, L_rk for the rows below panel k (k < 3) and X_kj = -X_kk Z_kj (j < k).
+__device__ __forceinline__ void diag_panel_solve(float2* sS, const float2* s_d, float2* Wt, int k, int tid) {
+  const int c0 = DW * k, c1 = c0 + DW, nrb = 3 - k;
+  // W: thread -> columns cg + 8 jj, rows c1 + rg + 32 ii
+  const int cg = tid & 7, rg = tid >> 3;
+  float2 w[3][4];
+#pragma unroll
+  for (int ii = 0; ii < 3; ++ii)
+#pragma unroll
+    for (int jj = 0; jj < 4; ++jj) w[ii][jj] = make_float2(0.f, 0.f);
+  if (nrb > 0) {
+#pragma unroll 4
+    for (int q = 0; q < DW; ++q) {
+      float2 xq[4], aq[3];
+#pragma unroll
+      for (int jj = 0; jj < 4; ++jj) xq[jj] = xkk(sS, c0, cg + 8 * jj, q);
+#pragma unroll
+      for (int ii = 0; ii < 3; ++ii) aq[ii] = ii < nrb ? sS[(c1 + rg + 32 * ii) * LDS + c0 + q] : make_float2(0.f, 0.f);
+#pragma unroll
+      for (int ii = 0; ii < 3; ++ii)
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) w[ii][jj] = cfma(aq[ii], xq[jj], w[ii][jj]);
+    }
+  }
+  // X_kj: thread -> rows a = (tid >> 5) + 8 i, column b = tid & 31
+  const int b = tid & 31, ar = tid >> 5;
+  float2 xo[3][4];
+#pragma unroll
+  for (int j = 0; j < 3; ++j)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) xo[j][i] = make_float2(0.f, 0.f);
+  if (k > 0) {
+#pragma unroll 4
+    for (int q = 0; q < DW; ++q) {
+      float2 xa[4], z[3];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) xa[i] = xkk(sS, c0, ar + 8 * i, q);
+#pragma unroll
+      for (int j = 0; j < 3; ++j) z[j] = j < k ? sS[(DW * j + b) * LDS + c0 + q] : make_float2(0.f, 0.f);
+#pragma unroll
+      for (int j = 0; j < 3; ++j)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) xo[j][i] = cfma(xa[i], z[j], xo[j][i]);
+    }
+  }
+  __syncthreads();   // every A_rk and Z_kj has been read
+  if (nrb > 0) {
+#pragma unroll
+    for (int jj = 0; jj < 4; ++jj) {
+      const int c = cg + 8 * jj;
+      const float2 dinv = cdiv(make_float2(1.f, 0.f), s_d[c0 + c]);
+#pragma unroll
+      for (int ii = 0; ii < 3; ++ii)
+        if (ii < nrb) {
+          sS[(c1 + rg + 32 * ii) * LDS + c0 + c] = cmul(w[ii][jj], dinv);
+          Wt[c * WT_LD + rg + 32 * ii] = w[ii][jj];
+        }
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < 3; ++j)
+    if (j < k)
+#pragma unroll
+      for (int i = 0; i < 4; ++i) sS[(DW * j + b) * LDS + c0 + ar + 8 * i] = make_float2(-xo[j][i].x, -xo[j][i].y);
+  __syncthreads();
+}
+
+// All threads: A_{k+1,k+1} -= L_{k+1,k} W_{k+1,k}^T (lower triangle).
+__device__ __forceinline__ void diag_next_block(float2* sS, const float2* Wt, int k, int tid) {
+  const int c0 = DW * k, c1 = c0 + DW;
+  const int b = tid & 31, ar = tid >> 5;
+  float2 acc[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) acc[i] = make_float2(0.f, 0.f);
+#pragma unroll 4
+  for (int c = 0; c < DW; ++c) {
+    const float2 wv = Wt[c * WT_LD + b];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) acc[i] = cfma(sS[(c1 + ar + 8 * i) * LDS + c0 + c], wv, acc[i]);
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int a = ar + 8 * i;
+    if (b <= a) {
+      float2* o = sS + (c1 + a) * LDS + c1 + b;
+      *o = csub(*o, acc[i]);
+    }
+  }
+}
+
+// Warps 2..7 (t = thread index among them): the rest of panel k's updates as 32 x 32 block jobs --
+// trailing blocks (r, s), k < s <= r, other than (k+1, k+1), then Z blocks (r, j), r > k, j <= k.
+// A job is four chunks of 32 threads; each thread owns rows aa, aa + 16 and columns bb + 8 q.
+__device__ __forceinline__ void diag_panel_update(float2* sS, const float2* Wt, int k, int t) {
+  const int c0 = DW * k, c1 = c0 + DW;
+  const int nT = (3 - k) * (4 - k) / 2 - 1, nZ = (3 - k) * (k + 1);
+  const int nchunks = 4 * (nT + nZ);
+  const int wi = t >> 5, lane = t & 31;
+#pragma unroll 1
+  for (int ch = wi; ch < nchunks; ch += 6) {
+    const int job = ch >> 2;
+    const int aa = (ch & 3) * 4 + (lane >> 3), bb = lane & 7;
+    int rb, sb = 0, j = 0;
+    const bool trailing = job < nT;
+    if (trailing) {
+      int e = job + 1;            // skip (k+1, k+1), the first pair in this order
+      sb = k + 1;
+      rb = k + 1;
+      while (e > 0) {
+        if (++rb > 3) { ++sb; rb = sb; }
+        --e;
+      }
+    } else {
+      const int e = job - nT;
+      rb = k + 1 + e / (k + 1);
+      j = e % (k + 1);
+    }
+    const float2* P0 = sS + (DW * rb + aa) * LDS + c0;
+    const float2* P1 = P0 + 16 * LDS;
+    float2 acc[2][4];
+#pragma unroll
+    for (int ii = 0; ii < 2; ++ii)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[ii][q] = make_float2(0.f, 0.f);
+    if (trailing) {
+      const float2* Q = Wt + DW * sb - c1 + bb;
+#pragma unroll 4
+      for (int c = 0; c < DW; ++c) {
+        const float2 p0 = P0[c], p1 = P1[c];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const float2 qv = Q[c * WT_LD + 8 * q];
+          acc[0][q] = cfma(p0, qv, acc[0][q]);
+          acc[1][q] = cfma(p1, qv, acc[1][q]);
+        }
+      }
+#pragma unroll
+      for (int ii = 0; ii < 2; ++ii)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int a = aa + 16 * ii, b = bb + 8 * q;
+          if (rb != sb || b <= a) {
+            float2* o = sS + (DW * rb + a) * LDS + DW * sb + b;
+            *o = csub(*o, acc[ii][q]);
+          }
+        }
+    } else {
+      // Q[c][b] = X_kj[c][b] at sS[(32 j + b) * LDS + c0 + c]; for j = k only b < c is stored
+      const float2* Q = sS + (DW * j + bb) * LDS + c0;
+      const bool tri = (j == k);
+#pragma unroll 4
+      for (int c = 0; c < DW; ++c) {
+        const float2 p0 = P0[c], p1 = P1[c];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int b = bb + 8 * q;
+          float2 qv = Q[8 * q * LDS + c];
+          if (tri) qv = b < c ? qv : make_float2(b == c ? 1.f : 0.f, 0.f);
+          acc[0][q] = cfma(p0, qv, acc[0][q]);
+          acc[1][q] = cfma(p1, qv, acc[1][q]);
+        }
+      }
+#pragma unroll
+      for (int ii = 0; ii < 2; ++ii)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          float2* o = sS + (DW * j + bb + 8 * q) * LDS + DW * rb + aa + 16 * ii;
+          *o = make_float2(o->x + acc[ii][q].x, o->y + acc[ii][q].y);
+        }
+    }
+  }
+}
+
 }  // namespace
 
 __global__ void __launch_bounds__(NTHR, 1)
@@ -384,94 +651,25 @@ __global__ void __launch_bounds__(NTHR, 1)
       for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
       if (lane == 0) s_red[warp] = mx;
       __syncthreads();
-      // Unpivoted LDL^T fused with the inverse of L, right-looking on both, two columns per step.
-      // Storage: S (Schur complement, then L) below the diagonal; X = L^{-1} transposed above it
-      // (Xt[s][r] = X[r][s]).  Step (c, c+1), with a_s = column c and b_s = column c+1 of sS:
-      //   d_c, l_s(c) = a_s / d_c;  l' = l_{c+1}(c);  d_{c+1} = S[c+1][c+1] - l' S[c+1][c];
-      //   v'_s = b_s - l_s(c) S[c+1][c];  l_s(c+1) = v'_s / d_{c+1};
-      //   u0_s = X[c][s] (s < c), 1 (s = c), 0 (s = c+1), S[s][c] (s > c+1);
-      //   u1_s = X[c+1][s] - l' X[c][s] (s < c), -l' (s = c), 1 (s = c+1), v'_s (s > c+1);
-      //   every (r > c+1, s <= r): entry -= l_r(c) u0_s + l_r(c+1) u1_s  (S below, Xt above);
-      //   column c / c+1 of L and row c+1 of X are written back in the same phase.
-      // Thread (tr, tc) of a 16 x 16 grid owns rows r = tr (mod 16) and columns s = tc (mod 16).
+      // Unpivoted LDL^T and X = L^{-1}, blocked in panels of DW columns (the diag_* functions)
       {
-        // the upper triangle starts at zero (X = I below the diagonal)
+        // the upper triangle starts at zero (it accumulates the blocks of X)
         for (int i = tid; i < TB * TB; i += NTHR) {
           const int rr = i >> 7, cc = i & 127;
           if (cc > rr) sS[rr * LDS + cc] = make_float2(0.f, 0.f);
         }
+        float2* Wt = s_d + TB;
         __syncthreads();
-        const int tr = tid >> 4, tcol = tid & 15;
-        float2* s_l0 = s_d + TB;              // l_s(c)
-        float2* s_u0 = s_d + 2 * TB;          // u0_s
-        float2* s_l1 = s_d + 3 * TB;          // l_s(c+1)
-        float2* s_u1 = s_d + 4 * TB;          // u1_s
-        for (int c = 0; c < TB; c += 2) {
-          if (tid < TB) {
-            const int sI = tid;
-            const float2 dc = sS[c * LDS + c];
-            const float2 v1 = sS[(c + 1) * LDS + c];
-            const float2 l1c = cdiv(v1, dc);
-            const float2 d1 = csub(sS[(c + 1) * LDS + c + 1], cmul(l1c, v1));
-            const float2 a = sS[sI * LDS + c];
-            const float2 bb = sS[sI * LDS + c + 1];
-            const float2 l0 = (sI > c) ? cdiv(a, dc) : make_float2(0.f, 0.f);
-            const float2 vp = csub(bb, cmul(l0, v1));
-            const float2 l1 = (sI > c + 1) ? cdiv(vp, d1) : make_float2(0.f, 0.f);
-            float2 u0, u1;
-            if (sI < c) {
-              u0 = a;
-              u1 = csub(bb, cmul(l1c, a));
-            } else if (sI == c) {
-              u0 = make_float2(1.f, 0.f);
-              u1 = make_float2(-l1c.x, -l1c.y);
-            } else if (sI == c + 1) {
-              u0 = make_float2(0.f, 0.f);
-              u1 = make_float2(1.f, 0.f);
-            } else {
-              u0 = a;
-              u1 = vp;
-            }
-            s_l0[sI] = l0;
-            s_u0[sI] = u0;
-            s_l1[sI] = l1;
-            s_u1[sI] = u1;
-            if (sI == 0) {
-              s_d[c] = dc;
-              s_d[c + 1] = d1;
-            }
-          }
+        if (warp < 2) diag_block_2warps(sS, s_d, 0, warp, lane);
+        __syncthreads();
+#pragma unroll 1
+        for (int k = 0; k < TB / DW; ++k) {
+          diag_panel_solve(sS, s_d, Wt, k, tid);
+          if (k == TB / DW - 1) break;
+          diag_next_block(sS, Wt, k, tid);
           __syncthreads();
-          float2 la[8], lb[8], ua[8], ub[8];
-#pragma unroll
-          for (int a = 0; a < 8; ++a) {
-            la[a] = s_l0[tr + 16 * a];
-            lb[a] = s_l1[tr + 16 * a];
-            ua[a] = s_u0[tcol + 16 * a];
-            ub[a] = s_u1[tcol + 16 * a];
-          }
-#pragma unroll
-          for (int a = 0; a < 8; ++a) {
-            const int rr = tr + 16 * a;
-            if (rr <= c + 1) continue;
-            float2 v[8];
-            int off[8];
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {          // all loads of the row first
-              const int ss = tcol + 16 * q;
-              off[q] = (ss > c + 1) ? rr * LDS + ss : ss * LDS + rr;
-              if (ss <= rr) v[q] = sS[off[q]];
-            }
-#pragma unroll
-            for (int q = 0; q < 8; ++q)
-              if (tcol + 16 * q <= rr) sS[off[q]] = cfms(lb[a], ub[q], cfms(la[a], ua[q], v[q]));
-          }
-          if (tid < TB) {                          // write back L columns c, c+1 and X row c+1
-            const int sI = tid;
-            if (sI > c) sS[sI * LDS + c] = s_l0[sI];
-            if (sI > c + 1) sS[sI * LDS + c + 1] = s_l1[sI];
-            if (sI <= c) sS[sI * LDS + c + 1] = s_u1[sI];
-          }
+          if (warp < 2) diag_block_2warps(sS, s_d, DW * (k + 1), warp, lane);
+          else diag_panel_update(sS, Wt, k, tid - 64);
           __syncthreads();
         }
         // L_JJ (unit lower) and D_J

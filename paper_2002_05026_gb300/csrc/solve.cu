@@ -1216,10 +1216,10 @@ __global__ void vec_absmax_kernel(const double2* __restrict__ V, int64_t n, int 
 __global__ void omega_kernel(const unsigned* rmax, const unsigned* xmax, const unsigned* bmax,
                              const unsigned* kmax, const unsigned* dmax, float* dprev, int ninst, int ld,
                              int nrhs, int* done, double tol, double ftol, double* omega, double* stat) {
-  double w = 0.0;
+  double w = 0.0, mu = 0.0;   // mu: how far the open instances are from both targets
   int open = 0;
   for (int i = threadIdx.x; i < ninst; i += blockDim.x) {
-    double wi = 0.0;
+    double wi = 0.0, mui = 0.0;
     if (!done[i]) {
       const double kn = (double)__uint_as_float(kmax[i]);
       bool ok = true;
@@ -1235,23 +1235,29 @@ __global__ void omega_kernel(const unsigned* rmax, const unsigned* xmax, const u
         const double rho = dp > 0 ? d / dp : 1.0;
         const bool fwd = ftol <= 0 || ratio <= ftol || (rho < 1.0 && rho / (1.0 - rho) * ratio <= ftol);
         ok = ok && o <= tol && fwd;
+        mui = fmax(mui, fmax(o / tol, ftol > 0 ? ratio / ftol : 0.0));
         dprev[q] = (float)d;
       }
       if (ok) done[i] = 1;
-      else ++open;
+      else {
+        ++open;
+        mu = fmax(mu, mui);
+      }
     } else {
       for (int j = 0; j < nrhs; ++j) wi = fmax(wi, omega[i * ld + j]);
     }
     w = fmax(w, wi);
   }
-  __shared__ double s_w[256];
+  __shared__ double s_w[256], s_mu[256];
   __shared__ int s_o[256];
   s_w[threadIdx.x] = w;
+  s_mu[threadIdx.x] = mu;
   s_o[threadIdx.x] = open;
   __syncthreads();
   for (int h = blockDim.x / 2; h > 0; h >>= 1) {
     if (threadIdx.x < h) {
       s_w[threadIdx.x] = fmax(s_w[threadIdx.x], s_w[threadIdx.x + h]);
+      s_mu[threadIdx.x] = fmax(s_mu[threadIdx.x], s_mu[threadIdx.x + h]);
       s_o[threadIdx.x] += s_o[threadIdx.x + h];
     }
     __syncthreads();
@@ -1259,6 +1265,7 @@ __global__ void omega_kernel(const unsigned* rmax, const unsigned* xmax, const u
   if (threadIdx.x == 0) {
     stat[0] = s_w[0];
     stat[1] = (double)s_o[0];
+    stat[2] = s_mu[0];
   }
 }
 
