@@ -132,6 +132,13 @@ constexpr int RCMAX = 8;
 __host__ __device__ constexpr int vec_ld(int rc) { return rc | 1; }
 
 template <typename C>
+__device__ __forceinline__ C shfl_xor_c(C v, int o) {
+  v.x = __shfl_xor_sync(0xffffffffu, v.x, o);
+  v.y = __shfl_xor_sync(0xffffffffu, v.y, o);
+  return v;
+}
+
+template <typename C>
 __device__ __forceinline__ void quad_reduce(C* acc) {
 #pragma unroll
   for (int j = 0; j < RCMAX; ++j)
@@ -274,109 +281,219 @@ __device__ __forceinline__ void stage_item(C* sT, C* sV, int ldv, const C* half,
         : "memory");
 }
 
+// Persistent gather: CTA c takes units u = c, c + grid, ... of the level (unit = one group's products
+// for one 64-row half of its tiles, units of finished instances skipped); the tile halves and source
+// rows of the next nstg - 1 items are in flight while one is multiplied.  Warp 0 issues the copies;
+// it fetches the next unit's group and item at the top of an iteration (the loads overlap the
+// products) and leaves each staged item's output slot in a small shared ring for the consumers.
+constexpr int GMAXSTG = 4;
+constexpr int GGT = 512;   // threads of a gather block (16 warps)
+
+struct GatherMeta {
+  int slot, h, end, more;   // partial slot, half, last item of its unit, another item follows
+};
+
 template <typename R, bool FWD>
-__global__ void __launch_bounds__(GT) gather_kernel(const SolveGroup* __restrict__ groups,
-                                                    const SolveItem* __restrict__ items,
-                                                    const typename CT<R>::C* __restrict__ L,
-                                                    const typename CT<R>::C* __restrict__ Y,
-                                                    typename CT<R>::C* __restrict__ P,
-                                                    int64_t npad, int b, int nrhs, int* status, Mask mk) {
+__global__ void __launch_bounds__(GGT, 1) gather_kernel(const SolveGroup* __restrict__ groups,
+                                                        const SolveItem* __restrict__ items,
+                                                        const typename CT<R>::C* __restrict__ L,
+                                                        const typename CT<R>::C* __restrict__ Y,
+                                                        typename CT<R>::C* __restrict__ P, int64_t npad, int b,
+                                                        int nrhs, int* status, Mask mk, int nunits, int nstg) {
   using C = typename CT<R>::C;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int nh = b / HR;
-  if (mk.off(groups[blockIdx.x / nh].dst)) return;
   const int vlen = FWD ? b : HR;                         // source rows per right-hand side
   const int ldv = vlen + (int)(16 / sizeof(C));
   const int stg = HR * b + RCMAX * ldv;                  // elements of one stage buffer
-  C* buf[2] = {reinterpret_cast<C*>(smem_raw), reinterpret_cast<C*>(smem_raw) + stg};
-  __shared__ __align__(8) uint64_t bars[2];
-  const SolveGroup gr = groups[blockIdx.x / nh];
-  const int h = blockIdx.x % nh;
+  C* const sbase = reinterpret_cast<C*>(smem_raw);
+  __shared__ __align__(8) uint64_t bars[GMAXSTG];
+  __shared__ GatherMeta s_meta[GMAXSTG];
   const int j0 = blockIdx.y * RCMAX;
   const int rc = min(RCMAX, nrhs - j0);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  auto skip = [&](int u) {                               // first active unit >= u (whole warps)
+    if (!mk.done) return u;
+    while (u < nunits) {
+      const int cand = u + lane * (int)gridDim.x;        // 32 candidates per step
+      const bool act = cand < nunits && !mk.off(groups[cand / nh].dst);
+      const unsigned bal = __ballot_sync(0xffffffffu, act);
+      if (bal) return u + (__ffs(bal) - 1) * (int)gridDim.x;
+      u += 32 * (int)gridDim.x;
+    }
+    return u;
+  };
+  int pu = skip(blockIdx.x), pk = 0;                     // next unit / item to issue (warp 0)
+  if (pu >= nunits) return;                              // uniform: nothing to do for this block
   if (threadIdx.x == 0) {
-    mbar_init_s(&bars[0]);
-    mbar_init_s(&bars[1]);
+    for (int i = 0; i < nstg; ++i) mbar_init_s(&bars[i]);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
+  // source rows past rc stay zero in every stage (the products run over all RCMAX rows)
+  for (int i = threadIdx.x; i < nstg * (RCMAX - rc) * ldv; i += GGT) {
+    const int st = i / ((RCMAX - rc) * ldv), e = i % ((RCMAX - rc) * ldv);
+    sbase[(int64_t)st * stg + HR * b + rc * ldv + e] = CT<R>::make(0, 0);
+  }
   __syncthreads();
-  auto stage = [&](int k) {
-    const SolveItem it = items[gr.first + k];
-    const int64_t y0 = (int64_t)it.src * b + (FWD ? 0 : h * HR);
-    C* T = buf[k & 1];
-    stage_item(T, T + HR * b, ldv, L + (int64_t)it.tile * b * b + (int64_t)h * HR * b, Y, npad, y0, vlen, j0, rc, b,
-               &bars[k & 1]);
-  };
-  stage(0);
-  // backward: thread = (output column c, row group); b / 64 ... 256 / b row groups of 64 * b / 256 rows
-  const int ngrp = GT / b, rows_g = HR / ngrp;
-  const int bc = threadIdx.x % b, bg = threadIdx.x / b;
-  C acc[RCMAX];
-#pragma unroll
-  for (int j = 0; j < RCMAX; ++j) acc[j] = CT<R>::make(0, 0);
-  uint32_t phase[2] = {0u, 0u};
-  const uint64_t deadline = globaltimer_ns() + SWEEP_TIMEOUT_NS;
-  for (int k = 0; k < gr.count; ++k) {
-    if (k + 1 < gr.count) {
-      // the other buffer was last read in item k-1, which ended with a barrier
-      if (threadIdx.x < 32) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      stage(k + 1);
+  SolveGroup pg{};
+  SolveItem pit{};
+  auto fetch = [&]() {                                   // warp 0: group and item of (pu, pk)
+    if (pu < nunits) {
+      pg = groups[pu / nh];
+      pit = items[pg.first + pk];
     }
-    const bool late = !mbar_wait_s(&bars[k & 1], phase[k & 1], deadline);
-    phase[k & 1] ^= 1u;
+  };
+  auto issue = [&](int slot) {                           // warp 0: (pu, pk) into `slot`, then advance
+    const int h = pu % nh;
+    const int64_t y0 = (int64_t)pit.src * b + (FWD ? 0 : h * HR);
+    C* T = sbase + (int64_t)slot * stg;
+    stage_item(T, T + HR * b, ldv, L + (int64_t)pit.tile * b * b + (int64_t)h * HR * b, Y, npad, y0, vlen, j0, rc, b,
+               &bars[slot]);
+    const bool end = (pk + 1 == pg.count);
+    if (end) {
+      pk = 0;
+      pu = skip(pu + gridDim.x);
+    } else {
+      ++pk;
+    }
+    if (lane == 0) s_meta[slot] = GatherMeta{pg.slot, h, end ? 1 : 0, pu < nunits ? 1 : 0};
+  };
+  int inflight = 0;                                      // items issued, not yet consumed (warp 0)
+  if (warp == 0) {
+    for (int i = 0; i < nstg && pu < nunits; ++i, ++inflight) {
+      fetch();
+      issue(i);
+    }
+  }
+  __syncthreads();                                       // s_meta of the first stages
+  // forward: warp w, lane l -> rows rg + 32 i (rg = 2 w + l / 16, i < 2), columns l % 16 + 16 k, all
+  //   right-hand sides; the 16 column groups of a row are summed by a shuffle reduce-scatter
+  // backward: warp w -> rows 8 (w % 8) .. + 7 of the half and column half w / 8, lane l -> columns
+  //   l + 32 k of that half; the 8 row groups are summed through shared memory in a fixed order
+  constexpr int NA = 2;                                  // rows (forward) / column slots (backward) per thread
+  C acc[NA][RCMAX];
+#pragma unroll
+  for (int a = 0; a < NA; ++a)
+#pragma unroll
+    for (int j = 0; j < RCMAX; ++j) acc[a][j] = CT<R>::make(0, 0);
+  const uint64_t deadline = globaltimer_ns() + SWEEP_TIMEOUT_NS;
+  for (int it = 0;; ++it) {
+    const int slot = it % nstg;
+    const bool late = !mbar_wait_s(&bars[slot], (uint32_t)((it / nstg) & 1), deadline);
     if (__syncthreads_or(late)) {
-      if (threadIdx.x == 0) atomicExch(status, (int)D3M_ERR_TIMEOUT);
+      if (threadIdx.x == 0) {
+        atomicExch(status, (int)D3M_ERR_TIMEOUT);
+        // let the copies still in flight land before the block's shared memory is released
+        for (int i = it; i < it + inflight; ++i)
+          mbar_wait_s(&bars[i % nstg], (uint32_t)((i / nstg) & 1), globaltimer_ns() + SWEEP_TIMEOUT_NS);
+      }
+      __syncthreads();
       return;
     }
-    const C* M = buf[k & 1];
+    const GatherMeta mt = s_meta[slot];
+    --inflight;
+    if (warp == 0) fetch();                              // loads overlap the products below
+    const C* M = sbase + (int64_t)slot * stg;
     const C* V = M + HR * b;
     if (FWD) {
-      const int r = warp * 8 + (lane >> 2), cq = lane & 3, rot = 4 * (lane >> 2);
-#pragma unroll 4
-      for (int i = 0; i < b / 4; ++i) {
-        const int c = (4 * i + cq + rot) & (b - 1);
-        const C m = M[r * b + c];
+      const int rg = 2 * warp + (lane >> 4), cg = lane & 15;
+#pragma unroll 2
+      for (int c = cg; c < b; c += 16) {
+        C v[RCMAX];
 #pragma unroll
-        for (int j = 0; j < RCMAX; ++j)
-          if (j < rc) acc[j] = cfma(m, V[j * ldv + c], acc[j]);
+        for (int j = 0; j < RCMAX; ++j) v[j] = V[j * ldv + c];
+#pragma unroll
+        for (int a = 0; a < NA; ++a) {
+          const C m = M[(rg + 32 * a) * b + c];
+#pragma unroll
+          for (int j = 0; j < RCMAX; ++j) acc[a][j] = cfma(m, v[j], acc[a][j]);
+        }
       }
     } else {
-#pragma unroll 4
-      for (int rr = 0; rr < rows_g; ++rr) {
-        const int r = bg * rows_g + rr;
-        const C m = M[r * b + bc];
+      const int rg8 = warp & 7, chalf = (warp >> 3) * (b / 2);
+#pragma unroll 2
+      for (int r = 8 * rg8; r < 8 * rg8 + 8; ++r) {
+        C v[RCMAX];
 #pragma unroll
-        for (int j = 0; j < RCMAX; ++j)
-          if (j < rc) acc[j] = cfma(m, V[j * ldv + r], acc[j]);
+        for (int j = 0; j < RCMAX; ++j) v[j] = V[j * ldv + r];
+#pragma unroll
+        for (int a = 0; a < NA; ++a) {
+          if (lane + 32 * a < b / 2) {
+            const C m = M[r * b + chalf + lane + 32 * a];
+#pragma unroll
+            for (int j = 0; j < RCMAX; ++j) acc[a][j] = cfma(m, v[j], acc[a][j]);
+          }
+        }
       }
     }
-    __syncthreads();
-  }
-  if (FWD) {
-    quad_reduce(acc);
-    if ((lane & 3) == 0) {
-      const int r = warp * 8 + (lane >> 2);
-      C* out = P + (int64_t)gr.slot * nh * b * nrhs + (int64_t)(h * HR + r) * nrhs + j0;
+    __syncthreads();                                     // the slot is consumed
+    if (FWD) {
+      if (warp == 0 && pu < nunits) {
+        if (lane == 0) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncwarp();
+        issue(slot);
+        ++inflight;
+      }
+      if (mt.end) {
+        // reduce-scatter over the 16 lanes of a row group: value q = a * 8 + j; after the stage
+        // with offset o a lane keeps the half selected by its bit o, so lane cg ends with q = cg
+        C* f = &acc[0][0];
 #pragma unroll
-      for (int j = 0; j < RCMAX; ++j)
-        if (j < rc) out[j] = acc[j];
-    }
-  } else {
-    // sum the row groups of every column in a fixed order (reusing stage buffer 0)
-    C* red = buf[0];                                    // [ngrp][b][RCMAX]
+        for (int o = 8, n = 16; o >= 1; o >>= 1, n >>= 1) {
+          const bool up = (lane & o) != 0;
 #pragma unroll
-    for (int j = 0; j < RCMAX; ++j) red[(bg * b + bc) * RCMAX + j] = acc[j];
-    __syncthreads();
-    if (bg == 0) {
-      C* out = P + ((int64_t)gr.slot * nh + h) * b * nrhs + (int64_t)bc * nrhs + j0;
+          for (int q = 0; q < n / 2; ++q) {
+            const C lo = f[q], hi = f[q + n / 2];
+            const C send = up ? lo : hi;
+            C keep = up ? hi : lo;
+            keep = cadd(keep, shfl_xor_c(send, o));
+            f[q] = keep;
+          }
+        }
+        const int rg = 2 * warp + (lane >> 4), cg = lane & 15;
+        const int a = cg >> 3, j = cg & 7;
+        if (j < rc)
+          P[(int64_t)mt.slot * nh * b * nrhs + (int64_t)(mt.h * HR + rg + 32 * a) * nrhs + j0 + j] = f[0];
 #pragma unroll
-      for (int j = 0; j < RCMAX; ++j) {
-        C v = red[bc * RCMAX + j];
-        for (int g = 1; g < ngrp; ++g) v = cadd(v, red[(g * b + bc) * RCMAX + j]);
-        if (j < rc) out[j] = v;
+        for (int a2 = 0; a2 < NA; ++a2)
+#pragma unroll
+          for (int j2 = 0; j2 < RCMAX; ++j2) acc[a2][j2] = CT<R>::make(0, 0);
+      }
+    } else {
+      if (mt.end) {
+        // sum the 8 row groups of every (column, rhs) in a fixed order, in the consumed slot
+        C* red = sbase + (int64_t)slot * stg;            // [8][b][RCMAX], within the tile part
+        const int rg8 = warp & 7, chalf = (warp >> 3) * (b / 2);
+#pragma unroll
+        for (int a = 0; a < NA; ++a) {
+          const int c = chalf + lane + 32 * a;
+          if (lane + 32 * a < b / 2)
+#pragma unroll
+            for (int j = 0; j < RCMAX; ++j) red[(rg8 * b + c) * RCMAX + j] = acc[a][j];
+        }
+        __syncthreads();
+        C* out = P + ((int64_t)mt.slot * nh + mt.h) * b * nrhs + j0;
+        for (int o = threadIdx.x; o < b * RCMAX; o += GGT) {
+          const int c = o / RCMAX, j = o % RCMAX;
+          C v = red[c * RCMAX + j];
+#pragma unroll
+          for (int w = 1; w < 8; ++w) v = cadd(v, red[(w * b + c) * RCMAX + j]);
+          if (j < rc) out[(int64_t)c * nrhs + j] = v;
+        }
+#pragma unroll
+        for (int a = 0; a < NA; ++a)
+#pragma unroll
+          for (int j = 0; j < RCMAX; ++j) acc[a][j] = CT<R>::make(0, 0);
+        __syncthreads();                                 // the slot is free again
+      }
+      if (warp == 0 && pu < nunits) {
+        if (lane == 0) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncwarp();
+        issue(slot);
+        ++inflight;
       }
     }
+    if (!mt.more) break;
   }
 }
 
@@ -1332,13 +1449,31 @@ static int sweep_impl(SweepLaunch& a, cudaStream_t st) {
   const Mask mk{a.done, a.tinst};
   permute_in_kernel<R><<<(unsigned)gblocks, nthreads, 0, st>>>(a.src, a.n, Y, a.npad, a.pad2orig, a.nrhs, mk, b);
   ++a.launches;
-  // gather: one stage buffer of a dense 64-row tile half and <= 8 source rows (padded by 16
-  // bytes), two when a block sums several items (the next item loads while the current one is used)
-  const size_t gsm = (a.max_group > 1 ? 2 : 1) * sizeof(C) *
-                     ((size_t)HR * b + (size_t)RCMAX * (b + 16 / sizeof(C)));
+  // gather: persistent, one block per SM; a stage buffer holds a dense 64-row tile half and <= 8
+  // source rows (padded by 16 bytes), as many stages as fit (<= GMAXSTG)
+  const size_t gstage = sizeof(C) * ((size_t)HR * b + (size_t)RCMAX * (b + 16 / sizeof(C)));
+  const int gstg = (int)std::max<size_t>(1, std::min<size_t>(GMAXSTG, SWEEP_SMEM_LIMIT / gstage));
+  const size_t gsm = (size_t)gstg * gstage;
   const unsigned gy = (unsigned)((a.nrhs + RCMAX - 1) / RCMAX);
   cudaFuncSetAttribute(gather_kernel<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm);
   cudaFuncSetAttribute(gather_kernel<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm);
+  int nsm = 0;
+  {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (nsm <= 0) nsm = 1;
+  }
+  auto launch_gather = [&](bool fwd, int64_t i0, int64_t i1) {
+    const int nunits = (int)((i1 - i0) * nh);
+    const dim3 grid((unsigned)std::min<int64_t>(nunits, nsm), gy);
+    if (fwd)
+      gather_kernel<R, true><<<grid, GGT, gsm, st>>>(a.fwd_groups + i0, a.fwd_items, L, Y, P, a.npad, b, a.nrhs,
+                                                    a.status, mk, nunits, gstg);
+    else
+      gather_kernel<R, false><<<grid, GGT, gsm, st>>>(a.bwd_groups + i0, a.bwd_items, L, Y, P, a.npad, b, a.nrhs,
+                                                     a.status, mk, nunits, gstg);
+  };
   // cluster chains: usable when every level's largest block fits CHAIN_MAXCL x CHAIN_MAXLOC strips
   const int crc = a.nrhs < RCMAX ? a.nrhs : RCMAX;
   const int cldv = vec_ld(crc);
@@ -1415,7 +1550,7 @@ static int sweep_impl(SweepLaunch& a, cudaStream_t st) {
     for (int lv = 0; lv < a.nlevels; ++lv) {
       const int64_t i0 = a.fwd_group_ptr[lv], i1 = a.fwd_group_ptr[lv + 1];
       if (i1 > i0) {
-        gather_kernel<R, true><<<dim3((unsigned)((i1 - i0) * nh), gy), GT, gsm, st>>>(a.fwd_groups + i0, a.fwd_items, L, Y, P, a.npad, b, a.nrhs, a.status, mk);
+        launch_gather(true, i0, i1);
         ++a.launches;
       }
       cs.slot_ptr = a.fwd_slot_ptr;
@@ -1436,7 +1571,7 @@ static int sweep_impl(SweepLaunch& a, cudaStream_t st) {
     for (int lv = a.nlevels - 1; lv >= 0; --lv) {
       const int64_t i0 = a.bwd_group_ptr[lv], i1 = a.bwd_group_ptr[lv + 1];
       if (i1 > i0) {
-        gather_kernel<R, false><<<dim3((unsigned)((i1 - i0) * nh), gy), GT, gsm, st>>>(a.bwd_groups + i0, a.bwd_items, L, Y, P, a.npad, b, a.nrhs, a.status, mk);
+        launch_gather(false, i0, i1);
         ++a.launches;
       }
       cs.slot_ptr = a.bwd_slot_ptr;
@@ -1482,7 +1617,7 @@ static int sweep_impl(SweepLaunch& a, cudaStream_t st) {
     const int64_t i0 = a.fwd_group_ptr[lv], i1 = a.fwd_group_ptr[lv + 1];
     const int64_t ntl = a.lev_tile_ptr[lv + 1] - a.lev_tile_ptr[lv];
     if (i1 > i0) {
-      gather_kernel<R, true><<<dim3((unsigned)((i1 - i0) * nh), gy), GT, gsm, st>>>(a.fwd_groups + i0, a.fwd_items, L, Y, P, a.npad, b, a.nrhs, a.status, mk);
+      launch_gather(true, i0, i1);
       const int64_t nthr = ntl * b * a.nrhs;
       reduce_kernel<R><<<(unsigned)((nthr + ET - 1) / ET), ET, 0, st>>>(a.lev_tiles + a.lev_tile_ptr[lv], (int)ntl,
                                                                      a.fwd_slot_ptr, P, Y, a.npad, b, a.nrhs, 1, nullptr, mk);
@@ -1500,7 +1635,7 @@ static int sweep_impl(SweepLaunch& a, cudaStream_t st) {
     const int64_t i0 = a.bwd_group_ptr[lv], i1 = a.bwd_group_ptr[lv + 1];
     const int64_t ntl = a.lev_tile_ptr[lv + 1] - a.lev_tile_ptr[lv];
     if (i1 > i0) {
-      gather_kernel<R, false><<<dim3((unsigned)((i1 - i0) * nh), gy), GT, gsm, st>>>(a.bwd_groups + i0, a.bwd_items, L, Y, P, a.npad, b, a.nrhs, a.status, mk);
+      launch_gather(false, i0, i1);
       const int64_t nthr = ntl * b * a.nrhs;
       reduce_kernel<R><<<(unsigned)((nthr + ET - 1) / ET), ET, 0, st>>>(a.lev_tiles + a.lev_tile_ptr[lv], (int)ntl,
                                                                      a.bwd_slot_ptr, P, Y, a.npad, b, a.nrhs, nh, nullptr, mk);
