@@ -186,30 +186,49 @@ __device__ __forceinline__ void rows_matvec(const typename CT<R>::C* M, int ldl,
 template <typename R, int MODE>
 __device__ __forceinline__ void rows_matvec_dense(const typename CT<R>::C* M, int b, const typename CT<R>::C* V,
                                                   int ldv, int rc, typename CT<R>::C* dst, int ldd) {
+  // warp w, lane l: rows rg + 16 a (rg = 2 w + l / 16, a < 4), columns l % 16 + 16 k, all right-hand
+  // sides; the 16 column groups of a row are summed by a shuffle reduce-scatter (lane l % 16 ends
+  // with values q = 2 (l % 16), 2 (l % 16) + 1 of q = a * 8 + j)
   using C = typename CT<R>::C;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int r = warp * 8 + (lane >> 2), cq = lane & 3, rot = 4 * (lane >> 2);
-  C acc[RCMAX];
+  const int rg = 2 * warp + (lane >> 4), cg = lane & 15;
+  C acc[4][RCMAX];
 #pragma unroll
-  for (int j = 0; j < RCMAX; ++j) acc[j] = CT<R>::make(0, 0);
-  const C* mrow = M + r * b;
-#pragma unroll 4
-  for (int i = 0; i < b / 4; ++i) {
-    const int c = (4 * i + cq + rot) & (b - 1);
-    const C m = mrow[c];
-    const C* v = V + c * ldv;
-    C vv[RCMAX];
+  for (int a = 0; a < 4; ++a)
 #pragma unroll
-    for (int j = 0; j < RCMAX; ++j) vv[j] = (j < rc) ? v[j] : CT<R>::make(0, 0);
+    for (int j = 0; j < RCMAX; ++j) acc[a][j] = CT<R>::make(0, 0);
+#pragma unroll 2
+  for (int c = cg; c < b; c += 16) {
+    C v[RCMAX];
 #pragma unroll
-    for (int j = 0; j < RCMAX; ++j) acc[j] = cfma(m, vv[j], acc[j]);
+    for (int j = 0; j < RCMAX; ++j) v[j] = (j < rc) ? V[c * ldv + j] : CT<R>::make(0, 0);
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      const C m = M[(rg + 16 * a) * b + c];
+#pragma unroll
+      for (int j = 0; j < RCMAX; ++j) acc[a][j] = cfma(m, v[j], acc[a][j]);
+    }
   }
-  quad_reduce(acc);
-  if (cq == 0) {
+  C* f = &acc[0][0];
 #pragma unroll
-    for (int j = 0; j < RCMAX; ++j)
-      if (j < rc)
-        dst[r * ldd + j] = MODE == 0 ? acc[j] : (MODE == 1 ? cadd(dst[r * ldd + j], acc[j]) : csub(dst[r * ldd + j], acc[j]));
+  for (int o = 8, n = 32; o >= 1; o >>= 1, n >>= 1) {
+    const bool up = (lane & o) != 0;
+#pragma unroll
+    for (int q = 0; q < n / 2; ++q) {
+      const C lo = f[q], hi = f[q + n / 2];
+      const C send = up ? lo : hi;
+      C keep = up ? hi : lo;
+      keep = cadd(keep, shfl_xor_c(send, o));
+      f[q] = keep;
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < 2; ++u) {
+    const int q = 2 * cg + u, a = q >> 3, j = q & 7;
+    if (j < rc) {
+      C* d = dst + (rg + 16 * a) * ldd + j;
+      *d = MODE == 0 ? f[u] : (MODE == 1 ? cadd(*d, f[u]) : csub(*d, f[u]));
+    }
   }
 }
 
@@ -521,36 +540,57 @@ __global__ void __launch_bounds__(ET) reduce_kernel(const int32_t* __restrict__ 
                                                     typename CT<R>::C* __restrict__ Y, int64_t npad, int b,
                                                     int nrhs, int nsub, const typename CT<R>::C* __restrict__ D,
                                                     Mask mk) {
+  // a block takes 32 consecutive outputs (tile, row, rhs); warp w sums the partials w, w + 8, ...
+  // of each (lanes = outputs, so the loads of a partial are contiguous), and the 8 sub-sums are
+  // added in warp order: the summation order depends only on the partial count
   using C = typename CT<R>::C;
-  const int64_t idx = blockIdx.x * (int64_t)ET + threadIdx.x;
+  constexpr int NW = ET / 32;
+  __shared__ C s_sub[NW][32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t idx = blockIdx.x * (int64_t)32 + lane;
   const int j = (int)(idx % nrhs);
   const int64_t rest = idx / nrhs;
   const int row = (int)(rest % b);
   const int64_t tl = rest / b;
-  if (tl >= ntl) return;
-  const int I = tiles[tl];
-  if (mk.off(I)) return;
-  const int64_t sp = slot_ptr[I];
-  const int64_t first = sp & 0xffffffffLL, cnt = (sp >> 32) * nsub;
-  if (cnt == 0 && !D) return;
+  bool live = tl < ntl;
+  int I = 0;
+  int64_t first = 0, cnt = 0;
+  if (live) {
+    I = tiles[tl];
+    live = !mk.off(I);
+  }
+  if (live) {
+    const int64_t sp = slot_ptr[I];
+    first = sp & 0xffffffffLL;
+    cnt = (sp >> 32) * nsub;
+  }
   const int nh = b / HR;
-  C* y = Y + (int64_t)j * npad + (int64_t)I * b + row;
-  C v = *y;
-  if (D) v = cdiv(v, D[(int64_t)I * b + row]);
-  if (cnt) {
+  C acc = czero<R>();
+  if (live && cnt > warp) {
     const C* pp = P + first * nh * (int64_t)b * nrhs + (int64_t)row * nrhs + j;
     const int64_t stride = (int64_t)b * nrhs * (nsub == 1 ? nh : 1);
-    C acc = czero<R>();
-    for (int64_t q0 = 0; q0 < cnt; q0 += 16) {
-      C t[16];
+    for (int64_t q0 = warp; q0 < cnt; q0 += 8 * NW) {
+      C t[8];
 #pragma unroll
-      for (int u = 0; u < 16; ++u) t[u] = (q0 + u < cnt) ? pp[(q0 + u) * stride] : czero<R>();
+      for (int u = 0; u < 8; ++u) t[u] = (q0 + u * NW < cnt) ? pp[(q0 + u * NW) * stride] : czero<R>();
 #pragma unroll
-      for (int u = 0; u < 16; ++u) acc = cadd(acc, t[u]);
+      for (int u = 0; u < 8; ++u) acc = cadd(acc, t[u]);
     }
-    v = csub(v, acc);
   }
-  *y = v;
+  s_sub[warp][lane] = acc;
+  __syncthreads();
+  if (warp == 0 && live && (cnt > 0 || D)) {
+    C* y = Y + (int64_t)j * npad + (int64_t)I * b + row;
+    C v = *y;
+    if (D) v = cdiv(v, D[(int64_t)I * b + row]);
+    if (cnt) {
+      C sum = s_sub[0][lane];
+#pragma unroll
+      for (int w = 1; w < NW; ++w) sum = cadd(sum, s_sub[w][lane]);
+      v = csub(v, sum);
+    }
+    *y = v;
+  }
 }
 
 // z = D^{-1} y over the whole padded vector (between the forward and backward sweeps)
@@ -956,16 +996,22 @@ __global__ void __launch_bounds__(GT) chain_kernel(ChainSweep s, const typename 
         C v = Y[(int64_t)(j0 + j) * s.npad + g];
         if (!FWD && s.apply_d) v = cdiv(v, D[g]);
         if (cnt) {
-          // 16 independent loads in flight per thread, summed in slot order within each batch
+          // 16 independent loads in flight per thread; partial q goes to sub-sum q % 8 and the
+          // sub-sums are added in order (the same order as reduce_kernel)
           const C* pp = P + first * nh * (int64_t)b * s.nrhs + (int64_t)(h * HR + row) * s.nrhs + (j0 + j);
-          C acc = czero<R>();
+          C sub[8];
+#pragma unroll
+          for (int w = 0; w < 8; ++w) sub[w] = czero<R>();
           for (int64_t q0 = 0; q0 < cnt; q0 += 16) {
             C t[16];
 #pragma unroll
             for (int u = 0; u < 16; ++u) t[u] = (q0 + u < cnt) ? pp[(q0 + u) * stride] : czero<R>();
 #pragma unroll
-            for (int u = 0; u < 16; ++u) acc = cadd(acc, t[u]);
+            for (int u = 0; u < 16; ++u) sub[u & 7] = cadd(sub[u & 7], t[u]);
           }
+          C acc = sub[0];
+#pragma unroll
+          for (int w = 1; w < 8; ++w) acc = cadd(acc, sub[w]);
           v = csub(v, acc);
         }
         rbuf[(l * HR + row) * ldv + j] = v;
@@ -1560,7 +1606,7 @@ static int sweep_impl(SweepLaunch& a, cudaStream_t st) {
         // many partials per row: a wide reduce launch is cheaper than the cluster's strip loads
         const int64_t ntl = a.lev_tile_ptr[lv + 1] - a.lev_tile_ptr[lv];
         const int64_t nthr = ntl * b * a.nrhs;
-        reduce_kernel<R><<<(unsigned)((nthr + ET - 1) / ET), ET, 0, st>>>(a.lev_tiles + a.lev_tile_ptr[lv], (int)ntl,
+        reduce_kernel<R><<<(unsigned)((nthr + 31) / 32), ET, 0, st>>>(a.lev_tiles + a.lev_tile_ptr[lv], (int)ntl,
                                                                        a.fwd_slot_ptr, P, Y, a.npad, b, a.nrhs, 1, nullptr, mk);
         ++a.launches;
         cs.has_partials = 0;
@@ -1580,7 +1626,7 @@ static int sweep_impl(SweepLaunch& a, cudaStream_t st) {
       if (i1 > i0 && a.lev_maxcnt_bwd[lv] > EXT_REDUCE) {
         const int64_t ntl = a.lev_tile_ptr[lv + 1] - a.lev_tile_ptr[lv];
         const int64_t nthr = ntl * b * a.nrhs;
-        reduce_kernel<R><<<(unsigned)((nthr + ET - 1) / ET), ET, 0, st>>>(a.lev_tiles + a.lev_tile_ptr[lv], (int)ntl,
+        reduce_kernel<R><<<(unsigned)((nthr + 31) / 32), ET, 0, st>>>(a.lev_tiles + a.lev_tile_ptr[lv], (int)ntl,
                                                                        a.bwd_slot_ptr, P, Y, a.npad, b, a.nrhs, nh, D, mk);
         ++a.launches;
         cs.has_partials = 0;
@@ -1619,7 +1665,7 @@ static int sweep_impl(SweepLaunch& a, cudaStream_t st) {
     if (i1 > i0) {
       launch_gather(true, i0, i1);
       const int64_t nthr = ntl * b * a.nrhs;
-      reduce_kernel<R><<<(unsigned)((nthr + ET - 1) / ET), ET, 0, st>>>(a.lev_tiles + a.lev_tile_ptr[lv], (int)ntl,
+      reduce_kernel<R><<<(unsigned)((nthr + 31) / 32), ET, 0, st>>>(a.lev_tiles + a.lev_tile_ptr[lv], (int)ntl,
                                                                      a.fwd_slot_ptr, P, Y, a.npad, b, a.nrhs, 1, nullptr, mk);
       a.launches += 2;
     }
@@ -1637,7 +1683,7 @@ static int sweep_impl(SweepLaunch& a, cudaStream_t st) {
     if (i1 > i0) {
       launch_gather(false, i0, i1);
       const int64_t nthr = ntl * b * a.nrhs;
-      reduce_kernel<R><<<(unsigned)((nthr + ET - 1) / ET), ET, 0, st>>>(a.lev_tiles + a.lev_tile_ptr[lv], (int)ntl,
+      reduce_kernel<R><<<(unsigned)((nthr + 31) / 32), ET, 0, st>>>(a.lev_tiles + a.lev_tile_ptr[lv], (int)ntl,
                                                                      a.bwd_slot_ptr, P, Y, a.npad, b, a.nrhs, nh, nullptr, mk);
       a.launches += 2;
     }
