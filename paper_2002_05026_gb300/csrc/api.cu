@@ -544,6 +544,15 @@ static int create_impl(d3m_handle* out, const d3m_pattern* pat, const int32_t* p
       ninvT += (int64_t)nt * (nt + 1) / 2;
       for (int tq = 0; tq < nt; ++tq) work.push_back(make_int2(k, tq));
     }
+    // longest columns first (tile products: sum over t > tq of t - tq + 1), so that the long
+    // sequential columns start in the first wave and the short ones fill the gaps after them
+    auto cost = [&](const int2& w) {
+      const int nt = S.ntile[w.x];
+      int64_t c = 0;
+      for (int t = w.y + 1; t < nt; ++t) c += t - w.y + 1;
+      return c;
+    };
+    std::stable_sort(work.begin(), work.end(), [&](const int2& a, const int2& c) { return cost(a) > cost(c); });
     UPLOAD(h->inv_off, off);
     UPLOAD(h->invT_off, offT);
     UPLOAD(h->inv_work, work);

@@ -1323,14 +1323,16 @@ __global__ void __launch_bounds__(128, 6) residual_kernel(ResidualParams p) {
 // ||K_i||_inf row sums (float magnitudes; a scale for omega), and the double-float split of K
 // used by the residual.
 __global__ void __launch_bounds__(256) knorm_kernel(ResidualParams p) {
-  const int i = threadIdx.x % 32, part = threadIdx.x / 32;   // 8 warps split the contributions
+  // 32 rows per block; warp w takes the w-th eighth of every contribution's columns (contiguous,
+  // so the transposed reads of a warp stay within the same cache lines), 4 loads in flight
+  const int i = threadIdx.x % 32, w = threadIdx.x / 32;
   const int2 ch = p.chunks[blockIdx.x];
   const int f = ch.x, u = ch.y + i;
   const int mf = p.m_orig[f];
   __shared__ float s_sum[8][32];
   float sum = 0.f;
   if (u < mf) {
-    for (int64_t e = p.res_ptr[f] + part; e < p.res_ptr[f + 1]; e += 8) {
+    for (int64_t e = p.res_ptr[f]; e < p.res_ptr[f + 1]; ++e) {
       const int blk = p.res_blk[e], g = p.res_src[e];
       const int mg = p.m_orig[g];
       const double2* Kp = p.K + p.kblk_off[blk];
@@ -1338,17 +1340,31 @@ __global__ void __launch_bounds__(256) knorm_kernel(ResidualParams p) {
       // untransposed visit: the split in K's layout; transposed visit: the split of the
       // transposed block (entry (u, c) at c * mf + u), written with coalesced stores
       float4* K2 = tr ? const_cast<float4*>(p.K2T) + p.res_ktoff[e] : const_cast<float4*>(p.K2) + p.kblk_off[blk];
-      for (int c = 0; c < mg; ++c) {
-        const int64_t o = tr ? (int64_t)u * mg + c : (int64_t)c * mf + u;
-        const float4 v = split_c_bits(__ldg(Kp + o));
-        K2[(int64_t)c * mf + u] = v;
-        sum += sqrtf(v.x * v.x + v.y * v.y);
+      const int per = (mg + 7) / 8;
+      const int c_lo = min(mg, w * per), c_hi = min(mg, c_lo + per);
+      auto off = [&](int c) -> int64_t { return tr ? (int64_t)u * mg + c : (int64_t)c * mf + u; };
+      int c = c_lo;
+      for (; c + 4 <= c_hi; c += 4) {
+        double2 v[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) v[q] = __ldg(Kp + off(c + q));
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const float4 sv = split_c_bits(v[q]);
+          K2[(int64_t)(c + q) * mf + u] = sv;
+          sum += sqrtf(sv.x * sv.x + sv.y * sv.y);
+        }
+      }
+      for (; c < c_hi; ++c) {
+        const float4 sv = split_c_bits(__ldg(Kp + off(c)));
+        K2[(int64_t)c * mf + u] = sv;
+        sum += sqrtf(sv.x * sv.x + sv.y * sv.y);
       }
     }
   }
-  s_sum[part][i] = sum;
+  s_sum[w][i] = sum;
   __syncthreads();
-  if (part == 0) {
+  if (w == 0) {
     float t = 0.f;
     for (int q = 0; q < 8; ++q) t += s_sum[q][i];
     for (int o = 16; o > 0; o >>= 1) t = fmaxf(t, __shfl_xor_sync(0xffffffffu, t, o));
