@@ -89,6 +89,9 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const void* tmap, int 
       "l"(reinterpret_cast<uint64_t>(tmap)), "r"(x), "r"(y), "r"(bar)
       : "memory");
 }
+__device__ __forceinline__ void bulk_prefetch_l2(const void* src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
 __device__ __forceinline__ void tma_prefetch_desc(const void* tmap) {
   asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(tmap)) : "memory");
 }
@@ -523,6 +526,18 @@ __global__ void __launch_bounds__(NTHR, 1)
     const uint64_t deadline = globaltimer_ns() + (uint64_t)p.timeout_ns;
     const int nchunk = T.nk * (TB / KC);
     asm volatile("fence.proxy.async.global;" ::: "memory");
+    // the tile's starting value (its accumulator, or K_IJ: up to 128 contiguous spans) is read
+    // after the products; warps 2..5 prefetch it into L2 while they run
+    if (warp >= 2 && warp < 6) {
+      const int sp = tid - 64;
+      if (T.flags & TF_S_IN) {
+        if (sp < 8 && T.sidx >= 0)
+          bulk_prefetch_l2(Sacc + (int64_t)T.sidx * TB * TB + sp * (TB * TB / 8), (uint32_t)(TB * TB / 8 * sizeof(float2)));
+      } else if (T.k_off >= 0 && sp < (T.k_tr ? T.rv : T.cv)) {
+        const int64_t base = T.k_tr ? (int64_t)(T.r0 + sp) * T.k_ld + T.c0 : (int64_t)(T.c0 + sp) * T.k_ld + T.r0;
+        bulk_prefetch_l2(p.K + T.k_off + base, (uint32_t)((T.k_tr ? T.cv : T.rv) * sizeof(double2)));
+      }
+    }
 
     // ---------------------------------------------------------------- phase 1: Schur GEMM
     if (nchunk > 0) {
