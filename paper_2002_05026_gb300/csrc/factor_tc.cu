@@ -214,6 +214,7 @@ __device__ __forceinline__ void load_s_in(const TileTask& T, const double2* K, f
 // updated first, so that two warps factor it while the other six finish panel k's updates.
 constexpr int DW = 32;          // panel width
 constexpr int WT_LD = 96;       // row length of the W panel scratch (c-major: Wt[c][row - c1])
+constexpr int XD_LD = DW + 1;   // row length of the dense copies of X_kk (two, by panel parity)
 
 // The DW x DW diagonal block at (c0, c0), two warps: warp 0 factors it (lane i = row i), warp 1
 // inverts L (lane j = column j of X) one phase of 8 columns behind, the two meeting at named
@@ -245,12 +246,13 @@ __device__ __forceinline__ void ldlt_phase(float2 (&a)[DW], int j0, float2* sS, 
 }
 
 template <int NM>
-__device__ __forceinline__ void linv_phase(float2 (&x)[DW], int q0, float2* sS, int c0, int lane) {
+__device__ __forceinline__ void linv_phase(float2 (&x)[DW], int q0, float2* sS, float2* Xd, int c0, int lane) {
 #pragma unroll 1
   for (int q = q0; q < q0 + 8; ++q) {
     // x holds rows q.. of column `lane` of X: X[q][lane] is final; X[m][lane] -= L[m][q] X[q][lane]
     const float2 xq = x[0];
     if (q > lane) sS[(c0 + lane) * LDS + c0 + q] = xq;      // X[q][lane] at sS[c0 + lane][c0 + q]
+    Xd[q * XD_LD + lane] = xq;                               // dense copy, zeros and ones included
 #pragma unroll
     for (int m = 1; m < NM; ++m) {
       const int row = min(q + m, DW - 1);                    // rows past the block feed unused slots
@@ -260,7 +262,7 @@ __device__ __forceinline__ void linv_phase(float2 (&x)[DW], int q0, float2* sS, 
   }
 }
 
-__device__ __forceinline__ void diag_block_2warps(float2* sS, float2* s_d, int c0, int warp, int lane) {
+__device__ __forceinline__ void diag_block_2warps(float2* sS, float2* s_d, float2* Xd, int c0, int warp, int lane) {
   float2 v[DW];
   if (warp == 0) {
 #pragma unroll
@@ -277,23 +279,20 @@ __device__ __forceinline__ void diag_block_2warps(float2* sS, float2* s_d, int c
 #pragma unroll
     for (int m = 0; m < DW; ++m) v[m] = make_float2(m == lane ? 1.f : 0.f, 0.f);
     asm volatile("bar.sync 1, 64;" ::: "memory");
-    linv_phase<32>(v, 0, sS, c0, lane);
+    linv_phase<32>(v, 0, sS, Xd, c0, lane);
     asm volatile("bar.sync 1, 64;" ::: "memory");
-    linv_phase<24>(v, 8, sS, c0, lane);
+    linv_phase<24>(v, 8, sS, Xd, c0, lane);
     asm volatile("bar.sync 1, 64;" ::: "memory");
-    linv_phase<16>(v, 16, sS, c0, lane);
+    linv_phase<16>(v, 16, sS, Xd, c0, lane);
     asm volatile("bar.sync 1, 64;" ::: "memory");
-    linv_phase<8>(v, 24, sS, c0, lane);
+    linv_phase<8>(v, 24, sS, Xd, c0, lane);
   }
 }
 
-// X_kk[c][q] of the current diagonal block (unit lower triangular)
-__device__ __forceinline__ float2 xkk(const float2* sS, int c0, int c, int q) {
-  return q < c ? sS[(c0 + q) * LDS + c0 + c] : make_float2(q == c ? 1.f : 0.f, 0.f);
-}
 
 // All threads: W_rk, L_rk for the rows below panel k (k < 3) and X_kj = -X_kk Z_kj (j < k).
-__device__ __forceinline__ void diag_panel_solve(float2* sS, const float2* s_d, float2* Wt, int k, int tid) {
+__device__ __forceinline__ void diag_panel_solve(float2* sS, const float2* s_d, float2* Wt, const float2* Xd, int k,
+                                                 int tid) {
   const int c0 = DW * k, c1 = c0 + DW, nrb = 3 - k;
   // W: thread -> columns cg + 8 jj, rows c1 + rg + 32 ii
   const int cg = tid & 7, rg = tid >> 3;
@@ -307,7 +306,7 @@ __device__ __forceinline__ void diag_panel_solve(float2* sS, const float2* s_d, 
     for (int q = 0; q < DW; ++q) {
       float2 xq[4], aq[3];
 #pragma unroll
-      for (int jj = 0; jj < 4; ++jj) xq[jj] = xkk(sS, c0, cg + 8 * jj, q);
+      for (int jj = 0; jj < 4; ++jj) xq[jj] = Xd[(cg + 8 * jj) * XD_LD + q];
 #pragma unroll
       for (int ii = 0; ii < 3; ++ii) aq[ii] = ii < nrb ? sS[(c1 + rg + 32 * ii) * LDS + c0 + q] : make_float2(0.f, 0.f);
 #pragma unroll
@@ -328,7 +327,7 @@ __device__ __forceinline__ void diag_panel_solve(float2* sS, const float2* s_d, 
     for (int q = 0; q < DW; ++q) {
       float2 xa[4], z[3];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) xa[i] = xkk(sS, c0, ar + 8 * i, q);
+      for (int i = 0; i < 4; ++i) xa[i] = Xd[(ar + 8 * i) * XD_LD + q];
 #pragma unroll
       for (int j = 0; j < 3; ++j) z[j] = j < k ? sS[(DW * j + b) * LDS + c0 + q] : make_float2(0.f, 0.f);
 #pragma unroll
@@ -384,16 +383,16 @@ __device__ __forceinline__ void diag_next_block(float2* sS, const float2* Wt, in
 
 // Warps 2..7 (t = thread index among them): the rest of panel k's updates as 32 x 32 block jobs --
 // trailing blocks (r, s), k < s <= r, other than (k+1, k+1), then Z blocks (r, j), r > k, j <= k.
-// A job is four chunks of 32 threads; each thread owns rows aa, aa + 16 and columns bb + 8 q.
-__device__ __forceinline__ void diag_panel_update(float2* sS, const float2* Wt, int k, int t) {
+// A job is two chunks of 32 threads; each thread owns rows aa + 8 i and columns bb + 8 q (i, q < 4).
+__device__ __forceinline__ void diag_panel_update(float2* sS, const float2* Wt, const float2* Xd, int k, int t) {
   const int c0 = DW * k, c1 = c0 + DW;
   const int nT = (3 - k) * (4 - k) / 2 - 1, nZ = (3 - k) * (k + 1);
-  const int nchunks = 4 * (nT + nZ);
+  const int nchunks = 2 * (nT + nZ);
   const int wi = t >> 5, lane = t & 31;
 #pragma unroll 1
   for (int ch = wi; ch < nchunks; ch += 6) {
-    const int job = ch >> 2;
-    const int aa = (ch & 3) * 4 + (lane >> 3), bb = lane & 7;
+    const int job = ch >> 1;
+    const int aa = (ch & 1) * 4 + (lane >> 3), bb = lane & 7;
     int rb, sb = 0, j = 0;
     const bool trailing = job < nT;
     if (trailing) {
@@ -410,55 +409,56 @@ __device__ __forceinline__ void diag_panel_update(float2* sS, const float2* Wt, 
       j = e % (k + 1);
     }
     const float2* P0 = sS + (DW * rb + aa) * LDS + c0;
-    const float2* P1 = P0 + 16 * LDS;
-    float2 acc[2][4];
+    float2 acc[4][4];
 #pragma unroll
-    for (int ii = 0; ii < 2; ++ii)
+    for (int ii = 0; ii < 4; ++ii)
 #pragma unroll
       for (int q = 0; q < 4; ++q) acc[ii][q] = make_float2(0.f, 0.f);
+    // Q[c][b]: W_sk (trailing), X_kj from the upper triangle (j < k) or the dense X_kk (j = k)
+    const float2* Q;
+    int qs_c, qs_b;
     if (trailing) {
-      const float2* Q = Wt + DW * sb - c1 + bb;
-#pragma unroll 4
-      for (int c = 0; c < DW; ++c) {
-        const float2 p0 = P0[c], p1 = P1[c];
+      Q = Wt + DW * sb - c1 + bb;
+      qs_c = WT_LD;
+      qs_b = 1;
+    } else if (j < k) {
+      Q = sS + (DW * j + bb) * LDS + c0;
+      qs_c = 1;
+      qs_b = LDS;
+    } else {
+      Q = Xd + bb;
+      qs_c = XD_LD;
+      qs_b = 1;
+    }
+#pragma unroll 2
+    for (int c = 0; c < DW; ++c) {
+      float2 pv[4], qv[4];
+#pragma unroll
+      for (int ii = 0; ii < 4; ++ii) pv[ii] = P0[8 * ii * LDS + c];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) qv[q] = Q[c * qs_c + 8 * q * qs_b];
+#pragma unroll
+      for (int ii = 0; ii < 4; ++ii)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[ii][q] = cfma(pv[ii], qv[q], acc[ii][q]);
+    }
+    if (trailing) {
+#pragma unroll
+      for (int ii = 0; ii < 4; ++ii)
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          const float2 qv = Q[c * WT_LD + 8 * q];
-          acc[0][q] = cfma(p0, qv, acc[0][q]);
-          acc[1][q] = cfma(p1, qv, acc[1][q]);
-        }
-      }
-#pragma unroll
-      for (int ii = 0; ii < 2; ++ii)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const int a = aa + 16 * ii, b = bb + 8 * q;
+          const int a = aa + 8 * ii, b = bb + 8 * q;
           if (rb != sb || b <= a) {
             float2* o = sS + (DW * rb + a) * LDS + DW * sb + b;
             *o = csub(*o, acc[ii][q]);
           }
         }
     } else {
-      // Q[c][b] = X_kj[c][b] at sS[(32 j + b) * LDS + c0 + c]; for j = k only b < c is stored
-      const float2* Q = sS + (DW * j + bb) * LDS + c0;
-      const bool tri = (j == k);
-#pragma unroll 4
-      for (int c = 0; c < DW; ++c) {
-        const float2 p0 = P0[c], p1 = P1[c];
+#pragma unroll
+      for (int ii = 0; ii < 4; ++ii)
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          const int b = bb + 8 * q;
-          float2 qv = Q[8 * q * LDS + c];
-          if (tri) qv = b < c ? qv : make_float2(b == c ? 1.f : 0.f, 0.f);
-          acc[0][q] = cfma(p0, qv, acc[0][q]);
-          acc[1][q] = cfma(p1, qv, acc[1][q]);
-        }
-      }
-#pragma unroll
-      for (int ii = 0; ii < 2; ++ii)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          float2* o = sS + (DW * j + bb + 8 * q) * LDS + DW * rb + aa + 16 * ii;
+          float2* o = sS + (DW * j + bb + 8 * q) * LDS + DW * rb + aa + 8 * ii;
           *o = make_float2(o->x + acc[ii][q].x, o->y + acc[ii][q].y);
         }
     }
@@ -674,17 +674,19 @@ __global__ void __launch_bounds__(NTHR, 1)
           if (cc > rr) sS[rr * LDS + cc] = make_float2(0.f, 0.f);
         }
         float2* Wt = s_d + TB;
+        float2* Xd = Wt + DW * WT_LD;                 // [2][DW][XD_LD]
         __syncthreads();
-        if (warp < 2) diag_block_2warps(sS, s_d, 0, warp, lane);
+        if (warp < 2) diag_block_2warps(sS, s_d, Xd, 0, warp, lane);
         __syncthreads();
 #pragma unroll 1
         for (int k = 0; k < TB / DW; ++k) {
-          diag_panel_solve(sS, s_d, Wt, k, tid);
+          float2* Xk = Xd + (k & 1) * DW * XD_LD;
+          diag_panel_solve(sS, s_d, Wt, Xk, k, tid);
           if (k == TB / DW - 1) break;
           diag_next_block(sS, Wt, k, tid);
           __syncthreads();
-          if (warp < 2) diag_block_2warps(sS, s_d, DW * (k + 1), warp, lane);
-          else diag_panel_update(sS, Wt, k, tid - 64);
+          if (warp < 2) diag_block_2warps(sS, s_d, Xd + ((k + 1) & 1) * DW * XD_LD, DW * (k + 1), warp, lane);
+          else diag_panel_update(sS, Wt, Xk, k, tid - 64);
           __syncthreads();
         }
         // L_JJ (unit lower) and D_J
