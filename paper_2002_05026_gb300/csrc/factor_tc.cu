@@ -222,23 +222,21 @@ constexpr int XD_LD = DW + 1;   // row length of the dense copies of X_kk (two, 
 // column / row j + m at step j) so that all register indices are static and the loops stay
 // rolled (straight-line code of this size would run out of the instruction cache).
 template <int NM>
-__device__ __forceinline__ void ldlt_phase(float2 (&a)[DW], int j0, float2* sS, float2* s_d, int c0, int lane) {
+__device__ __forceinline__ void ldlt_phase(float2 (&a)[DW], int j0, float2* sS, float2* s_d, float2* colb, int c0,
+                                           int lane) {
 #pragma unroll 1
   for (int j = j0; j < j0 + 8; ++j) {
     // d_j = a_j[j]; l_i = a_i[j] / d_j; a_i[m] -= l_i a_m[j] for m > j.  Lanes m > j are the only
-    // sources of a_m[j], so the unused entries above a lane's diagonal never reach a result.
+    // sources of a_m[j], so the unused entries above a lane's diagonal never reach a result.  The
+    // column goes through a shared buffer (one broadcast load per entry), two buffers by step parity.
     const float2 cj = a[0];
-    float2 dj;
-    dj.x = __shfl_sync(0xffffffffu, cj.x, j);
-    dj.y = __shfl_sync(0xffffffffu, cj.y, j);
+    float2* cb = colb + (j & 1) * DW;
+    cb[lane] = cj;
+    __syncwarp();
+    const float2 dj = cb[j];
     const float2 l = cdiv(cj, dj);
 #pragma unroll
-    for (int m = 1; m < NM; ++m) {
-      float2 cm;
-      cm.x = __shfl_sync(0xffffffffu, cj.x, (j + m) & 31);
-      cm.y = __shfl_sync(0xffffffffu, cj.y, (j + m) & 31);
-      a[m - 1] = cfms(l, cm, a[m]);
-    }
+    for (int m = 1; m < NM; ++m) a[m - 1] = cfms(l, cb[(j + m) & 31], a[m]);
     a[NM - 1] = make_float2(0.f, 0.f);
     if (lane > j) sS[(c0 + lane) * LDS + c0 + j] = l;
     if (lane == j) s_d[c0 + j] = dj;
@@ -263,17 +261,18 @@ __device__ __forceinline__ void linv_phase(float2 (&x)[DW], int q0, float2* sS, 
 }
 
 __device__ __forceinline__ void diag_block_2warps(float2* sS, float2* s_d, float2* Xd, int c0, int warp, int lane) {
+  float2* colb = s_d + TB + DW * WT_LD + 2 * DW * XD_LD;   // [2][DW] column buffers of warp 0
   float2 v[DW];
   if (warp == 0) {
 #pragma unroll
     for (int m = 0; m < DW; ++m) v[m] = (m <= lane) ? sS[(c0 + lane) * LDS + c0 + m] : make_float2(0.f, 0.f);
-    ldlt_phase<32>(v, 0, sS, s_d, c0, lane);
+    ldlt_phase<32>(v, 0, sS, s_d, colb, c0, lane);
     asm volatile("bar.sync 1, 64;" ::: "memory");
-    ldlt_phase<24>(v, 8, sS, s_d, c0, lane);
+    ldlt_phase<24>(v, 8, sS, s_d, colb, c0, lane);
     asm volatile("bar.sync 1, 64;" ::: "memory");
-    ldlt_phase<16>(v, 16, sS, s_d, c0, lane);
+    ldlt_phase<16>(v, 16, sS, s_d, colb, c0, lane);
     asm volatile("bar.sync 1, 64;" ::: "memory");
-    ldlt_phase<8>(v, 24, sS, s_d, c0, lane);
+    ldlt_phase<8>(v, 24, sS, s_d, colb, c0, lane);
     asm volatile("bar.sync 1, 64;" ::: "memory");
   } else {
 #pragma unroll
