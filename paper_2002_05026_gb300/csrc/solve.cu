@@ -37,11 +37,21 @@ struct Mask {
   __device__ __forceinline__ bool off(int64_t tile) const { return done && done[tinst[tile]] != 0; }
 };
 
+// Programmatic dependent launch between the kernels of a sweep: a kernel lets its successor be
+// scheduled at once (trigger) and does work that reads only data fixed before the solve (tiles of
+// L, inverses, task lists) before it waits for its predecessor; everything else follows the wait.
+// Every thread of every block waits before it exits, so completion stays transitive along the
+// stream.  Launched without the attribute, both instructions are no-ops.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // ------------------------------------------------------------------ permutation + padding
 template <typename R>
 __global__ void permute_in_kernel(const double2* __restrict__ src, int64_t n,
                                   typename CT<R>::C* __restrict__ Y, int64_t npad,
                                   const int64_t* __restrict__ pad2orig, int nrhs, Mask mk, int b) {
+  pdl_trigger();
+  pdl_wait();
   const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (g >= npad || mk.off(g / b)) return;
   const int64_t o = pad2orig[g];
@@ -56,6 +66,8 @@ __global__ void permute_out_kernel(const typename CT<R>::C* __restrict__ W, int6
                                    double2* __restrict__ X, int64_t n,
                                    const int64_t* __restrict__ pad2orig, int nrhs, int accumulate, Mask mk, int b,
                                    unsigned* dmax, int ld) {
+  pdl_trigger();
+  pdl_wait();
   const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (g - (threadIdx.x & 31) >= npad) return;              // whole warps past the end
   // a warp's 32 rows lie in one tile (tiles are >= 64 rows and warps 32-aligned)
@@ -312,6 +324,31 @@ struct GatherMeta {
   int slot, h, end, more;   // partial slot, half, last item of its unit, another item follows
 };
 
+// The two halves of stage_item: the tile half (thread 0 also arms the barrier for both parts) and
+// the source rows (lanes < rc of the issuing warp).
+template <typename C>
+__device__ __forceinline__ void stage_tile_only(C* sT, const C* half, int vlen, int rc, int b, uint64_t* bar) {
+  if (threadIdx.x != 0) return;
+  const uint32_t t_bytes = (uint32_t)(HR * b * sizeof(C)), v_bytes = (uint32_t)(vlen * sizeof(C));
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(t_bytes + rc * v_bytes)
+               : "memory");
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_addr(sT)),
+      "l"(half), "r"(t_bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+template <typename C>
+__device__ __forceinline__ void stage_rows_only(C* sV, int ldv, const C* Y, int64_t npad, int64_t y0, int vlen, int j0,
+                                                int rc, uint64_t* bar) {
+  const uint32_t v_bytes = (uint32_t)(vlen * sizeof(C));
+  for (int j = threadIdx.x; j < rc; j += 32)
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(sV + j * ldv)),
+        "l"(Y + (int64_t)(j0 + j) * npad + y0), "r"(v_bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
 template <typename R, bool FWD>
 __global__ void __launch_bounds__(GGT, 1) gather_kernel(const SolveGroup* __restrict__ groups,
                                                         const SolveItem* __restrict__ items,
@@ -342,8 +379,12 @@ __global__ void __launch_bounds__(GGT, 1) gather_kernel(const SolveGroup* __rest
     }
     return u;
   };
+  pdl_trigger();
   int pu = skip(blockIdx.x), pk = 0;                     // next unit / item to issue (warp 0)
-  if (pu >= nunits) return;                              // uniform: nothing to do for this block
+  if (pu >= nunits) {                                    // uniform: nothing to do for this block
+    pdl_wait();
+    return;
+  }
   if (threadIdx.x == 0) {
     for (int i = 0; i < nstg; ++i) mbar_init_s(&bars[i]);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -362,12 +403,20 @@ __global__ void __launch_bounds__(GGT, 1) gather_kernel(const SolveGroup* __rest
       pit = items[pg.first + pk];
     }
   };
-  auto issue = [&](int slot) {                           // warp 0: (pu, pk) into `slot`, then advance
+  // warp 0: (pu, pk) into `slot`, then advance; with rows == false only the tile half is copied
+  // (the source rows follow with stage_rows once the predecessor has finished)
+  int64_t y0s[GMAXSTG];
+  auto issue = [&](int slot, bool rows) {
     const int h = pu % nh;
     const int64_t y0 = (int64_t)pit.src * b + (FWD ? 0 : h * HR);
     C* T = sbase + (int64_t)slot * stg;
-    stage_item(T, T + HR * b, ldv, L + (int64_t)pit.tile * b * b + (int64_t)h * HR * b, Y, npad, y0, vlen, j0, rc, b,
-               &bars[slot]);
+    if (rows) {
+      stage_item(T, T + HR * b, ldv, L + (int64_t)pit.tile * b * b + (int64_t)h * HR * b, Y, npad, y0, vlen, j0, rc,
+                 b, &bars[slot]);
+    } else {
+      stage_tile_only(T, L + (int64_t)pit.tile * b * b + (int64_t)h * HR * b, vlen, rc, b, &bars[slot]);
+      y0s[slot] = y0;
+    }
     const bool end = (pk + 1 == pg.count);
     if (end) {
       pk = 0;
@@ -381,9 +430,15 @@ __global__ void __launch_bounds__(GGT, 1) gather_kernel(const SolveGroup* __rest
   if (warp == 0) {
     for (int i = 0; i < nstg && pu < nunits; ++i, ++inflight) {
       fetch();
-      issue(i);
+      issue(i, false);                                   // tiles of L are fixed during the solve
     }
   }
+  pdl_wait();                                            // the source rows come from the predecessor
+  if (warp == 0)
+    for (int i = 0; i < inflight; ++i) {
+      C* T = sbase + (int64_t)i * stg;
+      stage_rows_only(T + HR * b, ldv, Y, npad, y0s[i], vlen, j0, rc, &bars[i]);
+    }
   __syncthreads();                                       // s_meta of the first stages
   // forward: warp w, lane l -> rows rg + 32 i (rg = 2 w + l / 16, i < 2), columns l % 16 + 16 k, all
   //   right-hand sides; the 16 column groups of a row are summed by a shuffle reduce-scatter
@@ -450,7 +505,7 @@ __global__ void __launch_bounds__(GGT, 1) gather_kernel(const SolveGroup* __rest
       if (warp == 0 && pu < nunits) {
         if (lane == 0) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncwarp();
-        issue(slot);
+        issue(slot, true);
         ++inflight;
       }
       if (mt.end) {
@@ -508,7 +563,7 @@ __global__ void __launch_bounds__(GGT, 1) gather_kernel(const SolveGroup* __rest
       if (warp == 0 && pu < nunits) {
         if (lane == 0) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncwarp();
-        issue(slot);
+        issue(slot, true);
         ++inflight;
       }
     }
@@ -546,6 +601,8 @@ __global__ void __launch_bounds__(ET) reduce_kernel(const int32_t* __restrict__ 
   using C = typename CT<R>::C;
   constexpr int NW = ET / 32;
   __shared__ C s_sub[NW][32];
+  pdl_trigger();
+  pdl_wait();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t idx = blockIdx.x * (int64_t)32 + lane;
   const int j = (int)(idx % nrhs);
@@ -912,7 +969,11 @@ __global__ void __launch_bounds__(GT) chain_kernel(ChainSweep s, const typename 
   const int rc = min(s.rc, s.nrhs - j0);
   const int ldv = vec_ld(s.rc);
   const int t0 = s.tstart[k], nt = s.tstart[k + 1] - t0;
-  if (s.mk.off(t0)) return;                           // every CTA of the cluster, before any barrier
+  pdl_trigger();
+  if (s.mk.off(t0)) {                                 // every CTA of the cluster, before any barrier
+    pdl_wait();
+    return;
+  }
   const int S = nt * nh;
   const int nloc = S > rank ? (S - rank + CL - 1) / CL : 0;
   const int ldst = FWD ? stage_ld<C>(b) : stage_ld<C>(HR);
@@ -975,7 +1036,8 @@ __global__ void __launch_bounds__(GT) chain_kernel(ChainSweep s, const typename 
     else if (FWD) stage_rows(dst, ldst, s_job[jb], b, HR, b, &bars[jb & 1]);
     else stage_rows(dst, ldst, s_job[jb], b, b, HR, &bars[jb & 1]);
   };
-  if (nj > 0) stage(0);
+  if (nj > 0) stage(0);                                // tiles of L / the inverses: fixed during the solve
+  pdl_wait();                                         // Y and the partials come from the predecessors
   // strips of r: Y rows (backward: D^{-1} y) minus the level's partials in fixed slot order
   {
     const C* P = reinterpret_cast<const C*>(s.P);
@@ -1495,6 +1557,24 @@ __global__ void grad_pattern_kernel(const double2* __restrict__ Lam, const doubl
 }
 
 // ------------------------------------------------------------------ launchers
+// a kernel launch that may start before its predecessor in the stream has finished (the kernels
+// of a sweep wait for it with pdl_wait before they touch its results)
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
 template <typename R>
 static int sweep_impl(SweepLaunch& a, cudaStream_t st) {
   using C = typename CT<R>::C;
@@ -1509,7 +1589,7 @@ static int sweep_impl(SweepLaunch& a, cudaStream_t st) {
   const int nh = b / HR;
   a.launches = 0;
   const Mask mk{a.done, a.tinst};
-  permute_in_kernel<R><<<(unsigned)gblocks, nthreads, 0, st>>>(a.src, a.n, Y, a.npad, a.pad2orig, a.nrhs, mk, b);
+  launch_pdl(permute_in_kernel<R>, dim3((unsigned)gblocks), dim3(nthreads), 0, st, a.src, a.n, Y, a.npad, a.pad2orig, a.nrhs, mk, b);
   ++a.launches;
   // gather: persistent, one block per SM; a stage buffer holds a dense 64-row tile half and <= 8
   // source rows (padded by 16 bytes), as many stages as fit (<= GMAXSTG)
@@ -1530,11 +1610,11 @@ static int sweep_impl(SweepLaunch& a, cudaStream_t st) {
     const int nunits = (int)((i1 - i0) * nh);
     const dim3 grid((unsigned)std::min<int64_t>(nunits, nsm), gy);
     if (fwd)
-      gather_kernel<R, true><<<grid, GGT, gsm, st>>>(a.fwd_groups + i0, a.fwd_items, L, Y, P, a.npad, b, a.nrhs,
-                                                    a.status, mk, nunits, gstg);
+      launch_pdl(gather_kernel<R, true>, grid, dim3(GGT), gsm, st, a.fwd_groups + i0, a.fwd_items, L, Y, P, a.npad, b,
+                 a.nrhs, a.status, mk, nunits, gstg);
     else
-      gather_kernel<R, false><<<grid, GGT, gsm, st>>>(a.bwd_groups + i0, a.bwd_items, L, Y, P, a.npad, b, a.nrhs,
-                                                     a.status, mk, nunits, gstg);
+      launch_pdl(gather_kernel<R, false>, grid, dim3(GGT), gsm, st, a.bwd_groups + i0, a.bwd_items, L, Y, P, a.npad, b,
+                 a.nrhs, a.status, mk, nunits, gstg);
   };
   // cluster chains: usable when every level's largest block fits CHAIN_MAXCL x CHAIN_MAXLOC strips
   const int crc = a.nrhs < RCMAX ? a.nrhs : RCMAX;
@@ -1595,13 +1675,15 @@ static int sweep_impl(SweepLaunch& a, cudaStream_t st) {
       cfg.blockDim = dim3(GT, 1, 1);
       cfg.dynamicSmemBytes = chain_smem(cs.nloc);
       cfg.stream = st;
-      cudaLaunchAttribute attr[1];
+      cudaLaunchAttribute attr[2];
       attr[0].id = cudaLaunchAttributeClusterDimension;
       attr[0].val.clusterDim.x = (unsigned)cs.cl;
       attr[0].val.clusterDim.y = 1;
       attr[0].val.clusterDim.z = 1;
+      attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+      attr[1].val.programmaticStreamSerializationAllowed = 1;
       cfg.attrs = attr;
-      cfg.numAttrs = 1;
+      cfg.numAttrs = 2;
       ++a.launches;
       if (inv)
         return fwd ? cudaLaunchKernelEx(&cfg, chain_kernel<R, true, true>, cs, L, Linv, Y)
@@ -1622,7 +1704,7 @@ static int sweep_impl(SweepLaunch& a, cudaStream_t st) {
         // many partials per row: a wide reduce launch is cheaper than the cluster's strip loads
         const int64_t ntl = a.lev_tile_ptr[lv + 1] - a.lev_tile_ptr[lv];
         const int64_t nthr = ntl * b * a.nrhs;
-        reduce_kernel<R><<<(unsigned)((nthr + 31) / 32), ET, 0, st>>>(a.lev_tiles + a.lev_tile_ptr[lv], (int)ntl,
+        launch_pdl(reduce_kernel<R>, dim3((unsigned)((nthr + 31) / 32)), dim3(ET), 0, st, a.lev_tiles + a.lev_tile_ptr[lv], (int)ntl,
                                                                        a.fwd_slot_ptr, P, Y, a.npad, b, a.nrhs, 1, nullptr, mk);
         ++a.launches;
         cs.has_partials = 0;
@@ -1642,7 +1724,7 @@ static int sweep_impl(SweepLaunch& a, cudaStream_t st) {
       if (i1 > i0 && a.lev_maxcnt_bwd[lv] > EXT_REDUCE) {
         const int64_t ntl = a.lev_tile_ptr[lv + 1] - a.lev_tile_ptr[lv];
         const int64_t nthr = ntl * b * a.nrhs;
-        reduce_kernel<R><<<(unsigned)((nthr + 31) / 32), ET, 0, st>>>(a.lev_tiles + a.lev_tile_ptr[lv], (int)ntl,
+        launch_pdl(reduce_kernel<R>, dim3((unsigned)((nthr + 31) / 32)), dim3(ET), 0, st, a.lev_tiles + a.lev_tile_ptr[lv], (int)ntl,
                                                                        a.bwd_slot_ptr, P, Y, a.npad, b, a.nrhs, nh, D, mk);
         ++a.launches;
         cs.has_partials = 0;
@@ -1651,7 +1733,7 @@ static int sweep_impl(SweepLaunch& a, cudaStream_t st) {
       cudaError_t e = launch_chain(lv, false);
       if (e != cudaSuccess) return (int)e;
     }
-    permute_out_kernel<R><<<(unsigned)gblocks, nthreads, 0, st>>>(Y, a.npad, a.dst, a.n, a.pad2orig, a.nrhs, a.accumulate, mk, b, a.dmax, a.ld_norm);
+    launch_pdl(permute_out_kernel<R>, dim3((unsigned)gblocks), dim3(nthreads), 0, st, Y, a.npad, a.dst, a.n, a.pad2orig, a.nrhs, a.accumulate, mk, b, a.dmax, a.ld_norm);
     ++a.launches;
     return (int)cudaGetLastError();
   }
@@ -1681,7 +1763,7 @@ static int sweep_impl(SweepLaunch& a, cudaStream_t st) {
     if (i1 > i0) {
       launch_gather(true, i0, i1);
       const int64_t nthr = ntl * b * a.nrhs;
-      reduce_kernel<R><<<(unsigned)((nthr + 31) / 32), ET, 0, st>>>(a.lev_tiles + a.lev_tile_ptr[lv], (int)ntl,
+      launch_pdl(reduce_kernel<R>, dim3((unsigned)((nthr + 31) / 32)), dim3(ET), 0, st, a.lev_tiles + a.lev_tile_ptr[lv], (int)ntl,
                                                                      a.fwd_slot_ptr, P, Y, a.npad, b, a.nrhs, 1, nullptr, mk);
       a.launches += 2;
     }
@@ -1699,7 +1781,7 @@ static int sweep_impl(SweepLaunch& a, cudaStream_t st) {
     if (i1 > i0) {
       launch_gather(false, i0, i1);
       const int64_t nthr = ntl * b * a.nrhs;
-      reduce_kernel<R><<<(unsigned)((nthr + 31) / 32), ET, 0, st>>>(a.lev_tiles + a.lev_tile_ptr[lv], (int)ntl,
+      launch_pdl(reduce_kernel<R>, dim3((unsigned)((nthr + 31) / 32)), dim3(ET), 0, st, a.lev_tiles + a.lev_tile_ptr[lv], (int)ntl,
                                                                      a.bwd_slot_ptr, P, Y, a.npad, b, a.nrhs, nh, nullptr, mk);
       a.launches += 2;
     }
@@ -1709,7 +1791,7 @@ static int sweep_impl(SweepLaunch& a, cudaStream_t st) {
     block_bwd_kernel<R><<<dim3(nb, ny), GT, bsm, st>>>(bs, L, Linv, Y);
     ++a.launches;
   }
-  permute_out_kernel<R><<<(unsigned)gblocks, nthreads, 0, st>>>(Y, a.npad, a.dst, a.n, a.pad2orig, a.nrhs, a.accumulate, mk, b, a.dmax, a.ld_norm);
+  launch_pdl(permute_out_kernel<R>, dim3((unsigned)gblocks), dim3(nthreads), 0, st, Y, a.npad, a.dst, a.n, a.pad2orig, a.nrhs, a.accumulate, mk, b, a.dmax, a.ld_norm);
   ++a.launches;
   return (int)cudaGetLastError();
 }
