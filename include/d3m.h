@@ -194,9 +194,11 @@ int d3m_create_batch(d3m_handle* out, int32_t count, const d3m_pattern* pats,
  * d3m_info.instances entries.  Synchronizes `stream`. */
 int d3m_get_instance_omega(d3m_handle h, double* host_out, void* stream);
 
-/* Numeric factorization.  K: c128 lower blocks as described above (host or device).  The
- * library copies K, then runs one persistent kernel whose blocks pull ready tile tasks from
- * a device queue with atomic dependency counters (Sec. II task model, Fig. 1(c)).
+/* Numeric factorization.  K: c128 lower blocks as described above (host or device).  A host K
+ * is copied; a device K (16-byte aligned) is read in place, in stream order: it must not
+ * change until the factorization has completed on `stream` (nothing reads it afterwards).
+ * One persistent kernel then factors K, its blocks pulling ready tile tasks from a device
+ * queue with atomic dependency counters (Sec. II task model, Fig. 1(c)).
  * D3M_ERR_PIVOT if a pivot falls below the breakdown threshold, D3M_ERR_TIMEOUT if a device
  * wait expired.  Errors found on the device are returned by the next call that synchronizes
  * (d3m_get_info) and by d3m_solve. */

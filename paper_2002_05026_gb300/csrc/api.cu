@@ -743,7 +743,11 @@ static int enqueue_factor(d3m_ctx* h, const void* Kin, bool kdev, cudaStream_t s
   const Symbolic& S = h->S;
   const int64_t ntiles = (int64_t)S.tasks.size();   // all tasks (final + update)
   const size_t kbytes = (size_t)S.kblk_off.back() * sizeof(double2);
-  CUDA_TRY(h, cudaMemcpyAsync(h->K, Kin, kbytes, kdev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+  // a (16-byte aligned) device K is read in place by the two kernels that use it (the
+  // factorization and the norm/split of K, both below); a host K is copied first
+  const double2* Ksrc = h->K;
+  if (kdev && ((uintptr_t)Kin & 15) == 0) Ksrc = static_cast<const double2*>(Kin);
+  else CUDA_TRY(h, cudaMemcpyAsync(h->K, Kin, kbytes, kdev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
   // reset the task graph state
   CUDA_TRY(h, cudaMemcpyAsync(h->cnt, h->ndeps, ntiles * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
   CUDA_TRY(h, cudaMemsetAsync(h->ready, 0xff, ntiles * sizeof(int32_t), st));
@@ -767,7 +771,7 @@ static int enqueue_factor(d3m_ctx* h, const void* Kin, bool kdev, cudaStream_t s
   p.ctl = h->ctl;
   p.ntasks = (int32_t)ntiles;
   p.b = h->b;
-  p.K = h->K;
+  p.K = Ksrc;
   p.L = h->L;
   p.Linv = h->Linv;
   p.D = h->D;
@@ -789,6 +793,7 @@ static int enqueue_factor(d3m_ctx* h, const void* Kin, bool kdev, cudaStream_t s
   CUDA_TRY(h, cudaEventRecord(h->ev_fork, st));
   CUDA_TRY(h, cudaStreamWaitEvent(h->side, h->ev_fork, 0));
   ResidualParams rp = residual_params(h, nullptr, nullptr, 1);
+  rp.K = Ksrc;
   CUDA_TRY(h, cudaMemsetAsync(rp.kmax, 0, h->ninst * sizeof(unsigned), h->side));
   rc = launch_knorm(rp, h->nchunks, h->side);
   if (rc) return set_err(h, D3M_ERR_CUDA, std::string("knorm launch: ") + cudaGetErrorString((cudaError_t)rc));
