@@ -249,3 +249,22 @@ def test_device_omega_matches_extended_precision(torch_cuda, precision, g, m):
     else:
         assert w_ext <= 1e-12
         assert w_dev == pytest.approx(w_ext, rel=0.02), (w_dev, w_ext)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "bf16x3"])
+def test_device_k_read_in_place(torch_cuda, precision):
+    # a device K is read in place by the factorization (and the norm/split of K); nothing reads
+    # it afterwards, so overwriting it after d3m_factor (in stream order) leaves the solve intact
+    from paper_2002_05026_gb300 import D3M
+    torch = torch_cuda
+    p, pm, Kb, F = _setup((3, 3, 1), 64, k2=2.0, tau=0.05, seed=31)
+    B = synth.rhs(5, p.n, 3)
+    s = D3M(p.colptr, p.rowidx, m=p.m, perm=pm, precision=precision, max_nrhs=8)
+    Kd = torch.from_numpy(p.blocks_numpy()).cuda()
+    s.factor(Kd)
+    Kd.zero_()
+    X = s.solve(torch.from_numpy(np.ascontiguousarray(B)).cuda()).cpu().numpy()
+    s.close()
+    assert _fwd_err(X, O.block_solve(F, B)) <= 1e-9
+    if precision != "fp64":
+        assert np.max(O.omega(Kb, p.nblk, p.m, X, B)) <= 1e-12
