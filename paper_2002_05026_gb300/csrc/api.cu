@@ -867,7 +867,6 @@ static int sweep(d3m_ctx* h, const double2* src, double2* dst, int nrhs, int acc
   a.lev_maxnt = h->lev_maxnt.data();
   a.lev_maxcnt_fwd = h->lev_maxcnt_fwd.data();
   a.lev_maxcnt_bwd = h->lev_maxcnt_bwd.data();
-  a.max_group = S.max_group;
   a.Inv = h->use_inv ? h->Inv : nullptr;
   a.inv_off = h->inv_off;
   a.InvT = h->InvT;

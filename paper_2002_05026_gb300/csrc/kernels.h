@@ -72,7 +72,6 @@ struct SweepLaunch {
   const int32_t* lev_maxnt;        // host [nlevels]: most tiles of one block in the level
   const int32_t* lev_maxcnt_fwd;   // host [nlevels]: most forward partials of one tile row
   const int32_t* lev_maxcnt_bwd;   // host [nlevels]: most backward partials of one tile column
-  int max_group;                   // most items summed by one gather block
   const void* Inv;                 // off-diagonal tiles of the diagonal blocks' inverses, or nullptr
   const int* done;                 // device [instances]: converged instances are skipped, or nullptr
   const int32_t* tinst;            // device [NT]: instance of every tile row (permuted numbering)
