@@ -206,6 +206,78 @@ def reference_arm(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------ adjoint arm
+ADJ_METRIC = "adjoint gradient evaluations: factor + refined solve + refined adjoint solve + dJ/deps"
+
+
+def adjoint_arm(args, rank, world, local):
+    """J = Re(c^T x), x = K(eps)^{-1} b on the 8x8 grid with m = 256 (64 domain parameters eps_i).
+    One step = one gradient evaluation: factor K(eps), x = solve(b), Lambda = adjoint(c) (same
+    factors, K^T = K), dJ/deps_i = Re(k2 sum_{u in I(i)} Lambda_u x_u).  Value = evaluations/s."""
+    import numpy as np
+    import torch
+    import synth
+    from paper_2002_05026_gb300 import D3M, d3m_order_grid_nd
+
+    torch.cuda.set_device(local)
+    w = synth.WORKLOADS[args.workload]
+    seed = w["seed"] + rank
+    ndom = w["nx"] * w["ny"] * w["nz"]
+    eps = synth.domain_eps(seed + 3, ndom)
+    p = synth.make_problem(w["nx"], w["ny"], w["nz"], w["m"], w["k2"], w["tau"], seed, eps=eps, device="cuda")
+    perm = d3m_order_grid_nd(w["nx"], w["ny"], w["nz"])
+    b = torch.from_numpy(np.ascontiguousarray(synth.rhs(seed + 1, p.n, 1))).cuda()
+    c = torch.from_numpy(np.ascontiguousarray(synth.sparse_adjoint_vector(seed + 2, p.n, p.m,
+                                                                           support_block=int(perm[-1])))).cuda()
+    s = D3M(p.colptr, p.rowidx, m=p.m, perm=perm, precision=args.precision, max_nrhs=1)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        s.factor(p.blocks)
+        x = s.solve(b)
+        lam = s.adjoint(c)
+        return s.grad_eps(lam, x, p.dom_if, w["k2"])     # host array; synchronizes the stream
+
+    for _ in range(args.warmup):
+        g = step()
+    info0 = s.info()
+    clk = ClockSampler(local)
+    clk.start()
+    time.sleep(0.3)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        g = step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    info = s.info()
+    peaks, peak_kind = measured_peaks()
+    fms = info["factor_kernel_ms_total"] / max(1, info["factor_kernel_calls"])
+    roof = {"bound": "tensor", "achieved": info["factor_flops"] / (fms * 1e-3) / 1e12,
+            "peak": peaks["bf16_tflops_sustained"] / 3.0, "unit": "TFLOP/s", "kernel": "factor_kernel",
+            "kernel_ms": fms, "peak_source": "bf16_tflops_sustained/3", "traffic": None, "peak_kind": peak_kind}
+    if args.precision != "bf16x3":
+        roof.update({"bound": "alu", "peak": FP64_PEAK_GFLOPS / 1e3 if args.precision == "fp64" else
+                     152 * 2.07e9 * 256 / 1e12, "peak_source": "ALU nominal"})
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    line = {"metric": ADJ_METRIC, "value": 1e3 / ms * world, "unit": "gradients/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "c64+bf16x3/fp64-refine" if args.precision == "bf16x3"
+            else args.precision, "data": "synthetic",
+            "config": {"workload": args.workload, "grid": [w["nx"], w["ny"], w["nz"]], "m": w["m"], "n": p.n,
+                       "parameters": ndom, "k2": w["k2"], "tau": w["tau"], "precision": args.precision},
+            "roofline": roof,
+            "accuracy": {"omega": info["omega"], "refine_solves_last_call": info["refine_iters"],
+                         "max_abs_dJ_deps": float(np.max(np.abs(g)))},
+            "clocks": clocks, "gpu_launches": info["kernel_launches"] - info0["kernel_launches"]}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    s.close()
+
+
 # ------------------------------------------------------------------ batched arm
 BATCH_METRIC = "batched factor+solve throughput: uneven instances, mixed-prec + FP64 refinement"
 
@@ -405,6 +477,9 @@ def main():
     build.build()
     if args.workload == "batch256":
         batch_arm(args, rank, world, local)
+        return
+    if args.workload.startswith("adjoint"):
+        adjoint_arm(args, rank, world, local)
         return
     torch.cuda.set_device(local)
     dist = None
