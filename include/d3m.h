@@ -207,8 +207,10 @@ int d3m_factor(d3m_handle h, const void* K, void* stream);
 /* Solve K X = B for nrhs columns (1 <= nrhs <= max_nrhs).  B, X: c128, n x nrhs column-major
  * (host or device; may not alias).  FP64 mode: one forward/diagonal/backward sweep.  Mixed
  * modes: x = 0, r = b; repeat { d = solve_c64(r); x += d (FP64); r = b - K x (FP64, block
- * SpMV over the stored K) } until max_col omega <= refine_tol or the cap; D3M_ERR_NOT_CONVERGED
- * if the cap is hit or omega fails to halve over two steps (X then holds the best iterate). */
+ * SpMV over the stored K) } until, per instance, every column has omega <= refine_tol and an
+ * estimated forward error <= refine_fwd_tol, or the cap; D3M_ERR_NOT_CONVERGED if the cap is hit
+ * or the instances still open stop making progress (their largest omega / refine_tol and
+ * correction / refine_fwd_tol fails to halve over two steps); X then holds the best iterate. */
 int d3m_solve(d3m_handle h, const void* B, void* X, int32_t nrhs, void* stream);
 
 /* Adjoint solve with the same factors: K^T Lambda = G, which is K Lambda = G since K^T = K.
