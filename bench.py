@@ -53,6 +53,16 @@ def parse_args():
     return ap.parse_args()
 
 
+def cross_rank_max(v: float, dist, device) -> float:
+    """Largest v over the ranks (the step time a multi-rank line reports); v when dist is None."""
+    if dist is None:
+        return v
+    import torch
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -302,11 +312,7 @@ def batch_arm(args, rank, world, local):
             dist.barrier()
 
     def allmax(v: float) -> float:
-        if dist is None:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return cross_rank_max(v, dist, "cuda")
 
     count, nrhs = 256, 4
     specs = synth.batch_instances(count, seed=20260105 + 100003 * rank)   # each rank its own batch
@@ -492,11 +498,7 @@ def main():
             dist.barrier()
 
     def allmax(v: float) -> float:
-        if dist is None:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return cross_rank_max(v, dist, "cuda")
 
     w = synth.WORKLOADS[args.workload]
     seed = w["seed"] + rank
