@@ -350,3 +350,24 @@ def test_torch_philox_matches_definition():
     a = synth.normal_rows(5, 1, 3, np.arange(64), 130)
     b = synth.normal_rows_torch(5, 1, 3, 64, 130, "cpu").numpy()
     assert np.abs(a - b).max() < 1e-13
+
+
+def test_residual_and_omega_hand_worked():
+    """r = b - K x and omega = ||r||inf / (||K||inf ||x||inf + ||b||inf) (reading R7) on a 4 x 4 K
+    stored by its lower blocks (m = 2; K complex symmetric: the upper block is the TRANSPOSE of the
+    stored lower one, not its conjugate).  Worked by hand:
+        K = [[1, 0, 0,  0 ], [0, 1, 3i, 0], [0, 3i, 0.5, 0], [0, 0, 0, 0.5]],  ||K||inf = 4,
+        x = e_2, b = (0, 3i, 0, 0):  K x = (0, 3i, 0.5, 0),  r = (0, 0, -0.5, 0),  omega = 0.5 / 7.
+    A dropped mirror block gives omega 3/7, a conjugated one 6/7, an untransposed one 3/7, and a
+    norm from the lower triangle alone 1/13."""
+    I2 = np.eye(2, dtype=np.complex128)
+    K10 = np.array([[0, 3j], [0, 0]], dtype=np.complex128)
+    Kb = {(0, 0): I2, (1, 0): K10, (1, 1): 0.5 * I2}
+    x = np.array([0, 0, 1, 0], dtype=np.complex128)[:, None]
+    b = np.array([0, 3j, 0, 0], dtype=np.complex128)[:, None]
+    r = O.residual(Kb, 2, x, b)
+    assert np.array_equal(r[:, 0], np.array([0, 0, -0.5, 0], dtype=np.complex128))
+    assert O.k_inf_norm(Kb, 2, 2) == 4.0
+    assert O.omega(Kb, 2, 2, x, b)[0] == pytest.approx(0.5 / 7.0, rel=0, abs=1e-15)
+    A = O.dense_from_lower(Kb, 2, 2)
+    assert np.array_equal(A @ x[:, 0], np.array([0, 3j, 0.5, 0], dtype=np.complex128))
