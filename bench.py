@@ -43,13 +43,14 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="d3m", choices=["d3m", "reference"])
-    ap.add_argument("--workload", default="grid8x8_m512")
-    ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "simt32", "fp64"])
+    ap.add_argument("--workload", default="grid6x6x6_m512")
+    ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "tf32", "simt32", "fp64"])
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--report-modules", action="store_true", help=argparse.SUPPRESS)
     return ap.parse_args()
 
 
@@ -142,36 +143,82 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ CPU oracle sample
-def oracle_sample(p_blocks_np, p, perm, seconds: float):
-    """Time the oracle's right-looking block LDL^T on the first C block columns, with C chosen so
-    the run takes about `seconds`; returns (flops, time, C, share of the factor flops)."""
+def host_gemm_rate(m: int) -> float:
+    """Flops/s of the host's complex128 m x m matrix product (the step that dominates the oracle's
+    block factorization), used only to size the oracle sample."""
     import numpy as np
-    import oracle as O
-    Kb = O.lower_blocks(p.colptr, p.rowidx, p_blocks_np, p.m)
-    Kp = O.permute_lower(Kb, perm)
-    st, _ = O.block_symbolic(p.nblk, Kp.keys())
-    m = p.m
-
-    def col_flops(k):
-        s = len(st[k])
-        return (4 / 3) * m ** 3 + s * 4 * m ** 3 + s * 4 * m ** 3 + s * (s - 1) / 2 * 8 * m ** 3
-
-    total = sum(col_flops(k) for k in range(p.nblk))
-    # calibrate the host rate on one block column's worth of work
+    a = np.ones((m, m), dtype=np.complex128)
+    a @ a
     t0 = time.perf_counter()
-    O.block_ldlt(Kp, p.nblk, m, ncols=1)
-    rate = col_flops(0) / max(time.perf_counter() - t0, 1e-6)
-    budget = rate * seconds
-    C, acc = 0, 0.0
-    while C < p.nblk and acc + col_flops(C) <= budget:
-        acc += col_flops(C)
-        C += 1
-    C = max(C, 1)
-    flops = sum(col_flops(k) for k in range(C))
-    t0 = time.perf_counter()
-    O.block_ldlt(Kp, p.nblk, m, ncols=C)
-    dt = time.perf_counter() - t0
-    return flops, dt, C, flops / total
+    for _ in range(3):
+        a @ a
+    return 3 * 8.0 * m ** 3 / max(time.perf_counter() - t0, 1e-6)
+
+
+class OracleSample:
+    """The oracle (numpy FP64) right-looking block LDL^T of the first C block columns of a
+    workload, in the oracle's own nested-dissection order, C chosen for about `seconds` of host
+    work.  Only the domains adjacent to those C interfaces are generated: the factor of the first
+    C columns depends on K's first C (permuted) columns alone, and those are exact; the trailing
+    Schur updates they produce (timed as well) land in blocks that are left partial.  Nothing
+    here loads the CUDA library."""
+
+    def __init__(self, w: dict, seed: int, seconds: float):
+        import numpy as np
+        import oracle as O
+        import synth
+        nx, ny, nz, m = w["nx"], w["ny"], w["nz"], w["m"]
+        self.m = m
+        self.perm = O.nd_order(nx, ny, nz)
+        colptr, rowidx = synth.lower_pattern(nx, ny, nz)
+        N = colptr.size - 1
+        self.N = N
+        inv = np.empty(N, dtype=np.int64)
+        inv[self.perm] = np.arange(N)
+        keys = []
+        for g in range(N):
+            for e in range(colptr[g], colptr[g + 1]):
+                i, j = int(inv[rowidx[e]]), int(inv[g])
+                keys.append((max(i, j), min(i, j)))
+        st, _ = O.block_symbolic(N, keys)
+
+        def col_flops(k):
+            s_ = len(st[k])
+            return (4 / 3) * m ** 3 + s_ * 4 * m ** 3 + s_ * 4 * m ** 3 + s_ * (s_ - 1) / 2 * 8 * m ** 3
+
+        cf = [col_flops(k) for k in range(N)]
+        total = sum(cf)
+        budget = host_gemm_rate(m) * seconds
+        C, acc = 0, 0.0
+        while C < N and acc + cf[C] <= budget:
+            acc += cf[C]
+            C += 1
+        self.C = max(C, 1)
+        self.flops = sum(cf[:self.C])
+        self.share = self.flops / total
+        doms = synth.interface_domains(nx, ny, nz, self.perm[:self.C])
+        p = synth.make_problem(nx, ny, nz, m, w["k2"], w["tau"], seed, device="cpu", domains=doms)
+        flat = p.blocks.numpy()
+        Kb = {}
+        for g in range(N):
+            for e in range(colptr[g], colptr[g + 1]):
+                f = int(rowidx[e])
+                if min(inv[f], inv[g]) < self.C:
+                    Kb[(f, g)] = flat[e * m * m:(e + 1) * m * m].reshape(m, m).T.copy()
+        del p, flat
+        self.Kp = O.permute_lower(Kb, self.perm)
+        self.ndomains = len(doms)
+
+    def run(self) -> float:
+        import oracle as O
+        t0 = time.perf_counter()
+        O.block_ldlt(self.Kp, self.N, self.m, ncols=self.C)
+        return time.perf_counter() - t0
+
+    def describe(self, workload: str, dt: float) -> str:
+        return (f"oracle (numpy FP64) right-looking block LDL^T of the first {self.C} of {self.N} block columns "
+                f"({100 * self.share:.2f}% of the factor flops) of the {workload} matrix, {dt:.1f} s "
+                f"(the {self.ndomains} domains adjacent to those columns generated)")
 
 
 def make_workload(w, seed, device):
@@ -184,27 +231,21 @@ def make_workload(w, seed, device):
 
 # ------------------------------------------------------------------ reference arm (the oracle)
 def reference_arm(args, rank, world):
+    """The oracle on the host cores, on a bounded sample of the workload; loads neither torch's
+    CUDA nor the CUDA library (only `oracle` and `synth`)."""
     if rank != 0:
         return
-    import numpy as np
     import synth
-    from paper_2002_05026_gb300 import d3m_order_grid_nd  # host-only ordering routine
     w = synth.WORKLOADS[args.workload]
-    p, _ = make_workload(w, w["seed"], "cpu")
-    blocks = p.blocks.numpy()
-    perm = d3m_order_grid_nd(w["nx"], w["ny"], w["nz"])
     per_step = min(args.cpu_seconds, 150.0 / max(1, args.steps + args.warmup))
+    smp = OracleSample(w, w["seed"], per_step)
     for _ in range(args.warmup):
-        oracle_sample(blocks, p, perm, per_step)
-    vals, times = [], []
-    for _ in range(args.steps):
-        fl, dt, C, share = oracle_sample(blocks, p, perm, per_step)
-        vals.append(fl / dt / 1e12)
-        times.append(dt)
+        smp.run()
+    times = [smp.run() for _ in range(args.steps)]
+    vals = [smp.flops / t / 1e12 for t in times]
     value = sum(vals) / len(vals)
     cores = os.cpu_count()
-    sample = (f"oracle (numpy FP64) right-looking block LDL^T of the first {C} of {p.nblk} block "
-              f"columns ({100 * share:.1f}% of the factor flops) of the {args.workload} matrix")
+    sample = smp.describe(args.workload, sum(times) / len(times))
     line = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
@@ -213,6 +254,11 @@ def reference_arm(args, rank, world):
                        "nrhs": w["nrhs"], "k2": w["k2"], "tau": w["tau"]},
             "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    if args.report_modules:
+        # what this process loaded of the product: its Python package and any mapped libd3m.so
+        maps = open("/proc/self/maps").read() if os.path.exists("/proc/self/maps") else ""
+        line["product_modules"] = sorted(k for k in sys.modules if k.startswith("paper_2002_05026_gb300"))
+        line["product_so_mapped"] = "libd3m.so" in maps
     print(json.dumps(line), flush=True)
 
 
@@ -267,8 +313,8 @@ def adjoint_arm(args, rank, world, local):
     peaks, peak_kind = measured_peaks()
     fms = info["factor_kernel_ms_total"] / max(1, info["factor_kernel_calls"])
     roof = {"bound": "tensor", "achieved": info["factor_flops"] / (fms * 1e-3) / 1e12,
-            "peak": peaks["bf16_tflops_sustained"] / 3.0, "unit": "TFLOP/s", "kernel": "factor_kernel",
-            "kernel_ms": fms, "peak_source": "bf16_tflops_sustained/3", "traffic": None, "peak_kind": peak_kind}
+            "peak": peaks["bf16_tflops"] / 3.0, "unit": "TFLOP/s", "kernel": "factor_kernel",
+            "kernel_ms": fms, "peak_source": "bf16_tflops/3 (burst)", "traffic": None, "peak_kind": peak_kind}
     if args.precision != "bf16x3":
         roof.update({"bound": "alu", "peak": FP64_PEAK_GFLOPS / 1e3 if args.precision == "fp64" else
                      152 * 2.07e9 * 256 / 1e12, "peak_source": "ALU nominal"})
@@ -364,7 +410,7 @@ def batch_arm(args, rank, world, local):
     peaks, peak_kind = measured_peaks()
     fms = info["factor_kernel_ms_total"] / max(1, info["factor_kernel_calls"])
     if tune["precision"] == "bf16x3":
-        pk, bound, pname = peaks["bf16_tflops_sustained"] / 3.0, "tensor", "bf16_tflops_sustained/3"
+        pk, bound, pname = peaks["bf16_tflops"] / 3.0, "tensor", "bf16_tflops/3 (burst)"
     else:
         pk, bound, pname = 152 * 2.07e9 * 256 / 1e12, "alu", "FP32 FMA 152 SMs x 128 x 2 x 2.07 GHz"
     ach = info["factor_flops"] / (fms * 1e-3) / 1e12
@@ -432,9 +478,10 @@ def batch_arm(args, rank, world, local):
         import oracle as O
         t0 = time.perf_counter()
         done = 0
-        for w, p, pm, B in zip(specs, probs, perms, Bs):
+        for w, p, B in zip(specs, probs, Bs):
             if time.perf_counter() - t0 > args.cpu_seconds:
                 break
+            pm = O.nd_order(w["nx"], w["ny"], w["nz"])       # the oracle's own ordering
             blocks = p.blocks.cpu().numpy()
             Kb = O.lower_blocks(p.colptr, p.rowidx, blocks, p.m)
             F = O.block_ldlt(O.permute_lower(Kb, pm), p.nblk, p.m)
@@ -502,6 +549,14 @@ def main():
 
     w = synth.WORKLOADS[args.workload]
     seed = w["seed"] + rank
+    dev_total = torch.cuda.mem_get_info()[1]
+    mem_peak = [0]
+
+    def mem_sample():
+        # device-wide high-water mark: total - free at sampled points (cudaMemGetInfo)
+        free, total = torch.cuda.mem_get_info()
+        mem_peak[0] = max(mem_peak[0], total - free)
+
     p, Bnp = make_workload(w, seed, "cuda")
     nrhs = w["nrhs"]
     K = p.blocks                                            # device c128, lower blocks
@@ -512,6 +567,7 @@ def main():
     sp = ctypes.c_void_p(stream.cuda_stream)
     s = D3M(p.colptr, p.rowidx, m=p.m, perm=perm, precision=args.precision, max_nrhs=nrhs)
     lib = s._lib
+    mem_sample()
 
     def step(Kp, Bp, Xp):
         rc = lib.d3m_factor(s.h, ctypes.c_void_p(Kp), sp)
@@ -523,6 +579,8 @@ def main():
 
     for _ in range(args.warmup):
         step(K.data_ptr(), Bt.data_ptr(), Xt.data_ptr())
+    torch.cuda.synchronize()
+    mem_sample()
     info0 = s.info()
     clk = ClockSampler(local)
     clk.start()
@@ -546,14 +604,19 @@ def main():
     X_mixed = Xt.clone()
 
     # ---------------------------------------------------------------- roofline of the dominant kernel
+    # tensor-core kernels are scored against the BURST bf16 peak (the larger of the two measured
+    # figures): a conservative denominator whatever the clocks were during the run
     peaks, peak_kind = measured_peaks()
     b = info["tile"]
     kern = []
     if info["factor_kernel_calls"]:
         fms = info["factor_kernel_ms_total"] / info["factor_kernel_calls"]
         if args.precision == "bf16x3":
-            pk, unit, bound, pname = peaks["bf16_tflops_sustained"] / 3.0, "TFLOP/s", "tensor", \
-                "bf16_tflops_sustained/3 (split-BF16x3: 3 bf16 products per FP32-level product)"
+            pk, unit, bound, pname = peaks["bf16_tflops"] / 3.0, "TFLOP/s", "tensor", \
+                "bf16_tflops/3 (burst; split-BF16x3: 3 bf16 products per FP32-level product)"
+        elif args.precision == "tf32":
+            pk, unit, bound, pname = peaks["bf16_tflops"] / 2.0, "TFLOP/s", "tensor", \
+                "bf16_tflops/2 (burst; tf32 dense rate = half the bf16 rate, nominal 1.1 vs 2.25 PFLOP/s)"
         elif args.precision == "fp64":
             pk, unit, bound, pname = FP64_PEAK_GFLOPS / 1e3, "TFLOP/s", "alu", "FP64 nominal 1.25 TFLOP/s"
         else:
@@ -563,11 +626,13 @@ def main():
                       "unit": unit, "peak_source": pname, "kernel_ms": fms}))
     if info["residual_calls"]:
         rms = info["residual_ms_total"] / info["residual_calls"]
+        kbytes = info["residual_bytes_fixed"] + info["residual_bytes_per_rhs"] * nrhs
         kern.append(("residual", info["residual_ms_total"],
-                     {"bound": "alu", "achieved": info["residual_flops_per_rhs"] * nrhs / (rms * 1e-3) / 1e12,
-                      "peak": RESID_PEAK_TFLOPS, "unit": "TFLOP/s",
-                      "peak_source": "FP32 issue rate (152 SMs x 128 lanes x 2.07 GHz) x 8 flops / 60 FP32 "
-                                     "instructions per double-float complex multiply-add", "kernel_ms": rms}))
+                     {"bound": "hbm", "achieved": kbytes / (rms * 1e-3) / 1e9, "peak": peaks["hbm_gbs"],
+                      "unit": "GB/s", "peak_source": "hbm_gbs (algorithmic bytes: K's stored lower blocks in "
+                                                     "c128 + x, b and r per right-hand side)",
+                      "kernel_ms": rms,
+                      "fp64_accurate_tflops": info["residual_flops_per_rhs"] * nrhs / (rms * 1e-3) / 1e12}))
     if info["sweep_calls"]:
         sms = info["sweep_ms_total"] / info["sweep_calls"]
         esz = 16 if args.precision == "fp64" else 8
@@ -584,40 +649,11 @@ def main():
     roof["peak_kind"] = peak_kind
     breakdown = {k: {"ms_per_step": t / args.steps, **{kk: v for kk, v in r.items() if kk in ("achieved", "peak", "unit", "bound")}}
                  for k, t, r in kern}
-
-    # ---------------------------------------------------------------- plain FP64 GPU path
-    fp64 = None
-    if not args.no_fp64 and args.precision != "fp64":
-        s64 = D3M(p.colptr, p.rowidx, m=p.m, perm=perm, precision="fp64", max_nrhs=nrhs)
-        X64 = torch.empty_like(Bt)
-
-        def step64():
-            lib.d3m_factor(s64.h, ctypes.c_void_p(K.data_ptr()), sp)
-            rc = lib.d3m_solve(s64.h, ctypes.c_void_p(Bt.data_ptr()), ctypes.c_void_p(X64.data_ptr()), nrhs, sp)
-            if rc:
-                raise RuntimeError(s64.last_error())
-
-        step64()
-        torch.cuda.synchronize()
-        s64.info()
-        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        f0.record(stream)
-        for _ in range(args.fp64_steps):
-            step64()
-        f1.record(stream)
-        torch.cuda.synchronize()
-        ms64 = allmax(f0.elapsed_time(f1) / args.fp64_steps)
-        i64 = s64.info()
-        rel = (torch.linalg.norm(X_mixed - X64, dim=1) / torch.linalg.norm(X64, dim=1)).max().item()
-        fk = i64["factor_kernel_ms_total"] / max(1, i64["factor_kernel_calls"])
-        fp64 = {"ms_per_step": ms64, "tflops": flops_step / (ms64 * 1e-3) / 1e12,
-                "speedup_mixed_vs_fp64": ms64 / ms, "factor_kernel_ms": fk,
-                "factor_roofline": {"bound": "alu", "achieved": i64["factor_flops"] / (fk * 1e-3) / 1e12,
-                                    "peak": FP64_PEAK_GFLOPS / 1e3, "unit": "TFLOP/s",
-                                    "frac": i64["factor_flops"] / (fk * 1e-3) / 1e12 / (FP64_PEAK_GFLOPS / 1e3)},
-                "max_rel_diff_mixed_vs_fp64": rel}
-        s64.close()
-        del X64
+    memory = {"handle_device_bytes": int(info["device_bytes"]),
+              "torch_peak_allocated_bytes": int(torch.cuda.max_memory_allocated()),
+              "device_used_high_water_bytes": int(mem_peak[0]), "device_total_bytes": int(dev_total),
+              "how": "handle_device_bytes = every buffer the solver handle owns; device_used_high_water = max of "
+                     "(total - free) from cudaMemGetInfo after create, after warm-up and after the timed steps"}
 
     # ---------------------------------------------------------------- end to end, host buffers
     e2e = None
@@ -627,6 +663,7 @@ def main():
         Xh = torch.empty_like(Bh).pin_memory()
         step(Kh.data_ptr(), Bh.data_ptr(), Xh.data_ptr())
         torch.cuda.synchronize()
+        mem_sample()
         barrier()
         g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         g0.record(stream)
@@ -640,21 +677,66 @@ def main():
                "h2d_bytes_per_step": int(Kh.numel() * 16 + Bh.numel() * 16),
                "d2h_bytes_per_step": int(Xh.numel() * 16)}
         del Kh
+    memory["device_used_high_water_bytes"] = int(mem_peak[0])
+    s.close()
+    torch.cuda.empty_cache()
+
+    # ---------------------------------------------------------------- plain FP64 GPU path
+    fp64 = None
+    if not args.no_fp64 and args.precision != "fp64":
+        s64 = D3M(p.colptr, p.rowidx, m=p.m, perm=perm, precision="fp64", max_nrhs=nrhs)
+        X64 = torch.empty_like(Bt)
+
+        def step64():
+            rc = lib.d3m_factor(s64.h, ctypes.c_void_p(K.data_ptr()), sp)
+            if rc:
+                raise RuntimeError(s64.last_error())
+            rc = lib.d3m_solve(s64.h, ctypes.c_void_p(Bt.data_ptr()), ctypes.c_void_p(X64.data_ptr()), nrhs, sp)
+            if rc:
+                raise RuntimeError(s64.last_error())
+
+        # a factorization of more than 1e13 flops runs for minutes at FP64 rates: one timed run
+        # without a warm-up run (first-launch overheads are below a millisecond)
+        warm64 = info["factor_flops"] < 1e13
+        if warm64:
+            step64()
+            torch.cuda.synchronize()
+            s64.info()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(args.fp64_steps):
+            step64()
+        f1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = allmax(f0.elapsed_time(f1) / args.fp64_steps)
+        i64 = s64.info()
+        rel = (torch.linalg.norm(X_mixed - X64, dim=1) / torch.linalg.norm(X64, dim=1)).max().item()
+        fk = i64["factor_kernel_ms_total"] / max(1, i64["factor_kernel_calls"])
+        fp64 = {"ms_per_step": ms64, "tflops": flops_step / (ms64 * 1e-3) / 1e12,
+                "speedup_mixed_vs_fp64": ms64 / ms, "factor_kernel_ms": fk, "warmup_run": warm64,
+                "steps": args.fp64_steps, "handle_device_bytes": int(i64["device_bytes"]),
+                "factor_roofline": {"bound": "alu", "achieved": i64["factor_flops"] / (fk * 1e-3) / 1e12,
+                                    "peak": FP64_PEAK_GFLOPS / 1e3, "unit": "TFLOP/s",
+                                    "peak_source": "FP64 nominal 1.25 TFLOP/s (not measured)",
+                                    "frac": i64["factor_flops"] / (fk * 1e-3) / 1e12 / (FP64_PEAK_GFLOPS / 1e3)},
+                "max_rel_diff_mixed_vs_fp64": rel}
+        s64.close()
+        del X64
 
     # ---------------------------------------------------------------- CPU oracle sample
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        fl, dt, C, share = oracle_sample(K.cpu().numpy(), p, perm, args.cpu_seconds)
-        cpu = {"value": fl / dt / 1e12, "unit": "TFLOP/s", "cores": os.cpu_count(), "kind": "oracle",
-               "sample": (f"oracle (numpy FP64) right-looking block LDL^T of the first {C} of {p.nblk} block "
-                          f"columns ({100 * share:.1f}% of the factor flops), {dt:.1f} s")}
+        smp = OracleSample(w, seed, args.cpu_seconds)
+        dt = smp.run()
+        cpu = {"value": smp.flops / dt / 1e12, "unit": "TFLOP/s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": smp.describe(args.workload, dt)}
 
     if rank == 0:
+        dtype = {"bf16x3": "c64+bf16x3/fp64-refine", "tf32": "c64+tf32/fp64-refine", "fp64": "c128"}.get(
+            args.precision, "c64/fp64-refine")
         line = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "c64+bf16x3/fp64-refine" if args.precision == "bf16x3" else
-                ("c128" if args.precision == "fp64" else "c64/fp64-refine"),
-                "data": "synthetic",
+                "vs_baseline": None, "dtype": dtype, "data": "synthetic",
                 "config": {"workload": args.workload, "grid": [w["nx"], w["ny"], w["nz"]], "m": w["m"],
                            "n": p.n, "nrhs": nrhs, "k2": w["k2"], "tau": w["tau"], "precision": args.precision,
                            "order": "nested dissection", "l2": "inputs larger than L2 (K is "
@@ -662,11 +744,11 @@ def main():
                 "roofline": roof, "kernels": breakdown,
                 "accuracy": {"omega": info["omega"], "omega_first_solve": info["omega_first"],
                              "refine_solves": info["refine_iters"]},
+                "memory": memory,
                 "fp64_path": fp64, "e2e": e2e, "cpu_baseline": cpu, "clocks": clocks,
                 "gpu_launches": int(launches),
                 "flops_per_step": flops_step, "factor_flops": info["factor_flops"]}
         print(json.dumps(line), flush=True)
-    s.close()
     if dist is not None:
         dist.destroy_process_group()
 

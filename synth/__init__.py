@@ -246,10 +246,13 @@ def domain_eps(seed: int, ndom: int, lo: float = 1.0, hi: float = 4.0) -> np.nda
     return lo + (hi - lo) * uniform01(seed, TAG_EPS, np.arange(ndom))
 
 
-def make_problem(nx, ny, nz, m, k2, tau, seed, eps=None, real_g=False, device=None) -> Problem:
+def make_problem(nx, ny, nz, m, k2, tau, seed, eps=None, real_g=False, device=None, domains=None) -> Problem:
     """Assemble K's lower blocks.  `device`: None for numpy, or a torch device ("cpu", "cuda")
     for the random draws and the G G^T products (the result is then a torch complex128
-    tensor on that device)."""
+    tensor on that device).  `domains`: None for every domain, or a collection of domain ids
+    whose blocks M_i alone are added (the others contribute nothing).  A block K_fg is then
+    exact when every domain holding both f and g is listed (``interface_domains`` of g's
+    column gives such a set), and partial otherwise."""
     dom_if = domain_interfaces(nx, ny, nz)
     ndom = nx * ny * nz
     colptr, rowidx = lower_pattern(nx, ny, nz)
@@ -273,7 +276,7 @@ def make_problem(nx, ny, nz, m, k2, tau, seed, eps=None, real_g=False, device=No
     for i in range(ndom):
         I = dom_if[i]
         r = len(I) * m
-        if r == 0:
+        if r == 0 or (domains is not None and i not in domains):
             continue
         sigma = -k2 * eps[i] + 1j * tau
         if use_torch:
@@ -302,6 +305,19 @@ def make_problem(nx, ny, nz, m, k2, tau, seed, eps=None, real_g=False, device=No
                     blocks[blk_off[e]:blk_off[e + 1]] += sub.T.reshape(-1)
     return Problem(nx, ny, nz, m, float(k2), float(tau), int(seed), eps, colptr, rowidx,
                    blocks, blk_off, dom_if, real_g)
+
+
+def interface_domains(nx: int, ny: int, nz: int, ifaces) -> set:
+    """The domains adjacent to the listed interfaces (each interface joins two domains).  Every
+    K block K_fg with g in the list sums M_i over domains i containing g, so generating these
+    domains makes the columns of the listed interfaces exact."""
+    ifs = interfaces(nx, ny, nz)
+    out = set()
+    for f in ifaces:
+        d, _ax, e = ifs[int(f)]
+        out.add(d)
+        out.add(e)
+    return out
 
 
 def rhs(seed: int, n: int, nrhs: int, tag: int = TAG_B) -> np.ndarray:

@@ -86,3 +86,14 @@ def test_reference_arm_json_line():
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
     assert d["e2e"]["value"] == d["value"] and d["e2e"]["unit"] == d["unit"]
+
+
+def test_reference_arm_loads_no_product_code():
+    # the reference arm times the oracle alone: neither the CUDA library's Python package nor
+    # libd3m.so may be loaded by it (its ordering is the oracle's own nested dissection)
+    r = _run_bench(["--impl", "reference", "--workload", "grid2x2_m64", "--steps", "1", "--warmup", "0",
+                    "--cpu-seconds", "1", "--report-modules"])
+    assert r.returncode == 0, r.stderr
+    d = json.loads([l for l in r.stdout.splitlines() if l.startswith("{")][0])
+    assert d["product_modules"] == []
+    assert d["product_so_mapped"] is False
