@@ -31,7 +31,8 @@
  *     loop inside d3m_solve, which reads one convergence word per iteration.
  *
  * Ownership: the caller owns every buffer it passes and the stream.  The library owns the
- * factors, a copy of K (kept for the FP64 residual), the task graph and its workspaces, from
+ * factors, a float-pair split of K (kept for the FP64 residual), a copy buffer for a host K
+ * (allocated by the first d3m_factor that passes one), the task graph and its workspaces, from
  * d3m_create until d3m_destroy.  A handle is not thread-safe; use one per host thread.
  *
  * Errors: every int-returning call returns D3M_OK (0) or one of the D3M_ERR_* codes below;
@@ -147,6 +148,10 @@ typedef struct {
   int32_t reserved0;
   int64_t prio_tasks;       /* tasks the device scheduler serves first: slack within 8% of the
                                estimated critical path of the task graph */
+  /* algorithmic bytes of one FP64 residual r = b - K x: the stored lower blocks of K once in
+   * c128 (residual_bytes_fixed) plus x and b read and r written in c128 per right-hand side */
+  double residual_bytes_fixed;
+  double residual_bytes_per_rhs;
 } d3m_info;
 
 /* Default options (precision D3M_MIXED_BF16X3). */
@@ -226,18 +231,23 @@ int d3m_grad_eps(d3m_handle h, const void* Lambda, const void* X, int32_t nrhs,
                  int32_t ndom, const int32_t* dom_ptr, const int32_t* dom_if, double k2,
                  double* dJ_deps, void* stream);
 
-/* Same result as d3m_grad_eps, for callers that cannot allocate memory while it runs: code
- * being captured into a CUDA graph (cudaMalloc is not permitted during stream capture), or a
- * host application whose own allocator owns the device memory and forbids library
- * allocations.  The paper has no counterpart; this is an API convenience of this library.
+/* Same result as d3m_grad_eps, for callers that cannot allocate memory while it runs: a host
+ * application whose own allocator owns the device memory (a memory pool sized at start-up, a
+ * framework that hands every free byte to its caching allocator) and forbids allocations by
+ * libraries, or code running where the device is nearly full, so that a cudaMalloc of the
+ * temporaries could fail after the expensive solves have already been done.  The paper has no
+ * counterpart; this is an API convenience of this library.
  * It allocates nothing (no cudaMalloc / cudaFree / host allocation): its temporaries live in
  * one file-scope static device array of about 0.9 MB that every GPU loading the library keeps
  * until process exit.  Limits: at most 16384 interfaces, 16384 domains and 98304 dom_if
- * entries, else D3M_ERR_INVALID.  The first call on a device looks up that array's device
- * address (cudaGetSymbolAddress); make that first call before any stream capture.  All calls
- * share the array, so calls that overlap on the GPU (other streams, other host threads) race;
- * no entry of it needs to start at zero.  Lambda, X: device c128; dJ_deps: host or device
- * double [ndom]; synchronizes the stream. */
+ * entries, else D3M_ERR_INVALID; dom_ptr must start at 0 and be nondecreasing, and every dom_if
+ * entry must name an interface, else D3M_ERR_INVALID (checked on the host before anything is
+ * copied or launched).  The handle's device must be the current device (D3M_ERR_INVALID
+ * otherwise).  The first call on a device looks up that array's device address
+ * (cudaGetSymbolAddress).  All calls share the array, so calls that overlap on the GPU (other
+ * streams, other host threads) race; no entry of it needs to start at zero.  dom_ptr and
+ * dom_if are copied from (pageable) host memory and the call synchronizes the stream before it
+ * returns.  Lambda, X: device c128; dJ_deps: host or device double [ndom]. */
 int d3m_grad_eps_noalloc(d3m_handle h, const void* Lambda, const void* X, int32_t nrhs,
                          int32_t ndom, const int32_t* dom_ptr, const int32_t* dom_if, double k2,
                          double* dJ_deps, void* stream);

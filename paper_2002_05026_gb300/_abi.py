@@ -57,7 +57,8 @@ class d3m_info(ctypes.Structure):
                 ("kernel_launches", c_int64), ("factor_kernel_ms_total", c_double),
                 ("residual_ms_total", c_double), ("sweep_ms_total", c_double),
                 ("factor_kernel_calls", c_int64), ("residual_calls", c_int64), ("sweep_calls", c_int64),
-                ("instances", c_int32), ("reserved0", c_int32), ("prio_tasks", c_int64)]
+                ("instances", c_int32), ("reserved0", c_int32), ("prio_tasks", c_int64),
+                ("residual_bytes_fixed", c_double), ("residual_bytes_per_rhs", c_double)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -279,6 +279,8 @@ void fill_structure(const Symbolic& S, d3m_info* info) {
   info->solve_flops_per_rhs = S.solve_flops_rhs;
   info->residual_flops_per_rhs = S.residual_flops_rhs;
   info->prio_tasks = S.n_prio;
+  info->residual_bytes_fixed = (double)S.kblk_off.back() * 16.0;
+  info->residual_bytes_per_rhs = 3.0 * 16.0 * (double)S.n;
 }
 
 int factor_error(d3m_ctx* h) {
@@ -306,6 +308,7 @@ int handle_geometry(d3m_handle h, int64_t* n, int32_t* nblk, const int64_t** xof
   return D3M_OK;
 }
 int handle_error(d3m_handle h, int code, const char* msg) { return set_err(h, code, msg); }
+int handle_device(d3m_handle h) { return h->device; }
 }  // namespace d3m
 
 extern "C" {
@@ -423,8 +426,7 @@ static int create_impl(d3m_handle* out, const d3m_pattern* pat, const int32_t* p
     int rc_ = upload(h, &ptr, vec);             \
     if (rc_ != D3M_OK) return rc_;              \
   } while (0)
-  // factorization
-  ALLOC(h->K, double2, S.kblk_off.back());
+  // factorization (h->K, the copy target of a host K, is allocated by the first call that needs it)
   ALLOC(h->K2, float4, S.kblk_off.back());
   UPLOAD(h->tasks, S.tasks);
   UPLOAD(h->klist, S.klist);
@@ -815,6 +817,11 @@ int d3m_factor(d3m_handle h, const void* Kin, void* stream) {
   if (!Kin) return set_err(h, D3M_ERR_INVALID, "K is NULL");
   cudaStream_t st = (cudaStream_t)stream;
   const bool kdev = is_device_ptr(Kin);
+  if ((!kdev || ((uintptr_t)Kin & 15) != 0) && !h->K) {
+    // a host (or misaligned device) K is copied into a buffer of the handle, allocated on first use
+    h->K = dalloc<double2>(h, (size_t)h->S.kblk_off.back());
+    if (!h->K) return set_err(h, D3M_ERR_OOM, "cudaMalloc failed for the copy of K");
+  }
   int rc;
   if (h->opt.graphs && kdev) {
     // whole sequence as one graph; the event pair then spans the copy of K and ||K|| as well

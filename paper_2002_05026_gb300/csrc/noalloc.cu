@@ -1,11 +1,12 @@
 // d3m_grad_eps_noalloc: the epsilon gradient with all temporary storage in a fixed static
-// device array, for callers that must not allocate memory during the call (for example code
-// being captured into a CUDA graph, where cudaMalloc is not allowed, or a host that hands all
-// device memory to its own allocator and forbids allocations from libraries).
+// device array, for callers that must not allocate memory during the call (a host application
+// whose own allocator owns the device memory and forbids allocations by libraries, or a device
+// so full that a late cudaMalloc of temporaries could fail after the solves are done).
 //
 // The array g_noalloc_scratch lives in this file, is reserved on every device that loads the
 // library, and keeps its contents between calls.  Host code must not use its name as a device
-// address: the address is obtained once per device with cudaGetSymbolAddress.
+// address: the address is obtained once per device with cudaGetSymbolAddress.  The call copies
+// the caller's index arrays from host memory and synchronizes the stream before it returns.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -46,6 +47,7 @@ namespace d3m {
 // accessors to the handle (defined in api.cu)
 int handle_geometry(d3m_handle h, int64_t* n, int32_t* nblk, const int64_t** xoff_orig, const int32_t** m_orig);
 int handle_error(d3m_handle h, int code, const char* msg);
+int handle_device(d3m_handle h);
 }  // namespace d3m
 
 extern "C" int d3m_grad_eps_noalloc(d3m_handle h, const void* Lambda, const void* X, int32_t nrhs, int32_t ndom,
@@ -60,13 +62,23 @@ extern "C" int d3m_grad_eps_noalloc(d3m_handle h, const void* Lambda, const void
   const int64_t* xoff_orig = nullptr;
   const int32_t* m_orig = nullptr;
   handle_geometry(h, &n, &nblk, &xoff_orig, &m_orig);
-  if (nblk > NA_MAX_IF || ndom > NA_MAX_DOM || dom_ptr[ndom] > NA_MAX_DOMIF || dom_ptr[0] != 0)
+  if (nblk > NA_MAX_IF || ndom > NA_MAX_DOM)
     return handle_error(h, D3M_ERR_INVALID,
                         "d3m_grad_eps_noalloc: sizes exceed its fixed scratch (interfaces <= 16384, domains <= "
                         "16384, domain-interface entries <= 98304)");
+  // dom_ptr: starts at 0, nondecreasing (so every entry lies in [0, dom_ptr[ndom]]), and its
+  // total fits the scratch; checked entry by entry before anything is copied or launched, so
+  // the device kernel can only read the entries copied below
+  if (dom_ptr[0] != 0) return handle_error(h, D3M_ERR_INVALID, "d3m_grad_eps_noalloc: dom_ptr[0] must be 0");
   for (int i = 0; i < ndom; ++i)
-    for (int q = dom_ptr[i]; q < dom_ptr[i + 1]; ++q)
-      if (dom_if[q] < 0 || dom_if[q] >= nblk) return handle_error(h, D3M_ERR_INVALID, "dom_if entry out of range");
+    if (dom_ptr[i + 1] < dom_ptr[i])
+      return handle_error(h, D3M_ERR_INVALID, "d3m_grad_eps_noalloc: dom_ptr must be nondecreasing");
+  if (dom_ptr[ndom] > NA_MAX_DOMIF)
+    return handle_error(h, D3M_ERR_INVALID,
+                        "d3m_grad_eps_noalloc: sizes exceed its fixed scratch (interfaces <= 16384, domains <= "
+                        "16384, domain-interface entries <= 98304)");
+  for (int q = 0; q < dom_ptr[ndom]; ++q)
+    if (dom_if[q] < 0 || dom_if[q] >= nblk) return handle_error(h, D3M_ERR_INVALID, "dom_if entry out of range");
   cudaPointerAttributes pa;
   if (cudaPointerGetAttributes(&pa, Lambda) != cudaSuccess || pa.type != cudaMemoryTypeDevice ||
       cudaPointerGetAttributes(&pa, X) != cudaSuccess || pa.type != cudaMemoryTypeDevice) {
@@ -77,6 +89,9 @@ extern "C" int d3m_grad_eps_noalloc(d3m_handle h, const void* Lambda, const void
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NA_MAX_DEVICES)
     return handle_error(h, D3M_ERR_CUDA, "cudaGetDevice failed");
+  if (dev != handle_device(h))
+    return handle_error(h, D3M_ERR_INVALID,
+                        "d3m_grad_eps_noalloc: the current device is not the device the handle was created on");
   if (!g_scratch_ptr[dev]) {
     void* p = nullptr;
     const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
