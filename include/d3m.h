@@ -66,8 +66,11 @@ enum {
   D3M_MIXED_BF16X3 = 1,  /* complex64 factors; Schur/TRSM products on tcgen05 tensor cores as
                             split-BF16x3 (a = a_hi + a_lo; hi*hi + hi*lo + lo*hi) with FP32
                             accumulation in TMEM; FP64 residual + iterative refinement */
-  D3M_MIXED_SIMT32 = 2   /* complex64 factors on an FP32 SIMT tile engine (no tensor cores);
+  D3M_MIXED_SIMT32 = 2,  /* complex64 factors on an FP32 SIMT tile engine (no tensor cores);
                             FP64 residual + iterative refinement */
+  D3M_MIXED_TF32 = 3     /* complex64 factors; Schur/TRSM products on tcgen05 tensor cores as one
+                            kind::tf32 product (operands rounded to tf32, 10-bit mantissa) with
+                            FP32 accumulation in TMEM; FP64 residual + iterative refinement */
 };
 
 typedef struct {
@@ -79,7 +82,7 @@ typedef struct {
 } d3m_pattern;
 
 typedef struct {
-  int32_t precision;        /* D3M_FP64 | D3M_MIXED_BF16X3 | D3M_MIXED_SIMT32 */
+  int32_t precision;        /* D3M_FP64 | D3M_MIXED_BF16X3 | D3M_MIXED_SIMT32 | D3M_MIXED_TF32 */
   int32_t refine_max_iter;  /* cap on refinement steps (default 20) */
   double refine_tol;        /* target normwise backward error omega (default 1e-12) */
   int64_t timeout_ns;       /* bound on any device-side wait (default 5 s) */

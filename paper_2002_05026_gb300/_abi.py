@@ -25,6 +25,7 @@ D3M_ERR_STATE = 7
 D3M_FP64 = 0
 D3M_MIXED_BF16X3 = 1
 D3M_MIXED_SIMT32 = 2
+D3M_MIXED_TF32 = 3
 
 D3M_DEBUG_STALL_LAST_TASK = 1
 D3M_DEBUG_TRACE = 2

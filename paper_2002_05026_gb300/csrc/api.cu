@@ -19,7 +19,7 @@ using namespace d3m;
 struct d3m_ctx {
   Symbolic S;
   d3m_options opt{};
-  bool fp64 = true, tc = false;
+  bool fp64 = true, tc = false, tf32 = false;
   int b = 64;
   int device = 0, nsm = 0;
   size_t csize = 16;                 // bytes of one factor element
@@ -365,7 +365,7 @@ static int create_impl(d3m_handle* out, const d3m_pattern* pat, const int32_t* p
   if (opt) h->opt = *opt;
   else d3m_default_options(&h->opt);
   const int prec = h->opt.precision;
-  if (prec != D3M_FP64 && prec != D3M_MIXED_BF16X3 && prec != D3M_MIXED_SIMT32) {
+  if (prec != D3M_FP64 && prec != D3M_MIXED_BF16X3 && prec != D3M_MIXED_SIMT32 && prec != D3M_MIXED_TF32) {
     delete h;
     return set_err(nullptr, D3M_ERR_INVALID, "unknown precision");
   }
@@ -376,7 +376,8 @@ static int create_impl(d3m_handle* out, const d3m_pattern* pat, const int32_t* p
   if (!(h->opt.prio_slack >= 0)) h->opt.prio_slack = 0.08;
   if (!(h->opt.refine_fwd_tol >= 0)) h->opt.refine_fwd_tol = 1e-10;
   h->fp64 = (prec == D3M_FP64);
-  h->tc = (prec == D3M_MIXED_BF16X3);
+  h->tc = (prec == D3M_MIXED_BF16X3 || prec == D3M_MIXED_TF32);
+  h->tf32 = (prec == D3M_MIXED_TF32);
   h->b = h->tc ? 128 : 64;
   if (h->opt.tile != 0 && h->opt.tile != h->b) {
     delete h;
@@ -465,12 +466,13 @@ static int create_impl(d3m_handle* out, const d3m_pattern* pat, const int32_t* p
   h->Sacc = dalloc<unsigned char>(h, (size_t)std::max<int64_t>(1, S.n_acc) * b * b * h->csize);
   if (!h->L || !h->Linv || !h->D || !h->Sacc) return set_err(h, D3M_ERR_OOM, "cudaMalloc failed for the factor tiles");
   if (h->tc) {
-    // operand planes (bf16): A: [tile][2 splits][2 planes][b rows][b], B: [tile][2][2][b][b]
+    // operand planes, 8 bytes per complex element either way: bf16 A: [tile][2 splits][2 planes]
+    // [b rows][b], B: [tile][2][2][b][b]; tf32 A and B: [tile][2 planes][b rows][b]
     h->opA = dalloc<unsigned char>(h, (size_t)ntiles * 4 * b * b * 2);
     h->opB = dalloc<unsigned char>(h, (size_t)ntiles * 4 * b * b * 2);
     if (!h->opA || !h->opB) return set_err(h, D3M_ERR_OOM, "cudaMalloc failed for the tensor-core operands");
     std::string e2;
-    if (tc_make_maps(h->opA, h->opB, ntiles, &h->maps, e2) != 0) return set_err(h, D3M_ERR_CUDA, e2);
+    if (tc_make_maps(h->opA, h->opB, ntiles, h->tf32, &h->maps, e2) != 0) return set_err(h, D3M_ERR_CUDA, e2);
   }
   // solve
   UPLOAD(h->fwd_items, S.fwd_items);
@@ -785,7 +787,7 @@ static int enqueue_factor(d3m_ctx* h, const void* Kin, bool kdev, cudaStream_t s
   p.piv_tol = 1e3 * (h->fp64 ? 1.1102230246251565e-16 : 5.9604644775390625e-08);
   if (h->trace) CUDA_TRY(h, cudaMemsetAsync(h->trace, 0xff, (size_t)10 * ntiles * sizeof(int64_t), st));
   ev_begin(h, d3m_ctx::EV_FACTOR, st);
-  if (h->tc) rc = launch_factor_tc(p, h->maps, h->nsm, st);
+  if (h->tc) rc = launch_factor_tc(p, h->maps, h->tf32, h->nsm, st);
   else rc = launch_factor_simt(p, h->fp64, h->nsm, st);
   if (rc) return set_err(h, D3M_ERR_CUDA, std::string("factor launch: ") + cudaGetErrorString((cudaError_t)rc));
   ev_end(h, d3m_ctx::EV_FACTOR, st);

@@ -2,19 +2,26 @@
 //
 // Arithmetic: complex64 factors.  Every product of the factorization (the Schur updates
 // S_IJ -= L_IK D_K L_JK^T -- the paper's GEMM tasks, Sec. II -- and the triangular solve
-// L_IJ = S_IJ (D_J^{-1} L_JJ^{-1})^T) runs on the 5th-generation tensor cores as split-BF16x3:
-// a = a_hi + a_lo with a_hi = bf16(a), a_lo = bf16(a - a_hi); a*b ~ a_hi b_hi + a_hi b_lo +
-// a_lo b_hi, accumulated in FP32 in tensor memory (Henry, Tang, Heinecke, "Leveraging the
-// bfloat16 artificial intelligence datatype for higher-precision computations", ARITH 2019).
+// L_IJ = S_IJ (D_J^{-1} L_JJ^{-1})^T) runs on the 5th-generation tensor cores, in one of two
+// engines (template parameter TF):
+//  * split-BF16x3: a = a_hi + a_lo with a_hi = bf16(a), a_lo = bf16(a - a_hi); a*b ~ a_hi b_hi +
+//    a_hi b_lo + a_lo b_hi, accumulated in FP32 in tensor memory (Henry, Tang, Heinecke,
+//    "Leveraging the bfloat16 artificial intelligence datatype for higher-precision
+//    computations", ARITH 2019);
+//  * TF32: each operand rounded once to tf32 (10-bit mantissa, nearest), one kind::tf32 product,
+//    FP32 accumulation; a third of the split products at half the bf16 rate, for a factor
+//    accurate to about 2^-11 that the FP64 refinement then corrects.
 // Complex products use the real embedding with B stored as two 128-row planes [B_r; B_i]: one
 // M=128 x N=256 MMA of A_r over both planes adds [A_r B_r^T | A_r B_i^T] to a 256-column
 // accumulator, and two M=128 x N=128 MMAs of A_i add -A_i B_i^T (the instruction's negate-B
 // bit) to the real half and A_i B_r^T to the imaginary half: [Re | Im] of A B^T.
 //
-// Data movement: every finished L tile is written once, by its owner, as bf16 operand planes
-// (opA: L_IJ [hi_r, hi_i, lo_r, lo_i]; opB: W_IJ = L_IJ D_J as [W_r, W_i] x [hi, lo], or
-// T_J = D_J^{-1} L_JJ^{-1} for a diagonal tile), row-major with the K index contiguous.  TMA
-// tiled loads (64-byte swizzle) stage 32-wide K chunks into shared memory for the MMAs.
+// Data movement: every finished L tile is written once, by its owner, as operand planes
+// (opA: L_IJ; opB: W_IJ = L_IJ D_J, or T_J = D_J^{-1} L_JJ^{-1} for a diagonal tile), row-major
+// with the K index contiguous: bf16 [hi_r, hi_i, lo_r, lo_i] / [hi, lo] x [W_r, W_i] (512 rows of
+// 256 bytes), or tf32 [r, i] (256 rows of 512 bytes), 128 KB per tile either way.  TMA tiled
+// loads (64-byte swizzle) stage K chunks of 64-byte rows (32 bf16 or 16 tf32 elements) into
+// shared memory for the MMAs.
 //
 // Roles inside a 256-thread block: warp 0 lane 0 issues TMA loads, warp 1 lane 0 issues MMAs,
 // all 8 warps run the epilogues (warp w reads TMEM lanes 32*(w%4).., columns half w/4).
@@ -33,26 +40,43 @@ namespace d3m {
 namespace {
 constexpr int TB = 128;
 constexpr int NTHR = 256;
-constexpr int KC = 32;                          // K elements per chunk (64 bytes of bf16)
-constexpr uint32_t PLANE = TB * KC * 2;         // 8 KB: one 128-row plane of one chunk
-constexpr uint32_t STAGE_A = 4 * PLANE;         // 32 KB
-constexpr uint32_t STAGE_B = 4 * PLANE;         // 32 KB
-constexpr uint32_t STAGE = STAGE_A + STAGE_B;   // 64 KB
-constexpr int NSTAGE = 3;                       // GEMM pipeline depth (192 KB)
-constexpr uint32_t SMEM_S = 0;                  // TRSM A operand (4 chunks x 32 KB)
-constexpr uint32_t SMEM_T = 128 * 1024;         // TRSM B stages (2 x 32 KB)
-constexpr uint32_t SMEM_BYTES = NSTAGE * STAGE > SMEM_T + 2 * STAGE_B ? NSTAGE * STAGE : SMEM_T + 2 * STAGE_B;
-constexpr uint32_t BROWS = 512;                 // opB rows per tile: [hi, lo] x [B_r, B_i] x 128
+constexpr uint32_t PLANE = TB * 64;             // 8 KB: one 128-row plane of one chunk (64-byte rows)
+
+// Operand formats of the two engines.  A chunk is 64 bytes of every operand row (the 64-byte
+// swizzle span): 32 bf16 or 16 tf32 elements of K.
+template <bool TF> struct Eng;
+template <> struct Eng<false> {                 // split-BF16x3
+  static constexpr int KC = 32;                 // K elements per chunk
+  static constexpr int NPA = 4, NPB = 4;        // planes per stage: A [hi_r, hi_i, lo_r, lo_i], B [hi, lo] x [r, i]
+  static constexpr int NSTAGE = 3;              // GEMM pipeline depth (3 x 64 KB)
+  static constexpr uint32_t ROWS = 512;         // operand rows of one tile in global memory
+};
+template <> struct Eng<true> {                  // TF32
+  static constexpr int KC = 16;
+  static constexpr int NPA = 2, NPB = 2;        // A [r, i], B [r, i]
+  static constexpr int NSTAGE = 6;              // 6 x 32 KB
+  static constexpr uint32_t ROWS = 256;
+};
+template <bool TF> constexpr uint32_t stage_a() { return Eng<TF>::NPA * PLANE; }
+template <bool TF> constexpr uint32_t stage_b() { return Eng<TF>::NPB * PLANE; }
+template <bool TF> constexpr uint32_t stage_ab() { return stage_a<TF>() + stage_b<TF>(); }
+constexpr uint32_t SMEM_S = 0;                  // TRSM A operand: TB / KC chunks of stage_a (128 KB)
+constexpr uint32_t SMEM_T = 128 * 1024;         // TRSM B stages (2 x stage_b)
+constexpr uint32_t SMEM_BYTES = 192 * 1024;
+static_assert(Eng<false>::NSTAGE * stage_ab<false>() <= SMEM_BYTES && SMEM_T + 2 * stage_b<false>() <= SMEM_BYTES, "smem");
+static_assert(Eng<true>::NSTAGE * stage_ab<true>() <= SMEM_BYTES && SMEM_T + 2 * stage_b<true>() <= SMEM_BYTES, "smem");
+static_assert((TB / Eng<false>::KC) * stage_a<false>() == SMEM_T && (TB / Eng<true>::KC) * stage_a<true>() == SMEM_T, "S");
 constexpr int LDS = 129;                        // c64 diagonal tile row stride (elements)
 constexpr uint32_t DIAG_AUX = 130 * 1024;       // d / column / scratch vectors of a diagonal task
 constexpr uint32_t TMEM_COLS = 512;
 constexpr uint32_t ACC1 = 0, ACC2 = 256;        // TMEM columns of the two accumulators
 
-// instruction descriptors: kind::f16, A/B bf16, D f32, both K-major, M = 128, N = 256 or 128
-// (bit 14: negate B)
-constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((256u >> 3) << 17) | ((128u >> 4) << 24);
-constexpr uint32_t IDESC_N128 = (1u << 4) | (1u << 7) | (1u << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
-constexpr uint32_t IDESC_N128_NEGB = IDESC_N128 | (1u << 14);
+// instruction descriptors: D f32 (bits 4-5 = 1), A and B format (bits 7-9, 10-12: 1 = bf16 for
+// kind::f16, 2 = tf32 for kind::tf32), both K-major, N >> 3 at bit 17, M >> 4 at bit 24 (M = 128,
+// N = 256 or 128); bit 14 negates B
+template <bool TF> constexpr uint32_t idesc(uint32_t n) {
+  return (1u << 4) | ((TF ? 2u : 1u) << 7) | ((TF ? 2u : 1u) << 10) | ((n >> 3) << 17) | ((128u >> 4) << 24);
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -106,20 +130,50 @@ __device__ __forceinline__ uint64_t desc_sw64(uint32_t saddr) {
   d |= (uint64_t)4 << 61;                 // 64-byte swizzle
   return d;
 }
-__device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t accum,
-                                         uint32_t idesc = IDESC) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
-      : "memory");
+template <bool TF>
+__device__ __forceinline__ void mma_tc(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t accum, uint32_t idsc) {
+  if constexpr (TF) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+        "l"(adesc), "l"(bdesc), "r"(idsc), "r"(accum)
+        : "memory");
+  } else {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+        "l"(adesc), "l"(bdesc), "r"(idsc), "r"(accum)
+        : "memory");
+  }
 }
-// [Re | Im] += A B^T for one split pair: A planes a_r, a_i; B planes b (B_r) and b + PLANE (B_i)
+// [Re | Im] += A B^T for one operand pair: A planes a_r, a_i; B planes b (B_r) and b + PLANE (B_i)
 // (accum = 0 on the very first product: the N = 256 MMA initialises every column)
+template <bool TF>
 __device__ __forceinline__ void cmma(uint32_t d, uint32_t a_r, uint32_t a_i, uint32_t b, uint32_t accum) {
-  mma_bf16(d, desc_sw64(a_r), desc_sw64(b), accum);                              // [A_r B_r | A_r B_i]
-  mma_bf16(d, desc_sw64(a_i), desc_sw64(b + PLANE), 1u, IDESC_N128_NEGB);        // Re -= A_i B_i
-  mma_bf16(d + 128, desc_sw64(a_i), desc_sw64(b), 1u, IDESC_N128);               // Im += A_i B_r
+  mma_tc<TF>(d, desc_sw64(a_r), desc_sw64(b), accum, idesc<TF>(256));                          // [A_r B_r | A_r B_i]
+  mma_tc<TF>(d, desc_sw64(a_i), desc_sw64(b + PLANE), 1u, idesc<TF>(128) | (1u << 14));        // Re -= A_i B_i
+  mma_tc<TF>(d + 128, desc_sw64(a_i), desc_sw64(b), 1u, idesc<TF>(128));                       // Im += A_i B_r
+}
+// All products of one staged chunk (64-byte rows; two MMA K-steps of 32 bytes each): A planes at
+// a (stage layout of the engine), B planes at b.  first: the chunk starts the accumulation.
+template <bool TF>
+__device__ __forceinline__ void chunk_mma(uint32_t d, uint32_t a, uint32_t b, bool first) {
+#pragma unroll
+  for (int kk = 0; kk < 2; ++kk) {
+    const uint32_t ko = kk * 32;
+    const uint32_t acc = (first && kk == 0) ? 0u : 1u;
+    if constexpr (TF) {
+      cmma<true>(d, a + ko, a + PLANE + ko, b + ko, acc);
+    } else {
+      const uint32_t a_hr = a + 0 * PLANE + ko, a_hi = a + 1 * PLANE + ko;
+      const uint32_t a_lr = a + 2 * PLANE + ko, a_li = a + 3 * PLANE + ko;
+      const uint32_t bh = b + ko, bl = b + 2 * PLANE + ko;
+      // lo*hi and hi*lo first, then hi*hi
+      cmma<false>(d, a_lr, a_li, bh, acc);
+      cmma<false>(d, a_hr, a_hi, bl, 1u);
+      cmma<false>(d, a_hr, a_hi, bh, 1u);
+    }
+  }
 }
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
@@ -155,6 +209,24 @@ __device__ __forceinline__ uint4 pack8(const __nv_bfloat16* v) {
   u.z = (uint32_t)__bfloat16_as_ushort(v[4]) | ((uint32_t)__bfloat16_as_ushort(v[5]) << 16);
   u.w = (uint32_t)__bfloat16_as_ushort(v[6]) | ((uint32_t)__bfloat16_as_ushort(v[7]) << 16);
   return u;
+}
+
+// Round to tf32 (nearest, ties away; the low 13 bits of the result are zero).
+__device__ __forceinline__ uint32_t tf32_rn(float a) {
+  uint32_t u;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(u) : "f"(a));
+  return u;
+}
+__device__ __forceinline__ uint4 pack4_tf32(const float* v) {
+  return make_uint4(tf32_rn(v[0]), tf32_rn(v[1]), tf32_rn(v[2]), tf32_rn(v[3]));
+}
+// Write 16 K values of row r into a shared-memory K-major SW64 plane (one tf32 chunk).
+__device__ __forceinline__ void store_smem_plane16_tf32(unsigned char* plane, int r, const float* v) {
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const uint32_t off = (uint32_t)r * 64u + ((uint32_t)(q ^ ((r >> 1) & 3)) << 4);
+    *reinterpret_cast<uint4*>(plane + off) = pack4_tf32(v + 4 * q);
+  }
 }
 
 // Write 32 K values of row r into a shared-memory K-major SW64 plane (one chunk) as hi/lo.
@@ -466,9 +538,13 @@ __device__ __forceinline__ void diag_panel_update(float2* sS, const float2* Wt, 
 
 }  // namespace
 
+template <bool TF>
 __global__ void __launch_bounds__(NTHR, 1)
     factor_tc_kernel(const FactorParams p, const __grid_constant__ CUtensorMap mapA,
                      const __grid_constant__ CUtensorMap mapB) {
+  constexpr int KC = Eng<TF>::KC, NSTAGE = Eng<TF>::NSTAGE, NCH = TB / KC;
+  constexpr uint32_t STAGE_A = stage_a<TF>(), STAGE_B = stage_b<TF>(), STAGE = stage_ab<TF>();
+  constexpr uint32_t ROWS = Eng<TF>::ROWS;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   // 1024-byte alignment of the dynamic region (swizzle atoms); pointer arithmetic on the shared
   // array keeps the accesses in the shared address space
@@ -484,8 +560,8 @@ __global__ void __launch_bounds__(NTHR, 1)
   float2* Linv = reinterpret_cast<float2*>(p.Linv);
   float2* Dg = reinterpret_cast<float2*>(p.D);
   float2* Sacc = reinterpret_cast<float2*>(p.Sacc);
-  __nv_bfloat16* opA = reinterpret_cast<__nv_bfloat16*>(p.opA);
-  __nv_bfloat16* opB = reinterpret_cast<__nv_bfloat16*>(p.opB);
+  unsigned char* opA = reinterpret_cast<unsigned char*>(p.opA);
+  unsigned char* opB = reinterpret_cast<unsigned char*>(p.opB);
 
   if (tid == 0) {
     for (int s = 0; s < NSTAGE; ++s) {
@@ -523,7 +599,7 @@ __global__ void __launch_bounds__(NTHR, 1)
     if (task < 0) break;
     const TileTask T = p.tasks[task];
     const uint64_t deadline = globaltimer_ns() + (uint64_t)p.timeout_ns;
-    const int nchunk = T.nk * (TB / KC);
+    const int nchunk = T.nk * NCH;
     asm volatile("fence.proxy.async.global;" ::: "memory");
     // the tile's starting value (its accumulator, or K_IJ: up to 128 contiguous spans) is read
     // after the products; warps 2..5 prefetch it into L2 while they run
@@ -545,15 +621,17 @@ __global__ void __launch_bounds__(NTHR, 1)
           for (int c = 0; c < nchunk && !failed; ++c) {
             const uint32_t s = g_load % NSTAGE, use = g_load / NSTAGE;
             if (!mbar_wait(smem_u32(&bar_empty[s]), (use & 1) ^ 1, deadline)) { failed = true; break; }
-            const KEntry ke = p.klist[T.kl_off + c / (TB / KC)];
-            const int x = (c % (TB / KC)) * KC;
+            const KEntry ke = p.klist[T.kl_off + c / NCH];
+            const int x = (c % NCH) * KC;
             const uint32_t sb = smem_u32(smem + s * STAGE);
             const uint32_t fb = smem_u32(&bar_full[s]);
             mbar_expect_tx(fb, STAGE);
 #pragma unroll
-            for (int q = 0; q < 4; ++q) tma_load_2d(sb + q * PLANE, &mapA, x, ke.a_tile * 512 + q * 128, fb);
+            for (int q = 0; q < Eng<TF>::NPA; ++q)
+              tma_load_2d(sb + q * PLANE, &mapA, x, ke.a_tile * (int)ROWS + q * 128, fb);
 #pragma unroll
-            for (int q = 0; q < 4; ++q) tma_load_2d(sb + STAGE_A + q * PLANE, &mapB, x, ke.b_tile * BROWS + q * 128, fb);
+            for (int q = 0; q < Eng<TF>::NPB; ++q)
+              tma_load_2d(sb + STAGE_A + q * PLANE, &mapB, x, ke.b_tile * (int)ROWS + q * 128, fb);
             ++g_load;
           }
         }
@@ -565,18 +643,7 @@ __global__ void __launch_bounds__(NTHR, 1)
             if (!mbar_wait(smem_u32(&bar_full[s]), use & 1, deadline)) { failed = true; break; }
             tc_fence_after();
             const uint32_t sb = smem_u32(smem + s * STAGE);
-#pragma unroll
-            for (int kk = 0; kk < 2; ++kk) {
-              const uint32_t ko = kk * 32;
-              const uint32_t a_hr = sb + 0 * PLANE + ko, a_hi = sb + 1 * PLANE + ko;
-              const uint32_t a_lr = sb + 2 * PLANE + ko, a_li = sb + 3 * PLANE + ko;
-              const uint32_t bh = sb + STAGE_A + ko, bl = sb + STAGE_A + 2 * PLANE + ko;
-              const uint32_t first = (c == 0 && kk == 0) ? 0u : 1u;
-              // lo*hi and hi*lo first, then hi*hi
-              cmma(tmem + ACC1, a_lr, a_li, bh, first);
-              cmma(tmem + ACC1, a_hr, a_hi, bl, 1u);
-              cmma(tmem + ACC1, a_hr, a_hi, bh, 1u);
-            }
+            chunk_mma<TF>(tmem + ACC1, sb, sb + STAGE_A, c == 0);
             mma_commit(smem_u32(&bar_empty[s]));
             ++g_mma;
           }
@@ -629,7 +696,8 @@ __global__ void __launch_bounds__(NTHR, 1)
         const uint32_t fb = smem_u32(&bar_tfull[s]);
         mbar_expect_tx(fb, STAGE_B);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) tma_load_2d(sb + q * PLANE, &mapB, c * KC, T.diag * BROWS + q * 128, fb);
+        for (int q = 0; q < Eng<TF>::NPB; ++q)
+          tma_load_2d(sb + q * PLANE, &mapB, c * KC, T.diag * (int)ROWS + q * 128, fb);
         ++t_load;
       }
     }
@@ -723,24 +791,38 @@ __global__ void __launch_bounds__(NTHR, 1)
       }
       {
         // T_J = D^{-1} L^{-1}: row n, columns k (X[n][k] = sS[k][n] for k < n); coalesced 16-byte
-        // stores of the planes [T_r, T_i] x [hi, lo] (16 threads per 256-byte plane row)
-        uint4* Bt = reinterpret_cast<uint4*>(opB + (int64_t)T.tile * BROWS * TB);
+        // stores of the planes: bf16 [T_r, T_i] x [hi, lo] (16 threads per 256-byte plane row) or
+        // tf32 [T_r, T_i] (32 threads per 512-byte plane row)
+        uint4* Bt = reinterpret_cast<uint4*>(opB + (int64_t)T.tile * ROWS * TB * (TF ? 4 : 2));
         for (int it = tid; it < TB * 16; it += NTHR) {
           const int n = it >> 4, c8 = it & 15;
           const float2 dinv = cdiv(make_float2(1.f, 0.f), s_d[n]);
-          __nv_bfloat16 h[2][8], lo[2][8];
+          float tr[8], ti[8];
 #pragma unroll
           for (int k8 = 0; k8 < 8; ++k8) {
             const int k = c8 * 8 + k8;
             const float2 lv = (k < n) ? sS[k * LDS + n] : make_float2(k == n ? 1.f : 0.f, 0.f);
             const float2 tv = cmul(dinv, lv);
-            split2(tv.x, h[0][k8], lo[0][k8]);
-            split2(tv.y, h[1][k8], lo[1][k8]);
+            tr[k8] = tv.x;
+            ti[k8] = tv.y;
           }
+          if constexpr (TF) {
+            Bt[(0 * 128 + n) * 32 + 2 * c8] = pack4_tf32(tr);
+            Bt[(0 * 128 + n) * 32 + 2 * c8 + 1] = pack4_tf32(tr + 4);
+            Bt[(1 * 128 + n) * 32 + 2 * c8] = pack4_tf32(ti);
+            Bt[(1 * 128 + n) * 32 + 2 * c8 + 1] = pack4_tf32(ti + 4);
+          } else {
+            __nv_bfloat16 h[2][8], lo[2][8];
 #pragma unroll
-          for (int pl = 0; pl < 2; ++pl) {
-            Bt[((0 * 256 + pl * 128) + n) * 16 + c8] = pack8(h[pl]);
-            Bt[((1 * 256 + pl * 128) + n) * 16 + c8] = pack8(lo[pl]);
+            for (int k8 = 0; k8 < 8; ++k8) {
+              split2(tr[k8], h[0][k8], lo[0][k8]);
+              split2(ti[k8], h[1][k8], lo[1][k8]);
+            }
+#pragma unroll
+            for (int pl = 0; pl < 2; ++pl) {
+              Bt[((0 * 256 + pl * 128) + n) * 16 + c8] = pack8(h[pl]);
+              Bt[((1 * 256 + pl * 128) + n) * 16 + c8] = pack8(lo[pl]);
+            }
           }
         }
       }
@@ -767,9 +849,18 @@ __global__ void __launch_bounds__(NTHR, 1)
             vi[i] = kin[i].y - vi[i];
           }
         }
-        unsigned char* ch = smem + SMEM_S + (c0 / KC) * STAGE_A;
-        store_smem_plane32(ch + 0 * PLANE, ch + 2 * PLANE, r, vr);
-        store_smem_plane32(ch + 1 * PLANE, ch + 3 * PLANE, r, vi);
+        if constexpr (TF) {
+#pragma unroll
+          for (int hh = 0; hh < 2; ++hh) {
+            unsigned char* ch = smem + SMEM_S + (c0 / KC + hh) * STAGE_A;
+            store_smem_plane16_tf32(ch + 0 * PLANE, r, vr + 16 * hh);
+            store_smem_plane16_tf32(ch + 1 * PLANE, r, vi + 16 * hh);
+          }
+        } else {
+          unsigned char* ch = smem + SMEM_S + (c0 / KC) * STAGE_A;
+          store_smem_plane32(ch + 0 * PLANE, ch + 2 * PLANE, r, vr);
+          store_smem_plane32(ch + 1 * PLANE, ch + 3 * PLANE, r, vi);
+        }
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       tc_fence_before();
@@ -778,14 +869,15 @@ __global__ void __launch_bounds__(NTHR, 1)
       // ---------------------------------------------------------------- phase 3: TRSM product
       if (warp == 0) {
         if (lane == 0) {
-          for (int c = 2; c < TB / KC && !failed; ++c) {
+          for (int c = 2; c < NCH && !failed; ++c) {
             const uint32_t s = t_load & 1, use = t_load >> 1;
             if (!mbar_wait(smem_u32(&bar_tempty[s]), (use & 1) ^ 1, deadline)) { failed = true; break; }
             const uint32_t sb = smem_u32(smem + SMEM_T + s * STAGE_B);
             const uint32_t fb = smem_u32(&bar_tfull[s]);
             mbar_expect_tx(fb, STAGE_B);
 #pragma unroll
-            for (int q = 0; q < 4; ++q) tma_load_2d(sb + q * PLANE, &mapB, c * KC, T.diag * BROWS + q * 128, fb);
+            for (int q = 0; q < Eng<TF>::NPB; ++q)
+              tma_load_2d(sb + q * PLANE, &mapB, c * KC, T.diag * (int)ROWS + q * 128, fb);
             ++t_load;
           }
         }
@@ -793,23 +885,13 @@ __global__ void __launch_bounds__(NTHR, 1)
       } else if (warp == 1) {
         if (lane == 0) {
           tc_fence_after();
-          for (int c = 0; c < TB / KC && !failed; ++c) {
+          for (int c = 0; c < NCH && !failed; ++c) {
             const uint32_t s = t_mma & 1, use = t_mma >> 1;
             if (!mbar_wait(smem_u32(&bar_tfull[s]), use & 1, deadline)) { failed = true; break; }
             tc_fence_after();
             const uint32_t ab = smem_u32(smem + SMEM_S + c * STAGE_A);
             const uint32_t tb = smem_u32(smem + SMEM_T + s * STAGE_B);
-#pragma unroll
-            for (int kk = 0; kk < 2; ++kk) {
-              const uint32_t ko = kk * 32;
-              const uint32_t a_hr = ab + 0 * PLANE + ko, a_hi = ab + 1 * PLANE + ko;
-              const uint32_t a_lr = ab + 2 * PLANE + ko, a_li = ab + 3 * PLANE + ko;
-              const uint32_t bh = tb + ko, bl = tb + 2 * PLANE + ko;
-              const uint32_t first = (c == 0 && kk == 0) ? 0u : 1u;
-              cmma(tmem + ACC2, a_lr, a_li, bh, first);
-              cmma(tmem + ACC2, a_hr, a_hi, bl, 1u);
-              cmma(tmem + ACC2, a_hr, a_hi, bh, 1u);
-            }
+            chunk_mma<TF>(tmem + ACC2, ab, tb, c == 0);
             mma_commit(smem_u32(&bar_tempty[s]));
             ++t_mma;
           }
@@ -849,8 +931,8 @@ __global__ void __launch_bounds__(NTHR, 1)
         const int rr = e >> 6, u = e & 63;
         Lt4[e] = stg[rr * 64 + (u ^ (rr & 7))];
       }
-      uint4* A = reinterpret_cast<uint4*>(opA + (int64_t)T.tile * 512 * TB);
-      uint4* B = reinterpret_cast<uint4*>(opB + (int64_t)T.tile * BROWS * TB);
+      uint4* A = reinterpret_cast<uint4*>(opA + (int64_t)T.tile * ROWS * TB * (TF ? 4 : 2));
+      uint4* B = reinterpret_cast<uint4*>(opB + (int64_t)T.tile * ROWS * TB * (TF ? 4 : 2));
       for (int it = tid; it < TB * 16; it += NTHR) {
         const int rr = it >> 4, c8 = it & 15;   // row, group of 8 columns
         float2 l[8];
@@ -861,25 +943,41 @@ __global__ void __launch_bounds__(NTHR, 1)
           l[2 * k] = make_float2(v.x, v.y);
           l[2 * k + 1] = make_float2(v.z, v.w);
         }
-        __nv_bfloat16 h[4][8], lo[4][8];   // planes: L_r, L_i, W_r, W_i
+        float pv[4][8];   // planes: L_r, L_i, W_r, W_i
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
           const float2 w = cmul(l[k], s_d[c8 * 8 + k]);
-          split2(l[k].x, h[0][k], lo[0][k]);
-          split2(l[k].y, h[1][k], lo[1][k]);
-          split2(w.x, h[2][k], lo[2][k]);
-          split2(w.y, h[3][k], lo[3][k]);
+          pv[0][k] = l[k].x;
+          pv[1][k] = l[k].y;
+          pv[2][k] = w.x;
+          pv[3][k] = w.y;
         }
-        // opA rows: split * 256 + plane * 128 + row; 16 uint4 per 256-byte row
-        A[((0 * 256 + 0 * 128) + rr) * 16 + c8] = pack8(h[0]);
-        A[((0 * 256 + 1 * 128) + rr) * 16 + c8] = pack8(h[1]);
-        A[((1 * 256 + 0 * 128) + rr) * 16 + c8] = pack8(lo[0]);
-        A[((1 * 256 + 1 * 128) + rr) * 16 + c8] = pack8(lo[1]);
-        // opB rows: split * 256 + plane * 128 + row (planes W_r, W_i)
+        if constexpr (TF) {
+          // opA rows: plane * 128 + row (L_r, L_i); opB rows: the same for W; 32 uint4 per 512-byte row
 #pragma unroll
-        for (int pl = 0; pl < 2; ++pl) {
-          B[((0 * 256 + pl * 128) + rr) * 16 + c8] = pack8(h[2 + pl]);
-          B[((1 * 256 + pl * 128) + rr) * 16 + c8] = pack8(lo[2 + pl]);
+          for (int pl = 0; pl < 2; ++pl) {
+            A[(pl * 128 + rr) * 32 + 2 * c8] = pack4_tf32(pv[pl]);
+            A[(pl * 128 + rr) * 32 + 2 * c8 + 1] = pack4_tf32(pv[pl] + 4);
+            B[(pl * 128 + rr) * 32 + 2 * c8] = pack4_tf32(pv[2 + pl]);
+            B[(pl * 128 + rr) * 32 + 2 * c8 + 1] = pack4_tf32(pv[2 + pl] + 4);
+          }
+        } else {
+          __nv_bfloat16 h[4][8], lo[4][8];
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int k = 0; k < 8; ++k) split2(pv[q][k], h[q][k], lo[q][k]);
+          // opA rows: split * 256 + plane * 128 + row; 16 uint4 per 256-byte row
+          A[((0 * 256 + 0 * 128) + rr) * 16 + c8] = pack8(h[0]);
+          A[((0 * 256 + 1 * 128) + rr) * 16 + c8] = pack8(h[1]);
+          A[((1 * 256 + 0 * 128) + rr) * 16 + c8] = pack8(lo[0]);
+          A[((1 * 256 + 1 * 128) + rr) * 16 + c8] = pack8(lo[1]);
+          // opB rows: split * 256 + plane * 128 + row (planes W_r, W_i)
+#pragma unroll
+          for (int pl = 0; pl < 2; ++pl) {
+            B[((0 * 256 + pl * 128) + rr) * 16 + c8] = pack8(h[2 + pl]);
+            B[((1 * 256 + pl * 128) + rr) * 16 + c8] = pack8(lo[2 + pl]);
+          }
         }
       }
       __syncthreads();
@@ -906,7 +1004,7 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
-int tc_make_maps(void* opA, void* opB, int64_t ntiles, TcMaps* out, std::string& err) {
+int tc_make_maps(void* opA, void* opB, int64_t ntiles, bool tf32, TcMaps* out, std::string& err) {
   static EncodeTiledFn encode = nullptr;
   if (!encode) {
     cudaDriverEntryPointQueryResult q;
@@ -920,18 +1018,19 @@ int tc_make_maps(void* opA, void* opB, int64_t ntiles, TcMaps* out, std::string&
     encode = (EncodeTiledFn)fn;
   }
   static_assert(sizeof(CUtensorMap) == 128, "CUtensorMap size");
-  const cuuint32_t box[2] = {(cuuint32_t)KC, (cuuint32_t)TB};
+  // rows of 128 elements (256 bytes bf16, 512 bytes tf32); a box is one chunk (64 bytes) of 128 rows
+  const int esz = tf32 ? 4 : 2;
+  const cuuint64_t rows = (cuuint64_t)(tf32 ? Eng<true>::ROWS : Eng<false>::ROWS);
+  const cuuint32_t box[2] = {(cuuint32_t)(64 / esz), (cuuint32_t)TB};
   const cuuint32_t estr[2] = {1, 1};
-  const cuuint64_t stride[1] = {(cuuint64_t)TB * 2};
+  const cuuint64_t stride[1] = {(cuuint64_t)TB * esz};
+  const CUtensorMapDataType dt = tf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
   CUtensorMap ma, mb;
-  const cuuint64_t dimA[2] = {(cuuint64_t)TB, (cuuint64_t)ntiles * 512};
-  const cuuint64_t dimB[2] = {(cuuint64_t)TB, (cuuint64_t)ntiles * BROWS};
-  CUresult r1 = encode(&ma, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, opA, dimA, stride, box, estr,
-                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  CUresult r2 = encode(&mb, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, opB, dimB, stride, box, estr,
-                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  const cuuint64_t dim[2] = {(cuuint64_t)TB, (cuuint64_t)ntiles * rows};
+  CUresult r1 = encode(&ma, dt, 2, opA, dim, stride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                       CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  CUresult r2 = encode(&mb, dt, 2, opB, dim, stride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                       CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r1 != CUDA_SUCCESS || r2 != CUDA_SUCCESS) {
     err = "cuTensorMapEncodeTiled failed (" + std::to_string((int)r1) + ", " + std::to_string((int)r2) + ")";
     return 1;
@@ -941,14 +1040,15 @@ int tc_make_maps(void* opA, void* opB, int64_t ntiles, TcMaps* out, std::string&
   return 0;
 }
 
-int launch_factor_tc(const FactorParams& p, const TcMaps& maps, int nblocks, cudaStream_t st) {
+int launch_factor_tc(const FactorParams& p, const TcMaps& maps, bool tf32, int nblocks, cudaStream_t st) {
   const size_t smem = SMEM_BYTES + 1024;   // + alignment slack
-  cudaError_t e = cudaFuncSetAttribute(factor_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  auto kern = tf32 ? factor_tc_kernel<true> : factor_tc_kernel<false>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return (int)e;
   CUtensorMap ma, mb;
   std::memcpy(&ma, maps.a, 128);
   std::memcpy(&mb, maps.b, 128);
-  factor_tc_kernel<<<nblocks, NTHR, smem, st>>>(p, ma, mb);
+  kern<<<nblocks, NTHR, smem, st>>>(p, ma, mb);
   return (int)cudaGetLastError();
 }
 

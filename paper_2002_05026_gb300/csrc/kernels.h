@@ -83,6 +83,51 @@ struct SweepLaunch {
   int64_t launches;                // out: kernels launched by launch_sweep
 };
 
+// FP64-accurate residual on the tensor cores (resid_tc.cu): digit planes of K and x.
+struct ResidualTc {
+  const double2* K;              // stored lower blocks (c128), read by the digit kernels only
+  const int64_t* kblk_off;       // [nnzb+1]
+  const int32_t* blk_row;        // [nnzb] row block f of every stored block (caller numbering)
+  const int32_t* blk_col;        // [nnzb] column block g
+  const int32_t* m_orig;         // [N]
+  const int64_t* xoff_orig;      // [N]
+  const int64_t* res_ptr;        // [N+1] residual contributions of every row block
+  const int32_t* res_row;        // [contributions] row block f
+  const int32_t* res_src;        // [contributions] source block g
+  const int32_t* res_blk;        // [contributions] stored block
+  const int32_t* res_tr;         // [contributions] 1: the stored block is used transposed
+  const int64_t* ks_plane;       // [contributions] first K digit plane
+  const int64_t* xs_plane;       // [N] first x digit plane of block g
+  const int2* rtiles;            // [row tiles] (row block f, 128-row tile)
+  unsigned short* kdig;          // K digit planes (bf16), 128 x 32 each
+  unsigned short* xdig;          // x digit planes (bf16), 64 x 32 each
+  unsigned long long* Kmax_bits; // [nnzb] max |Re|, |Im| of every stored block (double bits)
+  double2* Kdiag;                // [n] diagonal entries of K (applied in FP64)
+  float* rowsum;                 // [n] row sums of |K| (for ||K||_inf)
+  int* xT;                       // [N][32] scale exponents of the x blocks (one group of 32 rhs)
+  int64_t n;
+  const int32_t* inst;           // [N] instance of every block
+  const int* done;               // [instances] converged instances are skipped (or nullptr)
+  int ld_norm;
+  unsigned* rmax;                // [instances][ld_norm] max |r| as float bits
+  unsigned* xmax;
+  unsigned* bmax;
+  unsigned* kmax;                // [instances] ||K_i||_inf
+  int* status;                   // device word: D3M_ERR_TIMEOUT if a bounded wait expired
+  int64_t timeout_ns;
+};
+
+struct ResidTcMaps {
+  alignas(64) unsigned char a[128];
+  alignas(64) unsigned char b[4][128];
+};
+
+int resid_tc_make_maps(void* kdig, int64_t nplanes_a, void* xdig, int64_t nplanes_b, ResidTcMaps* out,
+                       std::string& err);
+int launch_kdigits(const ResidualTc& p, int nnzb, int nres, int max_rtiles, int nblk, cudaStream_t st);
+int launch_resid_tc(const ResidualTc& p, const ResidTcMaps& maps, const double2* X, const double2* B, double2* R,
+                    int nrhs, int nrtiles, int nblk, cudaStream_t st, int64_t* launches);
+
 // Tensor maps (CUtensorMap, 128 bytes each) of the tensor-core operand planes.
 struct TcMaps {
   alignas(64) unsigned char a[128];
@@ -90,8 +135,9 @@ struct TcMaps {
 };
 
 int launch_factor_simt(const FactorParams& p, bool fp64, int nblocks, cudaStream_t st);
-int tc_make_maps(void* opA, void* opB, int64_t ntiles, TcMaps* out, std::string& err);
-int launch_factor_tc(const FactorParams& p, const TcMaps& maps, int nblocks, cudaStream_t st);
+// tf32 = false: bf16 planes of the split-BF16x3 engine; true: tf32 planes
+int tc_make_maps(void* opA, void* opB, int64_t ntiles, bool tf32, TcMaps* out, std::string& err);
+int launch_factor_tc(const FactorParams& p, const TcMaps& maps, bool tf32, int nblocks, cudaStream_t st);
 int launch_sweep(SweepLaunch& a, bool fp64, cudaStream_t st);
 // Inverses of the unit-lower diagonal blocks (c64 tiles of edge b in {64, 128}), built from L and
 // the inverses of the diagonal tiles: work = (block, tile column) pairs.

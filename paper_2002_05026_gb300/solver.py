@@ -14,7 +14,8 @@ import numpy as np
 from . import _abi
 from ._abi import check, load
 
-PRECISIONS = {"fp64": _abi.D3M_FP64, "bf16x3": _abi.D3M_MIXED_BF16X3, "simt32": _abi.D3M_MIXED_SIMT32}
+PRECISIONS = {"fp64": _abi.D3M_FP64, "bf16x3": _abi.D3M_MIXED_BF16X3, "simt32": _abi.D3M_MIXED_SIMT32,
+              "tf32": _abi.D3M_MIXED_TF32}
 
 
 def _stream_ptr(stream=None) -> int:

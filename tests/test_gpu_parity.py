@@ -6,8 +6,9 @@ Bars:
 * mixed paths after FP64 refinement: relative forward error <= 1e-9 per column and normwise
   backward error omega <= 1e-12, omega recomputed by the oracle from the returned X;
 * mixed-path factors are complex64 with split-BF16x3 products (about 2^-16 relative per
-  product), so they are compared with a loose 5e-3 relative bound that still catches any
-  structural error (wrong tile, sign, transpose or pivot).
+  product) or TF32 products (operands rounded to 11 significant bits, about 2^-11 relative per
+  product), so they are compared with loose relative bounds (5e-3, 2e-2 for TF32) that still
+  catch any structural error (wrong tile, sign, transpose or pivot).
 """
 import numpy as np
 import pytest
@@ -97,7 +98,7 @@ def test_fp64_natural_order_and_omega(torch_cuda):
     assert s.info()["omega"] <= 1e-14
 
 
-@pytest.mark.parametrize("precision", ["simt32", "bf16x3"])
+@pytest.mark.parametrize("precision", ["simt32", "bf16x3", "tf32"])
 @pytest.mark.parametrize("g,m", [((2, 2, 1), 64), ((3, 3, 1), 100), ((2, 2, 2), 128), ((1, 3, 1), 1),
                                  ((4, 4, 1), 128), ((3, 2, 1), 200)])
 def test_mixed_refined_solution(torch_cuda, precision, g, m):
@@ -110,19 +111,25 @@ def test_mixed_refined_solution(torch_cuda, precision, g, m):
     info = s.info()
     assert info["status"] == 0 and info["omega"] <= 1e-12
     eL, eD, _ = _factor_err(s, F, m)
-    assert eL <= 5e-3 and eD <= 5e-3, (eL, eD)
+    bound = 2e-2 if precision == "tf32" else 5e-3
+    assert eL <= bound and eD <= bound, (eL, eD)
 
 
 def test_mixed_factor_accuracy_simt_vs_tc(torch_cuda):
-    # the FP32 SIMT factor is at FP32 level; the split-BF16x3 factor within ~2^-16 * growth
+    # the FP32 SIMT factor is at FP32 level; the split-BF16x3 factor within ~2^-16 * growth; the
+    # TF32 factor within ~2^-11 * growth, and measurably less accurate than split-BF16x3 (each
+    # engine really computes in its own precision)
     p, pm, Kb, F = _setup((3, 3, 1), 128, k2=2.0, tau=0.05, seed=3)
     B = synth.rhs(9, p.n, 1)
     s1, _ = _run(torch_cuda, p, pm, "simt32", B)
     s2, _ = _run(torch_cuda, p, pm, "bf16x3", B)
+    s3, _ = _run(torch_cuda, p, pm, "tf32", B)
     e1 = _factor_err(s1, F, 128)[0]
     e2 = _factor_err(s2, F, 128)[0]
+    e3 = _factor_err(s3, F, 128)[0]
     assert e1 <= 1e-5, e1
     assert e2 <= 2e-4, e2
+    assert 5 * e2 <= e3 <= 5e-3, (e2, e3)
 
 
 def test_decoupled_blocks(torch_cuda):
@@ -210,7 +217,7 @@ def test_refactor_same_handle(torch_cuda):
         assert _fwd_err(X, O.block_solve(F, B)) <= 1e-9
 
 
-@pytest.mark.parametrize("precision", ["fp64", "bf16x3"])
+@pytest.mark.parametrize("precision", ["fp64", "bf16x3", "tf32"])
 def test_full_interface_size_many_rhs(torch_cuda, precision):
     # m = 512 as in the 8x8 and 6x6x6 workloads: the in-block chains span 4 (8) tiles of 128
     # (64) rows, i.e. 8 row strips per interface block, one cluster of 8 CTAs per block;
@@ -232,7 +239,7 @@ def _omega_extended(Kb, nblk, m, X, B):
     return (np.abs(R).max(axis=0) / (kn * np.abs(X).max(axis=0) + np.abs(B).max(axis=0))).astype(np.float64)
 
 
-@pytest.mark.parametrize("precision", ["fp64", "bf16x3"])
+@pytest.mark.parametrize("precision", ["fp64", "bf16x3", "tf32"])
 @pytest.mark.parametrize("g,m", [((3, 3, 1), 100), ((2, 2, 2), 128)])
 def test_device_omega_matches_extended_precision(torch_cuda, precision, g, m):
     # the device residual (double-float products, FP64 accumulation) reports the backward
