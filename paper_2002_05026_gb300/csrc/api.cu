@@ -44,12 +44,6 @@ struct d3m_ctx {
   int64_t launches = 0;
   // factor data
   double2* K = nullptr;
-  float4* K2 = nullptr;              // double-float split of K for the residual
-  float4* K2T = nullptr;             // the split of the transposed off-diagonal blocks
-  int64_t* res_ktoff = nullptr;      // per residual entry: its transposed block in K2T
-  double2* part_acc = nullptr;       // residual partial sums [2][n * max_nrhs]
-  int* part_cnt = nullptr;           // residual arrival counters [chunks * rhs groups]
-  float4* X2 = nullptr;              // double-float split of x, n x max_nrhs
   TileTask* tasks = nullptr;
   KEntry* klist = nullptr;
   int32_t* ndeps = nullptr;
@@ -111,8 +105,6 @@ struct d3m_ctx {
   int32_t* res_tr = nullptr;
   int32_t* m_orig = nullptr;
   int64_t* xoff_orig = nullptr;
-  int2* chunks = nullptr;
-  int nchunks = 0;
   unsigned* norms = nullptr;         // [3 * ninst * max_nrhs + ninst]: rmax, xmax, bmax, kmax
   double* omega_dev = nullptr;       // [ninst][max_nrhs]
   double* stat_dev = nullptr;        // [3]: max omega, instances still refining, their progress measure
@@ -125,6 +117,11 @@ struct d3m_ctx {
   int32_t* blk_col = nullptr;
   int64_t* colptr = nullptr;
   double2* contract = nullptr;
+  // FP64-accurate residual on the tensor cores: digit planes of K (per factorization) and x
+  ResidualTc rtc{};
+  ResidTcMaps rtc_maps;
+  std::vector<int2> rtile_host;      // (row block f, 128-row tile)
+  int max_rtiles = 1;
   // batched handles: independent systems stored as one block-diagonal system
   int ninst = 1;
   std::vector<int32_t> inst_blk;     // [ninst+1] first block (caller numbering) of each instance
@@ -428,7 +425,6 @@ static int create_impl(d3m_handle* out, const d3m_pattern* pat, const int32_t* p
     if (rc_ != D3M_OK) return rc_;              \
   } while (0)
   // factorization (h->K, the copy target of a host K, is allocated by the first call that needs it)
-  ALLOC(h->K2, float4, S.kblk_off.back());
   UPLOAD(h->tasks, S.tasks);
   UPLOAD(h->klist, S.klist);
   {
@@ -573,36 +569,70 @@ static int create_impl(d3m_handle* out, const d3m_pattern* pat, const int32_t* p
   ALLOC(h->d_x, double2, S.n * mr);
   ALLOC(h->d_xbest, double2, S.n * mr);
   ALLOC(h->d_r, double2, S.n * mr);
-  ALLOC(h->X2, float4, S.n * mr);
-  ALLOC(h->part_acc, double2, 2 * S.n * mr);
   UPLOAD(h->kblk_off, S.kblk_off);
   UPLOAD(h->res_ptr, S.res_ptr);
   UPLOAD(h->res_blk, S.res_blk);
   UPLOAD(h->res_src, S.res_src);
   UPLOAD(h->res_tr, S.res_tr);
   {
-    // transposed copies of the off-diagonal stored blocks, one per transposed residual entry
-    std::vector<int64_t> kt(S.res_tr.size(), -1);
-    int64_t tot = 0;
+    // residual digit planes: per contribution e of row block f from block g, ceil(m_f / 128) row
+    // tiles x ceil(m_g / 32) chunks x 2 parts x 9 digits planes of 128 x 32 bf16; per block g,
+    // ceil(m_g / 32) chunks x 2 x 9 planes of 64 x 32 bf16 for the digits of x
+    const int64_t nres = (int64_t)S.res_blk.size();
+    std::vector<int64_t> ksp(nres), xsp(S.N);
+    std::vector<int32_t> rrow(nres), brow(S.nnzb_K), bcol(S.nnzb_K);
+    int64_t pa = 0, pb = 0;
     for (int f = 0; f < S.N; ++f)
-      for (int64_t e = S.res_ptr[f]; e < S.res_ptr[f + 1]; ++e)
-        if (S.res_tr[e]) {
-          kt[e] = tot;
-          tot += (int64_t)S.m_orig[f] * S.m_orig[S.res_src[e]];
-        }
-    UPLOAD(h->res_ktoff, kt);
-    ALLOC(h->K2T, float4, std::max<int64_t>(1, tot));
+      for (int64_t e = S.res_ptr[f]; e < S.res_ptr[f + 1]; ++e) {
+        ksp[e] = pa;
+        rrow[e] = f;
+        pa += (int64_t)((S.m_orig[f] + 127) / 128) * ((S.m_orig[S.res_src[e]] + 31) / 32) * 2 * kResidDigits;
+      }
+    for (int g = 0; g < S.N; ++g) {
+      xsp[g] = pb;
+      pb += (int64_t)((S.m_orig[g] + 31) / 32) * 2 * kResidDigits;
+      for (int64_t q = S.colptr[g]; q < S.colptr[g + 1]; ++q) {
+        brow[q] = S.rowidx[q];
+        bcol[q] = g;
+      }
+      for (int r = 0; r < S.m_orig[g]; r += 128) h->rtile_host.push_back(make_int2(g, r / 128));
+      h->max_rtiles = std::max(h->max_rtiles, (S.m_orig[g] + 127) / 128);
+    }
+    if (pa >= (int64_t)1 << 31 || pb >= (int64_t)1 << 31)
+      return set_err(h, D3M_ERR_INVALID, "K too large for the residual's digit planes (2^31 planes)");
+    ResidualTc& r = h->rtc;
+    int64_t* d_ksp = nullptr;
+    int64_t* d_xsp = nullptr;
+    int32_t *d_rrow = nullptr, *d_brow = nullptr, *d_bcol = nullptr;
+    int2* d_rt = nullptr;
+    UPLOAD(d_ksp, ksp);
+    UPLOAD(d_xsp, xsp);
+    UPLOAD(d_rrow, rrow);
+    UPLOAD(d_brow, brow);
+    UPLOAD(d_bcol, bcol);
+    UPLOAD(d_rt, h->rtile_host);
+    r.ks_plane = d_ksp;
+    r.xs_plane = d_xsp;
+    r.res_row = d_rrow;
+    r.blk_row = d_brow;
+    r.blk_col = d_bcol;
+    r.rtiles = d_rt;
+    int nr_grp = 8;
+    const int ngrp = resid_tc_groups(mr, &nr_grp);   // the most groups any nrhs <= max_nrhs uses
+    r.xs_total = pb;
+    r.nblk = S.N;
+    ALLOC(r.kdig, unsigned short, pa * 128 * 32);
+    ALLOC(r.xdig, unsigned short, pb * ngrp * 64 * 32);
+    ALLOC(r.Kmax_bits, unsigned long long, S.nnzb_K);
+    ALLOC(r.Kdiag, double2, S.n);
+    ALLOC(r.rowsum, float, S.n);
+    ALLOC(r.xT, int, (size_t)ngrp * S.N * 32);
+    std::string e3;
+    if (resid_tc_make_maps(r.kdig, pa, r.xdig, pb * ngrp, &h->rtc_maps, e3) != 0) return set_err(h, D3M_ERR_CUDA, e3);
   }
   UPLOAD(h->m_orig, S.m_orig);
   UPLOAD(h->xoff_orig, S.xoff_orig);
   {
-    std::vector<int2> ch;
-    for (int f = 0; f < S.N; ++f)
-      for (int r = 0; r < S.m_orig[f]; r += 32) ch.push_back(make_int2(f, r));
-    h->nchunks = (int)ch.size();
-    UPLOAD(h->chunks, ch);
-    ALLOC(h->part_cnt, int, (size_t)h->nchunks * mr);
-    CUDA_TRY(h, cudaMemset(h->part_cnt, 0, (size_t)h->nchunks * mr * sizeof(int)));
     std::vector<int32_t> bc(S.nnzb_K);
     for (int g = 0; g < S.N; ++g)
       for (int64_t p = S.colptr[g]; p < S.colptr[g + 1]; ++p) bc[p] = g;
@@ -706,38 +736,28 @@ int d3m_get_instance_omega(d3m_handle h, double* host_out, void* stream) {
   return D3M_OK;
 }
 
-static ResidualParams residual_params(d3m_ctx* h, const double2* X, const double2* B, int nrhs) {
-  ResidualParams p;
-  p.K = h->K;
-  p.K2 = h->K2;
-  p.K2T = h->K2T;
-  p.res_ktoff = h->res_ktoff;
-  p.part_acc = h->part_acc;
-  p.part_ld = h->S.n * (int64_t)h->opt.max_nrhs;
-  p.part_cnt = h->part_cnt;
-  p.X2 = h->X2;
+// parameters of the tensor-core residual (digit planes and geometry are fixed at create time)
+static ResidualTc resid_params(d3m_ctx* h, const double2* K) {
+  ResidualTc p = h->rtc;
+  p.K = K;
   p.kblk_off = h->kblk_off;
-  p.res_ptr = h->res_ptr;
-  p.res_blk = h->res_blk;
-  p.res_src = h->res_src;
-  p.res_tr = h->res_tr;
   p.m_orig = h->m_orig;
   p.xoff_orig = h->xoff_orig;
-  p.chunks = h->chunks;
-  p.nrhs = nrhs;
+  p.res_ptr = h->res_ptr;
+  p.res_src = h->res_src;
+  p.res_blk = h->res_blk;
+  p.res_tr = h->res_tr;
   p.n = h->S.n;
-  p.X = X;
-  p.B = B;
-  p.R = h->d_r;
   const int mr = h->opt.max_nrhs, ni = h->ninst;
   p.inst = h->inst;
   p.done = h->done;
-  p.tol = h->opt.refine_tol;
   p.ld_norm = mr;
   p.rmax = h->norms;
   p.xmax = h->norms + (size_t)ni * mr;
   p.bmax = h->norms + 2 * (size_t)ni * mr;
   p.kmax = h->norms + 3 * (size_t)ni * mr;
+  p.status = h->sweep_status;
+  p.timeout_ns = h->opt.timeout_ns;
   return p;
 }
 
@@ -792,16 +812,18 @@ static int enqueue_factor(d3m_ctx* h, const void* Kin, bool kdev, cudaStream_t s
   if (rc) return set_err(h, D3M_ERR_CUDA, std::string("factor launch: ") + cudaGetErrorString((cudaError_t)rc));
   ev_end(h, d3m_ctx::EV_FACTOR, st);
   h->launches += 1;
-  // ||K_i||_inf and the split of K (for the residual) on a second stream, concurrently with the
-  // block inverses: the persistent factorization holds every SM, the two smaller kernels share them
+  // ||K_i||_inf and the digit planes of K (for the residual) on a second stream, concurrently
+  // with the block inverses: the persistent factorization holds every SM, the smaller kernels
+  // share them
   CUDA_TRY(h, cudaEventRecord(h->ev_fork, st));
   CUDA_TRY(h, cudaStreamWaitEvent(h->side, h->ev_fork, 0));
-  ResidualParams rp = residual_params(h, nullptr, nullptr, 1);
-  rp.K = Ksrc;
-  CUDA_TRY(h, cudaMemsetAsync(rp.kmax, 0, h->ninst * sizeof(unsigned), h->side));
-  rc = launch_knorm(rp, h->nchunks, h->side);
-  if (rc) return set_err(h, D3M_ERR_CUDA, std::string("knorm launch: ") + cudaGetErrorString((cudaError_t)rc));
-  h->launches += 1;
+  {
+    ResidualTc rp = resid_params(h, Ksrc);
+    CUDA_TRY(h, cudaMemsetAsync(rp.kmax, 0, h->ninst * sizeof(unsigned), h->side));
+    rc = launch_kdigits(rp, (int)S.nnzb_K, (int)S.res_blk.size(), h->max_rtiles, S.N, h->side);
+    if (rc) return set_err(h, D3M_ERR_CUDA, std::string("K digit launch: ") + cudaGetErrorString((cudaError_t)rc));
+    h->launches += 3;
+  }
   CUDA_TRY(h, cudaEventRecord(h->ev_join, h->side));
   if (h->use_inv && h->n_inv_work > 0) {
     rc = launch_inv_build(h->inv_work, h->n_inv_work, h->tstart, h->tcolptr, h->inv_off, h->invT_off, h->L, h->Linv,
@@ -896,11 +918,13 @@ static int sweep(d3m_ctx* h, const double2* src, double2* dst, int nrhs, int acc
 static int residual_omega(d3m_ctx* h, const double2* X, const double2* B, int nrhs, cudaStream_t st) {
   const int mr = h->opt.max_nrhs, ni = h->ninst;
   CUDA_TRY(h, cudaMemsetAsync(h->norms, 0, 3 * (size_t)ni * mr * sizeof(unsigned), st));
-  ResidualParams rp = residual_params(h, X, B, nrhs);
+  ResidualTc rp = resid_params(h, nullptr);
   ev_begin(h, d3m_ctx::EV_RESID, st);
-  int rc = launch_residual(rp, h->nchunks, st);
+  int64_t nl = 0;
+  int rc = launch_resid_tc(rp, h->rtc_maps, X, B, h->d_r, nrhs, (int)h->rtile_host.size(), h->S.N, st, &nl);
   if (rc) return set_err(h, D3M_ERR_CUDA, std::string("residual launch: ") + cudaGetErrorString((cudaError_t)rc));
   ev_end(h, d3m_ctx::EV_RESID, st);
+  h->launches += nl;
   rc = launch_omega(rp.rmax, rp.xmax, rp.bmax, rp.kmax, h->dmax, h->dprev, ni, mr, nrhs, h->done, h->opt.refine_tol,
                     h->opt.refine_fwd_tol, h->omega_dev, h->stat_dev, st);
   h->last_nrhs = nrhs;

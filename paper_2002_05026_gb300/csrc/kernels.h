@@ -11,38 +11,6 @@ namespace d3m {
 
 struct FactorParams;
 
-struct ResidualParams {
-  const double2* K;
-  const float4* K2;        // double-float split of K (hi_r, hi_i, lo_r, lo_i), K's layout
-  const float4* K2T;       // the same split of the transposed off-diagonal blocks
-  const int64_t* res_ktoff;  // [residual entries] offset of a transposed entry's block in K2T
-  double2* part_acc;       // [2][part_ld] partial sums of the blocks sharing a row chunk
-  int64_t part_ld;         // n * max_nrhs
-  int* part_cnt;           // [row chunks * rhs groups] arrivals (returned to 0 by the last)
-  float4* X2;              // double-float split of X for the current residual (n x nrhs)
-  const int64_t* kblk_off;
-  const int64_t* res_ptr;
-  const int32_t* res_blk;
-  const int32_t* res_src;
-  const int32_t* res_tr;
-  const int32_t* m_orig;
-  const int64_t* xoff_orig;
-  const int2* chunks;      // (block f, first row) of every 32-row chunk
-  int nrhs;
-  int64_t n;
-  const double2* X;
-  const double2* B;
-  double2* R;
-  const int32_t* inst;     // [N] instance of every block (caller numbering); all 0 unless batched
-  int* done;               // [instances] 1 once an instance's omega met the tolerance (skipped after)
-  double tol;              // refinement tolerance on omega
-  int ld_norm;             // row stride of the per-(instance, column) maxima
-  unsigned* rmax;          // [instances][ld_norm] max |r| as float bits
-  unsigned* xmax;          // [instances][ld_norm] max |x|
-  unsigned* bmax;          // [instances][ld_norm] max |b|
-  unsigned* kmax;          // [instances] ||K_i||_inf
-};
-
 struct SweepLaunch {
   int* status;                     // device word: D3M_ERR_TIMEOUT if a bounded wait expired
   int b, nrhs, nlevels, max_rows, accumulate;
@@ -84,6 +52,7 @@ struct SweepLaunch {
 };
 
 // FP64-accurate residual on the tensor cores (resid_tc.cu): digit planes of K and x.
+constexpr int kResidDigits = 9;       // base-64 digits per value; 2 x kResidDigits planes per chunk
 struct ResidualTc {
   const double2* K;              // stored lower blocks (c128), read by the digit kernels only
   const int64_t* kblk_off;       // [nnzb+1]
@@ -97,14 +66,16 @@ struct ResidualTc {
   const int32_t* res_blk;        // [contributions] stored block
   const int32_t* res_tr;         // [contributions] 1: the stored block is used transposed
   const int64_t* ks_plane;       // [contributions] first K digit plane
-  const int64_t* xs_plane;       // [N] first x digit plane of block g
+  const int64_t* xs_plane;       // [N] first x digit plane of block g (within a group's planes)
+  int64_t xs_total;              // x digit planes of one right-hand-side group
+  int nblk;                      // N
   const int2* rtiles;            // [row tiles] (row block f, 128-row tile)
   unsigned short* kdig;          // K digit planes (bf16), 128 x 32 each
   unsigned short* xdig;          // x digit planes (bf16), 64 x 32 each
   unsigned long long* Kmax_bits; // [nnzb] max |Re|, |Im| of every stored block (double bits)
   double2* Kdiag;                // [n] diagonal entries of K (applied in FP64)
   float* rowsum;                 // [n] row sums of |K| (for ||K||_inf)
-  int* xT;                       // [N][32] scale exponents of the x blocks (one group of 32 rhs)
+  int* xT;                       // [groups][N][32] scale exponents of the x blocks
   int64_t n;
   const int32_t* inst;           // [N] instance of every block
   const int* done;               // [instances] converged instances are skipped (or nullptr)
@@ -125,6 +96,7 @@ struct ResidTcMaps {
 int resid_tc_make_maps(void* kdig, int64_t nplanes_a, void* xdig, int64_t nplanes_b, ResidTcMaps* out,
                        std::string& err);
 int launch_kdigits(const ResidualTc& p, int nnzb, int nres, int max_rtiles, int nblk, cudaStream_t st);
+int resid_tc_groups(int nrhs, int* NR);
 int launch_resid_tc(const ResidualTc& p, const ResidTcMaps& maps, const double2* X, const double2* B, double2* R,
                     int nrhs, int nrtiles, int nblk, cudaStream_t st, int64_t* launches);
 
@@ -144,8 +116,6 @@ int launch_sweep(SweepLaunch& a, bool fp64, cudaStream_t st);
 int launch_inv_build(const int2* work, int nwork, const int32_t* tstart, const int64_t* tcolptr,
                      const int64_t* inv_off, const int64_t* invT_off, const void* L, const void* Linv, void* Inv,
                      void* InvT, int b, cudaStream_t st);
-int launch_residual(const ResidualParams& p, int nchunks, cudaStream_t st);
-int launch_knorm(const ResidualParams& p, int nchunks, cudaStream_t st);
 int launch_absmax(const double2* V, int64_t n, int nrhs, unsigned* out, cudaStream_t st);
 int launch_omega(const unsigned* rmax, const unsigned* xmax, const unsigned* bmax, const unsigned* kmax,
                  const unsigned* dmax, float* dprev, int ninst, int ld, int nrhs, int* done, double tol, double ftol,

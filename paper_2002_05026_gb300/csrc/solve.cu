@@ -1190,250 +1190,7 @@ __global__ void __launch_bounds__(GT) chain_kernel(ChainSweep s, const typename 
   if (bad && threadIdx.x == 0) atomicExch(s.status, (int)D3M_ERR_TIMEOUT);
 }
 
-// ------------------------------------------------------------------ FP64 residual
-// r = b - K x (caller numbering) to FP64 accuracy without the FP64 pipe doing the products.
-// GB300 issues FP32 instructions about 64x faster than FP64 ones, so every product runs on the
-// FP32 pipe in double-float form: K and x are held as unevaluated sums of two floats
-// (a = a_hi + a_lo, |a - a_hi - a_lo| <= 2^-48 |a|, split once per factorization / per call),
-// a_hi x_hi is formed exactly (product plus its FMA-recovered error), the two cross terms
-// a_hi x_lo + a_lo x_hi are added to that error, and the sum is kept as a renormalised pair
-// (s, c) (Knuth's two-sum of s and the product, then a fast two-sum), i.e. with about 2^-48
-// relative rounding per term.  Every 128 columns the pair is added into an FP64 accumulator
-// (more often costs FP64-pipe conversions), and r = b - acc is formed in FP64.  Error: 2^-48
-// relative from the splits plus at most 128 * 2^-48 of the chunk's absolute sum per chunk
-// (typically about 10 * 2^-48), then FP64 rounding
-// of the chunk sums: a few 1e-16 of |K||x| in practice, comparable to a plain FP64 dot product
-// and far below the 1e-12 backward-error target.
-// Thread (row u of block f, rhs group): RPT right-hand sides per thread share each K load.
-__device__ __forceinline__ void df_mac(float& s, float& c, float ah, float al, float xh, float xl) {
-  const float p = __fmul_rn(ah, xh);
-  float e = fmaf(ah, xh, -p);          // a_hi x_hi - p, exact
-  e = fmaf(ah, xl, e);
-  e = fmaf(al, xh, e);
-  const float t = __fadd_rn(s, p);     // two-sum s + p = t + err
-  const float bp = __fsub_rn(t, s);
-  const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(p, bp));
-  const float lo = __fadd_rn(c, __fadd_rn(err, e));
-  s = __fadd_rn(t, lo);                // renormalise: |c| stays within half an ulp of s
-  c = __fsub_rn(lo, __fsub_rn(s, t));
-}
-
-__device__ __forceinline__ float4 split_c(double2 v) {
-  const float hr = (float)v.x, hi = (float)v.y;
-  return make_float4(hr, hi, (float)(v.x - (double)hr), (float)(v.y - (double)hi));
-}
-
-// The same split with integer operations only (the split of K runs once per factorization
-// over every stored entry; FP64 conversions would make it FP64-pipe bound): hi = x truncated
-// to 24 significant bits, lo = the remaining 29 bits rounded to a float, |x - hi - lo| <=
-// 2^-47 |x|.  Zeros and magnitudes outside [2^-74, 2^127] take the FP64 conversion path.
-__device__ __forceinline__ void split_bits(double x, float& hi, float& lo) {
-  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
-  const int e = (int)((u >> 52) & 0x7ff);
-  if (e < 949 || e > 1150) {
-    hi = (float)x;
-    lo = (float)(x - (double)hi);
-    return;
-  }
-  const unsigned sign = (unsigned)(u >> 63) << 31;
-  const unsigned long long mant = u & 0xFFFFFFFFFFFFFull;
-  hi = __uint_as_float(sign | ((unsigned)(e - 896) << 23) | (unsigned)(mant >> 29));
-  const float r = __uint2float_rn((unsigned)(mant & 0x1FFFFFFFull)) * __uint_as_float((unsigned)(e - 948) << 23);
-  lo = __uint_as_float(__float_as_uint(r) | sign);
-}
-__device__ __forceinline__ float4 split_c_bits(double2 v) {
-  float4 o;
-  split_bits(v.x, o.x, o.z);
-  split_bits(v.y, o.y, o.w);
-  return o;
-}
-
-// X2 = split(X) for the columns of one residual (n x nrhs, same layout)
-__global__ void split_x_kernel(const double2* __restrict__ X, float4* __restrict__ X2, int64_t total) {
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i < total) X2[i] = split_c(X[i]);
-}
-
-constexpr int RES_CHUNK = 128;
-constexpr int RES_PARTS = 2;      // blocks sharing one row chunk's contributions
-
-template <int RPT>
-__global__ void __launch_bounds__(128, 6) residual_kernel(ResidualParams p) {
-  const int i = threadIdx.x % 32, w = threadIdx.x / 32;
-  const int j0 = (blockIdx.y * (blockDim.x / 32) + w) * RPT;
-  const int2 ch = p.chunks[blockIdx.x];
-  const int f = ch.x, u = ch.y + i;
-  if (p.done && p.done[p.inst[f]]) return;             // converged instance: r and its norms are kept
-  const int mf = p.m_orig[f];
-  const bool active = (u < mf) && (j0 < p.nrhs);
-  int nj = p.nrhs - j0;
-  nj = nj < RPT ? nj : RPT;
-  double accr[RPT], acci[RPT];
-#pragma unroll
-  for (int q = 0; q < RPT; ++q) accr[q] = acci[q] = 0.0;
-  // the row's contributions are split over gridDim.z blocks (more, shorter warps: no half-empty
-  // last wave); the last block to finish adds the parts in part order and forms r
-  const int part = blockIdx.z, nparts = gridDim.z;
-  const int64_t eb = p.res_ptr[f], ee = p.res_ptr[f + 1], eh = (ee - eb + nparts - 1) / nparts;
-  const int64_t e_lo = min(ee, eb + part * eh), e_hi = min(ee, e_lo + eh);
-  if (active) {
-    for (int64_t e = e_lo; e < e_hi; ++e) {
-      const int blk = p.res_blk[e], g = p.res_src[e];
-      const int mg = p.m_orig[g];
-      // stored (f, g): entry (u, c) at K2[c * mf + u]; a block stored as (g, f) is read from its
-      // transposed copy in the same layout, so a warp's 32 rows always read 32 consecutive entries
-      const bool tr = p.res_tr[e] != 0;
-      const float4* kb = (tr ? p.K2T + p.res_ktoff[e] : p.K2 + p.kblk_off[blk]) + u;
-      const int64_t ks = mf;
-      const float4* xg = p.X2 + (int64_t)j0 * p.n + p.xoff_orig[g];
-      for (int c0 = 0; c0 < mg; c0 += RES_CHUNK) {
-        const int c1 = min(mg, c0 + RES_CHUNK);
-        float sr[RPT], cr[RPT], si[RPT], ci[RPT];
-#pragma unroll
-        for (int q = 0; q < RPT; ++q) sr[q] = cr[q] = si[q] = ci[q] = 0.f;
-        // the next column's K entry and x values are loaded while this column is multiplied
-        float4 an = __ldg(kb + c0 * ks), xn[RPT];
-#pragma unroll
-        for (int q = 0; q < RPT; ++q) xn[q] = (q < nj) ? __ldg(xg + (int64_t)q * p.n + c0) : make_float4(0.f, 0.f, 0.f, 0.f);
-        for (int c = c0; c < c1; ++c) {
-          const float4 a = an;                           // (hi_r, hi_i, lo_r, lo_i)
-          float4 xv[RPT];
-#pragma unroll
-          for (int q = 0; q < RPT; ++q) xv[q] = xn[q];
-          if (c + 1 < c1) {
-            an = __ldg(kb + (c + 1) * ks);
-#pragma unroll
-            for (int q = 0; q < RPT; ++q)
-              if (q < nj) xn[q] = __ldg(xg + (int64_t)q * p.n + c + 1);
-          }
-#pragma unroll
-          for (int q = 0; q < RPT; ++q) {
-            if (q < nj) {
-              const float4 x = xv[q];
-              df_mac(sr[q], cr[q], a.x, a.z, x.x, x.z);       // + a_r x_r
-              df_mac(sr[q], cr[q], -a.y, -a.w, x.y, x.w);     // - a_i x_i
-              df_mac(si[q], ci[q], a.x, a.z, x.y, x.w);       // + a_r x_i
-              df_mac(si[q], ci[q], a.y, a.w, x.x, x.z);       // + a_i x_r
-            }
-          }
-        }
-#pragma unroll
-        for (int q = 0; q < RPT; ++q) {
-          accr[q] += (double)sr[q] + (double)cr[q];
-          acci[q] += (double)si[q] + (double)ci[q];
-        }
-      }
-    }
-  }
-  if (nparts > 1) {
-    __shared__ int s_last;
-#pragma unroll
-    for (int q = 0; q < RPT; ++q)
-      if (active && q < nj)
-        p.part_acc[(int64_t)part * p.part_ld + (int64_t)(j0 + q) * p.n + p.xoff_orig[f] + u] =
-            make_double2(accr[q], acci[q]);
-    __threadfence();
-    __syncthreads();
-    int* ctr = p.part_cnt + ((int64_t)blockIdx.y * gridDim.x + blockIdx.x);
-    if (threadIdx.x == 0) s_last = atomicAdd(ctr, 1) == nparts - 1;
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
-    if (threadIdx.x == 0) *ctr = 0;                     // ready for the next residual
-#pragma unroll
-    for (int q = 0; q < RPT; ++q) {
-      accr[q] = acci[q] = 0.0;
-      if (active && q < nj)
-        for (int pp = 0; pp < nparts; ++pp) {
-          const double2 v = __ldcg(p.part_acc + (int64_t)pp * p.part_ld + (int64_t)(j0 + q) * p.n + p.xoff_orig[f] + u);
-          accr[q] += v.x;
-          acci[q] += v.y;
-        }
-    }
-  }
-#pragma unroll
-  for (int q = 0; q < RPT; ++q) {
-    const int j = j0 + q;
-    float ra = 0.f, xa = 0.f, ba = 0.f;
-    if (active && q < nj) {
-      const int64_t o = (int64_t)j * p.n + p.xoff_orig[f] + u;
-      const double2 bv = p.B[o];
-      const double2 r = make_double2(bv.x - accr[q], bv.y - acci[q]);
-      p.R[o] = r;
-      const float rx = (float)r.x, ry = (float)r.y;
-      ra = sqrtf(rx * rx + ry * ry);
-      const double2 xv = p.X[o];
-      const float xx = (float)xv.x, xy = (float)xv.y;
-      xa = sqrtf(xx * xx + xy * xy);
-      const float bx = (float)bv.x, by = (float)bv.y;
-      ba = sqrtf(bx * bx + by * by);
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-      ra = fmaxf(ra, __shfl_xor_sync(0xffffffffu, ra, o));
-      xa = fmaxf(xa, __shfl_xor_sync(0xffffffffu, xa, o));
-      ba = fmaxf(ba, __shfl_xor_sync(0xffffffffu, ba, o));
-    }
-    if (i == 0 && j0 < p.nrhs && q < nj) {
-      const int qq = p.inst[f] * p.ld_norm + j;
-      atomicMax(p.rmax + qq, __float_as_uint(ra));
-      atomicMax(p.xmax + qq, __float_as_uint(xa));
-      atomicMax(p.bmax + qq, __float_as_uint(ba));
-    }
-  }
-}
-
-// ||K_i||_inf row sums (float magnitudes; a scale for omega), and the double-float split of K
-// used by the residual.
-__global__ void __launch_bounds__(256) knorm_kernel(ResidualParams p) {
-  // 32 rows per block; warp w takes the w-th eighth of every contribution's columns (contiguous,
-  // so the transposed reads of a warp stay within the same cache lines), 4 loads in flight
-  const int i = threadIdx.x % 32, w = threadIdx.x / 32;
-  const int2 ch = p.chunks[blockIdx.x];
-  const int f = ch.x, u = ch.y + i;
-  const int mf = p.m_orig[f];
-  __shared__ float s_sum[8][32];
-  float sum = 0.f;
-  if (u < mf) {
-    for (int64_t e = p.res_ptr[f]; e < p.res_ptr[f + 1]; ++e) {
-      const int blk = p.res_blk[e], g = p.res_src[e];
-      const int mg = p.m_orig[g];
-      const double2* Kp = p.K + p.kblk_off[blk];
-      const bool tr = p.res_tr[e] != 0;
-      // untransposed visit: the split in K's layout; transposed visit: the split of the
-      // transposed block (entry (u, c) at c * mf + u), written with coalesced stores
-      float4* K2 = tr ? const_cast<float4*>(p.K2T) + p.res_ktoff[e] : const_cast<float4*>(p.K2) + p.kblk_off[blk];
-      const int per = (mg + 7) / 8;
-      const int c_lo = min(mg, w * per), c_hi = min(mg, c_lo + per);
-      auto off = [&](int c) -> int64_t { return tr ? (int64_t)u * mg + c : (int64_t)c * mf + u; };
-      int c = c_lo;
-      for (; c + 4 <= c_hi; c += 4) {
-        double2 v[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) v[q] = __ldg(Kp + off(c + q));
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const float4 sv = split_c_bits(v[q]);
-          K2[(int64_t)(c + q) * mf + u] = sv;
-          sum += sqrtf(sv.x * sv.x + sv.y * sv.y);
-        }
-      }
-      for (; c < c_hi; ++c) {
-        const float4 sv = split_c_bits(__ldg(Kp + off(c)));
-        K2[(int64_t)c * mf + u] = sv;
-        sum += sqrtf(sv.x * sv.x + sv.y * sv.y);
-      }
-    }
-  }
-  s_sum[w][i] = sum;
-  __syncthreads();
-  if (w == 0) {
-    float t = 0.f;
-    for (int q = 0; q < 8; ++q) t += s_sum[q][i];
-    for (int o = 16; o > 0; o >>= 1) t = fmaxf(t, __shfl_xor_sync(0xffffffffu, t, o));
-    if (i == 0) atomicMax(p.kmax + p.inst[f], __float_as_uint(t));
-  }
-}
-
+// ------------------------------------------------------------------ norms, omega, gradients
 __global__ void vec_absmax_kernel(const double2* __restrict__ V, int64_t n, int nrhs, unsigned* out) {
   const int j = blockIdx.y;
   float a = 0.f;
@@ -1798,26 +1555,6 @@ static int sweep_impl(SweepLaunch& a, cudaStream_t st) {
 
 int launch_sweep(SweepLaunch& a, bool fp64, cudaStream_t st) {
   return fp64 ? sweep_impl<double>(a, st) : sweep_impl<float>(a, st);
-}
-
-int launch_residual(const ResidualParams& p, int nchunks, cudaStream_t st) {
-  const int64_t total = p.n * (int64_t)p.nrhs;
-  split_x_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(p.X, p.X2, total);
-  // 4 warps per block, RPT right-hand sides per warp
-  if (p.nrhs == 1) {
-    residual_kernel<1><<<dim3((unsigned)nchunks, 1, RES_PARTS), 32, 0, st>>>(p);
-  } else {
-    // RPT = 2 measured faster than 4 (more warps in flight; the pair chains already give ILP)
-    const int groups = (p.nrhs + 1) / 2;
-    const int wpb = groups < 4 ? groups : 4;
-    residual_kernel<2><<<dim3((unsigned)nchunks, (unsigned)((groups + wpb - 1) / wpb), RES_PARTS), 32 * wpb, 0, st>>>(p);
-  }
-  return (int)cudaGetLastError();
-}
-
-int launch_knorm(const ResidualParams& p, int nchunks, cudaStream_t st) {
-  knorm_kernel<<<nchunks, 256, 0, st>>>(p);
-  return (int)cudaGetLastError();
 }
 
 int launch_absmax(const double2* V, int64_t n, int nrhs, unsigned* out, cudaStream_t st) {
