@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libd3m.so")
-SOURCES = ["symbolic.cpp", "api.cu", "factor_simt.cu", "factor_tc.cu", "solve.cu", "resid_tc.cu", "blockinv.cu",
+SOURCES = ["symbolic.cpp", "api.cu", "factor_simt.cu", "factor_tc.cu", "solve.cu", "resid_tc.cu", "gather_tc.cu", "blockinv.cu",
            "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -65,6 +65,8 @@ struct d3m_ctx {
   void* Sacc = nullptr;
   int64_t* trace = nullptr;
   TcMaps maps;
+  GatherTcMaps gmaps;                // L's operand planes for the tensor-core solve gathers
+  bool gather_tc = false;
   // solve
   SolveItem* fwd_items = nullptr;
   SolveItem* bwd_items = nullptr;
@@ -469,6 +471,11 @@ static int create_impl(d3m_handle* out, const d3m_pattern* pat, const int32_t* p
     if (!h->opA || !h->opB) return set_err(h, D3M_ERR_OOM, "cudaMalloc failed for the tensor-core operands");
     std::string e2;
     if (tc_make_maps(h->opA, h->opB, ntiles, h->tf32, &h->maps, e2) != 0) return set_err(h, D3M_ERR_CUDA, e2);
+    if (!h->tf32) {
+      // the solve's off-block products run on the tensor cores from the same bf16 planes
+      if (gather_tc_make_maps(h->opA, ntiles, &h->gmaps, e2) != 0) return set_err(h, D3M_ERR_CUDA, e2);
+      h->gather_tc = true;
+    }
   }
   // solve
   UPLOAD(h->fwd_items, S.fwd_items);
@@ -906,6 +913,8 @@ static int sweep(d3m_ctx* h, const double2* src, double2* dst, int nrhs, int acc
   a.tinst = h->tinst;
   a.dmax = h->dmax;
   a.ld_norm = h->opt.max_nrhs;
+  a.tcmaps = h->gather_tc ? &h->gmaps : nullptr;
+  a.nsm = h->nsm;
   ev_begin(h, d3m_ctx::EV_SWEEP, st);
   int rc = launch_sweep(a, h->fp64, st);
   if (rc) return set_err(h, D3M_ERR_CUDA, std::string("sweep launch: ") + cudaGetErrorString((cudaError_t)rc));

@@ -48,8 +48,21 @@ struct SweepLaunch {
   const int64_t* inv_off;          // device [N]: first tile of block k in Inv
   const void* InvT;                // transposed inverse tiles (diagonal included)
   const int64_t* invT_off;         // device [N]: first tile of block k in InvT
+  const struct GatherTcMaps* tcmaps;  // operand-plane maps for the tensor-core gathers, or nullptr
+  int nsm;
   int64_t launches;                // out: kernels launched by launch_sweep
 };
+
+// Tensor maps of L's bf16 operand planes for the tensor-core gathers of the solve (gather_tc.cu):
+// k = box {32, 128} (forward, K-major), t = box {32, 32} (backward, MN-major blocks).
+struct GatherTcMaps {
+  alignas(64) unsigned char k[128];
+  alignas(64) unsigned char t[128];
+};
+int gather_tc_make_maps(void* opA, int64_t ntiles, GatherTcMaps* out, std::string& err);
+int launch_gather_tc(bool fwd, const GatherTcMaps& maps, const SolveGroup* groups, const SolveItem* items,
+                     const void* Y, void* P, int64_t npad, int nrhs, int* status, const int* done,
+                     const int32_t* tinst, int nunits, int nsm, cudaStream_t st);
 
 // FP64-accurate residual on the tensor cores (resid_tc.cu): digit planes of K and x.
 constexpr int kResidDigits = 9;       // base-64 digits per value; 2 x kResidDigits planes per chunk

@@ -1364,6 +1364,12 @@ static int sweep_impl(SweepLaunch& a, cudaStream_t st) {
     if (nsm <= 0) nsm = 1;
   }
   auto launch_gather = [&](bool fwd, int64_t i0, int64_t i1) {
+    if (a.tcmaps && sizeof(R) == 4) {
+      // tensor-core gather (split-BF16x3 on L's operand planes): one unit per group
+      launch_gather_tc(fwd, *a.tcmaps, (fwd ? a.fwd_groups : a.bwd_groups) + i0, fwd ? a.fwd_items : a.bwd_items,
+                       Y, P, a.npad, a.nrhs, a.status, a.done, a.tinst, (int)(i1 - i0), nsm, st);
+      return;
+    }
     const int nunits = (int)((i1 - i0) * nh);
     const dim3 grid((unsigned)std::min<int64_t>(nunits, nsm), gy);
     if (fwd)
