@@ -5,3 +5,4 @@ leg of ``bench.py`` may import this package.  It shares no code with the CUDA li
 never imports it; the product path does not call it.
 """
 from .ldlt import *  # noqa: F401,F403
+from .ldlt_bk import *  # noqa: F401,F403
