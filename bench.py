@@ -373,7 +373,7 @@ def batch_arm(args, rank, world, local):
     stream = torch.cuda.current_stream()
     sp = ctypes.c_void_p(stream.cuda_stream)
     tune = autotune.tune_batch(inst, perms, K, Bt, nrhs)
-    s = D3MBatch(inst, perms, precision=tune["precision"], max_nrhs=nrhs, graphs=True)
+    s = D3MBatch(inst, perms, precision=tune["precision"], max_nrhs=nrhs, graphs=True, task_cost=tune["task_cost"])
     lib = s._lib
     Xt = torch.empty_like(Bt)
 
@@ -501,6 +501,7 @@ def batch_arm(args, rank, world, local):
                            "grids": "2-D, uniform over {2x2,3x3,4x4,6x6}", "m": "uniform over {64,128,256}",
                            "k2": "U(0.5,4)", "tau": "U(0.01,0.2)", "tile_engine": tune["precision"],
                            "autotune_ms": {k: v["ms"] for k, v in tune["timings"].items()}, "graphs": True,
+                           "task_cost_ns": tune["task_cost"],
                            "l2": f"inputs larger than L2 (K is {K.numel() * 16 / 1e9:.2f} GB)"},
                 "roofline": roof,
                 "accuracy": {"omega_max_over_instances": float(np.max(w_inst)), "refine_solves": info["refine_iters"]},

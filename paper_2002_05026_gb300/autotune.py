@@ -1,5 +1,6 @@
-"""Autotuner for batched handles: picks the tile engine (tile shape and tensor-core or SIMT
-tiles) for a given mix of instances by timing the real factor + refined solve on the device.
+"""Autotuner: picks the tile engine (tile shape and tensor-core or SIMT tiles) for a given mix
+of instances by timing the real factor + refined solve on the device, and measures the task
+durations of the chosen engine that the device scheduler's critical-path priority is built from.
 
 Candidates (each a complete configuration of libd3m.so):
   * "bf16x3" - 128 x 128 tiles, Schur updates as split-BF16x3 tcgen05 products;
@@ -33,6 +34,54 @@ def signature(instances, nrhs: int) -> str:
     items.sort()
     h = hashlib.sha1(repr((items, int(nrhs))).encode()).hexdigest()[:16]
     return h
+
+
+def fit_task_costs(trace: np.ndarray) -> list:
+    """Duration model cost = base + per_k * nk (ns) for the three task kinds of the factorization
+    (update, diagonal final, off-diagonal final), least squares over the traced tasks
+    (trace rows: start_ns, end_ns, sm, flags | tile << 8 | nk << 40, ...).  The paper weights its
+    dual tasks with benchmarked GEMM, sytrf and triSolve times (Sec. II); here the benchmark is a
+    traced factorization of the actual pattern."""
+    ok = (trace[:, 0] > 0) & (trace[:, 1] >= trace[:, 0])
+    t = trace[ok]
+    dur = (t[:, 1] - t[:, 0]).astype(np.float64)
+    flags = t[:, 3] & 0xFF
+    nk = (t[:, 3] >> 40).astype(np.float64)
+    kind = np.where(flags & 4, 0, np.where(flags & 1, 1, 2))
+    out = []
+    for k in range(3):
+        sel = kind == k
+        if sel.sum() == 0:
+            out += [0.0, 0.0]
+            continue
+        A = np.stack([np.ones(sel.sum()), nk[sel]], axis=1)
+        if np.ptp(nk[sel]) == 0:
+            coef = np.array([np.median(dur[sel]), 0.0])
+        else:
+            coef, *_ = np.linalg.lstsq(A, dur[sel], rcond=None)
+        base, per = float(coef[0]), float(coef[1])
+        # a model must stay positive over the tasks it covers
+        base = max(base, 1.0)
+        per = max(per, 0.0)
+        out += [base, per]
+    return out
+
+
+def measure_task_costs(instances, perms, K, precision: str, batch: bool = True, stream=None) -> list:
+    """Factor once with task tracing (after one untimed warm-up) and fit the duration model."""
+    from .solver import D3M
+    if batch:
+        s = D3MBatch(instances, perms, precision=precision, debug_flags=2, stream=stream)
+    else:
+        colptr, rowidx, m = instances[0]
+        s = D3M(colptr, rowidx, m=m, perm=perms[0] if perms else None, precision=precision, debug_flags=2,
+                stream=stream)
+    try:
+        s.factor(K)
+        s.factor(K)
+        return fit_task_costs(s.trace())
+    finally:
+        s.close()
 
 
 def _time_candidate(instances, perms, K, B, nrhs, precision, reps, stream):
@@ -83,7 +132,8 @@ def tune_batch(instances, perms, K, B, nrhs: int, candidates=CANDIDATES, reps: i
     if not ok:
         raise RuntimeError(f"no candidate reached omega <= {tol}: {timings}")
     best = min(ok, key=lambda c: timings[c]["ms"])
-    res = {"precision": best, "ms": timings[best]["ms"], "timings": timings, "key": key}
+    res = {"precision": best, "ms": timings[best]["ms"], "timings": timings, "key": key,
+           "task_cost": measure_task_costs(instances, perms, K, best, batch=True, stream=stream)}
     _memo[key] = res
     if cache_path:
         disk = {}

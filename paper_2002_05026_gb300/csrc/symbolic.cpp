@@ -34,7 +34,7 @@ static int fail(std::string& err, const char* msg, long a = -1, long b = -1) {
 }
 
 int analyze(const d3m_pattern* pat, const int32_t* perm_in, int b, bool build_tasks,
-            Symbolic& s, std::string& err, double prio_slack, int seg_group) {
+            Symbolic& s, std::string& err, double prio_slack, int seg_group, const double* task_cost) {
   if (seg_group < 1) seg_group = 1;
   if (!pat || !pat->colptr || !pat->rowidx) return fail(err, "pattern or its arrays are NULL");
   const int N = pat->nblk;
@@ -373,17 +373,27 @@ int analyze(const d3m_pattern* pat, const int32_t* perm_in, int b, bool build_ta
     for (int32_t d : tdeps[id]) s.succ[wpos[d]++] = (int32_t)id;
   std::vector<std::vector<int32_t>>().swap(tdeps);
   s.n_edges = (int64_t)s.succ.size();
-  // Priority: a static estimate of each task's duration (diagonal factorization + inverse,
+  // Priority: an estimate of each task's duration (diagonal factorization + inverse,
   // triangular-solve final, update segment of nk tile products) gives the longest path from
   // the sources to a task's start (tl) and from its start to the end (bl); tasks whose slack
   // CP - tl - bl is within prio_slack * CP go to the priority lane, which the device
   // scheduler serves first, so the chain of diagonal factorizations does not queue behind
-  // hundreds of ready updates.
+  // hundreds of ready updates.  The durations are the caller's measured model (the paper
+  // weights its dual tasks with benchmarked GEMM, sytrf and triSolve times, Sec. II) or, without
+  // one, a built-in model in microseconds of the tensor-core engine.
   {
+    double cm[6] = {4.0, 3.0, 110.0, 3.0, 20.0, 3.0};
+    if (task_cost) {
+      bool any = false;
+      for (int q = 0; q < 6; ++q) any = any || task_cost[q] > 0;
+      if (any)
+        for (int q = 0; q < 6; ++q) cm[q] = task_cost[q] > 0 ? task_cost[q] : 0.0;
+    }
     std::vector<double> cost(ntask), tl(ntask, 0.0), bl(ntask, 0.0);
     for (int64_t id = 0; id < ntask; ++id) {
       const TileTask& T = s.tasks[id];
-      cost[id] = (T.flags & TF_UPDATE) ? 4.0 + 3.0 * T.nk : ((T.flags & TF_DIAG) ? 110.0 + 3.0 * T.nk : 20.0 + 3.0 * T.nk);
+      const int k = (T.flags & TF_UPDATE) ? 0 : ((T.flags & TF_DIAG) ? 2 : 4);
+      cost[id] = cm[k] + cm[k + 1] * T.nk;
     }
     std::vector<int32_t> indeg(s.ndeps.begin(), s.ndeps.end()), order;
     order.reserve(ntask);

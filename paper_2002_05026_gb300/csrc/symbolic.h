@@ -120,8 +120,13 @@ struct Symbolic {
 // Validate the pattern and permutation, then run the full analysis for tile edge b.  Tasks whose
 // estimated slack is within prio_slack of the critical path are flagged TF_PRIO.
 // Returns D3M_OK or an error code with a message in `err`.
+// task_cost (6 values or nullptr): the duration model of the priority estimate, cost = base +
+// per_k * nk (nk = tile products of the task) for update tasks (task_cost[0], [1]), diagonal
+// final tasks ([2], [3]) and off-diagonal final tasks ([4], [5]), in any common unit; nullptr or
+// all zeros = the built-in model.
 int analyze(const d3m_pattern* pat, const int32_t* perm, int b, bool build_tasks,
-            Symbolic& s, std::string& err, double prio_slack = 0.08, int seg_group = 1);
+            Symbolic& s, std::string& err, double prio_slack = 0.08, int seg_group = 1,
+            const double* task_cost = nullptr);
 
 // Grid nested dissection (see d3m_order_grid_nd).
 int order_grid_nd(int nx, int ny, int nz, std::vector<int32_t>& perm);

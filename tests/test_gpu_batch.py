@@ -138,7 +138,11 @@ def test_autotuner_picks_a_converging_engine(torch_cuda):
     assert set(res["timings"]) == set(autotune.CANDIDATES)
     assert res["ms"] == min(v["ms"] for v in res["timings"].values() if v["omega"] <= 1e-12)
     assert autotune.tune_batch(spec, perms, K, Bt, nrhs=2) is res          # cached by signature
-    s = D3MBatch(spec, perms, precision=res["precision"], max_nrhs=2)
+    # the measured task-duration model (ns): positive, and the update tasks' cost grows with
+    # their tile products; the handle built with it still solves to the oracle's accuracy
+    tc = res["task_cost"]
+    assert len(tc) == 6 and all(v >= 0 for v in tc) and tc[0] > 0 and tc[2] > 0
+    s = D3MBatch(spec, perms, precision=res["precision"], max_nrhs=2, task_cost=tc)
     s.factor(K)
     X = s.solve(Bt.T).cpu().numpy()
     for i, (p, pm, Kb, F) in enumerate(inst):
@@ -146,3 +150,23 @@ def test_autotuner_picks_a_converging_engine(torch_cuda):
         Bi = B[int(s.offsets[i]):int(s.offsets[i + 1])]
         Xo = O.block_solve(F, Bi)
         assert np.max(np.linalg.norm(Xi - Xo, axis=0) / np.linalg.norm(Xo, axis=0)) <= 1e-9
+
+
+def test_measured_task_costs_single_handle(torch_cuda):
+    # a traced factorization of the 4x4 m = 512 pattern gives the duration model: the update
+    # tasks' cost per tile product and the diagonal tasks' cost are positive and of the order of
+    # the tensor-core engine's tile times (microseconds); a handle built with the model factors
+    # and solves to the oracle's accuracy
+    from paper_2002_05026_gb300 import D3M, autotune
+    g, m = (4, 4, 1), 512
+    p = synth.make_problem(*g, m, 2.0, 0.05, 41)
+    perm = O.nd_order(*g)
+    K = torch_cuda.from_numpy(p.blocks).cuda()
+    tc = autotune.measure_task_costs([(p.colptr, p.rowidx, m)], [perm], K, "bf16x3", batch=False)
+    assert 100.0 < tc[1] < 1e6 and 100.0 < tc[2] < 1e7, tc
+    s = D3M(p.colptr, p.rowidx, m=m, perm=perm, precision="bf16x3", max_nrhs=4, task_cost=tc)
+    s.factor(K)
+    B = synth.rhs(5, p.n, 2)
+    X = s.solve(torch_cuda.from_numpy(np.ascontiguousarray(B)).cuda()).cpu().numpy()
+    Kb = O.lower_blocks(p.colptr, p.rowidx, p.blocks, m)
+    assert np.max(O.omega(Kb, p.nblk, m, X, B)) <= 1e-12
