@@ -104,6 +104,19 @@ typedef struct {
                                correction d_k be <= refine_fwd_tol |x|, or that the error it
                                leaves, rho/(1-rho) |d_k| with rho = |d_k|/|d_(k-1)| < 1, be
                                (default 1e-10; 0 = backward error only) */
+  double task_cost[6];      /* duration model of the scheduler's critical-path priority (the paper
+                               weights its dual tasks with benchmarked GEMM / sytrf / triSolve
+                               times, Sec. II): cost = base + per_k * nk, nk = tile products of
+                               the task, for update tasks [0], [1], diagonal final tasks
+                               (LDL^T + inverse) [2], [3] and off-diagonal final tasks
+                               (triangular solve) [4], [5]; any common unit (e.g. measured ns,
+                               see d3m_get_trace); all zero (default) = a built-in model */
+  int32_t pivot;            /* 1 = Bunch-Kaufman symmetric pivoting (1 x 1 and 2 x 2 pivots, the
+                               paper's sytrf, Sec. II) inside every diagonal tile: the tile is
+                               factored as S = Lt D Lt^T, Lt = P^T L; the block structure and task
+                               graph are unchanged.  SIMT engines only (D3M_FP64,
+                               D3M_MIXED_SIMT32; D3M_ERR_INVALID otherwise).  0 (default) =
+                               unpivoted, scalar D */
 } d3m_options;
 
 /* Test hook: upload the task graph with one extra unmet dependency on the last task, so the
@@ -174,6 +187,13 @@ int d3m_order_grid_nd(int32_t nx, int32_t ny, int32_t nz, int32_t* perm);
  * factor_flops, solve_flops_per_rhs, residual_flops_per_rhs).  perm may be NULL (identity).
  * This is the paper's symbolic simulation that yields the task graph (Sec. II). */
 int d3m_analyze(const d3m_pattern* pat, const int32_t* perm, int32_t tile, d3m_info* info);
+
+/* Symbolic analysis with the options a handle would be created with (host, no GPU): the same
+ * structural fields as d3m_analyze for the tile edge that opt->precision (or opt->tile) selects,
+ * and prio_tasks, the tasks that the critical-path priority built from opt->task_cost (or the
+ * built-in model), opt->prio_slack and opt->seg_group puts in the scheduler's priority lane.
+ * opt NULL = defaults. */
+int d3m_analyze_opts(const d3m_pattern* pat, const int32_t* perm, const d3m_options* opt, d3m_info* info);
 
 /* Create a solver for one pattern: validates the pattern and perm (perm[new] = old, NULL =
  * identity), runs the symbolic analysis, builds the tile task graph and allocates every
@@ -270,9 +290,18 @@ int d3m_get_factor_block(d3m_handle h, int32_t i, int32_t j, void* host_out, voi
 /* Copy the pivots D_j of block column j (NEW numbering) to host memory as c128 [m_j]. */
 int d3m_get_pivots(d3m_handle h, int32_t j, void* host_out, void* stream);
 
+/* Pivot data of block column j (NEW numbering) from a factorization with opt.pivot = 1, to host
+ * memory: e_out (c128 [m_j], may be NULL) holds the sub-diagonal entry of every 2 x 2 pivot block
+ * of D_j at its first row (0 elsewhere; d3m_get_pivots gives the diagonal), perm_out (int32
+ * [m_j], may be NULL) the order of the block's unknowns after the pivoting inside its tiles
+ * (pivot position i of the block holds its unknown perm_out[i]).  Without pivoting: zeros and
+ * the identity.  Synchronizes the stream. */
+int d3m_get_pivot_blocks(d3m_handle h, int32_t j, void* e_out, int32_t* perm_out, void* stream);
+
 /* Task trace of the last factorization (handle created with D3M_DEBUG_TRACE): copies up to
- * `cap` records of 10 int64 each {start_ns, end_ns, sm_id, flags | (tile << 8), t1, t2, t3,
- * t4, ready_ns, releaser}, indexed by task id, to host memory and stores the number of tasks
+ * `cap` records of 10 int64 each {start_ns, end_ns, sm_id, flags | (tile << 8) | (nk << 40), t1,
+ * t2, t3, t4, ready_ns, releaser}, indexed by task id (flags: 1 diagonal tile, 4 update task;
+ * nk: tile products of the task), to host memory and stores the number of tasks
  * in *count; t1..t4 are phase marks of the tensor-core engine (products done, S staged,
  * factor / triangular solve done, tile stored; -1 where a phase does not occur); ready_ns is
  * when the task's last dependency was released and releaser the task that released it (both

@@ -43,7 +43,8 @@ class d3m_options(ctypes.Structure):
     _fields_ = [("precision", c_int32), ("refine_max_iter", c_int32), ("refine_tol", c_double),
                 ("timeout_ns", c_int64), ("tile", c_int32), ("max_nrhs", c_int32),
                 ("fp64_omega", c_int32), ("debug_flags", c_int32), ("graphs", c_int32), ("seg_group", c_int32),
-                ("prio_slack", c_double), ("refine_fwd_tol", c_double)]
+                ("prio_slack", c_double), ("refine_fwd_tol", c_double), ("task_cost", c_double * 6),
+                ("pivot", c_int32)]
 
 
 class d3m_info(ctypes.Structure):
@@ -81,6 +82,7 @@ def load() -> ctypes.CDLL:
         "d3m_default_options": (None, [P(d3m_options)]),
         "d3m_order_grid_nd": (c_int32, [c_int32, c_int32, c_int32, P(c_int32)]),
         "d3m_analyze": (c_int32, [P(d3m_pattern), P(c_int32), c_int32, P(d3m_info)]),
+        "d3m_analyze_opts": (c_int32, [P(d3m_pattern), P(c_int32), P(d3m_options), P(d3m_info)]),
         "d3m_create": (c_int32, [P(c_void_p), P(d3m_pattern), P(c_int32), P(d3m_options), c_void_p]),
         "d3m_create_batch": (c_int32, [P(c_void_p), c_int32, P(d3m_pattern), P(P(c_int32)), P(d3m_options),
                                        c_void_p]),
@@ -95,6 +97,7 @@ def load() -> ctypes.CDLL:
         "d3m_grad_pattern": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_void_p, c_void_p]),
         "d3m_get_factor_block": (c_int32, [c_void_p, c_int32, c_int32, c_void_p, c_void_p]),
         "d3m_get_pivots": (c_int32, [c_void_p, c_int32, c_void_p, c_void_p]),
+        "d3m_get_pivot_blocks": (c_int32, [c_void_p, c_int32, c_void_p, P(c_int32), c_void_p]),
         "d3m_get_info": (c_int32, [c_void_p, P(d3m_info), c_void_p]),
         "d3m_get_trace": (c_int32, [c_void_p, c_void_p, c_int64, P(c_int64), c_void_p]),
         "d3m_last_error": (c_char_p, [c_void_p]),
@@ -159,6 +162,20 @@ def make_pattern(colptr, rowidx, m=None, blk_size=None):
     pat.colptr = colptr.ctypes.data_as(POINTER(c_int64))
     pat.rowidx = rowidx.ctypes.data_as(POINTER(c_int32))
     return pat, keep
+
+
+def d3m_analyze_opts(colptr, rowidx, m=None, blk_size=None, perm=None, opt=None) -> dict:
+    """Symbolic analysis with a handle's options (tile, priority model); opt: d3m_options or None."""
+    import numpy as np
+    pat, keep = make_pattern(colptr, rowidx, m, blk_size)
+    pp = None
+    if perm is not None:
+        perm = np.ascontiguousarray(perm, dtype=np.int32)
+        pp = perm.ctypes.data_as(POINTER(c_int32))
+    info = d3m_info()
+    check(load().d3m_analyze_opts(ctypes.byref(pat), pp, ctypes.byref(opt) if opt is not None else None,
+                                  ctypes.byref(info)))
+    return info.as_dict()
 
 
 def d3m_analyze(colptr, rowidx, m=None, blk_size=None, perm=None, tile: int = 128) -> dict:

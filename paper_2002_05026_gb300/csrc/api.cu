@@ -63,6 +63,8 @@ struct d3m_ctx {
   void* opA = nullptr;
   void* opB = nullptr;
   void* Sacc = nullptr;
+  void* E = nullptr;                 // pivot mode: sub-diagonals of the 2 x 2 pivot blocks [NT][b]
+  int32_t* piv = nullptr;            // pivot mode: permutation of every diagonal tile [NT][b]
   int64_t* trace = nullptr;
   TcMaps maps;
   GatherTcMaps gmaps;                // L's operand planes for the tensor-core solve gathers
@@ -350,6 +352,31 @@ int d3m_analyze(const d3m_pattern* pat, const int32_t* perm, int32_t tile, d3m_i
   return D3M_OK;
 }
 
+int d3m_analyze_opts(const d3m_pattern* pat, const int32_t* perm, const d3m_options* opt, d3m_info* info) {
+  if (!info) return set_err(nullptr, D3M_ERR_INVALID, "info is NULL");
+  d3m_options o;
+  if (opt) o = *opt;
+  else d3m_default_options(&o);
+  const int prec = o.precision;
+  if (prec != D3M_FP64 && prec != D3M_MIXED_BF16X3 && prec != D3M_MIXED_SIMT32 && prec != D3M_MIXED_TF32)
+    return set_err(nullptr, D3M_ERR_INVALID, "unknown precision");
+  const bool fp64 = prec == D3M_FP64, tc = prec == D3M_MIXED_BF16X3 || prec == D3M_MIXED_TF32;
+  const int b = tc ? 128 : 64;
+  if (o.tile != 0 && o.tile != b)
+    return set_err(nullptr, D3M_ERR_INVALID, "tile must be 0 or " + std::to_string(b) + " for this precision");
+  if (!(o.prio_slack >= 0)) o.prio_slack = 0.08;
+  if (o.seg_group <= 0) o.seg_group = fp64 ? 1 : 8;
+  Symbolic S;
+  std::string err;
+  int rc = analyze(pat, perm, b, true, S, err, o.prio_slack, o.seg_group, o.task_cost);
+  if (rc != D3M_OK) return set_err(nullptr, rc, err);
+  std::memset(info, 0, sizeof(*info));
+  fill_structure(S, info);
+  info->omega = NAN;
+  info->omega_first = NAN;
+  return D3M_OK;
+}
+
 }  // extern "C"
 
 // Shared by d3m_create and d3m_create_batch; inst_blk (batched handles) holds the first block
@@ -383,12 +410,20 @@ static int create_impl(d3m_handle* out, const d3m_pattern* pat, const int32_t* p
     return set_err(nullptr, D3M_ERR_INVALID, "tile must be 0 or " + std::to_string(h->tc ? 128 : 64) + " for this precision");
   }
   h->csize = h->fp64 ? sizeof(double2) : sizeof(float2);
+  if (h->opt.pivot != 0 && h->opt.pivot != 1) {
+    delete h;
+    return set_err(nullptr, D3M_ERR_INVALID, "pivot must be 0 or 1");
+  }
+  if (h->opt.pivot && h->tc) {
+    delete h;
+    return set_err(nullptr, D3M_ERR_INVALID, "pivoting needs a SIMT engine (D3M_FP64 or D3M_MIXED_SIMT32)");
+  }
   std::string err;
   // mixed precision: a tile's Schur updates from up to 8 source blocks form one update task (the
   // per-task epilogue through the accumulator dominates short segments); FP64 is DFMA bound and
   // keeps one task per source block
   if (h->opt.seg_group <= 0) h->opt.seg_group = h->fp64 ? 1 : 8;
-  int rc = analyze(pat, perm, h->b, true, h->S, err, h->opt.prio_slack, h->opt.seg_group);
+  int rc = analyze(pat, perm, h->b, true, h->S, err, h->opt.prio_slack, h->opt.seg_group, h->opt.task_cost);
   if (rc != D3M_OK) {
     delete h;
     return set_err(nullptr, rc, err);
@@ -463,6 +498,12 @@ static int create_impl(d3m_handle* out, const d3m_pattern* pat, const int32_t* p
   h->D = dalloc<unsigned char>(h, (size_t)S.NT * b * h->csize);
   h->Sacc = dalloc<unsigned char>(h, (size_t)std::max<int64_t>(1, S.n_acc) * b * b * h->csize);
   if (!h->L || !h->Linv || !h->D || !h->Sacc) return set_err(h, D3M_ERR_OOM, "cudaMalloc failed for the factor tiles");
+  if (h->opt.pivot) {
+    h->E = dalloc<unsigned char>(h, (size_t)S.NT * b * h->csize);
+    h->piv = dalloc<int32_t>(h, (size_t)S.NT * b);
+    if (!h->E || !h->piv) return set_err(h, D3M_ERR_OOM, "cudaMalloc failed for the pivot blocks");
+    CUDA_TRY(h, cudaMemset(h->E, 0, (size_t)S.NT * b * h->csize));
+  }
   if (h->tc) {
     // operand planes, 8 bytes per complex element either way: bf16 A: [tile][2 splits][2 planes]
     // [b rows][b], B: [tile][2][2][b][b]; tf32 A and B: [tile][2 planes][b rows][b]
@@ -618,6 +659,16 @@ static int create_impl(d3m_handle* out, const d3m_pattern* pat, const int32_t* p
     UPLOAD(d_brow, brow);
     UPLOAD(d_bcol, bcol);
     UPLOAD(d_rt, h->rtile_host);
+    {
+      // the two residual contributions of every stored block (as stored, and transposed)
+      std::vector<int32_t> eu(S.nnzb_K, -1), et(S.nnzb_K, -1);
+      for (int64_t e = 0; e < nres; ++e) (S.res_tr[e] ? et : eu)[S.res_blk[e]] = (int32_t)e;
+      int32_t *d_eu = nullptr, *d_et = nullptr;
+      UPLOAD(d_eu, eu);
+      UPLOAD(d_et, et);
+      r.blk_eu = d_eu;
+      r.blk_et = d_et;
+    }
     r.ks_plane = d_ksp;
     r.xs_plane = d_xsp;
     r.res_row = d_rrow;
@@ -812,6 +863,9 @@ static int enqueue_factor(d3m_ctx* h, const void* Kin, bool kdev, cudaStream_t s
   p.trace = h->trace;
   p.timeout_ns = h->opt.timeout_ns;
   p.piv_tol = 1e3 * (h->fp64 ? 1.1102230246251565e-16 : 5.9604644775390625e-08);
+  p.pivot = h->opt.pivot;
+  p.E = h->E;
+  p.piv = h->piv;
   if (h->trace) CUDA_TRY(h, cudaMemsetAsync(h->trace, 0xff, (size_t)10 * ntiles * sizeof(int64_t), st));
   ev_begin(h, d3m_ctx::EV_FACTOR, st);
   if (h->tc) rc = launch_factor_tc(p, h->maps, h->tf32, h->nsm, st);
@@ -914,6 +968,7 @@ static int sweep(d3m_ctx* h, const double2* src, double2* dst, int nrhs, int acc
   a.dmax = h->dmax;
   a.ld_norm = h->opt.max_nrhs;
   a.tcmaps = h->gather_tc ? &h->gmaps : nullptr;
+  a.E = h->E;
   a.nsm = h->nsm;
   ev_begin(h, d3m_ctx::EV_SWEEP, st);
   int rc = launch_sweep(a, h->fp64, st);
@@ -1158,6 +1213,35 @@ int d3m_get_pivots(d3m_handle h, int32_t j, void* host_out, void* stream) {
       const float2 f = ((float2*)buf.data())[u];
       out[u] = make_double2(f.x, f.y);
     }
+  }
+  return D3M_OK;
+}
+
+int d3m_get_pivot_blocks(d3m_handle h, int32_t j, void* e_out, int32_t* perm_out, void* stream) {
+  if (!h) return set_err(nullptr, D3M_ERR_INVALID, "handle is NULL");
+  const Symbolic& S = h->S;
+  if (j < 0 || j >= S.N) return set_err(h, D3M_ERR_INVALID, "bad block index");
+  CUDA_TRY(h, cudaStreamSynchronize((cudaStream_t)stream));
+  const int mj = S.m[j];
+  std::vector<unsigned char> buf((size_t)mj * h->csize, 0);
+  std::vector<int32_t> pv(mj);
+  for (int u = 0; u < mj; ++u) pv[u] = u % h->b;
+  if (h->E) {
+    CUDA_TRY(h, cudaMemcpy(buf.data(), (unsigned char*)h->E + (size_t)S.tstart[j] * h->b * h->csize, buf.size(),
+                           cudaMemcpyDeviceToHost));
+    CUDA_TRY(h, cudaMemcpy(pv.data(), h->piv + (size_t)S.tstart[j] * h->b, (size_t)mj * sizeof(int32_t),
+                           cudaMemcpyDeviceToHost));
+  }
+  for (int u = 0; u < mj; ++u) {
+    if (e_out) {
+      double2* out = (double2*)e_out;
+      if (h->fp64) out[u] = ((double2*)buf.data())[u];
+      else {
+        const float2 f = ((float2*)buf.data())[u];
+        out[u] = make_double2(f.x, f.y);
+      }
+    }
+    if (perm_out) perm_out[u] = (u / h->b) * h->b + pv[u];   // tile-local order + tile offset
   }
   return D3M_OK;
 }

@@ -50,6 +50,9 @@ struct FactorParams {
   int64_t* trace;        // [ntasks][8] task records, or nullptr
   int64_t timeout_ns;
   double piv_tol;        // breakdown: |d| < piv_tol * max|S| of the diagonal tile
+  int pivot;             // 1: Bunch-Kaufman pivoting inside diagonal tiles (SIMT engine)
+  void* E;               // [NT][b] sub-diagonal entry of each 2 x 2 pivot block (pivot mode), 0 else
+  int32_t* piv;          // [NT][b] permutation of each diagonal tile (pivot mode)
 };
 
 // ------------------------------------------------------------------ complex helpers
@@ -139,11 +142,11 @@ constexpr int TRACE_W = 10;
 __device__ __forceinline__ void trace_begin(const FactorParams& p, int task) {
   if (p.trace && threadIdx.x == 0) p.trace[TRACE_W * (int64_t)task] = (int64_t)globaltimer_ns();
 }
-__device__ __forceinline__ void trace_end(const FactorParams& p, int task, int flags, int tile) {
+__device__ __forceinline__ void trace_end(const FactorParams& p, int task, int flags, int tile, int nk) {
   if (p.trace && threadIdx.x == 0) {
     p.trace[TRACE_W * (int64_t)task + 1] = (int64_t)globaltimer_ns();
     p.trace[TRACE_W * (int64_t)task + 2] = (int64_t)sm_id();
-    p.trace[TRACE_W * (int64_t)task + 3] = (int64_t)flags | ((int64_t)tile << 8);
+    p.trace[TRACE_W * (int64_t)task + 3] = (int64_t)flags | ((int64_t)tile << 8) | ((int64_t)nk << 40);
   }
 }
 // phase mark k (0..3) of a task
@@ -218,7 +221,7 @@ __device__ __forceinline__ void sched_complete(const FactorParams& p, int task) 
   __syncthreads();
   if (p.trace) {
     const TileTask& T = p.tasks[task];
-    trace_end(p, task, T.flags, T.tile);
+    trace_end(p, task, T.flags, T.tile, T.nk);
   }
   if (threadIdx.x < 32) {
     __threadfence();  // release: this block's tile writes before the counter updates

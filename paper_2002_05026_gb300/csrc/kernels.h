@@ -49,6 +49,7 @@ struct SweepLaunch {
   const void* InvT;                // transposed inverse tiles (diagonal included)
   const int64_t* invT_off;         // device [N]: first tile of block k in InvT
   const struct GatherTcMaps* tcmaps;  // operand-plane maps for the tensor-core gathers, or nullptr
+  const void* E;                   // pivot mode: sub-diagonals of the 2 x 2 blocks of D, or nullptr
   int nsm;
   int64_t launches;                // out: kernels launched by launch_sweep
 };
@@ -78,6 +79,8 @@ struct ResidualTc {
   const int32_t* res_src;        // [contributions] source block g
   const int32_t* res_blk;        // [contributions] stored block
   const int32_t* res_tr;         // [contributions] 1: the stored block is used transposed
+  const int32_t* blk_eu;         // [nnzb] residual contribution of the block as stored (row block f)
+  const int32_t* blk_et;         // [nnzb] its transposed contribution (row block g), -1 for f == g
   const int64_t* ks_plane;       // [contributions] first K digit plane
   const int64_t* xs_plane;       // [N] first x digit plane of block g (within a group's planes)
   int64_t xs_total;              // x digit planes of one right-hand-side group

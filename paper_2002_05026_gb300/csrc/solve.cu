@@ -660,6 +660,31 @@ __global__ void diag_scale_kernel(typename CT<R>::C* __restrict__ Y, const typen
   for (int j = 0; j < nrhs; ++j) Y[(int64_t)j * npad + g] = cdiv(Y[(int64_t)j * npad + g], d);
 }
 
+// z = D^{-1} y with the 1 x 1 and 2 x 2 blocks of a pivoted factorization (E[g] != 0: rows g and
+// g + 1 of one tile form the block [[D[g], E[g]], [E[g], D[g+1]]]; the first row's thread
+// solves both)
+template <typename R>
+__global__ void diag_scale_bk_kernel(typename CT<R>::C* __restrict__ Y, const typename CT<R>::C* __restrict__ D,
+                                     const typename CT<R>::C* __restrict__ E, int64_t npad, int nrhs, int b) {
+  using C = typename CT<R>::C;
+  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (g >= npad) return;
+  const int c = (int)(g % b);
+  if (c > 0 && (E[g - 1].x != 0 || E[g - 1].y != 0)) return;   // second row of a 2 x 2 block
+  if (c + 1 < b && (E[g].x != 0 || E[g].y != 0)) {
+    const C d1 = D[g], d2 = D[g + 1], e = E[g];
+    const C det = csub(cmul(d1, d2), cmul(e, e));
+    for (int j = 0; j < nrhs; ++j) {
+      const C y1 = Y[(int64_t)j * npad + g], y2 = Y[(int64_t)j * npad + g + 1];
+      Y[(int64_t)j * npad + g] = cdiv(csub(cmul(d2, y1), cmul(e, y2)), det);
+      Y[(int64_t)j * npad + g + 1] = cdiv(csub(cmul(d1, y2), cmul(e, y1)), det);
+    }
+    return;
+  }
+  const C d = D[g];
+  for (int j = 0; j < nrhs; ++j) Y[(int64_t)j * npad + g] = cdiv(Y[(int64_t)j * npad + g], d);
+}
+
 // load one block's rows of Y into sv[row][rc]
 template <typename C>
 __device__ __forceinline__ void load_rows(const C* __restrict__ Y, int64_t npad, int64_t r0, int rows, int j0,
@@ -1475,6 +1500,12 @@ static int sweep_impl(SweepLaunch& a, cudaStream_t st) {
       cudaError_t e = launch_chain(lv, true);
       if (e != cudaSuccess) return (int)e;
     }
+    const bool bk = a.E != nullptr;
+    if (bk) {
+      // pivoted factor: z = D^{-1} y with its 2 x 2 blocks as one pass between the sweeps
+      diag_scale_bk_kernel<R><<<(unsigned)gblocks, nthreads, 0, st>>>(Y, D, (const C*)a.E, a.npad, a.nrhs, b);
+      ++a.launches;
+    }
     for (int lv = a.nlevels - 1; lv >= 0; --lv) {
       const int64_t i0 = a.bwd_group_ptr[lv], i1 = a.bwd_group_ptr[lv + 1];
       if (i1 > i0) {
@@ -1483,12 +1514,12 @@ static int sweep_impl(SweepLaunch& a, cudaStream_t st) {
       }
       cs.slot_ptr = a.bwd_slot_ptr;
       cs.has_partials = i1 > i0;
-      cs.apply_d = 1;
+      cs.apply_d = bk ? 0 : 1;
       if (i1 > i0 && a.lev_maxcnt_bwd[lv] > EXT_REDUCE) {
         const int64_t ntl = a.lev_tile_ptr[lv + 1] - a.lev_tile_ptr[lv];
         const int64_t nthr = ntl * b * a.nrhs;
         launch_pdl(reduce_kernel<R>, dim3((unsigned)((nthr + 31) / 32)), dim3(ET), 0, st, a.lev_tiles + a.lev_tile_ptr[lv], (int)ntl,
-                                                                       a.bwd_slot_ptr, P, Y, a.npad, b, a.nrhs, nh, D, mk);
+                                                                       a.bwd_slot_ptr, P, Y, a.npad, b, a.nrhs, nh, bk ? nullptr : D, mk);
         ++a.launches;
         cs.has_partials = 0;
         cs.apply_d = 0;
@@ -1536,7 +1567,8 @@ static int sweep_impl(SweepLaunch& a, cudaStream_t st) {
     block_fwd_kernel<R><<<dim3(nb, ny), GT, bsm, st>>>(bs, L, Linv, Y);
     ++a.launches;
   }
-  diag_scale_kernel<R><<<(unsigned)gblocks, nthreads, 0, st>>>(Y, D, a.npad, a.nrhs);
+  if (a.E) diag_scale_bk_kernel<R><<<(unsigned)gblocks, nthreads, 0, st>>>(Y, D, (const C*)a.E, a.npad, a.nrhs, b);
+  else diag_scale_kernel<R><<<(unsigned)gblocks, nthreads, 0, st>>>(Y, D, a.npad, a.nrhs);
   ++a.launches;
   for (int lv = a.nlevels - 1; lv >= 0; --lv) {
     const int64_t i0 = a.bwd_group_ptr[lv], i1 = a.bwd_group_ptr[lv + 1];

@@ -39,7 +39,7 @@ def _as_colmajor(B):
 
 
 def _options(precision, max_nrhs, refine_tol, refine_max_iter, timeout_ns, fp64_omega, debug_flags, graphs=False,
-             prio_slack=None, seg_group=0):
+             prio_slack=None, seg_group=0, task_cost=None, pivot=False):
     opt = _abi.d3m_default_options()
     opt.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     opt.max_nrhs = max_nrhs
@@ -53,6 +53,10 @@ def _options(precision, max_nrhs, refine_tol, refine_max_iter, timeout_ns, fp64_
     if prio_slack is not None:
         opt.prio_slack = float(prio_slack)
     opt.seg_group = int(seg_group)
+    if task_cost is not None:
+        for q in range(6):
+            opt.task_cost[q] = float(task_cost[q])
+    opt.pivot = int(bool(pivot))
     return opt
 
 
@@ -62,13 +66,13 @@ class D3M:
     def __init__(self, colptr, rowidx, m=None, blk_size=None, perm=None, precision="bf16x3",
                  max_nrhs: int = 32, refine_tol: float = 1e-12, refine_max_iter: int = 20,
                  timeout_ns: int = 0, fp64_omega: bool = False, debug_flags: int = 0, graphs: bool = False,
-                 prio_slack=None, seg_group: int = 0, stream=None):
+                 prio_slack=None, seg_group: int = 0, task_cost=None, pivot: bool = False, stream=None):
         lib = load()
         self._lib = lib
         self.h = c_void_p()
         pat, self._keep = _abi.make_pattern(colptr, rowidx, m, blk_size)
         opt = _options(precision, max_nrhs, refine_tol, refine_max_iter, timeout_ns, fp64_omega, debug_flags, graphs,
-                       prio_slack, seg_group)
+                       prio_slack, seg_group, task_cost, pivot)
         pp = None
         if perm is not None:
             self._perm = np.ascontiguousarray(perm, dtype=np.int32)
@@ -145,10 +149,18 @@ class D3M:
               self.h)
         return out
 
+    def pivot_blocks(self, j: int, mj: int):
+        """(e, perm) of block column j: 2 x 2 sub-diagonals of D_j (c128) and the pivot order."""
+        e = np.zeros(mj, dtype=np.complex128)
+        perm = np.zeros(mj, dtype=np.int32)
+        check(self._lib.d3m_get_pivot_blocks(self.h, j, c_void_p(e.ctypes.data), perm.ctypes.data_as(POINTER(c_int32)),
+                                             c_void_p(_stream_ptr(self.stream))), self.h)
+        return e, perm
+
     def trace(self) -> np.ndarray:
         """Task records of the last factorization (handle created with debug_flags=2):
-        int64 [ntasks, 10] = start_ns, end_ns, sm_id, flags | tile << 8, t1..t4, ready_ns, releaser
-        (task id = row)."""
+        int64 [ntasks, 10] = start_ns, end_ns, sm_id, flags | tile << 8 | nk << 40, t1..t4, ready_ns,
+        releaser (task id = row; flags 1 = diagonal tile, 4 = update task; nk = tile products)."""
         cnt = ctypes.c_int64()
         check(self._lib.d3m_get_trace(self.h, None, 0, ctypes.byref(cnt), c_void_p(_stream_ptr(self.stream))), self.h)
         out = np.zeros((cnt.value, 10), dtype=np.int64)
@@ -184,7 +196,7 @@ class D3MBatch(D3M):
 
     def __init__(self, instances, perms=None, precision="bf16x3", max_nrhs: int = 32, refine_tol: float = 1e-12,
                  refine_max_iter: int = 20, timeout_ns: int = 0, fp64_omega: bool = False, debug_flags: int = 0,
-                 graphs: bool = False, stream=None):
+                 graphs: bool = False, task_cost=None, stream=None):
         lib = load()
         self._lib = lib
         self.h = c_void_p()
@@ -207,7 +219,8 @@ class D3MBatch(D3M):
             pp = (POINTER(c_int32) * count)(*[
                 ctypes.cast(None, POINTER(c_int32)) if q is None else q.ctypes.data_as(POINTER(c_int32))
                 for q in self._perms])
-        opt = _options(precision, max_nrhs, refine_tol, refine_max_iter, timeout_ns, fp64_omega, debug_flags, graphs)
+        opt = _options(precision, max_nrhs, refine_tol, refine_max_iter, timeout_ns, fp64_omega, debug_flags, graphs,
+                       task_cost=task_cost)
         self.precision = precision
         self.stream = stream
         rc = lib.d3m_create_batch(ctypes.byref(self.h), count, pats, pp, ctypes.byref(opt),

@@ -123,3 +123,39 @@ def test_block_diagonal_union_analysis(lib):
         assert info[k] == sum(i[k] for i in infos), k
     assert info["factor_flops"] == pytest.approx(sum(i["factor_flops"] for i in infos), rel=1e-12)
     assert info["etree_depth"] == max(i["etree_depth"] for i in infos)
+
+
+def test_task_cost_model_changes_priority_set(lib):
+    # the scheduler's priority lane is built from a task-duration model (Sec. II weights the dual
+    # tasks with benchmarked kernel times): a measured model that makes the diagonal tasks cheaper
+    # and the updates dearer moves tasks in and out of the lane; an all-zero model is the default
+    from paper_2002_05026_gb300 import d3m_analyze_opts, d3m_default_options
+    colptr, rowidx = synth.lower_pattern(8, 8, 1)
+    perm = O.nd_order(8, 8, 1)
+    base = d3m_analyze_opts(colptr, rowidx, m=512, perm=perm, opt=d3m_default_options())
+    zero = d3m_default_options()
+    for q in range(6):
+        zero.task_cost[q] = 0.0
+    assert d3m_analyze_opts(colptr, rowidx, m=512, perm=perm, opt=zero)["prio_tasks"] == base["prio_tasks"]
+    meas = d3m_default_options()
+    for q, v in enumerate((2500.0, 4200.0, 48000.0, 300.0, 9000.0, 4100.0)):   # ns, e.g. a fitted trace
+        meas.task_cost[q] = v
+    got = d3m_analyze_opts(colptr, rowidx, m=512, perm=perm, opt=meas)
+    assert got["prio_tasks"] != base["prio_tasks"]
+    assert got["ntiles"] == base["ntiles"] and got["factor_flops"] == base["factor_flops"]
+
+
+def test_pivoting_needs_a_simt_engine(lib):
+    # Bunch-Kaufman pivoting inside diagonal tiles is built in the SIMT engines only: a tensor-core
+    # handle with pivot = 1 is refused at creation, before any device work
+    import ctypes
+    colptr, rowidx = synth.lower_pattern(2, 2, 1)
+    pat, keep = _abi.make_pattern(colptr, rowidx, 16, None)
+    for prec in (_abi.D3M_MIXED_BF16X3, _abi.D3M_MIXED_TF32):
+        opt = _abi.d3m_default_options()
+        opt.precision = prec
+        opt.pivot = 1
+        h = ctypes.c_void_p()
+        rc = lib.d3m_create(ctypes.byref(h), ctypes.byref(pat), None, ctypes.byref(opt), None)
+        assert rc == _abi.D3M_ERR_INVALID and not h
+        assert b"SIMT" in lib.d3m_last_error(None)
