@@ -193,59 +193,91 @@ __global__ void __launch_bounds__(256) kblock_max_kernel(ResidualTc p) {
   if ((threadIdx.x & 31) == 0 && mx) atomicMax(p.Kmax_bits + blk, mx);
 }
 
-// (2) digits of one oriented block (residual contribution e), row tile rt: 2 ND planes per 32-column
-// chunk ([part][digit], 128 rows x 32 bf16 each); thread = one row and 16 consecutive columns.
-// Also adds the row's |K| sums (both parts, for ||K||_inf) into rowsum.
+// (2) digits of the stored blocks: one tile of 128 rows x 16 columns of a stored block K_fg
+// (f >= g) per CTA (39 KB of shared memory: five CTAs per SM).  Every entry's 2 ND digits are
+// extracted once, into shared memory (int8), and written to the planes of both residual
+// contributions of the block: row block f (untransposed: planes of 128 rows u x 32 columns c, of
+// which this CTA fills 16 columns) and, for f != g, row block g (transposed: planes of 128 rows c
+// x 32 columns u, of which this CTA fills 16 rows).  K is read once, coalesced along u
+// (column-major blocks).  Also adds |K| row sums (rows u) and column sums (rows c of the
+// transposed use) into rowsum, for ||K||_inf.
+constexpr int KD_U = 128, KD_C = 16, KD_LD = 136;   // tile rows, tile columns, padded byte row
+constexpr size_t KD_SMEM = (size_t)2 * ND * KD_C * KD_LD;
+
 __global__ void __launch_bounds__(256) kdigits_kernel(ResidualTc p) {
-  const int e = blockIdx.x, rt = blockIdx.y;
-  const int f = p.res_row[e], g = p.res_src[e], blk = p.res_blk[e];
-  const bool tr = p.res_tr[e] != 0;
+  extern __shared__ __align__(16) signed char sdig[];   // [2 ND][KD_C][KD_LD]
+  __shared__ float s_cs[KD_C];
+  const int blk = blockIdx.x, rt = blockIdx.y, ct = blockIdx.z;
+  const int f = p.blk_row[blk], g = p.blk_col[blk];
   const int mf = p.m_orig[f], mg = p.m_orig[g];
-  if (rt * 128 >= mf) return;                      // the grid covers the tallest row block
-  const int u = rt * 128 + (threadIdx.x & 127);
-  const int half = threadIdx.x >> 7;
-  const int nkc = (mg + 31) / 32;
+  if (rt * KD_U >= mf || ct * KD_C >= mg) return;       // the grid covers the largest blocks
   const int E = scale_exp(p.Kmax_bits[blk]);
   const double2* Kb = p.K + p.kblk_off[blk];
   const bool diag = (f == g);
-  unsigned short* planes = p.kdig + (int64_t)p.ks_plane[e] * (128 * 32) +
-                           (int64_t)rt * nkc * 2 * ND * (128 * 32);
+  const int tid = threadIdx.x, lane = tid & 31, ul = tid & 127, ch = tid >> 7;
+  const int u = rt * KD_U + ul;
+  if (tid < KD_C) s_cs[tid] = 0.f;
+  __syncthreads();
   float rs = 0.f;
-  for (int kc = 0; kc < nkc; ++kc)
-#pragma unroll 1
-    for (int h8 = 0; h8 < 2; ++h8) {
-      // 8 columns at a time: one 16-byte word per digit plane
-      unsigned short dr[ND][8], di[ND][8];
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const int c = kc * 32 + half * 16 + h8 * 8 + q;
-        double2 v = make_double2(0.0, 0.0);
-        if (u < mf && c < mg) {
-          // oriented entry (u, c): stored (f, g) column-major -> c * mf + u; transposed: the stored
-          // block is (g, f), entry (c, u) at u * mg + c
-          v = __ldg(Kb + (tr ? (int64_t)u * mg + c : (int64_t)c * mf + u));
-          const float fx = (float)v.x, fy = (float)v.y;
-          rs += sqrtf(fx * fx + fy * fy);
-          if (diag && u == c) v = make_double2(0.0, 0.0);
-        }
-        int a[ND], b[ND];
-        digits64(v.x, E, a);
-        digits64(v.y, E, b);
-#pragma unroll
-        for (int s = 0; s < ND; ++s) {
-          dr[s][q] = bf16_of_int(a[s]);
-          di[s][q] = bf16_of_int(b[s]);
-        }
-      }
-      unsigned short* base =
-          planes + (int64_t)kc * 2 * ND * (128 * 32) + (int64_t)(u - rt * 128) * 32 + half * 16 + h8 * 8;
-#pragma unroll
-      for (int s = 0; s < ND; ++s) {
-        *reinterpret_cast<uint4*>(base + (int64_t)(0 * ND + s) * (128 * 32)) = *reinterpret_cast<uint4*>(&dr[s][0]);
-        *reinterpret_cast<uint4*>(base + (int64_t)(1 * ND + s) * (128 * 32)) = *reinterpret_cast<uint4*>(&di[s][0]);
-      }
+  for (int q = 0; q < KD_C / 2; ++q) {
+    const int cl = ch + 2 * q, c = ct * KD_C + cl;
+    double2 v = make_double2(0.0, 0.0);
+    float a = 0.f;
+    if (u < mf && c < mg) {
+      v = __ldg(Kb + (int64_t)c * mf + u);
+      const float fx = (float)v.x, fy = (float)v.y;
+      a = sqrtf(fx * fx + fy * fy);
+      if (diag && u == c) v = make_double2(0.0, 0.0);
     }
+    rs += a;
+    float cs = a;
+    for (int o = 16; o > 0; o >>= 1) cs += __shfl_xor_sync(0xffffffffu, cs, o);
+    if (lane == 0) atomicAdd(&s_cs[cl], cs);
+    int dr[ND], di[ND];
+    digits64(v.x, E, dr);
+    digits64(v.y, E, di);
+#pragma unroll
+    for (int s = 0; s < ND; ++s) {
+      sdig[((0 * ND + s) * KD_C + cl) * KD_LD + ul] = (signed char)dr[s];
+      sdig[((1 * ND + s) * KD_C + cl) * KD_LD + ul] = (signed char)di[s];
+    }
+  }
   if (u < mf) atomicAdd(p.rowsum + p.xoff_orig[f] + u, rs);
+  __syncthreads();
+  if (!diag && tid < KD_C && ct * KD_C + tid < mg) atomicAdd(p.rowsum + p.xoff_orig[g] + ct * KD_C + tid, s_cs[tid]);
+  auto bf8 = [](const signed char* v8, int stride) {
+    unsigned short h[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) h[q] = bf16_of_int((int)v8[q * stride]);
+    return *reinterpret_cast<uint4*>(h);
+  };
+  // untransposed planes (row block f): 16-byte units (row r, 8 columns); the CTA's 16 columns
+  // are units 2 (ct % 2) .. + 1 of chunk ct / 2
+  {
+    const int nkc = (mg + 31) / 32;
+    const int kc = ct / 2, u0 = (ct & 1) * 2;
+    unsigned short* base = p.kdig + ((int64_t)p.ks_plane[p.blk_eu[blk]] + (int64_t)rt * nkc * 2 * ND) * (128 * 32);
+    for (int w = tid; w < 2 * ND * 128 * 2; w += 256) {
+      const int j2 = w & 1, r = (w >> 1) & 127, pl = w >> 8;
+      const uint4 val = bf8(sdig + ((int64_t)pl * KD_C + j2 * 8) * KD_LD + r, KD_LD);
+      *reinterpret_cast<uint4*>(base + ((int64_t)kc * 2 * ND + pl) * (128 * 32) + r * 32 + (u0 + j2) * 8) = val;
+    }
+  }
+  // transposed planes (row block g, source f): rows c (16 of the 128 of tile ct / 8), 32-column
+  // chunks of u; a unit is 8 consecutive u of one c (consecutive shared bytes)
+  if (!diag) {
+    const int nkc = (mf + 31) / 32;
+    unsigned short* base =
+        p.kdig + ((int64_t)p.ks_plane[p.blk_et[blk]] + (int64_t)(ct / 8) * nkc * 2 * ND) * (128 * 32);
+    const int r0 = (ct & 7) * KD_C;
+    for (int w = tid; w < 2 * ND * 4 * KD_C * 4; w += 256) {
+      const int j8 = w & 3, cl = (w >> 2) & (KD_C - 1), kcl = (w >> 6) & 3, pl = w >> 8;
+      const int kc = rt * 4 + kcl;
+      if (kc >= nkc) continue;
+      const uint4 val = bf8(sdig + ((int64_t)pl * KD_C + cl) * KD_LD + kcl * 32 + j8 * 8, 1);
+      *reinterpret_cast<uint4*>(base + ((int64_t)kc * 2 * ND + pl) * (128 * 32) + (r0 + cl) * 32 + j8 * 8) = val;
+    }
+  }
 }
 
 // (3) ||K_i||_inf = max row sum over the rows of instance i
@@ -616,7 +648,8 @@ int launch_kdigits(const ResidualTc& p, int nnzb, int nres, int max_rtiles, int 
   cudaMemsetAsync(p.Kmax_bits, 0, (size_t)nnzb * sizeof(unsigned long long), st);
   cudaMemsetAsync(p.rowsum, 0, (size_t)p.n * sizeof(float), st);
   kblock_max_kernel<<<dim3((unsigned)nnzb, 8), 256, 0, st>>>(p);
-  kdigits_kernel<<<dim3((unsigned)nres, (unsigned)max_rtiles), 256, 0, st>>>(p);
+  cudaFuncSetAttribute(kdigits_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)KD_SMEM);
+  kdigits_kernel<<<dim3((unsigned)nnzb, (unsigned)max_rtiles, (unsigned)(8 * max_rtiles)), 256, KD_SMEM, st>>>(p);
   rowsum_max_kernel<<<nblk, 128, 0, st>>>(p.rowsum, p.xoff_orig, p.m_orig, p.inst, nblk, p.kmax);
   return (int)cudaGetLastError();
 }
