@@ -51,6 +51,9 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--report-modules", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--seg-group", type=int, default=0, help="source blocks per update task (0 = library default)")
+    ap.add_argument("--graphs", type=int, default=0, help="1: replay the factorization and each refinement "
+                    "step as CUDA graphs")
     return ap.parse_args()
 
 
@@ -566,7 +569,8 @@ def main():
     perm = d3m_order_grid_nd(w["nx"], w["ny"], w["nz"])
     stream = torch.cuda.current_stream()
     sp = ctypes.c_void_p(stream.cuda_stream)
-    s = D3M(p.colptr, p.rowidx, m=p.m, perm=perm, precision=args.precision, max_nrhs=nrhs)
+    s = D3M(p.colptr, p.rowidx, m=p.m, perm=perm, precision=args.precision, max_nrhs=nrhs, graphs=bool(args.graphs),
+            seg_group=args.seg_group)
     lib = s._lib
     mem_sample()
 
@@ -740,6 +744,7 @@ def main():
                 "vs_baseline": None, "dtype": dtype, "data": "synthetic",
                 "config": {"workload": args.workload, "grid": [w["nx"], w["ny"], w["nz"]], "m": w["m"],
                            "n": p.n, "nrhs": nrhs, "k2": w["k2"], "tau": w["tau"], "precision": args.precision,
+                           "cuda_graphs": bool(args.graphs), "seg_group": args.seg_group or "default",
                            "order": "nested dissection", "l2": "inputs larger than L2 (K is "
                            f"{K.numel() * 16 / 1e9:.2f} GB)"},
                 "roofline": roof, "kernels": breakdown,

@@ -423,7 +423,10 @@ static int create_impl(d3m_handle* out, const d3m_pattern* pat, const int32_t* p
   // per-task epilogue through the accumulator dominates short segments); FP64 is DFMA bound and
   // keeps one task per source block
   if (h->opt.seg_group <= 0) h->opt.seg_group = h->fp64 ? 1 : 8;
-  int rc = analyze(pat, perm, h->b, true, h->S, err, h->opt.prio_slack, h->opt.seg_group, h->opt.task_cost);
+  // the tensor-core gathers of the solve (split-BF16x3 engine) sum up to 16 items of one
+  // destination in tensor memory
+  const int ggroup = (h->tc && !h->tf32) ? 16 : 1;
+  int rc = analyze(pat, perm, h->b, true, h->S, err, h->opt.prio_slack, h->opt.seg_group, h->opt.task_cost, ggroup);
   if (rc != D3M_OK) {
     delete h;
     return set_err(nullptr, rc, err);

@@ -210,7 +210,9 @@ __global__ void __launch_bounds__(256) kdigits_kernel(ResidualTc p) {
   const int blk = blockIdx.x, rt = blockIdx.y, ct = blockIdx.z;
   const int f = p.blk_row[blk], g = p.blk_col[blk];
   const int mf = p.m_orig[f], mg = p.m_orig[g];
-  if (rt * KD_U >= mf || ct * KD_C >= mg) return;       // the grid covers the largest blocks
+  // the grid covers the largest blocks; a tile of columns past mg still runs while it lies in the
+  // block's last 32-column chunk, so that every chunk's padding columns get zero digits
+  if (rt * KD_U >= mf || ct * KD_C >= (mg + 31) / 32 * 32) return;
   const int E = scale_exp(p.Kmax_bits[blk]);
   const double2* Kb = p.K + p.kblk_off[blk];
   const bool diag = (f == g);

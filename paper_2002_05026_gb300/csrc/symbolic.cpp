@@ -34,7 +34,8 @@ static int fail(std::string& err, const char* msg, long a = -1, long b = -1) {
 }
 
 int analyze(const d3m_pattern* pat, const int32_t* perm_in, int b, bool build_tasks,
-            Symbolic& s, std::string& err, double prio_slack, int seg_group, const double* task_cost) {
+            Symbolic& s, std::string& err, double prio_slack, int seg_group, const double* task_cost,
+            int gather_group) {
   if (seg_group < 1) seg_group = 1;
   if (!pat || !pat->colptr || !pat->rowidx) return fail(err, "pattern or its arrays are NULL");
   const int N = pat->nblk;
@@ -460,10 +461,14 @@ int analyze(const d3m_pattern* pat, const int32_t* perm_in, int b, bool build_ta
   // products of up to G consecutive items of one destination into one partial slot; G grows
   // with the level's width so that wide levels write (and the chains read) fewer partials
   // while narrow levels keep one item per block.  slot_ptr[dst] = first slot of the level
-  // (relative to its start) | number of slots << 32.
+  // (relative to its start) | number of slots << 32.  gather_group caps G: 1 for the SIMT
+  // gathers (per-item latency dominates), more for the tensor-core gathers, whose items of one
+  // group accumulate in tensor memory.
   const int nh = s.b / 64;
-  constexpr int64_t kGatherBlocks = 304;     // about two gather blocks per SM
-  constexpr int64_t kGroupMax = 1;     // one item per gather block: per-item latency dominates
+  // about two gather blocks per SM (SIMT); four groups per SM for the tensor-core gathers, whose
+  // blocks are persistent over the level's groups
+  const int64_t kGatherBlocks = gather_group > 1 ? 1216 : 304;
+  const int64_t kGroupMax = std::max(1, gather_group);
   s.fwd_group_ptr.assign(s.nlevels + 1, 0);
   s.bwd_group_ptr.assign(s.nlevels + 1, 0);
   s.fwd_groups.clear();

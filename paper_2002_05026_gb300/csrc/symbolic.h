@@ -126,7 +126,7 @@ struct Symbolic {
 // all zeros = the built-in model.
 int analyze(const d3m_pattern* pat, const int32_t* perm, int b, bool build_tasks,
             Symbolic& s, std::string& err, double prio_slack = 0.08, int seg_group = 1,
-            const double* task_cost = nullptr);
+            const double* task_cost = nullptr, int gather_group = 1);
 
 // Grid nested dissection (see d3m_order_grid_nd).
 int order_grid_nd(int nx, int ny, int nz, std::vector<int32_t>& perm);
