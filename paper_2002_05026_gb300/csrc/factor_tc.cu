@@ -756,12 +756,7 @@ __global__ void __launch_bounds__(NTHR, 1)
           else diag_panel_update(sS, Wt, Xk, k, tid - 64);
           __syncthreads();
         }
-        // L_JJ (unit lower) and D_J
-        float2* Lt = Lg + (int64_t)T.tile * TB * TB;
-        for (int i = tid; i < TB * TB; i += NTHR) {
-          const int rr = i >> 7, cc = i & 127;
-          Lt[i] = (cc < rr) ? sS[rr * LDS + cc] : make_float2(cc == rr ? 1.f : 0.f, 0.f);
-        }
+        // D_J (L_JJ and L_JJ^{-1} in complex64 are written after the release, below)
         if (tid < TB) Dg[(int64_t)T.col * TB + tid] = s_d[tid];
       }
       trace_mark(p, task, 2);
@@ -783,12 +778,7 @@ __global__ void __launch_bounds__(NTHR, 1)
           if (!(amin >= (float)p.piv_tol * smax)) set_error(p.ctl, D3M_ERR_PIVOT, task);
         }
       }
-      // Linv (c64, for the solve) and T_J = D^{-1} Linv as B planes [-T_i, T_r, T_i] x [hi, lo]
-      float2* Li = Linv + (int64_t)T.col * TB * TB;
-      for (int i = tid; i < TB * TB; i += NTHR) {
-        const int rr = i >> 7, cc = i & 127;
-        Li[i] = (cc < rr) ? sS[cc * LDS + rr] : make_float2(cc == rr ? 1.f : 0.f, 0.f);
-      }
+      // T_J = D^{-1} Linv as B planes
       {
         // T_J = D^{-1} L^{-1}: row n, columns k (X[n][k] = sS[k][n] for k < n); coalesced 16-byte
         // stores of the planes: bf16 [T_r, T_i] x [hi, lo] (16 threads per 256-byte plane row) or
@@ -925,12 +915,8 @@ __global__ void __launch_bounds__(NTHR, 1)
       }
       __syncthreads();
       // ---------------------------------------------------------------- phase 4: store L_IJ
-      // coalesced: L c64 row-major; operand planes opA (L) and opB (W = L D_J), 16 bytes per thread
-      float4* Lt4 = reinterpret_cast<float4*>(Lg + (int64_t)T.tile * TB * TB);
-      for (int e = tid; e < TB * 64; e += NTHR) {
-        const int rr = e >> 6, u = e & 63;
-        Lt4[e] = stg[rr * 64 + (u ^ (rr & 7))];
-      }
+      // operand planes opA (L) and opB (W = L D_J), 16 bytes per thread; the complex64 copy of L
+      // (read only by the solve sweeps) is written after the release, below
       uint4* A = reinterpret_cast<uint4*>(opA + (int64_t)T.tile * ROWS * TB * (TF ? 4 : 2));
       uint4* B = reinterpret_cast<uint4*>(opB + (int64_t)T.tile * ROWS * TB * (TF ? 4 : 2));
       for (int it = tid; it < TB * 16; it += NTHR) {
@@ -985,6 +971,25 @@ __global__ void __launch_bounds__(NTHR, 1)
     }
     tc_fence_before();
     sched_complete(p, task);
+    // Complex64 copies of the tile for the solve sweeps: no task of this factorization reads
+    // them, so they are written after the successors are released (off the critical path).
+    if (is_diag) {
+      const float2* sS = reinterpret_cast<const float2*>(smem);
+      float2* Lt = Lg + (int64_t)T.tile * TB * TB;
+      float2* Li = Linv + (int64_t)T.col * TB * TB;
+      for (int i = tid; i < TB * TB; i += NTHR) {
+        const int rr = i >> 7, cc = i & 127;
+        Lt[i] = (cc < rr) ? sS[rr * LDS + cc] : make_float2(cc == rr ? 1.f : 0.f, 0.f);
+        Li[i] = (cc < rr) ? sS[cc * LDS + rr] : make_float2(cc == rr ? 1.f : 0.f, 0.f);
+      }
+    } else {
+      const float4* stg = reinterpret_cast<const float4*>(smem);
+      float4* Lt4 = reinterpret_cast<float4*>(Lg + (int64_t)T.tile * TB * TB);
+      for (int e = tid; e < TB * 64; e += NTHR) {
+        const int rr = e >> 6, u = e & 63;
+        Lt4[e] = stg[rr * 64 + (u ^ (rr & 7))];
+      }
+    }
   }
 
   // teardown: after a failed wait, give in-flight copies and MMAs time to land (bounded)
