@@ -137,17 +137,10 @@ __device__ __forceinline__ uint32_t sm_id() {
   return s;
 }
 
-// Trace record of one task: start (at pop) and end (before its successors are released).
+// Trace record of one task: start (at pop or claim) and end (before its successors are released).
 constexpr int TRACE_W = 10;
 __device__ __forceinline__ void trace_begin(const FactorParams& p, int task) {
   if (p.trace && threadIdx.x == 0) p.trace[TRACE_W * (int64_t)task] = (int64_t)globaltimer_ns();
-}
-__device__ __forceinline__ void trace_end(const FactorParams& p, int task, int flags, int tile, int nk) {
-  if (p.trace && threadIdx.x == 0) {
-    p.trace[TRACE_W * (int64_t)task + 1] = (int64_t)globaltimer_ns();
-    p.trace[TRACE_W * (int64_t)task + 2] = (int64_t)sm_id();
-    p.trace[TRACE_W * (int64_t)task + 3] = (int64_t)flags | ((int64_t)tile << 8) | ((int64_t)nk << 40);
-  }
 }
 // phase mark k (0..3) of a task
 __device__ __forceinline__ void trace_mark(const FactorParams& p, int task, int k) {
@@ -214,37 +207,82 @@ __device__ __forceinline__ int sched_pop(const FactorParams& p, int* s_task, int
   return t;
 }
 
+// Non-blocking claim of a normal-lane task by ONE thread of a block that is still running a
+// task (-1 if none is ready now).  The block's claimed slot (*s_pending) is taken if it has been
+// filled; without one, a slot is claimed only when the lane holds a pushed task past its head
+// (a pusher reserves a slot before writing it, so that wait is short; it is bounded all the
+// same).  Priority-lane tasks are left to blocks that are free now.  The claimed task is ready,
+// so it never depends on the caller's running task.
+__device__ __forceinline__ int sched_claim_normal(const FactorParams& p, int* s_pending) {
+  if (ld_volatile(&p.ctl->abort)) return -1;
+  int pend = *s_pending;
+  if (pend < 0) {
+    const int h = ld_volatile(&p.ctl->head);
+    if (h < ld_volatile(&p.ctl->tail) && atomicCAS(&p.ctl->head, h, h + 1) == h) pend = h;
+    else return -1;
+  }
+  int task = -1;
+  if (pend < p.n_norm) {
+    const uint64_t t0 = globaltimer_ns();
+    for (;;) {
+      task = ld_volatile(&p.ready[pend]);
+      if (task >= 0) {
+        pend = -1;
+        break;
+      }
+      if (pend >= ld_volatile(&p.ctl->tail)) break;   // not pushed yet: the block keeps the slot
+      if (ld_volatile(&p.ctl->abort) || globaltimer_ns() - t0 > (uint64_t)p.timeout_ns) {
+        set_error(p.ctl, D3M_ERR_TIMEOUT, -1 - pend);
+        task = -1;
+        break;
+      }
+    }
+  }
+  *s_pending = pend;
+  if (task >= 0) {
+    __threadfence();  // acquire, as in sched_pop
+    if (p.trace) p.trace[TRACE_W * (int64_t)task] = (int64_t)globaltimer_ns();
+  }
+  return task;
+}
+
+// Release the successors of `task`: one whole warp calls this (lane = its lane) after the
+// block's writes of the task are ordered before it (proxy fence + block barrier).
+__device__ __forceinline__ void release_successors(const FactorParams& p, int task, int lane) {
+  if (p.trace && lane == 0) {
+    const TileTask& T = p.tasks[task];
+    p.trace[TRACE_W * (int64_t)task + 1] = (int64_t)globaltimer_ns();
+    p.trace[TRACE_W * (int64_t)task + 2] = (int64_t)sm_id();
+    p.trace[TRACE_W * (int64_t)task + 3] = (int64_t)T.flags | ((int64_t)T.tile << 8) | ((int64_t)T.nk << 40);
+  }
+  __threadfence();  // release: this block's tile writes before the counter updates
+  const int64_t e0 = p.succ_ptr[task], e1 = p.succ_ptr[task + 1];
+  for (int64_t e = e0 + lane; e < e1; e += 32) {
+    const int s = p.succ[e];
+    if (atomicSub(&p.cnt[s], 1) == 1) {
+      if (p.trace) {
+        p.trace[TRACE_W * (int64_t)s + 8] = (int64_t)globaltimer_ns();
+        p.trace[TRACE_W * (int64_t)s + 9] = task;
+      }
+      __threadfence();
+      if (p.tasks[s].flags & TF_PRIO) {
+        const int pos = atomicAdd(&p.ctl->tail_hi, 1);
+        atomicExch(&p.ready_hi[pos], s);
+      } else {
+        const int pos = atomicAdd(&p.ctl->tail, 1);
+        atomicExch(&p.ready[pos], s);
+      }
+    }
+  }
+  if (lane == 0) atomicAdd(&p.ctl->done, 1);
+}
+
 // Release the successors of `task` (all threads call; warp 0 does the work).
 __device__ __forceinline__ void sched_complete(const FactorParams& p, int task) {
   // writes of this thread become visible to later TMA (async-proxy) reads of other blocks
   asm volatile("fence.proxy.async.global;" ::: "memory");
   __syncthreads();
-  if (p.trace) {
-    const TileTask& T = p.tasks[task];
-    trace_end(p, task, T.flags, T.tile, T.nk);
-  }
-  if (threadIdx.x < 32) {
-    __threadfence();  // release: this block's tile writes before the counter updates
-    const int64_t e0 = p.succ_ptr[task], e1 = p.succ_ptr[task + 1];
-    for (int64_t e = e0 + threadIdx.x; e < e1; e += 32) {
-      const int s = p.succ[e];
-      if (atomicSub(&p.cnt[s], 1) == 1) {
-        if (p.trace) {
-          p.trace[TRACE_W * (int64_t)s + 8] = (int64_t)globaltimer_ns();
-          p.trace[TRACE_W * (int64_t)s + 9] = task;
-        }
-        __threadfence();
-        if (p.tasks[s].flags & TF_PRIO) {
-          const int pos = atomicAdd(&p.ctl->tail_hi, 1);
-          atomicExch(&p.ready_hi[pos], s);
-        } else {
-          const int pos = atomicAdd(&p.ctl->tail, 1);
-          atomicExch(&p.ready[pos], s);
-        }
-      }
-    }
-    if (threadIdx.x == 0) atomicAdd(&p.ctl->done, 1);
-  }
+  if (threadIdx.x < 32) release_successors(p, task, threadIdx.x);
 }
 
 __device__ __forceinline__ void record_pivot_stats(Ctl* ctl, float amin, float amax) {

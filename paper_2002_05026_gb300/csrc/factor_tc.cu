@@ -552,6 +552,7 @@ __global__ void __launch_bounds__(NTHR, 1)
   __shared__ __align__(8) uint64_t bar_full[NSTAGE], bar_empty[NSTAGE], bar_tfull[2], bar_tempty[2], bar_acc, bar_acc2;
   __shared__ uint32_t s_tmem;
   __shared__ int s_task, s_pending;
+  __shared__ int s_next[2];                      // task claimed ahead, by task parity (-1: none)
   if (threadIdx.x == 0) s_pending = -1;          // read and written by thread 0 only
   __shared__ float s_red[NTHR / 32];
 
@@ -594,10 +595,15 @@ __global__ void __launch_bounds__(NTHR, 1)
   uint32_t n_acc = 0, n_acc2 = 0;
   bool failed = false;
 
-  for (;;) {
-    const int task = sched_pop(p, &s_task, &s_pending);
-    if (task < 0) break;
+  // The MMA-issuing lane claims the block's next normal-lane task while the products of an
+  // update or triangular-solve task run (sched_claim_normal), and warp 2 releases a finished
+  // task's successors while warps 0 and 1 already issue the next task's loads and products, so
+  // neither the queue round trips nor the release sit between two tasks.
+  int it = 0;
+  int task = sched_pop(p, &s_task, &s_pending);
+  while (task >= 0) {
     const TileTask T = p.tasks[task];
+    if (tid == 32) s_next[it & 1] = -1;
     const uint64_t deadline = globaltimer_ns() + (uint64_t)p.timeout_ns;
     const int nchunk = T.nk * NCH;
     asm volatile("fence.proxy.async.global;" ::: "memory");
@@ -648,6 +654,7 @@ __global__ void __launch_bounds__(NTHR, 1)
             ++g_mma;
           }
           mma_commit(smem_u32(&bar_acc));
+          if (T.flags & TF_UPDATE) s_next[it & 1] = sched_claim_normal(p, &s_pending);
         }
         __syncwarp();
       }
@@ -680,316 +687,324 @@ __global__ void __launch_bounds__(NTHR, 1)
         for (int i = 0; i < 32; i += 2)
           slot[(i / 2) * TB] = make_float4(kin[i].x - vr[i], kin[i].y - vi[i], kin[i + 1].x - vr[i + 1], kin[i + 1].y - vi[i + 1]);
       }
-      __syncthreads();
-      trace_mark(p, task, 3);
-      tc_fence_before();
-      sched_complete(p, task);
-      continue;
-    }
-
-    // off-diagonal: prefetch the first two chunks of T_J (B operand of the TRSM product)
-    if (!is_diag && tid == 0) {
-      for (int c = 0; c < 2; ++c) {
-        const uint32_t s = t_load & 1, use = t_load >> 1;
-        if (!mbar_wait(smem_u32(&bar_tempty[s]), (use & 1) ^ 1, deadline)) { failed = true; break; }
-        const uint32_t sb = smem_u32(smem + SMEM_T + s * STAGE_B);
-        const uint32_t fb = smem_u32(&bar_tfull[s]);
-        mbar_expect_tx(fb, STAGE_B);
-#pragma unroll
-        for (int q = 0; q < Eng<TF>::NPB; ++q)
-          tma_load_2d(sb + q * PLANE, &mapB, c * KC, T.diag * (int)ROWS + q * 128, fb);
-        ++t_load;
-      }
-    }
-
-    // ---------------------------------------------------------------- phase 2: S = S_in - acc
-    if (is_diag) {
-      float2* sS = reinterpret_cast<float2*>(smem);   // [128][129]
-      float2* s_d = reinterpret_cast<float2*>(smem + DIAG_AUX);
-      for (int pass = 0; pass < 2; ++pass) {
-        const int c0 = half * 64 + pass * 32;
-        float vr[32], vi[32];
-        if (nchunk > 0) {
-          tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + ACC1 + c0, vr);
-          tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + ACC1 + 128 + c0, vi);
-        } else {
-#pragma unroll
-          for (int i = 0; i < 32; ++i) vr[i] = vi[i] = 0.f;
-        }
-        float2 kin[32];
-        load_s_in(T, p.K, s_in ? Sa : nullptr, r, c0, kin);
-#pragma unroll
-        for (int i = 0; i < 32; ++i) sS[r * LDS + c0 + i] = make_float2(kin[i].x - vr[i], kin[i].y - vi[i]);
-      }
-      tc_fence_before();
-      __syncthreads();
-      trace_mark(p, task, 1);
-      // max |S| over the real lower triangle (breakdown scale)
-      float mx = 0.f;
-      for (int i = tid; i < TB * TB; i += NTHR) {
-        const int rr = i >> 7, cc = i & 127;
-        if (cc <= rr && rr < T.rv) mx = fmaxf(mx, sqrtf(cabs2(sS[rr * LDS + cc])));
-      }
-      for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-      if (lane == 0) s_red[warp] = mx;
-      __syncthreads();
-      // Unpivoted LDL^T and X = L^{-1}, blocked in panels of DW columns (the diag_* functions)
-      {
-        // the upper triangle starts at zero (it accumulates the blocks of X)
-        for (int i = tid; i < TB * TB; i += NTHR) {
-          const int rr = i >> 7, cc = i & 127;
-          if (cc > rr) sS[rr * LDS + cc] = make_float2(0.f, 0.f);
-        }
-        float2* Wt = s_d + TB;
-        float2* Xd = Wt + DW * WT_LD;                 // [2][DW][XD_LD]
-        __syncthreads();
-        if (warp < 2) diag_block_2warps(sS, s_d, Xd, 0, warp, lane);
-        __syncthreads();
-#pragma unroll 1
-        for (int k = 0; k < TB / DW; ++k) {
-          float2* Xk = Xd + (k & 1) * DW * XD_LD;
-          diag_panel_solve(sS, s_d, Wt, Xk, k, tid);
-          if (k == TB / DW - 1) break;
-          diag_next_block(sS, Wt, k, tid);
-          __syncthreads();
-          if (warp < 2) diag_block_2warps(sS, s_d, Xd + ((k + 1) & 1) * DW * XD_LD, DW * (k + 1), warp, lane);
-          else diag_panel_update(sS, Wt, Xk, k, tid - 64);
-          __syncthreads();
-        }
-        // D_J (L_JJ and L_JJ^{-1} in complex64 are written after the release, below)
-        if (tid < TB) Dg[(int64_t)T.col * TB + tid] = s_d[tid];
-      }
-      trace_mark(p, task, 2);
-      if (tid < 32) {
-        float smax = 0.f;
-        for (int w = 0; w < NTHR / 32; ++w) smax = fmaxf(smax, s_red[w]);
-        float amin = 3.0e38f, amax = 0.f;
-        for (int c = tid; c < T.cv; c += 32) {
-          const float a = sqrtf(cabs2(s_d[c]));
-          amin = fminf(amin, a);
-          amax = fmaxf(amax, a);
-        }
-        for (int o = 16; o > 0; o >>= 1) {
-          amin = fminf(amin, __shfl_xor_sync(0xffffffffu, amin, o));
-          amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
-        }
-        if (tid == 0) {
-          record_pivot_stats(p.ctl, amin, amax);
-          if (!(amin >= (float)p.piv_tol * smax)) set_error(p.ctl, D3M_ERR_PIVOT, task);
-        }
-      }
-      // T_J = D^{-1} Linv as B planes
-      {
-        // T_J = D^{-1} L^{-1}: row n, columns k (X[n][k] = sS[k][n] for k < n); coalesced 16-byte
-        // stores of the planes: bf16 [T_r, T_i] x [hi, lo] (16 threads per 256-byte plane row) or
-        // tf32 [T_r, T_i] (32 threads per 512-byte plane row)
-        uint4* Bt = reinterpret_cast<uint4*>(opB + (int64_t)T.tile * ROWS * TB * (TF ? 4 : 2));
-        for (int it = tid; it < TB * 16; it += NTHR) {
-          const int n = it >> 4, c8 = it & 15;
-          const float2 dinv = cdiv(make_float2(1.f, 0.f), s_d[n]);
-          float tr[8], ti[8];
-#pragma unroll
-          for (int k8 = 0; k8 < 8; ++k8) {
-            const int k = c8 * 8 + k8;
-            const float2 lv = (k < n) ? sS[k * LDS + n] : make_float2(k == n ? 1.f : 0.f, 0.f);
-            const float2 tv = cmul(dinv, lv);
-            tr[k8] = tv.x;
-            ti[k8] = tv.y;
-          }
-          if constexpr (TF) {
-            Bt[(0 * 128 + n) * 32 + 2 * c8] = pack4_tf32(tr);
-            Bt[(0 * 128 + n) * 32 + 2 * c8 + 1] = pack4_tf32(tr + 4);
-            Bt[(1 * 128 + n) * 32 + 2 * c8] = pack4_tf32(ti);
-            Bt[(1 * 128 + n) * 32 + 2 * c8 + 1] = pack4_tf32(ti + 4);
-          } else {
-            __nv_bfloat16 h[2][8], lo[2][8];
-#pragma unroll
-            for (int k8 = 0; k8 < 8; ++k8) {
-              split2(tr[k8], h[0][k8], lo[0][k8]);
-              split2(ti[k8], h[1][k8], lo[1][k8]);
-            }
-#pragma unroll
-            for (int pl = 0; pl < 2; ++pl) {
-              Bt[((0 * 256 + pl * 128) + n) * 16 + c8] = pack8(h[pl]);
-              Bt[((1 * 256 + pl * 128) + n) * 16 + c8] = pack8(lo[pl]);
-            }
-          }
-        }
-      }
-      __syncthreads();
-      trace_mark(p, task, 3);
     } else {
-      // S planes for the TRSM product (A operand, SW64 K-major, 4 chunks)
-      for (int pass = 0; pass < 2; ++pass) {
-        const int c0 = half * 64 + pass * 32;
-        float vr[32], vi[32];
-        if (nchunk > 0) {
-          tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + ACC1 + c0, vr);
-          tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + ACC1 + 128 + c0, vi);
-        } else {
+      // ------------------------------------------------------------ final task
+      // off-diagonal: prefetch the first two chunks of T_J (B operand of the TRSM product)
+      if (!is_diag && tid == 0) {
+        for (int c = 0; c < 2; ++c) {
+          const uint32_t s = t_load & 1, use = t_load >> 1;
+          if (!mbar_wait(smem_u32(&bar_tempty[s]), (use & 1) ^ 1, deadline)) { failed = true; break; }
+          const uint32_t sb = smem_u32(smem + SMEM_T + s * STAGE_B);
+          const uint32_t fb = smem_u32(&bar_tfull[s]);
+          mbar_expect_tx(fb, STAGE_B);
 #pragma unroll
-          for (int i = 0; i < 32; ++i) vr[i] = vi[i] = 0.f;
+          for (int q = 0; q < Eng<TF>::NPB; ++q)
+            tma_load_2d(sb + q * PLANE, &mapB, c * KC, T.diag * (int)ROWS + q * 128, fb);
+          ++t_load;
         }
-        {
+      }
+
+      // ---------------------------------------------------------------- phase 2: S = S_in - acc
+      if (is_diag) {
+        float2* sS = reinterpret_cast<float2*>(smem);   // [128][129]
+        float2* s_d = reinterpret_cast<float2*>(smem + DIAG_AUX);
+        for (int pass = 0; pass < 2; ++pass) {
+          const int c0 = half * 64 + pass * 32;
+          float vr[32], vi[32];
+          if (nchunk > 0) {
+            tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + ACC1 + c0, vr);
+            tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + ACC1 + 128 + c0, vi);
+          } else {
+#pragma unroll
+            for (int i = 0; i < 32; ++i) vr[i] = vi[i] = 0.f;
+          }
           float2 kin[32];
           load_s_in(T, p.K, s_in ? Sa : nullptr, r, c0, kin);
 #pragma unroll
-          for (int i = 0; i < 32; ++i) {
-            vr[i] = kin[i].x - vr[i];
-            vi[i] = kin[i].y - vi[i];
+          for (int i = 0; i < 32; ++i) sS[r * LDS + c0 + i] = make_float2(kin[i].x - vr[i], kin[i].y - vi[i]);
+        }
+        tc_fence_before();
+        __syncthreads();
+        trace_mark(p, task, 1);
+        // max |S| over the real lower triangle (breakdown scale)
+        float mx = 0.f;
+        for (int i = tid; i < TB * TB; i += NTHR) {
+          const int rr = i >> 7, cc = i & 127;
+          if (cc <= rr && rr < T.rv) mx = fmaxf(mx, sqrtf(cabs2(sS[rr * LDS + cc])));
+        }
+        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if (lane == 0) s_red[warp] = mx;
+        __syncthreads();
+        // Unpivoted LDL^T and X = L^{-1}, blocked in panels of DW columns (the diag_* functions)
+        {
+          // the upper triangle starts at zero (it accumulates the blocks of X)
+          for (int i = tid; i < TB * TB; i += NTHR) {
+            const int rr = i >> 7, cc = i & 127;
+            if (cc > rr) sS[rr * LDS + cc] = make_float2(0.f, 0.f);
+          }
+          float2* Wt = s_d + TB;
+          float2* Xd = Wt + DW * WT_LD;                 // [2][DW][XD_LD]
+          __syncthreads();
+          if (warp < 2) diag_block_2warps(sS, s_d, Xd, 0, warp, lane);
+          __syncthreads();
+#pragma unroll 1
+          for (int k = 0; k < TB / DW; ++k) {
+            float2* Xk = Xd + (k & 1) * DW * XD_LD;
+            diag_panel_solve(sS, s_d, Wt, Xk, k, tid);
+            if (k == TB / DW - 1) break;
+            diag_next_block(sS, Wt, k, tid);
+            __syncthreads();
+            if (warp < 2) diag_block_2warps(sS, s_d, Xd + ((k + 1) & 1) * DW * XD_LD, DW * (k + 1), warp, lane);
+            else diag_panel_update(sS, Wt, Xk, k, tid - 64);
+            __syncthreads();
+          }
+          // D_J (L_JJ and L_JJ^{-1} in complex64 are written after the release, below)
+          if (tid < TB) Dg[(int64_t)T.col * TB + tid] = s_d[tid];
+        }
+        trace_mark(p, task, 2);
+        if (tid < 32) {
+          float smax = 0.f;
+          for (int w = 0; w < NTHR / 32; ++w) smax = fmaxf(smax, s_red[w]);
+          float amin = 3.0e38f, amax = 0.f;
+          for (int c = tid; c < T.cv; c += 32) {
+            const float a = sqrtf(cabs2(s_d[c]));
+            amin = fminf(amin, a);
+            amax = fmaxf(amax, a);
+          }
+          for (int o = 16; o > 0; o >>= 1) {
+            amin = fminf(amin, __shfl_xor_sync(0xffffffffu, amin, o));
+            amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+          }
+          if (tid == 0) {
+            record_pivot_stats(p.ctl, amin, amax);
+            if (!(amin >= (float)p.piv_tol * smax)) set_error(p.ctl, D3M_ERR_PIVOT, task);
           }
         }
-        if constexpr (TF) {
+        // T_J = D^{-1} Linv as B planes
+        {
+          // T_J = D^{-1} L^{-1}: row n, columns k (X[n][k] = sS[k][n] for k < n); coalesced 16-byte
+          // stores of the planes: bf16 [T_r, T_i] x [hi, lo] (16 threads per 256-byte plane row) or
+          // tf32 [T_r, T_i] (32 threads per 512-byte plane row)
+          uint4* Bt = reinterpret_cast<uint4*>(opB + (int64_t)T.tile * ROWS * TB * (TF ? 4 : 2));
+          for (int it = tid; it < TB * 16; it += NTHR) {
+            const int n = it >> 4, c8 = it & 15;
+            const float2 dinv = cdiv(make_float2(1.f, 0.f), s_d[n]);
+            float tr[8], ti[8];
 #pragma unroll
-          for (int hh = 0; hh < 2; ++hh) {
-            unsigned char* ch = smem + SMEM_S + (c0 / KC + hh) * STAGE_A;
-            store_smem_plane16_tf32(ch + 0 * PLANE, r, vr + 16 * hh);
-            store_smem_plane16_tf32(ch + 1 * PLANE, r, vi + 16 * hh);
-          }
-        } else {
-          unsigned char* ch = smem + SMEM_S + (c0 / KC) * STAGE_A;
-          store_smem_plane32(ch + 0 * PLANE, ch + 2 * PLANE, r, vr);
-          store_smem_plane32(ch + 1 * PLANE, ch + 3 * PLANE, r, vi);
-        }
-      }
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      tc_fence_before();
-      __syncthreads();
-      trace_mark(p, task, 1);
-      // ---------------------------------------------------------------- phase 3: TRSM product
-      if (warp == 0) {
-        if (lane == 0) {
-          for (int c = 2; c < NCH && !failed; ++c) {
-            const uint32_t s = t_load & 1, use = t_load >> 1;
-            if (!mbar_wait(smem_u32(&bar_tempty[s]), (use & 1) ^ 1, deadline)) { failed = true; break; }
-            const uint32_t sb = smem_u32(smem + SMEM_T + s * STAGE_B);
-            const uint32_t fb = smem_u32(&bar_tfull[s]);
-            mbar_expect_tx(fb, STAGE_B);
+            for (int k8 = 0; k8 < 8; ++k8) {
+              const int k = c8 * 8 + k8;
+              const float2 lv = (k < n) ? sS[k * LDS + n] : make_float2(k == n ? 1.f : 0.f, 0.f);
+              const float2 tv = cmul(dinv, lv);
+              tr[k8] = tv.x;
+              ti[k8] = tv.y;
+            }
+            if constexpr (TF) {
+              Bt[(0 * 128 + n) * 32 + 2 * c8] = pack4_tf32(tr);
+              Bt[(0 * 128 + n) * 32 + 2 * c8 + 1] = pack4_tf32(tr + 4);
+              Bt[(1 * 128 + n) * 32 + 2 * c8] = pack4_tf32(ti);
+              Bt[(1 * 128 + n) * 32 + 2 * c8 + 1] = pack4_tf32(ti + 4);
+            } else {
+              __nv_bfloat16 h[2][8], lo[2][8];
 #pragma unroll
-            for (int q = 0; q < Eng<TF>::NPB; ++q)
-              tma_load_2d(sb + q * PLANE, &mapB, c * KC, T.diag * (int)ROWS + q * 128, fb);
-            ++t_load;
+              for (int k8 = 0; k8 < 8; ++k8) {
+                split2(tr[k8], h[0][k8], lo[0][k8]);
+                split2(ti[k8], h[1][k8], lo[1][k8]);
+              }
+#pragma unroll
+              for (int pl = 0; pl < 2; ++pl) {
+                Bt[((0 * 256 + pl * 128) + n) * 16 + c8] = pack8(h[pl]);
+                Bt[((1 * 256 + pl * 128) + n) * 16 + c8] = pack8(lo[pl]);
+              }
+            }
           }
         }
-        __syncwarp();
-      } else if (warp == 1) {
-        if (lane == 0) {
-          tc_fence_after();
-          for (int c = 0; c < NCH && !failed; ++c) {
-            const uint32_t s = t_mma & 1, use = t_mma >> 1;
-            if (!mbar_wait(smem_u32(&bar_tfull[s]), use & 1, deadline)) { failed = true; break; }
+        __syncthreads();
+        trace_mark(p, task, 3);
+      } else {
+        // S planes for the TRSM product (A operand, SW64 K-major, 4 chunks)
+        for (int pass = 0; pass < 2; ++pass) {
+          const int c0 = half * 64 + pass * 32;
+          float vr[32], vi[32];
+          if (nchunk > 0) {
+            tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + ACC1 + c0, vr);
+            tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + ACC1 + 128 + c0, vi);
+          } else {
+#pragma unroll
+            for (int i = 0; i < 32; ++i) vr[i] = vi[i] = 0.f;
+          }
+          {
+            float2 kin[32];
+            load_s_in(T, p.K, s_in ? Sa : nullptr, r, c0, kin);
+#pragma unroll
+            for (int i = 0; i < 32; ++i) {
+              vr[i] = kin[i].x - vr[i];
+              vi[i] = kin[i].y - vi[i];
+            }
+          }
+          if constexpr (TF) {
+#pragma unroll
+            for (int hh = 0; hh < 2; ++hh) {
+              unsigned char* ch = smem + SMEM_S + (c0 / KC + hh) * STAGE_A;
+              store_smem_plane16_tf32(ch + 0 * PLANE, r, vr + 16 * hh);
+              store_smem_plane16_tf32(ch + 1 * PLANE, r, vi + 16 * hh);
+            }
+          } else {
+            unsigned char* ch = smem + SMEM_S + (c0 / KC) * STAGE_A;
+            store_smem_plane32(ch + 0 * PLANE, ch + 2 * PLANE, r, vr);
+            store_smem_plane32(ch + 1 * PLANE, ch + 3 * PLANE, r, vi);
+          }
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        tc_fence_before();
+        __syncthreads();
+        trace_mark(p, task, 1);
+        // ---------------------------------------------------------------- phase 3: TRSM product
+        if (warp == 0) {
+          if (lane == 0) {
+            for (int c = 2; c < NCH && !failed; ++c) {
+              const uint32_t s = t_load & 1, use = t_load >> 1;
+              if (!mbar_wait(smem_u32(&bar_tempty[s]), (use & 1) ^ 1, deadline)) { failed = true; break; }
+              const uint32_t sb = smem_u32(smem + SMEM_T + s * STAGE_B);
+              const uint32_t fb = smem_u32(&bar_tfull[s]);
+              mbar_expect_tx(fb, STAGE_B);
+#pragma unroll
+              for (int q = 0; q < Eng<TF>::NPB; ++q)
+                tma_load_2d(sb + q * PLANE, &mapB, c * KC, T.diag * (int)ROWS + q * 128, fb);
+              ++t_load;
+            }
+          }
+          __syncwarp();
+        } else if (warp == 1) {
+          if (lane == 0) {
             tc_fence_after();
-            const uint32_t ab = smem_u32(smem + SMEM_S + c * STAGE_A);
-            const uint32_t tb = smem_u32(smem + SMEM_T + s * STAGE_B);
-            chunk_mma<TF>(tmem + ACC2, ab, tb, c == 0);
-            mma_commit(smem_u32(&bar_tempty[s]));
-            ++t_mma;
+            for (int c = 0; c < NCH && !failed; ++c) {
+              const uint32_t s = t_mma & 1, use = t_mma >> 1;
+              if (!mbar_wait(smem_u32(&bar_tfull[s]), use & 1, deadline)) { failed = true; break; }
+              tc_fence_after();
+              const uint32_t ab = smem_u32(smem + SMEM_S + c * STAGE_A);
+              const uint32_t tb = smem_u32(smem + SMEM_T + s * STAGE_B);
+              chunk_mma<TF>(tmem + ACC2, ab, tb, c == 0);
+              mma_commit(smem_u32(&bar_tempty[s]));
+              ++t_mma;
+            }
+            mma_commit(smem_u32(&bar_acc2));
+            s_next[it & 1] = sched_claim_normal(p, &s_pending);
           }
-          mma_commit(smem_u32(&bar_acc2));
+          __syncwarp();
         }
-        __syncwarp();
-      }
-      if (!mbar_wait(smem_u32(&bar_acc2), n_acc2 & 1, deadline)) failed = true;
-      ++n_acc2;
-      tc_fence_after();
-      if (__syncthreads_or(failed)) {
-        if (tid == 0) set_error(p.ctl, D3M_ERR_TIMEOUT, task);
-        break;
-      }
-      trace_mark(p, task, 2);
-      // D_J into the (now idle) TRSM stage area; L_IJ (c64) staged row-major in [0, 128K) with the
-      // 16-byte units of each 128-byte span XOR-swizzled by the row (conflict-free row writes)
-      float2* s_d = reinterpret_cast<float2*>(smem + SMEM_T);
-      if (tid < TB) s_d[tid] = ld_cg(Dg + (int64_t)T.col * TB + tid);
-      float4* stg = reinterpret_cast<float4*>(smem);
-      for (int pass = 0; pass < 2; ++pass) {
-        const int c0 = half * 64 + pass * 32;
-        float lr[32], li[32];
-        tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + ACC2 + c0, lr);
-        tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + ACC2 + 128 + c0, li);
-#pragma unroll
-        for (int i = 0; i < 32; i += 2) {
-          const int u = (c0 + i) >> 1;
-          stg[r * 64 + (u ^ (r & 7))] = make_float4(lr[i], li[i], lr[i + 1], li[i + 1]);
+        if (!mbar_wait(smem_u32(&bar_acc2), n_acc2 & 1, deadline)) failed = true;
+        ++n_acc2;
+        tc_fence_after();
+        if (__syncthreads_or(failed)) {
+          if (tid == 0) set_error(p.ctl, D3M_ERR_TIMEOUT, task);
+          break;
         }
-      }
-      __syncthreads();
-      // ---------------------------------------------------------------- phase 4: store L_IJ
-      // operand planes opA (L) and opB (W = L D_J), 16 bytes per thread; the complex64 copy of L
-      // (read only by the solve sweeps) is written after the release, below
-      uint4* A = reinterpret_cast<uint4*>(opA + (int64_t)T.tile * ROWS * TB * (TF ? 4 : 2));
-      uint4* B = reinterpret_cast<uint4*>(opB + (int64_t)T.tile * ROWS * TB * (TF ? 4 : 2));
-      for (int it = tid; it < TB * 16; it += NTHR) {
-        const int rr = it >> 4, c8 = it & 15;   // row, group of 8 columns
-        float2 l[8];
+        trace_mark(p, task, 2);
+        // D_J into the (now idle) TRSM stage area; L_IJ (c64) staged row-major in [0, 128K) with the
+        // 16-byte units of each 128-byte span XOR-swizzled by the row (conflict-free row writes)
+        float2* s_d = reinterpret_cast<float2*>(smem + SMEM_T);
+        if (tid < TB) s_d[tid] = ld_cg(Dg + (int64_t)T.col * TB + tid);
+        float4* stg = reinterpret_cast<float4*>(smem);
+        for (int pass = 0; pass < 2; ++pass) {
+          const int c0 = half * 64 + pass * 32;
+          float lr[32], li[32];
+          tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + ACC2 + c0, lr);
+          tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + ACC2 + 128 + c0, li);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          const int u = c8 * 4 + k;
-          const float4 v = stg[rr * 64 + (u ^ (rr & 7))];
-          l[2 * k] = make_float2(v.x, v.y);
-          l[2 * k + 1] = make_float2(v.z, v.w);
-        }
-        float pv[4][8];   // planes: L_r, L_i, W_r, W_i
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-          const float2 w = cmul(l[k], s_d[c8 * 8 + k]);
-          pv[0][k] = l[k].x;
-          pv[1][k] = l[k].y;
-          pv[2][k] = w.x;
-          pv[3][k] = w.y;
-        }
-        if constexpr (TF) {
-          // opA rows: plane * 128 + row (L_r, L_i); opB rows: the same for W; 32 uint4 per 512-byte row
-#pragma unroll
-          for (int pl = 0; pl < 2; ++pl) {
-            A[(pl * 128 + rr) * 32 + 2 * c8] = pack4_tf32(pv[pl]);
-            A[(pl * 128 + rr) * 32 + 2 * c8 + 1] = pack4_tf32(pv[pl] + 4);
-            B[(pl * 128 + rr) * 32 + 2 * c8] = pack4_tf32(pv[2 + pl]);
-            B[(pl * 128 + rr) * 32 + 2 * c8 + 1] = pack4_tf32(pv[2 + pl] + 4);
-          }
-        } else {
-          __nv_bfloat16 h[4][8], lo[4][8];
-#pragma unroll
-          for (int q = 0; q < 4; ++q)
-#pragma unroll
-            for (int k = 0; k < 8; ++k) split2(pv[q][k], h[q][k], lo[q][k]);
-          // opA rows: split * 256 + plane * 128 + row; 16 uint4 per 256-byte row
-          A[((0 * 256 + 0 * 128) + rr) * 16 + c8] = pack8(h[0]);
-          A[((0 * 256 + 1 * 128) + rr) * 16 + c8] = pack8(h[1]);
-          A[((1 * 256 + 0 * 128) + rr) * 16 + c8] = pack8(lo[0]);
-          A[((1 * 256 + 1 * 128) + rr) * 16 + c8] = pack8(lo[1]);
-          // opB rows: split * 256 + plane * 128 + row (planes W_r, W_i)
-#pragma unroll
-          for (int pl = 0; pl < 2; ++pl) {
-            B[((0 * 256 + pl * 128) + rr) * 16 + c8] = pack8(h[2 + pl]);
-            B[((1 * 256 + pl * 128) + rr) * 16 + c8] = pack8(lo[2 + pl]);
+          for (int i = 0; i < 32; i += 2) {
+            const int u = (c0 + i) >> 1;
+            stg[r * 64 + (u ^ (r & 7))] = make_float4(lr[i], li[i], lr[i + 1], li[i + 1]);
           }
         }
+        __syncthreads();
+        // ---------------------------------------------------------------- phase 4: store L_IJ
+        // operand planes opA (L) and opB (W = L D_J), 16 bytes per thread; the complex64 copy of L
+        // (read only by the solve sweeps) is written after the release, below
+        uint4* A = reinterpret_cast<uint4*>(opA + (int64_t)T.tile * ROWS * TB * (TF ? 4 : 2));
+        uint4* B = reinterpret_cast<uint4*>(opB + (int64_t)T.tile * ROWS * TB * (TF ? 4 : 2));
+        for (int it = tid; it < TB * 16; it += NTHR) {
+          const int rr = it >> 4, c8 = it & 15;   // row, group of 8 columns
+          float2 l[8];
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const int u = c8 * 4 + k;
+            const float4 v = stg[rr * 64 + (u ^ (rr & 7))];
+            l[2 * k] = make_float2(v.x, v.y);
+            l[2 * k + 1] = make_float2(v.z, v.w);
+          }
+          float pv[4][8];   // planes: L_r, L_i, W_r, W_i
+#pragma unroll
+          for (int k = 0; k < 8; ++k) {
+            const float2 w = cmul(l[k], s_d[c8 * 8 + k]);
+            pv[0][k] = l[k].x;
+            pv[1][k] = l[k].y;
+            pv[2][k] = w.x;
+            pv[3][k] = w.y;
+          }
+          if constexpr (TF) {
+            // opA rows: plane * 128 + row (L_r, L_i); opB rows: the same for W; 32 uint4 per 512-byte row
+#pragma unroll
+            for (int pl = 0; pl < 2; ++pl) {
+              A[(pl * 128 + rr) * 32 + 2 * c8] = pack4_tf32(pv[pl]);
+              A[(pl * 128 + rr) * 32 + 2 * c8 + 1] = pack4_tf32(pv[pl] + 4);
+              B[(pl * 128 + rr) * 32 + 2 * c8] = pack4_tf32(pv[2 + pl]);
+              B[(pl * 128 + rr) * 32 + 2 * c8 + 1] = pack4_tf32(pv[2 + pl] + 4);
+            }
+          } else {
+            __nv_bfloat16 h[4][8], lo[4][8];
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+#pragma unroll
+              for (int k = 0; k < 8; ++k) split2(pv[q][k], h[q][k], lo[q][k]);
+            // opA rows: split * 256 + plane * 128 + row; 16 uint4 per 256-byte row
+            A[((0 * 256 + 0 * 128) + rr) * 16 + c8] = pack8(h[0]);
+            A[((0 * 256 + 1 * 128) + rr) * 16 + c8] = pack8(h[1]);
+            A[((1 * 256 + 0 * 128) + rr) * 16 + c8] = pack8(lo[0]);
+            A[((1 * 256 + 1 * 128) + rr) * 16 + c8] = pack8(lo[1]);
+            // opB rows: split * 256 + plane * 128 + row (planes W_r, W_i)
+#pragma unroll
+            for (int pl = 0; pl < 2; ++pl) {
+              B[((0 * 256 + pl * 128) + rr) * 16 + c8] = pack8(h[2 + pl]);
+              B[((1 * 256 + pl * 128) + rr) * 16 + c8] = pack8(lo[2 + pl]);
+            }
+          }
+        }
+        __syncthreads();
+        trace_mark(p, task, 3);
       }
-      __syncthreads();
-      trace_mark(p, task, 3);
     }
+
+    // ---------------------------------------------------------------- completion
     tc_fence_before();
-    sched_complete(p, task);
+    asm volatile("fence.proxy.async.global;" ::: "memory");   // writes before other blocks' TMA reads
+    __syncthreads();
+    if (T.flags & TF_UPDATE) trace_mark(p, task, 3);
+    const int next = s_next[it & 1];
+    if (warp == 2) release_successors(p, task, lane);
     // Complex64 copies of the tile for the solve sweeps: no task of this factorization reads
     // them, so they are written after the successors are released (off the critical path).
-    if (is_diag) {
-      const float2* sS = reinterpret_cast<const float2*>(smem);
-      float2* Lt = Lg + (int64_t)T.tile * TB * TB;
-      float2* Li = Linv + (int64_t)T.col * TB * TB;
-      for (int i = tid; i < TB * TB; i += NTHR) {
-        const int rr = i >> 7, cc = i & 127;
-        Lt[i] = (cc < rr) ? sS[rr * LDS + cc] : make_float2(cc == rr ? 1.f : 0.f, 0.f);
-        Li[i] = (cc < rr) ? sS[cc * LDS + rr] : make_float2(cc == rr ? 1.f : 0.f, 0.f);
+    if (!(T.flags & TF_UPDATE)) {
+      if (is_diag) {
+        const float2* sS = reinterpret_cast<const float2*>(smem);
+        float2* Lt = Lg + (int64_t)T.tile * TB * TB;
+        float2* Li = Linv + (int64_t)T.col * TB * TB;
+        for (int i = tid; i < TB * TB; i += NTHR) {
+          const int rr = i >> 7, cc = i & 127;
+          Lt[i] = (cc < rr) ? sS[rr * LDS + cc] : make_float2(cc == rr ? 1.f : 0.f, 0.f);
+          Li[i] = (cc < rr) ? sS[cc * LDS + rr] : make_float2(cc == rr ? 1.f : 0.f, 0.f);
+        }
+      } else {
+        const float4* stg = reinterpret_cast<const float4*>(smem);
+        float4* Lt4 = reinterpret_cast<float4*>(Lg + (int64_t)T.tile * TB * TB);
+        for (int e = tid; e < TB * 64; e += NTHR) {
+          const int rr = e >> 6, u = e & 63;
+          Lt4[e] = stg[rr * 64 + (u ^ (rr & 7))];
+        }
       }
-    } else {
-      const float4* stg = reinterpret_cast<const float4*>(smem);
-      float4* Lt4 = reinterpret_cast<float4*>(Lg + (int64_t)T.tile * TB * TB);
-      for (int e = tid; e < TB * 64; e += NTHR) {
-        const int rr = e >> 6, u = e & 63;
-        Lt4[e] = stg[rr * 64 + (u ^ (rr & 7))];
-      }
+      __syncthreads();   // shared memory is read before the next task's loads overwrite it
     }
+    ++it;
+    task = next >= 0 ? next : sched_pop(p, &s_task, &s_pending);
   }
 
   // teardown: after a failed wait, give in-flight copies and MMAs time to land (bounded)
