@@ -77,19 +77,26 @@ def measured_peaks():
 
 # ------------------------------------------------------------------ recorded DRAM traffic
 # Per-launch DRAM bytes of a kernel come from an ncu capture (profiles/traffic_<workload>.txt,
-# lines "<kernel> <bytes per launch> <sha1 of its source file>"); a number whose kernel source
-# has changed since the capture is not reported.
-TRAFFIC_SOURCES = {"factor_kernel": "factor_tc.cu", "residual": "solve.cu", "solve_sweep": "solve.cu"}
+# lines "<kernel> <bytes per launch> <sha1 of its source files>"); a number whose kernel sources
+# have changed since the capture is not reported.
+TRAFFIC_SOURCES = {"factor_kernel": ("factor_tc.cu", "device.cuh"), "residual": ("resid_tc.cu",),
+                   "solve_sweep": ("gather_tc.cu", "solve.cu")}
+
+
+def source_sha(kernel: str):
+    import hashlib
+    h = hashlib.sha1()
+    for src in TRAFFIC_SOURCES[kernel]:
+        with open(os.path.join(ROOT, "paper_2002_05026_gb300", "csrc", src), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
 
 
 def recorded_traffic(workload: str, kernel: str):
-    import hashlib
     path = os.path.join(ROOT, "profiles", f"traffic_{workload}.txt")
-    src = TRAFFIC_SOURCES.get(kernel)
-    if not src or not os.path.exists(path):
+    if kernel not in TRAFFIC_SOURCES or not os.path.exists(path):
         return None
-    with open(os.path.join(ROOT, "paper_2002_05026_gb300", "csrc", src), "rb") as f:
-        sha = hashlib.sha1(f.read()).hexdigest()
+    sha = source_sha(kernel)
     with open(path) as f:
         for line in f:
             parts = line.split()

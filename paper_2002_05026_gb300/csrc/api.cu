@@ -62,6 +62,7 @@ struct d3m_ctx {
   void* D = nullptr;
   void* opA = nullptr;
   void* opB = nullptr;
+  void* opS = nullptr;               // TF32: bf16 split planes of L for the solve's tensor-core products
   void* Sacc = nullptr;
   void* E = nullptr;                 // pivot mode: sub-diagonals of the 2 x 2 pivot blocks [NT][b]
   int32_t* piv = nullptr;            // pivot mode: permutation of every diagonal tile [NT][b]
@@ -425,7 +426,7 @@ static int create_impl(d3m_handle* out, const d3m_pattern* pat, const int32_t* p
   if (h->opt.seg_group <= 0) h->opt.seg_group = h->fp64 ? 1 : 8;
   // the tensor-core gathers of the solve (split-BF16x3 engine) sum up to 16 items of one
   // destination in tensor memory
-  const int ggroup = (h->tc && !h->tf32) ? 16 : 1;
+  const int ggroup = h->tc ? 16 : 1;
   int rc = analyze(pat, perm, h->b, true, h->S, err, h->opt.prio_slack, h->opt.seg_group, h->opt.task_cost, ggroup);
   if (rc != D3M_OK) {
     delete h;
@@ -515,11 +516,14 @@ static int create_impl(d3m_handle* out, const d3m_pattern* pat, const int32_t* p
     if (!h->opA || !h->opB) return set_err(h, D3M_ERR_OOM, "cudaMalloc failed for the tensor-core operands");
     std::string e2;
     if (tc_make_maps(h->opA, h->opB, ntiles, h->tf32, &h->maps, e2) != 0) return set_err(h, D3M_ERR_CUDA, e2);
-    if (!h->tf32) {
-      // the solve's off-block products run on the tensor cores from the same bf16 planes
-      if (gather_tc_make_maps(h->opA, ntiles, &h->gmaps, e2) != 0) return set_err(h, D3M_ERR_CUDA, e2);
-      h->gather_tc = true;
+    // the solve's off-block products run on the tensor cores from bf16 split planes of L: the
+    // BF16x3 engine's own opA, or (TF32) a copy in that layout written beside the tf32 planes
+    if (h->tf32) {
+      h->opS = dalloc<unsigned char>(h, (size_t)ntiles * 4 * b * b * 2);
+      if (!h->opS) return set_err(h, D3M_ERR_OOM, "cudaMalloc failed for the solve operand planes");
     }
+    if (gather_tc_make_maps(h->tf32 ? h->opS : h->opA, ntiles, &h->gmaps, e2) != 0) return set_err(h, D3M_ERR_CUDA, e2);
+    h->gather_tc = true;
   }
   // solve
   UPLOAD(h->fwd_items, S.fwd_items);
@@ -862,6 +866,7 @@ static int enqueue_factor(d3m_ctx* h, const void* Kin, bool kdev, cudaStream_t s
   p.D = h->D;
   p.opA = h->opA;
   p.opB = h->opB;
+  p.opS = h->opS;
   p.Sacc = h->Sacc;
   p.trace = h->trace;
   p.timeout_ns = h->opt.timeout_ns;

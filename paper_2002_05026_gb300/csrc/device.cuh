@@ -46,6 +46,7 @@ struct FactorParams {
   void* D;               // [NT][b] pivots
   void* opA;             // tensor-core operand planes (bf16) of L tiles
   void* opB;             // tensor-core operand planes (bf16) of W tiles / T_J
+  void* opS;             // TF32 engine: bf16 split planes of the L tiles for the solve's products, or nullptr
   void* Sacc;            // [n_acc][b][b] partial Schur accumulators (complex, working precision)
   int64_t* trace;        // [ntasks][8] task records, or nullptr
   int64_t timeout_ns;

@@ -599,11 +599,11 @@ __global__ void __launch_bounds__(NTHR, 1)
   // update or triangular-solve task run (sched_claim_normal), and warp 2 releases a finished
   // task's successors while warps 0 and 1 already issue the next task's loads and products, so
   // neither the queue round trips nor the release sit between two tasks.
-  int it = 0;
+  int tcount = 0;                    // tasks this block has run (parity selects s_next)
   int task = sched_pop(p, &s_task, &s_pending);
   while (task >= 0) {
     const TileTask T = p.tasks[task];
-    if (tid == 32) s_next[it & 1] = -1;
+    if (tid == 32) s_next[tcount & 1] = -1;
     const uint64_t deadline = globaltimer_ns() + (uint64_t)p.timeout_ns;
     const int nchunk = T.nk * NCH;
     asm volatile("fence.proxy.async.global;" ::: "memory");
@@ -654,7 +654,7 @@ __global__ void __launch_bounds__(NTHR, 1)
             ++g_mma;
           }
           mma_commit(smem_u32(&bar_acc));
-          if (T.flags & TF_UPDATE) s_next[it & 1] = sched_claim_normal(p, &s_pending);
+          if (T.flags & TF_UPDATE) s_next[tcount & 1] = sched_claim_normal(p, &s_pending);
         }
         __syncwarp();
       }
@@ -888,7 +888,7 @@ __global__ void __launch_bounds__(NTHR, 1)
               ++t_mma;
             }
             mma_commit(smem_u32(&bar_acc2));
-            s_next[it & 1] = sched_claim_normal(p, &s_pending);
+            s_next[tcount & 1] = sched_claim_normal(p, &s_pending);
           }
           __syncwarp();
         }
@@ -950,6 +950,20 @@ __global__ void __launch_bounds__(NTHR, 1)
               B[(pl * 128 + rr) * 32 + 2 * c8] = pack4_tf32(pv[2 + pl]);
               B[(pl * 128 + rr) * 32 + 2 * c8 + 1] = pack4_tf32(pv[2 + pl] + 4);
             }
+            if (p.opS) {
+              // bf16 split planes of L for the solve's tensor-core products, in the layout of the
+              // split-BF16x3 engine's opA (rows split * 256 + plane * 128 + row)
+              __nv_bfloat16 h[2][8], lo[2][8];
+#pragma unroll
+              for (int q = 0; q < 2; ++q)
+#pragma unroll
+                for (int k = 0; k < 8; ++k) split2(pv[q][k], h[q][k], lo[q][k]);
+              uint4* Sp = reinterpret_cast<uint4*>(reinterpret_cast<unsigned char*>(p.opS) + (int64_t)T.tile * 512 * TB * 2);
+              Sp[((0 * 256 + 0 * 128) + rr) * 16 + c8] = pack8(h[0]);
+              Sp[((0 * 256 + 1 * 128) + rr) * 16 + c8] = pack8(h[1]);
+              Sp[((1 * 256 + 0 * 128) + rr) * 16 + c8] = pack8(lo[0]);
+              Sp[((1 * 256 + 1 * 128) + rr) * 16 + c8] = pack8(lo[1]);
+            }
           } else {
             __nv_bfloat16 h[4][8], lo[4][8];
 #pragma unroll
@@ -979,7 +993,7 @@ __global__ void __launch_bounds__(NTHR, 1)
     asm volatile("fence.proxy.async.global;" ::: "memory");   // writes before other blocks' TMA reads
     __syncthreads();
     if (T.flags & TF_UPDATE) trace_mark(p, task, 3);
-    const int next = s_next[it & 1];
+    const int next = s_next[tcount & 1];
     if (warp == 2) release_successors(p, task, lane);
     // Complex64 copies of the tile for the solve sweeps: no task of this factorization reads
     // them, so they are written after the successors are released (off the critical path).
@@ -1003,7 +1017,7 @@ __global__ void __launch_bounds__(NTHR, 1)
       }
       __syncthreads();   // shared memory is read before the next task's loads overwrite it
     }
-    ++it;
+    ++tcount;
     task = next >= 0 ? next : sched_pop(p, &s_task, &s_pending);
   }
 
