@@ -44,7 +44,8 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="d3m", choices=["d3m", "reference"])
     ap.add_argument("--workload", default="grid6x6x6_m512")
-    ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "tf32", "simt32", "fp64"])
+    ap.add_argument("--precision", default="auto", choices=["auto", "bf16x3", "tf32", "simt32", "fp64"],
+                    help="tile engine; auto: tf32 for a throughput-bound factorization, else bf16x3")
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -77,8 +78,8 @@ def measured_peaks():
 
 # ------------------------------------------------------------------ recorded DRAM traffic
 # Per-launch DRAM bytes of a kernel come from an ncu capture (profiles/traffic_<workload>.txt,
-# lines "<kernel> <bytes per launch> <sha1 of its source files>"); a number whose kernel sources
-# have changed since the capture is not reported.
+# lines "<kernel>:<engine> <bytes per launch> <sha1 of its source files>"); a number whose kernel
+# sources have changed since the capture is not reported.
 TRAFFIC_SOURCES = {"factor_kernel": ("factor_tc.cu", "device.cuh"), "residual": ("resid_tc.cu",),
                    "solve_sweep": ("gather_tc.cu", "solve.cu")}
 
@@ -92,7 +93,7 @@ def source_sha(kernel: str):
     return h.hexdigest()
 
 
-def recorded_traffic(workload: str, kernel: str):
+def recorded_traffic(workload: str, kernel: str, engine: str):
     path = os.path.join(ROOT, "profiles", f"traffic_{workload}.txt")
     if kernel not in TRAFFIC_SOURCES or not os.path.exists(path):
         return None
@@ -100,7 +101,7 @@ def recorded_traffic(workload: str, kernel: str):
     with open(path) as f:
         for line in f:
             parts = line.split()
-            if len(parts) == 3 and parts[0] == kernel and parts[2] == sha:
+            if len(parts) == 3 and parts[0] == f"{kernel}:{engine}" and parts[2] == sha:
                 return float(parts[1])
     return None
 
@@ -239,6 +240,24 @@ def make_workload(w, seed, device):
     return p, np.ascontiguousarray(B.T)      # (nrhs, n) = column-major (n, nrhs)
 
 
+# ------------------------------------------------------------------ engine choice
+# TF32 does two thirds of split-BF16x3's tensor-core work per product but its factor is less
+# accurate (about 2^-11), so the refinement needs one more solve.  On a factorization large
+# enough to keep every SM busy (throughput-bound, under the power cap) the cheaper products win;
+# on a smaller one, bound by its critical path of diagonal tiles, they do not.  Measured on one
+# GB300: 6x6x6 m=512 (1.8e14 factor flops, 32 RHS) 466 ms (tf32) vs 498 ms (bf16x3) per step;
+# 8x8 m=512 (3.6e12 flops, 8 RHS) 25.7 vs 22.8 ms.  Both reach omega <= 1e-12.
+AUTO_TF32_FLOPS = 5e13
+
+
+def resolve_precision(args, colptr, rowidx, m, perm) -> str:
+    if args.precision != "auto":
+        return args.precision
+    from paper_2002_05026_gb300 import d3m_analyze
+    flops = d3m_analyze(colptr, rowidx, m=m, perm=perm)["factor_flops"]
+    return "tf32" if flops >= AUTO_TF32_FLOPS else "bf16x3"
+
+
 # ------------------------------------------------------------------ reference arm (the oracle)
 def reference_arm(args, rank, world):
     """The oracle on the host cores, on a bounded sample of the workload; loads neither torch's
@@ -295,6 +314,7 @@ def adjoint_arm(args, rank, world, local):
     b = torch.from_numpy(np.ascontiguousarray(synth.rhs(seed + 1, p.n, 1))).cuda()
     c = torch.from_numpy(np.ascontiguousarray(synth.sparse_adjoint_vector(seed + 2, p.n, p.m,
                                                                            support_block=int(perm[-1])))).cuda()
+    args.precision = resolve_precision(args, p.colptr, p.rowidx, p.m, perm)
     s = D3M(p.colptr, p.rowidx, m=p.m, perm=perm, precision=args.precision, max_nrhs=1)
     stream = torch.cuda.current_stream()
 
@@ -325,14 +345,17 @@ def adjoint_arm(args, rank, world, local):
     roof = {"bound": "tensor", "achieved": info["factor_flops"] / (fms * 1e-3) / 1e12,
             "peak": peaks["bf16_tflops"] / 3.0, "unit": "TFLOP/s", "kernel": "factor_kernel",
             "kernel_ms": fms, "peak_source": "bf16_tflops/3 (burst)", "traffic": None, "peak_kind": peak_kind}
-    if args.precision != "bf16x3":
+    if args.precision == "tf32":
+        roof.update({"peak": peaks["bf16_tflops"] / 2.0, "peak_source": "bf16_tflops/2 (burst; tf32 dense rate)"})
+    elif args.precision != "bf16x3":
         roof.update({"bound": "alu", "peak": FP64_PEAK_GFLOPS / 1e3 if args.precision == "fp64" else
                      152 * 2.07e9 * 256 / 1e12, "peak_source": "ALU nominal"})
     roof["frac"] = roof["achieved"] / roof["peak"]
     line = {"metric": ADJ_METRIC, "value": 1e3 / ms * world, "unit": "gradients/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "c64+bf16x3/fp64-refine" if args.precision == "bf16x3"
-            else args.precision, "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": {"bf16x3": "c64+bf16x3/fp64-refine", "tf32": "c64+tf32/fp64-refine", "fp64": "c128"}.get(
+                args.precision, "c64/fp64-refine"), "data": "synthetic",
             "config": {"workload": args.workload, "grid": [w["nx"], w["ny"], w["nz"]], "m": w["m"], "n": p.n,
                        "parameters": ndom, "k2": w["k2"], "tau": w["tau"], "precision": args.precision},
             "roofline": roof,
@@ -576,6 +599,7 @@ def main():
     perm = d3m_order_grid_nd(w["nx"], w["ny"], w["nz"])
     stream = torch.cuda.current_stream()
     sp = ctypes.c_void_p(stream.cuda_stream)
+    args.precision = resolve_precision(args, p.colptr, p.rowidx, p.m, perm)
     s = D3M(p.colptr, p.rowidx, m=p.m, perm=perm, precision=args.precision, max_nrhs=nrhs, graphs=bool(args.graphs),
             seg_group=args.seg_group)
     lib = s._lib
@@ -657,7 +681,7 @@ def main():
     roof = dict(roof)
     roof["kernel"] = dom_name
     roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = recorded_traffic(args.workload, dom_name)
+    roof["traffic"] = recorded_traffic(args.workload, dom_name, args.precision)
     roof["peak_kind"] = peak_kind
     breakdown = {k: {"ms_per_step": t / args.steps, **{kk: v for kk, v in r.items() if kk in ("achieved", "peak", "unit", "bound")}}
                  for k, t, r in kern}

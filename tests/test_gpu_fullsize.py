@@ -8,7 +8,7 @@ any size (Sec. I/II method; readings R7, R8, R14):
 * the mixed-precision solution must agree with the plain FP64 GPU path to 1e-9 (relative, per
   column), and the FP64 path's own omega must be at the FP64 rounding level;
 * the 6 x 6 x 6 grid with m = 512 (n = 276,480, 32 right-hand sides, the largest single-GPU
-  workload and the bench's default) gets the same two checks;
+  workload and the bench's default) gets the same two checks, for both tensor-core engines;
 * batched: every one of the 256 uneven instances meets omega <= 1e-12 (oracle residual) and its
   solution agrees with a single-instance FP64 handle on a sample of instances.
 """
@@ -59,6 +59,8 @@ def test_grid8x8_m512_full_size(torch_cuda):
 
 
 def test_grid6x6x6_m512_full_size(torch_cuda):
+    """Both tensor-core engines (split-BF16x3 and TF32, the bench's choice at this size) against the
+    oracle residual and the plain FP64 GPU path."""
     torch = torch_cuda
     from paper_2002_05026_gb300 import D3M, d3m_order_grid_nd
     w = synth.WORKLOADS["grid6x6x6_m512"]
@@ -66,22 +68,26 @@ def test_grid6x6x6_m512_full_size(torch_cuda):
     perm = d3m_order_grid_nd(w["nx"], w["ny"], w["nz"])
     B = synth.rhs(w["seed"] + 1, p.n, w["nrhs"])
     Bd = torch.from_numpy(np.ascontiguousarray(B)).cuda()
-    s = D3M(p.colptr, p.rowidx, m=p.m, perm=perm, precision="bf16x3", max_nrhs=w["nrhs"])
-    s.factor(p.blocks)
-    X = s.solve(Bd).cpu().numpy()
-    info = s.info()
-    s.close()
-    torch.cuda.empty_cache()
+    Xs, infos = {}, {}
+    for prec in ("bf16x3", "tf32"):
+        s = D3M(p.colptr, p.rowidx, m=p.m, perm=perm, precision=prec, max_nrhs=w["nrhs"])
+        s.factor(p.blocks)
+        Xs[prec] = s.solve(Bd).cpu().numpy()
+        infos[prec] = s.info()
+        s.close()
+        torch.cuda.empty_cache()
     Kb = O.lower_blocks(p.colptr, p.rowidx, p.blocks.cpu().numpy(), p.m)
-    om = O.omega(Kb, p.nblk, p.m, X, B)
+    for prec, X in Xs.items():
+        om = O.omega(Kb, p.nblk, p.m, X, B)
+        assert np.max(om) <= 1e-12, (prec, np.max(om))
+        assert infos[prec]["omega"] == pytest.approx(np.max(om), rel=0.05, abs=5e-15), prec
     del Kb
-    assert np.max(om) <= 1e-12, np.max(om)
-    assert info["omega"] == pytest.approx(np.max(om), rel=0.05, abs=5e-15)
     s64 = D3M(p.colptr, p.rowidx, m=p.m, perm=perm, precision="fp64", max_nrhs=w["nrhs"])
     s64.factor(p.blocks)
     X64 = s64.solve(Bd).cpu().numpy()
     s64.close()
-    assert _fwd(X, X64) <= 1e-9
+    for prec, X in Xs.items():
+        assert _fwd(X, X64) <= 1e-9, prec
 
 
 def test_batch256_full_size(torch_cuda):
