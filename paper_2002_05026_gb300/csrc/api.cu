@@ -369,7 +369,8 @@ int d3m_analyze_opts(const d3m_pattern* pat, const int32_t* perm, const d3m_opti
   if (o.seg_group <= 0) o.seg_group = fp64 ? 1 : 8;
   Symbolic S;
   std::string err;
-  int rc = analyze(pat, perm, b, true, S, err, o.prio_slack, o.seg_group, o.task_cost);
+  int rc = analyze(pat, perm, b, true, S, err, o.prio_slack, o.seg_group, o.task_cost, tc ? 16 : 1,
+                   prec == D3M_MIXED_TF32);
   if (rc != D3M_OK) return set_err(nullptr, rc, err);
   std::memset(info, 0, sizeof(*info));
   fill_structure(S, info);
@@ -427,7 +428,8 @@ static int create_impl(d3m_handle* out, const d3m_pattern* pat, const int32_t* p
   // the tensor-core gathers of the solve (split-BF16x3 engine) sum up to 16 items of one
   // destination in tensor memory
   const int ggroup = h->tc ? 16 : 1;
-  int rc = analyze(pat, perm, h->b, true, h->S, err, h->opt.prio_slack, h->opt.seg_group, h->opt.task_cost, ggroup);
+  int rc = analyze(pat, perm, h->b, true, h->S, err, h->opt.prio_slack, h->opt.seg_group, h->opt.task_cost, ggroup,
+                   h->tf32);
   if (rc != D3M_OK) {
     delete h;
     return set_err(nullptr, rc, err);

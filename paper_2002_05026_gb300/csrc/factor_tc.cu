@@ -48,23 +48,26 @@ template <bool TF> struct Eng;
 template <> struct Eng<false> {                 // split-BF16x3
   static constexpr int KC = 32;                 // K elements per chunk
   static constexpr int NPA = 4, NPB = 4;        // planes per stage: A [hi_r, hi_i, lo_r, lo_i], B [hi, lo] x [r, i]
+  static constexpr int NB = 1;                  // B operands per stage (no paired update tasks)
   static constexpr int NSTAGE = 3;              // GEMM pipeline depth (3 x 64 KB)
   static constexpr uint32_t ROWS = 512;         // operand rows of one tile in global memory
 };
 template <> struct Eng<true> {                  // TF32
   static constexpr int KC = 16;
   static constexpr int NPA = 2, NPB = 2;        // A [r, i], B [r, i]
-  static constexpr int NSTAGE = 6;              // 6 x 32 KB
+  static constexpr int NB = 2;                  // B operands per stage: a paired task's two tiles
+  static constexpr int NSTAGE = 4;              // 4 x 48 KB
   static constexpr uint32_t ROWS = 256;
 };
 template <bool TF> constexpr uint32_t stage_a() { return Eng<TF>::NPA * PLANE; }
 template <bool TF> constexpr uint32_t stage_b() { return Eng<TF>::NPB * PLANE; }
 template <bool TF> constexpr uint32_t stage_ab() { return stage_a<TF>() + stage_b<TF>(); }
+template <bool TF> constexpr uint32_t stage_slot() { return stage_a<TF>() + Eng<TF>::NB * stage_b<TF>(); }
 constexpr uint32_t SMEM_S = 0;                  // TRSM A operand: TB / KC chunks of stage_a (128 KB)
 constexpr uint32_t SMEM_T = 128 * 1024;         // TRSM B stages (2 x stage_b)
 constexpr uint32_t SMEM_BYTES = 192 * 1024;
-static_assert(Eng<false>::NSTAGE * stage_ab<false>() <= SMEM_BYTES && SMEM_T + 2 * stage_b<false>() <= SMEM_BYTES, "smem");
-static_assert(Eng<true>::NSTAGE * stage_ab<true>() <= SMEM_BYTES && SMEM_T + 2 * stage_b<true>() <= SMEM_BYTES, "smem");
+static_assert(Eng<false>::NSTAGE * stage_slot<false>() <= SMEM_BYTES && SMEM_T + 2 * stage_b<false>() <= SMEM_BYTES, "smem");
+static_assert(Eng<true>::NSTAGE * stage_slot<true>() <= SMEM_BYTES && SMEM_T + 2 * stage_b<true>() <= SMEM_BYTES, "smem");
 static_assert((TB / Eng<false>::KC) * stage_a<false>() == SMEM_T && (TB / Eng<true>::KC) * stage_a<true>() == SMEM_T, "S");
 constexpr int LDS = 129;                        // c64 diagonal tile row stride (elements)
 constexpr uint32_t DIAG_AUX = 130 * 1024;       // d / column / scratch vectors of a diagonal task
@@ -544,6 +547,7 @@ __global__ void __launch_bounds__(NTHR, 1)
                      const __grid_constant__ CUtensorMap mapB) {
   constexpr int KC = Eng<TF>::KC, NSTAGE = Eng<TF>::NSTAGE, NCH = TB / KC;
   constexpr uint32_t STAGE_A = stage_a<TF>(), STAGE_B = stage_b<TF>(), STAGE = stage_ab<TF>();
+  constexpr uint32_t SLOT = stage_slot<TF>();    // bytes between pipeline stages
   constexpr uint32_t ROWS = Eng<TF>::ROWS;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   // 1024-byte alignment of the dynamic region (swizzle atoms); pointer arithmetic on the shared
@@ -619,6 +623,20 @@ __global__ void __launch_bounds__(NTHR, 1)
         bulk_prefetch_l2(p.K + T.k_off + base, (uint32_t)((T.k_tr ? T.cv : T.rv) * sizeof(double2)));
       }
     }
+    const bool pair = TF && (T.flags & TF_PAIR) != 0;   // a second tile (I, J + 1) shares the A operand
+    if (pair && warp >= 6) {
+      // the same for the second tile: its accumulator, or the spans of K_{I,J+1}
+      const int sp = tid - 192;
+      if (T.flags & TF_S_IN) {
+        if (sp < 8 && T.sidx2 >= 0)
+          bulk_prefetch_l2(Sacc + (int64_t)T.sidx2 * TB * TB + sp * (TB * TB / 8), (uint32_t)(TB * TB / 8 * sizeof(float2)));
+      } else if (T.k_off >= 0) {
+        for (int q = sp; q < (T.k_tr ? T.rv : T.cv2); q += 64) {
+          const int64_t base = T.k_tr ? (int64_t)(T.r0 + q) * T.k_ld + T.c0_2 : (int64_t)(T.c0_2 + q) * T.k_ld + T.r0;
+          bulk_prefetch_l2(p.K + T.k_off + base, (uint32_t)((T.k_tr ? T.cv2 : T.rv) * sizeof(double2)));
+        }
+      }
+    }
 
     // ---------------------------------------------------------------- phase 1: Schur GEMM
     if (nchunk > 0) {
@@ -629,15 +647,20 @@ __global__ void __launch_bounds__(NTHR, 1)
             if (!mbar_wait(smem_u32(&bar_empty[s]), (use & 1) ^ 1, deadline)) { failed = true; break; }
             const KEntry ke = p.klist[T.kl_off + c / NCH];
             const int x = (c % NCH) * KC;
-            const uint32_t sb = smem_u32(smem + s * STAGE);
+            const uint32_t sb = smem_u32(smem + s * SLOT);
             const uint32_t fb = smem_u32(&bar_full[s]);
-            mbar_expect_tx(fb, STAGE);
+            mbar_expect_tx(fb, pair ? STAGE + STAGE_B : STAGE);
 #pragma unroll
             for (int q = 0; q < Eng<TF>::NPA; ++q)
               tma_load_2d(sb + q * PLANE, &mapA, x, ke.a_tile * (int)ROWS + q * 128, fb);
 #pragma unroll
             for (int q = 0; q < Eng<TF>::NPB; ++q)
               tma_load_2d(sb + STAGE_A + q * PLANE, &mapB, x, ke.b_tile * (int)ROWS + q * 128, fb);
+            if (pair) {
+#pragma unroll
+              for (int q = 0; q < Eng<TF>::NPB; ++q)
+                tma_load_2d(sb + STAGE + q * PLANE, &mapB, x, ke.b2_tile * (int)ROWS + q * 128, fb);
+            }
             ++g_load;
           }
         }
@@ -648,8 +671,9 @@ __global__ void __launch_bounds__(NTHR, 1)
             const uint32_t s = g_mma % NSTAGE, use = g_mma / NSTAGE;
             if (!mbar_wait(smem_u32(&bar_full[s]), use & 1, deadline)) { failed = true; break; }
             tc_fence_after();
-            const uint32_t sb = smem_u32(smem + s * STAGE);
+            const uint32_t sb = smem_u32(smem + s * SLOT);
             chunk_mma<TF>(tmem + ACC1, sb, sb + STAGE_A, c == 0);
+            if (pair) chunk_mma<TF>(tmem + ACC2, sb, sb + STAGE, c == 0);
             mma_commit(smem_u32(&bar_empty[s]));
             ++g_mma;
           }
@@ -675,17 +699,29 @@ __global__ void __launch_bounds__(NTHR, 1)
     const int r = quarter * 32 + lane;
     if (T.flags & TF_UPDATE) {
       // ------------------------------------------------------------ partial update task
-      for (int pass = 0; pass < 2; ++pass) {
-        const int c0 = half * 64 + pass * 32;
-        float vr[32], vi[32];
-        tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + ACC1 + c0, vr);
-        tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + ACC1 + 128 + c0, vi);
-        float4* slot = acc_slot(Sa, r, c0);
-        float2 kin[32];
-        load_s_in(T, p.K, s_in ? Sa : nullptr, r, c0, kin);   // all loads first
+      // (a paired task: the second tile from the accumulator at ACC2, with its own columns)
+      for (int u = 0; u < (pair ? 2 : 1); ++u) {
+        TileTask Tu = T;
+        if (u) {
+          Tu.tile = T.tile2;
+          Tu.c0 = T.c0_2;
+          Tu.cv = T.cv2;
+          Tu.sidx = T.sidx2;
+        }
+        float2* Su = (Tu.sidx >= 0) ? Sacc + (int64_t)Tu.sidx * TB * TB : nullptr;
+        const uint32_t acc = u ? ACC2 : ACC1;
+        for (int pass = 0; pass < 2; ++pass) {
+          const int c0 = half * 64 + pass * 32;
+          float vr[32], vi[32];
+          tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + acc + c0, vr);
+          tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + acc + 128 + c0, vi);
+          float4* slot = acc_slot(Su, r, c0);
+          float2 kin[32];
+          load_s_in(Tu, p.K, s_in ? Su : nullptr, r, c0, kin);   // all loads first
 #pragma unroll
-        for (int i = 0; i < 32; i += 2)
-          slot[(i / 2) * TB] = make_float4(kin[i].x - vr[i], kin[i].y - vi[i], kin[i + 1].x - vr[i + 1], kin[i + 1].y - vi[i + 1]);
+          for (int i = 0; i < 32; i += 2)
+            slot[(i / 2) * TB] = make_float4(kin[i].x - vr[i], kin[i].y - vi[i], kin[i + 1].x - vr[i + 1], kin[i + 1].y - vi[i + 1]);
+        }
       }
     } else {
       // ------------------------------------------------------------ final task

@@ -35,7 +35,7 @@ static int fail(std::string& err, const char* msg, long a = -1, long b = -1) {
 
 int analyze(const d3m_pattern* pat, const int32_t* perm_in, int b, bool build_tasks,
             Symbolic& s, std::string& err, double prio_slack, int seg_group, const double* task_cost,
-            int gather_group) {
+            int gather_group, bool pair_updates) {
   if (seg_group < 1) seg_group = 1;
   if (!pat || !pat->colptr || !pat->rowidx) return fail(err, "pattern or its arrays are NULL");
   const int N = pat->nblk;
@@ -239,6 +239,7 @@ int analyze(const d3m_pattern* pat, const int32_t* perm_in, int b, bool build_ta
   };
   std::vector<int32_t> ks;
   std::vector<int32_t> nseg(ntiles, 0);
+  std::vector<int32_t> nsrc(ntiles, 0);   // source-block segments (the ones that may be paired)
   for (int J = 0; J < s.NT; ++J) {
     int q = s.tblk[J];
     for (int64_t t = s.tcolptr[J]; t < s.tcolptr[J + 1]; ++t) {
@@ -251,7 +252,8 @@ int analyze(const d3m_pattern* pat, const int32_t* perm_in, int b, bool build_ta
       // becomes ready last (it is on the critical path), the others earlier; the source blocks
       // before it go seg_group to a segment
       const int nib = J - s.tstart[q];
-      nseg[t] = (int32_t)((ks.size() + seg_group - 1) / seg_group) + (nib >= 2 ? 2 : nib);
+      nsrc[t] = (int32_t)((ks.size() + seg_group - 1) / seg_group);
+      nseg[t] = nsrc[t] + (nib >= 2 ? 2 : nib);
     }
   }
   for (int64_t t = 0; t < ntiles; ++t) kl_ptr[t + 1] += kl_ptr[t];
@@ -262,7 +264,30 @@ int analyze(const d3m_pattern* pat, const int32_t* perm_in, int b, bool build_ta
   std::vector<uint8_t> offd(ntiles, 0);
   for (int J = 0; J < s.NT; ++J)
     for (int64_t t = s.tcolptr[J]; t < s.tcolptr[J + 1]; ++t) offd[t] = (s.trow[t] != J);
-  auto n_upd = [&](int64_t t) -> int64_t { return offd[t] ? nseg[t] : std::max(0, nseg[t] - 1); };
+  auto n_seg_upd = [&](int64_t t) -> int64_t { return offd[t] ? nseg[t] : std::max(0, nseg[t] - 1); };
+  // pairs: leader (I, J) with J at an even offset in block q, follower (I, J + 1) in the same
+  // block; both have the same source blocks, so the first nsrc segments coincide
+  std::vector<int64_t> partner(ntiles, -1), leader_of(ntiles, -1);
+  std::vector<int32_t> npair(ntiles, 0);
+  if (pair_updates) {
+    for (int J = 0; J + 1 < s.NT; ++J) {
+      const int q = s.tblk[J];
+      if ((J - s.tstart[q]) % 2 != 0 || J + 1 >= s.tstart[q + 1]) continue;
+      for (int64_t t = s.tcolptr[J]; t < s.tcolptr[J + 1]; ++t) {
+        const int I = s.trow[t];
+        if (I < J + 1 || nsrc[t] == 0) continue;
+        const int64_t t2 = s.tile_of(I, J + 1);
+        if (t2 < 0) continue;
+        const int np = (int)std::min<int64_t>(nsrc[t], std::min(n_seg_upd(t), n_seg_upd(t2)));
+        if (np <= 0) continue;
+        partner[t] = t2;
+        leader_of[t2] = t;
+        npair[t] = npair[t2] = np;
+      }
+    }
+  }
+  // update TASKS of a tile: a follower's paired segments run in its leader's tasks
+  auto n_upd = [&](int64_t t) -> int64_t { return n_seg_upd(t) - (leader_of[t] >= 0 ? npair[t] : 0); };
   int64_t nupd = 0;
   for (int64_t t = 0; t < ntiles; ++t) nupd += n_upd(t);
   const int64_t ntask = ntiles + nupd;
@@ -277,6 +302,15 @@ int analyze(const d3m_pattern* pat, const int32_t* perm_in, int b, bool build_ta
     for (int64_t t = 0; t < ntiles; ++t)
       if (n_upd(t) > 0) { upd_first[t] = nextu; nextu += n_upd(t); }
   }
+  // accumulator slots: every tile with at least one update segment
+  std::vector<int32_t> sidx_of(ntiles, -1);
+  for (int64_t t = 0; t < ntiles; ++t)
+    if (n_seg_upd(t) > 0) sidx_of[t] = (int32_t)(s.n_acc++);
+  // task id of update segment sg of tile t (paired segments of a follower: its leader's task)
+  auto upd_id = [&](int64_t t, int sg) -> int64_t {
+    if (leader_of[t] >= 0) return sg < npair[t] ? upd_first[leader_of[t]] + sg : upd_first[t] + (sg - npair[t]);
+    return upd_first[t] + sg;
+  };
   // dependencies per task id, then successor lists (CSR)
   std::vector<std::vector<int32_t>> tdeps(ntask);
   for (int J = 0; J < s.NT; ++J) {
@@ -290,7 +324,8 @@ int analyze(const d3m_pattern* pat, const int32_t* perm_in, int b, bool build_ta
       sb.push_back(w);
       auto push = [&](int K) {
         int64_t a = s.tile_of(I, K), bb = s.tile_of(J, K);
-        s.klist[w++] = KEntry{(int32_t)a, (int32_t)bb, K, 0};
+        const int64_t b2 = partner[t] >= 0 ? s.tile_of(J + 1, K) : -1;
+        s.klist[w++] = KEntry{(int32_t)a, (int32_t)bb, K, (int32_t)b2};
       };
       for (size_t a = 0; a < ks.size(); ++a) {
         for (int K = s.tstart[ks[a]]; K < s.tstart[ks[a] + 1]; ++K) push(K);
@@ -325,25 +360,43 @@ int analyze(const d3m_pattern* pat, const int32_t* perm_in, int b, bool build_ta
       const int32_t* it = std::lower_bound(first, last, srow);
       if (it != last && *it == srow) base.k_off = s.kblk_off[s.colptr[scol] + (it - first)];
       base.flags = (I == J ? TF_DIAG : 0) | (p == q ? TF_SAME_BLOCK : 0);
-      const int nu = (int)n_upd(t);                 // update tasks of this tile
-      base.sidx = nu > 0 ? (int32_t)(s.n_acc++) : -1;
+      const int nu = (int)n_seg_upd(t);             // update segments of this tile
+      base.sidx = sidx_of[t];
+      base.tile2 = -1;
+      base.c0_2 = base.cv2 = 0;
+      base.sidx2 = -1;
       auto seg_deps = [&](int sg, std::vector<int32_t>& d) {
         for (int64_t e = sb[sg]; e < sb[sg + 1]; ++e) {
           d.push_back(s.klist[e].a_tile);
           if (I != J) d.push_back(s.klist[e].b_tile);
         }
       };
-      // update tasks: segments 0..nu-1, chained
-      for (int sg = 0; sg < nu; ++sg) {
-        const int64_t id = upd_first[t] + sg;
+      // update tasks: segments 0..nu-1, chained (a follower's first npair segments are its
+      // leader's paired tasks, built there)
+      const int sg0 = leader_of[t] >= 0 ? npair[t] : 0;
+      for (int sg = sg0; sg < nu; ++sg) {
+        const int64_t id = upd_id(t, sg);
         TileTask T = base;
         T.kl_off = sb[sg];
         T.nk = (int32_t)(sb[sg + 1] - sb[sg]);
         T.flags |= TF_UPDATE | (sg > 0 ? TF_S_IN : 0);
-        s.tasks[id] = T;
         auto& d = tdeps[id];
         seg_deps(sg, d);
-        if (sg > 0) d.push_back((int32_t)(id - 1));
+        if (partner[t] >= 0 && sg < npair[t]) {
+          // paired segment: the follower (I, J + 1) takes the same L_IK tiles and W_{J+1,K}
+          const int64_t t2 = partner[t];
+          T.flags |= TF_PAIR;
+          T.tile2 = (int32_t)t2;
+          T.c0_2 = (J + 1 - s.tstart[q]) * b;
+          T.cv2 = std::min(b, s.m[q] - T.c0_2);
+          T.sidx2 = sidx_of[t2];
+          for (int64_t e = sb[sg]; e < sb[sg + 1]; ++e) {
+            if (s.klist[e].b2_tile < 0) return fail(err, "internal: paired segment without tile (J+1, K)");
+            d.push_back(s.klist[e].b2_tile);
+          }
+        }
+        if (sg > 0) d.push_back((int32_t)upd_id(t, sg - 1));
+        s.tasks[id] = T;
         s.ndeps[id] = (int32_t)d.size();
       }
       // final task: the remaining segment (diagonal tile only), then factor / triangular solve
@@ -356,7 +409,7 @@ int analyze(const d3m_pattern* pat, const int32_t* perm_in, int b, bool build_ta
         s.tasks[t] = T;
         auto& d = tdeps[t];
         if (has_seg) seg_deps(nu, d);
-        if (nu > 0) d.push_back((int32_t)(upd_first[t] + nu - 1));
+        if (nu > 0) d.push_back((int32_t)upd_id(t, nu - 1));
         if (I != J) d.push_back(s.diag_tile[J]);
         s.ndeps[t] = (int32_t)d.size();
       }
@@ -394,7 +447,7 @@ int analyze(const d3m_pattern* pat, const int32_t* perm_in, int b, bool build_ta
     for (int64_t id = 0; id < ntask; ++id) {
       const TileTask& T = s.tasks[id];
       const int k = (T.flags & TF_UPDATE) ? 0 : ((T.flags & TF_DIAG) ? 2 : 4);
-      cost[id] = cm[k] + cm[k + 1] * T.nk;
+      cost[id] = cm[k] + cm[k + 1] * T.nk * ((T.flags & TF_PAIR) ? 2 : 1);
     }
     std::vector<int32_t> indeg(s.ndeps.begin(), s.ndeps.end()), order;
     order.reserve(ntask);
@@ -408,6 +461,7 @@ int analyze(const d3m_pattern* pat, const int32_t* perm_in, int b, bool build_ta
         if (--indeg[v] == 0) order.push_back(v);
       }
     }
+    if ((int64_t)order.size() != ntask) return fail(err, "internal: the task graph has a cycle");
     double cp = 0.0;
     for (int64_t q = (int64_t)order.size() - 1; q >= 0; --q) {
       const int32_t t = order[q];

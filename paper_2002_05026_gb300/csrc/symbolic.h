@@ -16,6 +16,7 @@ enum : int32_t {
   TF_UPDATE = 4,      // partial-update task (else: the tile's final task)
   TF_S_IN = 8,        // start from the tile's accumulator S (else from K_IJ)
   TF_PRIO = 16,       // on or near the critical path: served from the priority lane
+  TF_PAIR = 32,       // update task over two tiles (I, J) and (I, J + 1) that share the L_IK operand
 };
 
 // One task of the factorization DAG.  The paper's task model (Sec. II: one task per nonzero
@@ -38,12 +39,16 @@ struct TileTask {
   int32_t rv, cv;      // valid rows / columns (the rest is padding up to the tile edge)
   int32_t flags;       // TF_* bits
   int32_t sidx;        // accumulator slot of the tile, -1 if it has a single segment
+  // TF_PAIR: the second tile (I, J + 1), its first column inside block (p, q), valid columns and
+  // accumulator slot; its K-list entries are those of the first tile with b2_tile = (J + 1, K)
+  int32_t tile2, c0_2, cv2, sidx2;
 };
-static_assert(sizeof(TileTask) == 64, "TileTask layout");
+static_assert(sizeof(TileTask) == 80, "TileTask layout");
 
-// One K-list entry: S_IJ -= L_IK D_K L_JK^T uses tiles a = (I, K), b = (J, K), column K.
+// One K-list entry: S_IJ -= L_IK D_K L_JK^T uses tiles a = (I, K), b = (J, K), column K; in a
+// paired segment b2 = (J + 1, K) for the second tile (else -1).
 struct KEntry {
-  int32_t a_tile, b_tile, kcol, pad;
+  int32_t a_tile, b_tile, kcol, b2_tile;
 };
 
 // One solve gather item: partial = L(tile) * y(src tile) (forward) or L(tile)^T * w(src)
@@ -124,9 +129,11 @@ struct Symbolic {
 // per_k * nk (nk = tile products of the task) for update tasks (task_cost[0], [1]), diagonal
 // final tasks ([2], [3]) and off-diagonal final tasks ([4], [5]), in any common unit; nullptr or
 // all zeros = the built-in model.
+// pair_updates: the source-block update segments of tiles (I, J) and (I, J + 1) (J at an even
+// tile offset in its block) become one TF_PAIR task that reads each L_IK tile once for both.
 int analyze(const d3m_pattern* pat, const int32_t* perm, int b, bool build_tasks,
             Symbolic& s, std::string& err, double prio_slack = 0.08, int seg_group = 1,
-            const double* task_cost = nullptr, int gather_group = 1);
+            const double* task_cost = nullptr, int gather_group = 1, bool pair_updates = false);
 
 // Grid nested dissection (see d3m_order_grid_nd).
 int order_grid_nd(int nx, int ny, int nz, std::vector<int32_t>& perm);
