@@ -1,4 +1,5 @@
 // C ABI of the D3M dual-system solver (declarations and contracts in include/d3m.h).
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -139,6 +140,11 @@ struct d3m_ctx {
   cudaStream_t cap = nullptr;
   bool capturing = false;
   cudaStream_t side = nullptr;       // second stream of a factorization (norm and split of K)
+  // upload of a host K while the factorization runs (tensor-core engines, page-locked K)
+  cudaStream_t kup = nullptr;
+  cudaEvent_t ev_kup0 = nullptr, ev_kup1 = nullptr;
+  int32_t* k_arrived = nullptr;      // blocks uploaded so far, in the analysis' upload order
+  bool kup_ok = false;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   struct Graph { const void* src; int nrhs, accumulate; cudaGraphExec_t exec; int64_t launches; };
   std::vector<Graph> g_factor, g_solve;
@@ -212,6 +218,32 @@ int upload(d3m_ctx* h, T** dst, const std::vector<T>& v) {
   if (!*dst) return set_err(h, D3M_ERR_OOM, "cudaMalloc failed (" + std::to_string(v.size() * sizeof(T)) + " bytes)");
   if (!v.empty()) CUDA_TRY(h, cudaMemcpy(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
   return D3M_OK;
+}
+
+// page-locked (or registered) host memory, which the copy engines read asynchronously
+static bool is_pinned_host_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeHost;
+}
+
+typedef CUresult (*WriteValue32Fn)(CUstream, CUdeviceptr, cuuint32_t, unsigned int);
+static WriteValue32Fn write_value32() {
+  static WriteValue32Fn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    cudaDriverEntryPointQueryResult q;
+    void* f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuStreamWriteValue32", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (WriteValue32Fn)f;
+    cudaGetLastError();
+  }
+  return fn;
 }
 
 bool is_device_ptr(const void* p) {
@@ -467,6 +499,19 @@ static int create_impl(d3m_handle* out, const d3m_pattern* pat, const int32_t* p
     int rc_ = upload(h, &ptr, vec);             \
     if (rc_ != D3M_OK) return rc_;              \
   } while (0)
+  // upload stream of a host K (tensor-core engines): its progress counter is written by stream
+  // memory operations, which the persistent factorization polls; without them a host K is
+  // copied before the factorization starts
+  if (h->tc && write_value32()) {
+    ALLOC(h->k_arrived, int32_t, 1);
+    if (cudaStreamCreateWithFlags(&h->kup, cudaStreamNonBlocking) == cudaSuccess &&
+        cudaEventCreateWithFlags(&h->ev_kup0, cudaEventDisableTiming) == cudaSuccess &&
+        cudaEventCreateWithFlags(&h->ev_kup1, cudaEventDisableTiming) == cudaSuccess &&
+        write_value32()((CUstream)h->kup, (CUdeviceptr)h->k_arrived, 0u, 0u) == CUDA_SUCCESS &&
+        cudaStreamSynchronize(h->kup) == cudaSuccess)
+      h->kup_ok = true;
+    cudaGetLastError();
+  }
   // factorization (h->K, the copy target of a host K, is allocated by the first call that needs it)
   UPLOAD(h->tasks, S.tasks);
   UPLOAD(h->klist, S.klist);
@@ -837,8 +882,25 @@ static int enqueue_factor(d3m_ctx* h, const void* Kin, bool kdev, cudaStream_t s
   // a (16-byte aligned) device K is read in place by the two kernels that use it (the
   // factorization and the norm/split of K, both below); a host K is copied first
   const double2* Ksrc = h->K;
+  // a page-locked host K is uploaded on a stream of its own in the analysis' order (the blocks of
+  // the first columns to be eliminated first) while the factorization runs; a task that reads a
+  // block waits for it
+  const bool kup = !kdev && h->kup_ok && !h->capturing && is_pinned_host_ptr(Kin);
   if (kdev && ((uintptr_t)Kin & 15) == 0) Ksrc = static_cast<const double2*>(Kin);
-  else CUDA_TRY(h, cudaMemcpyAsync(h->K, Kin, kbytes, kdev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+  else if (!kup) CUDA_TRY(h, cudaMemcpyAsync(h->K, Kin, kbytes, kdev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+  if (kup) {
+    CUDA_TRY(h, cudaMemsetAsync(h->k_arrived, 0, sizeof(int32_t), st));
+    CUDA_TRY(h, cudaEventRecord(h->ev_kup0, st));
+    CUDA_TRY(h, cudaStreamWaitEvent(h->kup, h->ev_kup0, 0));
+    const double2* Kh = static_cast<const double2*>(Kin);
+    for (size_t r = 0; r < S.kc_off.size(); ++r) {
+      CUDA_TRY(h, cudaMemcpyAsync(h->K + S.kc_off[r], Kh + S.kc_off[r], (size_t)S.kc_len[r] * sizeof(double2),
+                                  cudaMemcpyHostToDevice, h->kup));
+      if (write_value32()((CUstream)h->kup, (CUdeviceptr)h->k_arrived, (cuuint32_t)S.kc_seq_end[r], 0u) != CUDA_SUCCESS)
+        return set_err(h, D3M_ERR_CUDA, "cuStreamWriteValue32 failed during the upload of K");
+    }
+    CUDA_TRY(h, cudaEventRecord(h->ev_kup1, h->kup));
+  }
   // reset the task graph state
   CUDA_TRY(h, cudaMemcpyAsync(h->cnt, h->ndeps, ntiles * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
   CUDA_TRY(h, cudaMemsetAsync(h->ready, 0xff, ntiles * sizeof(int32_t), st));
@@ -869,6 +931,7 @@ static int enqueue_factor(d3m_ctx* h, const void* Kin, bool kdev, cudaStream_t s
   p.opA = h->opA;
   p.opB = h->opB;
   p.opS = h->opS;
+  p.k_arrived = kup ? h->k_arrived : nullptr;
   p.Sacc = h->Sacc;
   p.trace = h->trace;
   p.timeout_ns = h->opt.timeout_ns;
@@ -883,6 +946,7 @@ static int enqueue_factor(d3m_ctx* h, const void* Kin, bool kdev, cudaStream_t s
   if (rc) return set_err(h, D3M_ERR_CUDA, std::string("factor launch: ") + cudaGetErrorString((cudaError_t)rc));
   ev_end(h, d3m_ctx::EV_FACTOR, st);
   h->launches += 1;
+  if (kup) CUDA_TRY(h, cudaStreamWaitEvent(st, h->ev_kup1, 0));   // the whole of K before the kernels below
   // ||K_i||_inf and the digit planes of K (for the residual) on a second stream, concurrently
   // with the block inverses: the persistent factorization holds every SM, the smaller kernels
   // share them
@@ -1340,6 +1404,9 @@ void d3m_destroy(d3m_handle h) {
   if (!h) return;
   for (auto& g : h->g_factor) cudaGraphExecDestroy(g.exec);
   if (h->side) cudaStreamDestroy(h->side);
+  if (h->kup) cudaStreamDestroy(h->kup);
+  if (h->ev_kup0) cudaEventDestroy(h->ev_kup0);
+  if (h->ev_kup1) cudaEventDestroy(h->ev_kup1);
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
   if (h->ev_join) cudaEventDestroy(h->ev_join);
   for (auto& g : h->g_solve) cudaGraphExecDestroy(g.exec);

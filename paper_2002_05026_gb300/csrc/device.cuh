@@ -47,6 +47,7 @@ struct FactorParams {
   void* opA;             // tensor-core operand planes (bf16) of L tiles
   void* opB;             // tensor-core operand planes (bf16) of W tiles / T_J
   void* opS;             // TF32 engine: bf16 split planes of the L tiles for the solve's products, or nullptr
+  const int32_t* k_arrived;  // upload progress of a host K (stored blocks in upload order), or nullptr
   void* Sacc;            // [n_acc][b][b] partial Schur accumulators (complex, working precision)
   int64_t* trace;        // [ntasks][8] task records, or nullptr
   int64_t timeout_ns;
@@ -284,6 +285,21 @@ __device__ __forceinline__ void sched_complete(const FactorParams& p, int task) 
   asm volatile("fence.proxy.async.global;" ::: "memory");
   __syncthreads();
   if (threadIdx.x < 32) release_successors(p, task, threadIdx.x);
+}
+
+// A task that reads its stored K block while a host K is still being uploaded waits (bounded)
+// until the block has arrived: the upload stream raises *k_arrived past the block's sequence
+// number after its copy (all threads call; on expiry the factorization is aborted).
+__device__ __forceinline__ void wait_k_block(const FactorParams& p, int kseq, int task, uint64_t deadline) {
+  if (!p.k_arrived || kseq < 0) return;
+  while (ld_volatile(p.k_arrived) <= kseq) {
+    if (ld_volatile(&p.ctl->abort) || globaltimer_ns() > deadline) {
+      set_error(p.ctl, D3M_ERR_TIMEOUT, task);
+      return;
+    }
+    __nanosleep(256);
+  }
+  __threadfence();  // the block's data is read after the progress counter
 }
 
 __device__ __forceinline__ void record_pivot_stats(Ctl* ctl, float amin, float amax) {

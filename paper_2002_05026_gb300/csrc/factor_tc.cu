@@ -700,6 +700,7 @@ __global__ void __launch_bounds__(NTHR, 1)
     if (T.flags & TF_UPDATE) {
       // ------------------------------------------------------------ partial update task
       // (a paired task: the second tile from the accumulator at ACC2, with its own columns)
+      if (!s_in) wait_k_block(p, T.kseq, task, deadline);
       for (int u = 0; u < (pair ? 2 : 1); ++u) {
         TileTask Tu = T;
         if (u) {
@@ -725,6 +726,7 @@ __global__ void __launch_bounds__(NTHR, 1)
       }
     } else {
       // ------------------------------------------------------------ final task
+      if (!s_in) wait_k_block(p, T.kseq, task, deadline);
       // off-diagonal: prefetch the first two chunks of T_J (B operand of the TRSM product)
       if (!is_diag && tid == 0) {
         for (int c = 0; c < 2; ++c) {

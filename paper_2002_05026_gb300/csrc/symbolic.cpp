@@ -77,6 +77,35 @@ int analyze(const d3m_pattern* pat, const int32_t* perm_in, int b, bool build_ta
     s.perm[k] = f;
     s.inv[f] = k;
   }
+  // upload order of K: by the elimination position of the block's lower column, then of its row
+  {
+    std::vector<int64_t> ord(s.nnzb_K);
+    std::vector<std::pair<int, int>> key(s.nnzb_K);
+    for (int g = 0; g < N; ++g)
+      for (int64_t e = s.colptr[g]; e < s.colptr[g + 1]; ++e) {
+        const int a = s.inv[g], c = s.inv[s.rowidx[e]];
+        key[e] = {std::min(a, c), std::max(a, c)};
+      }
+    std::iota(ord.begin(), ord.end(), (int64_t)0);
+    std::stable_sort(ord.begin(), ord.end(), [&](int64_t x, int64_t y) { return key[x] < key[y]; });
+    s.kseq.assign(s.nnzb_K, 0);
+    s.kc_off.clear();
+    s.kc_len.clear();
+    s.kc_seq_end.clear();
+    for (int64_t q = 0; q < s.nnzb_K; ++q) {
+      const int64_t e = ord[q];
+      s.kseq[e] = (int32_t)q;
+      const int64_t off = s.kblk_off[e], len = s.kblk_off[e + 1] - s.kblk_off[e];
+      if (!s.kc_off.empty() && s.kc_off.back() + s.kc_len.back() == off && s.kc_len.back() < ((int64_t)1 << 22)) {
+        s.kc_len.back() += len;
+        s.kc_seq_end.back() = (int32_t)(q + 1);
+      } else {
+        s.kc_off.push_back(off);
+        s.kc_len.push_back(len);
+        s.kc_seq_end.push_back((int32_t)(q + 1));
+      }
+    }
+  }
   s.m.resize(N);
   for (int k = 0; k < N; ++k) s.m[k] = s.m_orig[s.perm[k]];
   s.xoff_orig.assign(N + 1, 0);
@@ -354,11 +383,15 @@ int analyze(const d3m_pattern* pat, const int32_t* perm_in, int b, bool build_ta
       base.k_tr = 0;
       if (fp < fq) { scol = fp; srow = fq; base.k_tr = 1; }
       base.k_off = -1;
+      base.kseq = -1;
       base.k_ld = s.m_orig[srow];
       const int32_t* first = s.rowidx.data() + s.colptr[scol];
       const int32_t* last = s.rowidx.data() + s.colptr[scol + 1];
       const int32_t* it = std::lower_bound(first, last, srow);
-      if (it != last && *it == srow) base.k_off = s.kblk_off[s.colptr[scol] + (it - first)];
+      if (it != last && *it == srow) {
+        base.k_off = s.kblk_off[s.colptr[scol] + (it - first)];
+        base.kseq = s.kseq[s.colptr[scol] + (it - first)];
+      }
       base.flags = (I == J ? TF_DIAG : 0) | (p == q ? TF_SAME_BLOCK : 0);
       const int nu = (int)n_seg_upd(t);             // update segments of this tile
       base.sidx = sidx_of[t];

@@ -42,8 +42,10 @@ struct TileTask {
   // TF_PAIR: the second tile (I, J + 1), its first column inside block (p, q), valid columns and
   // accumulator slot; its K-list entries are those of the first tile with b2_tile = (J + 1, K)
   int32_t tile2, c0_2, cv2, sidx2;
+  int32_t kseq;        // position of the stored K block in the upload order (-1: fill block)
+  int32_t pad_;
 };
-static_assert(sizeof(TileTask) == 80, "TileTask layout");
+static_assert(sizeof(TileTask) == 88, "TileTask layout");
 
 // One K-list entry: S_IJ -= L_IK D_K L_JK^T uses tiles a = (I, K), b = (J, K), column K; in a
 // paired segment b2 = (J + 1, K) for the second tile (else -1).
@@ -83,6 +85,12 @@ struct Symbolic {
   std::vector<int64_t> colptr;
   std::vector<int32_t> rowidx;
   std::vector<int64_t> kblk_off;             // [nnzb+1] element offsets
+  // upload order of the stored blocks (a host K is copied in this order while the factorization
+  // runs): blocks sorted by the elimination position of their lower column, merged into runs
+  // that are contiguous in storage; run r covers blocks up to sequence number kc_seq_end[r] - 1
+  std::vector<int32_t> kseq;                 // [nnzb] sequence number of each stored block
+  std::vector<int64_t> kc_off, kc_len;       // runs: element offset and length
+  std::vector<int32_t> kc_seq_end;
   std::vector<int32_t> m_orig;               // block sizes, caller numbering
 
   // tile level

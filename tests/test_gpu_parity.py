@@ -174,6 +174,31 @@ def test_host_buffers(torch_cuda):
     assert _fwd_err(X, O.block_solve(F, B)) <= 1e-9
 
 
+@pytest.mark.parametrize("prec", ["bf16x3", "tf32"])
+def test_host_k_uploaded_during_factorization(torch_cuda, prec):
+    # a page-locked host K is uploaded block by block while the factorization runs (tasks wait for
+    # their block); a pageable one is copied first.  Both factor exactly like a device K: the same
+    # arithmetic in the same order, so the solutions are bitwise equal.
+    from paper_2002_05026_gb300 import D3M
+    p, pm, Kb, F = _setup((3, 3, 1), 200, seed=6)
+    B = synth.rhs(5, p.n, 3)
+    Bd = torch_cuda.from_numpy(np.ascontiguousarray(B)).cuda()
+    ref = D3M(p.colptr, p.rowidx, m=p.m, perm=pm, precision=prec, max_nrhs=3)
+    ref.factor(torch_cuda.from_numpy(p.blocks_numpy()).cuda())
+    Xref = ref.solve(Bd).cpu().numpy()
+    ref.close()
+    assert _fwd_err(Xref, O.block_solve(F, B)) <= 1e-9
+    Kpage = torch_cuda.from_numpy(p.blocks_numpy())
+    for Kh in (Kpage.pin_memory(), Kpage):
+        s = D3M(p.colptr, p.rowidx, m=p.m, perm=pm, precision=prec, max_nrhs=3)
+        for _ in range(2):                       # the second call uploads into the same buffer
+            s.factor(Kh)
+            X = s.solve(Bd).cpu().numpy()
+            assert s.info()["status"] == 0
+            assert np.array_equal(X, Xref)
+        s.close()
+
+
 def test_zero_pivot_reported(torch_cuda):
     from paper_2002_05026_gb300 import D3M, D3MError
     p, pm, Kb, F = _setup((2, 2, 1), 64, seed=4)
