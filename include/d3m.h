@@ -222,9 +222,15 @@ int d3m_create_batch(d3m_handle* out, int32_t count, const d3m_pattern* pats,
  * d3m_info.instances entries.  Synchronizes `stream`. */
 int d3m_get_instance_omega(d3m_handle h, double* host_out, void* stream);
 
-/* Numeric factorization.  K: c128 lower blocks as described above (host or device).  A host K
- * is copied; a device K (16-byte aligned) is read in place, in stream order: it must not
- * change until the factorization has completed on `stream` (nothing reads it afterwards).
+/* Numeric factorization.  K: c128 lower blocks as described above (host or device).  A device
+ * K (16-byte aligned) is read in place, in stream order: it must not change until the
+ * factorization has completed on `stream` (nothing reads it afterwards).  A host K is copied
+ * into the handle's buffer: a page-locked one (cudaHostAlloc / cudaHostRegister), with the
+ * tensor-core engines, block by block in elimination order on a stream of the handle while the
+ * factorization runs (a task waits for its block; the copy is complete before the kernels
+ * that follow the factorization on `stream`), any other one before the factorization starts.
+ * Either way the host buffer must stay unchanged until the factorization has completed on
+ * `stream`.
  * One persistent kernel then factors K, its blocks pulling ready tile tasks from a device
  * queue with atomic dependency counters (Sec. II task model, Fig. 1(c)).
  * D3M_ERR_PIVOT if a pivot falls below the breakdown threshold, D3M_ERR_TIMEOUT if a device
