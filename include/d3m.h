@@ -31,7 +31,7 @@
  *     loop inside d3m_solve, which reads one convergence word per iteration.
  *
  * Ownership: the caller owns every buffer it passes and the stream.  The library owns the
- * factors, a float-pair split of K (kept for the FP64 residual), a copy buffer for a host K
+ * factors, the base-64 digit planes of K (kept for the FP64-accurate residual), a copy buffer for a host K
  * (allocated by the first d3m_factor that passes one), the task graph and its workspaces, from
  * d3m_create until d3m_destroy.  A handle is not thread-safe; use one per host thread.
  *
@@ -70,7 +70,10 @@ enum {
                             FP64 residual + iterative refinement */
   D3M_MIXED_TF32 = 3     /* complex64 factors; Schur/TRSM products on tcgen05 tensor cores as one
                             kind::tf32 product (operands rounded to tf32, 10-bit mantissa) with
-                            FP32 accumulation in TMEM; FP64 residual + iterative refinement */
+                            FP32 accumulation in TMEM, the source-block updates of tiles (I, J)
+                            and (I, J+1) in one task sharing L_IK; the solve's products use bf16
+                            split planes of L written beside the tf32 ones; FP64 residual +
+                            iterative refinement */
 };
 
 typedef struct {
