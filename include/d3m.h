@@ -98,7 +98,7 @@ typedef struct {
                                memory; one refinement step of a solve) into a CUDA graph on
                                first use and replay it afterwards; default 0 */
   int32_t seg_group;        /* source blocks whose Schur updates of a tile form one update task
-                               (0 = default: 8 in the mixed modes, 1 in FP64; 1 = a task per
+                               (0 = default: 32 with TF32, 8 in the other mixed modes, 1 in FP64; 1 = a task per
                                source block, the earliest start) */
   double prio_slack;        /* tasks whose estimated slack is within prio_slack x the critical
                                path are served first by the device scheduler (default 0.08;

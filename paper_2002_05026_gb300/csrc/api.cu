@@ -398,7 +398,7 @@ int d3m_analyze_opts(const d3m_pattern* pat, const int32_t* perm, const d3m_opti
   if (o.tile != 0 && o.tile != b)
     return set_err(nullptr, D3M_ERR_INVALID, "tile must be 0 or " + std::to_string(b) + " for this precision");
   if (!(o.prio_slack >= 0)) o.prio_slack = 0.08;
-  if (o.seg_group <= 0) o.seg_group = fp64 ? 1 : 8;
+  if (o.seg_group <= 0) o.seg_group = fp64 ? 1 : (prec == D3M_MIXED_TF32 ? 32 : 8);
   Symbolic S;
   std::string err;
   int rc = analyze(pat, perm, b, true, S, err, o.prio_slack, o.seg_group, o.task_cost, tc ? 16 : 1,
@@ -454,10 +454,11 @@ static int create_impl(d3m_handle* out, const d3m_pattern* pat, const int32_t* p
   }
   std::string err;
   // mixed precision: a tile's Schur updates from up to 8 source blocks form one update task (the
-  // per-task epilogue through the accumulator dominates short segments); FP64 is DFMA bound and
-  // keeps one task per source block
-  if (h->opt.seg_group <= 0) h->opt.seg_group = h->fp64 ? 1 : 8;
-  // the tensor-core gathers of the solve (split-BF16x3 engine) sum up to 16 items of one
+  // per-task epilogue through the accumulator dominates short segments), 32 with TF32 (its
+  // factorization is bound by DRAM, and every segment boundary writes and reads back the tile's
+  // accumulator); FP64 is DFMA bound and keeps one task per source block
+  if (h->opt.seg_group <= 0) h->opt.seg_group = h->fp64 ? 1 : (h->tf32 ? 32 : 8);
+  // the tensor-core gathers of the solve (split-BF16x3 products, both engines) sum up to 16 items of one
   // destination in tensor memory
   const int ggroup = h->tc ? 16 : 1;
   int rc = analyze(pat, perm, h->b, true, h->S, err, h->opt.prio_slack, h->opt.seg_group, h->opt.task_cost, ggroup,
