@@ -39,7 +39,8 @@ def signature(instances, nrhs: int) -> str:
 def fit_task_costs(trace: np.ndarray) -> list:
     """Duration model cost = base + per_k * nk (ns) for the three task kinds of the factorization
     (update, diagonal final, off-diagonal final), least squares over the traced tasks
-    (trace rows: start_ns, end_ns, sm, flags | tile << 8 | nk << 40, ...).  The paper weights its
+    (trace rows: start_ns, end_ns, sm, flags | tile << 8 | nk << 40, ...; a paired update task,
+    flag 32, counts 2 nk tile products).  The paper weights its
     dual tasks with benchmarked GEMM, sytrf and triSolve times (Sec. II); here the benchmark is a
     traced factorization of the actual pattern."""
     ok = (trace[:, 0] > 0) & (trace[:, 1] >= trace[:, 0])
@@ -47,6 +48,7 @@ def fit_task_costs(trace: np.ndarray) -> list:
     dur = (t[:, 1] - t[:, 0]).astype(np.float64)
     flags = t[:, 3] & 0xFF
     nk = (t[:, 3] >> 40).astype(np.float64)
+    nk = np.where(flags & 32, 2.0 * nk, nk)      # a paired update task does nk products for two tiles
     kind = np.where(flags & 4, 0, np.where(flags & 1, 1, 2))
     out = []
     for k in range(3):

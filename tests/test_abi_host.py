@@ -159,3 +159,53 @@ def test_pivoting_needs_a_simt_engine(lib):
         rc = lib.d3m_create(ctypes.byref(h), ctypes.byref(pat), None, ctypes.byref(opt), None)
         assert rc == _abi.D3M_ERR_INVALID and not h
         assert b"SIMT" in lib.d3m_last_error(None)
+
+
+@pytest.mark.parametrize("g,m", [((2, 2, 1), 512), ((3, 3, 1), 300), ((3, 3, 3), 200), ((8, 8, 1), 512)])
+def test_tf32_paired_task_graph(lib, g, m):
+    # the TF32 engine runs the source-block update segments of tiles (I, J) and (I, J + 1) as one
+    # task that reads each L_IK tile once for both; the analysis builds that graph (it rejects a
+    # cyclic one) with the same tiles, tile updates and flops as the unpaired graph, and the
+    # shared operands remove dependency edges
+    from paper_2002_05026_gb300 import d3m_analyze_opts, d3m_default_options
+    colptr, rowidx = synth.lower_pattern(*g)
+    perm = O.nd_order(*g)
+    got = {}
+    for prec in (_abi.D3M_MIXED_BF16X3, _abi.D3M_MIXED_TF32):
+        opt = d3m_default_options()
+        opt.precision = prec
+        opt.seg_group = 8
+        got[prec] = d3m_analyze_opts(colptr, rowidx, m=m, perm=perm, opt=opt)
+    a, b = got[_abi.D3M_MIXED_BF16X3], got[_abi.D3M_MIXED_TF32]
+    for key in ("ntiles", "ntile_updates", "factor_flops", "etree_depth"):
+        assert a[key] == b[key], key
+    assert b["ndep_edges"] < a["ndep_edges"]
+
+
+def test_bench_engine_choice(lib):
+    # bench.py --precision auto: TF32 for a throughput-bound factorization (>= 5e13 flops), the
+    # split-BF16x3 engine for a smaller, critical-path-bound one; an explicit choice is kept
+    import argparse
+    import bench
+    for wname, want in (("grid6x6x6_m512", "tf32"), ("grid8x8_m512", "bf16x3"), ("grid2x2_m64", "bf16x3")):
+        w = synth.WORKLOADS[wname]
+        colptr, rowidx = synth.lower_pattern(w["nx"], w["ny"], w["nz"])
+        perm = O.nd_order(w["nx"], w["ny"], w["nz"])
+        assert bench.resolve_precision(argparse.Namespace(precision="auto"), colptr, rowidx, w["m"], perm) == want
+        assert bench.resolve_precision(argparse.Namespace(precision="simt32"), colptr, rowidx, w["m"], perm) == "simt32"
+
+
+def test_task_cost_fit_counts_paired_products():
+    # the autotuner's duration model from a task trace: cost = base + per * nk per task kind, where
+    # a paired update task (flag 32) does 2 nk tile products
+    from paper_2002_05026_gb300.autotune import fit_task_costs
+    rows = []
+    t = 1000
+    for nk in range(1, 9):
+        for flags, base, per, mult in ((4, 1500.0, 400.0, 1), (4 | 32, 1500.0, 400.0, 2), (1, 60000.0, 250.0, 1),
+                                       (0, 9000.0, 120.0, 1)):
+            dur = base + per * mult * nk
+            rows.append([t, t + int(dur), 0, flags | (7 << 8) | (nk << 40), 0, 0, 0, 0, 0, 0])
+            t += 10
+    got = fit_task_costs(np.array(rows, dtype=np.int64))
+    assert np.allclose(got, [1500.0, 400.0, 60000.0, 250.0, 9000.0, 120.0], rtol=1e-6, atol=1.0)
