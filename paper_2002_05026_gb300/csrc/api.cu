@@ -1404,6 +1404,8 @@ const char* d3m_last_error(d3m_handle h) {
 void d3m_destroy(d3m_handle h) {
   if (!h) return;
   for (auto& g : h->g_factor) cudaGraphExecDestroy(g.exec);
+  if (h->side) cudaStreamSynchronize(h->side);   // work still running on the library's streams
+  if (h->kup) cudaStreamSynchronize(h->kup);
   if (h->side) cudaStreamDestroy(h->side);
   if (h->kup) cudaStreamDestroy(h->kup);
   if (h->ev_kup0) cudaEventDestroy(h->ev_kup0);
