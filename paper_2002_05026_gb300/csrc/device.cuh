@@ -8,7 +8,9 @@
 // A block claims a slot, then waits (bounded by timeout_ns of %globaltimer, with backoff)
 // until the slot is filled.  Every slot < ntasks is eventually filled while some block
 // runs a task, so the only way a wait expires is a broken graph or an abort; then the block
-// records D3M_ERR_TIMEOUT, raises `abort`, and returns.
+// records D3M_ERR_TIMEOUT, raises `abort`, and returns.  A block that is still running a task
+// may also take a task that is already pushed (sched_claim_normal), never one that is not, so
+// it cannot wait on work that depends on its own.
 // Memory order: data writes -> __syncthreads -> fence (release) -> atomicSub on successors;
 // the pusher fences again before publishing the id; the consumer fences after reading it
 // (acquire) and reads producer data with L1-bypassing loads or the TMA (async proxy).

@@ -19,12 +19,15 @@
 // Data movement: every finished L tile is written once, by its owner, as operand planes
 // (opA: L_IJ; opB: W_IJ = L_IJ D_J, or T_J = D_J^{-1} L_JJ^{-1} for a diagonal tile), row-major
 // with the K index contiguous: bf16 [hi_r, hi_i, lo_r, lo_i] / [hi, lo] x [W_r, W_i] (512 rows of
-// 256 bytes), or tf32 [r, i] (256 rows of 512 bytes), 128 KB per tile either way.  TMA tiled
-// loads (64-byte swizzle) stage K chunks of 64-byte rows (32 bf16 or 16 tf32 elements) into
-// shared memory for the MMAs.
+// 256 bytes), or tf32 [r, i] (256 rows of 512 bytes), 128 KB per tile either way; the TF32
+// engine also writes bf16 split planes of every off-diagonal L tile (opS) for the solve.  TMA
+// tiled loads (64-byte swizzle) stage K chunks of 64-byte rows (32 bf16 or 16 tf32 elements) into
+// shared memory for the MMAs.  A paired update task (TF32 engine) stages one A chunk with the B
+// chunks of two tiles (I, J) and (I, J + 1) and accumulates them in TMEM columns 0-255 and 256-511.
 //
-// Roles inside a 256-thread block: warp 0 lane 0 issues TMA loads, warp 1 lane 0 issues MMAs,
-// all 8 warps run the epilogues (warp w reads TMEM lanes 32*(w%4).., columns half w/4).
+// Roles inside a 256-thread block: warp 0 lane 0 issues TMA loads, warp 1 lane 0 issues MMAs
+// (and claims the block's next ready task while they run), all 8 warps run the epilogues (warp w
+// reads TMEM lanes 32*(w%4).., columns half w/4), warp 2 releases a finished task's successors.
 // Diagonal tiles are factored (unpivoted LDL^T) and inverted with SIMT FP32 in shared memory.
 #include <cuda.h>
 #include <cuda_bf16.h>
