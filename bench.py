@@ -78,18 +78,29 @@ def measured_peaks():
 
 # ------------------------------------------------------------------ recorded DRAM traffic
 # Per-launch DRAM bytes of a kernel come from an ncu capture (profiles/traffic_<workload>.txt,
-# lines "<kernel>:<engine> <bytes per launch> <sha1 of its source files>"); a number whose kernel
+# lines "<kernel>:<engine> <bytes per launch> <sha1 of the code of its source files>"); a number whose kernel
 # sources have changed since the capture is not reported.
 TRAFFIC_SOURCES = {"factor_kernel": ("factor_tc.cu", "device.cuh"), "residual": ("resid_tc.cu",),
                    "solve_sweep": ("gather_tc.cu", "solve.cu")}
 
 
 def source_sha(kernel: str):
+    """SHA-1 of the code of a kernel's source files: comments, blank lines and trailing spaces
+    removed, so that an edit of the comments keeps a record valid and any change of code voids it."""
     import hashlib
+    import re
     h = hashlib.sha1()
     for src in TRAFFIC_SOURCES[kernel]:
-        with open(os.path.join(ROOT, "paper_2002_05026_gb300", "csrc", src), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(ROOT, "paper_2002_05026_gb300", "csrc", src)) as f:
+            text = f.read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        code = []
+        for line in text.splitlines():
+            # a // comment outside a string literal (the sources have no "//" inside strings)
+            line = line.split("//", 1)[0].rstrip()
+            if line:
+                code.append(line)
+        h.update("\n".join(code).encode())
     return h.hexdigest()
 
 
