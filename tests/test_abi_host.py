@@ -209,3 +209,28 @@ def test_task_cost_fit_counts_paired_products():
             t += 10
     got = fit_task_costs(np.array(rows, dtype=np.int64))
     assert np.allclose(got, [1500.0, 400.0, 60000.0, 250.0, 9000.0, 120.0], rtol=1e-6, atol=1.0)
+
+
+def test_recorded_traffic_follows_the_kernel_code(tmp_path):
+    # bench.py reports a kernel's DRAM traffic from profiles/traffic_<workload>.txt only while the
+    # record's hash matches the kernel's code: a comment edit keeps it, a code edit voids it
+    import bench
+    csrc = tmp_path / "paper_2002_05026_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    (tmp_path / "profiles").mkdir()
+    (csrc / "factor_tc.cu").write_text("// header\nint f() { return 1; }  // one\n")
+    (csrc / "device.cuh").write_text("/* block\n comment */\nint g();\n")
+    old_root = bench.ROOT
+    try:
+        bench.ROOT = str(tmp_path)
+        sha = bench.source_sha("factor_kernel")
+        (tmp_path / "profiles" / "traffic_w.txt").write_text(
+            "# a comment line with several words\nfactor_kernel:tf32 123 %s\n" % sha)
+        assert bench.recorded_traffic("w", "factor_kernel", "tf32") == 123.0
+        assert bench.recorded_traffic("w", "factor_kernel", "bf16x3") is None
+        (csrc / "factor_tc.cu").write_text("// another header\n\nint f() { return 1; }\n")
+        assert bench.recorded_traffic("w", "factor_kernel", "tf32") == 123.0
+        (csrc / "factor_tc.cu").write_text("int f() { return 2; }\n")
+        assert bench.recorded_traffic("w", "factor_kernel", "tf32") is None
+    finally:
+        bench.ROOT = old_root
